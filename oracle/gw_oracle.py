@@ -1,0 +1,331 @@
+"""FP64 CPU oracle for the Lanczos full-frequency GW hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.  It shares no code
+with the CUDA library and never calls it.
+
+Everything here is plain numpy float64, written for a reader checking it
+against the paper (Gao, Tang, Zhao, Chelikowsky, "Efficient Full-frequency GW
+Calculations using a Lanczos Method", arXiv 2310.20103).  Index names follow
+the code convention: ``t`` is the target orbital (the paper's m in
+Sigma_mm), ``m`` is the summed orbital (the paper's n in Eq. 10), ``vc`` the
+electron-hole pair, ``s`` a Casida eigenpair.
+
+Readings of the paper used below (each is listed with its reason in the
+design notes of the repository):
+  * the Casida matrix is C = (A-B)^1/2 (A+B) (A-B)^1/2 with A-B = diag(Delta)
+    and A+B = Delta + (c_K/2) K, i.e. C = Delta^2 + c_K Delta^1/2 K Delta^1/2,
+    with c_K = 4 by default (closed-shell spin sum) and K = L L^T;
+  * the sign factor eta and the energy in z belong to the summed orbital m;
+  * z_m = omega - eps_m - i eta_m delta (Eq. 11), and Eq. 11 equals
+    sum_s p_s^2 / (Omega_s (z_m + eta_m Omega_s)), which is Eq. 7 with
+    W^s_{tm} = p_s Omega_s^-1/2 (Eq. 9);
+  * a k-step Lanczos gives a k x k tridiagonal T_k (alpha_1..alpha_k on the
+    diagonal, beta_2..beta_k off it); Sigma follows from the Gauss rule of
+    T_k mapped through Omega = sqrt(theta) (Eq. 12 with D = C^1/2);
+  * the quasiparticle equation is E = eps_t + s_t + Re Sigma_t(E) (the paper
+    does not print it), solved by Newton from eps_t + s_t, falling back to
+    a bracketed bisection on the frequency grid.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "pair_energies", "occupation_sign", "casida_matrix", "apply_casida",
+    "coupling_vectors", "start_vectors", "casida_eigenpairs",
+    "closed_form_poles", "lanczos", "lanczos_poles", "sigma_from_poles",
+    "dsigma_from_poles", "sigma_closed_form", "sigma_lanczos", "qp_solve",
+    "solve_all_qp",
+]
+
+
+# --------------------------------------------------------------------------
+# Eq. 2-4: pair energies and the reduced Casida matrix
+# --------------------------------------------------------------------------
+def pair_energies(eps, n_v):
+    """Delta_vc = eps_c - eps_v, pair index vc = v * n_c + c.
+
+    Diagonal of A - B in Eq. 2-3 (the Coulomb terms cancel in A - B)."""
+    eps = np.asarray(eps, dtype=np.float64)
+    ev, ec = eps[:n_v], eps[n_v:]
+    return (ec[None, :] - ev[:, None]).reshape(-1)
+
+
+def occupation_sign(m, n_v):
+    """eta_m: +1 for an occupied orbital, -1 for an empty one (Eq. 7)."""
+    return np.where(np.asarray(m) < n_v, 1.0, -1.0)
+
+
+def casida_matrix(eps, n_v, L, kernel_factor=4.0):
+    """Dense C = Delta^2 + c_K Delta^1/2 (L L^T) Delta^1/2 (Eq. 4)."""
+    Delta = pair_energies(eps, n_v)
+    d = np.sqrt(Delta)
+    K = L @ L.T
+    H = kernel_factor * (d[:, None] * K * d[None, :])
+    H[np.diag_indices_from(H)] += Delta ** 2
+    return H
+
+
+def apply_casida(eps, n_v, L, X, kernel_factor=4.0):
+    """C applied to the rows of X ([n_vec, N_vc]) through the low-rank factor."""
+    Delta = pair_energies(eps, n_v)
+    d = np.sqrt(Delta)
+    Y = (X * d[None, :]) @ L          # L^T (Delta^1/2 x), one row per vector
+    U = Y @ L.T                       # L y
+    return (Delta ** 2)[None, :] * X + kernel_factor * d[None, :] * U
+
+
+# --------------------------------------------------------------------------
+# Start vectors |P_tm> (text after Eq. 8): (P)_vc = (tm|vc) (eps_c - eps_v)^1/2
+# --------------------------------------------------------------------------
+def coupling_vectors(L, M):
+    """(tm|vc) = sum_mu L[vc, mu] M^{tm}[mu]  ->  V[t, m, vc] (Eq. 16 fitted form)."""
+    return np.einsum("vu,tmu->tmv", L, M)
+
+
+def start_vectors(eps, n_v, V):
+    """b_tm = Delta^1/2 * V_tm, the vector |P_tm> of the text after Eq. 8."""
+    d = np.sqrt(pair_energies(eps, n_v))
+    return V * d
+
+
+# --------------------------------------------------------------------------
+# Closed form: Eq. 7-9 with the Casida eigenpairs
+# --------------------------------------------------------------------------
+def casida_eigenpairs(H):
+    """C Z^s = Z^s Omega_s^2 (Eq. 4).  Returns (Omega, Z).
+
+    Raises if C is not positive definite (Omega_s must be real, > 0)."""
+    theta, Z = np.linalg.eigh(H)
+    if theta.min() <= 0.0:
+        raise ValueError("Casida matrix is not positive definite")
+    return np.sqrt(theta), Z
+
+
+def closed_form_poles(wl, Omega=None, Z=None):
+    """Pole list of Sigma_t(omega) from the Casida eigenpairs.
+
+    For every target t, summed m and eigenpair s the pole is
+        W_tms / (omega - eps_m + eta_m Omega_s - i eta_m delta)      (Eq. 7)
+    with W_tms = (W^s_tm)^2 = p_s^2 / Omega_s, p_s = <P_tm|Z^s> (Eq. 9).
+    Returns arrays (pos, weight, eta) of shape [n_t, n_m * N_vc] where
+    pos = eps_m - eta_m Omega_s (the real part of the pole).
+    """
+    if Omega is None:
+        Omega, Z = casida_eigenpairs(casida_matrix(wl.eps, wl.n_v, wl.L, wl.kernel_factor))
+    b = start_vectors(wl.eps, wl.n_v, coupling_vectors(wl.L, wl.M))   # [n_t, n_m, N_vc]
+    p = b @ Z                                                          # [n_t, n_m, N_vc]
+    W = p ** 2 / Omega[None, None, :]
+    eps_m = wl.eps[wl.m_idx]
+    eta = occupation_sign(wl.m_idx, wl.n_v)
+    pos = eps_m[:, None] - eta[:, None] * Omega[None, :]               # [n_m, N_vc]
+    n_t = wl.n_t
+    pos = np.broadcast_to(pos, (n_t,) + pos.shape).reshape(n_t, -1)
+    etas = np.broadcast_to(eta[:, None], (wl.n_m, Omega.shape[0]))
+    etas = np.broadcast_to(etas, (n_t,) + etas.shape).reshape(n_t, -1)
+    return pos.copy(), W.reshape(n_t, -1), etas.copy()
+
+
+def sigma_from_poles(omega, pos, weight, eta, delta):
+    """Sigma(omega) = sum_p weight_p / (omega - pos_p - i eta_p delta)  (Eq. 7).
+
+    ``omega`` is a 1-D grid; pos/weight/eta are 1-D pole lists for one target.
+    Each term is evaluated as written; the sum runs over all poles."""
+    omega = np.asarray(omega, dtype=np.float64)
+    out = np.empty(omega.shape[0], dtype=np.complex128)
+    for i, w in enumerate(omega):
+        out[i] = np.sum(weight / ((w - pos) - 1j * eta * delta))
+    return out
+
+
+def dsigma_from_poles(omega, pos, weight, eta, delta):
+    """d Sigma / d omega of ``sigma_from_poles``."""
+    omega = np.atleast_1d(np.asarray(omega, dtype=np.float64))
+    out = np.empty(omega.shape[0], dtype=np.complex128)
+    for i, w in enumerate(omega):
+        den = (w - pos) - 1j * eta * delta
+        out[i] = -np.sum(weight / den ** 2)
+    return out
+
+
+def sigma_closed_form(wl):
+    """Sigma_t(omega_f) for every target on the workload grid, Eq. 7-9.
+
+    Returns complex [n_t, n_freq] and the per-target pole lists used."""
+    pos, W, eta = closed_form_poles(wl)
+    poles = [(pos[i], W[i], eta[i]) for i in range(wl.n_t)]
+    sig = np.stack([sigma_from_poles(wl.omega, *poles[i], wl.delta)
+                    for i in range(wl.n_t)])
+    return sig, poles
+
+
+# --------------------------------------------------------------------------
+# Lanczos tridiagonalisation (Eq. 13), run on C itself from |P_tm>
+# --------------------------------------------------------------------------
+def lanczos(apply_op, b, k, reorth=True, breakdown_tol=1e-13):
+    """k-step Lanczos from each row of ``b`` ([n_vec, N]).
+
+    Every row is an independent recurrence (own basis, own coefficients); the
+    rows are only processed side by side.  Step j:
+        w = C q_j - beta_j q_{j-1}
+        alpha_j = q_j . w ;  w = w - alpha_j q_j
+        (reorth) twice: w = w - Q_j (Q_j^T w)     (classical Gram-Schmidt)
+        beta_{j+1} = ||w|| ;  q_{j+1} = w / beta_{j+1}
+    A row stops (k_eff = j) when beta_{j+1} <= breakdown_tol * max_i |alpha_i|.
+
+    Returns alpha [n_vec, k], beta [n_vec, k] (beta[:, j] couples steps j and
+    j+1, i.e. the paper's b_{j+1}; beta[:, k-1] is the residual norm),
+    beta0 = ||b|| [n_vec] and k_eff [n_vec].
+    """
+    b = np.atleast_2d(np.asarray(b, dtype=np.float64))
+    n_vec, N = b.shape
+    k = int(min(k, N))
+    alpha = np.zeros((n_vec, k))
+    beta = np.zeros((n_vec, k))
+    beta0 = np.sqrt(np.einsum("vi,vi->v", b, b))
+    k_eff = np.full(n_vec, k, dtype=np.int64)
+    active = beta0 > 0.0
+    k_eff[~active] = 0
+    Q = np.zeros((k + 1, n_vec, N)) if reorth else None
+    q = np.where(active[:, None], b / np.where(active, beta0, 1.0)[:, None], 0.0)
+    q_prev = np.zeros_like(q)
+    beta_j = np.zeros(n_vec)
+    amax = np.zeros(n_vec)
+    for j in range(k):
+        if reorth:
+            Q[j] = q
+        w = apply_op(q) - beta_j[:, None] * q_prev
+        a = np.einsum("vi,vi->v", q, w)
+        w = w - a[:, None] * q
+        if reorth:
+            for _ in range(2):
+                h = np.einsum("jvi,vi->jv", Q[: j + 1], w)
+                w = w - np.einsum("jvi,jv->vi", Q[: j + 1], h)
+        bn = np.sqrt(np.einsum("vi,vi->v", w, w))
+        alpha[:, j] = np.where(active, a, 0.0)
+        amax = np.maximum(amax, np.abs(alpha[:, j]))
+        beta[:, j] = np.where(active, bn, 0.0)
+        stop = active & (bn <= breakdown_tol * amax)
+        k_eff[stop] = j + 1
+        active = active & ~stop
+        q_prev = q
+        q = np.where(active[:, None], w / np.where(active, bn, 1.0)[:, None], 0.0)
+        beta_j = np.where(active, bn, 0.0)
+    return alpha, beta, beta0, k_eff
+
+
+def lanczos_poles(alpha, beta, beta0, k_eff):
+    """Gauss rule of one tridiagonal: nodes theta_j, weights beta0^2 u_1j^2.
+
+    Mapped to the D = C^1/2 spectrum (Eq. 12): Omega_j = sqrt(theta_j) and the
+    Eq. 7 weight p^2/Omega becomes beta0^2 u_1j^2 / Omega_j."""
+    ke = int(k_eff)
+    if ke == 0:
+        return np.zeros(0), np.zeros(0)
+    T = np.diag(alpha[:ke])
+    if ke > 1:
+        off = beta[: ke - 1]
+        T += np.diag(off, 1) + np.diag(off, -1)
+    theta, U = np.linalg.eigh(T)
+    if theta.min() <= 0.0:
+        raise ValueError("Lanczos tridiagonal is not positive definite")
+    Om = np.sqrt(theta)
+    return Om, beta0 ** 2 * U[0, :] ** 2 / Om
+
+
+def sigma_lanczos(wl, k=None, reorth=True, apply_op=None, coeffs=None):
+    """Sigma_t(omega_f) from k-step Lanczos on C for every (t, m) start vector.
+
+    Returns (sigma [n_t, n_freq], pole lists, (alpha, beta, beta0, k_eff))."""
+    k = wl.k if k is None else k
+    if coeffs is None:
+        b = start_vectors(wl.eps, wl.n_v, coupling_vectors(wl.L, wl.M))
+        b = b.reshape(wl.n_t * wl.n_m, -1)
+        if apply_op is None:
+            def apply_op(X):
+                return apply_casida(wl.eps, wl.n_v, wl.L, X, wl.kernel_factor)
+        coeffs = lanczos(apply_op, b, k, reorth=reorth)
+    alpha, beta, beta0, k_eff = coeffs
+    eta_all = occupation_sign(wl.m_idx, wl.n_v)
+    poles = []
+    for ti in range(wl.n_t):
+        P, Wt, E = [], [], []
+        for mi, m in enumerate(wl.m_idx):
+            v = ti * wl.n_m + mi
+            Om, wt = lanczos_poles(alpha[v], beta[v], beta0[v], k_eff[v])
+            P.append(wl.eps[m] - eta_all[mi] * Om)
+            Wt.append(wt)
+            E.append(np.full(Om.shape[0], eta_all[mi]))
+        poles.append((np.concatenate(P), np.concatenate(Wt), np.concatenate(E)))
+    sig = np.stack([sigma_from_poles(wl.omega, *poles[ti], wl.delta) for ti in range(wl.n_t)])
+    return sig, poles, coeffs
+
+
+# --------------------------------------------------------------------------
+# Quasiparticle equation (not printed in the paper; reading stated above)
+# --------------------------------------------------------------------------
+def qp_solve(e0, sigma_fn, dsigma_fn, grid=None, tol=1e-10, max_iter=50):
+    """Solve E = e0 + Re Sigma(E) with e0 = eps_t + s_t.
+
+    Newton from E = e0 with f(E) = E - e0 - Re Sigma(E), f' = 1 - Re Sigma'(E);
+    converged when |dE| <= tol * max(1, |E|).  If Newton fails, scan ``grid``
+    for sign changes of f, bisect each bracket, and keep the root closest to
+    e0 (ties: larger Z).  Returns (E, Z) with Z = 1 / (1 - Re Sigma'(E))."""
+    E = float(e0)
+    ok = False
+    for _ in range(max_iter):
+        f = E - e0 - sigma_fn(E).real
+        fp = 1.0 - dsigma_fn(E).real
+        if fp == 0.0 or not np.isfinite(f / fp):
+            break
+        dE = f / fp
+        E -= dE
+        if abs(dE) <= tol * max(1.0, abs(E)):
+            ok = True
+            break
+    if ok:
+        return E, 1.0 / (1.0 - dsigma_fn(E).real)
+    if grid is None:
+        raise RuntimeError("quasiparticle equation did not converge")
+    g = np.asarray(grid, dtype=np.float64)
+    fg = g - e0 - np.array([sigma_fn(x).real for x in g])
+    best = None
+    for i in range(len(g) - 1):
+        if fg[i] == 0.0 or fg[i] * fg[i + 1] < 0.0:
+            lo, hi, flo = g[i], g[i + 1], fg[i]
+            for _ in range(200):
+                mid = 0.5 * (lo + hi)
+                fm = mid - e0 - sigma_fn(mid).real
+                if (fm < 0.0) == (flo < 0.0):
+                    lo, flo = mid, fm
+                else:
+                    hi = mid
+                if hi - lo <= tol * max(1.0, abs(mid)):
+                    break
+            r = 0.5 * (lo + hi)
+            Zr = 1.0 / (1.0 - dsigma_fn(r).real)
+            key = (abs(r - e0), -Zr)
+            if best is None or key < best[0]:
+                best = (key, r, Zr)
+    if best is None:
+        raise RuntimeError("quasiparticle equation has no root on the grid")
+    return best[1], best[2]
+
+
+def solve_all_qp(wl, poles, static_shift=None):
+    """QP energies and renormalisation factors for every target."""
+    E = np.empty(wl.n_t)
+    Z = np.empty(wl.n_t)
+    for ti, t in enumerate(wl.targets):
+        pos, W, eta = poles[ti]
+        e0 = wl.eps[t] + (0.0 if static_shift is None else static_shift[ti])
+
+        def sfn(x, pos=pos, W=W, eta=eta):
+            return sigma_from_poles([x], pos, W, eta, wl.delta)[0]
+
+        def dfn(x, pos=pos, W=W, eta=eta):
+            return dsigma_from_poles([x], pos, W, eta, wl.delta)[0]
+
+        E[ti], Z[ti] = qp_solve(e0, sfn, dfn, grid=wl.omega)
+    return E, Z
