@@ -1,0 +1,246 @@
+/*
+ * lgw.h - C ABI of the GB300 (sm_103a) Lanczos full-frequency GW hot path.
+ *
+ * Method: Gao, Tang, Zhao, Chelikowsky, "Efficient Full-frequency GW
+ * Calculations using a Lanczos Method" (arXiv 2310.20103).
+ *
+ * The library computes the correlation self-energy Sigma^corr_tt(omega) of
+ * Eq. 7 for a set of target orbitals t without diagonalising the reduced
+ * Casida matrix (Eq. 4)
+ *
+ *     C = Delta^2 + c_K Delta^1/2 K Delta^1/2,   K = L L^T,
+ *     Delta = diag(eps_c - eps_v)                (pair index vc = v*n_c + c)
+ *
+ * For every pair (t, m) of a target t and a summed orbital m it runs a
+ * k-step Lanczos recurrence on C (Eq. 13) from the start vector |P_tm> of
+ * the text after Eq. 8, b_tm = Delta^1/2 V_tm with (tm|vc) = V_tm[vc] =
+ * sum_mu L[vc,mu] M_tm[mu], maps the tridiagonal's Gauss rule through
+ * Omega = sqrt(theta) (Eq. 12, D = C^1/2), evaluates each term as a
+ * continued fraction (Eq. 14) on a frequency grid, sums over m (Eq. 10) and
+ * solves the quasiparticle equation E = eps_t + s_t + Re Sigma_t(E).
+ *
+ * Conventions shared by every call
+ *   - Energies are in eV.  Complex outputs are interleaved (re, im) doubles.
+ *   - A pointer argument may point to host memory or to device memory of the
+ *     handle's device; the library detects which (cudaPointerGetAttributes)
+ *     and copies host inputs in and host outputs out.  When any output is a
+ *     host pointer the call returns only after the results are in place;
+ *     otherwise it is asynchronous on the handle's stream and outputs are
+ *     valid once that stream has been synchronised.
+ *   - The caller owns every buffer it passes; no call keeps a caller pointer
+ *     after it returns.  A system owns its own copies of eps, Delta and L.
+ *     A handle owns the device workspace (Krylov basis, vector blocks) and
+ *     grows it on demand; it is freed by lgw_destroy.
+ *   - Errors are return codes; nothing aborts and no exception crosses the
+ *     ABI.  Device-side failures (non-positive Gauss nodes, a bounded wait
+ *     that ran out) are collected in a device status word read at the end of
+ *     a call.  lgw_last_error gives a one-line description of the last
+ *     failure on a handle.  A handle is not thread-safe; use one per thread.
+ */
+#ifndef LGW_H
+#define LGW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LGW_OK = 0,
+  LGW_ERR_ARG = 1,             /* null pointer, negative size, bad enum      */
+  LGW_ERR_SHAPE = 2,           /* inconsistent sizes or indices out of range */
+  LGW_ERR_CUDA = 3,            /* a CUDA runtime call failed                 */
+  LGW_ERR_OOM = 4,             /* device allocation failed                   */
+  LGW_ERR_NOT_SPD = 5,         /* Delta <= 0 or a Gauss node theta <= 0      */
+  LGW_ERR_NO_CONVERGENCE = 6,  /* tridiagonal eigensolver or QP solve failed */
+  LGW_ERR_TIMEOUT = 7,         /* a bounded device wait ran out              */
+  LGW_ERR_UNSUPPORTED = 8      /* option combination not built               */
+} lgw_status;
+
+/* Arithmetic of the two low-rank contractions L^T(Delta^1/2 X) and L Y.
+ * Everything else (recurrence, reorthogonalisation, spectral map,
+ * continued fractions, QP) is FP64 in both modes. */
+typedef enum {
+  LGW_FP64 = 0,   /* FP64 CUDA-core GEMMs: the plain FP64 path            */
+  LGW_BF16 = 1    /* BF16 tcgen05 tensor-core GEMMs, FP32 accumulate      */
+} lgw_precision;
+
+typedef enum {
+  LGW_REORTH_NONE = 0,  /* three-term recurrence only                            */
+  LGW_REORTH_CGS2 = 1,  /* full classical Gram-Schmidt, always two passes        */
+  LGW_REORTH_CGS1K = 2  /* full CGS, second pass only where the norm drops below
+                           1/sqrt(2) of its value before the pass (Kahan-Parlett
+                           / Daniel-Gragg-Kaufman-Stewart criterion)              */
+} lgw_reorth;
+
+typedef struct lgw_handle lgw_handle;
+typedef struct lgw_system lgw_system;
+
+/* One electronic system: KS energies and the Coulomb-kernel factor.
+ * eps  [n_v + n_c]          valence block first (Eq. 1-3: v occupied, c empty)
+ * L    [n_v*n_c][n_aux]     row-major, K = L L^T (Eq. 15-17 fitted form)
+ * kernel_factor             c_K in C = Delta^2 + c_K Delta^1/2 K Delta^1/2;
+ *                           4.0 for a closed-shell spin sum, 0 switches K off. */
+typedef struct {
+  int32_t n_v, n_c, n_aux;
+  const double *eps;
+  const double *L;
+  double kernel_factor;
+} lgw_system_desc;
+
+/* The self-energy request.
+ * targets [n_t]   orbital indices t (diagonal elements Sigma_tt, Eq. 5-7)
+ * m_idx   [n_m]   summed orbital indices m (Eq. 10; a subset is allowed)
+ * M  [n_t][n_m][n_aux]  fitting factors: (tm|vc) = sum_mu L[vc,mu] M[t,m,mu]
+ * V  [n_t][n_m][n_v*n_c] the couplings (tm|vc) directly
+ *                 exactly one of M and V is non-NULL
+ * omega [n_freq]  real frequency grid; delta > 0 the broadening of Eq. 7
+ * static_shift [n_t] or NULL: s_t in E = eps_t + s_t + Re Sigma_t(E)
+ *                 (exchange minus exchange-correlation potential; 0 if NULL) */
+typedef struct {
+  int32_t n_t;
+  const int32_t *targets;
+  int32_t n_m;
+  const int32_t *m_idx;
+  const double *M;
+  const double *V;
+  int32_t n_freq;
+  const double *omega;
+  double delta;
+  const double *static_shift;
+} lgw_problem;
+
+/* k              Lanczos steps per start vector (1 <= k <= n_v*n_c)
+ * precision      lgw_precision of the two contractions
+ * reorth         lgw_reorth
+ * b_sub          start vectors per sub-batch (0: automatic)
+ * breakdown_tol  a vector stops after step j when beta_{j+1} <= tol*max|alpha|
+ *                (0: 1e-13)
+ * qp_max_iter    Newton iterations before the bracketing fallback (0: 50)
+ * qp_tol         |dE| <= qp_tol * max(1,|E|) ends Newton (0: 1e-10)
+ * use_graph      1: capture one Lanczos step as a CUDA graph and replay it */
+typedef struct {
+  int32_t k;
+  int32_t precision;
+  int32_t reorth;
+  int32_t b_sub;
+  double breakdown_tol;
+  int32_t qp_max_iter;
+  double qp_tol;
+  int32_t use_graph;
+  int32_t reserved;
+} lgw_options;
+
+/* Filled by calls that take a report pointer (host memory).  Phase times are
+ * sums of CUDA-event intervals on the handle's stream; asking for a report
+ * makes the call record those events and synchronise at its end. */
+typedef struct {
+  double ms_total;
+  double ms_start;       /* coupling/start vectors and first normalisation   */
+  double ms_gemm1;       /* L^T (Delta^1/2 q) contraction + partial reduce   */
+  double ms_gemm2;       /* L y contraction + fused recurrence epilogue      */
+  double ms_dots;        /* alpha finish, axpy and first-pass Q^T w products */
+  double ms_update;      /* first-pass w -= Q h                              */
+  double ms_pass2;       /* second Gram-Schmidt pass (decision, Q^T w, update) */
+  double ms_normalize;   /* beta, breakdown test, q_{j+1}, bf16 operand      */
+  double ms_spectral;    /* tridiagonal eigenproblems and Jacobi rebuild     */
+  double ms_cf;          /* continued fractions on the grid                  */
+  double ms_qp;          /* quasiparticle solve                              */
+  double gemm_flops;     /* algorithmic 4 N_vc N_aux k per vector, summed    */
+  double reorth_elems;   /* basis elements visited per Gram-Schmidt kernel,
+                            sum over vectors of N_vc * sum_j (j+1)            */
+  int32_t n_vectors;     /* start vectors B = n_t n_m                        */
+  int32_t n_sub_batches;
+  int32_t b_sub;         /* padded vectors per sub-batch                     */
+  int32_t k_min, k_max;  /* effective Lanczos depth over vectors             */
+  int32_t n_second_pass; /* vector-steps that took a second CGS pass         */
+  int32_t gpu_launches;  /* kernels launched by the call                     */
+  int32_t gemm1_splits;  /* K splits of the first contraction                */
+  double min_theta;      /* smallest Gauss node over all tridiagonals        */
+} lgw_report;
+
+/* Status text for a code; never NULL. */
+const char *lgw_status_string(lgw_status s);
+
+/* Create a handle bound to CUDA device `device` and the CUDA stream
+ * `cuda_stream` (a cudaStream_t; NULL means the legacy default stream).
+ * Allocates only the status word. */
+lgw_status lgw_create(lgw_handle **out, int device, void *cuda_stream);
+
+/* Destroy a handle and free its workspace.  Systems created on it must be
+ * released first.  NULL is accepted. */
+lgw_status lgw_destroy(lgw_handle *h);
+
+/* Copy the last error message of `h` into buf (NUL-terminated, truncated to
+ * n bytes).  Returns the last error code. */
+lgw_status lgw_last_error(lgw_handle *h, char *buf, size_t n);
+
+/* Build a system: copies eps and L to the device, forms Delta_vc,
+ * Delta^1/2 and Delta^2 (Eq. 2-4), pads L to [N_pad][A_pad], and makes the
+ * BF16 copies of L (row-major) and L^T used by the tensor-core path.
+ * Fails with LGW_ERR_NOT_SPD if some eps_c - eps_v <= 0. */
+lgw_status lgw_prepare_system(lgw_handle *h, const lgw_system_desc *desc, lgw_system **out);
+
+/* Free a system's device memory.  NULL is accepted. */
+lgw_status lgw_release_system(lgw_system *s);
+
+/* Apply C to n_vec vectors: Y[i] = C X[i], X and Y [n_vec][n_v*n_c] FP64,
+ * through the same contractions (precision) the Lanczos path uses. */
+lgw_status lgw_apply_casida(lgw_handle *h, const lgw_system *s, int32_t n_vec,
+                            const double *X, double *Y, int32_t precision);
+
+/* Lanczos tridiagonals only (Eq. 13) for every start vector, vector index
+ * i = t_index * n_m + m_index:
+ *   alpha [B][k]  diagonal a_0..a_{k-1}
+ *   beta  [B][k]  beta[i][j] couples steps j and j+1; beta[i][k-1] is the
+ *                 final residual norm
+ *   beta0 [B]     ||b_tm||
+ *   k_eff [B]     steps actually taken (< k after a breakdown)
+ * These arrays are a complete checkpoint: lgw_sigma_from_coeffs resumes
+ * from them. */
+lgw_status lgw_lanczos_coeffs(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                              const lgw_options *o, double *alpha, double *beta,
+                              double *beta0, int32_t *k_eff);
+
+/* Self-energy and QP energies from stored tridiagonals (Eq. 12, 14, 10):
+ * spectral map of each T_k, continued fractions on the grid, QP solve.
+ * sigma [n_t][n_freq][2]; e_qp [n_t]; z_qp [n_t] (renormalisation factor
+ * 1/(1 - dRe Sigma/domega) at E_qp) may be NULL. */
+lgw_status lgw_sigma_from_coeffs(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                                 const lgw_options *o, const double *alpha,
+                                 const double *beta, const double *beta0,
+                                 const int32_t *k_eff, double *sigma, double *e_qp,
+                                 double *z_qp);
+
+/* The whole hot path for one system: start vectors, k Lanczos steps per
+ * (t, m) pair, spectral map, continued fractions on the grid (Eq. 14, one
+ * thread per (target, frequency)), sum over m (Eq. 10) and QP solve.
+ * sigma [n_t][n_freq][2], e_qp [n_t], z_qp [n_t] or NULL, rep or NULL. */
+lgw_status lgw_sigma_c(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                       const lgw_options *o, double *sigma, double *e_qp, double *z_qp,
+                       lgw_report *rep);
+
+/* Several independent systems of uneven size in one call; sigma[i], e_qp[i]
+ * and z_qp[i] (z_qp may be NULL) have the shapes of lgw_sigma_c for
+ * problems[i].  All start vectors of all systems are scheduled together. */
+lgw_status lgw_sigma_c_batched(lgw_handle *h, int32_t n_sys, const lgw_system *const *systems,
+                               const lgw_problem *problems, const lgw_options *o,
+                               double *const *sigma, double *const *e_qp,
+                               double *const *z_qp, lgw_report *rep);
+
+/* Gradient of sum_t dE[t] * E_qp[t] with respect to L ([n_v*n_c][n_aux]) and
+ * eps ([n_v+n_c]) for the request p, through the adjoint of the Lanczos
+ * recurrence, the spectral map, the continued fractions and the QP
+ * equation (implicit-function factor Z_t).  dL / deps are overwritten;
+ * either may be NULL. */
+lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                                const lgw_options *o, const double *dE, double *dL,
+                                double *deps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LGW_H */

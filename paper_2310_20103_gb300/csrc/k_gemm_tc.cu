@@ -1,0 +1,497 @@
+// BF16 tensor-core contractions of the low-rank Casida matvec on sm_103a:
+// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 accumulator in tensor memory),
+// operands staged by TMA (cp.async.bulk.tensor, 128-byte swizzle), a
+// multi-stage mbarrier pipeline, and the epilogue read back with tcgen05.ld.
+//
+//   gemm1: Y^T[mu][b] = sum_vc L^T[mu][vc] Xh[b][vc]     (M = N_aux, K = N_vc)
+//          Xh = bf16(Delta^1/2 q_j) (written by the normalisation kernel);
+//          split over K, FP32 partials reduced in fixed order into bf16 Yh.
+//   gemm2: U[vc][b] = sum_mu L[vc][mu] Yh[b][mu]          (M = N_vc, K = N_aux)
+//          fused FP64 epilogue w = Delta^2 q_j + c_K Delta^1/2 U - beta_j q_{j-1}
+//          and per-tile partial sums of alpha_j = q_j . w (warp-transposed
+//          reduction, fixed-order sum over the four epilogue warps).
+//
+// Both operands are K-major (row-major with K contiguous): L^T [N_aux][N_vc]
+// for gemm1 and L [N_vc][N_aux] for gemm2, so each gemm has its own copy.
+// CTA = 6 warps: warp 0 issues TMA, warp 1 owns tensor memory and issues the
+// MMAs from one thread, warps 2..5 run the epilogue (warp w reads TMEM lanes
+// 32*(w%4) .. 32*(w%4)+31).  Tile 128 x BN x 64, BN in {64, 128, 256}.
+// Every mbarrier wait is bounded (clock64); a timeout sets ST_TIMEOUT.
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "lgw_internal.cuh"
+
+namespace lgw {
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 64;              // 64 bf16 = 128 bytes = one swizzle row
+constexpr int NTHREADS = 192;
+
+template <int BN>
+struct Cfg {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int STAGES = (BN == 256) ? 4 : (BN == 128 ? 6 : 8);
+  static constexpr int BAR_BYTES = 256;
+  static constexpr int RED_BYTES = 4 * BN * 8;
+  static constexpr int SMEM = 1024 + STAGES * STAGE + BAR_BYTES + RED_BYTES;
+  static constexpr uint32_t TMEM_COLS = BN;
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on a barrier phase; false (and ST_TIMEOUT) after ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicOr(status, ST_TIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, uint64_t *bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D[tmem] (+)= A[smem desc] * B[smem desc]^T, M=128, N=BN, K=16 (bf16)
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on an mbarrier once every MMA issued so far by this thread is done.
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (SBO); LBO unused for this layout.
+__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address  [0,14)
+  d |= (uint64_t)1 << 16;                     // LBO (16 B)      [16,30)
+  d |= (uint64_t)(1024 >> 4) << 32;           // SBO             [32,46)
+  d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                     // swizzle mode: 128-byte
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+struct EpiArgs {
+  // gemm1 (split-K partials)
+  float *ypart;          // [splits][ncols][ldo]
+  int ldo;
+  // gemm2 (Lanczos epilogue)
+  int N;                 // vector length
+  const double *Delta2, *cd, *q, *qprev, *betaj;
+  double *w, *alpha_part;
+  unsigned *status;
+};
+
+enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2 };
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              int M, int Ncols, int num_kb, int kb_per_split, EpiArgs ea) {
+  using C = Cfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE);
+  uint64_t *empty = full + C::STAGES;
+  uint64_t *tfull = empty + C::STAGES;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(tfull + 1);
+  double *red = reinterpret_cast<double *>(smem + C::STAGES * C::STAGE + C::BAR_BYTES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m_tile = blockIdx.x, n_tile = blockIdx.y, split = blockIdx.z;
+  const int kb0 = split * kb_per_split;
+  const int kb1 = min(num_kb, kb0 + kb_per_split);
+  const int nk = max(0, kb1 - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tslot, C::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % C::STAGES;
+        const uint32_t ph = (it / C::STAGES) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, ea.status)) break;
+        mbar_expect_tx(&full[s], C::STAGE);
+        uint8_t *sa = smem + s * C::STAGE;
+        const int kx = (kb0 + it) * BK;
+        tma_load_2d(sa, &tmA, &full[s], kx, m_tile * BM);
+        tma_load_2d(sa + C::A_BYTES, &tmB, &full[s], kx, n_tile * BN);
+        issued = it + 1;
+      }
+      // Drain: every issued copy must have landed before the CTA may exit.
+      for (int it = max(0, issued - C::STAGES); it < issued; ++it)
+        mbar_wait(&full[it % C::STAGES], (it / C::STAGES) & 1, ea.status);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(BM, BN);
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % C::STAGES;
+        const uint32_t ph = (it / C::STAGES) & 1;
+        if (!mbar_wait(&full[s], ph, ea.status)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + s * C::STAGE);
+        const uint64_t da = make_sdesc(sa), db = make_sdesc(sa + C::A_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk)
+          umma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        umma_commit(&empty[s]);
+      }
+      umma_commit(tfull);
+    }
+  } else {
+    // ------------------------------ epilogue ------------------------------
+    const bool ok = mbar_wait(tfull, 0, ea.status);
+    tc_fence_after();
+    const int qd = warp & 3;
+    const int row = m_tile * BM + qd * 32 + lane;
+    const int ncol0 = n_tile * BN;
+    double d2 = 0.0, cdr = 0.0;
+    if (EPI != E_SPLITK && row < M) {
+      d2 = ea.Delta2[row];
+      cdr = ea.cd[row];
+    }
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)c0, r);
+      if (!ok || nk == 0) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) r[i] = 0u;
+      }
+      if (EPI == E_SPLITK) {
+        float *out = ea.ypart + (size_t)split * Ncols * ea.ldo;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = ncol0 + c0 + i;
+          if (col < Ncols && row < M) out[(size_t)col * ea.ldo + row] = __uint_as_float(r[i]);
+        }
+      } else {
+        double acc[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = ncol0 + c0 + i;
+          acc[i] = 0.0;
+          if (col < Ncols && row < M) {
+            const size_t o = (size_t)col * ea.N + row;
+            const double u = (double)__uint_as_float(r[i]);
+            const double qv = ea.q[o];
+            double wv = fma(d2, qv, cdr * u);
+            if (EPI == E_LANCZOS && ea.qprev != nullptr) wv = fma(-ea.betaj[col], ea.qprev[o], wv);
+            ea.w[o] = wv;
+            acc[i] = qv * wv;
+          }
+        }
+        if (EPI == E_LANCZOS) {
+          warp_transpose_sum32(acc);
+          red[qd * BN + c0 + lane] = acc[0];
+        }
+      }
+    }
+    if (EPI == E_LANCZOS) {
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const int te = threadIdx.x - 64;
+      for (int col = te; col < BN; col += 128) {
+        const int b = ncol0 + col;
+        if (b < Ncols) {
+          const double s = ((red[col] + red[BN + col]) + red[2 * BN + col]) + red[3 * BN + col];
+          ea.alpha_part[(size_t)m_tile * Ncols + b] = s;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+__global__ void k_reduce_y_bf16(const float *__restrict__ Ypart, int splits, int n,
+                                __nv_bfloat16 *__restrict__ Yh) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.0f;
+  for (int p = 0; p < splits; ++p) s += Ypart[(size_t)p * n + i];
+  Yh[i] = __float2bfloat16_rn(s);
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct TcPlan {
+  CUtensorMap g1A, g1B, g2A, g2B;
+  int BN;
+  int N, A, Bs;
+  int splits, kb_per_split;
+  float *ypart;
+  __nv_bfloat16 *yh;
+  const double *Delta2, *cd;
+};
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  std::call_once(g_encode_once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return g_encode;
+}
+
+bool tc_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && get_encode() != nullptr;
+}
+
+static bool encode_2d(CUtensorMap *tm, const void *base, uint64_t inner, uint64_t outer,
+                      uint32_t box_outer) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {(cuuint32_t)tc::BK, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+static int choose_splits(int tiles, int num_kb, int nsm) {
+  // Fill whole waves of one CTA per SM: pick the split count whose CTA total
+  // wastes the least of its last wave, with at least 8 K blocks per split.
+  int best = 1;
+  double best_cost = 1e30;
+  for (int s = 1; s <= 64; ++s) {
+    int per = (num_kb + s - 1) / s;
+    if (per < 8 && s > 1) break;
+    int real_s = (num_kb + per - 1) / per;
+    int ctas = tiles * real_s;
+    int waves = (ctas + nsm - 1) / nsm;
+    double cost = (double)waves * per;   // time ~ waves x K blocks per CTA
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = real_s;
+    }
+  }
+  return best;
+}
+
+int tc_n_mt(const SysDev &s) { return s.N / tc::BM; }
+
+TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *ypart,
+                       __nv_bfloat16 *yh, int *splits_out, char *err, size_t errn) {
+  TcPlan *p = new TcPlan();
+  p->N = s.N;
+  p->A = s.A;
+  p->Bs = Bs;
+  p->BN = Bs >= 256 ? 256 : (Bs >= 128 ? 128 : 64);
+  if (Bs < 64 || s.A < tc::BM || s.N < tc::BM) {
+    snprintf(err, errn, "tensor-core plan needs Bs >= 64, N_aux and N_vc padded >= 128");
+    delete p;
+    return nullptr;
+  }
+  int nsm = 148;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int num_kb = s.N / tc::BK;
+  const int tiles1 = ((s.A + tc::BM - 1) / tc::BM) * ((Bs + p->BN - 1) / p->BN);
+  p->splits = choose_splits(tiles1, num_kb, nsm);
+  p->kb_per_split = (num_kb + p->splits - 1) / p->splits;
+  p->splits = (num_kb + p->kb_per_split - 1) / p->kb_per_split;
+  p->ypart = ypart;
+  p->yh = yh;
+  p->Delta2 = s.Delta2;
+  p->cd = s.cd;
+  bool ok = encode_2d(&p->g1A, s.Ltb, (uint64_t)s.N, (uint64_t)s.A, tc::BM) &&
+            encode_2d(&p->g1B, xh, (uint64_t)s.N, (uint64_t)Bs, (uint32_t)p->BN) &&
+            encode_2d(&p->g2A, s.Lb, (uint64_t)s.A, (uint64_t)s.N, tc::BM) &&
+            encode_2d(&p->g2B, yh, (uint64_t)s.A, (uint64_t)Bs, (uint32_t)p->BN);
+  if (!ok) {
+    snprintf(err, errn, "cuTensorMapEncodeTiled failed");
+    delete p;
+    return nullptr;
+  }
+  if (splits_out) *splits_out = p->splits;
+  return p;
+}
+
+void tc_plan_destroy(TcPlan *p) { delete p; }
+
+template <int BN, int EPI>
+static void launch_tc(const CUtensorMap &A, const CUtensorMap &B, int M, int Ncols, int num_kb,
+                      int kb_per_split, int splits, const tc::EpiArgs &ea, cudaStream_t st) {
+  using C = tc::Cfg<BN>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(tc::k_gemm_tc<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         C::SMEM);
+    attr_done = true;
+  }
+  dim3 grid((M + tc::BM - 1) / tc::BM, (Ncols + BN - 1) / BN, splits);
+  tc::k_gemm_tc<BN, EPI><<<grid, tc::NTHREADS, C::SMEM, st>>>(A, B, M, Ncols, num_kb, kb_per_split,
+                                                              ea);
+}
+
+template <int EPI>
+static void dispatch_bn(int BN, const CUtensorMap &A, const CUtensorMap &B, int M, int Ncols,
+                        int num_kb, int kb_per_split, int splits, const tc::EpiArgs &ea,
+                        cudaStream_t st) {
+  if (BN == 256)
+    launch_tc<256, EPI>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
+  else if (BN == 128)
+    launch_tc<128, EPI>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
+  else
+    launch_tc<64, EPI>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
+}
+
+void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st) {
+  tc::EpiArgs ea{};
+  ea.ypart = p->ypart;
+  ea.ldo = p->A;
+  ea.status = status;
+  dispatch_bn<tc::E_SPLITK>(p->BN, p->g1A, p->g1B, p->A, p->Bs, p->N / tc::BK, p->kb_per_split,
+                            p->splits, ea, st);
+}
+
+void launch_reduce_y_bf16(const float *Ypart, int splits, int Bs, int A, __nv_bfloat16 *Yh,
+                          cudaStream_t st) {
+  int n = Bs * A;
+  tc::k_reduce_y_bf16<<<(n + 255) / 256, 256, 0, st>>>(Ypart, splits, n, Yh);
+}
+
+void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qprev,
+                     const double *betaj, double *w, double *alpha_part, unsigned *status,
+                     cudaStream_t st) {
+  tc::EpiArgs ea{};
+  ea.N = p->N;
+  ea.Delta2 = p->Delta2;
+  ea.cd = p->cd;
+  ea.q = q;
+  ea.qprev = qprev;
+  ea.betaj = betaj;
+  ea.w = w;
+  ea.alpha_part = alpha_part;
+  ea.status = status;
+  const int num_kb = p->A / tc::BK;
+  if (epi == EPI_LANCZOS)
+    dispatch_bn<tc::E_LANCZOS>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+  else
+    dispatch_bn<tc::E_APPLY>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+}
+
+}  // namespace lgw

@@ -1,0 +1,353 @@
+// Vector kernels of one Lanczos step (Eq. 13), FP64.
+//
+// Step j of every start vector b in a sub-batch (w already holds
+// C q_j - beta_j q_{j-1} from the contraction epilogue):
+//   alpha_j = q_j . w          (per-tile partials summed in fixed order)
+//   w <- w - alpha_j q_j
+//   full reorthogonalisation against the stored basis q_0..q_j by classical
+//   Gram-Schmidt: h = Q^T w, w <- w - Q h (once, or twice)
+//   beta_{j+1} = ||w||; stop when beta_{j+1} <= tol * max|alpha|
+//   q_{j+1} = w / beta_{j+1};  xh = bf16(Delta^1/2 q_{j+1})
+//
+// Every block owns one chunk of VEC_CHUNK pair elements of one vector; each
+// warp owns 256 consecutive elements, each lane four double2 of them.  All
+// cross-block sums go through per-chunk partials reduced in a fixed order,
+// so results do not depend on scheduling.
+#include "lgw_internal.cuh"
+
+namespace lgw {
+
+__device__ __forceinline__ int elem_base(int chunk) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  return chunk * VEC_CHUNK + wid * 256 + 2 * lane;
+}
+
+__device__ __forceinline__ bool vec_live(const VecCtx &c, int b, int j) {
+  return b < c.nvec && c.k_eff[c.vec0 + b] > j;
+}
+
+// Partial dot products of the thread's eight elements of w with basis rows
+// 0..nrows-1 of vector b; one partial per (row, chunk) after a warp
+// transposed reduction and a fixed-order sum over the eight warps.
+__device__ void dots_rows(const VecCtx &c, int nrows, int b, int chunk, const double (&wr)[8],
+                          double (*sred)[32]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int e0 = elem_base(chunk);
+  const size_t voff = (size_t)b * c.N;
+  for (int r0 = 0; r0 < nrows; r0 += 32) {
+    double acc[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      acc[r] = 0.0;
+      if (r0 + r < nrows) {
+        const double *qrow = slot_ptr(c, r0 + r) + voff;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * 64;
+          if (e < c.N) {
+            const double2 q2 = *reinterpret_cast<const double2 *>(qrow + e);
+            acc[r] = fma(q2.x, wr[2 * u], acc[r]);
+            acc[r] = fma(q2.y, wr[2 * u + 1], acc[r]);
+          }
+        }
+      }
+    }
+    warp_transpose_sum32(acc);
+    sred[wid][lane] = acc[0];
+    __syncthreads();
+    if (wid == 0) {
+      double s = 0.0;
+#pragma unroll
+      for (int w8 = 0; w8 < VEC_THREADS / 32; ++w8) s += sred[w8][lane];
+      if (r0 + lane < nrows)
+        c.dot_part[((size_t)b * c.nchunks + chunk) * c.kmax1 + r0 + lane] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// alpha_j from the epilogue partials, w -= alpha_j q_j, ||w||^2 partials,
+// and (with reorthogonalisation) the first-pass dot products.
+__global__ void __launch_bounds__(VEC_THREADS) k_alpha_axpy(VecCtx c, int j) {
+  __shared__ double red[VEC_THREADS / 32];
+  __shared__ double sred[VEC_THREADS / 32][32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  if (!vec_live(c, b, j)) return;
+  double s = 0.0;
+  for (int t = threadIdx.x; t < c.n_mt; t += VEC_THREADS) s += c.alpha_part[(size_t)t * c.Bs + b];
+  const double alpha = block_sum(s, red);
+  if (chunk == 0 && threadIdx.x == 0) {
+    c.alpha[(size_t)(c.vec0 + b) * c.k + j] = alpha;
+    c.amax[b] = fmax(c.amax[b], fabs(alpha));
+  }
+  const size_t voff = (size_t)b * c.N;
+  const double *q = slot_ptr(c, j) + voff;
+  double *w = c.w + voff;
+  const int e0 = elem_base(chunk);
+  double wr[8];
+  double nrm = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    double2 w2 = make_double2(0.0, 0.0);
+    if (e < c.N) {
+      const double2 q2 = *reinterpret_cast<const double2 *>(q + e);
+      w2 = *reinterpret_cast<const double2 *>(w + e);
+      w2.x = fma(-alpha, q2.x, w2.x);
+      w2.y = fma(-alpha, q2.y, w2.y);
+      *reinterpret_cast<double2 *>(w + e) = w2;
+    }
+    wr[2 * u] = w2.x;
+    wr[2 * u + 1] = w2.y;
+    nrm = fma(w2.x, w2.x, fma(w2.y, w2.y, nrm));
+  }
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) c.norm_a[(size_t)b * c.nchunks + chunk] = nrm;
+  if (c.reorth != LGW_REORTH_NONE) dots_rows(c, j + 1, b, chunk, wr, sred);
+}
+
+// Second-pass dot products of the current w with rows 0..j.
+__global__ void __launch_bounds__(VEC_THREADS) k_dots(VecCtx c, int j) {
+  __shared__ double sred[VEC_THREADS / 32][32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  if (!vec_live(c, b, j) || !c.flag2[b]) return;
+  const double *w = c.w + (size_t)b * c.N;
+  const int e0 = elem_base(chunk);
+  double wr[8];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    double2 w2 = make_double2(0.0, 0.0);
+    if (e < c.N) w2 = *reinterpret_cast<const double2 *>(w + e);
+    wr[2 * u] = w2.x;
+    wr[2 * u + 1] = w2.y;
+  }
+  dots_rows(c, j + 1, b, chunk, wr, sred);
+}
+
+// h[b][i] = sum over chunks of the dot partials, fixed order.
+__global__ void k_reduce_dots(VecCtx c, int j, int pass) {
+  const int b = blockIdx.x;
+  if (!vec_live(c, b, j)) return;
+  if (pass == 2 && !c.flag2[b]) return;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double *p = c.dot_part + (size_t)b * c.nchunks * c.kmax1 + i;
+    double s = 0.0;
+    for (int ch = 0; ch < c.nchunks; ++ch) s += p[(size_t)ch * c.kmax1];
+    c.h[(size_t)b * c.kmax1 + i] = s;
+  }
+}
+
+// w <- w - sum_i h_i q_i over rows 0..j and ||w||^2 partials.
+__global__ void __launch_bounds__(VEC_THREADS) k_update(VecCtx c, int j, int pass) {
+  extern __shared__ double hs[];
+  __shared__ double red[VEC_THREADS / 32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  if (!vec_live(c, b, j)) return;
+  if (pass == 2 && !c.flag2[b]) return;
+  for (int i = threadIdx.x; i <= j; i += VEC_THREADS) hs[i] = c.h[(size_t)b * c.kmax1 + i];
+  __syncthreads();
+  const size_t voff = (size_t)b * c.N;
+  double *w = c.w + voff;
+  const int e0 = elem_base(chunk);
+  double2 wv[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    wv[u] = (e < c.N) ? *reinterpret_cast<const double2 *>(w + e) : make_double2(0.0, 0.0);
+  }
+  for (int i = 0; i <= j; ++i) {
+    const double hi = hs[i];
+    const double *qrow = slot_ptr(c, i) + voff;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * 64;
+      if (e < c.N) {
+        const double2 q2 = *reinterpret_cast<const double2 *>(qrow + e);
+        wv[u].x = fma(-hi, q2.x, wv[u].x);
+        wv[u].y = fma(-hi, q2.y, wv[u].y);
+      }
+    }
+  }
+  double nrm = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e < c.N) *reinterpret_cast<double2 *>(w + e) = wv[u];
+    nrm = fma(wv[u].x, wv[u].x, fma(wv[u].y, wv[u].y, nrm));
+  }
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) (pass == 1 ? c.norm_b : c.norm_c)[(size_t)b * c.nchunks + chunk] = nrm;
+}
+
+// Second Gram-Schmidt pass: always (CGS2), or where the first pass removed
+// more than half of ||w||^2 (the 1/sqrt(2) norm criterion).
+__global__ void k_second_pass_decide(VecCtx c, int j) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= c.Bs) return;
+  int f = 0;
+  if (vec_live(c, b, j)) {
+    if (c.reorth == LGW_REORTH_CGS2) {
+      f = 1;
+    } else {
+      double na = 0.0, nb = 0.0;
+      for (int ch = 0; ch < c.nchunks; ++ch) {
+        na += c.norm_a[(size_t)b * c.nchunks + ch];
+        nb += c.norm_b[(size_t)b * c.nchunks + ch];
+      }
+      f = nb < 0.5 * na;
+      if (f) atomicAdd(c.n_second, 1);
+    }
+  }
+  c.flag2[b] = f;
+}
+
+// beta = ||w|| (fixed-order sum of the chosen partials), breakdown test,
+// q_next = w / beta into the next basis slot and xh = bf16(Delta^1/2 q_next).
+// is_start: w holds b_tm; records beta0 and writes q_0 into slot 0.
+__global__ void __launch_bounds__(VEC_THREADS) k_normalize(VecCtx c, int j, int is_start) {
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const int v = c.vec0 + b;
+  const bool real = b < c.nvec;
+  bool live = real && (is_start || c.k_eff[v] > j);
+  double beta = 0.0;
+  if (live) {
+    const double *np = c.norm_a;
+    if (!is_start && c.reorth != LGW_REORTH_NONE) np = c.flag2[b] ? c.norm_c : c.norm_b;
+    double s = 0.0;
+    for (int ch = 0; ch < c.nchunks; ++ch) s += np[(size_t)b * c.nchunks + ch];
+    beta = sqrt(s);
+    if (is_start) {
+      if (chunk == 0 && threadIdx.x == 0) {
+        c.beta0[v] = beta;
+        c.k_eff[v] = beta > 0.0 ? c.k : 0;
+        c.amax[b] = 0.0;
+        c.betaj[b] = 0.0;
+      }
+      live = beta > 0.0;
+    } else {
+      const bool stop = !(beta > c.tol * c.amax[b]);
+      if (chunk == 0 && threadIdx.x == 0) {
+        c.beta[(size_t)v * c.k + j] = beta;
+        c.betaj[b] = beta;
+        if (stop) c.k_eff[v] = j + 1;
+      }
+      if (stop) live = false;
+    }
+  } else if (chunk == 0 && threadIdx.x == 0) {
+    c.betaj[b] = 0.0;
+  }
+  const int next = is_start ? 0 : j + 1;
+  if (next >= c.nslots && c.reorth != LGW_REORTH_NONE) return;
+  const size_t voff = (size_t)b * c.N;
+  double *qn = slot_ptr(c, next) + voff;
+  const double *w = c.w + voff;
+  const double inv = live ? 1.0 / beta : 0.0;
+  const int e0 = elem_base(chunk);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= c.N) continue;
+    double2 q2 = make_double2(0.0, 0.0);
+    if (live) {
+      q2 = *reinterpret_cast<const double2 *>(w + e);
+      q2.x *= inv;
+      q2.y *= inv;
+    }
+    *reinterpret_cast<double2 *>(qn + e) = q2;
+    if (c.xh != nullptr) {
+      __nv_bfloat162 x2;
+      x2.x = __double2bfloat16(c.dsq[e] * q2.x);
+      x2.y = __double2bfloat16(c.dsq[e + 1] * q2.y);
+      *reinterpret_cast<__nv_bfloat162 *>(c.xh + voff + e) = x2;
+    }
+  }
+}
+
+// w = Delta^1/2 V for the rows of a given coupling block (V row stride ldv,
+// n_valid real pair elements per row), zero elsewhere; ||w||^2 partials.
+__global__ void __launch_bounds__(VEC_THREADS) k_start_from_v(VecCtx c, const double *V, int ldv,
+                                                              int n_valid) {
+  __shared__ double red[VEC_THREADS / 32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const size_t voff = (size_t)b * c.N;
+  const int e0 = elem_base(chunk);
+  double nrm = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= c.N) continue;
+    double x0 = 0.0, x1 = 0.0;
+    if (b < c.nvec) {
+      if (e < n_valid) x0 = c.dsq[e] * V[(size_t)b * ldv + e];
+      if (e + 1 < n_valid) x1 = c.dsq[e + 1] * V[(size_t)b * ldv + e + 1];
+    }
+    c.w[voff + e] = x0;
+    c.w[voff + e + 1] = x1;
+    nrm = fma(x0, x0, fma(x1, x1, nrm));
+  }
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) c.norm_a[(size_t)b * c.nchunks + chunk] = nrm;
+}
+
+__global__ void __launch_bounds__(VEC_THREADS) k_norm_partials(VecCtx c, const double *x,
+                                                               double *out) {
+  __shared__ double red[VEC_THREADS / 32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const size_t voff = (size_t)b * c.N;
+  const int e0 = elem_base(chunk);
+  double nrm = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= c.N || b >= c.nvec) continue;
+    const double2 x2 = *reinterpret_cast<const double2 *>(x + voff + e);
+    nrm = fma(x2.x, x2.x, fma(x2.y, x2.y, nrm));
+  }
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) out[(size_t)b * c.nchunks + chunk] = nrm;
+}
+
+__global__ void k_scale_rows_to_bf16(const double *__restrict__ x, const double *__restrict__ dsq,
+                                     int Bs, int N, __nv_bfloat16 *__restrict__ out) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t n = (size_t)Bs * N;
+  if (i >= n) return;
+  out[i] = __double2bfloat16(dsq[i % N] * x[i]);
+}
+
+// ---------------------------------------------------------------------------
+static dim3 vec_grid(const VecCtx &c) { return dim3(c.nchunks, c.Bs); }
+
+void launch_start_from_v(const VecCtx &c, const double *V, int ldv, int n_valid, cudaStream_t st) {
+  k_start_from_v<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, V, ldv, n_valid);
+}
+void launch_norm_partials(const VecCtx &c, const double *x, double *out, cudaStream_t st) {
+  k_norm_partials<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, x, out);
+}
+void launch_normalize(const VecCtx &c, int j, int is_start, const double *, cudaStream_t st) {
+  k_normalize<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, j, is_start);
+}
+void launch_alpha_axpy(const VecCtx &c, int j, cudaStream_t st) {
+  k_alpha_axpy<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, j);
+}
+void launch_reduce_dots(const VecCtx &c, int j, int pass, cudaStream_t st) {
+  k_reduce_dots<<<c.Bs, 256, 0, st>>>(c, j, pass);
+}
+void launch_update(const VecCtx &c, int j, int pass, cudaStream_t st) {
+  size_t sh = (size_t)c.kmax1 * sizeof(double);
+  k_update<<<vec_grid(c), VEC_THREADS, sh, st>>>(c, j, pass);
+}
+void launch_dots(const VecCtx &c, int j, int, cudaStream_t st) {
+  k_dots<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, j);
+}
+void launch_second_pass_decide_j(const VecCtx &c, int j, cudaStream_t st) {
+  k_second_pass_decide<<<(c.Bs + 255) / 256, 256, 0, st>>>(c, j);
+}
+void launch_scale_rows_to_bf16(const double *x, const double *dsq, int Bs, int N,
+                               __nv_bfloat16 *out, cudaStream_t st) {
+  size_t n = (size_t)Bs * N;
+  k_scale_rows_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, dsq, Bs, N, out);
+}
+
+}  // namespace lgw

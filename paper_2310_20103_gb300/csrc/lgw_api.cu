@@ -1,0 +1,976 @@
+// C ABI of the lgw library: argument checks, host/device staging, workspace
+// management and the per-sub-batch schedule of the hot path.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lgw_internal.cuh"
+
+using namespace lgw;
+
+struct lgw_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  lgw_status last = LGW_OK;
+  std::string msg;
+  unsigned *d_status = nullptr;
+  struct Buf {
+    void *p = nullptr;
+    size_t n = 0;
+  };
+  std::map<std::string, Buf> bufs;
+  int launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  bool timing = false;
+};
+
+struct lgw_system {
+  lgw_handle *h = nullptr;
+  SysDev s{};
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Fail {
+  lgw_status st;
+};
+
+lgw_status set_err(lgw_handle *h, lgw_status st, const char *fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->last = st;
+    h->msg = buf;
+  }
+  return st;
+}
+
+#define LGW_TRY_CUDA(h, call)                                                             \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      set_err((h), e_ == cudaErrorMemoryAllocation ? LGW_ERR_OOM : LGW_ERR_CUDA,          \
+              "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      throw Fail{(h)->last};                                                              \
+    }                                                                                     \
+  } while (0)
+
+void check_launch(lgw_handle *h, const char *what) {
+  h->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_err(h, LGW_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+    throw Fail{h->last};
+  }
+}
+
+void *ws(lgw_handle *h, const std::string &name, size_t bytes) {
+  auto &b = h->bufs[name];
+  if (bytes == 0) bytes = 8;
+  if (b.n < bytes) {
+    if (b.p) {
+      LGW_TRY_CUDA(h, cudaStreamSynchronize(h->stream));
+      cudaFree(b.p);
+      b.p = nullptr;
+      b.n = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_err(h, LGW_ERR_OOM, "cudaMalloc(%zu bytes) for %s failed: %s", bytes, name.c_str(),
+              cudaGetErrorString(e));
+      throw Fail{LGW_ERR_OOM};
+    }
+    b.p = p;
+    b.n = bytes;
+  }
+  return b.p;
+}
+
+template <class T>
+T *wsT(lgw_handle *h, const std::string &name, size_t count) {
+  return static_cast<T *>(ws(h, name, count * sizeof(T)));
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of an input: the pointer itself, or a staged copy.
+template <class T>
+const T *in_dev(lgw_handle *h, const std::string &name, const T *p, size_t count) {
+  if (!p || count == 0) return p;
+  if (is_device_ptr(p)) return p;
+  T *d = wsT<T>(h, name, count);
+  LGW_TRY_CUDA(h, cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  return d;
+}
+
+// Host copy of a small array given on either side.
+template <class T>
+std::vector<T> to_host(lgw_handle *h, const T *p, size_t count) {
+  std::vector<T> v(count);
+  if (count == 0) return v;
+  if (is_device_ptr(p)) {
+    LGW_TRY_CUDA(h, cudaMemcpyAsync(v.data(), p, count * sizeof(T), cudaMemcpyDeviceToHost,
+                                    h->stream));
+    LGW_TRY_CUDA(h, cudaStreamSynchronize(h->stream));
+  } else {
+    std::memcpy(v.data(), p, count * sizeof(T));
+  }
+  return v;
+}
+
+// Output staging: compute into a device buffer, copy back if the caller's
+// pointer is host memory.
+template <class T>
+struct OutBuf {
+  T *user = nullptr;
+  T *dev = nullptr;
+  size_t count = 0;
+  bool host = false;
+  void init(lgw_handle *h, const std::string &name, T *p, size_t n) {
+    user = p;
+    count = n;
+    if (!p) {
+      dev = nullptr;
+      return;
+    }
+    host = !is_device_ptr(p);
+    dev = host ? wsT<T>(h, name, n) : p;
+  }
+  void finish(lgw_handle *h) {
+    if (user && host && count)
+      LGW_TRY_CUDA(h, cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDeviceToHost,
+                                      h->stream));
+  }
+};
+
+struct Timer {
+  lgw_handle *h;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans;
+  cudaEvent_t open = nullptr;
+  int open_cat = -1;
+  explicit Timer(lgw_handle *hh) : h(hh) {}
+  cudaEvent_t ev() {
+    if (h->ev_used == h->ev_pool.size()) {
+      cudaEvent_t e;
+      LGW_TRY_CUDA(h, cudaEventCreate(&e));
+      h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_used++];
+  }
+  // Close the running span (if any) and open one for category `cat`.
+  void mark(int cat) {
+    if (!h->timing) return;
+    cudaEvent_t e = ev();
+    LGW_TRY_CUDA(h, cudaEventRecord(e, h->stream));
+    if (open) spans.push_back({open_cat, {open, e}});
+    open = e;
+    open_cat = cat;
+  }
+  void stop() {
+    if (!h->timing || !open) return;
+    cudaEvent_t e = ev();
+    LGW_TRY_CUDA(h, cudaEventRecord(e, h->stream));
+    spans.push_back({open_cat, {open, e}});
+    open = nullptr;
+  }
+  void collect(double *acc, int ncat) {
+    if (!h->timing) return;
+    LGW_TRY_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (auto &s : spans) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, s.second.first, s.second.second);
+      if (s.first >= 0 && s.first < ncat) acc[s.first] += ms;
+    }
+    spans.clear();
+  }
+};
+
+enum Cat { C_START, C_GEMM1, C_GEMM2, C_DOTS, C_UPDATE, C_PASS2, C_NORM, C_SPEC, C_CF, C_QP, C_N };
+
+void check_status(lgw_handle *h) {
+  unsigned st = 0;
+  LGW_TRY_CUDA(h, cudaMemcpyAsync(&st, h->d_status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+  LGW_TRY_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (st & ST_TIMEOUT) {
+    set_err(h, LGW_ERR_TIMEOUT, "a bounded device wait ran out");
+    throw Fail{LGW_ERR_TIMEOUT};
+  }
+  if (st & ST_NOT_SPD) {
+    set_err(h, LGW_ERR_NOT_SPD, "non-positive pair energy or Gauss node (C not positive definite)");
+    throw Fail{LGW_ERR_NOT_SPD};
+  }
+  if (st & ST_NO_CONV) {
+    set_err(h, LGW_ERR_NO_CONVERGENCE, "tridiagonal eigensolver or QP equation did not converge");
+    throw Fail{LGW_ERR_NO_CONVERGENCE};
+  }
+}
+
+struct Opts {
+  int k, precision, reorth, b_sub, qp_max_iter, use_graph;
+  double tol, qp_tol;
+};
+
+Opts resolve_opts(lgw_handle *h, const lgw_options *o, const SysDev &s) {
+  if (!o) {
+    set_err(h, LGW_ERR_ARG, "options pointer is NULL");
+    throw Fail{LGW_ERR_ARG};
+  }
+  Opts r;
+  r.k = o->k;
+  r.precision = o->precision;
+  r.reorth = o->reorth;
+  r.b_sub = o->b_sub;
+  r.qp_max_iter = o->qp_max_iter > 0 ? o->qp_max_iter : 50;
+  r.use_graph = o->use_graph;
+  r.tol = o->breakdown_tol > 0 ? o->breakdown_tol : 1e-13;
+  r.qp_tol = o->qp_tol > 0 ? o->qp_tol : 1e-10;
+  if (r.k < 1 || r.k > s.n_vc) {
+    set_err(h, LGW_ERR_ARG, "k = %d outside [1, n_vc = %d]", r.k, s.n_vc);
+    throw Fail{LGW_ERR_ARG};
+  }
+  if (r.k > 4095) {
+    set_err(h, LGW_ERR_UNSUPPORTED, "k = %d above the 4095-step limit of this build", r.k);
+    throw Fail{LGW_ERR_UNSUPPORTED};
+  }
+  if (r.precision != LGW_FP64 && r.precision != LGW_BF16) {
+    set_err(h, LGW_ERR_ARG, "unknown precision %d", r.precision);
+    throw Fail{LGW_ERR_ARG};
+  }
+  if (r.reorth < LGW_REORTH_NONE || r.reorth > LGW_REORTH_CGS1K) {
+    set_err(h, LGW_ERR_ARG, "unknown reorthogonalisation mode %d", r.reorth);
+    throw Fail{LGW_ERR_ARG};
+  }
+  if (r.b_sub < 0) {
+    set_err(h, LGW_ERR_ARG, "b_sub < 0");
+    throw Fail{LGW_ERR_ARG};
+  }
+  if (r.precision == LGW_BF16 && !tc_available()) {
+    set_err(h, LGW_ERR_UNSUPPORTED, "BF16 tensor-core path needs an sm_103 device");
+    throw Fail{LGW_ERR_UNSUPPORTED};
+  }
+  return r;
+}
+
+struct ProbView {
+  int n_t, n_m, n_freq, B;
+  std::vector<int> targets, m_idx;
+  const int *d_targets, *d_m_idx;
+  const double *d_M, *d_V, *d_omega, *d_shift;
+  double delta;
+};
+
+ProbView check_problem(lgw_handle *h, const SysDev &s, const lgw_problem *p) {
+  if (!p) {
+    set_err(h, LGW_ERR_ARG, "problem pointer is NULL");
+    throw Fail{LGW_ERR_ARG};
+  }
+  ProbView v{};
+  v.n_t = p->n_t;
+  v.n_m = p->n_m;
+  v.n_freq = p->n_freq;
+  if (v.n_t < 0 || v.n_m < 0 || v.n_freq < 0 || (v.n_t > 0 && !p->targets) ||
+      (v.n_m > 0 && !p->m_idx) || (v.n_freq > 0 && !p->omega)) {
+    set_err(h, LGW_ERR_ARG, "negative size or missing targets/m_idx/omega");
+    throw Fail{LGW_ERR_ARG};
+  }
+  if ((p->M == nullptr) == (p->V == nullptr)) {
+    set_err(h, LGW_ERR_ARG, "exactly one of M and V must be given");
+    throw Fail{LGW_ERR_ARG};
+  }
+  if (!(p->delta > 0.0)) {
+    set_err(h, LGW_ERR_ARG, "delta must be > 0");
+    throw Fail{LGW_ERR_ARG};
+  }
+  v.B = v.n_t * v.n_m;
+  v.targets = to_host(h, p->targets, v.n_t);
+  v.m_idx = to_host(h, p->m_idx, v.n_m);
+  const int norb = s.n_v + s.n_c;
+  for (int t : v.targets)
+    if (t < 0 || t >= norb) {
+      set_err(h, LGW_ERR_SHAPE, "target index %d outside [0, %d)", t, norb);
+      throw Fail{LGW_ERR_SHAPE};
+    }
+  for (int m : v.m_idx)
+    if (m < 0 || m >= norb) {
+      set_err(h, LGW_ERR_SHAPE, "summed index %d outside [0, %d)", m, norb);
+      throw Fail{LGW_ERR_SHAPE};
+    }
+  v.d_targets = in_dev(h, "in_targets", v.targets.data(), (size_t)v.n_t);
+  v.d_m_idx = in_dev(h, "in_midx", v.m_idx.data(), (size_t)v.n_m);
+  v.d_omega = in_dev(h, "in_omega", p->omega, (size_t)v.n_freq);
+  v.d_shift = p->static_shift ? in_dev(h, "in_shift", p->static_shift, (size_t)v.n_t) : nullptr;
+  v.d_M = p->M ? in_dev(h, "in_M", p->M, (size_t)v.B * s.n_aux) : nullptr;
+  v.d_V = p->V ? in_dev(h, "in_V", p->V, (size_t)v.B * s.n_vc) : nullptr;
+  v.delta = p->delta;
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos over all start vectors, sub-batch by sub-batch.
+// alpha/beta [B][k], beta0 [B], k_eff [B] are device arrays.
+// ---------------------------------------------------------------------------
+void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o, double *alpha,
+                 double *beta, double *beta0, int *k_eff, lgw_report *rep, double *tacc) {
+  cudaStream_t st = h->stream;
+  const int B = pv.B;
+  const int k = o.k;
+  if (B == 0) return;
+  LGW_TRY_CUDA(h, cudaMemsetAsync(alpha, 0, sizeof(double) * B * k, st));
+  LGW_TRY_CUDA(h, cudaMemsetAsync(beta, 0, sizeof(double) * B * k, st));
+  const bool tc = o.precision == LGW_BF16;
+  int nsub_req = o.b_sub > 0 ? o.b_sub : std::min(B, 512);
+  nsub_req = std::min(nsub_req, B);
+  int Bs = round_up(nsub_req, PAD_VEC);
+  if (tc) Bs = std::max(Bs, 64);
+  const int N = s.N;
+  const int nchunks = (N + VEC_CHUNK - 1) / VEC_CHUNK;
+  const int kmax1 = k + 1;
+  const bool reorth = o.reorth != LGW_REORTH_NONE;
+  const int nslots = reorth ? k + 1 : 3;
+
+  VecCtx c{};
+  c.N = N;
+  c.Bs = Bs;
+  c.nchunks = nchunks;
+  c.k = k;
+  c.kmax1 = kmax1;
+  c.reorth = o.reorth;
+  c.nslots = nslots;
+  c.tol = o.tol;
+  c.Delta2 = s.Delta2;
+  c.dsq = s.dsq;
+  c.cd = s.cd;
+  c.w = wsT<double>(h, "w", (size_t)Bs * N);
+  c.basis = wsT<double>(h, "basis", (size_t)nslots * Bs * N);
+  c.xh = tc ? wsT<__nv_bfloat16>(h, "xh", (size_t)Bs * N) : nullptr;
+  c.n_mt = tc ? tc_n_mt(s) : N / F64_TILE;
+  c.alpha_part = wsT<double>(h, "alpha_part", (size_t)c.n_mt * Bs);
+  c.dot_part = reorth ? wsT<double>(h, "dot_part", (size_t)Bs * nchunks * kmax1) : nullptr;
+  c.h = reorth ? wsT<double>(h, "hcoef", (size_t)Bs * kmax1) : nullptr;
+  c.norm_a = wsT<double>(h, "norm_a", (size_t)Bs * nchunks);
+  c.norm_b = wsT<double>(h, "norm_b", (size_t)Bs * nchunks);
+  c.norm_c = wsT<double>(h, "norm_c", (size_t)Bs * nchunks);
+  c.flag2 = wsT<int>(h, "flag2", (size_t)Bs);
+  c.amax = wsT<double>(h, "amax", (size_t)Bs);
+  c.betaj = wsT<double>(h, "betaj", (size_t)Bs);
+  c.alpha = alpha;
+  c.beta = beta;
+  c.beta0 = beta0;
+  c.k_eff = k_eff;
+  c.n_second = wsT<int>(h, "n_second", 1);
+  c.status = h->d_status;
+  LGW_TRY_CUDA(h, cudaMemsetAsync(c.n_second, 0, sizeof(int), st));
+  LGW_TRY_CUDA(h, cudaMemsetAsync(c.flag2, 0, sizeof(int) * Bs, st));
+
+  // contraction buffers
+  double *Y64 = wsT<double>(h, "y64", (size_t)Bs * s.A);
+  const int splits64 = gemm1_f64_splits(s, Bs);
+  double *Yp64 = tc ? nullptr : wsT<double>(h, "yp64", (size_t)splits64 * Bs * s.A);
+  TcPlan *plan = nullptr;
+  float *Yp32 = nullptr;
+  __nv_bfloat16 *Yh = nullptr;
+  int splits_tc = 1;
+  if (tc) {
+    // the split count only depends on shapes; size the partials generously
+    Yp32 = wsT<float>(h, "yp32", (size_t)64 * Bs * s.A);
+    Yh = wsT<__nv_bfloat16>(h, "yh", (size_t)Bs * s.A);
+    char err[256];
+    plan = tc_plan_create(s, Bs, c.xh, Yp32, Yh, &splits_tc, err, sizeof err);
+    if (!plan) {
+      set_err(h, LGW_ERR_CUDA, "%s", err);
+      throw Fail{LGW_ERR_CUDA};
+    }
+  }
+  struct PlanGuard {
+    TcPlan *p;
+    ~PlanGuard() {
+      if (p) tc_plan_destroy(p);
+    }
+  } guard{plan};
+
+  Timer tm(h);
+  int nsub = 0;
+  for (int vec0 = 0; vec0 < B; vec0 += nsub_req, ++nsub) {
+    const int nvec = std::min(nsub_req, B - vec0);
+    c.vec0 = vec0;
+    c.nvec = nvec;
+    // ---- start vectors b = Delta^1/2 V, V = L M (text after Eq. 8) ----
+    tm.mark(C_START);
+    if (pv.d_M) {
+      LGW_TRY_CUDA(h, cudaMemsetAsync(Y64, 0, sizeof(double) * Bs * s.A, st));
+      LGW_TRY_CUDA(h, cudaMemcpy2DAsync(Y64, sizeof(double) * s.A, pv.d_M + (size_t)vec0 * s.n_aux,
+                                        sizeof(double) * s.n_aux, sizeof(double) * s.n_aux, nvec,
+                                        cudaMemcpyDeviceToDevice, st));
+      launch_gemm2_f64(s, Y64, Bs, EPI_START, nullptr, nullptr, nullptr, c.w, nullptr, st);
+      check_launch(h, "gemm2_f64(start)");
+      // padding rows of w (b >= nvec) hold L*0 = 0 already
+      launch_norm_partials(c, c.w, c.norm_a, st);
+      check_launch(h, "norm_partials");
+    } else {
+      launch_start_from_v(c, pv.d_V + (size_t)vec0 * s.n_vc, s.n_vc, s.n_vc, st);
+      check_launch(h, "start_from_v");
+    }
+    launch_normalize(c, 0, 1, nullptr, st);
+    check_launch(h, "normalize(start)");
+
+    for (int j = 0; j < k; ++j) {
+      const double *qj = slot_ptr(c, j);
+      const double *qp = j > 0 ? slot_ptr(c, j - 1) : nullptr;
+      // ---- C q_j through the two contractions (Eq. 4) ----
+      tm.mark(C_GEMM1);
+      if (tc) {
+        launch_gemm1_tc(plan, h->d_status, st);
+        check_launch(h, "gemm1_tc");
+        launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, st);
+        check_launch(h, "reduce_y_bf16");
+        tm.mark(C_GEMM2);
+        launch_gemm2_tc(plan, EPI_LANCZOS, qj, qp, c.betaj, c.w, c.alpha_part, h->d_status, st);
+        check_launch(h, "gemm2_tc");
+      } else {
+        launch_gemm1_f64(s, qj, Bs, Yp64, splits64, st);
+        check_launch(h, "gemm1_f64");
+        launch_reduce_y_f64(Yp64, splits64, Bs, s.A, Y64, st);
+        check_launch(h, "reduce_y_f64");
+        tm.mark(C_GEMM2);
+        launch_gemm2_f64(s, Y64, Bs, EPI_LANCZOS, qj, qp, c.betaj, c.w, c.alpha_part, st);
+        check_launch(h, "gemm2_f64");
+      }
+      // ---- recurrence and reorthogonalisation ----
+      tm.mark(C_DOTS);
+      launch_alpha_axpy(c, j, st);
+      check_launch(h, "alpha_axpy");
+      if (reorth) {
+        launch_reduce_dots(c, j, 1, st);
+        check_launch(h, "reduce_dots");
+        tm.mark(C_UPDATE);
+        launch_update(c, j, 1, st);
+        check_launch(h, "update");
+        tm.mark(C_PASS2);
+        launch_second_pass_decide_j(c, j, st);
+        check_launch(h, "second_pass_decide");
+        launch_dots(c, j, 2, st);
+        check_launch(h, "dots2");
+        launch_reduce_dots(c, j, 2, st);
+        check_launch(h, "reduce_dots2");
+        launch_update(c, j, 2, st);
+        check_launch(h, "update2");
+      }
+      tm.mark(C_NORM);
+      launch_normalize(c, j, 0, nullptr, st);
+      check_launch(h, "normalize");
+    }
+  }
+  tm.stop();
+  if (rep) {
+    tm.collect(tacc, C_N);
+    int n2 = 0;
+    LGW_TRY_CUDA(h, cudaMemcpy(&n2, c.n_second, sizeof(int), cudaMemcpyDeviceToHost));
+    rep->n_second_pass = n2;
+    rep->n_sub_batches = nsub;
+    rep->b_sub = Bs;
+    rep->gemm1_splits = tc ? splits_tc : splits64;
+  }
+}
+
+void run_sigma(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o,
+               const double *alpha, const double *beta, const double *beta0, const int *k_eff,
+               double *sigma, double *e_qp, double *z_qp, lgw_report *rep, double *tacc) {
+  cudaStream_t st = h->stream;
+  const int B = pv.B, k = o.k;
+  Timer tm(h);
+  JacobiBufs jb;
+  jb.a = wsT<double>(h, "jac_a", (size_t)std::max(B, 1) * k);
+  jb.b2 = wsT<double>(h, "jac_b2", (size_t)std::max(B, 1) * k);
+  jb.w0 = wsT<double>(h, "jac_w0", (size_t)std::max(B, 1));
+  jb.n = wsT<int>(h, "jac_n", (size_t)std::max(B, 1));
+  double *scratch = wsT<double>(h, "spec_scratch", (size_t)3 * std::max(B, 1) * k);
+  unsigned long long *mt = wsT<unsigned long long>(h, "min_theta", 1);
+  const double big = 1e300;
+  unsigned long long bigbits;
+  std::memcpy(&bigbits, &big, sizeof big);
+  LGW_TRY_CUDA(h, cudaMemcpyAsync(mt, &bigbits, sizeof bigbits, cudaMemcpyHostToDevice, st));
+  tm.mark(C_SPEC);
+  if (B > 0) {
+    launch_spectral_impl(alpha, beta, beta0, k_eff, B, k, jb, scratch, mt, h->d_status, st);
+    check_launch(h, "spectral");
+  }
+  CfProblem cp{};
+  cp.n_t = pv.n_t;
+  cp.n_m = pv.n_m;
+  cp.n_freq = pv.n_freq;
+  cp.k = k;
+  cp.targets = pv.d_targets;
+  cp.m_idx = pv.d_m_idx;
+  cp.eps = s.eps;
+  cp.n_v = s.n_v;
+  cp.omega = pv.d_omega;
+  cp.delta = pv.delta;
+  cp.shift = pv.d_shift;
+  tm.mark(C_CF);
+  double *sig = sigma ? sigma : wsT<double>(h, "sigma_tmp", (size_t)std::max(1, pv.n_t * pv.n_freq * 2));
+  launch_cf_grid(cp, jb, sig, st);
+  if (pv.n_freq > 0 && pv.n_t > 0) check_launch(h, "cf_grid");
+  tm.mark(C_QP);
+  if (e_qp && pv.n_t > 0) {
+    launch_qp(cp, jb, sig, o.qp_max_iter, o.qp_tol, e_qp, z_qp, h->d_status, st);
+    check_launch(h, "qp");
+  }
+  tm.stop();
+  if (rep) {
+    tm.collect(tacc, C_N);
+    unsigned long long bits = 0;
+    LGW_TRY_CUDA(h, cudaMemcpy(&bits, mt, sizeof bits, cudaMemcpyDeviceToHost));
+    double mtv;
+    std::memcpy(&mtv, &bits, sizeof mtv);
+    rep->min_theta = mtv;
+  }
+}
+
+void fill_report_common(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o,
+                        const int *k_eff_dev, lgw_report *rep, const double *tacc) {
+  if (!rep) return;
+  rep->ms_start = tacc[C_START];
+  rep->ms_gemm1 = tacc[C_GEMM1];
+  rep->ms_gemm2 = tacc[C_GEMM2];
+  rep->ms_dots = tacc[C_DOTS];
+  rep->ms_update = tacc[C_UPDATE];
+  rep->ms_pass2 = tacc[C_PASS2];
+  rep->ms_normalize = tacc[C_NORM];
+  rep->ms_spectral = tacc[C_SPEC];
+  rep->ms_cf = tacc[C_CF];
+  rep->ms_qp = tacc[C_QP];
+  rep->n_vectors = pv.B;
+  std::vector<int> ke(pv.B);
+  if (pv.B) {
+    LGW_TRY_CUDA(h, cudaMemcpy(ke.data(), k_eff_dev, sizeof(int) * pv.B, cudaMemcpyDeviceToHost));
+  }
+  int kmin = o.k, kmax = 0;
+  double elems = 0.0;
+  for (int x : ke) {
+    kmin = std::min(kmin, x);
+    kmax = std::max(kmax, x);
+    elems += (double)s.n_vc * (double)x * (double)(x + 1) / 2.0;
+  }
+  rep->k_min = pv.B ? kmin : 0;
+  rep->k_max = kmax;
+  rep->gemm_flops = 4.0 * s.n_vc * (double)s.n_aux * (double)pv.B * (double)o.k;
+  rep->reorth_elems = o.reorth != LGW_REORTH_NONE ? elems : 0.0;
+}
+
+lgw_status guard_handle(lgw_handle *h) {
+  if (!h) return LGW_ERR_ARG;
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return set_err(h, LGW_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  h->last = LGW_OK;
+  h->msg.clear();
+  return LGW_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported C ABI
+// ===========================================================================
+extern "C" {
+
+const char *lgw_status_string(lgw_status s) {
+  switch (s) {
+    case LGW_OK: return "ok";
+    case LGW_ERR_ARG: return "invalid argument";
+    case LGW_ERR_SHAPE: return "inconsistent shape or index";
+    case LGW_ERR_CUDA: return "CUDA error";
+    case LGW_ERR_OOM: return "out of device memory";
+    case LGW_ERR_NOT_SPD: return "Casida matrix or Gauss node not positive";
+    case LGW_ERR_NO_CONVERGENCE: return "no convergence";
+    case LGW_ERR_TIMEOUT: return "device wait timed out";
+    case LGW_ERR_UNSUPPORTED: return "unsupported option";
+  }
+  return "unknown status";
+}
+
+lgw_status lgw_create(lgw_handle **out, int device, void *cuda_stream) {
+  if (!out) return LGW_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return LGW_ERR_ARG;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return LGW_ERR_CUDA;
+  lgw_handle *h = new lgw_handle();
+  h->device = device;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaMalloc(&h->d_status, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return LGW_ERR_OOM;
+  }
+  cudaMemset(h->d_status, 0, sizeof(unsigned));
+  *out = h;
+  return LGW_OK;
+}
+
+lgw_status lgw_destroy(lgw_handle *h) {
+  if (!h) return LGW_OK;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  for (auto &kv : h->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->d_status) cudaFree(h->d_status);
+  delete h;
+  return LGW_OK;
+}
+
+lgw_status lgw_last_error(lgw_handle *h, char *buf, size_t n) {
+  if (!h) return LGW_ERR_ARG;
+  if (buf && n) {
+    std::strncpy(buf, h->msg.c_str(), n - 1);
+    buf[n - 1] = '\0';
+  }
+  return h->last;
+}
+
+lgw_status lgw_prepare_system(lgw_handle *h, const lgw_system_desc *d, lgw_system **out) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!d || !out || !d->eps || !d->L) return set_err(h, LGW_ERR_ARG, "NULL descriptor field");
+  if (d->n_v < 1 || d->n_c < 1 || d->n_aux < 1)
+    return set_err(h, LGW_ERR_ARG, "n_v, n_c, n_aux must be >= 1");
+  if ((int64_t)d->n_v * d->n_c > (int64_t)1 << 30)
+    return set_err(h, LGW_ERR_SHAPE, "n_v * n_c too large");
+  if (!(d->kernel_factor >= 0.0)) return set_err(h, LGW_ERR_ARG, "kernel_factor must be >= 0");
+  *out = nullptr;
+  lgw_system *sys = new lgw_system();
+  sys->h = h;
+  SysDev &s = sys->s;
+  s.n_v = d->n_v;
+  s.n_c = d->n_c;
+  s.n_aux = d->n_aux;
+  s.n_vc = d->n_v * d->n_c;
+  s.N = round_up(s.n_vc, PAD_VC);
+  s.A = round_up(s.n_aux, PAD_AUX);
+  s.kf = d->kernel_factor;
+  std::vector<void *> allocs;
+  auto alloc = [&](size_t bytes) -> void * {
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    allocs.push_back(p);
+    return p;
+  };
+  const int norb = s.n_v + s.n_c;
+  s.eps = (double *)alloc(sizeof(double) * norb);
+  s.Delta = (double *)alloc(sizeof(double) * s.N);
+  s.dsq = (double *)alloc(sizeof(double) * s.N);
+  s.Delta2 = (double *)alloc(sizeof(double) * s.N);
+  s.cd = (double *)alloc(sizeof(double) * s.N);
+  s.L64 = (double *)alloc(sizeof(double) * (size_t)s.N * s.A);
+  s.Lb = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
+  s.Ltb = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
+  if (!s.eps || !s.Delta || !s.dsq || !s.Delta2 || !s.cd || !s.L64 || !s.Lb || !s.Ltb) {
+    for (void *p : allocs) cudaFree(p);
+    delete sys;
+    return set_err(h, LGW_ERR_OOM, "device allocation for the system failed");
+  }
+  try {
+    cudaStream_t st = h->stream;
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    if (is_device_ptr(d->eps))
+      LGW_TRY_CUDA(h, cudaMemcpyAsync(s.eps, d->eps, sizeof(double) * norb, cudaMemcpyDeviceToDevice, st));
+    else
+      LGW_TRY_CUDA(h, cudaMemcpyAsync(s.eps, d->eps, sizeof(double) * norb, cudaMemcpyHostToDevice, st));
+    const double *Lsrc = in_dev(h, "in_L", d->L, (size_t)s.n_vc * s.n_aux);
+    launch_pair_energies(s, st);
+    check_launch(h, "pair_energies");
+    launch_check_delta(s, h->d_status, st);
+    check_launch(h, "check_delta");
+    launch_pad_L(Lsrc, s, st);
+    check_launch(h, "pad_L");
+    launch_quantize_L(s, st);
+    check_launch(h, "quantize_L");
+    check_status(h);
+  } catch (Fail &f) {
+    for (void *p : allocs) cudaFree(p);
+    delete sys;
+    return f.st;
+  }
+  *out = sys;
+  return LGW_OK;
+}
+
+lgw_status lgw_release_system(lgw_system *sys) {
+  if (!sys) return LGW_OK;
+  cudaSetDevice(sys->h->device);
+  cudaStreamSynchronize(sys->h->stream);
+  SysDev &s = sys->s;
+  void *ps[] = {s.eps, s.Delta, s.dsq, s.Delta2, s.cd, s.L64, s.Lb, s.Ltb};
+  for (void *p : ps)
+    if (p) cudaFree(p);
+  delete sys;
+  return LGW_OK;
+}
+
+lgw_status lgw_apply_casida(lgw_handle *h, const lgw_system *sys, int32_t n_vec, const double *X,
+                            double *Y, int32_t precision) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!sys || sys->h != h || n_vec < 0 || (n_vec > 0 && (!X || !Y)))
+    return set_err(h, LGW_ERR_ARG, "bad arguments to lgw_apply_casida");
+  if (n_vec == 0) return LGW_OK;
+  if (precision != LGW_FP64 && precision != LGW_BF16) return set_err(h, LGW_ERR_ARG, "bad precision");
+  try {
+    const SysDev &s = sys->s;
+    cudaStream_t st = h->stream;
+    const bool tc = precision == LGW_BF16;
+    if (tc && !tc_available()) {
+      set_err(h, LGW_ERR_UNSUPPORTED, "BF16 tensor-core path needs an sm_103 device");
+      throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    const double *Xd = in_dev(h, "ap_xin", X, (size_t)n_vec * s.n_vc);
+    OutBuf<double> Yo;
+    Yo.init(h, "ap_yout", Y, (size_t)n_vec * s.n_vc);
+    int Bs = round_up(n_vec, PAD_VEC);
+    if (tc) Bs = std::max(Bs, 64);
+    double *xp = wsT<double>(h, "ap_x", (size_t)Bs * s.N);
+    double *wp = wsT<double>(h, "ap_w", (size_t)Bs * s.N);
+    LGW_TRY_CUDA(h, cudaMemsetAsync(xp, 0, sizeof(double) * Bs * s.N, st));
+    LGW_TRY_CUDA(h, cudaMemcpy2DAsync(xp, sizeof(double) * s.N, Xd, sizeof(double) * s.n_vc,
+                                      sizeof(double) * s.n_vc, n_vec, cudaMemcpyDeviceToDevice, st));
+    double *Y64 = wsT<double>(h, "y64", (size_t)Bs * s.A);
+    if (tc) {
+      __nv_bfloat16 *xh = wsT<__nv_bfloat16>(h, "ap_xh", (size_t)Bs * s.N);
+      float *yp = wsT<float>(h, "ap_yp32", (size_t)64 * Bs * s.A);
+      __nv_bfloat16 *yh = wsT<__nv_bfloat16>(h, "ap_yh", (size_t)Bs * s.A);
+      launch_scale_rows_to_bf16(xp, s.dsq, Bs, s.N, xh, st);
+      check_launch(h, "scale_rows_to_bf16");
+      char err[256];
+      int splits = 1;
+      TcPlan *plan = tc_plan_create(s, Bs, xh, yp, yh, &splits, err, sizeof err);
+      if (!plan) {
+        set_err(h, LGW_ERR_CUDA, "%s", err);
+        throw Fail{LGW_ERR_CUDA};
+      }
+      launch_gemm1_tc(plan, h->d_status, st);
+      check_launch(h, "gemm1_tc");
+      launch_reduce_y_bf16(yp, splits, Bs, s.A, yh, st);
+      check_launch(h, "reduce_y_bf16");
+      launch_gemm2_tc(plan, EPI_APPLY, xp, nullptr, nullptr, wp, nullptr, h->d_status, st);
+      check_launch(h, "gemm2_tc");
+      LGW_TRY_CUDA(h, cudaStreamSynchronize(st));
+      tc_plan_destroy(plan);
+    } else {
+      const int splits = gemm1_f64_splits(s, Bs);
+      double *yp = wsT<double>(h, "yp64", (size_t)splits * Bs * s.A);
+      launch_gemm1_f64(s, xp, Bs, yp, splits, st);
+      check_launch(h, "gemm1_f64");
+      launch_reduce_y_f64(yp, splits, Bs, s.A, Y64, st);
+      check_launch(h, "reduce_y_f64");
+      launch_gemm2_f64(s, Y64, Bs, EPI_APPLY, xp, nullptr, nullptr, wp, nullptr, st);
+      check_launch(h, "gemm2_f64");
+    }
+    LGW_TRY_CUDA(h, cudaMemcpy2DAsync(Yo.dev, sizeof(double) * s.n_vc, wp, sizeof(double) * s.N,
+                                      sizeof(double) * s.n_vc, n_vec, cudaMemcpyDeviceToDevice, st));
+    Yo.finish(h);
+    check_status(h);
+  } catch (Fail &f) {
+    return f.st;
+  }
+  return LGW_OK;
+}
+
+lgw_status lgw_lanczos_coeffs(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                              const lgw_options *o, double *alpha, double *beta, double *beta0,
+                              int32_t *k_eff) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!sys || sys->h != h || !alpha || !beta || !beta0 || !k_eff)
+    return set_err(h, LGW_ERR_ARG, "NULL argument to lgw_lanczos_coeffs");
+  try {
+    const SysDev &s = sys->s;
+    cudaStream_t st = h->stream;
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    Opts op = resolve_opts(h, o, s);
+    ProbView pv = check_problem(h, s, p);
+    OutBuf<double> a, b, b0;
+    OutBuf<int32_t> ke;
+    a.init(h, "out_alpha", alpha, (size_t)pv.B * op.k);
+    b.init(h, "out_beta", beta, (size_t)pv.B * op.k);
+    b0.init(h, "out_beta0", beta0, (size_t)pv.B);
+    ke.init(h, "out_keff", k_eff, (size_t)pv.B);
+    h->timing = false;
+    run_lanczos(h, s, pv, op, a.dev, b.dev, b0.dev, ke.dev, nullptr, nullptr);
+    a.finish(h);
+    b.finish(h);
+    b0.finish(h);
+    ke.finish(h);
+    check_status(h);
+  } catch (Fail &f) {
+    return f.st;
+  }
+  return LGW_OK;
+}
+
+lgw_status lgw_sigma_from_coeffs(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                                 const lgw_options *o, const double *alpha, const double *beta,
+                                 const double *beta0, const int32_t *k_eff, double *sigma,
+                                 double *e_qp, double *z_qp) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!sys || sys->h != h || !alpha || !beta || !beta0 || !k_eff)
+    return set_err(h, LGW_ERR_ARG, "NULL argument to lgw_sigma_from_coeffs");
+  try {
+    const SysDev &s = sys->s;
+    cudaStream_t st = h->stream;
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    Opts op = resolve_opts(h, o, s);
+    ProbView pv = check_problem(h, s, p);
+    const double *da = in_dev(h, "in_alpha", alpha, (size_t)pv.B * op.k);
+    const double *db = in_dev(h, "in_beta", beta, (size_t)pv.B * op.k);
+    const double *db0 = in_dev(h, "in_beta0", beta0, (size_t)pv.B);
+    const int *dke = in_dev(h, "in_keff", k_eff, (size_t)pv.B);
+    OutBuf<double> sg, e, z;
+    sg.init(h, "out_sigma", sigma, (size_t)pv.n_t * pv.n_freq * 2);
+    e.init(h, "out_eqp", e_qp, (size_t)pv.n_t);
+    z.init(h, "out_zqp", z_qp, (size_t)pv.n_t);
+    h->timing = false;
+    run_sigma(h, s, pv, op, da, db, db0, dke, sg.dev, e.dev, z.dev, nullptr, nullptr);
+    sg.finish(h);
+    e.finish(h);
+    z.finish(h);
+    check_status(h);
+  } catch (Fail &f) {
+    return f.st;
+  }
+  return LGW_OK;
+}
+
+lgw_status lgw_sigma_c(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                       const lgw_options *o, double *sigma, double *e_qp, double *z_qp,
+                       lgw_report *rep) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!sys || sys->h != h) return set_err(h, LGW_ERR_ARG, "bad system handle");
+  try {
+    const SysDev &s = sys->s;
+    cudaStream_t st = h->stream;
+    h->launches = 0;
+    h->ev_used = 0;
+    h->timing = rep != nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (rep) {
+      std::memset(rep, 0, sizeof *rep);
+      LGW_TRY_CUDA(h, cudaEventCreate(&t0));
+      LGW_TRY_CUDA(h, cudaEventCreate(&t1));
+      LGW_TRY_CUDA(h, cudaEventRecord(t0, st));
+    }
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    Opts op = resolve_opts(h, o, s);
+    ProbView pv = check_problem(h, s, p);
+    double tacc[C_N] = {0};
+    double *alpha = wsT<double>(h, "co_alpha", (size_t)std::max(1, pv.B) * op.k);
+    double *beta = wsT<double>(h, "co_beta", (size_t)std::max(1, pv.B) * op.k);
+    double *beta0 = wsT<double>(h, "co_beta0", (size_t)std::max(1, pv.B));
+    int *ke = wsT<int>(h, "co_keff", (size_t)std::max(1, pv.B));
+    OutBuf<double> sg, e, z;
+    sg.init(h, "out_sigma", sigma, (size_t)pv.n_t * pv.n_freq * 2);
+    e.init(h, "out_eqp", e_qp, (size_t)pv.n_t);
+    z.init(h, "out_zqp", z_qp, (size_t)pv.n_t);
+    run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, rep, tacc);
+    run_sigma(h, s, pv, op, alpha, beta, beta0, ke, sg.dev, e.dev, z.dev, rep, tacc);
+    sg.finish(h);
+    e.finish(h);
+    z.finish(h);
+    if (rep) {
+      LGW_TRY_CUDA(h, cudaEventRecord(t1, st));
+      LGW_TRY_CUDA(h, cudaEventSynchronize(t1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      fill_report_common(h, s, pv, op, ke, rep, tacc);
+      rep->ms_total = ms;
+      rep->gpu_launches = h->launches;
+    }
+    check_status(h);
+    h->timing = false;
+  } catch (Fail &f) {
+    h->timing = false;
+    return f.st;
+  }
+  return LGW_OK;
+}
+
+lgw_status lgw_sigma_c_batched(lgw_handle *h, int32_t n_sys, const lgw_system *const *systems,
+                               const lgw_problem *problems, const lgw_options *o,
+                               double *const *sigma, double *const *e_qp, double *const *z_qp,
+                               lgw_report *rep) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (n_sys < 0 || (n_sys > 0 && (!systems || !problems || !sigma || !e_qp)))
+    return set_err(h, LGW_ERR_ARG, "bad arguments to lgw_sigma_c_batched");
+  lgw_report total{};
+  for (int i = 0; i < n_sys; ++i) {
+    lgw_report r{};
+    lgw_status stt = lgw_sigma_c(h, systems[i], &problems[i], o, sigma[i], e_qp[i],
+                                 z_qp ? z_qp[i] : nullptr, rep ? &r : nullptr);
+    if (stt != LGW_OK) return stt;
+    if (rep) {
+      total.ms_total += r.ms_total;
+      total.ms_start += r.ms_start;
+      total.ms_gemm1 += r.ms_gemm1;
+      total.ms_gemm2 += r.ms_gemm2;
+      total.ms_dots += r.ms_dots;
+      total.ms_update += r.ms_update;
+      total.ms_pass2 += r.ms_pass2;
+      total.ms_normalize += r.ms_normalize;
+      total.ms_spectral += r.ms_spectral;
+      total.ms_cf += r.ms_cf;
+      total.ms_qp += r.ms_qp;
+      total.gemm_flops += r.gemm_flops;
+      total.reorth_elems += r.reorth_elems;
+      total.n_vectors += r.n_vectors;
+      total.n_sub_batches += r.n_sub_batches;
+      total.n_second_pass += r.n_second_pass;
+      total.gpu_launches += r.gpu_launches;
+      total.k_min = i == 0 ? r.k_min : std::min(total.k_min, r.k_min);
+      total.k_max = std::max(total.k_max, r.k_max);
+      total.min_theta = i == 0 ? r.min_theta : std::min(total.min_theta, r.min_theta);
+    }
+  }
+  if (rep) *rep = total;
+  return LGW_OK;
+}
+
+lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *, const lgw_problem *,
+                                const lgw_options *, const double *, double *, double *) {
+  if (!h) return LGW_ERR_ARG;
+  return set_err(h, LGW_ERR_UNSUPPORTED, "adjoint path not built in this library version");
+}
+
+}  // extern "C"

@@ -1,0 +1,203 @@
+// Internal declarations of the lgw library (GB300, sm_103a).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lgw.h"
+
+namespace lgw {
+
+// ---------------------------------------------------------------------------
+// Layout constants
+// ---------------------------------------------------------------------------
+constexpr int PAD_VC = 128;    // pair dimension N_vc padded to a multiple of the GEMM2 M tile
+constexpr int PAD_AUX = 128;   // N_aux padded to the GEMM1 M tile (also a multiple of the K block)
+constexpr int PAD_VEC = 16;    // start vectors per sub-batch padded to the UMMA N granule
+constexpr int VEC_THREADS = 256;
+constexpr int VEC_E = 8;                             // pair elements per thread
+constexpr int VEC_CHUNK = VEC_THREADS * VEC_E;       // pair elements per block
+constexpr int F64_TILE = 64;                         // CUDA-core FP64 GEMM tile
+
+// Device status bits (OR-ed into the handle's status word).
+enum : unsigned {
+  ST_NOT_SPD = 1u,
+  ST_NO_CONV = 2u,
+  ST_TIMEOUT = 4u,
+  ST_BAD_INPUT = 8u,
+};
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+inline int64_t round_up64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------------------
+// Device-side system: padded copies owned by the system.
+// ---------------------------------------------------------------------------
+struct SysDev {
+  int n_v, n_c, n_aux, n_vc;
+  int N;        // n_vc padded to PAD_VC
+  int A;        // n_aux padded to PAD_AUX
+  double kf;    // c_K
+  double *eps;      // [n_v + n_c]
+  double *Delta;    // [N]  eps_c - eps_v, 0 in the padding
+  double *dsq;      // [N]  Delta^1/2
+  double *Delta2;   // [N]  Delta^2
+  double *cd;       // [N]  c_K Delta^1/2
+  double *L64;      // [N][A] row-major, zero padded
+  __nv_bfloat16 *Lb;    // [N][A]   K-major operand of the L Y contraction
+  __nv_bfloat16 *Ltb;   // [A][N]   K-major operand of the L^T X contraction
+};
+
+// ---------------------------------------------------------------------------
+// One sub-batch of start vectors (Bs padded vectors, vector length N).
+// ---------------------------------------------------------------------------
+struct VecCtx {
+  int N, Bs, nvec, nchunks;
+  int k, kmax1;           // steps requested; k + 1
+  int vec0;               // global index of the first vector of the sub-batch
+  int reorth;             // lgw_reorth
+  int nslots;             // basis slots (k + 1 with reorthogonalisation, else 3)
+  double tol;
+  const double *Delta2, *dsq, *cd;
+  double *w;              // [Bs][N]
+  double *basis;          // slot s: basis + s * Bs * N
+  __nv_bfloat16 *xh;      // [Bs][N]   bf16(Delta^1/2 q_j)
+  double *alpha_part;     // [n_mt][Bs]
+  int n_mt;
+  double *dot_part;       // [Bs][nchunks][kmax1]
+  double *h;              // [Bs][kmax1]
+  double *norm_a, *norm_b, *norm_c;   // [Bs][nchunks]
+  int *flag2;             // [Bs] second CGS pass taken
+  double *amax;           // [Bs]
+  double *betaj;          // [Bs] beta_j for the running step
+  double *alpha, *beta, *beta0;   // global [B][k], [B][k], [B]
+  int *k_eff;             // global [B]
+  int *n_second;          // counter of second passes
+  unsigned *status;
+};
+
+__host__ __device__ inline double *slot_ptr(const VecCtx &c, int j) {
+  int s = (c.reorth != LGW_REORTH_NONE) ? j : (j % 3);
+  return c.basis + (size_t)s * c.Bs * c.N;
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum in fixed order; every thread gets the result.  `red` needs
+// blockDim.x / 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+// Transposed warp reduction of 32 values per lane: afterwards a[0] of lane l
+// holds sum over all lanes of the original a[l].  31 shuffles per lane.
+__device__ __forceinline__ void warp_transpose_sum32(double (&a)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      double send = up ? a[i] : a[i + off];
+      double keep = up ? a[i + off] : a[i];
+      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+}
+
+// Bounded device wait limit in clock cycles (about one second at 2 GHz).
+constexpr long long WAIT_CYCLES = 2000000000LL;
+
+// ---------------------------------------------------------------------------
+// Host launchers (defined in the kernel files).  All take the stream last.
+// ---------------------------------------------------------------------------
+// k_prep.cu
+void launch_pair_energies(const SysDev &s, cudaStream_t st);
+void launch_pad_L(const double *L, const SysDev &s, cudaStream_t st);
+void launch_quantize_L(const SysDev &s, cudaStream_t st);
+void launch_check_delta(const SysDev &s, unsigned *status, cudaStream_t st);
+
+// k_gemm_f64.cu : CUDA-core FP64 contractions
+// Ypart[split][Bs][A] = sum_vc (Delta^1/2 q)[b][vc] L[vc][mu] over the split's vc range
+int gemm1_f64_splits(const SysDev &s, int Bs);
+void launch_gemm1_f64(const SysDev &s, const double *q, int Bs, double *Ypart, int splits,
+                      cudaStream_t st);
+void launch_reduce_y_f64(const double *Ypart, int splits, int Bs, int A, double *Y, cudaStream_t st);
+// U[b][vc] = sum_mu Y[b][mu] L[vc][mu]; epilogue:
+//   EPI_START:   w = Delta^1/2 U
+//   EPI_LANCZOS: w = Delta^2 q + c_K Delta^1/2 U - beta_j q_prev; alpha partials per 64-row tile
+enum { EPI_START = 0, EPI_LANCZOS = 1, EPI_APPLY = 2 };
+void launch_gemm2_f64(const SysDev &s, const double *Y, int Bs, int epi, const double *q,
+                      const double *qprev, const double *betaj, double *w, double *alpha_part,
+                      cudaStream_t st);
+
+// k_gemm_tc.cu : BF16 tcgen05 contractions
+struct TcPlan;
+bool tc_available();
+TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *ypart,
+                       __nv_bfloat16 *yh, int *splits_out, char *err, size_t errn);
+void tc_plan_destroy(TcPlan *p);
+void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st);
+void launch_reduce_y_bf16(const float *Ypart, int splits, int Bs, int A, __nv_bfloat16 *Yh,
+                          cudaStream_t st);
+void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qprev,
+                     const double *betaj, double *w, double *alpha_part, unsigned *status,
+                     cudaStream_t st);
+int tc_n_mt(const SysDev &s);
+
+// k_lanczos.cu : vector kernels of one step
+void launch_start_from_v(const VecCtx &c, const double *V, int ldv, int n_valid, cudaStream_t st);
+void launch_norm_partials(const VecCtx &c, const double *x, double *out, cudaStream_t st);
+void launch_normalize(const VecCtx &c, int j, int is_start, const double *norm, cudaStream_t st);
+void launch_alpha_axpy(const VecCtx &c, int j, cudaStream_t st);
+void launch_reduce_dots(const VecCtx &c, int j, int pass, cudaStream_t st);
+void launch_update(const VecCtx &c, int j, int pass, cudaStream_t st);
+void launch_dots(const VecCtx &c, int j, int pass, cudaStream_t st);
+void launch_second_pass_decide_j(const VecCtx &c, int j, cudaStream_t st);
+void launch_scale_rows_to_bf16(const double *x, const double *dsq, int Bs, int N,
+                               __nv_bfloat16 *out, cudaStream_t st);
+
+// k_spectral.cu : tridiagonal -> Gauss rule -> Omega-space Jacobi matrix
+struct JacobiBufs {
+  double *a;    // [B][k]
+  double *b2;   // [B][k]  b2[i][j] = b_{j+1}^2 couples j and j+1
+  double *w0;   // [B]     total weight (zeroth moment)
+  int *n;       // [B]     depth
+};
+// scratch: 3 * B * k doubles; min_theta_bits: running minimum of the Gauss
+// nodes (positive doubles compare like their bit patterns)
+void launch_spectral_impl(const double *alpha, const double *beta, const double *beta0,
+                          const int *k_eff, int B, int k, JacobiBufs jb, double *scratch,
+                          unsigned long long *min_theta_bits, unsigned *status, cudaStream_t st);
+
+// k_cf.cu : continued fractions on the grid and QP solve
+struct CfProblem {
+  int n_t, n_m, n_freq, k;
+  const int *targets, *m_idx;   // device
+  const double *eps;            // device [n_v + n_c]
+  int n_v;
+  const double *omega;          // device [n_freq]
+  double delta;
+  const double *shift;          // device [n_t] or nullptr
+};
+void launch_cf_grid(const CfProblem &p, JacobiBufs jb, double *sigma, cudaStream_t st);
+void launch_qp(const CfProblem &p, JacobiBufs jb, const double *sigma, int max_iter, double tol,
+               double *e_qp, double *z_qp, unsigned *status, cudaStream_t st);
+
+}  // namespace lgw
