@@ -1,0 +1,381 @@
+"""Throughput benchmark of the Lanczos GW hot path on GB300.
+
+One step = one lgw_sigma_c call on the mid-size system (N_v=128, N_c=1024,
+N_vc=131072, N_aux=2048, k=200 Lanczos steps with full CGS2
+reorthogonalisation, 1000 frequencies) for a batch of target states, each
+summed over 256 orbitals: start vectors, every Lanczos step, spectral map,
+continued fractions on the grid and the QP solve.  Metric: QP states per
+second (higher is better), whole job over all ranks.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "QP states/sec & Lanczos GEMM TFLOP/s, mixed vs FP64 plain path at 1 meV"
+M_PER_TARGET = 256
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), \
+            d.get("bf16_tflops_sustained", 1700.0), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                s, mx = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            sm.append(s)
+            smax.append(mx)
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = sorted(sm)[len(sm) // 4:] or sm   # drop the idle quarter
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (reported baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(n_vec=2, k=200, seed=1):
+    """Oracle Lanczos (numpy FP64, CGS2) + Gauss-rule pole sums on n_vec start
+    vectors of the mid-size system; returns (seconds, states/s, cores)."""
+    import gw_inputs
+    import oracle as O
+    wl = gw_inputs.mid(n_targets=1, k=k)
+    wl.M = wl.M[:, :n_vec]
+    wl.m_idx = wl.m_idx[:n_vec]
+    t0 = time.perf_counter()
+    sig, poles, _ = O.sigma_lanczos(wl, k=k)
+    O.solve_all_qp(wl, poles)
+    dt = time.perf_counter() - t0
+    per_state = dt / n_vec * M_PER_TARGET
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    return dt, 1.0 / per_state, cores
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    k = args.k
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, sps, cores = oracle_sample(n_vec=args.ref_vectors, k=k)
+        if i >= args.warmup:
+            times.append(dt)
+    per_step = statistics.mean(times)
+    value = args.ref_vectors / per_step / M_PER_TARGET
+    sample = (f"{args.ref_vectors} start vectors (of 256 per QP state) of the N_vc=131072, "
+              f"N_aux=2048 system, k={k} CGS2 Lanczos + pole-sum Sigma + QP per step; "
+              f"states/s = vectors/s / 256")
+    line = {
+        "metric": METRIC, "value": value, "unit": "QP states/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": _config(args), "gpu_launches": 0,
+        "cpu_baseline": {"value": value, "unit": "QP states/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "QP states/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(args):
+    return {"workload": (f"Lanczos GW Sigma_c + QP, N_v=128 N_c=1024 (N_vc=131072) "
+                         f"N_aux=2048, k={args.k} {args.reorth.upper()}, {args.tps} targets x "
+                         f"256 summed orbitals per step, 1000 frequencies"),
+            "n_vc": 131072, "n_aux": 2048, "k": args.k, "targets_per_step": args.tps,
+            "start_vectors_per_step": args.tps * M_PER_TARGET, "n_freq": 1000,
+            "reorth": args.reorth, "precision": args.precision,
+            "l2": "inputs larger than L2 (Krylov basis ~107 GB, bf16 L 2x0.54 GB)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import gw_inputs
+    from paper_2310_20103_gb300 import lgw as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    wl = gw_inputs.mid(n_targets=32, k=args.k)
+    n_t_all = wl.n_t
+    stream = torch.cuda.current_stream(dev)
+    h = L.lgw_create(local, stream)
+    eps_d = torch.from_numpy(wl.eps).to(dev)
+    L_d = torch.from_numpy(wl.L).to(dev)
+    M_all = torch.from_numpy(wl.M).to(dev)
+    omega_d = torch.from_numpy(wl.omega).to(dev)
+    m_idx_d = torch.from_numpy(wl.m_idx).to(dev)
+    tgt_all = torch.from_numpy(wl.targets).to(dev)
+    sysd = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, eps_d, L_d, wl.kernel_factor)
+    opts = L.Options(k=args.k, precision=args.precision, reorth=args.reorth,
+                     b_sub=args.tps * M_PER_TARGET)
+    tps = args.tps
+    sig = torch.empty(tps, wl.omega.size, 2, dtype=torch.float64, device=dev)
+    e = torch.empty(tps, dtype=torch.float64, device=dev)
+    z = torch.empty(tps, dtype=torch.float64, device=dev)
+
+    def batch(i):
+        off = ((i * world + rank) * tps) % n_t_all
+        sl = slice(off, off + tps)
+        return L.Problem(targets=tgt_all[sl].contiguous(), m_idx=m_idx_d, omega=omega_d,
+                         delta=wl.delta, M=M_all[sl].contiguous())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for i in range(args.warmup):
+        L.lgw_sigma_c(h, sysd, batch(i), opts, sig, e, z)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    reps = []
+    for i in range(args.steps):
+        reps.append(L.lgw_sigma_c(h, sysd, batch(args.warmup + i), opts, sig, e, z,
+                                  report=True))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    states = tps * args.steps * world
+    value = states / (ms_max / 1e3)
+
+    # --- end to end through the public API with pinned host buffers ---
+    eps_h = torch.from_numpy(wl.eps).pin_memory()
+    L_h = torch.from_numpy(wl.L).pin_memory()
+    M_h = torch.from_numpy(wl.M).pin_memory()
+    om_h = torch.from_numpy(wl.omega).pin_memory()
+    mi_h = torch.from_numpy(wl.m_idx).pin_memory()
+    tg_h = torch.from_numpy(wl.targets).pin_memory()
+    sig_h = torch.empty(tps, wl.omega.size, 2, dtype=torch.float64).pin_memory()
+    e_h = torch.empty(tps, dtype=torch.float64).pin_memory()
+    z_h = torch.empty(tps, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    h2d = d2h = 0
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        off = ((i * world + rank) * tps) % n_t_all
+        Mb = M_h[off:off + tps]
+        tb = tg_h[off:off + tps]
+        s2 = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, eps_h, L_h, wl.kernel_factor)
+        prob = L.Problem(targets=tb, m_idx=mi_h, omega=om_h, delta=wl.delta, M=Mb)
+        L.lgw_sigma_c(h, s2, prob, opts, sig_h, e_h, z_h)
+        L.lgw_release_system(s2)
+        h2d = (eps_h.numel() + L_h.numel() + Mb.numel() + om_h.numel()) * 8 + \
+            (tb.numel() + mi_h.numel()) * 4
+        d2h = (sig_h.numel() + e_h.numel() + z_h.numel()) * 8
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = tps * e2e_steps * world / float(te.item())
+
+    # --- per-kernel breakdown from the timed steps (CUDA events on the stream) ---
+    agg = {k: sum(r[k] for r in reps) for k in reps[0] if k.startswith("ms_") or k in (
+        "gemm_flops", "reorth_elems", "gpu_launches", "n_second_pass")}
+    r0 = reps[0]
+    nvc, A = wl.n_vc, wl.n_aux
+    B = r0["n_vectors"] * args.steps
+    kk = args.k
+    launches_per_cat = r0["n_sub_batches"] * kk * args.steps
+    hbm, bf16_burst, bf16_sus, peak_src = _peaks()
+    by = {
+        "update": (8.0 * agg["reorth_elems"] + 16.0 * nvc * B * kk, agg["ms_update"],
+                   "k_update (first Gram-Schmidt update w -= Q h)"),
+        "dots": (8.0 * agg["reorth_elems"] + 24.0 * nvc * B * kk, agg["ms_dots"],
+                 "k_alpha_axpy (alpha, axpy, first-pass Q^T w)"),
+    }
+    dom = max(by, key=lambda x: by[x][1])
+    bytes_, ms_k, kname = by[dom]
+    achieved = bytes_ / (ms_k / 1e3) / 1e9
+    gemm_ms = agg["ms_gemm1"] + agg["ms_gemm2"]
+    gemm_tflops = agg["gemm_flops"] / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "QP states/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 contractions, f64 recurrence/reorth/CF" if args.precision == "bf16" else "f64",
+        "data": "synthetic (seeded stand-in for the Si-cluster workloads)",
+        "config": _config(args),
+        "gpu_launches": int(agg["gpu_launches"]),
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "QP states/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
+                     "traffic": None, "launches": launches_per_cat,
+                     "avg_launch_ms": ms_k / launches_per_cat},
+        "gemm": {"tflops": gemm_tflops, "peak_bf16_tflops": bf16_sus,
+                 "frac": (gemm_tflops / bf16_sus) if gemm_tflops else None,
+                 "ms_gemm1": agg["ms_gemm1"], "ms_gemm2": agg["ms_gemm2"],
+                 "splits": r0["gemm1_splits"]},
+        "breakdown_ms": {k: agg[k] for k in agg if k.startswith("ms_")},
+    }
+    if rank == 0 and world == 1 and not args.no_fp64_compare:
+        line["fp64_path"] = fp64_compare(args, L, h, sysd, wl, tgt_all, m_idx_d, omega_d, M_all,
+                                         dev)
+        if line["fp64_path"].get("value"):
+            line["fp64_path"]["mixed_over_fp64"] = value / line["fp64_path"]["value"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, sps, cores = oracle_sample(n_vec=args.ref_vectors, k=args.k)
+        line["cpu_baseline"] = {
+            "value": sps, "unit": "QP states/s", "cores": cores, "kind": "oracle",
+            "sample": f"{args.ref_vectors} of 256 start vectors of one QP state, k={args.k} "
+                      f"CGS2, numpy FP64 ({dt:.1f} s); extrapolated x256/{args.ref_vectors}"}
+    L.lgw_release_system(sysd)
+    L.lgw_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def fp64_compare(args, L, h, sysd, wl, tgt_all, m_idx_d, omega_d, M_all, dev):
+    """The plain FP64 path on a subsample: one target with the first n_m
+    summed orbitals, both precisions, same k and reorthogonalisation; gives
+    the FP64 states/s (vectors/s / 256) and the QP difference in meV."""
+    import torch
+    n_m = args.fp64_vectors
+    prob = L.Problem(targets=tgt_all[:1].contiguous(), m_idx=m_idx_d[:n_m].contiguous(),
+                     omega=omega_d, delta=wl.delta, M=M_all[:1, :n_m].contiguous())
+    out = {}
+    for prec in ("fp64", "bf16"):
+        sg = torch.empty(1, wl.omega.size, 2, dtype=torch.float64, device=dev)
+        ee = torch.empty(1, dtype=torch.float64, device=dev)
+        o = L.Options(k=args.k, precision=prec, reorth=args.reorth)
+        L.lgw_sigma_c(h, sysd, prob, o, sg, ee)          # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.lgw_sigma_c(h, sysd, prob, o, sg, ee)
+        torch.cuda.synchronize()
+        out[prec] = (time.perf_counter() - t0, sg.cpu().numpy(), float(ee.item()))
+    t64 = out["fp64"][0]
+    dsig = np.abs(out["bf16"][1] - out["fp64"][1]).max() * 1e3
+    return {"value": n_m / t64 / M_PER_TARGET, "unit": "QP states/s",
+            "sample": f"1 target x {n_m} summed orbitals (of 256), same k and reorth; "
+                      f"states/s = vectors/s / 256",
+            "seconds": t64, "qp_diff_mev_bf16_vs_fp64": abs(out["bf16"][2] - out["fp64"][2]) * 1e3,
+            "sigma_max_diff_mev": dsig}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lgw", choices=["lgw", "reference"])
+    ap.add_argument("--k", type=int, default=200)
+    ap.add_argument("--tps", type=int, default=2, help="target states per step")
+    ap.add_argument("--reorth", default="cgs2", choices=["cgs2", "cgs1k", "none"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--fp64-vectors", type=int, default=16)
+    ap.add_argument("--ref-vectors", type=int, default=2)
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

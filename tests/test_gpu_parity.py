@@ -149,11 +149,17 @@ def test_tiny_fp64_full_k_vs_closed_form(L, handle, tiny_ref):
 
 
 def test_tiny_bf16_within_1meV(L, handle, tiny_ref):
+    """BF16 contractions: QP energies within 1 meV of the FP64 closed form.
+    On the grid, with k = N_vc (Gauss nodes = Casida eigenvalues, so only
+    the BF16 perturbation of C moves them), Sigma stays within 1% of the
+    closed form; near a pole |dSigma| ~ (w/delta^2) dOmega, and BF16
+    rounding (2^-9) of the coupling moves Omega by well under delta."""
     wl, _, (sigx, Ex, Zx) = tiny_ref
     sig, e, z, _ = _run(L, handle, wl, L.Options(k=64, precision="bf16", reorth="cgs2"))
     assert np.abs(e - Ex).max() < 1e-3
-    # Sigma on the grid: BF16 contractions perturb the screening term only
-    assert _rel_sigma_err(sig, sigx) < 5e-2
+    sigf, ef, _, _ = _run(L, handle, wl, L.Options(k=wl.n_vc, precision="bf16", reorth="cgs2"))
+    assert np.abs(ef - Ex).max() < 1e-3
+    assert _rel_sigma_err(sigf, sigx) < 1e-2
 
 
 def test_coefficients_vs_oracle(L, handle, tiny_ref):
