@@ -275,12 +275,21 @@ def run_gpu(args):
     kk = args.k
     launches_per_cat = r0["n_sub_batches"] * kk * args.steps
     hbm, bf16_burst, bf16_sus, peak_src = _peaks()
-    by = {
-        "update": (8.0 * agg["reorth_elems"] + 16.0 * nvc * B * kk, agg["ms_update"],
-                   "k_update (first Gram-Schmidt update w -= Q h)"),
-        "dots": (8.0 * agg["reorth_elems"] + 24.0 * nvc * B * kk, agg["ms_dots"],
-                 "k_alpha_axpy (alpha, axpy, first-pass Q^T w)"),
-    }
+    split = args.precision == "bf16"     # the library's automatic choice
+    if split:   # float-pair basis: hi+lo read by the dots, hi by the update
+        by = {
+            "update": (4.0 * agg["reorth_elems"] + 16.0 * nvc * B * kk, agg["ms_update"],
+                       "k_update_split<1> (w -= Q h in FP32 from the hi basis)"),
+            "dots": (8.0 * agg["reorth_elems"] + 24.0 * nvc * B * kk, agg["ms_dots"],
+                     "k_dots_split<1> (alpha axpy + double-float Q^T w)"),
+        }
+    else:
+        by = {
+            "update": (8.0 * agg["reorth_elems"] + 16.0 * nvc * B * kk, agg["ms_update"],
+                       "k_update (first Gram-Schmidt update w -= Q h)"),
+            "dots": (8.0 * agg["reorth_elems"] + 24.0 * nvc * B * kk, agg["ms_dots"],
+                     "k_alpha_axpy (alpha, axpy, first-pass Q^T w)"),
+        }
     dom = max(by, key=lambda x: by[x][1])
     bytes_, ms_k, kname = by[dom]
     achieved = bytes_ / (ms_k / 1e3) / 1e9

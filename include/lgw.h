@@ -75,6 +75,17 @@ typedef enum {
                            / Daniel-Gragg-Kaufman-Stewart criterion)              */
 } lgw_reorth;
 
+/* Arithmetic of the full reorthogonalisation.
+ * LGW_RA_FP64:  basis stored in FP64, every product and sum on the FP64 pipe.
+ * LGW_RA_SPLIT: basis stored as float pairs (hi + lo, 48 significant bits);
+ *               dot products in double-float arithmetic on the FP32 pipe; the
+ *               update applies the two O(||w||) coefficients (q_j, q_{j-1}) in
+ *               FP64 and the O(eps||w||) rest in FP32 from the hi part.
+ *               Orthogonality stays at FP64 level; the FP64 pipe, which runs at
+ *               1/58 of the FP32 rate on GB300, leaves the inner loops.
+ * LGW_RA_AUTO:  SPLIT with BF16 contractions, FP64 with FP64 contractions. */
+typedef enum { LGW_RA_AUTO = 0, LGW_RA_FP64 = 1, LGW_RA_SPLIT = 2 } lgw_reorth_arith;
+
 typedef struct lgw_handle lgw_handle;
 typedef struct lgw_system lgw_system;
 
@@ -120,7 +131,8 @@ typedef struct {
  *                (0: 1e-13)
  * qp_max_iter    Newton iterations before the bracketing fallback (0: 50)
  * qp_tol         |dE| <= qp_tol * max(1,|E|) ends Newton (0: 1e-10)
- * use_graph      1: capture one Lanczos step as a CUDA graph and replay it */
+ * use_graph      1: capture one Lanczos step as a CUDA graph and replay it
+ * reorth_arith   arithmetic of the Gram-Schmidt passes (lgw_reorth_arith) */
 typedef struct {
   int32_t k;
   int32_t precision;
@@ -130,7 +142,7 @@ typedef struct {
   int32_t qp_max_iter;
   double qp_tol;
   int32_t use_graph;
-  int32_t reserved;
+  int32_t reorth_arith;
 } lgw_options;
 
 /* Filled by calls that take a report pointer (host memory).  Phase times are

@@ -168,9 +168,12 @@ struct EpiArgs {
   const double *Delta2, *cd, *q, *qprev, *betaj;
   double *w, *alpha_part;
   unsigned *status;
+  // split-basis epilogue (FP32)
+  const float *qh, *qph, *d2f, *cdf;
+  float *ucd;
 };
 
-enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2 };
+enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2, E_LANCZOS_NA = 3, E_SPLITB = 4 };
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -187,7 +190,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   double *red = reinterpret_cast<double *>(smem + C::STAGES * C::STAGE + C::BAR_BYTES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m_tile = blockIdx.x, n_tile = blockIdx.y, split = blockIdx.z;
+  // N tiles vary fastest so the CTAs sharing an L tile run together (second
+  // read from L2); each CTA starts its K loop at a different block so that
+  // concurrent CTAs do not stream the same column offset of the row-strided
+  // operand at the same time (spreads the requests over HBM channels).
+  const int n_tiles = gridDim.y;
+  const int lin = blockIdx.x * n_tiles + blockIdx.y;
+  const int m_tile = lin / n_tiles, n_tile = lin % n_tiles, split = blockIdx.z;
   const int kb0 = split * kb_per_split;
   const int kb1 = min(num_kb, kb0 + kb_per_split);
   const int nk = max(0, kb1 - kb0);
@@ -215,7 +224,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(&empty[s], ph ^ 1, ea.status)) break;
         mbar_expect_tx(&full[s], C::STAGE);
         uint8_t *sa = smem + s * C::STAGE;
-        const int kx = (kb0 + it) * BK;
+        const int kx = (kb0 + (it + m_tile) % nk) * BK;
         tma_load_2d(sa, &tmA, &full[s], kx, m_tile * BM);
         tma_load_2d(sa + C::A_BYTES, &tmB, &full[s], kx, n_tile * BN);
         issued = it + 1;
@@ -249,9 +258,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int row = m_tile * BM + qd * 32 + lane;
     const int ncol0 = n_tile * BN;
     double d2 = 0.0, cdr = 0.0;
-    if (EPI != E_SPLITK && row < M) {
+    float d2f = 0.f, cdf = 0.f;
+    if (EPI != E_SPLITK && EPI != E_SPLITB && row < M) {
       d2 = ea.Delta2[row];
       cdr = ea.cd[row];
+    }
+    if (EPI == E_SPLITB && row < M) {
+      d2f = ea.d2f[row];
+      cdf = ea.cdf[row];
     }
     for (int c0 = 0; c0 < BN; c0 += 32) {
       uint32_t r[32];
@@ -267,6 +281,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int col = ncol0 + c0 + i;
           if (col < Ncols && row < M) out[(size_t)col * ea.ldo + row] = __uint_as_float(r[i]);
         }
+      } else if (EPI == E_SPLITB) {
+        float acc[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = ncol0 + c0 + i;
+          acc[i] = 0.f;
+          if (col < Ncols && row < M) {
+            const size_t o = (size_t)col * ea.N + row;
+            const float up = cdf * __uint_as_float(r[i]);
+            ea.ucd[o] = up;
+            const float qf = ea.qh[o];
+            float t = fmaf(d2f, qf, up);
+            if (ea.qph != nullptr) t = fmaf(-(float)ea.betaj[col], ea.qph[o], t);
+            acc[i] = qf * t;
+          }
+        }
+        // transposed warp reduction, FP32: lane l ends with column c0 + l
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+          const bool up = (lane & off) != 0;
+#pragma unroll
+          for (int i = 0; i < off; ++i) {
+            const float send = up ? acc[i] : acc[i + off];
+            const float keep = up ? acc[i + off] : acc[i];
+            acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+          }
+        }
+        red[qd * BN + c0 + lane] = (double)acc[0];
       } else {
         double acc[32];
 #pragma unroll
@@ -278,7 +320,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const double u = (double)__uint_as_float(r[i]);
             const double qv = ea.q[o];
             double wv = fma(d2, qv, cdr * u);
-            if (EPI == E_LANCZOS && ea.qprev != nullptr) wv = fma(-ea.betaj[col], ea.qprev[o], wv);
+            if ((EPI == E_LANCZOS || EPI == E_LANCZOS_NA) && ea.qprev != nullptr)
+              wv = fma(-ea.betaj[col], ea.qprev[o], wv);
             ea.w[o] = wv;
             acc[i] = qv * wv;
           }
@@ -289,7 +332,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-    if (EPI == E_LANCZOS) {
+    if (EPI == E_LANCZOS || EPI == E_SPLITB) {
       asm volatile("bar.sync 1, 128;" ::: "memory");
       const int te = threadIdx.x - 64;
       for (int col = te; col < BN; col += 128) {
@@ -331,6 +374,7 @@ struct TcPlan {
   float *ypart;
   __nv_bfloat16 *yh;
   const double *Delta2, *cd;
+  const float *d2f, *cdf;
 };
 
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -417,6 +461,8 @@ TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *
   p->yh = yh;
   p->Delta2 = s.Delta2;
   p->cd = s.cd;
+  p->d2f = s.d2f;
+  p->cdf = s.cdf;
   bool ok = encode_2d(&p->g1A, s.Ltb, (uint64_t)s.N, (uint64_t)s.A, tc::BM) &&
             encode_2d(&p->g1B, xh, (uint64_t)s.N, (uint64_t)Bs, (uint32_t)p->BN) &&
             encode_2d(&p->g2A, s.Lb, (uint64_t)s.A, (uint64_t)s.N, tc::BM) &&
@@ -488,10 +534,29 @@ void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qp
   ea.alpha_part = alpha_part;
   ea.status = status;
   const int num_kb = p->A / tc::BK;
-  if (epi == EPI_LANCZOS)
+  if (epi == EPI_LANCZOS && alpha_part == nullptr)
+    dispatch_bn<tc::E_LANCZOS_NA>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+  else if (epi == EPI_LANCZOS)
     dispatch_bn<tc::E_LANCZOS>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
   else
     dispatch_bn<tc::E_APPLY>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+}
+
+void launch_gemm2_tc_split(const TcPlan *p, const float *qh, const float *qph,
+                           const double *betaj, float *ucd, double *alpha_part, unsigned *status,
+                           cudaStream_t st) {
+  tc::EpiArgs ea{};
+  ea.N = p->N;
+  ea.qh = qh;
+  ea.qph = qph;
+  ea.d2f = p->d2f;
+  ea.cdf = p->cdf;
+  ea.betaj = betaj;
+  ea.ucd = ucd;
+  ea.alpha_part = alpha_part;
+  ea.status = status;
+  const int num_kb = p->A / tc::BK;
+  dispatch_bn<tc::E_SPLITB>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
 }
 
 }  // namespace lgw

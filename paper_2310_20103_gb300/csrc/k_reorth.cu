@@ -1,0 +1,383 @@
+// Full reorthogonalisation against a split-precision Krylov basis.
+//
+// GB300 executes FP64 at ~1/58 of its FP32 rate (1.2 vs 70 TFLOP/s), so a
+// Gram-Schmidt pass with one DFMA per 8-byte basis element stalls on the FP64
+// pipe well below HBM bandwidth.  Here every basis vector q_i is stored as a
+// pair of floats (q_hi = fl32(q), q_lo = fl32(q - q_hi); q_hi + q_lo carries
+// 48 significant bits) and the recurrence keeps exact FP64 copies of
+// q_{j-1}, q_j, q_{j+1} in a three-slot ring.
+//
+//  dots   h_i = q_i . w in double-float arithmetic on the FP32 pipe: the
+//         product q_hi w_hi is split exactly with an FMA, the cross terms are
+//         added in FP32, and the running sum is a (hi, lo) pair updated by
+//         Knuth's TwoSum (non-contracted intrinsics).  Relative error of a
+//         partial ~2^-48 of sum |q_i,e w_e|, comparable to FP64 summation.
+//  alpha  alpha_j = q_j . w from the contraction epilogue's partials, and
+//         w <- w - alpha_j q_j in FP64 (exact q_j from the ring) BEFORE the
+//         projections, as in the three-term recurrence of Eq. 13.  Projecting
+//         alpha_j q_j out inside classical Gram-Schmidt instead would leave
+//         residues ~ ||Q^T Q - I|| alpha_j / beta_{j+1} that grow every step.
+//  update w <- w - sum_i h_i q_i.  After the alpha subtraction every h_i is
+//         O(eps ||w||) (or O(u_bf16 ||w||) from the slight asymmetry of the
+//         BF16 operator), so the sum is formed in FP32 from q_hi alone (4
+//         bytes per element); its rounding is far below the FP64 resolution
+//         of w.  The second pass (where taken) is identical.
+//
+// Block layout as in the FP64 kernels: one block per (chunk of VEC_CHUNK
+// elements, vector), eight elements per thread.
+#include "lgw_internal.cuh"
+
+namespace lgw {
+
+__device__ __forceinline__ int elem_base_s(int chunk) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  return chunk * VEC_CHUNK + wid * 256 + 2 * lane;
+}
+
+__device__ __forceinline__ bool live_s(const VecCtx &c, int b, int j) {
+  return b < c.nvec && c.k_eff[c.vec0 + b] > j;
+}
+
+// (s_hi, s_lo) += p exactly representable part via TwoSum; never contracted.
+__device__ __forceinline__ void two_sum_acc(float &s_hi, float &s_lo, float p) {
+  const float s = __fadd_rn(s_hi, p);
+  const float bb = __fsub_rn(s, s_hi);
+  const float err = __fadd_rn(__fsub_rn(s_hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  s_hi = s;
+  s_lo = __fadd_rn(s_lo, err);
+}
+
+// Double-float sum of two (hi, lo) pairs.
+__device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl) {
+  const float s = __fadd_rn(ah, bh);
+  const float bb = __fsub_rn(s, ah);
+  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  ah = s;
+  al = __fadd_rn(__fadd_rn(al, bl), err);
+}
+
+__device__ __forceinline__ const float *bhi_row(const VecCtx &c, int i, int b) {
+  return c.bhi + ((size_t)i * c.Bs + b) * c.N;
+}
+__device__ __forceinline__ const float *blo_row(const VecCtx &c, int i, int b) {
+  return c.blo + ((size_t)i * c.Bs + b) * c.N;
+}
+
+// One lane's share of a row . w over a VEC_CHUNK chunk in double-float:
+// four quarters of 512 elements, each lane a float4 of hi and of lo per 128
+// elements (4 + 4 independent 128-bit loads per quarter).
+__device__ __forceinline__ void dot_row_df(const float *__restrict__ qh,
+                                           const float *__restrict__ ql, const float *swh,
+                                           const float *swl, int lane, int nvalid, float &sh,
+                                           float &sl) {
+#pragma unroll
+  for (int qt = 0; qt < 4; ++qt) {
+    float4 hv[4], lv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int off = qt * 512 + 128 * t + 4 * lane;
+      if (off < nvalid) {
+        hv[t] = __ldg(reinterpret_cast<const float4 *>(qh + off));
+        lv[t] = __ldg(reinterpret_cast<const float4 *>(ql + off));
+      } else {
+        hv[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        lv[t] = hv[t];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int off = qt * 512 + 128 * t + 4 * lane;
+      const float4 a = *reinterpret_cast<const float4 *>(swh + off);
+      const float4 al = *reinterpret_cast<const float4 *>(swl + off);
+      const float qa[4] = {hv[t].x, hv[t].y, hv[t].z, hv[t].w};
+      const float qb[4] = {lv[t].x, lv[t].y, lv[t].z, lv[t].w};
+      const float wa[4] = {a.x, a.y, a.z, a.w};
+      const float wb[4] = {al.x, al.y, al.z, al.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float pr = __fmul_rn(qa[q], wa[q]);
+        float err = __fmaf_rn(qa[q], wa[q], -pr);
+        err = __fmaf_rn(qa[q], wb[q], err);
+        err = __fmaf_rn(qb[q], wa[q], err);
+        two_sum_acc(sh, sl, pr);
+        sl = __fadd_rn(sl, err);
+      }
+    }
+  }
+}
+
+// Dot products of w with basis rows 0..j.  Pass 1 first finishes alpha_j,
+// applies w <- w - alpha_j q_j and writes ||w||^2 partials (norm_a).
+//
+// The block's chunk of w is split once into (hi, lo) floats in shared memory;
+// then each warp takes whole rows (i = warp, warp + 8, ...) over the chunk:
+// every lane streams 8 independent 128-bit loads per quarter row, accumulates
+// its 64 products in double-float, and one 5-step butterfly gives the row's
+// partial.  No block barrier inside the row loop.
+template <int PASS>
+__global__ void __launch_bounds__(VEC_THREADS, 2) k_dots_split(VecCtx c, int j) {
+  __shared__ __align__(16) float swh[VEC_CHUNK];
+  __shared__ __align__(16) float swl[VEC_CHUNK];
+  __shared__ double red[VEC_THREADS / 32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  if (!live_s(c, b, j)) return;
+  if (PASS == 2 && !c.flag2[b]) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double alpha = 0.0;
+  if (PASS == 1) {
+    double s = 0.0;
+    for (int t = threadIdx.x; t < c.n_mt; t += VEC_THREADS)
+      s += c.alpha_part[(size_t)t * c.Bs + b];
+    alpha = block_sum(s, red);
+    // alpha used for the subtraction; k_reduce_dots_split adds the residual
+    // projection h_j so the recorded alpha_j is the FP64 Rayleigh quotient
+    if (chunk == 0 && threadIdx.x == 0) c.alpha[(size_t)(c.vec0 + b) * c.k + j] = alpha;
+  }
+  double *w = c.w + (size_t)b * c.N;
+  const double *qj = slot_ptr(c, j) + (size_t)b * c.N;
+  const double *qp = (j >= 1) ? slot_ptr(c, j - 1) + (size_t)b * c.N : nullptr;
+  const float *ucd = c.ucd ? c.ucd + (size_t)b * c.N : nullptr;
+  const double bj = c.betaj[b];
+  const int cbase = chunk * VEC_CHUNK;
+  const int e0 = elem_base_s(chunk);
+  double nrm = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    double2 w2 = make_double2(0.0, 0.0);
+    if (e < c.N) {
+      if (PASS == 1) {
+        const double2 q2 = *reinterpret_cast<const double2 *>(qj + e);
+        if (ucd != nullptr) {
+          // w = Delta^2 q_j + c_K Delta^1/2 (L y) - beta_j q_{j-1}   (Eq. 4, 13)
+          const float2 u2 = *reinterpret_cast<const float2 *>(ucd + e);
+          w2.x = fma(c.Delta2[e], q2.x, (double)u2.x);
+          w2.y = fma(c.Delta2[e + 1], q2.y, (double)u2.y);
+          if (qp != nullptr) {
+            const double2 p2 = *reinterpret_cast<const double2 *>(qp + e);
+            w2.x = fma(-bj, p2.x, w2.x);
+            w2.y = fma(-bj, p2.y, w2.y);
+          }
+        } else {
+          w2 = *reinterpret_cast<const double2 *>(w + e);
+        }
+        w2.x = fma(-alpha, q2.x, w2.x);
+        w2.y = fma(-alpha, q2.y, w2.y);
+        *reinterpret_cast<double2 *>(w + e) = w2;
+      } else {
+        w2 = *reinterpret_cast<const double2 *>(w + e);
+      }
+    }
+    nrm = fma(w2.x, w2.x, fma(w2.y, w2.y, nrm));
+    const float hx = __double2float_rn(w2.x), hy = __double2float_rn(w2.y);
+    const int le = e - cbase;
+    swh[le] = hx;
+    swh[le + 1] = hy;
+    swl[le] = __double2float_rn(w2.x - (double)hx);
+    swl[le + 1] = __double2float_rn(w2.y - (double)hy);
+  }
+  if (PASS == 1) {
+    nrm = block_sum(nrm, red);   // contains a __syncthreads
+    if (threadIdx.x == 0) c.norm_a[(size_t)b * c.nchunks + chunk] = nrm;
+  } else {
+    __syncthreads();
+  }
+  const int nvalid = min(VEC_CHUNK, c.N - cbase);   // multiple of 128
+  double *dp = c.dot_part + ((size_t)b * c.nchunks + chunk) * c.kmax1;
+  for (int i = wid; i <= j; i += VEC_THREADS / 32) {
+    const float *qh = bhi_row(c, i, b) + cbase;
+    const float *ql = blo_row(c, i, b) + cbase;
+    float sh = 0.f, sl = 0.f;
+    dot_row_df(qh, ql, swh, swl, lane, nvalid, sh, sl);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const float rh = __shfl_xor_sync(0xffffffffu, sh, o);
+      const float rl = __shfl_xor_sync(0xffffffffu, sl, o);
+      df_add(sh, sl, rh, rl);
+    }
+    if (lane == 0) dp[i] = (double)sh + (double)sl;
+  }
+}
+
+// h[b][i] = sum over chunks (fixed order).
+__global__ void k_reduce_dots_split(VecCtx c, int j, int pass) {
+  const int b = blockIdx.x;
+  if (!live_s(c, b, j)) return;
+  if (pass == 2 && !c.flag2[b]) return;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double *p = c.dot_part + (size_t)b * c.nchunks * c.kmax1 + i;
+    double s = 0.0;
+    for (int ch = 0; ch < c.nchunks; ++ch) s += p[(size_t)ch * c.kmax1];
+    c.h[(size_t)b * c.kmax1 + i] = s;
+    if (pass == 1 && i == j) {
+      const size_t ai = (size_t)(c.vec0 + b) * c.k + j;
+      const double a = c.alpha[ai] + s;
+      c.alpha[ai] = a;
+      c.amax[b] = fmax(c.amax[b], fabs(a));
+    }
+  }
+}
+
+// w <- w - Q h with every coefficient small: FP32 products and sum from q_hi.
+template <int PASS>
+__global__ void __launch_bounds__(VEC_THREADS) k_update_split(VecCtx c, int j) {
+  extern __shared__ float hsf[];
+  __shared__ double red[VEC_THREADS / 32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  if (!live_s(c, b, j)) return;
+  if (PASS == 2 && !c.flag2[b]) return;
+  const double *hb = c.h + (size_t)b * c.kmax1;
+  const int nrows = j + 1;
+  for (int i = threadIdx.x; i < nrows; i += VEC_THREADS) hsf[i] = (float)hb[i];
+  __syncthreads();
+  const size_t voff = (size_t)b * c.N;
+  double *w = c.w + voff;
+  const int e0 = elem_base_s(chunk);
+  float r[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) r[t] = 0.f;
+  for (int i = 0; i < nrows; ++i) {
+    const float hf = hsf[i];
+    const float *qh = bhi_row(c, i, b);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * 64;
+      if (e < c.N) {
+        const float2 q2 = *reinterpret_cast<const float2 *>(qh + e);
+        r[2 * u] = fmaf(hf, q2.x, r[2 * u]);
+        r[2 * u + 1] = fmaf(hf, q2.y, r[2 * u + 1]);
+      }
+    }
+  }
+  double nrm = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= c.N) continue;
+    double2 w2 = *reinterpret_cast<const double2 *>(w + e);
+    w2.x -= (double)r[2 * u];
+    w2.y -= (double)r[2 * u + 1];
+    *reinterpret_cast<double2 *>(w + e) = w2;
+    nrm = fma(w2.x, w2.x, fma(w2.y, w2.y, nrm));
+  }
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) (PASS == 1 ? c.norm_b : c.norm_c)[(size_t)b * c.nchunks + chunk] = nrm;
+}
+
+// Second pass where the first pass removed more than half of ||w||^2
+// (1/sqrt(2) norm criterion), or always (CGS2).
+__global__ void k_second_pass_decide_split(VecCtx c, int j) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= c.Bs) return;
+  int f = 0;
+  if (live_s(c, b, j)) {
+    if (c.reorth == LGW_REORTH_CGS2) {
+      f = 1;
+    } else {
+      double na = 0.0, nb = 0.0;
+      for (int ch = 0; ch < c.nchunks; ++ch) {
+        na += c.norm_a[(size_t)b * c.nchunks + ch];
+        nb += c.norm_b[(size_t)b * c.nchunks + ch];
+      }
+      f = nb < 0.5 * na;
+      if (f) atomicAdd(c.n_second, 1);
+    }
+  }
+  c.flag2[b] = f;
+}
+
+// beta = ||w||, breakdown test, q_next = w / beta into the FP64 ring, the
+// split basis slot and the bf16 contraction operand.  is_start: w = b_tm.
+__global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j, int is_start) {
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const int v = c.vec0 + b;
+  const bool real = b < c.nvec;
+  bool live = real && (is_start || c.k_eff[v] > j);
+  double beta = 0.0;
+  if (live) {
+    const double *np = is_start ? c.norm_a : (c.flag2[b] ? c.norm_c : c.norm_b);
+    if (!is_start && c.reorth == LGW_REORTH_NONE) np = c.norm_a;
+    double s = 0.0;
+    for (int ch = 0; ch < c.nchunks; ++ch) s += np[(size_t)b * c.nchunks + ch];
+    beta = sqrt(s);
+    if (is_start) {
+      if (chunk == 0 && threadIdx.x == 0) {
+        c.beta0[v] = beta;
+        c.k_eff[v] = beta > 0.0 ? c.k : 0;
+        c.amax[b] = 0.0;
+        c.betaj[b] = 0.0;
+      }
+      live = beta > 0.0;
+    } else {
+      const bool stop = !(beta > c.tol * c.amax[b]);
+      if (chunk == 0 && threadIdx.x == 0) {
+        c.beta[(size_t)v * c.k + j] = beta;
+        c.betaj[b] = beta;
+        if (stop) c.k_eff[v] = j + 1;
+      }
+      if (stop) live = false;
+    }
+  } else if (chunk == 0 && threadIdx.x == 0) {
+    c.betaj[b] = 0.0;
+  }
+  const int next = is_start ? 0 : j + 1;
+  const size_t voff = (size_t)b * c.N;
+  double *qn = slot_ptr(c, next) + voff;
+  const bool keep_basis = next < c.k + 1;
+  float *hn = c.bhi + ((size_t)next * c.Bs + b) * c.N;
+  float *ln = c.blo + ((size_t)next * c.Bs + b) * c.N;
+  const double *w = c.w + voff;
+  const double inv = live ? 1.0 / beta : 0.0;
+  const int e0 = elem_base_s(chunk);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= c.N) continue;
+    double2 q2 = make_double2(0.0, 0.0);
+    if (live) {
+      q2 = *reinterpret_cast<const double2 *>(w + e);
+      q2.x *= inv;
+      q2.y *= inv;
+    }
+    *reinterpret_cast<double2 *>(qn + e) = q2;
+    const float hx = __double2float_rn(q2.x), hy = __double2float_rn(q2.y);
+    if (keep_basis) {
+      *reinterpret_cast<float2 *>(hn + e) = make_float2(hx, hy);
+      *reinterpret_cast<float2 *>(ln + e) = make_float2(__double2float_rn(q2.x - (double)hx),
+                                                        __double2float_rn(q2.y - (double)hy));
+    }
+    if (c.xh != nullptr) {
+      __nv_bfloat162 x2;
+      x2.x = __float2bfloat16_rn(c.dsqf[e] * hx);
+      x2.y = __float2bfloat16_rn(c.dsqf[e + 1] * hy);
+      *reinterpret_cast<__nv_bfloat162 *>(c.xh + voff + e) = x2;
+    }
+  }
+}
+
+static dim3 grid_s(const VecCtx &c) { return dim3(c.nchunks, c.Bs); }
+
+void launch_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st) {
+  if (pass == 1)
+    k_dots_split<1><<<grid_s(c), VEC_THREADS, 0, st>>>(c, j);
+  else
+    k_dots_split<2><<<grid_s(c), VEC_THREADS, 0, st>>>(c, j);
+}
+void launch_reduce_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st) {
+  k_reduce_dots_split<<<c.Bs, 256, 0, st>>>(c, j, pass);
+}
+void launch_update_split(const VecCtx &c, int j, int pass, cudaStream_t st) {
+  const size_t sh = (size_t)c.kmax1 * sizeof(float);
+  if (pass == 1)
+    k_update_split<1><<<grid_s(c), VEC_THREADS, sh, st>>>(c, j);
+  else
+    k_update_split<2><<<grid_s(c), VEC_THREADS, sh, st>>>(c, j);
+}
+void launch_second_pass_decide_split(const VecCtx &c, int j, cudaStream_t st) {
+  k_second_pass_decide_split<<<(c.Bs + 255) / 256, 256, 0, st>>>(c, j);
+}
+void launch_normalize_split(const VecCtx &c, int j, int is_start, cudaStream_t st) {
+  k_normalize_split<<<grid_s(c), VEC_THREADS, 0, st>>>(c, j, is_start);
+}
+
+}  // namespace lgw

@@ -228,7 +228,7 @@ void check_status(lgw_handle *h) {
 }
 
 struct Opts {
-  int k, precision, reorth, b_sub, qp_max_iter, use_graph;
+  int k, precision, reorth, b_sub, qp_max_iter, use_graph, split;
   double tol, qp_tol;
 };
 
@@ -244,6 +244,12 @@ Opts resolve_opts(lgw_handle *h, const lgw_options *o, const SysDev &s) {
   r.b_sub = o->b_sub;
   r.qp_max_iter = o->qp_max_iter > 0 ? o->qp_max_iter : 50;
   r.use_graph = o->use_graph;
+  if (o->reorth_arith < LGW_RA_AUTO || o->reorth_arith > LGW_RA_SPLIT) {
+    set_err(h, LGW_ERR_ARG, "unknown reorthogonalisation arithmetic %d", o->reorth_arith);
+    throw Fail{LGW_ERR_ARG};
+  }
+  r.split = o->reorth_arith == LGW_RA_SPLIT ||
+            (o->reorth_arith == LGW_RA_AUTO && o->precision == LGW_BF16);
   r.tol = o->breakdown_tol > 0 ? o->breakdown_tol : 1e-13;
   r.qp_tol = o->qp_tol > 0 ? o->qp_tol : 1e-10;
   if (r.k < 1 || r.k > s.n_vc) {
@@ -348,7 +354,8 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   const int nchunks = (N + VEC_CHUNK - 1) / VEC_CHUNK;
   const int kmax1 = k + 1;
   const bool reorth = o.reorth != LGW_REORTH_NONE;
-  const int nslots = reorth ? k + 1 : 3;
+  const bool split = reorth && o.split;
+  const int nslots = (reorth && !split) ? k + 1 : 3;
 
   VecCtx c{};
   c.N = N;
@@ -357,13 +364,20 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   c.k = k;
   c.kmax1 = kmax1;
   c.reorth = o.reorth;
+  c.ring = (reorth && !split) ? 0 : 1;
   c.nslots = nslots;
   c.tol = o.tol;
   c.Delta2 = s.Delta2;
   c.dsq = s.dsq;
   c.cd = s.cd;
   c.w = wsT<double>(h, "w", (size_t)Bs * N);
-  c.basis = wsT<double>(h, "basis", (size_t)nslots * Bs * N);
+  c.basis = wsT<double>(h, split ? "ring" : "basis", (size_t)nslots * Bs * N);
+  if (split) {
+    c.bhi = wsT<float>(h, "basis_hi", (size_t)(k + 1) * Bs * N);
+    c.blo = wsT<float>(h, "basis_lo", (size_t)(k + 1) * Bs * N);
+  }
+  c.dsqf = s.dsqf;
+  c.ucd = (split && tc) ? wsT<float>(h, "ucd", (size_t)Bs * N) : nullptr;
   c.xh = tc ? wsT<__nv_bfloat16>(h, "xh", (size_t)Bs * N) : nullptr;
   c.n_mt = tc ? tc_n_mt(s) : N / F64_TILE;
   c.alpha_part = wsT<double>(h, "alpha_part", (size_t)c.n_mt * Bs);
@@ -432,7 +446,10 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
       launch_start_from_v(c, pv.d_V + (size_t)vec0 * s.n_vc, s.n_vc, s.n_vc, st);
       check_launch(h, "start_from_v");
     }
-    launch_normalize(c, 0, 1, nullptr, st);
+    if (split)
+      launch_normalize_split(c, 0, 1, st);
+    else
+      launch_normalize(c, 0, 1, nullptr, st);
     check_launch(h, "normalize(start)");
 
     for (int j = 0; j < k; ++j) {
@@ -446,7 +463,13 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
         launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, st);
         check_launch(h, "reduce_y_bf16");
         tm.mark(C_GEMM2);
-        launch_gemm2_tc(plan, EPI_LANCZOS, qj, qp, c.betaj, c.w, c.alpha_part, h->d_status, st);
+        if (split)
+          launch_gemm2_tc_split(plan, c.bhi + (size_t)j * Bs * N,
+                                j > 0 ? c.bhi + (size_t)(j - 1) * Bs * N : nullptr, c.betaj,
+                                const_cast<float *>(c.ucd), c.alpha_part, h->d_status, st);
+        else
+          launch_gemm2_tc(plan, EPI_LANCZOS, qj, qp, c.betaj, c.w, c.alpha_part, h->d_status,
+                          st);
         check_launch(h, "gemm2_tc");
       } else {
         launch_gemm1_f64(s, qj, Bs, Yp64, splits64, st);
@@ -459,6 +482,28 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
       }
       // ---- recurrence and reorthogonalisation ----
       tm.mark(C_DOTS);
+      if (split) {
+        launch_dots_split(c, j, 1, st);
+        check_launch(h, "dots_split");
+        launch_reduce_dots_split(c, j, 1, st);
+        check_launch(h, "reduce_dots_split");
+        tm.mark(C_UPDATE);
+        launch_update_split(c, j, 1, st);
+        check_launch(h, "update_split");
+        tm.mark(C_PASS2);
+        launch_second_pass_decide_split(c, j, st);
+        check_launch(h, "second_pass_decide_split");
+        launch_dots_split(c, j, 2, st);
+        check_launch(h, "dots_split2");
+        launch_reduce_dots_split(c, j, 2, st);
+        check_launch(h, "reduce_dots_split2");
+        launch_update_split(c, j, 2, st);
+        check_launch(h, "update_split2");
+        tm.mark(C_NORM);
+        launch_normalize_split(c, j, 0, st);
+        check_launch(h, "normalize_split");
+        continue;
+      }
       launch_alpha_axpy(c, j, st);
       check_launch(h, "alpha_axpy");
       if (reorth) {
@@ -689,10 +734,14 @@ lgw_status lgw_prepare_system(lgw_handle *h, const lgw_system_desc *d, lgw_syste
   s.dsq = (double *)alloc(sizeof(double) * s.N);
   s.Delta2 = (double *)alloc(sizeof(double) * s.N);
   s.cd = (double *)alloc(sizeof(double) * s.N);
+  s.dsqf = (float *)alloc(sizeof(float) * s.N);
+  s.d2f = (float *)alloc(sizeof(float) * s.N);
+  s.cdf = (float *)alloc(sizeof(float) * s.N);
   s.L64 = (double *)alloc(sizeof(double) * (size_t)s.N * s.A);
   s.Lb = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
   s.Ltb = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
-  if (!s.eps || !s.Delta || !s.dsq || !s.Delta2 || !s.cd || !s.L64 || !s.Lb || !s.Ltb) {
+  if (!s.eps || !s.Delta || !s.dsq || !s.Delta2 || !s.cd || !s.dsqf || !s.d2f || !s.cdf ||
+      !s.L64 || !s.Lb || !s.Ltb) {
     for (void *p : allocs) cudaFree(p);
     delete sys;
     return set_err(h, LGW_ERR_OOM, "device allocation for the system failed");
@@ -728,7 +777,7 @@ lgw_status lgw_release_system(lgw_system *sys) {
   cudaSetDevice(sys->h->device);
   cudaStreamSynchronize(sys->h->stream);
   SysDev &s = sys->s;
-  void *ps[] = {s.eps, s.Delta, s.dsq, s.Delta2, s.cd, s.L64, s.Lb, s.Ltb};
+  void *ps[] = {s.eps, s.Delta, s.dsq, s.Delta2, s.cd, s.dsqf, s.d2f, s.cdf, s.L64, s.Lb, s.Ltb};
   for (void *p : ps)
     if (p) cudaFree(p);
   delete sys;

@@ -45,6 +45,9 @@ struct SysDev {
   double *dsq;      // [N]  Delta^1/2
   double *Delta2;   // [N]  Delta^2
   double *cd;       // [N]  c_K Delta^1/2
+  float *dsqf;      // [N]  Delta^1/2 rounded to float (bf16 operand scaling)
+  float *d2f;       // [N]  Delta^2 rounded to float   (alpha estimate)
+  float *cdf;       // [N]  c_K Delta^1/2 rounded to float (FP32 epilogue)
   double *L64;      // [N][A] row-major, zero padded
   __nv_bfloat16 *Lb;    // [N][A]   K-major operand of the L Y contraction
   __nv_bfloat16 *Ltb;   // [A][N]   K-major operand of the L^T X contraction
@@ -58,12 +61,17 @@ struct VecCtx {
   int k, kmax1;           // steps requested; k + 1
   int vec0;               // global index of the first vector of the sub-batch
   int reorth;             // lgw_reorth
-  int nslots;             // basis slots (k + 1 with reorthogonalisation, else 3)
+  int ring;               // 1: FP64 vectors live in a 3-slot ring (slot j % 3)
+  int nslots;             // FP64 slots (k + 1 for the FP64 basis, else 3)
   double tol;
   const double *Delta2, *dsq, *cd;
   double *w;              // [Bs][N]
   double *basis;          // slot s: basis + s * Bs * N
   __nv_bfloat16 *xh;      // [Bs][N]   bf16(Delta^1/2 q_j)
+  float *bhi, *blo;       // split basis [k+1][Bs][N]: q = hi + lo (48 bits)
+  const float *dsqf;      // [N]
+  const float *ucd;       // [Bs][N] c_K Delta^1/2 (L y) from the FP32 epilogue, or null
+                          // (then w holds the full FP64 epilogue result)
   double *alpha_part;     // [n_mt][Bs]
   int n_mt;
   double *dot_part;       // [Bs][nchunks][kmax1]
@@ -79,7 +87,7 @@ struct VecCtx {
 };
 
 __host__ __device__ inline double *slot_ptr(const VecCtx &c, int j) {
-  int s = (c.reorth != LGW_REORTH_NONE) ? j : (j % 3);
+  int s = c.ring ? (j % 3) : j;
   return c.basis + (size_t)s * c.Bs * c.N;
 }
 
@@ -159,6 +167,12 @@ void launch_reduce_y_bf16(const float *Ypart, int splits, int Bs, int A, __nv_bf
 void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qprev,
                      const double *betaj, double *w, double *alpha_part, unsigned *status,
                      cudaStream_t st);
+// FP32 epilogue for the split basis: ucd = c_K Delta^1/2 U (float) and FP32
+// estimates of alpha_j = q_j . (Delta^2 q_j + ucd - beta_j q_{j-1}) per tile,
+// from the hi parts of q_j and q_{j-1} (qph may be null at step 0).
+void launch_gemm2_tc_split(const TcPlan *p, const float *qh, const float *qph,
+                           const double *betaj, float *ucd, double *alpha_part, unsigned *status,
+                           cudaStream_t st);
 int tc_n_mt(const SysDev &s);
 
 // k_lanczos.cu : vector kernels of one step
@@ -170,6 +184,12 @@ void launch_reduce_dots(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_update(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_dots(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_second_pass_decide_j(const VecCtx &c, int j, cudaStream_t st);
+// k_reorth.cu : split-precision basis (double-float dots, FP32 small updates)
+void launch_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st);
+void launch_reduce_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st);
+void launch_update_split(const VecCtx &c, int j, int pass, cudaStream_t st);
+void launch_second_pass_decide_split(const VecCtx &c, int j, cudaStream_t st);
+void launch_normalize_split(const VecCtx &c, int j, int is_start, cudaStream_t st);
 void launch_scale_rows_to_bf16(const double *x, const double *dsq, int Bs, int N,
                                __nv_bfloat16 *out, cudaStream_t st);
 

@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "LGW_OK", 1: "LGW_ERR_ARG", 2: "LGW_ERR_SHAPE", 3: "LGW_ERR_C
                 7: "LGW_ERR_TIMEOUT", 8: "LGW_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "bf16": 1}
 REORTH = {"none": 0, "cgs2": 1, "cgs1k": 2}
+REORTH_ARITH = {"auto": 0, "fp64": 1, "split": 2}
 
 
 class LgwError(RuntimeError):
@@ -52,7 +53,7 @@ class lgw_options(ctypes.Structure):
                 ("reorth", ctypes.c_int32), ("b_sub", ctypes.c_int32),
                 ("breakdown_tol", ctypes.c_double), ("qp_max_iter", ctypes.c_int32),
                 ("qp_tol", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reorth_arith", ctypes.c_int32)]
 
 
 class lgw_report(ctypes.Structure):
@@ -202,6 +203,7 @@ class Options:
     qp_max_iter: int = 0
     qp_tol: float = 0.0
     use_graph: int = 0
+    reorth_arith: str = "auto"
 
     def to_c(self) -> lgw_options:
         o = lgw_options()
@@ -213,6 +215,7 @@ class Options:
         o.qp_max_iter = int(self.qp_max_iter)
         o.qp_tol = float(self.qp_tol)
         o.use_graph = int(self.use_graph)
+        o.reorth_arith = REORTH_ARITH[self.reorth_arith]
         return o
 
 

@@ -132,18 +132,24 @@ def tiny_ref():
     return wl, (sig64, E64, Z64, co64), (sigx, Ex, Zx)
 
 
+@pytest.mark.parametrize("arith", ["fp64", "split"])
 @pytest.mark.parametrize("reorth", ["cgs2", "cgs1k"])
-def test_tiny_fp64_k64_vs_oracle_lanczos(L, handle, tiny_ref, reorth):
+def test_tiny_fp64_k64_vs_oracle_lanczos(L, handle, tiny_ref, reorth, arith):
+    """FP64 contractions with either reorthogonalisation arithmetic: the
+    split (double-float) basis must be as accurate as the FP64 one."""
     wl, (sig64, E64, Z64, _), _ = tiny_ref
-    sig, e, z, _ = _run(L, handle, wl, L.Options(k=64, precision="fp64", reorth=reorth))
+    sig, e, z, _ = _run(L, handle, wl, L.Options(k=64, precision="fp64", reorth=reorth,
+                                                 reorth_arith=arith))
     assert _rel_sigma_err(sig, sig64) < 1e-9
     assert np.all(np.abs(e - E64) <= 1e-9 * np.maximum(1, np.abs(E64)))
     assert np.all(np.abs(z - Z64) <= 1e-8)
 
 
-def test_tiny_fp64_full_k_vs_closed_form(L, handle, tiny_ref):
+@pytest.mark.parametrize("arith", ["fp64", "split"])
+def test_tiny_fp64_full_k_vs_closed_form(L, handle, tiny_ref, arith):
     wl, _, (sigx, Ex, Zx) = tiny_ref
-    sig, e, z, _ = _run(L, handle, wl, L.Options(k=wl.n_vc, precision="fp64", reorth="cgs2"))
+    sig, e, z, _ = _run(L, handle, wl, L.Options(k=wl.n_vc, precision="fp64", reorth="cgs2",
+                                                 reorth_arith=arith))
     assert _rel_sigma_err(sig, sigx) < 1e-9
     assert np.all(np.abs(e - Ex) <= 1e-9 * np.maximum(1, np.abs(Ex)))
 
@@ -283,13 +289,15 @@ def test_mid_ragged_fp64_and_bf16(L, handle):
                           aux_scaled=True)
     ref, poles, _ = O.sigma_lanczos(wl, k=40)
     Er, _ = O.solve_all_qp(wl, poles)
-    sig, e, _, rep = _run(L, handle, wl, L.Options(k=40, precision="fp64", b_sub=32),
-                          report=True)
-    assert rep["n_sub_batches"] == 2
-    assert _rel_sigma_err(sig, ref) < 1e-9
-    assert np.abs(e - Er).max() < 1e-9
-    sigb, eb, _, _ = _run(L, handle, wl, L.Options(k=40, precision="bf16"))
-    assert np.abs(eb - Er).max() < 1e-3
+    for arith in ("fp64", "split"):
+        sig, e, _, rep = _run(L, handle, wl, L.Options(k=40, precision="fp64", b_sub=32,
+                                                       reorth_arith=arith), report=True)
+        assert rep["n_sub_batches"] == 2
+        assert _rel_sigma_err(sig, ref) < 1e-9
+        assert np.abs(e - Er).max() < 1e-9
+    for reorth in ("cgs2", "cgs1k"):
+        sigb, eb, _, _ = _run(L, handle, wl, L.Options(k=40, precision="bf16", reorth=reorth))
+        assert np.abs(eb - Er).max() < 1e-3
 
 
 def test_errors_are_reported(L, handle):
