@@ -282,33 +282,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (col < Ncols && row < M) out[(size_t)col * ea.ldo + row] = __uint_as_float(r[i]);
         }
       } else if (EPI == E_SPLITB) {
-        float acc[32];
+        // c_K Delta^1/2 (L y), FP32, store only (the FP64 assembly of w and
+        // the alpha estimate happen elsewhere; loads here would be scattered
+        // 128-byte pieces across 256 vector rows)
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int col = ncol0 + c0 + i;
-          acc[i] = 0.f;
-          if (col < Ncols && row < M) {
-            const size_t o = (size_t)col * ea.N + row;
-            const float up = cdf * __uint_as_float(r[i]);
-            ea.ucd[o] = up;
-            const float qf = ea.qh[o];
-            float t = fmaf(d2f, qf, up);
-            if (ea.qph != nullptr) t = fmaf(-(float)ea.betaj[col], ea.qph[o], t);
-            acc[i] = qf * t;
-          }
+          if (col < Ncols && row < M) ea.ucd[(size_t)col * ea.N + row] = cdf * __uint_as_float(r[i]);
         }
-        // transposed warp reduction, FP32: lane l ends with column c0 + l
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-          const bool up = (lane & off) != 0;
-#pragma unroll
-          for (int i = 0; i < off; ++i) {
-            const float send = up ? acc[i] : acc[i + off];
-            const float keep = up ? acc[i + off] : acc[i];
-            acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-          }
-        }
-        red[qd * BN + c0 + lane] = (double)acc[0];
       } else {
         double acc[32];
 #pragma unroll
@@ -332,7 +313,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-    if (EPI == E_LANCZOS || EPI == E_SPLITB) {
+    if (EPI == E_LANCZOS) {
       asm volatile("bar.sync 1, 128;" ::: "memory");
       const int te = threadIdx.x - 64;
       for (int col = te; col < BN; col += 128) {
@@ -352,13 +333,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-__global__ void k_reduce_y_bf16(const float *__restrict__ Ypart, int splits, int n,
-                                __nv_bfloat16 *__restrict__ Yh) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// Yh = bf16(sum_p Ypart[p]) in fixed order; optionally per-block partials of
+// sum_mu y_mu Yh_mu (grid: A/256 blocks per vector row).
+__global__ void k_reduce_y_bf16(const float *__restrict__ Ypart, int splits, int Bs, int A,
+                                __nv_bfloat16 *__restrict__ Yh, float *__restrict__ yy) {
+  __shared__ float red[8];
+  const int b = blockIdx.y;
+  const int mu = blockIdx.x * 256 + threadIdx.x;
+  const size_t n = (size_t)Bs * A;
   float s = 0.0f;
-  for (int p = 0; p < splits; ++p) s += Ypart[(size_t)p * n + i];
-  Yh[i] = __float2bfloat16_rn(s);
+  const size_t i = (size_t)b * A + mu;
+  if (mu < A) {
+    for (int p = 0; p < splits; ++p) s += Ypart[(size_t)p * n + i];
+    const __nv_bfloat16 hq = __float2bfloat16_rn(s);
+    Yh[i] = hq;
+    s *= __bfloat162float(hq);
+  } else {
+    s = 0.0f;
+  }
+  if (yy != nullptr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.0f;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      yy[(size_t)b * gridDim.x + blockIdx.x] = t;
+    }
+  }
 }
 
 }  // namespace tc
@@ -515,9 +518,9 @@ void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st) {
 }
 
 void launch_reduce_y_bf16(const float *Ypart, int splits, int Bs, int A, __nv_bfloat16 *Yh,
-                          cudaStream_t st) {
-  int n = Bs * A;
-  tc::k_reduce_y_bf16<<<(n + 255) / 256, 256, 0, st>>>(Ypart, splits, n, Yh);
+                          float *yy, cudaStream_t st) {
+  dim3 grid((A + 255) / 256, Bs);
+  tc::k_reduce_y_bf16<<<grid, 256, 0, st>>>(Ypart, splits, Bs, A, Yh, yy);
 }
 
 void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qprev,
@@ -542,18 +545,11 @@ void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qp
     dispatch_bn<tc::E_APPLY>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
 }
 
-void launch_gemm2_tc_split(const TcPlan *p, const float *qh, const float *qph,
-                           const double *betaj, float *ucd, double *alpha_part, unsigned *status,
-                           cudaStream_t st) {
+void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaStream_t st) {
   tc::EpiArgs ea{};
   ea.N = p->N;
-  ea.qh = qh;
-  ea.qph = qph;
-  ea.d2f = p->d2f;
   ea.cdf = p->cdf;
-  ea.betaj = betaj;
   ea.ucd = ucd;
-  ea.alpha_part = alpha_part;
   ea.status = status;
   const int num_kb = p->A / tc::BK;
   dispatch_bn<tc::E_SPLITB>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);

@@ -210,13 +210,23 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize(VecCtx c, int j, int 
   const int v = c.vec0 + b;
   const bool real = b < c.nvec;
   bool live = real && (is_start || c.k_eff[v] > j);
+  __shared__ double sbeta, sinv;
   double beta = 0.0;
   if (live) {
-    const double *np = c.norm_a;
-    if (!is_start && c.reorth != LGW_REORTH_NONE) np = c.flag2[b] ? c.norm_c : c.norm_b;
-    double s = 0.0;
-    for (int ch = 0; ch < c.nchunks; ++ch) s += np[(size_t)b * c.nchunks + ch];
-    beta = sqrt(s);
+    // ||w||^2 from the per-chunk partials: one warp, fixed order, broadcast
+    if (threadIdx.x < 32) {
+      const double *np = c.norm_a;
+      if (!is_start && c.reorth != LGW_REORTH_NONE) np = c.flag2[b] ? c.norm_c : c.norm_b;
+      double s = 0.0;
+      for (int ch = threadIdx.x; ch < c.nchunks; ch += 32) s += np[(size_t)b * c.nchunks + ch];
+      s = warp_sum(s);
+      if (threadIdx.x == 0) {
+        sbeta = sqrt(s);
+        sinv = sbeta > 0.0 ? 1.0 / sbeta : 0.0;
+      }
+    }
+    __syncthreads();
+    beta = sbeta;
     if (is_start) {
       if (chunk == 0 && threadIdx.x == 0) {
         c.beta0[v] = beta;
@@ -242,7 +252,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize(VecCtx c, int j, int 
   const size_t voff = (size_t)b * c.N;
   double *qn = slot_ptr(c, next) + voff;
   const double *w = c.w + voff;
-  const double inv = live ? 1.0 / beta : 0.0;
+  const double inv = live ? sinv : 0.0;
   const int e0 = elem_base(chunk);
 #pragma unroll
   for (int u = 0; u < 4; ++u) {

@@ -126,8 +126,17 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_dots_split(VecCtx c, int j) 
   double alpha = 0.0;
   if (PASS == 1) {
     double s = 0.0;
-    for (int t = threadIdx.x; t < c.n_mt; t += VEC_THREADS)
-      s += c.alpha_part[(size_t)t * c.Bs + b];
+    if (c.ucd != nullptr) {
+      // estimate alpha_j = sum Delta^2 q_j^2 + c_K y . bf16(y)  (y = L^T Delta^1/2 q_j,
+      // so q_j . c_K Delta^1/2 L y_hat = c_K y . y_hat); beta_j q_j . q_{j-1} ~ 0.
+      for (int t = threadIdx.x; t < c.nchunks; t += VEC_THREADS)
+        s += (double)c.dq2_part[(size_t)b * c.nchunks + t];
+      for (int t = threadIdx.x; t < c.n_yb; t += VEC_THREADS)
+        s += c.kf * (double)c.yy_part[(size_t)b * c.n_yb + t];
+    } else {
+      for (int t = threadIdx.x; t < c.n_mt; t += VEC_THREADS)
+        s += c.alpha_part[(size_t)t * c.Bs + b];
+    }
     alpha = block_sum(s, red);
     // alpha used for the subtraction; k_reduce_dots_split adds the residual
     // projection h_j so the recorded alpha_j is the FP64 Rayleigh quotient
@@ -293,13 +302,24 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j
   const int v = c.vec0 + b;
   const bool real = b < c.nvec;
   bool live = real && (is_start || c.k_eff[v] > j);
+  __shared__ double sbeta, sinv;
+  __shared__ float sdq[VEC_THREADS / 32];
   double beta = 0.0;
   if (live) {
-    const double *np = is_start ? c.norm_a : (c.flag2[b] ? c.norm_c : c.norm_b);
-    if (!is_start && c.reorth == LGW_REORTH_NONE) np = c.norm_a;
-    double s = 0.0;
-    for (int ch = 0; ch < c.nchunks; ++ch) s += np[(size_t)b * c.nchunks + ch];
-    beta = sqrt(s);
+    // ||w||^2 from the per-chunk partials: one warp, fixed order, broadcast
+    if (threadIdx.x < 32) {
+      const double *np = is_start ? c.norm_a : (c.flag2[b] ? c.norm_c : c.norm_b);
+      if (!is_start && c.reorth == LGW_REORTH_NONE) np = c.norm_a;
+      double s = 0.0;
+      for (int ch = threadIdx.x; ch < c.nchunks; ch += 32) s += np[(size_t)b * c.nchunks + ch];
+      s = warp_sum(s);
+      if (threadIdx.x == 0) {
+        sbeta = sqrt(s);
+        sinv = sbeta > 0.0 ? 1.0 / sbeta : 0.0;
+      }
+    }
+    __syncthreads();
+    beta = sbeta;
     if (is_start) {
       if (chunk == 0 && threadIdx.x == 0) {
         c.beta0[v] = beta;
@@ -327,8 +347,9 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j
   float *hn = c.bhi + ((size_t)next * c.Bs + b) * c.N;
   float *ln = c.blo + ((size_t)next * c.Bs + b) * c.N;
   const double *w = c.w + voff;
-  const double inv = live ? 1.0 / beta : 0.0;
+  const double inv = live ? sinv : 0.0;
   const int e0 = elem_base_s(chunk);
+  float dq = 0.0f;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int e = e0 + u * 64;
@@ -341,6 +362,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j
     }
     *reinterpret_cast<double2 *>(qn + e) = q2;
     const float hx = __double2float_rn(q2.x), hy = __double2float_rn(q2.y);
+    dq = fmaf(c.d2f[e] * hx, hx, fmaf(c.d2f[e + 1] * hy, hy, dq));
     if (keep_basis) {
       *reinterpret_cast<float2 *>(hn + e) = make_float2(hx, hy);
       *reinterpret_cast<float2 *>(ln + e) = make_float2(__double2float_rn(q2.x - (double)hx),
@@ -351,6 +373,17 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j
       x2.x = __float2bfloat16_rn(c.dsqf[e] * hx);
       x2.y = __float2bfloat16_rn(c.dsqf[e + 1] * hy);
       *reinterpret_cast<__nv_bfloat162 *>(c.xh + voff + e) = x2;
+    }
+  }
+  if (c.dq2_part != nullptr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dq += __shfl_xor_sync(0xffffffffu, dq, o);
+    if ((threadIdx.x & 31) == 0) sdq[threadIdx.x >> 5] = dq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.0f;
+      for (int w8 = 0; w8 < VEC_THREADS / 32; ++w8) t += sdq[w8];
+      c.dq2_part[(size_t)b * c.nchunks + chunk] = t;
     }
   }
 }

@@ -169,7 +169,7 @@ __global__ void k_spectral(const double *__restrict__ alpha, const double *__res
 void launch_spectral_impl(const double *alpha, const double *beta, const double *beta0,
                           const int *k_eff, int B, int k, JacobiBufs jb, double *scratch,
                           unsigned long long *min_theta_bits, unsigned *status, cudaStream_t st) {
-  const int th = 32;
+  const int th = 4;   // spread the latency-bound per-vector chains over many SMs
   k_spectral<<<(B + th - 1) / th, th, 0, st>>>(alpha, beta, beta0, k_eff, B, k, scratch,
                                                scratch + (size_t)B * k, scratch + (size_t)2 * B * k,
                                                jb, min_theta_bits, status);

@@ -378,6 +378,12 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   }
   c.dsqf = s.dsqf;
   c.ucd = (split && tc) ? wsT<float>(h, "ucd", (size_t)Bs * N) : nullptr;
+  c.d2f = s.d2f;
+  c.kf = s.kf;
+  c.n_yb = (s.A + 255) / 256;
+  float *yy = (split && tc) ? wsT<float>(h, "yy_part", (size_t)Bs * c.n_yb) : nullptr;
+  c.yy_part = yy;
+  c.dq2_part = (split && tc) ? wsT<float>(h, "dq2_part", (size_t)Bs * nchunks) : nullptr;
   c.xh = tc ? wsT<__nv_bfloat16>(h, "xh", (size_t)Bs * N) : nullptr;
   c.n_mt = tc ? tc_n_mt(s) : N / F64_TILE;
   c.alpha_part = wsT<double>(h, "alpha_part", (size_t)c.n_mt * Bs);
@@ -460,13 +466,11 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
       if (tc) {
         launch_gemm1_tc(plan, h->d_status, st);
         check_launch(h, "gemm1_tc");
-        launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, st);
+        launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, yy, st);
         check_launch(h, "reduce_y_bf16");
         tm.mark(C_GEMM2);
         if (split)
-          launch_gemm2_tc_split(plan, c.bhi + (size_t)j * Bs * N,
-                                j > 0 ? c.bhi + (size_t)(j - 1) * Bs * N : nullptr, c.betaj,
-                                const_cast<float *>(c.ucd), c.alpha_part, h->d_status, st);
+          launch_gemm2_tc_split(plan, const_cast<float *>(c.ucd), h->d_status, st);
         else
           launch_gemm2_tc(plan, EPI_LANCZOS, qj, qp, c.betaj, c.w, c.alpha_part, h->d_status,
                           st);
@@ -827,7 +831,7 @@ lgw_status lgw_apply_casida(lgw_handle *h, const lgw_system *sys, int32_t n_vec,
       }
       launch_gemm1_tc(plan, h->d_status, st);
       check_launch(h, "gemm1_tc");
-      launch_reduce_y_bf16(yp, splits, Bs, s.A, yh, st);
+      launch_reduce_y_bf16(yp, splits, Bs, s.A, yh, nullptr, st);
       check_launch(h, "reduce_y_bf16");
       launch_gemm2_tc(plan, EPI_APPLY, xp, nullptr, nullptr, wp, nullptr, h->d_status, st);
       check_launch(h, "gemm2_tc");

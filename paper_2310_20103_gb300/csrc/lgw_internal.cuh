@@ -70,8 +70,13 @@ struct VecCtx {
   __nv_bfloat16 *xh;      // [Bs][N]   bf16(Delta^1/2 q_j)
   float *bhi, *blo;       // split basis [k+1][Bs][N]: q = hi + lo (48 bits)
   const float *dsqf;      // [N]
+  const float *d2f;       // [N] Delta^2 (float)
   const float *ucd;       // [Bs][N] c_K Delta^1/2 (L y) from the FP32 epilogue, or null
                           // (then w holds the full FP64 epilogue result)
+  float *dq2_part;        // [Bs][nchunks] partials of sum Delta^2 q_j^2 (FP32)
+  const float *yy_part;   // [Bs][n_yb]    partials of y . bf16(y) for the current q_j
+  int n_yb;
+  double kf;
   double *alpha_part;     // [n_mt][Bs]
   int n_mt;
   double *dot_part;       // [Bs][nchunks][kmax1]
@@ -162,17 +167,15 @@ TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *
                        __nv_bfloat16 *yh, int *splits_out, char *err, size_t errn);
 void tc_plan_destroy(TcPlan *p);
 void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st);
+// Yh = bf16(sum of split partials); yy (optional, [Bs][A/256]) receives
+// per-block partials of sum_mu y_mu * Yh_mu for the alpha estimate.
 void launch_reduce_y_bf16(const float *Ypart, int splits, int Bs, int A, __nv_bfloat16 *Yh,
-                          cudaStream_t st);
+                          float *yy, cudaStream_t st);
 void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qprev,
                      const double *betaj, double *w, double *alpha_part, unsigned *status,
                      cudaStream_t st);
-// FP32 epilogue for the split basis: ucd = c_K Delta^1/2 U (float) and FP32
-// estimates of alpha_j = q_j . (Delta^2 q_j + ucd - beta_j q_{j-1}) per tile,
-// from the hi parts of q_j and q_{j-1} (qph may be null at step 0).
-void launch_gemm2_tc_split(const TcPlan *p, const float *qh, const float *qph,
-                           const double *betaj, float *ucd, double *alpha_part, unsigned *status,
-                           cudaStream_t st);
+// Store-only FP32 epilogue for the split basis: ucd = c_K Delta^1/2 U.
+void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaStream_t st);
 int tc_n_mt(const SysDev &s);
 
 // k_lanczos.cu : vector kernels of one step
