@@ -242,6 +242,38 @@ lgw_status lgw_sigma_c_batched(lgw_handle *h, int32_t n_sys, const lgw_system *c
                                double *const *sigma, double *const *e_qp,
                                double *const *z_qp, lgw_report *rep);
 
+/* Allocation-free variant of lgw_sigma_from_coeffs (the paper has no
+ * counterpart; this is a service for callers).
+ *
+ * Some callers cannot let a library allocate device memory while they run:
+ * services that give the library a fixed device-memory budget at start-up,
+ * or latency-bound loops where cudaMalloc/cudaFree would synchronise the
+ * device and stall other streams.  This call computes exactly what
+ * lgw_sigma_from_coeffs computes -- spectral map, continued fractions on the
+ * grid, QP solve -- without any allocation: its scratch is one static device
+ * array of 16 MiB (2^21 doubles) that every GPU loading the library holds
+ * until the process exits.
+ *
+ * Requirements and limits
+ *   - every array (alpha, beta, beta0, k_eff, sigma, e_qp, z_qp if given, and
+ *     p->targets, p->m_idx, p->omega, p->static_shift if given) must be
+ *     device memory of the handle's device; host pointers give LGW_ERR_ARG.
+ *     p->M and p->V are not used.  sigma and e_qp are required.
+ *   - B = n_t * n_m vectors with k steps need B * (5k + 2) + 1 doubles; larger
+ *     requests are rejected with LGW_ERR_UNSUPPORTED and nothing runs.
+ *   - indices out of range give LGW_ERR_SHAPE (checked on the device).
+ *   - the first call on a device looks up the device address of the static
+ *     array (cudaGetSymbolAddress); make that first call before any stream
+ *     capture on that device.
+ *   - all calls share the one array and overwrite it; calls whose work
+ *     overlaps on the GPU (several streams or handles at once) race and give
+ *     undefined results.  The call returns after its stream has finished. */
+lgw_status lgw_sigma_from_coeffs_noalloc(lgw_handle *h, const lgw_system *s,
+                                         const lgw_problem *p, const lgw_options *o,
+                                         const double *alpha, const double *beta,
+                                         const double *beta0, const int32_t *k_eff,
+                                         double *sigma, double *e_qp, double *z_qp);
+
 /* Gradient of sum_t dE[t] * E_qp[t] with respect to L ([n_v*n_c][n_aux]) and
  * eps ([n_v+n_c]) for the request p, through the adjoint of the Lanczos
  * recurrence, the spectral map, the continued fractions and the QP

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1027,3 +1028,134 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *, const lgw_pro
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free variant of lgw_sigma_from_coeffs.
+//
+// Some callers cannot let a library allocate device memory while they run:
+// services that hand the library a fixed device-memory budget at start-up,
+// or latency-bound loops where cudaMalloc/cudaFree would synchronise the
+// device and stall other streams.  This entry point performs the spectral
+// map, the continued fractions on the grid and the QP solve with all of its
+// scratch in one file-scope device array of fixed size; the caller passes
+// inputs and outputs as device pointers.
+// ===========================================================================
+namespace {
+
+// 2^21 doubles = 16 MiB on every device that loads the library, held until
+// the process exits.  Layout per call: Jacobi a [B][k], b2 [B][k], w0 [B],
+// depth [B] (ints, rounded up), three tridiagonal work rows [3][B][k], one
+// word for the smallest Gauss node.
+constexpr size_t kNoallocDoubles = (size_t)1 << 21;
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Sets the Gauss-node minimum word and checks every target / summed index.
+__global__ void k_noalloc_prologue(unsigned long long *min_theta_bits, const int *targets, int n_t,
+                                   const int *m_idx, int n_m, int norb, unsigned *status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *min_theta_bits = 0x7FEFFFFFFFFFFFFFull;   // largest finite double
+  if (i < n_t && (targets[i] < 0 || targets[i] >= norb)) atomicOr(status, ST_BAD_INPUT);
+  if (i < n_m && (m_idx[i] < 0 || m_idx[i] >= norb)) atomicOr(status, ST_BAD_INPUT);
+}
+
+size_t noalloc_doubles_needed(size_t B, size_t k) {
+  return 2 * B * k + B + (B + 1) / 2 + 3 * B * k + 1;
+}
+
+}  // namespace
+
+extern "C" lgw_status lgw_sigma_from_coeffs_noalloc(lgw_handle *h, const lgw_system *sys,
+                                                    const lgw_problem *p, const lgw_options *o,
+                                                    const double *alpha, const double *beta,
+                                                    const double *beta0, const int32_t *k_eff,
+                                                    double *sigma, double *e_qp, double *z_qp) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!sys || sys->h != h || !p || !o || !alpha || !beta || !beta0 || !k_eff || !sigma ||
+      !e_qp)
+    return set_err(h, LGW_ERR_ARG, "NULL argument to lgw_sigma_from_coeffs_noalloc");
+  const SysDev &s = sys->s;
+  const int n_t = p->n_t, n_m = p->n_m, n_freq = p->n_freq, k = o->k;
+  if (n_t < 1 || n_m < 1 || n_freq < 1 || !p->targets || !p->m_idx || !p->omega)
+    return set_err(h, LGW_ERR_ARG, "noalloc: n_t, n_m, n_freq must be >= 1 with their arrays");
+  if (k < 1 || k > s.n_vc) return set_err(h, LGW_ERR_ARG, "noalloc: k outside [1, n_vc]");
+  if (!(p->delta > 0.0)) return set_err(h, LGW_ERR_ARG, "noalloc: delta must be > 0");
+  const void *dev_ptrs[] = {alpha, beta, beta0, k_eff, sigma, e_qp, p->targets, p->m_idx,
+                            p->omega};
+  for (const void *q : dev_ptrs)
+    if (!is_device_ptr(q))
+      return set_err(h, LGW_ERR_ARG, "noalloc: every array must be device memory");
+  if ((z_qp && !is_device_ptr(z_qp)) || (p->static_shift && !is_device_ptr(p->static_shift)))
+    return set_err(h, LGW_ERR_ARG, "noalloc: every array must be device memory");
+  const size_t B = (size_t)n_t * (size_t)n_m;
+  if (noalloc_doubles_needed(B, (size_t)k) > kNoallocDoubles)
+    return set_err(h, LGW_ERR_UNSUPPORTED,
+                   "noalloc: n_t*n_m*(5k+2) exceeds the %zu-double static scratch (B=%zu, k=%d)",
+                   kNoallocDoubles, B, k);
+  if (h->device < 0 || h->device >= kMaxDevices)
+    return set_err(h, LGW_ERR_UNSUPPORTED, "noalloc: device index beyond %d", kMaxDevices);
+
+  // One-time set-up per device: host code cannot use the array's name as a
+  // device address, so fetch the address with that device current.
+  double *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[h->device]) {
+      void *ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return set_err(h, LGW_ERR_CUDA, "noalloc: cudaGetSymbolAddress failed: %s",
+                       cudaGetErrorString(e));
+      g_noalloc_addr[h->device] = static_cast<double *>(ptr);
+    }
+    base = g_noalloc_addr[h->device];
+  }
+  JacobiBufs jb;
+  jb.a = base;
+  jb.b2 = jb.a + B * k;
+  jb.w0 = jb.b2 + B * k;
+  jb.n = reinterpret_cast<int *>(jb.w0 + B);
+  double *work = jb.w0 + B + (B + 1) / 2;
+  unsigned long long *mt = reinterpret_cast<unsigned long long *>(work + 3 * B * k);
+
+  cudaStream_t st = h->stream;
+  if (cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st) != cudaSuccess)
+    return set_err(h, LGW_ERR_CUDA, "noalloc: status reset failed");
+  const int nmax = n_t > n_m ? n_t : n_m;
+  k_noalloc_prologue<<<(nmax + 255) / 256, 256, 0, st>>>(mt, p->targets, n_t, p->m_idx, n_m,
+                                                         s.n_v + s.n_c, h->d_status);
+  launch_spectral_impl(alpha, beta, beta0, k_eff, (int)B, k, jb, work, mt, h->d_status, st);
+  CfProblem cp{};
+  cp.n_t = n_t;
+  cp.n_m = n_m;
+  cp.n_freq = n_freq;
+  cp.k = k;
+  cp.targets = p->targets;
+  cp.m_idx = p->m_idx;
+  cp.eps = s.eps;
+  cp.n_v = s.n_v;
+  cp.omega = p->omega;
+  cp.delta = p->delta;
+  cp.shift = p->static_shift;
+  launch_cf_grid(cp, jb, sigma, st);
+  const int qp_iter = o->qp_max_iter > 0 ? o->qp_max_iter : 50;
+  const double qp_tol = o->qp_tol > 0 ? o->qp_tol : 1e-10;
+  launch_qp(cp, jb, sigma, qp_iter, qp_tol, e_qp, z_qp, h->d_status, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return set_err(h, LGW_ERR_CUDA, "noalloc: kernel launch failed: %s", cudaGetErrorString(e));
+  unsigned stw = 0;
+  if (cudaMemcpyAsync(&stw, h->d_status, sizeof stw, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return set_err(h, LGW_ERR_CUDA, "noalloc: status read failed");
+  if (stw & ST_BAD_INPUT) return set_err(h, LGW_ERR_SHAPE, "noalloc: orbital index out of range");
+  if (stw & ST_TIMEOUT) return set_err(h, LGW_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (stw & ST_NOT_SPD) return set_err(h, LGW_ERR_NOT_SPD, "non-positive Gauss node");
+  if (stw & ST_NO_CONV)
+    return set_err(h, LGW_ERR_NO_CONVERGENCE, "tridiagonal eigensolver or QP did not converge");
+  return LGW_OK;
+}

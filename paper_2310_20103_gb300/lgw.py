@@ -324,3 +324,21 @@ def lgw_sigma_c_backward(h: Handle, s: System, problem: Problem, options: Option
     _check(h, load_library().lgw_sigma_c_backward(
         h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), _ptr(dE, "f64"), _ptr(dL, "f64"),
         _ptr(deps, "f64")))
+
+
+def lgw_sigma_from_coeffs_noalloc(h: Handle, s: System, problem: Problem, options: Options,
+                                  alpha, beta, beta0, k_eff, sigma, e_qp, z_qp=None) -> None:
+    """Allocation-free lgw_sigma_from_coeffs: all arrays must be CUDA tensors;
+    the library's scratch is a fixed 16 MiB static device array (see
+    include/lgw.h for the size limit and the concurrency rule)."""
+    lib = load_library()
+    fn = lib.lgw_sigma_from_coeffs_noalloc
+    if fn.argtypes is None:
+        P = ctypes.c_void_p
+        fn.argtypes = [P, P, ctypes.POINTER(lgw_problem), ctypes.POINTER(lgw_options),
+                       P, P, P, P, P, P, P]
+        fn.restype = ctypes.c_int32
+    p, o = problem.to_c(), options.to_c()
+    _check(h, fn(h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), _ptr(alpha, "f64"),
+                 _ptr(beta, "f64"), _ptr(beta0, "f64"), _ptr(k_eff, "i32"),
+                 _ptr(sigma, "f64"), _ptr(e_qp, "f64"), _ptr(z_qp, "f64")))
