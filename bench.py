@@ -1,8 +1,9 @@
 """Throughput benchmark of the Lanczos GW hot path on GB300.
 
 One step = one lgw_sigma_c call on the mid-size system (N_v=128, N_c=1024,
-N_vc=131072, N_aux=2048, k=200 Lanczos steps with full CGS2
-reorthogonalisation, 1000 frequencies) for a batch of target states, each
+N_vc=131072, N_aux=2048, k=200 Lanczos steps with full classical
+Gram-Schmidt reorthogonalisation against every stored basis vector -- a
+second pass where the norm criterion asks for it -- and 1000 frequencies) for a batch of target states, each
 summed over 256 orbitals: start vectors, every Lanczos step, spectral map,
 continued fractions on the grid and the QP solve.  Metric: QP states per
 second (higher is better), whole job over all ranks.
@@ -226,6 +227,20 @@ def run_gpu(args):
     torch.cuda.synchronize()
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1)
+    # one CGS2 step (always two Gram-Schmidt passes) on the same workload, for comparison
+    cgs2 = None
+    if args.reorth == "cgs1k" and not args.no_cgs2_step:
+        o2 = L.Options(k=args.k, precision=args.precision, reorth="cgs2",
+                       b_sub=args.tps * M_PER_TARGET)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.lgw_sigma_c(h, sysd, batch(args.warmup + args.steps), o2, sig, e, z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1)
+        cgs2 = {"value": tps / (cms / 1e3), "unit": "QP states/s", "ms_per_step": cms,
+                "steps": 1}
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -280,8 +295,8 @@ def run_gpu(args):
         by = {
             "update": (4.0 * agg["reorth_elems"] + 16.0 * nvc * B * kk, agg["ms_update"],
                        "k_update_split<1> (w -= Q h in FP32 from the hi basis)"),
-            "dots": (8.0 * agg["reorth_elems"] + 24.0 * nvc * B * kk, agg["ms_dots"],
-                     "k_dots_split<1> (alpha axpy + double-float Q^T w)"),
+            "dots": (8.0 * agg["reorth_elems"] + 28.0 * nvc * B * kk, agg["ms_dots"],
+                     "k_dots_split<1> (w assembly, alpha axpy, double-float Q^T w)"),
         }
     else:
         by = {
@@ -293,6 +308,7 @@ def run_gpu(args):
     dom = max(by, key=lambda x: by[x][1])
     bytes_, ms_k, kname = by[dom]
     achieved = bytes_ / (ms_k / 1e3) / 1e9
+    traffic = _dram_traffic(dom, split, agg["reorth_elems"], nvc * B * kk, launches_per_cat)
     gemm_ms = agg["ms_gemm1"] + agg["ms_gemm2"]
     gemm_tflops = agg["gemm_flops"] / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
 
@@ -309,13 +325,18 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
-                     "traffic": None, "launches": launches_per_cat,
+                     "traffic": traffic, "traffic_source": "ncu dram bytes of the same kernel "
+                     "on a 64-vector case, scaled per processed element (profiles/)",
+                     "algorithmic_bytes_per_launch": bytes_ / launches_per_cat,
+                     "launches": launches_per_cat,
                      "avg_launch_ms": ms_k / launches_per_cat},
         "gemm": {"tflops": gemm_tflops, "peak_bf16_tflops": bf16_sus,
                  "frac": (gemm_tflops / bf16_sus) if gemm_tflops else None,
                  "ms_gemm1": agg["ms_gemm1"], "ms_gemm2": agg["ms_gemm2"],
                  "splits": r0["gemm1_splits"]},
         "breakdown_ms": {k: agg[k] for k in agg if k.startswith("ms_")},
+        "n_second_pass": int(agg["n_second_pass"]),
+        "cgs2_step": cgs2,
     }
     if rank == 0 and world == 1 and not args.no_fp64_compare:
         line["fp64_path"] = fp64_compare(args, L, h, sysd, wl, tgt_all, m_idx_d, omega_d, M_all,
@@ -334,6 +355,26 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _dram_traffic(dom, split, reorth_elems, elem_steps, launches):
+    """DRAM bytes per launch of the dominant kernel from the ncu coefficients in
+    profiles/k_dots_split_traffic.txt (bytes per basis-row element and per
+    element-step, measured on a small case of the same kernel), or None."""
+    if not (split and dom == "dots"):
+        return None
+    try:
+        vals = {}
+        with open(os.path.join(ROOT, "profiles", "k_dots_split_traffic.txt")) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 2:
+                    vals[parts[0]] = parts[1]
+        per_row = float(vals["bytes_per_row_element"])
+        per_step = float(vals["bytes_per_element_step"])
+    except Exception:
+        return None
+    return (per_row * reorth_elems + per_step * elem_steps) / launches
 
 
 def fp64_compare(args, L, h, sysd, wl, tgt_all, m_idx_d, omega_d, M_all, dev):
@@ -372,13 +413,14 @@ def main():
     ap.add_argument("--impl", default="lgw", choices=["lgw", "reference"])
     ap.add_argument("--k", type=int, default=200)
     ap.add_argument("--tps", type=int, default=2, help="target states per step")
-    ap.add_argument("--reorth", default="cgs2", choices=["cgs2", "cgs1k", "none"])
+    ap.add_argument("--reorth", default="cgs1k", choices=["cgs2", "cgs1k", "none"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--fp64-vectors", type=int, default=16)
     ap.add_argument("--ref-vectors", type=int, default=2)
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cgs2-step", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
