@@ -170,6 +170,7 @@ def run_gpu(args):
 
     import gw_inputs
     from paper_2310_20103_gb300 import lgw as L
+    from paper_2310_20103_gb300 import replicas as R
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -198,10 +199,9 @@ def run_gpu(args):
     z = torch.empty(tps, dtype=torch.float64, device=dev)
 
     def batch(i):
-        off = ((i * world + rank) * tps) % n_t_all
-        sl = slice(off, off + tps)
-        return L.Problem(targets=tgt_all[sl].contiguous(), m_idx=m_idx_d, omega=omega_d,
-                         delta=wl.delta, M=M_all[sl].contiguous())
+        ts = torch.tensor(R.targets_for_step(i, rank, world, tps, n_t_all), device=dev)
+        return L.Problem(targets=tgt_all[ts].contiguous(), m_idx=m_idx_d, omega=omega_d,
+                         delta=wl.delta, M=M_all[ts].contiguous())
 
     def barrier():
         if world > 1:
@@ -241,10 +241,7 @@ def run_gpu(args):
         cms = e0.elapsed_time(e1)
         cgs2 = {"value": tps / (cms / 1e3), "unit": "QP states/s", "ms_per_step": cms,
                 "steps": 1}
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = R.max_over_ranks(ms, dev) if world > 1 else ms
     states = tps * args.steps * world
     value = states / (ms_max / 1e3)
 
@@ -264,9 +261,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        off = ((i * world + rank) * tps) % n_t_all
-        Mb = M_h[off:off + tps]
-        tb = tg_h[off:off + tps]
+        ts = R.targets_for_step(i, rank, world, tps, n_t_all)
+        Mb = M_h[ts].contiguous().pin_memory()
+        tb = tg_h[ts].contiguous().pin_memory()
         s2 = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, eps_h, L_h, wl.kernel_factor)
         prob = L.Problem(targets=tb, m_idx=mi_h, omega=om_h, delta=wl.delta, M=Mb)
         L.lgw_sigma_c(h, s2, prob, opts, sig_h, e_h, z_h)
@@ -276,10 +273,8 @@ def run_gpu(args):
         d2h = (sig_h.numel() + e_h.numel() + z_h.numel()) * 8
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = tps * e2e_steps * world / float(te.item())
+    e2e_max = R.max_over_ranks(e2e_s, dev) if world > 1 else e2e_s
+    e2e_value = tps * e2e_steps * world / e2e_max
 
     # --- per-kernel breakdown from the timed steps (CUDA events on the stream) ---
     agg = {k: sum(r[k] for r in reps) for k in reps[0] if k.startswith("ms_") or k in (
