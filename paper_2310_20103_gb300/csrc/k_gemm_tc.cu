@@ -173,7 +173,7 @@ struct EpiArgs {
   float *ucd;
 };
 
-enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2, E_LANCZOS_NA = 3, E_SPLITB = 4 };
+enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2, E_LANCZOS_NA = 3, E_SPLITB = 4, E_VACC = 5 };
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -281,6 +281,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int col = ncol0 + c0 + i;
           if (col < Ncols && row < M) out[(size_t)col * ea.ldo + row] = __uint_as_float(r[i]);
         }
+      } else if (EPI == E_VACC) {
+        // FP32 accumulation of split-BF16 partial products (ea.ldo != 0: add)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = ncol0 + c0 + i;
+          if (col < Ncols && row < M) {
+            float *o = ea.ucd + (size_t)col * ea.N + row;
+            *o = (ea.ldo ? *o : 0.0f) + __uint_as_float(r[i]);
+          }
+        }
       } else if (EPI == E_SPLITB) {
         // c_K Delta^1/2 (L y), FP32, store only (the FP64 assembly of w and
         // the alpha estimate happen elsewhere; loads here would be scattered
@@ -370,7 +380,7 @@ __global__ void k_reduce_y_bf16(const float *__restrict__ Ypart, int splits, int
 // Host side
 // ---------------------------------------------------------------------------
 struct TcPlan {
-  CUtensorMap g1A, g1B, g2A, g2B;
+  CUtensorMap g1A, g1B, g2A, g2B, g2Alo;
   int BN;
   int N, A, Bs;
   int splits, kb_per_split;
@@ -469,6 +479,7 @@ TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *
   bool ok = encode_2d(&p->g1A, s.Ltb, (uint64_t)s.N, (uint64_t)s.A, tc::BM) &&
             encode_2d(&p->g1B, xh, (uint64_t)s.N, (uint64_t)Bs, (uint32_t)p->BN) &&
             encode_2d(&p->g2A, s.Lb, (uint64_t)s.A, (uint64_t)s.N, tc::BM) &&
+            encode_2d(&p->g2Alo, s.Lb_lo, (uint64_t)s.A, (uint64_t)s.N, tc::BM) &&
             encode_2d(&p->g2B, yh, (uint64_t)s.A, (uint64_t)Bs, (uint32_t)p->BN);
   if (!ok) {
     snprintf(err, errn, "cuTensorMapEncodeTiled failed");
@@ -543,6 +554,42 @@ void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qp
     dispatch_bn<tc::E_LANCZOS>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
   else
     dispatch_bn<tc::E_APPLY>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+}
+
+namespace tc {
+// bf16 hi / lo halves of M rows into a zero-padded [Bs][A] operand.
+__global__ void k_split_m(const double *__restrict__ M, int nvec, int n_aux, int Bs, int A,
+                          int lo, __nv_bfloat16 *__restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)Bs * A) return;
+  const int b = (int)(i / A), mu = (int)(i - (size_t)b * A);
+  float v = 0.0f;
+  if (b < nvec && mu < n_aux) {
+    const double x = M[(size_t)b * n_aux + mu];
+    const __nv_bfloat16 hi = __double2bfloat16(x);
+    v = lo ? (float)(x - (double)__bfloat162float(hi)) : __bfloat162float(hi);
+  }
+  out[i] = __float2bfloat16_rn(v);
+}
+}  // namespace tc
+
+void launch_coupling_tc(const TcPlan *p, const SysDev &s, const double *M, int nvec,
+                        float *vf, unsigned *status, cudaStream_t st) {
+  const size_t n = (size_t)p->Bs * p->A;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  tc::EpiArgs ea{};
+  ea.N = p->N;
+  ea.ucd = vf;
+  ea.status = status;
+  const int num_kb = p->A / tc::BK;
+  // L_hi M_hi, then + L_hi M_lo, then + L_lo M_hi
+  tc::k_split_m<<<blocks, 256, 0, st>>>(M, nvec, s.n_aux, p->Bs, p->A, 0, p->yh);
+  ea.ldo = 0;
+  dispatch_bn<tc::E_VACC>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+  ea.ldo = 1;
+  dispatch_bn<tc::E_VACC>(p->BN, p->g2Alo, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+  tc::k_split_m<<<blocks, 256, 0, st>>>(M, nvec, s.n_aux, p->Bs, p->A, 1, p->yh);
+  dispatch_bn<tc::E_VACC>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
 }
 
 void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaStream_t st) {

@@ -300,6 +300,31 @@ __global__ void __launch_bounds__(VEC_THREADS) k_start_from_v(VecCtx c, const do
   if (threadIdx.x == 0) c.norm_a[(size_t)b * c.nchunks + chunk] = nrm;
 }
 
+// w = Delta^1/2 * vf (float coupling vectors from the tensor cores) and
+// ||w||^2 partials; padding vectors get zeros.
+__global__ void __launch_bounds__(VEC_THREADS) k_start_from_vf(VecCtx c, const float *vf) {
+  __shared__ double red[VEC_THREADS / 32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const size_t voff = (size_t)b * c.N;
+  const int e0 = elem_base(chunk);
+  double nrm = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= c.N) continue;
+    double x0 = 0.0, x1 = 0.0;
+    if (b < c.nvec) {
+      const float2 v2 = *reinterpret_cast<const float2 *>(vf + voff + e);
+      x0 = c.dsq[e] * (double)v2.x;
+      x1 = c.dsq[e + 1] * (double)v2.y;
+    }
+    *reinterpret_cast<double2 *>(c.w + voff + e) = make_double2(x0, x1);
+    nrm = fma(x0, x0, fma(x1, x1, nrm));
+  }
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) c.norm_a[(size_t)b * c.nchunks + chunk] = nrm;
+}
+
 __global__ void __launch_bounds__(VEC_THREADS) k_norm_partials(VecCtx c, const double *x,
                                                                double *out) {
   __shared__ double red[VEC_THREADS / 32];
@@ -331,6 +356,9 @@ static dim3 vec_grid(const VecCtx &c) { return dim3(c.nchunks, c.Bs); }
 
 void launch_start_from_v(const VecCtx &c, const double *V, int ldv, int n_valid, cudaStream_t st) {
   k_start_from_v<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, V, ldv, n_valid);
+}
+void launch_start_from_vf(const VecCtx &c, const float *vf, cudaStream_t st) {
+  k_start_from_vf<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, vf);
 }
 void launch_norm_partials(const VecCtx &c, const double *x, double *out, cudaStream_t st) {
   k_norm_partials<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, x, out);

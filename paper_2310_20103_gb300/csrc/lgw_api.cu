@@ -378,7 +378,10 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
     c.blo = wsT<float>(h, "basis_lo", (size_t)(k + 1) * Bs * N);
   }
   c.dsqf = s.dsqf;
-  c.ucd = (split && tc) ? wsT<float>(h, "ucd", (size_t)Bs * N) : nullptr;
+  // float [Bs][N]: the split-basis epilogue output (c_K Delta^1/2 U) and, at
+  // the start of each sub-batch, the tensor-core coupling vectors V = L M
+  float *ucd_buf = tc ? wsT<float>(h, "ucd", (size_t)Bs * N) : nullptr;
+  c.ucd = split ? ucd_buf : nullptr;
   c.d2f = s.d2f;
   c.kf = s.kf;
   c.n_yb = (s.A + 255) / 256;
@@ -439,7 +442,14 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
     c.nvec = nvec;
     // ---- start vectors b = Delta^1/2 V, V = L M (text after Eq. 8) ----
     tm.mark(C_START);
-    if (pv.d_M) {
+    if (pv.d_M && tc) {
+      // V = L M on the tensor cores in split BF16 (three products, FP32 sum)
+      float *vf = ucd_buf;
+      launch_coupling_tc(plan, s, pv.d_M + (size_t)vec0 * s.n_aux, nvec, vf, h->d_status, st);
+      check_launch(h, "coupling_tc");
+      launch_start_from_vf(c, vf, st);
+      check_launch(h, "start_from_vf");
+    } else if (pv.d_M) {
       LGW_TRY_CUDA(h, cudaMemsetAsync(Y64, 0, sizeof(double) * Bs * s.A, st));
       LGW_TRY_CUDA(h, cudaMemcpy2DAsync(Y64, sizeof(double) * s.A, pv.d_M + (size_t)vec0 * s.n_aux,
                                         sizeof(double) * s.n_aux, sizeof(double) * s.n_aux, nvec,
@@ -745,8 +755,9 @@ lgw_status lgw_prepare_system(lgw_handle *h, const lgw_system_desc *d, lgw_syste
   s.L64 = (double *)alloc(sizeof(double) * (size_t)s.N * s.A);
   s.Lb = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
   s.Ltb = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
+  s.Lb_lo = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
   if (!s.eps || !s.Delta || !s.dsq || !s.Delta2 || !s.cd || !s.dsqf || !s.d2f || !s.cdf ||
-      !s.L64 || !s.Lb || !s.Ltb) {
+      !s.L64 || !s.Lb || !s.Ltb || !s.Lb_lo) {
     for (void *p : allocs) cudaFree(p);
     delete sys;
     return set_err(h, LGW_ERR_OOM, "device allocation for the system failed");
@@ -782,7 +793,8 @@ lgw_status lgw_release_system(lgw_system *sys) {
   cudaSetDevice(sys->h->device);
   cudaStreamSynchronize(sys->h->stream);
   SysDev &s = sys->s;
-  void *ps[] = {s.eps, s.Delta, s.dsq, s.Delta2, s.cd, s.dsqf, s.d2f, s.cdf, s.L64, s.Lb, s.Ltb};
+  void *ps[] = {s.eps,  s.Delta, s.dsq, s.Delta2, s.cd,  s.dsqf,
+                s.d2f, s.cdf,   s.L64, s.Lb,     s.Ltb, s.Lb_lo};
   for (void *p : ps)
     if (p) cudaFree(p);
   delete sys;

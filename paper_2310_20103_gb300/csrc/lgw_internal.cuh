@@ -51,6 +51,7 @@ struct SysDev {
   double *L64;      // [N][A] row-major, zero padded
   __nv_bfloat16 *Lb;    // [N][A]   K-major operand of the L Y contraction
   __nv_bfloat16 *Ltb;   // [A][N]   K-major operand of the L^T X contraction
+  __nv_bfloat16 *Lb_lo; // [N][A]   bf16(L - bf16(L)): second half of a split-BF16 L
 };
 
 // ---------------------------------------------------------------------------
@@ -176,10 +177,18 @@ void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qp
                      cudaStream_t st);
 // Store-only FP32 epilogue for the split basis: ucd = c_K Delta^1/2 U.
 void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaStream_t st);
+// Coupling vectors V = L M in split BF16 on the tensor cores:
+// V ~ L_hi M_hi + L_hi M_lo + L_lo M_hi (FP32 accumulation into vf [Bs][N]).
+// M rows [nvec][n_aux] (FP64, device); uses the plan's yh buffer for the
+// bf16 halves of M.
+void launch_coupling_tc(const TcPlan *p, const SysDev &s, const double *M, int nvec,
+                        float *vf, unsigned *status, cudaStream_t st);
 int tc_n_mt(const SysDev &s);
 
 // k_lanczos.cu : vector kernels of one step
 void launch_start_from_v(const VecCtx &c, const double *V, int ldv, int n_valid, cudaStream_t st);
+// w = Delta^1/2 vf (vf float [Bs][N], rows >= nvec ignored) and ||w||^2 partials.
+void launch_start_from_vf(const VecCtx &c, const float *vf, cudaStream_t st);
 void launch_norm_partials(const VecCtx &c, const double *x, double *out, cudaStream_t st);
 void launch_normalize(const VecCtx &c, int j, int is_start, const double *norm, cudaStream_t st);
 void launch_alpha_axpy(const VecCtx &c, int j, cudaStream_t st);
