@@ -239,8 +239,23 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         cms = e0.elapsed_time(e1)
+        e_cgs2 = e.cpu().numpy().copy()
         cgs2 = {"value": tps / (cms / 1e3), "unit": "QP states/s", "ms_per_step": cms,
                 "steps": 1}
+    # one step with the float-only Krylov basis (option), same batch as above
+    fbasis = None
+    if cgs2 is not None:
+        o3 = L.Options(k=args.k, precision=args.precision, reorth=args.reorth,
+                       b_sub=args.tps * M_PER_TARGET, reorth_arith="split32")
+        e0.record(stream)
+        L.lgw_sigma_c(h, sysd, batch(args.warmup + args.steps), o3, sig, e, z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1)
+        fbasis = {"value": tps / (fms / 1e3), "unit": "QP states/s", "ms_per_step": fms,
+                  "steps": 1, "reorth_arith": "split32 (float-only basis)",
+                  "qp_diff_mev_vs_cgs2_split48": float(
+                      np.abs(e.cpu().numpy() - e_cgs2).max() * 1e3)}
     ms_max = R.max_over_ranks(ms, dev) if world > 1 else ms
     states = tps * args.steps * world
     value = states / (ms_max / 1e3)
@@ -332,6 +347,7 @@ def run_gpu(args):
         "breakdown_ms": {k: agg[k] for k in agg if k.startswith("ms_")},
         "n_second_pass": int(agg["n_second_pass"]),
         "cgs2_step": cgs2,
+        "float_basis_step": fbasis,
     }
     if rank == 0 and world == 1 and not args.no_fp64_compare:
         line["fp64_path"] = fp64_compare(args, L, h, sysd, wl, tgt_all, m_idx_d, omega_d, M_all,

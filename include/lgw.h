@@ -83,8 +83,19 @@ typedef enum {
  *               FP64 and the O(eps||w||) rest in FP32 from the hi part.
  *               Orthogonality stays at FP64 level; the FP64 pipe, which runs at
  *               1/58 of the FP32 rate on GB300, leaves the inner loops.
+ * LGW_RA_SPLIT32: as SPLIT but only the hi float of each basis vector is
+ *               stored and read (4 instead of 8 bytes per element in the dot
+ *               products).  Products with the FP64 w stay exact; w ends up
+ *               orthogonal to fl32(q_i), i.e. within ~2^-24 / sqrt(N_vc) of
+ *               orthogonal to q_i (about 1e-10 at N_vc = 131072), inside the
+ *               semi-orthogonality (sqrt(eps)) that keeps T_k accurate.
  * LGW_RA_AUTO:  SPLIT with BF16 contractions, FP64 with FP64 contractions. */
-typedef enum { LGW_RA_AUTO = 0, LGW_RA_FP64 = 1, LGW_RA_SPLIT = 2 } lgw_reorth_arith;
+typedef enum {
+  LGW_RA_AUTO = 0,
+  LGW_RA_FP64 = 1,
+  LGW_RA_SPLIT = 2,
+  LGW_RA_SPLIT32 = 3
+} lgw_reorth_arith;
 
 typedef struct lgw_handle lgw_handle;
 typedef struct lgw_system lgw_system;

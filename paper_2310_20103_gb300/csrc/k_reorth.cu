@@ -66,6 +66,7 @@ __device__ __forceinline__ const float *blo_row(const VecCtx &c, int i, int b) {
 // One lane's share of a row . w over a VEC_CHUNK chunk in double-float:
 // four quarters of 512 elements, each lane a float4 of hi and of lo per 128
 // elements (4 + 4 independent 128-bit loads per quarter).
+template <bool LO>
 __device__ __forceinline__ void dot_row_df(const float *__restrict__ qh,
                                            const float *__restrict__ ql, const float *swh,
                                            const float *swl, int lane, int nvalid, float &sh,
@@ -78,7 +79,8 @@ __device__ __forceinline__ void dot_row_df(const float *__restrict__ qh,
       const int off = qt * 512 + 128 * t + 4 * lane;
       if (off < nvalid) {
         hv[t] = __ldg(reinterpret_cast<const float4 *>(qh + off));
-        lv[t] = __ldg(reinterpret_cast<const float4 *>(ql + off));
+        lv[t] = LO ? __ldg(reinterpret_cast<const float4 *>(ql + off))
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
       } else {
         hv[t] = make_float4(0.f, 0.f, 0.f, 0.f);
         lv[t] = hv[t];
@@ -195,9 +197,11 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_dots_split(VecCtx c, int j) 
   double *dp = c.dot_part + ((size_t)b * c.nchunks + chunk) * c.kmax1;
   for (int i = wid; i <= j; i += VEC_THREADS / 32) {
     const float *qh = bhi_row(c, i, b) + cbase;
-    const float *ql = blo_row(c, i, b) + cbase;
     float sh = 0.f, sl = 0.f;
-    dot_row_df(qh, ql, swh, swl, lane, nvalid, sh, sl);
+    if (c.blo != nullptr)
+      dot_row_df<true>(qh, blo_row(c, i, b) + cbase, swh, swl, lane, nvalid, sh, sl);
+    else
+      dot_row_df<false>(qh, nullptr, swh, swl, lane, nvalid, sh, sl);
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
       const float rh = __shfl_xor_sync(0xffffffffu, sh, o);
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j
   double *qn = slot_ptr(c, next) + voff;
   const bool keep_basis = next < c.k + 1;
   float *hn = c.bhi + ((size_t)next * c.Bs + b) * c.N;
-  float *ln = c.blo + ((size_t)next * c.Bs + b) * c.N;
+  float *ln = c.blo ? c.blo + ((size_t)next * c.Bs + b) * c.N : nullptr;
   const double *w = c.w + voff;
   const double inv = live ? sinv : 0.0;
   const int e0 = elem_base_s(chunk);
@@ -365,8 +369,9 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j
     dq = fmaf(c.d2f[e] * hx, hx, fmaf(c.d2f[e + 1] * hy, hy, dq));
     if (keep_basis) {
       *reinterpret_cast<float2 *>(hn + e) = make_float2(hx, hy);
-      *reinterpret_cast<float2 *>(ln + e) = make_float2(__double2float_rn(q2.x - (double)hx),
-                                                        __double2float_rn(q2.y - (double)hy));
+      if (c.blo != nullptr)
+        *reinterpret_cast<float2 *>(ln + e) = make_float2(__double2float_rn(q2.x - (double)hx),
+                                                          __double2float_rn(q2.y - (double)hy));
     }
     if (c.xh != nullptr) {
       __nv_bfloat162 x2;

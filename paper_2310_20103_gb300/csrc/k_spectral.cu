@@ -28,6 +28,22 @@ __device__ __forceinline__ void rot_sym(double c, double s, double *d, double *e
   e[i] = cs * (cc - a) + (c2 - s2) * bb;
 }
 
+// Givens pair (c, s) with c x + s z = r >= 0, -s x + c z = 0, from one
+// reciprocal square root (no FP64 division: GB300 runs FP64 at 1/58 rate).
+__device__ __forceinline__ void givens(double x, double z, double &c, double &s, double &r) {
+  const double r2 = fma(x, x, z * z);
+  if (r2 > 0.0) {
+    const double inv = rsqrt(r2);
+    c = x * inv;
+    s = z * inv;
+    r = r2 * inv;
+  } else {
+    c = 1.0;
+    s = 0.0;
+    r = 0.0;
+  }
+}
+
 // Eigenvalues of the symmetric tridiagonal (d[0..n), e[0..n-1)) and the first
 // row u of its eigenvector matrix, by implicit symmetric QR steps with the
 // Wilkinson shift (Golub & Van Loan, implicit symmetric QR).  On return d
@@ -56,9 +72,8 @@ __device__ bool tridiag_eig_first_row(double *d, double *e, double *u, int n) {
     const double mu = d[hi] - bb * bb / den;
     double x = d[lo] - mu, z = e[lo];
     for (int kk = lo; kk < hi; ++kk) {
-      const double r = hypot(x, z);
-      const double c = (r != 0.0) ? x / r : 1.0;
-      const double s = (r != 0.0) ? z / r : 0.0;
+      double c, s, r;
+      givens(x, z, c, s, r);
       if (kk > lo) e[kk - 1] = r;
       rot_sym(c, s, d, e, kk);
       if (kk + 1 < hi) {
@@ -92,9 +107,12 @@ __device__ double jacobi_from_nodes(const double *x, const double *wt, int n, do
     a[0] = x[jn];
     b[0] = 0.0;
     const double wj = wt[jn];
-    const double r = sqrt(W + wj);
-    double c = (r > 0.0) ? sqrt(wj) / r : 1.0;
-    double s = (r > 0.0) ? sqrt(W) / r : 0.0;
+    double c = 1.0, s = 0.0;
+    if (W + wj > 0.0) {
+      const double inv = rsqrt(W + wj);
+      c = sqrt(wj) * inv;
+      s = sqrt(W) * inv;
+    }
     ++m;
     rot_sym(c, s, a, b, 0);
     double bulge = 0.0;
@@ -103,10 +121,8 @@ __device__ double jacobi_from_nodes(const double *x, const double *wt, int n, do
       b[1] *= c;
     }
     for (int kk = 1; kk < m - 1 && bulge != 0.0; ++kk) {
-      const double xx = b[kk - 1];
-      const double rr = hypot(xx, bulge);
-      c = xx / rr;
-      s = bulge / rr;
+      double rr;
+      givens(b[kk - 1], bulge, c, s, rr);
       b[kk - 1] = rr;
       rot_sym(c, s, a, b, kk);
       if (kk + 1 < m - 1) {
@@ -121,10 +137,18 @@ __device__ double jacobi_from_nodes(const double *x, const double *wt, int n, do
   return W;
 }
 
+// Work rows (d, e, u and the Jacobi diagonal a) live in shared memory when
+// they fit: the rotation chains read values the same thread just wrote, and
+// through global memory each of those round trips costs an L2 latency.
+constexpr int SPEC_THREADS = 4;
+constexpr size_t SPEC_SMEM_MAX = 96 * 1024;
+
+template <bool SMEM>
 __global__ void k_spectral(const double *__restrict__ alpha, const double *__restrict__ beta,
                            const double *__restrict__ beta0, const int *__restrict__ k_eff, int B,
                            int k, double *sd, double *se, double *su, JacobiBufs jb,
                            unsigned long long *min_theta_bits, unsigned *status) {
+  extern __shared__ double sm[];
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= B) return;
   const int n = k_eff[v];
@@ -133,7 +157,19 @@ __global__ void k_spectral(const double *__restrict__ alpha, const double *__res
     jb.w0[v] = 0.0;
     return;
   }
-  double *d = sd + (size_t)v * k, *e = se + (size_t)v * k, *u = su + (size_t)v * k;
+  double *d, *e, *u, *a;
+  if (SMEM) {
+    double *base = sm + (size_t)threadIdx.x * 4 * k;
+    d = base;
+    e = base + k;
+    u = base + 2 * k;
+    a = base + 3 * k;
+  } else {
+    d = sd + (size_t)v * k;
+    e = se + (size_t)v * k;
+    u = su + (size_t)v * k;
+    a = jb.a + (size_t)v * k;
+  }
   for (int i = 0; i < n; ++i) {
     d[i] = alpha[(size_t)v * k + i];
     e[i] = (i + 1 < n) ? beta[(size_t)v * k + i] : 0.0;
@@ -159,19 +195,34 @@ __global__ void k_spectral(const double *__restrict__ alpha, const double *__res
   } else {
     atomicMin(min_theta_bits, (unsigned long long)__double_as_longlong(tmin));
   }
-  double *a = jb.a + (size_t)v * k, *b2 = jb.b2 + (size_t)v * k;
   const double W = jacobi_from_nodes(d, u, n, a, e);
-  for (int i = 0; i + 1 < n; ++i) b2[i] = e[i] * e[i];
-  if (n > 0) b2[n - 1] = 0.0;
+  double *ga = jb.a + (size_t)v * k, *b2 = jb.b2 + (size_t)v * k;
+  for (int i = 0; i < n; ++i) {
+    if (SMEM) ga[i] = a[i];
+    b2[i] = (i + 1 < n) ? e[i] * e[i] : 0.0;
+  }
   jb.w0[v] = W;
 }
 
 void launch_spectral_impl(const double *alpha, const double *beta, const double *beta0,
                           const int *k_eff, int B, int k, JacobiBufs jb, double *scratch,
                           unsigned long long *min_theta_bits, unsigned *status, cudaStream_t st) {
-  const int th = 4;   // spread the latency-bound per-vector chains over many SMs
-  k_spectral<<<(B + th - 1) / th, th, 0, st>>>(alpha, beta, beta0, k_eff, B, k, scratch,
-                                               scratch + (size_t)B * k, scratch + (size_t)2 * B * k,
-                                               jb, min_theta_bits, status);
+  const int th = SPEC_THREADS;
+  const size_t smem = (size_t)th * 4 * k * sizeof(double);
+  const dim3 grid((B + th - 1) / th);
+  if (smem <= SPEC_SMEM_MAX) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_spectral<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SPEC_SMEM_MAX);
+      attr = true;
+    }
+    k_spectral<true><<<grid, th, smem, st>>>(alpha, beta, beta0, k_eff, B, k, nullptr, nullptr,
+                                             nullptr, jb, min_theta_bits, status);
+  } else {
+    k_spectral<false><<<grid, th, 0, st>>>(alpha, beta, beta0, k_eff, B, k, scratch,
+                                           scratch + (size_t)B * k, scratch + (size_t)2 * B * k,
+                                           jb, min_theta_bits, status);
+  }
 }
 }  // namespace lgw

@@ -229,7 +229,7 @@ void check_status(lgw_handle *h) {
 }
 
 struct Opts {
-  int k, precision, reorth, b_sub, qp_max_iter, use_graph, split;
+  int k, precision, reorth, b_sub, qp_max_iter, use_graph, split, split32;
   double tol, qp_tol;
 };
 
@@ -245,12 +245,13 @@ Opts resolve_opts(lgw_handle *h, const lgw_options *o, const SysDev &s) {
   r.b_sub = o->b_sub;
   r.qp_max_iter = o->qp_max_iter > 0 ? o->qp_max_iter : 50;
   r.use_graph = o->use_graph;
-  if (o->reorth_arith < LGW_RA_AUTO || o->reorth_arith > LGW_RA_SPLIT) {
+  if (o->reorth_arith < LGW_RA_AUTO || o->reorth_arith > LGW_RA_SPLIT32) {
     set_err(h, LGW_ERR_ARG, "unknown reorthogonalisation arithmetic %d", o->reorth_arith);
     throw Fail{LGW_ERR_ARG};
   }
-  r.split = o->reorth_arith == LGW_RA_SPLIT ||
+  r.split = o->reorth_arith == LGW_RA_SPLIT || o->reorth_arith == LGW_RA_SPLIT32 ||
             (o->reorth_arith == LGW_RA_AUTO && o->precision == LGW_BF16);
+  r.split32 = o->reorth_arith == LGW_RA_SPLIT32;
   r.tol = o->breakdown_tol > 0 ? o->breakdown_tol : 1e-13;
   r.qp_tol = o->qp_tol > 0 ? o->qp_tol : 1e-10;
   if (r.k < 1 || r.k > s.n_vc) {
@@ -375,7 +376,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   c.basis = wsT<double>(h, split ? "ring" : "basis", (size_t)nslots * Bs * N);
   if (split) {
     c.bhi = wsT<float>(h, "basis_hi", (size_t)(k + 1) * Bs * N);
-    c.blo = wsT<float>(h, "basis_lo", (size_t)(k + 1) * Bs * N);
+    c.blo = o.split32 ? nullptr : wsT<float>(h, "basis_lo", (size_t)(k + 1) * Bs * N);
   }
   c.dsqf = s.dsqf;
   // float [Bs][N]: the split-basis epilogue output (c_K Delta^1/2 U) and, at

@@ -69,7 +69,8 @@ struct VecCtx {
   double *w;              // [Bs][N]
   double *basis;          // slot s: basis + s * Bs * N
   __nv_bfloat16 *xh;      // [Bs][N]   bf16(Delta^1/2 q_j)
-  float *bhi, *blo;       // split basis [k+1][Bs][N]: q = hi + lo (48 bits)
+  float *bhi, *blo;       // split basis [k+1][Bs][N]: q = hi + lo (48 bits); blo may be
+                          // null (float-only basis)
   const float *dsqf;      // [N]
   const float *d2f;       // [N] Delta^2 (float)
   const float *ucd;       // [Bs][N] c_K Delta^1/2 (L y) from the FP32 epilogue, or null

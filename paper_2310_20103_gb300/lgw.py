@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "LGW_OK", 1: "LGW_ERR_ARG", 2: "LGW_ERR_SHAPE", 3: "LGW_ERR_C
                 7: "LGW_ERR_TIMEOUT", 8: "LGW_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "bf16": 1}
 REORTH = {"none": 0, "cgs2": 1, "cgs1k": 2}
-REORTH_ARITH = {"auto": 0, "fp64": 1, "split": 2}
+REORTH_ARITH = {"auto": 0, "fp64": 1, "split": 2, "split32": 3}
 
 
 class LgwError(RuntimeError):

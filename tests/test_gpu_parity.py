@@ -145,6 +145,19 @@ def test_tiny_fp64_k64_vs_oracle_lanczos(L, handle, tiny_ref, reorth, arith):
     assert np.all(np.abs(z - Z64) <= 1e-8)
 
 
+def test_float_basis_option(L, handle, tiny_ref):
+    """Float-only basis (split32): w is orthogonalised against fl32(q_i), so
+    orthogonality to the FP64 q_i is ~2^-24 / sqrt(N_vc) ~ 4e-9 here and T_k
+    inherits errors of that relative size; Sigma within 1e-6 relative and
+    E_qp within 1e-8 eV of the oracle (FP64 contractions)."""
+    wl, (sig64, E64, _, _), _ = tiny_ref
+    for reorth in ("cgs2", "cgs1k"):
+        sig, e, _, _ = _run(L, handle, wl, L.Options(k=64, precision="fp64", reorth=reorth,
+                                                     reorth_arith="split32"))
+        assert _rel_sigma_err(sig, sig64) < 1e-6
+        assert np.abs(e - E64).max() < 1e-8
+
+
 @pytest.mark.parametrize("arith", ["fp64", "split"])
 def test_tiny_fp64_full_k_vs_closed_form(L, handle, tiny_ref, arith):
     wl, _, (sigx, Ex, Zx) = tiny_ref
@@ -296,8 +309,10 @@ def test_mid_ragged_fp64_and_bf16(L, handle):
         assert _rel_sigma_err(sig, ref) < 1e-9
         assert np.abs(e - Er).max() < 1e-9
     for reorth in ("cgs2", "cgs1k"):
-        sigb, eb, _, _ = _run(L, handle, wl, L.Options(k=40, precision="bf16", reorth=reorth))
-        assert np.abs(eb - Er).max() < 1e-3
+        for arith in ("auto", "split32"):
+            sigb, eb, _, _ = _run(L, handle, wl, L.Options(k=40, precision="bf16", reorth=reorth,
+                                                           reorth_arith=arith))
+            assert np.abs(eb - Er).max() < 1e-3
 
 
 def test_errors_are_reported(L, handle):
