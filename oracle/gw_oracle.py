@@ -36,7 +36,7 @@ __all__ = [
     "coupling_vectors", "start_vectors", "casida_eigenpairs",
     "closed_form_poles", "lanczos", "lanczos_poles", "sigma_from_poles",
     "dsigma_from_poles", "sigma_closed_form", "sigma_lanczos", "qp_solve",
-    "solve_all_qp",
+    "solve_all_qp", "qp_gradient", "qp_energies_closed_form", "qp_gradient_closed_form",
 ]
 
 
@@ -329,3 +329,82 @@ def solve_all_qp(wl, poles, static_shift=None):
 
         E[ti], Z[ti] = qp_solve(e0, sfn, dfn, grid=wl.omega)
     return E, Z
+
+
+# --------------------------------------------------------------------------
+# Gradients of the QP energies (implicit function of the QP equation)
+# --------------------------------------------------------------------------
+def _f_and_divdiff(Om, z, eta):
+    """f(theta) = 1 / (sqrt(theta) (z + eta sqrt(theta))) at theta = Om^2 and
+    its divided differences f[theta_s, theta_t] (f' on the diagonal), through
+    g(Om) = 1/(Om (z + eta Om)):  f[.,.] = g[Om_s, Om_t] / (Om_s + Om_t),
+    g[Om_s, Om_t] = -(z + eta (Om_s + Om_t)) / (Om_s Om_t (z+eta Om_s)(z+eta Om_t))."""
+    a = z + eta * Om
+    f = 1.0 / (Om * a)
+    num = -(z + eta * (Om[:, None] + Om[None, :]))
+    den = (Om[:, None] * Om[None, :]) * (a[:, None] * a[None, :]) * (Om[:, None] + Om[None, :])
+    return f, num / den
+
+
+def qp_gradient(wl, dE, E, Z, basis):
+    """d(sum_t dE[t] E_t)/dL and /d(eps) of the QP energies.
+
+    E_t = eps_t + s_t + Re Sigma_t(E_t) gives dE_t = Z_t (d eps_t + Re dSigma_t)
+    at fixed omega = E_t.  Each term F = b^T f(C) b of Sigma_t (Eq. 7-9 with
+    f(theta) = 1/(sqrt(theta)(z_m + eta_m sqrt(theta)))) varies as
+        dF = 2 (f(C) b) . db + tr(G dC) - (dF/dz) d eps_m,
+        G = Y (F_div o (p p^T)) Y^T,   p = Y^T b          (Daleckii-Krein)
+    where `basis(v)` returns (Y, theta) for start vector v: the Casida
+    eigenvectors and eigenvalues (closed form) or a Lanczos basis Q_k with
+    the eigen-decomposition of T_k (Q_k U, theta) (Krylov form; exact at
+    k = N_vc).  With C = Delta^2 + c_K D L L^T D, D = diag(Delta^1/2),
+    b = D L M:
+        dF/dL     = 2 c_K D G D L + (D y) M^T,     y = 2 f(C) b
+        dF/dDelta = 2 Delta diag(G) + c_K diag(K D G)/d + y V / (2 d).
+    Returns (dL [N_vc, N_aux], deps [n_v + n_c])."""
+    Delta = pair_energies(wl.eps, wl.n_v)
+    d = np.sqrt(Delta)
+    V_all = coupling_vectors(wl.L, wl.M)                       # [n_t, n_m, N_vc]
+    eta_all = occupation_sign(wl.m_idx, wl.n_v)
+    SC = np.zeros_like(wl.L)          # sum c G D L (C path)
+    SB = np.zeros_like(wl.L)          # sum (D y) M^T (b path)
+    dDelta = np.zeros(wl.n_vc)
+    deps = np.zeros(wl.n_v + wl.n_c)
+    for ti, t in enumerate(wl.targets):
+        cw = dE[ti] * Z[ti]
+        deps[t] += cw
+        for mi, m in enumerate(wl.m_idx):
+            v = ti * wl.n_m + mi
+            Y, theta = basis(v)
+            Om = np.sqrt(theta)
+            b = d * V_all[ti, mi]
+            p = Y.T @ b
+            z = E[ti] - wl.eps[m] - 1j * eta_all[mi] * wl.delta
+            f, F = _f_and_divdiff(Om, z, eta_all[mi])
+            y = 2.0 * (Y @ (f * p)).real                       # dF/db
+            Gm = (Y @ ((F * np.outer(p, p)).real) @ Y.T)       # dF/dC
+            dFdz = -np.sum(p * p / (Om * (z + eta_all[mi] * Om) ** 2))
+            SC += cw * (Gm @ (d[:, None] * wl.L))
+            SB += cw * np.outer(d * y, wl.M[ti, mi])
+            dDelta += cw * (2.0 * Delta * np.diag(Gm) + y * V_all[ti, mi] / (2.0 * d))
+            deps[m] -= cw * dFdz.real
+    dL = 2.0 * wl.kernel_factor * d[:, None] * SC + SB
+    dDelta += wl.kernel_factor * np.sum(wl.L * SC, axis=1) / d
+    # Delta_vc = eps_c - eps_v, vc = v * n_c + c
+    dD = dDelta.reshape(wl.n_v, wl.n_c)
+    deps[wl.n_v:] += dD.sum(axis=0)
+    deps[: wl.n_v] -= dD.sum(axis=1)
+    return dL, deps
+
+
+def qp_energies_closed_form(wl):
+    """E_t and Z_t from the closed form (Eq. 7-9)."""
+    _, poles = sigma_closed_form(wl)
+    return solve_all_qp(wl, poles)
+
+
+def qp_gradient_closed_form(wl, dE):
+    """Gradient of sum_t dE[t] E_t with the Casida eigenpairs (exact)."""
+    E, Z = qp_energies_closed_form(wl)
+    theta, Y = np.linalg.eigh(casida_matrix(wl.eps, wl.n_v, wl.L, wl.kernel_factor))
+    return qp_gradient(wl, dE, E, Z, lambda v: (Y, theta))
