@@ -37,6 +37,7 @@ __all__ = [
     "closed_form_poles", "lanczos", "lanczos_poles", "sigma_from_poles",
     "dsigma_from_poles", "sigma_closed_form", "sigma_lanczos", "qp_solve",
     "solve_all_qp", "qp_gradient", "qp_energies_closed_form", "qp_gradient_closed_form",
+    "qp_gradient_lanczos",
 ]
 
 
@@ -163,7 +164,7 @@ def sigma_closed_form(wl):
 # --------------------------------------------------------------------------
 # Lanczos tridiagonalisation (Eq. 13), run on C itself from |P_tm>
 # --------------------------------------------------------------------------
-def lanczos(apply_op, b, k, reorth=True, breakdown_tol=1e-13):
+def lanczos(apply_op, b, k, reorth=True, breakdown_tol=1e-13, return_basis=False):
     """k-step Lanczos from each row of ``b`` ([n_vec, N]).
 
     Every row is an independent recurrence (own basis, own coefficients); the
@@ -176,7 +177,8 @@ def lanczos(apply_op, b, k, reorth=True, breakdown_tol=1e-13):
 
     Returns alpha [n_vec, k], beta [n_vec, k] (beta[:, j] couples steps j and
     j+1, i.e. the paper's b_{j+1}; beta[:, k-1] is the residual norm),
-    beta0 = ||b|| [n_vec] and k_eff [n_vec].
+    beta0 = ||b|| [n_vec] and k_eff [n_vec]; with return_basis also the
+    basis Q [k, n_vec, N] (rows past k_eff are zero).
     """
     b = np.atleast_2d(np.asarray(b, dtype=np.float64))
     n_vec, N = b.shape
@@ -187,13 +189,13 @@ def lanczos(apply_op, b, k, reorth=True, breakdown_tol=1e-13):
     k_eff = np.full(n_vec, k, dtype=np.int64)
     active = beta0 > 0.0
     k_eff[~active] = 0
-    Q = np.zeros((k + 1, n_vec, N)) if reorth else None
+    Q = np.zeros((k + 1, n_vec, N)) if (reorth or return_basis) else None
     q = np.where(active[:, None], b / np.where(active, beta0, 1.0)[:, None], 0.0)
     q_prev = np.zeros_like(q)
     beta_j = np.zeros(n_vec)
     amax = np.zeros(n_vec)
     for j in range(k):
-        if reorth:
+        if Q is not None:
             Q[j] = q
         w = apply_op(q) - beta_j[:, None] * q_prev
         a = np.einsum("vi,vi->v", q, w)
@@ -212,6 +214,8 @@ def lanczos(apply_op, b, k, reorth=True, breakdown_tol=1e-13):
         q_prev = q
         q = np.where(active[:, None], w / np.where(active, bn, 1.0)[:, None], 0.0)
         beta_j = np.where(active, bn, 0.0)
+    if return_basis:
+        return alpha, beta, beta0, k_eff, Q[:k]
     return alpha, beta, beta0, k_eff
 
 
@@ -401,6 +405,29 @@ def qp_energies_closed_form(wl):
     """E_t and Z_t from the closed form (Eq. 7-9)."""
     _, poles = sigma_closed_form(wl)
     return solve_all_qp(wl, poles)
+
+
+def qp_gradient_lanczos(wl, dE, k=None, reorth=True):
+    """Krylov form of the gradient at k Lanczos steps: E_t, Z_t from the
+    k-step pole sums and, per start vector, (Y, theta) = (Q_k U, theta) with
+    T_k = U diag(theta) U^T.  Equals the closed form at k = N_vc."""
+    k = wl.k if k is None else k
+    b = start_vectors(wl.eps, wl.n_v, coupling_vectors(wl.L, wl.M)).reshape(wl.n_t * wl.n_m, -1)
+    alpha, beta, beta0, k_eff, Q = lanczos(
+        lambda X: apply_casida(wl.eps, wl.n_v, wl.L, X, wl.kernel_factor), b, k, reorth=reorth,
+        return_basis=True)
+    _, poles, _ = sigma_lanczos(wl, coeffs=(alpha, beta, beta0, k_eff))
+    E, Z = solve_all_qp(wl, poles)
+
+    def basis(v):
+        ke = int(k_eff[v])
+        T = np.diag(alpha[v, :ke])
+        if ke > 1:
+            T += np.diag(beta[v, : ke - 1], 1) + np.diag(beta[v, : ke - 1], -1)
+        theta, U = np.linalg.eigh(T)
+        return Q[:ke, v, :].T @ U, theta
+
+    return qp_gradient(wl, dE, E, Z, basis)
 
 
 def qp_gradient_closed_form(wl, dE):

@@ -1,0 +1,431 @@
+// Adjoint of the QP energies: d(sum_t dE_t E_t)/dL and /d(eps).
+//
+// E_t = eps_t + s_t + Re Sigma_t(E_t), so dE_t = Z_t (d eps_t + Re dSigma_t)
+// at fixed omega = E_t (implicit function).  Each term of Sigma_t is
+// F = b^T f(C) b with f(theta) = 1 / (sqrt(theta) (z_m + eta_m sqrt(theta)))
+// (Eq. 7-12).  In the k-step Krylov basis Q of (C, b) with
+// T_k = U diag(theta) U^T and u1 = U^T e1:
+//   dF/db = y = 2 f(C) b      ~ Q a_y,   a_y = 2 beta0 Re U (f(theta) o u1)
+//   dF/dC = G                 ~ Q Gam Q^T,  Gam = beta0^2 Re U (F o u1 u1^T) U^T
+//   dF/dz = -beta0^2 sum_s u1s^2 / (Omega_s (z + eta Omega_s)^2)
+// with F_st the divided differences of f (Daleckii-Krein); exact when the
+// Krylov space is the whole space.  With C = Delta^2 + c_K D L L^T D,
+// D = diag(Delta^1/2) and b = D L M:
+//   dL     = 2 c_K D (G D L) + D (y M^T)
+//   dDelta = 2 Delta diag(G) + c_K diag(L (G D L)^T) / d + y b / (2 Delta)
+// All per-vector weights c_v = dE_t Z_t are folded into a_y, Gam and dz.
+// FP64 throughout.
+#include "lgw_internal.cuh"
+
+namespace lgw {
+
+// --------------------------------------------------------------------------
+// Full eigen-decomposition of each T_k: implicit symmetric QR with Wilkinson
+// shifts (Golub & Van Loan, symmetric QR algorithm).  Lane 0 runs the scalar
+// chain and stages each sweep's rotations in shared memory; all 32 lanes then
+// rotate the rows of V = U^T (row s = eigenvector s, coalesced).  One warp
+// per vector.
+// --------------------------------------------------------------------------
+constexpr int EIG_WARPS = 4;
+
+__global__ void __launch_bounds__(EIG_WARPS * 32) k_eig_full(AdjCtx a) {
+  extern __shared__ double sm[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * EIG_WARPS + wid;
+  if (b >= a.Bs) return;
+  const int k = a.k;
+  double *d = sm + (size_t)wid * 4 * k;
+  double *e = d + k;
+  double *cs = e + k;      // c, s pairs of one sweep: cs[2*i], cs[2*i+1]
+  __shared__ int ctl[EIG_WARPS][3];
+  double *V = a.V + (size_t)b * k * k;
+  const int v = a.vec0 + b;
+  const int n = (b < a.nvec) ? a.k_eff[v] : 0;
+  for (int i = lane; i < k * k; i += 32) V[i] = ((i / k) == (i % k) && (i / k) < n) ? 1.0 : 0.0;
+  if (lane == 0) {
+    for (int i = 0; i < k; ++i) {
+      d[i] = (i < n) ? a.alpha[(size_t)v * k + i] : 0.0;
+      e[i] = (i + 1 < n) ? a.beta[(size_t)v * k + i] : 0.0;
+    }
+  }
+  __syncwarp();
+  const double eps = 2.220446049250313e-16;
+  int hi = n - 1, iter = 0;
+  const int max_iter = 60 * n + 60;
+  while (true) {
+    if (lane == 0) {
+      int lo = -1, ncs = 0;
+      while (hi > 0 && fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+        e[hi - 1] = 0.0;
+        --hi;
+      }
+      if (hi > 0 && ++iter <= max_iter) {
+        lo = hi - 1;
+        while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
+        if (lo > 0) e[lo - 1] = 0.0;
+        // Wilkinson shift from the trailing 2 x 2 block
+        const double dl = 0.5 * (d[hi - 1] - d[hi]);
+        const double bb = e[hi - 1];
+        const double den = dl + copysign(sqrt(fma(dl, dl, bb * bb)), dl != 0.0 ? dl : 1.0);
+        const double mu = d[hi] - bb * bb / den;
+        double x = d[lo] - mu, z = e[lo];
+        for (int kk = lo; kk < hi; ++kk) {
+          // R = [[c, s], [-s, c]] maps (x, z) to (r, 0); T <- R T R^T on rows kk, kk+1
+          const double r = hypot(x, z);
+          double c = 1.0, s = 0.0;
+          if (r > 0.0) {
+            c = x / r;
+            s = z / r;
+          }
+          if (kk > lo) e[kk - 1] = r;
+          const double a0 = d[kk], b0 = e[kk], c0 = d[kk + 1];
+          const double csn = c * s, c2 = c * c, s2 = s * s;
+          d[kk] = c2 * a0 + 2.0 * csn * b0 + s2 * c0;
+          d[kk + 1] = s2 * a0 - 2.0 * csn * b0 + c2 * c0;
+          e[kk] = csn * (c0 - a0) + (c2 - s2) * b0;
+          if (kk + 1 < hi) {
+            const double bulge = s * e[kk + 1];
+            e[kk + 1] *= c;
+            x = e[kk];
+            z = bulge;
+          }
+          cs[2 * ncs] = c;
+          cs[2 * ncs + 1] = s;
+          ++ncs;
+        }
+      }
+      ctl[wid][0] = lo;
+      ctl[wid][1] = ncs;
+      ctl[wid][2] = (hi > 0 && iter > max_iter) ? 1 : 0;
+    }
+    __syncwarp();
+    const int lo = ctl[wid][0], ncs = ctl[wid][1];
+    if (ctl[wid][2]) {
+      if (lane == 0) atomicOr(a.status, ST_NO_CONV);
+      break;
+    }
+    if (lo < 0) break;
+    // U <- U R^T, i.e. rows kk, kk+1 of V = U^T rotate by R
+    for (int r = 0; r < ncs; ++r) {
+      const double c = cs[2 * r], s = cs[2 * r + 1];
+      double *v0 = V + (size_t)(lo + r) * k;
+      double *v1 = v0 + k;
+      for (int i = lane; i < n; i += 32) {
+        const double x0 = v0[i], x1 = v1[i];
+        v0[i] = c * x0 + s * x1;
+        v1[i] = -s * x0 + c * x1;
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < k; i += 32) a.theta[(size_t)b * k + i] = (i < n) ? d[i] : 0.0;
+}
+
+// --------------------------------------------------------------------------
+// Per-vector adjoint coefficients a_y, Gam, dz (weights dE_t Z_t folded in).
+// One block of COEF_THREADS per vector:
+//   Phi_st = Re(F_st) u1_s u1_t,  X = U Phi,  Gam = c b0^2 X U^T.
+// --------------------------------------------------------------------------
+constexpr int COEF_THREADS = 128;
+
+__global__ void __launch_bounds__(COEF_THREADS) k_adj_coeffs(AdjCtx a) {
+  extern __shared__ double sm[];   // Om[k], u1[k], fu[k]
+  __shared__ double red[COEF_THREADS / 32];
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int k = a.k;
+  double *Ay = a.ay + (size_t)b * k;
+  double *Gm = a.Gam + (size_t)b * k * k;
+  const int v = a.vec0 + b;
+  const int n = (b < a.nvec) ? a.k_eff[v] : 0;
+  if (n <= 0) {
+    for (int i = tid; i < k; i += COEF_THREADS) Ay[i] = 0.0;
+    for (int i = tid; i < k * k; i += COEF_THREADS) Gm[i] = 0.0;
+    if (tid == 0) a.dz[b] = 0.0;
+    return;
+  }
+  const int ti = v / a.n_m, mi = v % a.n_m;
+  const int m = a.m_idx[mi];
+  const double eta = (m < a.n_v) ? 1.0 : -1.0;
+  const double cw = a.dE[ti] * a.Z[ti];
+  const double zr = a.E[ti] - a.eps[m], zi = -eta * a.delta;
+  const double b0 = a.beta0[v];
+  const double *V = a.V + (size_t)b * k * k;     // V[s][i]: component i of eigenvector s
+  const double *th = a.theta + (size_t)b * k;
+  double *Om = sm, *u1 = sm + k, *fu = sm + 2 * k;
+  double dzp = 0.0;
+  for (int s = tid; s < n; s += COEF_THREADS) {
+    const double om = sqrt(fmax(th[s], 0.0));
+    const double u = V[(size_t)s * k];
+    Om[s] = om;
+    u1[s] = u;
+    // a = z + eta Om;  Re f = Re 1/(Om a);  dF/dz term -u^2 / (Om a^2)
+    const double ar = zr + eta * om;
+    fu[s] = ar / (om * (ar * ar + zi * zi)) * u;
+    const double sr = ar * ar - zi * zi, si = 2.0 * ar * zi;
+    dzp += -(u * u / om) * (sr / (sr * sr + si * si));
+  }
+  dzp = block_sum(dzp, red);
+  if (tid == 0) a.dz[b] = cw * b0 * b0 * dzp;
+  __syncthreads();
+  // a_y[j] = 2 c b0 sum_s U[j][s] Re f_s u1_s = 2 c b0 sum_s V[s][j] fu[s]
+  for (int j = tid; j < k; j += COEF_THREADS) {
+    double acc = 0.0;
+    if (j < n)
+      for (int s = 0; s < n; ++s) acc = fma(V[(size_t)s * k + j], fu[s], acc);
+    Ay[j] = cw * 2.0 * b0 * acc;
+  }
+  // Phi_st = Re F_st u1_s u1_t,
+  // F_st = -(z + eta(Om_s + Om_t)) / (Om_s Om_t (z+eta Om_s)(z+eta Om_t) (Om_s + Om_t))
+  double *Phi = a.Phi + (size_t)b * k * k;
+  for (int idx = tid; idx < n * n; idx += COEF_THREADS) {
+    const int s = idx / n, t = idx % n;
+    const double as_r = zr + eta * Om[s], at_r = zr + eta * Om[t];
+    const double nr = -(zr + eta * (Om[s] + Om[t])), ni = -zi;
+    const double pr = as_r * at_r - zi * zi, pi = zi * (as_r + at_r);   // a_s a_t
+    const double scale = Om[s] * Om[t] * (Om[s] + Om[t]);
+    const double Fr = (nr * pr + ni * pi) / ((pr * pr + pi * pi) * scale);
+    Phi[(size_t)s * k + t] = Fr * u1[s] * u1[t];
+  }
+  __syncthreads();
+  // X[l][s] = sum_t U[l][t] Phi[t][s] = sum_t V[t][l] Phi[t][s]
+  double *X = a.X + (size_t)b * k * k;
+  for (int idx = tid; idx < n * n; idx += COEF_THREADS) {
+    const int l = idx / n, s = idx % n;
+    double acc = 0.0;
+    for (int t = 0; t < n; ++t) acc = fma(V[(size_t)t * k + l], Phi[(size_t)t * k + s], acc);
+    X[(size_t)l * k + s] = acc;
+  }
+  __syncthreads();
+  // Gam[j][l] = c b0^2 sum_s X[j][s] U[l][s] = c b0^2 sum_s X[j][s] V[s][l]
+  const double g = cw * b0 * b0;
+  for (int idx = tid; idx < k * k; idx += COEF_THREADS) {
+    const int j = idx / k, l = idx % k;
+    double acc = 0.0;
+    if (j < n && l < n)
+      for (int s = 0; s < n; ++s) acc = fma(X[(size_t)j * k + s], V[(size_t)s * k + l], acc);
+    Gm[idx] = g * acc;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Per element of each vector: y = Q a_y and g = diag(Q Gam Q^T) (Gam
+// symmetric: g = sum_j q_j (Gam_jj q_j + 2 sum_{l>j} Gam_jl q_l)).  Block =
+// (ROW_THREADS elements, one vector); the block's basis entries staged in
+// shared memory.
+// --------------------------------------------------------------------------
+constexpr int ROW_THREADS = 32;
+
+__global__ void __launch_bounds__(ROW_THREADS) k_adj_rows(AdjCtx a, const double *basis,
+                                                          double *Y, double *Gd) {
+  extern __shared__ double qs[];   // [k][ROW_THREADS]
+  const int b = blockIdx.y;
+  const int i = blockIdx.x * ROW_THREADS + threadIdx.x;
+  const int k = a.k;
+  const bool ok = i < a.N;
+  const double *Ay = a.ay + (size_t)b * k;
+  const double *Gm = a.Gam + (size_t)b * k * k;
+  double y = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double q = ok ? basis[((size_t)j * a.Bs + b) * a.N + i] : 0.0;
+    qs[j * ROW_THREADS + threadIdx.x] = q;
+    y = fma(Ay[j], q, y);
+  }
+  double g = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double qj = qs[j * ROW_THREADS + threadIdx.x];
+    const double *gr = Gm + (size_t)j * k;
+    double t = 0.0;
+    for (int l = j + 1; l < k; ++l) t = fma(gr[l], qs[l * ROW_THREADS + threadIdx.x], t);
+    g = fma(qj, fma(gr[j], qj, 2.0 * t), g);
+  }
+  if (ok) {
+    Y[(size_t)b * a.N + i] = y;
+    Gd[(size_t)b * a.N + i] = g;
+  }
+}
+
+// R[j*Bs + b][mu] = sum_l Gam_b[j][l] P[l*Bs + b][mu]
+__global__ void k_gamma_p(AdjCtx a, const double *P, int A, double *R) {
+  const int b = blockIdx.y;
+  const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mu >= A) return;
+  const int k = a.k;
+  const double *Gm = a.Gam + (size_t)b * k * k;
+  for (int j = 0; j < k; ++j) {
+    double acc = 0.0;
+    for (int l = 0; l < k; ++l)
+      acc = fma(Gm[(size_t)j * k + l], P[((size_t)l * a.Bs + b) * A + mu], acc);
+    R[((size_t)j * a.Bs + b) * A + mu] = acc;
+  }
+}
+
+// S[i][mu] += sum_r X[r][i] Yr[r][mu]  (FP64, 64 x 64 tiles, r = contraction)
+__global__ void __launch_bounds__(256) k_atb_f64(const double *__restrict__ X, int ldx,
+                                                 const double *__restrict__ Yr, int ldy, int R,
+                                                 int Ni, int Nmu, double *__restrict__ S) {
+  __shared__ double Xs[16][65];
+  __shared__ double Ys[16][65];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int i0 = blockIdx.y * 64, mu0 = blockIdx.x * 64;
+  double acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = 0.0;
+  for (int r0 = 0; r0 < R; r0 += 16) {
+#pragma unroll
+    for (int rep = 0; rep < 4; ++rep) {
+      const int idx = t + 256 * rep;
+      const int rr = idx >> 6, cc = idx & 63;
+      const int r = r0 + rr;
+      Xs[rr][cc] = (r < R && i0 + cc < Ni) ? X[(size_t)r * ldx + i0 + cc] : 0.0;
+      Ys[rr][cc] = (r < R && mu0 + cc < Nmu) ? Yr[(size_t)r * ldy + mu0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) {
+      double xa[4], yb[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) xa[p] = Xs[rr][ty + 16 * p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) yb[q] = Ys[rr][tx + 16 * q];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(xa[p], yb[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int i = i0 + ty + 16 * p;
+    if (i >= Ni) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int mu = mu0 + tx + 16 * q;
+      if (mu < Nmu) S[(size_t)i * Nmu + mu] += acc[p][q];
+    }
+  }
+}
+
+// dDelta[i] += sum_b (2 Delta_i Gd[b][i] + Y[b][i] beta0_b q0_b[i] / (2 Delta_i))
+// (fixed order over b); deps[m] -= dz over the sub-batch (one thread per m).
+__global__ void k_adj_accumulate(AdjCtx a, const double *Delta, const double *basis,
+                                 const double *Y, const double *Gd, double *dDelta,
+                                 double *deps) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.N && Delta[i] > 0.0) {
+    double s = 0.0;
+    for (int b = 0; b < a.nvec; ++b) {
+      const double q0 = basis[(size_t)b * a.N + i];
+      s += 2.0 * Delta[i] * Gd[(size_t)b * a.N + i] +
+           Y[(size_t)b * a.N + i] * a.beta0[a.vec0 + b] * q0 / (2.0 * Delta[i]);
+    }
+    dDelta[i] += s;
+  }
+  if (blockIdx.x == 0) {
+    for (int mi = threadIdx.x; mi < a.n_m; mi += blockDim.x) {
+      double s = 0.0;
+      for (int b = 0; b < a.nvec; ++b)
+        if ((a.vec0 + b) % a.n_m == mi) s += a.dz[b];
+      deps[a.m_idx[mi]] -= s;
+    }
+  }
+}
+
+// dL = D (2 c_K SC + SB) (unpadded output), dDelta += c_K (L o SC) 1 / d.
+// SC [N][A], SB [N][n_aux] or NULL (coupling vectors given directly).
+__global__ void k_adj_dL(const double *L64, const double *dsq, const double *SC,
+                         const double *SB, int A, int n_vc, int n_aux, double kf, double *dL,
+                         double *dDelta) {
+  const int i = blockIdx.x;
+  if (i >= n_vc) return;
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int mu = threadIdx.x; mu < A; mu += blockDim.x) {
+    const double sc = SC[(size_t)i * A + mu];
+    s = fma(L64[(size_t)i * A + mu], sc, s);
+    if (mu < n_aux) {
+      const double sb = SB ? SB[(size_t)i * n_aux + mu] : 0.0;
+      dL[(size_t)i * n_aux + mu] = dsq[i] * (2.0 * kf * sc + sb);
+    }
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0 && dsq[i] > 0.0) dDelta[i] += kf * s / dsq[i];
+}
+
+// deps from dDelta (Delta_vc = eps_c - eps_v) plus the direct dE_t Z_t term.
+__global__ void k_adj_deps(const double *dDelta, int n_v, int n_c, const int *targets, int n_t,
+                           const double *Z, const double *dE, double *deps) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_v + n_c) return;
+  double s = 0.0;
+  if (o < n_v) {
+    for (int c = 0; c < n_c; ++c) s -= dDelta[(size_t)o * n_c + c];
+  } else {
+    const int c = o - n_v;
+    for (int v = 0; v < n_v; ++v) s += dDelta[(size_t)v * n_c + c];
+  }
+  for (int ti = 0; ti < n_t; ++ti)
+    if (targets[ti] == o) s += dE[ti] * Z[ti];
+  deps[o] += s;
+}
+
+// ----------------------------------------------------------------------------
+int adj_max_k() {
+  // k_adj_rows stages k * ROW_THREADS doubles; k_eig_full 4 k per warp
+  return 768;
+}
+
+void launch_eig_full(const AdjCtx &a, cudaStream_t st) {
+  const size_t smem = (size_t)EIG_WARPS * 4 * a.k * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_eig_full, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_eig_full<<<(a.Bs + EIG_WARPS - 1) / EIG_WARPS, EIG_WARPS * 32, smem, st>>>(a);
+}
+void launch_adj_coeffs(const AdjCtx &a, cudaStream_t st) {
+  const size_t smem = (size_t)3 * a.k * sizeof(double);
+  k_adj_coeffs<<<a.Bs, COEF_THREADS, smem, st>>>(a);
+}
+void launch_adj_rows(const AdjCtx &a, const double *basis, double *Y, double *Gd,
+                     cudaStream_t st) {
+  const size_t smem = (size_t)a.k * ROW_THREADS * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_adj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  dim3 grid((a.N + ROW_THREADS - 1) / ROW_THREADS, a.Bs);
+  k_adj_rows<<<grid, ROW_THREADS, smem, st>>>(a, basis, Y, Gd);
+}
+void launch_gamma_p(const AdjCtx &a, const double *P, int A, double *R, cudaStream_t st) {
+  dim3 grid((A + 127) / 128, a.Bs);
+  k_gamma_p<<<grid, 128, 0, st>>>(a, P, A, R);
+}
+void launch_atb_f64(const double *X, int ldx, const double *Yr, int ldy, int R, int Ni, int Nmu,
+                    double *S, cudaStream_t st) {
+  dim3 grid((Nmu + 63) / 64, (Ni + 63) / 64);
+  k_atb_f64<<<grid, 256, 0, st>>>(X, ldx, Yr, ldy, R, Ni, Nmu, S);
+}
+void launch_adj_accumulate(const AdjCtx &a, const double *Delta, const double *basis,
+                           const double *Y, const double *Gd, double *dDelta, double *deps,
+                           cudaStream_t st) {
+  k_adj_accumulate<<<(a.N + 255) / 256, 256, 0, st>>>(a, Delta, basis, Y, Gd, dDelta, deps);
+}
+void launch_adj_dL(const double *L64, const double *dsq, const double *SC, const double *SB,
+                   int A, int n_vc, int n_aux, double kf, double *dL, double *dDelta,
+                   cudaStream_t st) {
+  k_adj_dL<<<n_vc, 256, 0, st>>>(L64, dsq, SC, SB, A, n_vc, n_aux, kf, dL, dDelta);
+}
+void launch_adj_deps(const double *dDelta, int n_v, int n_c, const int *targets, int n_t,
+                     const double *Z, const double *dE, double *deps, cudaStream_t st) {
+  const int n = n_v + n_c;
+  k_adj_deps<<<(n + 127) / 128, 128, 0, st>>>(dDelta, n_v, n_c, targets, n_t, Z, dE, deps);
+}
+
+}  // namespace lgw

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -339,8 +340,14 @@ ProbView check_problem(lgw_handle *h, const SysDev &s, const lgw_problem *p) {
 // Lanczos over all start vectors, sub-batch by sub-batch.
 // alpha/beta [B][k], beta0 [B], k_eff [B] are device arrays.
 // ---------------------------------------------------------------------------
+// keep_basis stores all k + 1 FP64 basis vectors of a sub-batch (slot j of
+// sub-batch row b at basis + (j * Bs + b) * N) whatever the reorthogonalisation
+// mode; after_sub, if given, runs once each sub-batch's recurrence is done.
+using SubBatchHook = std::function<void(const VecCtx &)>;
+
 void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o, double *alpha,
-                 double *beta, double *beta0, int *k_eff, lgw_report *rep, double *tacc) {
+                 double *beta, double *beta0, int *k_eff, lgw_report *rep, double *tacc,
+                 bool keep_basis = false, const SubBatchHook *after_sub = nullptr) {
   cudaStream_t st = h->stream;
   const int B = pv.B;
   const int k = o.k;
@@ -356,8 +363,9 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   const int nchunks = (N + VEC_CHUNK - 1) / VEC_CHUNK;
   const int kmax1 = k + 1;
   const bool reorth = o.reorth != LGW_REORTH_NONE;
-  const bool split = reorth && o.split;
-  const int nslots = (reorth && !split) ? k + 1 : 3;
+  const bool split = reorth && o.split && !keep_basis;
+  const bool full_basis = (reorth && !split) || keep_basis;
+  const int nslots = full_basis ? k + 1 : 3;
 
   VecCtx c{};
   c.N = N;
@@ -366,7 +374,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   c.k = k;
   c.kmax1 = kmax1;
   c.reorth = o.reorth;
-  c.ring = (reorth && !split) ? 0 : 1;
+  c.ring = full_basis ? 0 : 1;
   c.nslots = nslots;
   c.tol = o.tol;
   c.Delta2 = s.Delta2;
@@ -542,6 +550,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
       launch_normalize(c, j, 0, nullptr, st);
       check_launch(h, "normalize");
     }
+    if (after_sub) (*after_sub)(c);
   }
   tm.stop();
   if (rep) {
@@ -1034,10 +1043,160 @@ lgw_status lgw_sigma_c_batched(lgw_handle *h, int32_t n_sys, const lgw_system *c
   return LGW_OK;
 }
 
-lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *, const lgw_problem *,
-                                const lgw_options *, const double *, double *, double *) {
-  if (!h) return LGW_ERR_ARG;
-  return set_err(h, LGW_ERR_UNSUPPORTED, "adjoint path not built in this library version");
+lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                                const lgw_options *o, const double *dE, double *dL,
+                                double *deps) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!sys || sys->h != h || !dE) return set_err(h, LGW_ERR_ARG, "NULL argument to lgw_sigma_c_backward");
+  try {
+    const SysDev &s = sys->s;
+    cudaStream_t st = h->stream;
+    h->timing = false;
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    Opts op = resolve_opts(h, o, s);
+    // the adjoint contracts with the stored FP64 Krylov basis
+    op.split = 0;
+    op.split32 = 0;
+    if (op.k > adj_max_k()) {
+      set_err(h, LGW_ERR_UNSUPPORTED, "k = %d above the %d-step limit of the adjoint", op.k,
+              adj_max_k());
+      throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    ProbView pv = check_problem(h, s, p);
+    const int B = pv.B, k = op.k, N = s.N, A = s.A;
+    const double *d_dE = in_dev(h, "in_dE", dE, (size_t)pv.n_t);
+    OutBuf<double> oL, oe;
+    oL.init(h, "out_dL", dL, (size_t)s.n_vc * s.n_aux);
+    oe.init(h, "out_deps", deps, (size_t)(s.n_v + s.n_c));
+    double *gdeps = wsT<double>(h, "adj_deps", (size_t)(s.n_v + s.n_c));
+    LGW_TRY_CUDA(h, cudaMemsetAsync(gdeps, 0, sizeof(double) * (s.n_v + s.n_c), st));
+    if (B == 0 || pv.n_t == 0) {
+      if (oL.dev) LGW_TRY_CUDA(h, cudaMemsetAsync(oL.dev, 0, sizeof(double) * s.n_vc * s.n_aux, st));
+      if (pv.n_t > 0) {
+        // no summed orbitals: E_t = eps_t + s_t, Z_t = 1
+        std::vector<double> one(pv.n_t, 1.0);
+        double *Z1 = wsT<double>(h, "adj_Z", (size_t)pv.n_t);
+        LGW_TRY_CUDA(h, cudaMemcpyAsync(Z1, one.data(), sizeof(double) * pv.n_t,
+                                        cudaMemcpyHostToDevice, st));
+        double *dD = wsT<double>(h, "adj_dDelta", (size_t)N);
+        LGW_TRY_CUDA(h, cudaMemsetAsync(dD, 0, sizeof(double) * N, st));
+        launch_adj_deps(dD, s.n_v, s.n_c, pv.d_targets, pv.n_t, Z1, d_dE, gdeps, st);
+        check_launch(h, "adj_deps");
+      }
+      if (oe.dev)
+        LGW_TRY_CUDA(h, cudaMemcpyAsync(oe.dev, gdeps, sizeof(double) * (s.n_v + s.n_c),
+                                        cudaMemcpyDeviceToDevice, st));
+      oL.finish(h);
+      oe.finish(h);
+      LGW_TRY_CUDA(h, cudaStreamSynchronize(st));
+      return LGW_OK;
+    }
+    const int bsub = std::min(op.b_sub > 0 ? op.b_sub : std::min(B, 512), B);
+    const bool one_pass = bsub >= B;
+    // coefficients of the forward pass
+    double *alpha = wsT<double>(h, "co_alpha", (size_t)B * k);
+    double *beta = wsT<double>(h, "co_beta", (size_t)B * k);
+    double *beta0 = wsT<double>(h, "co_beta0", (size_t)B);
+    int *ke = wsT<int>(h, "co_keff", (size_t)B);
+    double *E = wsT<double>(h, "adj_E", (size_t)pv.n_t);
+    double *Z = wsT<double>(h, "adj_Z", (size_t)pv.n_t);
+    // accumulators
+    double *SC = wsT<double>(h, "adj_SC", (size_t)N * A);
+    double *SB = pv.d_M ? wsT<double>(h, "adj_SB", (size_t)N * s.n_aux) : nullptr;
+    double *dD = wsT<double>(h, "adj_dDelta", (size_t)N);
+    LGW_TRY_CUDA(h, cudaMemsetAsync(SC, 0, sizeof(double) * N * A, st));
+    if (SB) LGW_TRY_CUDA(h, cudaMemsetAsync(SB, 0, sizeof(double) * N * s.n_aux, st));
+    LGW_TRY_CUDA(h, cudaMemsetAsync(dD, 0, sizeof(double) * N, st));
+
+    auto forward_sigma = [&]() {
+      run_sigma(h, s, pv, op, alpha, beta, beta0, ke, nullptr, E, Z, nullptr, nullptr);
+    };
+    SubBatchHook adjoint = [&](const VecCtx &c) {
+      if (one_pass) forward_sigma();
+      const int Bs = c.Bs;
+      AdjCtx a{};
+      a.N = N;
+      a.Bs = Bs;
+      a.nvec = c.nvec;
+      a.vec0 = c.vec0;
+      a.k = k;
+      a.n_m = pv.n_m;
+      a.n_v = s.n_v;
+      a.alpha = alpha;
+      a.beta = beta;
+      a.beta0 = beta0;
+      a.k_eff = ke;
+      a.E = E;
+      a.Z = Z;
+      a.dE = d_dE;
+      a.eps = s.eps;
+      a.m_idx = pv.d_m_idx;
+      a.delta = pv.delta;
+      const size_t kk = (size_t)k * k;
+      a.theta = wsT<double>(h, "adj_theta", (size_t)Bs * k);
+      a.V = wsT<double>(h, "adj_V", (size_t)Bs * kk);
+      a.Phi = wsT<double>(h, "adj_Phi", (size_t)Bs * kk);
+      a.X = wsT<double>(h, "adj_X", (size_t)Bs * kk);
+      a.ay = wsT<double>(h, "adj_ay", (size_t)Bs * k);
+      a.Gam = wsT<double>(h, "adj_Gam", (size_t)Bs * kk);
+      a.dz = wsT<double>(h, "adj_dz", (size_t)Bs);
+      a.status = h->d_status;
+      launch_eig_full(a, st);
+      check_launch(h, "eig_full");
+      launch_adj_coeffs(a, st);
+      check_launch(h, "adj_coeffs");
+      double *Y = wsT<double>(h, "adj_Y", (size_t)Bs * N);
+      double *Gd = wsT<double>(h, "adj_Gd", (size_t)Bs * N);
+      launch_adj_rows(a, c.basis, Y, Gd, st);
+      check_launch(h, "adj_rows");
+      // P = Q^T D L over the k * Bs basis rows (FP64 GEMM1), R = Gam P
+      const int rows = k * Bs;
+      const int sp = gemm1_f64_splits(s, rows);
+      double *P = wsT<double>(h, "adj_P", (size_t)rows * A);
+      double *Pp = sp > 1 ? wsT<double>(h, "adj_Pp", (size_t)sp * rows * A) : P;
+      launch_gemm1_f64(s, c.basis, rows, Pp, sp, st);
+      check_launch(h, "gemm1_f64(adjoint)");
+      if (sp > 1) {
+        launch_reduce_y_f64(Pp, sp, rows, A, P, st);
+        check_launch(h, "reduce_y_f64(adjoint)");
+      }
+      double *R = wsT<double>(h, "adj_R", (size_t)rows * A);
+      launch_gamma_p(a, P, A, R, st);
+      check_launch(h, "gamma_p");
+      // SC += Q R ; SB += Y^T M
+      launch_atb_f64(c.basis, N, R, A, rows, N, A, SC, st);
+      check_launch(h, "atb_f64(SC)");
+      if (SB) {
+        launch_atb_f64(Y, N, pv.d_M + (size_t)c.vec0 * s.n_aux, s.n_aux, c.nvec, N, s.n_aux, SB,
+                       st);
+        check_launch(h, "atb_f64(SB)");
+      }
+      launch_adj_accumulate(a, s.Delta, c.basis, Y, Gd, dD, gdeps, st);
+      check_launch(h, "adj_accumulate");
+    };
+    if (one_pass) {
+      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, true, &adjoint);
+    } else {
+      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, false, nullptr);
+      forward_sigma();
+      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, true, &adjoint);
+    }
+    double *dLdev = oL.dev ? oL.dev : wsT<double>(h, "adj_dL", (size_t)s.n_vc * s.n_aux);
+    launch_adj_dL(s.L64, s.dsq, SC, SB, A, s.n_vc, s.n_aux, s.kf, dLdev, dD, st);
+    check_launch(h, "adj_dL");
+    launch_adj_deps(dD, s.n_v, s.n_c, pv.d_targets, pv.n_t, Z, d_dE, gdeps, st);
+    check_launch(h, "adj_deps");
+    if (oe.dev)
+      LGW_TRY_CUDA(h, cudaMemcpyAsync(oe.dev, gdeps, sizeof(double) * (s.n_v + s.n_c),
+                                      cudaMemcpyDeviceToDevice, st));
+    oL.finish(h);
+    oe.finish(h);
+    check_status(h);
+  } catch (Fail &f) {
+    return f.st;
+  }
+  return LGW_OK;
 }
 
 }  // extern "C"

@@ -233,4 +233,39 @@ void launch_cf_grid(const CfProblem &p, JacobiBufs jb, double *sigma, cudaStream
 void launch_qp(const CfProblem &p, JacobiBufs jb, const double *sigma, int max_iter, double tol,
                double *e_qp, double *z_qp, unsigned *status, cudaStream_t st);
 
+// k_adjoint.cu : gradient of the QP energies (implicit function + Daleckii-Krein)
+struct AdjCtx {
+  int N, Bs, nvec, vec0, k, n_m, n_v;
+  const double *alpha, *beta, *beta0;   // [B][k], [B][k], [B]
+  const int *k_eff;                     // [B]
+  const double *E, *Z, *dE;             // [n_t]
+  const double *eps;                    // [n_v + n_c]
+  const int *m_idx;                     // [n_m]
+  double delta;
+  double *theta;   // [Bs][k]
+  double *V;       // [Bs][k][k]  V[s][i]: component i of eigenvector s of T_k
+  double *Phi;     // [Bs][k][k]
+  double *X;       // [Bs][k][k]  U Phi
+  double *ay;      // [Bs][k]
+  double *Gam;     // [Bs][k][k]
+  double *dz;      // [Bs]
+  unsigned *status;
+};
+int adj_max_k();
+void launch_eig_full(const AdjCtx &a, cudaStream_t st);
+void launch_adj_coeffs(const AdjCtx &a, cudaStream_t st);
+void launch_adj_rows(const AdjCtx &a, const double *basis, double *Y, double *Gd,
+                     cudaStream_t st);
+void launch_gamma_p(const AdjCtx &a, const double *P, int A, double *R, cudaStream_t st);
+void launch_atb_f64(const double *X, int ldx, const double *Yr, int ldy, int R, int Ni, int Nmu,
+                    double *S, cudaStream_t st);
+void launch_adj_accumulate(const AdjCtx &a, const double *Delta, const double *basis,
+                           const double *Y, const double *Gd, double *dDelta, double *deps,
+                           cudaStream_t st);
+void launch_adj_dL(const double *L64, const double *dsq, const double *SC, const double *SB,
+                   int A, int n_vc, int n_aux, double kf, double *dL, double *dDelta,
+                   cudaStream_t st);
+void launch_adj_deps(const double *dDelta, int n_v, int n_c, const int *targets, int n_t,
+                     const double *Z, const double *dE, double *deps, cudaStream_t st);
+
 }  // namespace lgw

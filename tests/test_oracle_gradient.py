@@ -69,3 +69,43 @@ def test_krylov_gradient_at_full_k_equals_closed_form():
     dL, deps = O.qp_gradient_closed_form(wl, dE)
     np.testing.assert_allclose(dLk, dL, rtol=1e-7, atol=1e-10)
     np.testing.assert_allclose(depsk, deps, rtol=1e-7, atol=1e-10)
+
+
+def test_lanczos_gradient_at_full_k_equals_closed_form():
+    """The oracle's Krylov-form gradient (its own Lanczos basis) reproduces
+    the closed form when k = N_vc."""
+    wl = _wl()
+    rng = np.random.default_rng(6)
+    dE = rng.normal(size=wl.n_t)
+    dLk, depsk = O.qp_gradient_lanczos(wl, dE, k=wl.n_vc)
+    dL, deps = O.qp_gradient_closed_form(wl, dE)
+    np.testing.assert_allclose(dLk, dL, rtol=1e-7, atol=1e-10)
+    np.testing.assert_allclose(depsk, deps, rtol=1e-7, atol=1e-10)
+
+
+def test_lanczos_gradient_truncated_k_tracks_finite_differences():
+    """At truncated k the Krylov-form gradient approximates the derivative
+    of the k-step QP energies; the gap shrinks as k grows and closes at
+    k = N_vc."""
+    wl = _wl()
+    rng = np.random.default_rng(7)
+    dE = rng.normal(size=wl.n_t)
+    PL = rng.normal(size=wl.L.shape)
+    h = 1e-6
+
+    def Ek(w, k):
+        _, poles, _ = O.sigma_lanczos(w, k=k)
+        return O.solve_all_qp(w, poles)[0]
+
+    errs = []
+    for k in (8, 14, wl.n_vc):
+        dLk, _ = O.qp_gradient_lanczos(wl, dE, k=k)
+        wp = gi.Workload(**wl.__dict__)
+        wm = gi.Workload(**wl.__dict__)
+        wp.L = wl.L + h * PL
+        wm.L = wl.L - h * PL
+        fd = (dE @ Ek(wp, k) - dE @ Ek(wm, k)) / (2 * h)
+        errs.append(abs(np.sum(dLk * PL) - fd) / abs(fd))
+    print("relative gap by k:", errs)
+    assert errs[-1] < 1e-6
+    assert errs[1] < errs[0]
