@@ -117,6 +117,18 @@ def mid(seed=1, n_targets=32, k=200, n_freq=1000, target_offset=0):
                          k=k, aux_scaled=True)
 
 
+def differentiation(seed=4, n_targets=8, n_m=128, k=120, n_freq=1000, target_offset=0):
+    """Differentiation workload: N_v=64, N_c=512 (N_vc=32768), N_aux=1024,
+    scaled distributions; 8 targets HOMO-3..LUMO+3, each summing over 128
+    orbitals (64 valence + lowest 64 conduction); k=120.
+    ``n_targets``/``n_m``/``target_offset`` select a subsample."""
+    n_v, n_c, A = 64, 512, 1024
+    all_t = list(range(n_v - 4, n_v + 4))
+    t = all_t[target_offset:target_offset + n_targets]
+    return make_workload("differentiation", n_v, n_c, A, t, list(range(n_m)), n_freq, seed,
+                         k=k, aux_scaled=True)
+
+
 def custom(n_v, n_c, n_aux, n_targets, n_m, n_freq, seed, k, aux_scaled=True):
     """Arbitrary shape with the same recipe: targets straddle the gap,
     the summed set is the lowest ``n_m`` orbitals."""

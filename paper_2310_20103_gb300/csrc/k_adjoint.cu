@@ -14,7 +14,11 @@
 //   dL     = 2 c_K D (G D L) + D (y M^T)
 //   dDelta = 2 Delta diag(G) + c_K diag(L (G D L)^T) / d + y b / (2 Delta)
 // All per-vector weights c_v = dE_t Z_t are folded into a_y, Gam and dz.
-// FP64 throughout.
+// The eigen-decompositions, coefficients and Gam P are FP64.  The large
+// contractions P = Q^T D L and SC = Q R run on the FP64 pipe in the FP64
+// mode and as three split-BF16 tensor-core products (hi hi + hi lo + lo hi,
+// FP64 sums of FP32 chunks) in the BF16 mode, where y and diag(Q Gam Q^T)
+// also move to the FP32 pipe.
 #include "lgw_internal.cuh"
 
 namespace lgw {
@@ -142,6 +146,8 @@ __global__ void __launch_bounds__(COEF_THREADS) k_adj_coeffs(AdjCtx a) {
   if (n <= 0) {
     for (int i = tid; i < k; i += COEF_THREADS) Ay[i] = 0.0;
     for (int i = tid; i < k * k; i += COEF_THREADS) Gm[i] = 0.0;
+    if (a.Gamf)
+      for (int i = tid; i < k * k; i += COEF_THREADS) a.Gamf[(size_t)b * k * k + i] = 0.0f;
     if (tid == 0) a.dz[b] = 0.0;
     return;
   }
@@ -206,6 +212,7 @@ __global__ void __launch_bounds__(COEF_THREADS) k_adj_coeffs(AdjCtx a) {
     if (j < n && l < n)
       for (int s = 0; s < n; ++s) acc = fma(X[(size_t)j * k + s], V[(size_t)s * k + l], acc);
     Gm[idx] = g * acc;
+    if (a.Gamf) a.Gamf[(size_t)b * k * k + idx] = (float)(g * acc);
   }
 }
 
@@ -243,6 +250,76 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rows(AdjCtx a, const double
   if (ok) {
     Y[(size_t)b * a.N + i] = y;
     Gd[(size_t)b * a.N + i] = g;
+  }
+}
+
+// FP32 variant of k_adj_rows (BF16 mode: the gradient there is good to
+// ~1e-4, so y and diag(Q Gam Q^T) run on the FP32 pipe).
+__global__ void __launch_bounds__(ROW_THREADS) k_adj_rows_f32(AdjCtx a, const double *basis,
+                                                              double *Y, double *Gd) {
+  extern __shared__ float qsf[];   // [k][ROW_THREADS]
+  const int b = blockIdx.y;
+  const int i = blockIdx.x * ROW_THREADS + threadIdx.x;
+  const int k = a.k;
+  const bool ok = i < a.N;
+  const double *Ay = a.ay + (size_t)b * k;
+  const float *Gm = a.Gamf + (size_t)b * k * k;
+  float y = 0.0f;
+  for (int j = 0; j < k; ++j) {
+    const float q = ok ? (float)basis[((size_t)j * a.Bs + b) * a.N + i] : 0.0f;
+    qsf[j * ROW_THREADS + threadIdx.x] = q;
+    y = fmaf((float)Ay[j], q, y);
+  }
+  float g = 0.0f;
+  for (int j = 0; j < k; ++j) {
+    const float qj = qsf[j * ROW_THREADS + threadIdx.x];
+    const float *gr = Gm + (size_t)j * k;
+    float t = 0.0f;
+    for (int l = j + 1; l < k; ++l) t = fmaf(gr[l], qsf[l * ROW_THREADS + threadIdx.x], t);
+    g = fmaf(qj, fmaf(gr[j], qj, 2.0f * t), g);
+  }
+  if (ok) {
+    Y[(size_t)b * a.N + i] = (double)y;
+    Gd[(size_t)b * a.N + i] = (double)g;
+  }
+}
+
+// BF16 hi / lo split of a transposed FP64 matrix: src [R][C] (row stride
+// lds) -> hi, lo [C][R]; 32 x 32 shared-memory tiles so both sides coalesce.
+// Either output may be NULL.
+__global__ void k_split_t(const double *__restrict__ src, int R, int C, int lds,
+                          __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+  __shared__ double tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int r = r0 + rr, c = c0 + tx;
+    tile[rr][tx] = (r < R && c < C) ? src[(size_t)r * lds + c] : 0.0;
+  }
+  __syncthreads();
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int c = c0 + cc, r = r0 + tx;
+    if (r < R && c < C) {
+      const double x = tile[tx][cc];
+      const __nv_bfloat16 h = __double2bfloat16(x);
+      if (hi) hi[(size_t)c * R + r] = h;
+      if (lo) lo[(size_t)c * R + r] = __double2bfloat16(x - (double)__bfloat162float(h));
+    }
+  }
+}
+
+// BF16 hi / lo split of scale[c] * src[r][c] (same layout [R][C]).
+__global__ void k_split_scaled(const double *__restrict__ src, int R, int C,
+                               const double *__restrict__ scale, __nv_bfloat16 *__restrict__ hi,
+                               __nv_bfloat16 *__restrict__ lo) {
+  const size_t n = (size_t)R * C;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % C);
+    const double x = scale[c] * src[idx];
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    hi[idx] = h;
+    lo[idx] = __double2bfloat16(x - (double)__bfloat162float(h));
   }
 }
 
@@ -402,6 +479,29 @@ void launch_adj_rows(const AdjCtx &a, const double *basis, double *Y, double *Gd
   }
   dim3 grid((a.N + ROW_THREADS - 1) / ROW_THREADS, a.Bs);
   k_adj_rows<<<grid, ROW_THREADS, smem, st>>>(a, basis, Y, Gd);
+}
+void launch_adj_rows_f32(const AdjCtx &a, const double *basis, double *Y, double *Gd,
+                         cudaStream_t st) {
+  const size_t smem = (size_t)a.k * ROW_THREADS * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_adj_rows_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  dim3 grid((a.N + ROW_THREADS - 1) / ROW_THREADS, a.Bs);
+  k_adj_rows_f32<<<grid, ROW_THREADS, smem, st>>>(a, basis, Y, Gd);
+}
+void launch_split_t(const double *src, int R, int C, int lds, __nv_bfloat16 *hi,
+                    __nv_bfloat16 *lo, cudaStream_t st) {
+  dim3 grid((C + 31) / 32, (R + 31) / 32);
+  k_split_t<<<grid, 256, 0, st>>>(src, R, C, lds, hi, lo);
+}
+void launch_split_scaled(const double *src, int R, int C, const double *scale,
+                         __nv_bfloat16 *hi, __nv_bfloat16 *lo, cudaStream_t st) {
+  const size_t n = (size_t)R * C;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > (size_t)152 * 32) blocks = (size_t)152 * 32;
+  k_split_scaled<<<(unsigned)blocks, 256, 0, st>>>(src, R, C, scale, hi, lo);
 }
 void launch_gamma_p(const AdjCtx &a, const double *P, int A, double *R, cudaStream_t st) {
   dim3 grid((A + 127) / 128, a.Bs);

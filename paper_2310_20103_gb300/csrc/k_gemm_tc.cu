@@ -19,6 +19,7 @@
 // Every mbarrier wait is bounded (clock64); a timeout sets ST_TIMEOUT.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -171,9 +172,13 @@ struct EpiArgs {
   // split-basis epilogue (FP32)
   const float *qh, *qph, *d2f, *cdf;
   float *ucd;
+  // FP64 output (E_F64): out[col * ldo + row] (=, or += when add != 0)
+  double *out;
+  int add;
 };
 
-enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2, E_LANCZOS_NA = 3, E_SPLITB = 4, E_VACC = 5 };
+enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2, E_LANCZOS_NA = 3, E_SPLITB = 4, E_VACC = 5,
+       E_F64 = 6 };
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int ncol0 = n_tile * BN;
     double d2 = 0.0, cdr = 0.0;
     float d2f = 0.f, cdf = 0.f;
-    if (EPI != E_SPLITK && EPI != E_SPLITB && row < M) {
+    if (EPI != E_SPLITK && EPI != E_SPLITB && EPI != E_VACC && EPI != E_F64 && row < M) {
       d2 = ea.Delta2[row];
       cdr = ea.cd[row];
     }
@@ -280,6 +285,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int i = 0; i < 32; ++i) {
           const int col = ncol0 + c0 + i;
           if (col < Ncols && row < M) out[(size_t)col * ea.ldo + row] = __uint_as_float(r[i]);
+        }
+      } else if (EPI == E_F64) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = ncol0 + c0 + i;
+          if (col < Ncols && row < M) {
+            double *o = ea.out + (size_t)col * ea.ldo + row;
+            *o = (ea.add ? *o : 0.0) + (double)__uint_as_float(r[i]);
+          }
         }
       } else if (EPI == E_VACC) {
         // FP32 accumulation of split-BF16 partial products (ea.ldo != 0: add)
@@ -414,11 +428,11 @@ bool tc_available() {
 }
 
 static bool encode_2d(CUtensorMap *tm, const void *base, uint64_t inner, uint64_t outer,
-                      uint32_t box_outer) {
+                      uint32_t box_outer, uint64_t row_elems = 0) {
   auto enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {inner * 2};
+  cuuint64_t strides[1] = {(row_elems ? row_elems : inner) * 2};
   cuuint32_t box[2] = {(cuuint32_t)tc::BK, box_outer};
   cuuint32_t es[2] = {1, 1};
   CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
@@ -600,6 +614,40 @@ void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaSt
   ea.status = status;
   const int num_kb = p->A / tc::BK;
   dispatch_bn<tc::E_SPLITB>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+}
+
+// out (=, or += if add) sum_{p < np} A_p B_p^T with A_p [M][K], B_p [Ncols][K]
+// BF16 row-major (K contiguous), FP32 accumulation in tensor memory over
+// K chunks of at most kchunk, each chunk added to the FP64 output.
+// out[col * ldo + row].  K % 8 == 0 (16-byte TMA row stride).
+bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const __nv_bfloat16 *const *B, int M,
+                    int Ncols, int K, int kchunk, double *out, int ldo, int add, unsigned *status,
+                    cudaStream_t st, char *err, size_t errn) {
+  if (K % 8 != 0 || kchunk % tc::BK != 0 || kchunk <= 0) {
+    snprintf(err, errn, "tc_gemm_f64out: K = %d not a multiple of 8 or bad chunk", K);
+    return false;
+  }
+  tc::EpiArgs ea{};
+  ea.out = out;
+  ea.ldo = ldo;
+  ea.status = status;
+  bool first = add == 0;
+  for (int k0 = 0; k0 < K; k0 += kchunk) {
+    const int kc = std::min(kchunk, K - k0);
+    for (int p = 0; p < np; ++p) {
+      CUtensorMap ta, tb;
+      if (!encode_2d(&ta, A[p] + k0, (uint64_t)kc, (uint64_t)M, tc::BM, (uint64_t)K) ||
+          !encode_2d(&tb, B[p] + k0, (uint64_t)kc, (uint64_t)Ncols, 256, (uint64_t)K)) {
+        snprintf(err, errn, "cuTensorMapEncodeTiled failed (tc_gemm_f64out)");
+        return false;
+      }
+      ea.add = first ? 0 : 1;
+      first = false;
+      const int nkb = (kc + tc::BK - 1) / tc::BK;
+      launch_tc<256, tc::E_F64>(ta, tb, M, Ncols, nkb, nkb, 1, ea, st);
+    }
+  }
+  return true;
 }
 
 }  // namespace lgw

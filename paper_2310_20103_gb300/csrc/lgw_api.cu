@@ -35,6 +35,7 @@ struct lgw_handle {
 struct lgw_system {
   lgw_handle *h = nullptr;
   SysDev s{};
+  __nv_bfloat16 *Ltb_lo = nullptr;   // bf16(L - bf16(L))^T [A][N], made on first use
 };
 
 // ---------------------------------------------------------------------------
@@ -807,6 +808,7 @@ lgw_status lgw_release_system(lgw_system *sys) {
                 s.d2f, s.cdf,   s.L64, s.Lb,     s.Ltb, s.Lb_lo};
   for (void *p : ps)
     if (p) cudaFree(p);
+  if (sys->Ltb_lo) cudaFree(sys->Ltb_lo);
   delete sys;
   return LGW_OK;
 }
@@ -1092,8 +1094,29 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
       LGW_TRY_CUDA(h, cudaStreamSynchronize(st));
       return LGW_OK;
     }
-    const int bsub = std::min(op.b_sub > 0 ? op.b_sub : std::min(B, 512), B);
+    const bool tc = op.precision == LGW_BF16;
+    // sub-batch: the caller's b_sub, else as many vectors as fit in half of
+    // the free device memory (plus what the handle already holds)
+    {
+      size_t fr = 0, tot = 0;
+      LGW_TRY_CUDA(h, cudaMemGetInfo(&fr, &tot));
+      size_t held = 0;
+      for (auto &kv : h->bufs) held += kv.second.n;
+      const double per_vec = 8.0 * (k + 1) * N + (tc ? 4.0 * k * N : 0.0) + 20.0 * k * A +
+                             48.0 * N + 40.0 * k * k;
+      const double budget = 0.5 * (double)(fr + held);
+      int fit = (int)std::min<double>(budget / per_vec, 1 << 20);
+      fit = std::max(PAD_VEC, fit / PAD_VEC * PAD_VEC);
+      if (op.b_sub <= 0) op.b_sub = std::min(B, fit);
+    }
+    const int bsub = std::min(op.b_sub, B);
     const bool one_pass = bsub >= B;
+    if (tc && !sys->Ltb_lo) {
+      lgw_system *ms = const_cast<lgw_system *>(sys);
+      LGW_TRY_CUDA(h, cudaMalloc(&ms->Ltb_lo, sizeof(__nv_bfloat16) * (size_t)N * A));
+      launch_split_t(s.L64, N, A, A, nullptr, ms->Ltb_lo, st);
+      check_launch(h, "split_t(L lo)");
+    }
     // coefficients of the forward pass
     double *alpha = wsT<double>(h, "co_alpha", (size_t)B * k);
     double *beta = wsT<double>(h, "co_beta", (size_t)B * k);
@@ -1140,6 +1163,7 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
       a.X = wsT<double>(h, "adj_X", (size_t)Bs * kk);
       a.ay = wsT<double>(h, "adj_ay", (size_t)Bs * k);
       a.Gam = wsT<double>(h, "adj_Gam", (size_t)Bs * kk);
+      a.Gamf = tc ? wsT<float>(h, "adj_Gamf", (size_t)Bs * kk) : nullptr;
       a.dz = wsT<double>(h, "adj_dz", (size_t)Bs);
       a.status = h->d_status;
       launch_eig_full(a, st);
@@ -1148,25 +1172,62 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
       check_launch(h, "adj_coeffs");
       double *Y = wsT<double>(h, "adj_Y", (size_t)Bs * N);
       double *Gd = wsT<double>(h, "adj_Gd", (size_t)Bs * N);
-      launch_adj_rows(a, c.basis, Y, Gd, st);
+      if (tc)
+        launch_adj_rows_f32(a, c.basis, Y, Gd, st);
+      else
+        launch_adj_rows(a, c.basis, Y, Gd, st);
       check_launch(h, "adj_rows");
-      // P = Q^T D L over the k * Bs basis rows (FP64 GEMM1), R = Gam P
       const int rows = k * Bs;
-      const int sp = gemm1_f64_splits(s, rows);
       double *P = wsT<double>(h, "adj_P", (size_t)rows * A);
-      double *Pp = sp > 1 ? wsT<double>(h, "adj_Pp", (size_t)sp * rows * A) : P;
-      launch_gemm1_f64(s, c.basis, rows, Pp, sp, st);
-      check_launch(h, "gemm1_f64(adjoint)");
-      if (sp > 1) {
-        launch_reduce_y_f64(Pp, sp, rows, A, P, st);
-        check_launch(h, "reduce_y_f64(adjoint)");
-      }
       double *R = wsT<double>(h, "adj_R", (size_t)rows * A);
-      launch_gamma_p(a, P, A, R, st);
-      check_launch(h, "gamma_p");
-      // SC += Q R ; SB += Y^T M
-      launch_atb_f64(c.basis, N, R, A, rows, N, A, SC, st);
-      check_launch(h, "atb_f64(SC)");
+      if (tc) {
+        // P = Q^T D L: three split-BF16 products, FP64 sums of 16384-long chunks
+        __nv_bfloat16 *Shi = wsT<__nv_bfloat16>(h, "adj_Shi", (size_t)rows * N);
+        __nv_bfloat16 *Slo = wsT<__nv_bfloat16>(h, "adj_Slo", (size_t)rows * N);
+        __nv_bfloat16 *Rhi = wsT<__nv_bfloat16>(h, "adj_Rhi", (size_t)rows * A);
+        __nv_bfloat16 *Rlo = wsT<__nv_bfloat16>(h, "adj_Rlo", (size_t)rows * A);
+        char err[256];
+        launch_split_scaled(c.basis, rows, N, s.dsq, Shi, Slo, st);
+        check_launch(h, "split_scaled(D Q)");
+        const __nv_bfloat16 *pa[3] = {s.Ltb, s.Ltb, sys->Ltb_lo};
+        const __nv_bfloat16 *pb[3] = {Shi, Slo, Shi};
+        if (!tc_gemm_f64out(3, pa, pb, A, rows, N, 16384, P, A, 0, h->d_status, st, err,
+                            sizeof err)) {
+          set_err(h, LGW_ERR_CUDA, "%s", err);
+          throw Fail{LGW_ERR_CUDA};
+        }
+        check_launch(h, "tc_gemm_f64out(P)");
+        launch_gamma_p(a, P, A, R, st);
+        check_launch(h, "gamma_p");
+        // SC += Q R  (M = N_aux, N = N_vc, K = k Bs, transposed split operands)
+        launch_split_t(R, rows, A, A, Rhi, Rlo, st);
+        check_launch(h, "split_t(R)");
+        launch_split_t(c.basis, rows, N, N, Shi, Slo, st);
+        check_launch(h, "split_t(Q)");
+        const __nv_bfloat16 *qa[3] = {Rhi, Rhi, Rlo};
+        const __nv_bfloat16 *qb[3] = {Shi, Slo, Shi};
+        if (!tc_gemm_f64out(3, qa, qb, A, N, rows, 16384, SC, A, 1, h->d_status, st, err,
+                            sizeof err)) {
+          set_err(h, LGW_ERR_CUDA, "%s", err);
+          throw Fail{LGW_ERR_CUDA};
+        }
+        check_launch(h, "tc_gemm_f64out(SC)");
+      } else {
+        // P = Q^T D L over the k * Bs basis rows (FP64 GEMM1), R = Gam P
+        const int sp = gemm1_f64_splits(s, rows);
+        double *Pp = sp > 1 ? wsT<double>(h, "adj_Pp", (size_t)sp * rows * A) : P;
+        launch_gemm1_f64(s, c.basis, rows, Pp, sp, st);
+        check_launch(h, "gemm1_f64(adjoint)");
+        if (sp > 1) {
+          launch_reduce_y_f64(Pp, sp, rows, A, P, st);
+          check_launch(h, "reduce_y_f64(adjoint)");
+        }
+        launch_gamma_p(a, P, A, R, st);
+        check_launch(h, "gamma_p");
+        launch_atb_f64(c.basis, N, R, A, rows, N, A, SC, st);
+        check_launch(h, "atb_f64(SC)");
+      }
+      // SB += Y^T M
       if (SB) {
         launch_atb_f64(Y, N, pv.d_M + (size_t)c.vec0 * s.n_aux, s.n_aux, c.nvec, N, s.n_aux, SB,
                        st);

@@ -248,10 +248,20 @@ struct AdjCtx {
   double *X;       // [Bs][k][k]  U Phi
   double *ay;      // [Bs][k]
   double *Gam;     // [Bs][k][k]
+  float *Gamf;     // [Bs][k][k] FP32 copy of Gam, or NULL
   double *dz;      // [Bs]
   unsigned *status;
 };
 int adj_max_k();
+bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const __nv_bfloat16 *const *B, int M,
+                    int Ncols, int K, int kchunk, double *out, int ldo, int add, unsigned *status,
+                    cudaStream_t st, char *err, size_t errn);
+void launch_split_t(const double *src, int R, int C, int lds, __nv_bfloat16 *hi,
+                    __nv_bfloat16 *lo, cudaStream_t st);
+void launch_split_scaled(const double *src, int R, int C, const double *scale,
+                         __nv_bfloat16 *hi, __nv_bfloat16 *lo, cudaStream_t st);
+void launch_adj_rows_f32(const AdjCtx &a, const double *basis, double *Y, double *Gd,
+                         cudaStream_t st);
 void launch_eig_full(const AdjCtx &a, cudaStream_t st);
 void launch_adj_coeffs(const AdjCtx &a, cudaStream_t st);
 void launch_adj_rows(const AdjCtx &a, const double *basis, double *Y, double *Gd,
