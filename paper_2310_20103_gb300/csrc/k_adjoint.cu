@@ -109,18 +109,21 @@ __global__ void __launch_bounds__(EIG_WARPS * 32) k_eig_full(AdjCtx a) {
       break;
     }
     if (lo < 0) break;
-    // U <- U R^T, i.e. rows kk, kk+1 of V = U^T rotate by R
-    for (int r = 0; r < ncs; ++r) {
-      const double c = cs[2 * r], s = cs[2 * r + 1];
-      double *v0 = V + (size_t)(lo + r) * k;
-      double *v1 = v0 + k;
-      for (int i = lane; i < n; i += 32) {
-        const double x0 = v0[i], x1 = v1[i];
-        v0[i] = c * x0 + s * x1;
-        v1[i] = -s * x0 + c * x1;
+    // U <- U R^T: the sweep's rotations act on consecutive row pairs of
+    // V = U^T.  Each lane carries its columns through the whole sweep in a
+    // register (one load and one store per rotation, no reload of a row that
+    // the previous rotation wrote).
+    for (int i = lane; i < n; i += 32) {
+      double x = V[(size_t)lo * k + i];
+      for (int r = 0; r < ncs; ++r) {
+        const double c = cs[2 * r], s = cs[2 * r + 1];
+        const double y = V[(size_t)(lo + r + 1) * k + i];
+        V[(size_t)(lo + r) * k + i] = c * x + s * y;
+        x = -s * x + c * y;
       }
-      __syncwarp();
+      V[(size_t)(lo + ncs) * k + i] = x;
     }
+    __syncwarp();
   }
   __syncwarp();
   for (int i = lane; i < k; i += 32) a.theta[(size_t)b * k + i] = (i < n) ? d[i] : 0.0;
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(COEF_THREADS) k_adj_coeffs(AdjCtx a) {
 // --------------------------------------------------------------------------
 constexpr int ROW_THREADS = 32;
 
-__global__ void __launch_bounds__(ROW_THREADS) k_adj_rows(AdjCtx a, const double *basis,
+__global__ void __launch_bounds__(ROW_THREADS) k_adj_rows(AdjCtx a, BasisRef basis,
                                                           double *Y, double *Gd) {
   extern __shared__ double qs[];   // [k][ROW_THREADS]
   const int b = blockIdx.y;
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rows(AdjCtx a, const double
   const double *Gm = a.Gam + (size_t)b * k * k;
   double y = 0.0;
   for (int j = 0; j < k; ++j) {
-    const double q = ok ? basis[((size_t)j * a.Bs + b) * a.N + i] : 0.0;
+    const double q = ok ? basis.at(((size_t)j * a.Bs + b) * a.N + i) : 0.0;
     qs[j * ROW_THREADS + threadIdx.x] = q;
     y = fma(Ay[j], q, y);
   }
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rows(AdjCtx a, const double
 
 // FP32 variant of k_adj_rows (BF16 mode: the gradient there is good to
 // ~1e-4, so y and diag(Q Gam Q^T) run on the FP32 pipe).
-__global__ void __launch_bounds__(ROW_THREADS) k_adj_rows_f32(AdjCtx a, const double *basis,
+__global__ void __launch_bounds__(ROW_THREADS) k_adj_rows_f32(AdjCtx a, BasisRef basis,
                                                               double *Y, double *Gd) {
   extern __shared__ float qsf[];   // [k][ROW_THREADS]
   const int b = blockIdx.y;
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rows_f32(AdjCtx a, const do
   const float *Gm = a.Gamf + (size_t)b * k * k;
   float y = 0.0f;
   for (int j = 0; j < k; ++j) {
-    const float q = ok ? (float)basis[((size_t)j * a.Bs + b) * a.N + i] : 0.0f;
+    const float q = ok ? (float)basis.at(((size_t)j * a.Bs + b) * a.N + i) : 0.0f;
     qsf[j * ROW_THREADS + threadIdx.x] = q;
     y = fmaf((float)Ay[j], q, y);
   }
@@ -287,14 +290,14 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rows_f32(AdjCtx a, const do
 // BF16 hi / lo split of a transposed FP64 matrix: src [R][C] (row stride
 // lds) -> hi, lo [C][R]; 32 x 32 shared-memory tiles so both sides coalesce.
 // Either output may be NULL.
-__global__ void k_split_t(const double *__restrict__ src, int R, int C, int lds,
+__global__ void k_split_t(BasisRef src, int R, int C, int lds,
                           __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
   __shared__ double tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
   for (int rr = ty; rr < 32; rr += 8) {
     const int r = r0 + rr, c = c0 + tx;
-    tile[rr][tx] = (r < R && c < C) ? src[(size_t)r * lds + c] : 0.0;
+    tile[rr][tx] = (r < R && c < C) ? src.at((size_t)r * lds + c) : 0.0;
   }
   __syncthreads();
   for (int cc = ty; cc < 32; cc += 8) {
@@ -309,14 +312,14 @@ __global__ void k_split_t(const double *__restrict__ src, int R, int C, int lds,
 }
 
 // BF16 hi / lo split of scale[c] * src[r][c] (same layout [R][C]).
-__global__ void k_split_scaled(const double *__restrict__ src, int R, int C,
+__global__ void k_split_scaled(BasisRef src, int R, int C,
                                const double *__restrict__ scale, __nv_bfloat16 *__restrict__ hi,
                                __nv_bfloat16 *__restrict__ lo) {
   const size_t n = (size_t)R * C;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(idx % C);
-    const double x = scale[c] * src[idx];
+    const double x = scale[c] * src.at(idx);
     const __nv_bfloat16 h = __double2bfloat16(x);
     hi[idx] = h;
     lo[idx] = __double2bfloat16(x - (double)__bfloat162float(h));
@@ -389,14 +392,14 @@ __global__ void __launch_bounds__(256) k_atb_f64(const double *__restrict__ X, i
 
 // dDelta[i] += sum_b (2 Delta_i Gd[b][i] + Y[b][i] beta0_b q0_b[i] / (2 Delta_i))
 // (fixed order over b); deps[m] -= dz over the sub-batch (one thread per m).
-__global__ void k_adj_accumulate(AdjCtx a, const double *Delta, const double *basis,
+__global__ void k_adj_accumulate(AdjCtx a, const double *Delta, BasisRef basis,
                                  const double *Y, const double *Gd, double *dDelta,
                                  double *deps) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.N && Delta[i] > 0.0) {
     double s = 0.0;
     for (int b = 0; b < a.nvec; ++b) {
-      const double q0 = basis[(size_t)b * a.N + i];
+      const double q0 = basis.at((size_t)b * a.N + i);
       s += 2.0 * Delta[i] * Gd[(size_t)b * a.N + i] +
            Y[(size_t)b * a.N + i] * a.beta0[a.vec0 + b] * q0 / (2.0 * Delta[i]);
     }
@@ -469,8 +472,7 @@ void launch_adj_coeffs(const AdjCtx &a, cudaStream_t st) {
   const size_t smem = (size_t)3 * a.k * sizeof(double);
   k_adj_coeffs<<<a.Bs, COEF_THREADS, smem, st>>>(a);
 }
-void launch_adj_rows(const AdjCtx &a, const double *basis, double *Y, double *Gd,
-                     cudaStream_t st) {
+void launch_adj_rows(const AdjCtx &a, BasisRef basis, double *Y, double *Gd, cudaStream_t st) {
   const size_t smem = (size_t)a.k * ROW_THREADS * sizeof(double);
   static bool attr = false;
   if (!attr) {
@@ -480,7 +482,7 @@ void launch_adj_rows(const AdjCtx &a, const double *basis, double *Y, double *Gd
   dim3 grid((a.N + ROW_THREADS - 1) / ROW_THREADS, a.Bs);
   k_adj_rows<<<grid, ROW_THREADS, smem, st>>>(a, basis, Y, Gd);
 }
-void launch_adj_rows_f32(const AdjCtx &a, const double *basis, double *Y, double *Gd,
+void launch_adj_rows_f32(const AdjCtx &a, BasisRef basis, double *Y, double *Gd,
                          cudaStream_t st) {
   const size_t smem = (size_t)a.k * ROW_THREADS * sizeof(float);
   static bool attr = false;
@@ -491,13 +493,13 @@ void launch_adj_rows_f32(const AdjCtx &a, const double *basis, double *Y, double
   dim3 grid((a.N + ROW_THREADS - 1) / ROW_THREADS, a.Bs);
   k_adj_rows_f32<<<grid, ROW_THREADS, smem, st>>>(a, basis, Y, Gd);
 }
-void launch_split_t(const double *src, int R, int C, int lds, __nv_bfloat16 *hi,
-                    __nv_bfloat16 *lo, cudaStream_t st) {
+void launch_split_t(BasisRef src, int R, int C, int lds, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                    cudaStream_t st) {
   dim3 grid((C + 31) / 32, (R + 31) / 32);
   k_split_t<<<grid, 256, 0, st>>>(src, R, C, lds, hi, lo);
 }
-void launch_split_scaled(const double *src, int R, int C, const double *scale,
-                         __nv_bfloat16 *hi, __nv_bfloat16 *lo, cudaStream_t st) {
+void launch_split_scaled(BasisRef src, int R, int C, const double *scale, __nv_bfloat16 *hi,
+                         __nv_bfloat16 *lo, cudaStream_t st) {
   const size_t n = (size_t)R * C;
   size_t blocks = (n + 255) / 256;
   if (blocks > (size_t)152 * 32) blocks = (size_t)152 * 32;
@@ -512,7 +514,7 @@ void launch_atb_f64(const double *X, int ldx, const double *Yr, int ldy, int R, 
   dim3 grid((Nmu + 63) / 64, (Ni + 63) / 64);
   k_atb_f64<<<grid, 256, 0, st>>>(X, ldx, Yr, ldy, R, Ni, Nmu, S);
 }
-void launch_adj_accumulate(const AdjCtx &a, const double *Delta, const double *basis,
+void launch_adj_accumulate(const AdjCtx &a, const double *Delta, BasisRef basis,
                            const double *Y, const double *Gd, double *dDelta, double *deps,
                            cudaStream_t st) {
   k_adj_accumulate<<<(a.N + 255) / 256, 256, 0, st>>>(a, Delta, basis, Y, Gd, dDelta, deps);

@@ -364,8 +364,8 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   const int nchunks = (N + VEC_CHUNK - 1) / VEC_CHUNK;
   const int kmax1 = k + 1;
   const bool reorth = o.reorth != LGW_REORTH_NONE;
-  const bool split = reorth && o.split && !keep_basis;
-  const bool full_basis = (reorth && !split) || keep_basis;
+  const bool split = reorth && o.split;
+  const bool full_basis = !split && (reorth || keep_basis);
   const int nslots = full_basis ? k + 1 : 3;
 
   VecCtx c{};
@@ -1057,9 +1057,13 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
     h->timing = false;
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     Opts op = resolve_opts(h, o, s);
-    // the adjoint contracts with the stored FP64 Krylov basis
-    op.split = 0;
-    op.split32 = 0;
+    // the adjoint contracts with the stored Krylov basis: FP64 (FP64 mode)
+    // or the split float pair (BF16 mode with split arithmetic); the split
+    // basis needs reorthogonalisation (otherwise the FP64 basis is kept)
+    if (op.reorth == LGW_REORTH_NONE || op.precision == LGW_FP64) {
+      op.split = 0;
+      op.split32 = 0;
+    }
     if (op.k > adj_max_k()) {
       set_err(h, LGW_ERR_UNSUPPORTED, "k = %d above the %d-step limit of the adjoint", op.k,
               adj_max_k());
@@ -1114,7 +1118,7 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
     if (tc && !sys->Ltb_lo) {
       lgw_system *ms = const_cast<lgw_system *>(sys);
       LGW_TRY_CUDA(h, cudaMalloc(&ms->Ltb_lo, sizeof(__nv_bfloat16) * (size_t)N * A));
-      launch_split_t(s.L64, N, A, A, nullptr, ms->Ltb_lo, st);
+      launch_split_t(BasisRef{s.L64, nullptr, nullptr}, N, A, A, nullptr, ms->Ltb_lo, st);
       check_launch(h, "split_t(L lo)");
     }
     // coefficients of the forward pass
@@ -1138,6 +1142,8 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
     SubBatchHook adjoint = [&](const VecCtx &c) {
       if (one_pass) forward_sigma();
       const int Bs = c.Bs;
+      const BasisRef qb = op.split ? BasisRef{nullptr, c.bhi, c.blo}
+                                   : BasisRef{c.basis, nullptr, nullptr};
       AdjCtx a{};
       a.N = N;
       a.Bs = Bs;
@@ -1173,9 +1179,9 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
       double *Y = wsT<double>(h, "adj_Y", (size_t)Bs * N);
       double *Gd = wsT<double>(h, "adj_Gd", (size_t)Bs * N);
       if (tc)
-        launch_adj_rows_f32(a, c.basis, Y, Gd, st);
+        launch_adj_rows_f32(a, qb, Y, Gd, st);
       else
-        launch_adj_rows(a, c.basis, Y, Gd, st);
+        launch_adj_rows(a, qb, Y, Gd, st);
       check_launch(h, "adj_rows");
       const int rows = k * Bs;
       double *P = wsT<double>(h, "adj_P", (size_t)rows * A);
@@ -1187,7 +1193,7 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
         __nv_bfloat16 *Rhi = wsT<__nv_bfloat16>(h, "adj_Rhi", (size_t)rows * A);
         __nv_bfloat16 *Rlo = wsT<__nv_bfloat16>(h, "adj_Rlo", (size_t)rows * A);
         char err[256];
-        launch_split_scaled(c.basis, rows, N, s.dsq, Shi, Slo, st);
+        launch_split_scaled(qb, rows, N, s.dsq, Shi, Slo, st);
         check_launch(h, "split_scaled(D Q)");
         const __nv_bfloat16 *pa[3] = {s.Ltb, s.Ltb, sys->Ltb_lo};
         const __nv_bfloat16 *pb[3] = {Shi, Slo, Shi};
@@ -1200,9 +1206,9 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
         launch_gamma_p(a, P, A, R, st);
         check_launch(h, "gamma_p");
         // SC += Q R  (M = N_aux, N = N_vc, K = k Bs, transposed split operands)
-        launch_split_t(R, rows, A, A, Rhi, Rlo, st);
+        launch_split_t(BasisRef{R, nullptr, nullptr}, rows, A, A, Rhi, Rlo, st);
         check_launch(h, "split_t(R)");
-        launch_split_t(c.basis, rows, N, N, Shi, Slo, st);
+        launch_split_t(qb, rows, N, N, Shi, Slo, st);
         check_launch(h, "split_t(Q)");
         const __nv_bfloat16 *qa[3] = {Rhi, Rhi, Rlo};
         const __nv_bfloat16 *qb[3] = {Shi, Slo, Shi};
@@ -1233,7 +1239,7 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
                        st);
         check_launch(h, "atb_f64(SB)");
       }
-      launch_adj_accumulate(a, s.Delta, c.basis, Y, Gd, dD, gdeps, st);
+      launch_adj_accumulate(a, s.Delta, qb, Y, Gd, dD, gdeps, st);
       check_launch(h, "adj_accumulate");
     };
     if (one_pass) {

@@ -234,6 +234,15 @@ void launch_qp(const CfProblem &p, JacobiBufs jb, const double *sigma, int max_i
                double *e_qp, double *z_qp, unsigned *status, cudaStream_t st);
 
 // k_adjoint.cu : gradient of the QP energies (implicit function + Daleckii-Krein)
+// A stored Krylov basis [slot][Bs][N]: FP64, or the float pair hi (+ lo).
+struct BasisRef {
+  const double *d;
+  const float *hi, *lo;
+  __device__ __forceinline__ double at(size_t i) const {
+    if (d) return d[i];
+    return lo ? (double)hi[i] + (double)lo[i] : (double)hi[i];
+  }
+};
 struct AdjCtx {
   int N, Bs, nvec, vec0, k, n_m, n_v;
   const double *alpha, *beta, *beta0;   // [B][k], [B][k], [B]
@@ -256,20 +265,19 @@ int adj_max_k();
 bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const __nv_bfloat16 *const *B, int M,
                     int Ncols, int K, int kchunk, double *out, int ldo, int add, unsigned *status,
                     cudaStream_t st, char *err, size_t errn);
-void launch_split_t(const double *src, int R, int C, int lds, __nv_bfloat16 *hi,
-                    __nv_bfloat16 *lo, cudaStream_t st);
-void launch_split_scaled(const double *src, int R, int C, const double *scale,
-                         __nv_bfloat16 *hi, __nv_bfloat16 *lo, cudaStream_t st);
-void launch_adj_rows_f32(const AdjCtx &a, const double *basis, double *Y, double *Gd,
+void launch_split_t(BasisRef src, int R, int C, int lds, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                    cudaStream_t st);
+void launch_split_scaled(BasisRef src, int R, int C, const double *scale, __nv_bfloat16 *hi,
+                         __nv_bfloat16 *lo, cudaStream_t st);
+void launch_adj_rows_f32(const AdjCtx &a, BasisRef basis, double *Y, double *Gd,
                          cudaStream_t st);
 void launch_eig_full(const AdjCtx &a, cudaStream_t st);
 void launch_adj_coeffs(const AdjCtx &a, cudaStream_t st);
-void launch_adj_rows(const AdjCtx &a, const double *basis, double *Y, double *Gd,
-                     cudaStream_t st);
+void launch_adj_rows(const AdjCtx &a, BasisRef basis, double *Y, double *Gd, cudaStream_t st);
 void launch_gamma_p(const AdjCtx &a, const double *P, int A, double *R, cudaStream_t st);
 void launch_atb_f64(const double *X, int ldx, const double *Yr, int ldy, int R, int Ni, int Nmu,
                     double *S, cudaStream_t st);
-void launch_adj_accumulate(const AdjCtx &a, const double *Delta, const double *basis,
+void launch_adj_accumulate(const AdjCtx &a, const double *Delta, BasisRef basis,
                            const double *Y, const double *Gd, double *dDelta, double *deps,
                            cudaStream_t st);
 void launch_adj_dL(const double *L64, const double *dsq, const double *SC, const double *SB,

@@ -155,15 +155,18 @@ def test_bf16_recurrence_gradient(L, handle):
     assert rl <= 1e-3 and re <= 1e-4
 
 
-def test_bf16_adjoint_vs_fp64_differentiation_shapes(L, handle):
+@pytest.mark.parametrize("arith", ["auto", "fp64", "split32"])
+def test_bf16_adjoint_vs_fp64_differentiation_shapes(L, handle, arith):
     """Differentiation shapes (N_vc 32768, N_aux 1024, k 120), 1 target x 32
     summed orbitals: the BF16 mode (BF16 recurrence, split-BF16 tensor-core
     contractions P = Q^T D L and S = Q R, FP32 diagonal) against the FP64
-    mode, 1e-4 relative to the largest entry."""
+    mode, 1e-4 relative to the largest entry.  The stored basis is the
+    48-bit float pair (auto), FP64, or the float-only basis (split32)."""
     wl = gi.differentiation(n_targets=1, n_m=32)
     dE = np.array([1.0])
     g64 = _grad(L, handle, wl, dE, L.Options(k=120, precision="fp64", reorth="cgs2"))
-    g16 = _grad(L, handle, wl, dE, L.Options(k=120, precision="bf16", reorth="cgs2"))
+    g16 = _grad(L, handle, wl, dE, L.Options(k=120, precision="bf16", reorth="cgs2",
+                                             reorth_arith=arith))
     for name, a, b in zip(("dL", "deps"), g16, g64):
         rel = np.abs(a - b).max() / np.abs(b).max()
         print(f"{name}: bf16 vs fp64 max rel {rel:.2e}")
