@@ -354,6 +354,8 @@ def run_gpu(args):
                                          dev)
         if line["fp64_path"].get("value"):
             line["fp64_path"]["mixed_over_fp64"] = value / line["fp64_path"]["value"]
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        line["adjoint"] = adjoint_leg(L, h, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, sps, cores = oracle_sample(n_vec=args.ref_vectors, k=args.k)
         line["cpu_baseline"] = {
@@ -416,6 +418,57 @@ def fp64_compare(args, L, h, sysd, wl, tgt_all, m_idx_d, omega_d, M_all, dev):
             "sigma_max_diff_mev": dsig}
 
 
+def adjoint_leg(L, h, dev):
+    """Differentiation workload (N_v 64, N_c 512, N_aux 1024, 8 targets x 128
+    summed orbitals, k 120): time of the BF16 forward and of the backward
+    (dE/dL, dE/deps), and on one target x 128 orbitals the BF16 gradient
+    against the FP64 gradient (relative to the largest entry)."""
+    import torch
+    import gw_inputs as gi
+
+    def tt(x):
+        return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+    def one(wl, prec, reps):
+        s = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, tt(wl.eps), tt(wl.L))
+        prob = L.Problem(targets=tt(wl.targets), m_idx=tt(wl.m_idx), omega=tt(wl.omega),
+                         delta=wl.delta, M=tt(wl.M))
+        o = L.Options(k=wl.k, precision=prec, reorth="cgs2")
+        sg = torch.empty(wl.n_t, wl.omega.size, 2, dtype=torch.float64, device=dev)
+        e = torch.empty(wl.n_t, dtype=torch.float64, device=dev)
+        dL = torch.empty(wl.n_vc, wl.n_aux, dtype=torch.float64, device=dev)
+        de = torch.empty(wl.n_v + wl.n_c, dtype=torch.float64, device=dev)
+        dE = tt(np.linspace(-1.0, 1.0, wl.n_t))
+        tf, tb = [], []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            L.lgw_sigma_c(h, s, prob, o, sg, e)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            L.lgw_sigma_c_backward(h, s, prob, o, dE, dL, de)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            tf.append(t1 - t0)
+            tb.append(t2 - t1)
+        L.lgw_release_system(s)
+        return min(tf), min(tb), dL.cpu().numpy(), de.cpu().numpy()
+
+    wl = gi.differentiation()
+    f16, b16, _, _ = one(wl, "bf16", 2)
+    sub = gi.differentiation(n_targets=1, n_m=128)
+    _, bs16, dl16, de16 = one(sub, "bf16", 1)
+    f64, b64, dl64, de64 = one(sub, "fp64", 1)
+    return {"workload": "differentiation: N_v 64, N_c 512 (N_vc 32768), N_aux 1024, "
+                        "8 targets x 128 summed orbitals (B 1024), k 120, CGS2, BF16",
+            "forward_s": f16, "backward_s": b16, "backward_over_forward": b16 / f16,
+            "gradient_vs_fp64": {
+                "sample": "1 target x 128 summed orbitals",
+                "dL_rel": float(np.abs(dl16 - dl64).max() / np.abs(dl64).max()),
+                "deps_rel": float(np.abs(de16 - de64).max() / np.abs(de64).max()),
+                "fp64_forward_s": f64, "fp64_backward_s": b64, "bf16_backward_s": bs16}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -432,6 +485,7 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cgs2-step", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
