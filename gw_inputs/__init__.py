@@ -129,6 +129,30 @@ def differentiation(seed=4, n_targets=8, n_m=128, k=120, n_freq=1000, target_off
                          k=k, aux_scaled=True)
 
 
+def batched_uneven(i, k=150, n_freq=1000, max_targets=None, max_m=256):
+    """System i (0..15) of the batched-uneven workload, seed 100+i.  From a
+    generator seeded 100+i the shapes are drawn first: N_vc log-uniform in
+    [4096, 65536], N_v = max(8, round(sqrt(N_vc / 8))), N_c = round(N_vc /
+    N_v), N_aux log-uniform in [512, 2048] rounded to a multiple of 64, and
+    the number of targets uniform in {8..64} (straddling the gap).  The
+    summed orbitals are all valence states plus the lowest conduction states,
+    max_m in total.  Energies, L and M then come from make_workload with the
+    same seed and the 1/sqrt(N_aux)-scaled distributions."""
+    rng = np.random.default_rng(100 + i)
+    n_vc = int(round(np.exp(rng.uniform(np.log(4096), np.log(65536)))))
+    n_v = max(8, int(round(np.sqrt(n_vc / 8))))
+    n_c = max(1, int(round(n_vc / n_v)))
+    A = int(round(np.exp(rng.uniform(np.log(512), np.log(2048))) / 64)) * 64
+    n_t = int(rng.integers(8, 65))
+    if max_targets is not None:
+        n_t = min(n_t, max_targets)
+    t0 = max(0, n_v - n_t // 2)
+    targets = list(range(t0, min(t0 + n_t, n_v + n_c)))
+    m_idx = list(range(min(max_m, n_v + n_c)))
+    return make_workload(f"batched{i}", n_v, n_c, A, targets, m_idx, n_freq, 100 + i, k=k,
+                         aux_scaled=True)
+
+
 def custom(n_v, n_c, n_aux, n_targets, n_m, n_freq, seed, k, aux_scaled=True):
     """Arbitrary shape with the same recipe: targets straddle the gap,
     the summed set is the lowest ``n_m`` orbitals."""

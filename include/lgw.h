@@ -142,7 +142,11 @@ typedef struct {
  *                (0: 1e-13)
  * qp_max_iter    Newton iterations before the bracketing fallback (0: 50)
  * qp_tol         |dE| <= qp_tol * max(1,|E|) ends Newton (0: 1e-10)
- * use_graph      1: capture one Lanczos step as a CUDA graph and replay it
+ * use_graph      1: capture each sub-batch's launch sequence (start vectors
+ *                and the k Lanczos steps) as a CUDA graph on first use and
+ *                replay it from a per-handle cache when the same system,
+ *                shapes, options and buffers come again; the report's
+ *                per-category times are then zero (ms_total stays)
  * reorth_arith   arithmetic of the Gram-Schmidt passes (lgw_reorth_arith) */
 typedef struct {
   int32_t k;

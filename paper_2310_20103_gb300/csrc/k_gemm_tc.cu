@@ -21,6 +21,8 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
+#include <map>
 #include <mutex>
 
 #include "lgw_internal.cuh"
@@ -395,7 +397,8 @@ __global__ void k_reduce_y_bf16(const float *__restrict__ Ypart, int splits, int
 // ---------------------------------------------------------------------------
 struct TcPlan {
   CUtensorMap g1A, g1B, g2A, g2B, g2Alo;
-  int BN;
+  int BN1, BN2;   // N tile of gemm1 / gemm2 (and the coupling products)
+  const __nv_bfloat16 *xh;
   int N, A, Bs;
   int splits, kb_per_split;
   float *ypart;
@@ -469,7 +472,8 @@ TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *
   p->N = s.N;
   p->A = s.A;
   p->Bs = Bs;
-  p->BN = Bs >= 256 ? 256 : (Bs >= 128 ? 128 : 64);
+  p->BN1 = p->BN2 = Bs >= 256 ? 256 : (Bs >= 128 ? 128 : 64);
+  p->xh = xh;
   if (Bs < 64 || s.A < tc::BM || s.N < tc::BM) {
     snprintf(err, errn, "tensor-core plan needs Bs >= 64, N_aux and N_vc padded >= 128");
     delete p;
@@ -480,7 +484,7 @@ TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int num_kb = s.N / tc::BK;
-  const int tiles1 = ((s.A + tc::BM - 1) / tc::BM) * ((Bs + p->BN - 1) / p->BN);
+  const int tiles1 = ((s.A + tc::BM - 1) / tc::BM) * ((Bs + p->BN1 - 1) / p->BN1);
   p->splits = choose_splits(tiles1, num_kb, nsm);
   p->kb_per_split = (num_kb + p->splits - 1) / p->splits;
   p->splits = (num_kb + p->kb_per_split - 1) / p->kb_per_split;
@@ -491,10 +495,10 @@ TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *
   p->d2f = s.d2f;
   p->cdf = s.cdf;
   bool ok = encode_2d(&p->g1A, s.Ltb, (uint64_t)s.N, (uint64_t)s.A, tc::BM) &&
-            encode_2d(&p->g1B, xh, (uint64_t)s.N, (uint64_t)Bs, (uint32_t)p->BN) &&
+            encode_2d(&p->g1B, xh, (uint64_t)s.N, (uint64_t)Bs, (uint32_t)p->BN1) &&
             encode_2d(&p->g2A, s.Lb, (uint64_t)s.A, (uint64_t)s.N, tc::BM) &&
             encode_2d(&p->g2Alo, s.Lb_lo, (uint64_t)s.A, (uint64_t)s.N, tc::BM) &&
-            encode_2d(&p->g2B, yh, (uint64_t)s.A, (uint64_t)Bs, (uint32_t)p->BN);
+            encode_2d(&p->g2B, yh, (uint64_t)s.A, (uint64_t)Bs, (uint32_t)p->BN2);
   if (!ok) {
     snprintf(err, errn, "cuTensorMapEncodeTiled failed");
     delete p;
@@ -538,7 +542,7 @@ void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st) {
   ea.ypart = p->ypart;
   ea.ldo = p->A;
   ea.status = status;
-  dispatch_bn<tc::E_SPLITK>(p->BN, p->g1A, p->g1B, p->A, p->Bs, p->N / tc::BK, p->kb_per_split,
+  dispatch_bn<tc::E_SPLITK>(p->BN1, p->g1A, p->g1B, p->A, p->Bs, p->N / tc::BK, p->kb_per_split,
                             p->splits, ea, st);
 }
 
@@ -563,11 +567,11 @@ void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qp
   ea.status = status;
   const int num_kb = p->A / tc::BK;
   if (epi == EPI_LANCZOS && alpha_part == nullptr)
-    dispatch_bn<tc::E_LANCZOS_NA>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+    dispatch_bn<tc::E_LANCZOS_NA>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
   else if (epi == EPI_LANCZOS)
-    dispatch_bn<tc::E_LANCZOS>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+    dispatch_bn<tc::E_LANCZOS>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
   else
-    dispatch_bn<tc::E_APPLY>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+    dispatch_bn<tc::E_APPLY>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
 }
 
 namespace tc {
@@ -599,11 +603,11 @@ void launch_coupling_tc(const TcPlan *p, const SysDev &s, const double *M, int n
   // L_hi M_hi, then + L_hi M_lo, then + L_lo M_hi
   tc::k_split_m<<<blocks, 256, 0, st>>>(M, nvec, s.n_aux, p->Bs, p->A, 0, p->yh);
   ea.ldo = 0;
-  dispatch_bn<tc::E_VACC>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+  dispatch_bn<tc::E_VACC>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
   ea.ldo = 1;
-  dispatch_bn<tc::E_VACC>(p->BN, p->g2Alo, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+  dispatch_bn<tc::E_VACC>(p->BN2, p->g2Alo, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
   tc::k_split_m<<<blocks, 256, 0, st>>>(M, nvec, s.n_aux, p->Bs, p->A, 1, p->yh);
-  dispatch_bn<tc::E_VACC>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+  dispatch_bn<tc::E_VACC>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
 }
 
 void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaStream_t st) {
@@ -613,7 +617,7 @@ void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaSt
   ea.ucd = ucd;
   ea.status = status;
   const int num_kb = p->A / tc::BK;
-  dispatch_bn<tc::E_SPLITB>(p->BN, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+  dispatch_bn<tc::E_SPLITB>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
 }
 
 // out (=, or += if add) sum_{p < np} A_p B_p^T with A_p [M][K], B_p [Ncols][K]
@@ -648,6 +652,144 @@ bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const __nv_bfloat16 *
     }
   }
   return true;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: the N tile of each contraction and the split count of gemm1 are
+// timed on the plan's own operands (CUDA events, best of 3 after a warm-up)
+// and cached per (device, N, A, Bs).  A candidate replaces the heuristic
+// choice only when it is more than 3% faster.  LGW_AUTOTUNE=0 disables it.
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+  int dev, N, A, Bs;
+  bool operator<(const TuneKey &o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (N != o.N) return N < o.N;
+    if (A != o.A) return A < o.A;
+    return Bs < o.Bs;
+  }
+};
+struct TuneVal {
+  int BN1, splits, BN2;
+};
+std::map<TuneKey, TuneVal> g_tune;
+std::mutex g_tune_mu;
+
+bool plan_encode_b(TcPlan *p) {
+  return encode_2d(&p->g1B, p->xh, (uint64_t)p->N, (uint64_t)p->Bs, (uint32_t)p->BN1) &&
+         encode_2d(&p->g2B, p->yh, (uint64_t)p->A, (uint64_t)p->Bs, (uint32_t)p->BN2);
+}
+
+void plan_set_splits(TcPlan *p, int splits) {
+  const int num_kb = p->N / tc::BK;
+  p->kb_per_split = (num_kb + splits - 1) / splits;
+  p->splits = (num_kb + p->kb_per_split - 1) / p->kb_per_split;
+}
+
+template <class F>
+float time_best(F &&f, cudaStream_t st) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  f();   // warm-up
+  float best = 1e30f;
+  for (int r = 0; r < 3; ++r) {
+    cudaEventRecord(a, st);
+    f();
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+}  // namespace
+
+bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, int *splits_out) {
+  const char *env = getenv("LGW_AUTOTUNE");
+  if (env && env[0] == '0') return true;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const TuneKey key{dev, p->N, p->A, p->Bs};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      p->BN1 = it->second.BN1;
+      p->BN2 = it->second.BN2;
+      plan_set_splits(p, it->second.splits);
+      if (splits_out) *splits_out = p->splits;
+      return plan_encode_b(p);
+    }
+  }
+  int nsm = 148;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int num_kb = p->N / tc::BK;
+  const int bn_max = p->Bs >= 256 ? 256 : (p->Bs >= 128 ? 128 : 64);
+  auto gemm1 = [&]() {
+    launch_gemm1_tc(p, status, st);
+    launch_reduce_y_bf16(p->ypart, p->splits, p->Bs, p->A, p->yh, nullptr, st);
+  };
+  // gemm1: N tile x split count
+  const TuneVal def{p->BN1, p->splits, p->BN2};
+  float t_def = time_best(gemm1, st);
+  TuneVal best = def;
+  float t_best = t_def;
+  for (int bn = 64; bn <= bn_max; bn *= 2) {
+    const int tiles = ((p->A + tc::BM - 1) / tc::BM) * ((p->Bs + bn - 1) / bn);
+    const int s0 = choose_splits(tiles, num_kb, nsm);
+    const int cands[3] = {std::max(1, s0 / 2), s0, std::min(64, 2 * s0)};
+    for (int ci = 0; ci < 3; ++ci) {
+      const int sreq = cands[ci];
+      if (num_kb / sreq < 8 && sreq > 1) continue;
+      p->BN1 = bn;
+      plan_set_splits(p, sreq);
+      if (bn == def.BN1 && p->splits == def.splits) continue;
+      if (!plan_encode_b(p)) return false;
+      const float t = time_best(gemm1, st);
+      if (t < t_best) {
+        t_best = t;
+        best.BN1 = bn;
+        best.splits = p->splits;
+      }
+    }
+  }
+  if (t_best > 0.97f * t_def) {
+    best.BN1 = def.BN1;
+    best.splits = def.splits;
+  }
+  p->BN1 = best.BN1;
+  plan_set_splits(p, best.splits);
+  // gemm2 (store-only epilogue into the caller's scratch): N tile
+  if (ucd != nullptr) {
+    auto gemm2 = [&]() { launch_gemm2_tc_split(p, ucd, status, st); };
+    if (!plan_encode_b(p)) return false;
+    const float t2_def = time_best(gemm2, st);
+    float t2_best = t2_def;
+    for (int bn = 64; bn <= bn_max; bn *= 2) {
+      if (bn == def.BN2) continue;
+      p->BN2 = bn;
+      if (!plan_encode_b(p)) return false;
+      const float t = time_best(gemm2, st);
+      if (t < t2_best) {
+        t2_best = t;
+        best.BN2 = bn;
+      }
+    }
+    if (t2_best > 0.97f * t2_def) best.BN2 = def.BN2;
+    p->BN2 = best.BN2;
+  }
+  if (!plan_encode_b(p)) return false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+  }
+  if (splits_out) *splits_out = p->splits;
+  return cudaGetLastError() == cudaSuccess;
 }
 
 }  // namespace lgw

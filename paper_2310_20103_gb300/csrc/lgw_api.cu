@@ -30,6 +30,20 @@ struct lgw_handle {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   bool timing = false;
+  // captured sub-batch graphs; ws_gen changes whenever a workspace buffer is
+  // (re)allocated, which also drops every cached graph
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+  };
+  std::map<std::string, Graph> graphs;
+  unsigned long long ws_gen = 0;
+  cudaStream_t cap_stream = nullptr;   // private non-blocking stream for captures
+  void drop_graphs() {
+    for (auto &kv : graphs)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    graphs.clear();
+  }
 };
 
 struct lgw_system {
@@ -99,6 +113,8 @@ void *ws(lgw_handle *h, const std::string &name, size_t bytes) {
     }
     b.p = p;
     b.n = bytes;
+    h->ws_gen++;
+    h->drop_graphs();
   }
   return b.p;
 }
@@ -230,6 +246,53 @@ void check_status(lgw_handle *h) {
   }
 }
 
+// Replay the cached graph for `key`, capturing `body` into it first if it
+// is not cached.  A failed capture runs `body` eagerly instead.
+template <class F>
+void run_graphed(lgw_handle *h, const std::string &key, F &&body) {
+  cudaStream_t st = h->stream;
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    if (h->graphs.size() >= 64) h->drop_graphs();
+    // the caller's stream may be the legacy default stream, which cannot be
+    // captured: record the launches on the handle's own stream (the graph is
+    // then launched on the caller's stream, which orders it)
+    if (!h->cap_stream)
+      LGW_TRY_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const int l0 = h->launches;
+    LGW_TRY_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t g = nullptr;
+    h->stream = h->cap_stream;
+    try {
+      body();
+    } catch (Fail &) {
+      h->stream = st;
+      cudaStreamEndCapture(h->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      throw;
+    }
+    h->stream = st;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->launches = l0;
+      body();
+      return;
+    }
+    lgw_handle::Graph gr;
+    gr.exec = ex;
+    gr.launches = h->launches - l0;
+    h->launches = l0;
+    it = h->graphs.emplace(key, gr).first;
+  }
+  LGW_TRY_CUDA(h, cudaGraphLaunch(it->second.exec, st));
+  h->launches += it->second.launches;
+}
+
 struct Opts {
   int k, precision, reorth, b_sub, qp_max_iter, use_graph, split, split32;
   double tol, qp_tol;
@@ -349,7 +412,8 @@ using SubBatchHook = std::function<void(const VecCtx &)>;
 void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o, double *alpha,
                  double *beta, double *beta0, int *k_eff, lgw_report *rep, double *tacc,
                  bool keep_basis = false, const SubBatchHook *after_sub = nullptr) {
-  cudaStream_t st = h->stream;
+  // a reference: a graph capture redirects the launches to the capture stream
+  cudaStream_t &st = h->stream;
   const int B = pv.B;
   const int k = o.k;
   if (B == 0) return;
@@ -436,6 +500,11 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
       set_err(h, LGW_ERR_CUDA, "%s", err);
       throw Fail{LGW_ERR_CUDA};
     }
+    if (!tc_plan_autotune(plan, ucd_buf, h->d_status, st, &splits_tc)) {
+      tc_plan_destroy(plan);
+      set_err(h, LGW_ERR_CUDA, "tensor-core tile autotuning failed");
+      throw Fail{LGW_ERR_CUDA};
+    }
   }
   struct PlanGuard {
     TcPlan *p;
@@ -444,112 +513,135 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
     }
   } guard{plan};
 
+  // use_graph: each sub-batch's launch sequence (start vectors and the k
+  // steps) is captured once and replayed from the handle's graph cache
+  const bool graph_mode = o.use_graph && after_sub == nullptr;
+  const bool timing_saved = h->timing;
+  if (graph_mode) h->timing = false;
+  struct TimingRestore {
+    lgw_handle *h;
+    bool v;
+    ~TimingRestore() { h->timing = v; }
+  } timing_restore{h, timing_saved};
   Timer tm(h);
   int nsub = 0;
   for (int vec0 = 0; vec0 < B; vec0 += nsub_req, ++nsub) {
     const int nvec = std::min(nsub_req, B - vec0);
     c.vec0 = vec0;
     c.nvec = nvec;
-    // ---- start vectors b = Delta^1/2 V, V = L M (text after Eq. 8) ----
-    tm.mark(C_START);
-    if (pv.d_M && tc) {
-      // V = L M on the tensor cores in split BF16 (three products, FP32 sum)
-      float *vf = ucd_buf;
-      launch_coupling_tc(plan, s, pv.d_M + (size_t)vec0 * s.n_aux, nvec, vf, h->d_status, st);
-      check_launch(h, "coupling_tc");
-      launch_start_from_vf(c, vf, st);
-      check_launch(h, "start_from_vf");
-    } else if (pv.d_M) {
-      LGW_TRY_CUDA(h, cudaMemsetAsync(Y64, 0, sizeof(double) * Bs * s.A, st));
-      LGW_TRY_CUDA(h, cudaMemcpy2DAsync(Y64, sizeof(double) * s.A, pv.d_M + (size_t)vec0 * s.n_aux,
-                                        sizeof(double) * s.n_aux, sizeof(double) * s.n_aux, nvec,
-                                        cudaMemcpyDeviceToDevice, st));
-      launch_gemm2_f64(s, Y64, Bs, EPI_START, nullptr, nullptr, nullptr, c.w, nullptr, st);
-      check_launch(h, "gemm2_f64(start)");
-      // padding rows of w (b >= nvec) hold L*0 = 0 already
-      launch_norm_partials(c, c.w, c.norm_a, st);
-      check_launch(h, "norm_partials");
-    } else {
-      launch_start_from_v(c, pv.d_V + (size_t)vec0 * s.n_vc, s.n_vc, s.n_vc, st);
-      check_launch(h, "start_from_v");
-    }
-    if (split)
-      launch_normalize_split(c, 0, 1, st);
-    else
-      launch_normalize(c, 0, 1, nullptr, st);
-    check_launch(h, "normalize(start)");
-
-    for (int j = 0; j < k; ++j) {
-      const double *qj = slot_ptr(c, j);
-      const double *qp = j > 0 ? slot_ptr(c, j - 1) : nullptr;
-      // ---- C q_j through the two contractions (Eq. 4) ----
-      tm.mark(C_GEMM1);
-      if (tc) {
-        launch_gemm1_tc(plan, h->d_status, st);
-        check_launch(h, "gemm1_tc");
-        launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, yy, st);
-        check_launch(h, "reduce_y_bf16");
-        tm.mark(C_GEMM2);
-        if (split)
-          launch_gemm2_tc_split(plan, const_cast<float *>(c.ucd), h->d_status, st);
-        else
-          launch_gemm2_tc(plan, EPI_LANCZOS, qj, qp, c.betaj, c.w, c.alpha_part, h->d_status,
-                          st);
-        check_launch(h, "gemm2_tc");
+    auto sub_body = [&]() {
+      // ---- start vectors b = Delta^1/2 V, V = L M (text after Eq. 8) ----
+      tm.mark(C_START);
+      if (pv.d_M && tc) {
+        // V = L M on the tensor cores in split BF16 (three products, FP32 sum)
+        float *vf = ucd_buf;
+        launch_coupling_tc(plan, s, pv.d_M + (size_t)vec0 * s.n_aux, nvec, vf, h->d_status, st);
+        check_launch(h, "coupling_tc");
+        launch_start_from_vf(c, vf, st);
+        check_launch(h, "start_from_vf");
+      } else if (pv.d_M) {
+        LGW_TRY_CUDA(h, cudaMemsetAsync(Y64, 0, sizeof(double) * Bs * s.A, st));
+        LGW_TRY_CUDA(h, cudaMemcpy2DAsync(Y64, sizeof(double) * s.A, pv.d_M + (size_t)vec0 * s.n_aux,
+                                          sizeof(double) * s.n_aux, sizeof(double) * s.n_aux, nvec,
+                                          cudaMemcpyDeviceToDevice, st));
+        launch_gemm2_f64(s, Y64, Bs, EPI_START, nullptr, nullptr, nullptr, c.w, nullptr, st);
+        check_launch(h, "gemm2_f64(start)");
+        // padding rows of w (b >= nvec) hold L*0 = 0 already
+        launch_norm_partials(c, c.w, c.norm_a, st);
+        check_launch(h, "norm_partials");
       } else {
-        launch_gemm1_f64(s, qj, Bs, Yp64, splits64, st);
-        check_launch(h, "gemm1_f64");
-        launch_reduce_y_f64(Yp64, splits64, Bs, s.A, Y64, st);
-        check_launch(h, "reduce_y_f64");
-        tm.mark(C_GEMM2);
-        launch_gemm2_f64(s, Y64, Bs, EPI_LANCZOS, qj, qp, c.betaj, c.w, c.alpha_part, st);
-        check_launch(h, "gemm2_f64");
+        launch_start_from_v(c, pv.d_V + (size_t)vec0 * s.n_vc, s.n_vc, s.n_vc, st);
+        check_launch(h, "start_from_v");
       }
-      // ---- recurrence and reorthogonalisation ----
-      tm.mark(C_DOTS);
-      if (split) {
-        launch_dots_split(c, j, 1, st);
-        check_launch(h, "dots_split");
-        launch_reduce_dots_split(c, j, 1, st);
-        check_launch(h, "reduce_dots_split");
-        tm.mark(C_UPDATE);
-        launch_update_split(c, j, 1, st);
-        check_launch(h, "update_split");
-        tm.mark(C_PASS2);
-        launch_second_pass_decide_split(c, j, st);
-        check_launch(h, "second_pass_decide_split");
-        launch_dots_split(c, j, 2, st);
-        check_launch(h, "dots_split2");
-        launch_reduce_dots_split(c, j, 2, st);
-        check_launch(h, "reduce_dots_split2");
-        launch_update_split(c, j, 2, st);
-        check_launch(h, "update_split2");
+      if (split)
+        launch_normalize_split(c, 0, 1, st);
+      else
+        launch_normalize(c, 0, 1, nullptr, st);
+      check_launch(h, "normalize(start)");
+
+      for (int j = 0; j < k; ++j) {
+        const double *qj = slot_ptr(c, j);
+        const double *qp = j > 0 ? slot_ptr(c, j - 1) : nullptr;
+        // ---- C q_j through the two contractions (Eq. 4) ----
+        tm.mark(C_GEMM1);
+        if (tc) {
+          launch_gemm1_tc(plan, h->d_status, st);
+          check_launch(h, "gemm1_tc");
+          launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, yy, st);
+          check_launch(h, "reduce_y_bf16");
+          tm.mark(C_GEMM2);
+          if (split)
+            launch_gemm2_tc_split(plan, const_cast<float *>(c.ucd), h->d_status, st);
+          else
+            launch_gemm2_tc(plan, EPI_LANCZOS, qj, qp, c.betaj, c.w, c.alpha_part, h->d_status,
+                            st);
+          check_launch(h, "gemm2_tc");
+        } else {
+          launch_gemm1_f64(s, qj, Bs, Yp64, splits64, st);
+          check_launch(h, "gemm1_f64");
+          launch_reduce_y_f64(Yp64, splits64, Bs, s.A, Y64, st);
+          check_launch(h, "reduce_y_f64");
+          tm.mark(C_GEMM2);
+          launch_gemm2_f64(s, Y64, Bs, EPI_LANCZOS, qj, qp, c.betaj, c.w, c.alpha_part, st);
+          check_launch(h, "gemm2_f64");
+        }
+        // ---- recurrence and reorthogonalisation ----
+        tm.mark(C_DOTS);
+        if (split) {
+          launch_dots_split(c, j, 1, st);
+          check_launch(h, "dots_split");
+          launch_reduce_dots_split(c, j, 1, st);
+          check_launch(h, "reduce_dots_split");
+          tm.mark(C_UPDATE);
+          launch_update_split(c, j, 1, st);
+          check_launch(h, "update_split");
+          tm.mark(C_PASS2);
+          launch_second_pass_decide_split(c, j, st);
+          check_launch(h, "second_pass_decide_split");
+          launch_dots_split(c, j, 2, st);
+          check_launch(h, "dots_split2");
+          launch_reduce_dots_split(c, j, 2, st);
+          check_launch(h, "reduce_dots_split2");
+          launch_update_split(c, j, 2, st);
+          check_launch(h, "update_split2");
+          tm.mark(C_NORM);
+          launch_normalize_split(c, j, 0, st);
+          check_launch(h, "normalize_split");
+          continue;
+        }
+        launch_alpha_axpy(c, j, st);
+        check_launch(h, "alpha_axpy");
+        if (reorth) {
+          launch_reduce_dots(c, j, 1, st);
+          check_launch(h, "reduce_dots");
+          tm.mark(C_UPDATE);
+          launch_update(c, j, 1, st);
+          check_launch(h, "update");
+          tm.mark(C_PASS2);
+          launch_second_pass_decide_j(c, j, st);
+          check_launch(h, "second_pass_decide");
+          launch_dots(c, j, 2, st);
+          check_launch(h, "dots2");
+          launch_reduce_dots(c, j, 2, st);
+          check_launch(h, "reduce_dots2");
+          launch_update(c, j, 2, st);
+          check_launch(h, "update2");
+        }
         tm.mark(C_NORM);
-        launch_normalize_split(c, j, 0, st);
-        check_launch(h, "normalize_split");
-        continue;
+        launch_normalize(c, j, 0, nullptr, st);
+        check_launch(h, "normalize");
       }
-      launch_alpha_axpy(c, j, st);
-      check_launch(h, "alpha_axpy");
-      if (reorth) {
-        launch_reduce_dots(c, j, 1, st);
-        check_launch(h, "reduce_dots");
-        tm.mark(C_UPDATE);
-        launch_update(c, j, 1, st);
-        check_launch(h, "update");
-        tm.mark(C_PASS2);
-        launch_second_pass_decide_j(c, j, st);
-        check_launch(h, "second_pass_decide");
-        launch_dots(c, j, 2, st);
-        check_launch(h, "dots2");
-        launch_reduce_dots(c, j, 2, st);
-        check_launch(h, "reduce_dots2");
-        launch_update(c, j, 2, st);
-        check_launch(h, "update2");
-      }
-      tm.mark(C_NORM);
-      launch_normalize(c, j, 0, nullptr, st);
-      check_launch(h, "normalize");
+    };
+    if (graph_mode) {
+      char key[512];
+      snprintf(key, sizeof key,
+               "s%p B%d n%d v%d k%d p%d r%d sp%d s32%d t%.17g M%p V%p a%p b%p b0%p ke%p g%llu",
+               (const void *)s.L64, Bs, nvec, vec0, k, o.precision, o.reorth, (int)split,
+               o.split32, o.tol, (const void *)pv.d_M, (const void *)pv.d_V, (void *)alpha,
+               (void *)beta, (void *)beta0, (void *)k_eff, h->ws_gen);
+      run_graphed(h, key, sub_body);
+    } else {
+      sub_body();
     }
     if (after_sub) (*after_sub)(c);
   }
@@ -707,6 +799,8 @@ lgw_status lgw_destroy(lgw_handle *h) {
   if (!h) return LGW_OK;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
+  h->drop_graphs();
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto &kv : h->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
@@ -803,6 +897,8 @@ lgw_status lgw_release_system(lgw_system *sys) {
   if (!sys) return LGW_OK;
   cudaSetDevice(sys->h->device);
   cudaStreamSynchronize(sys->h->stream);
+  // cached graphs may reference this system's buffers
+  sys->h->drop_graphs();
   SysDev &s = sys->s;
   void *ps[] = {s.eps,  s.Delta, s.dsq, s.Delta2, s.cd,  s.dsqf,
                 s.d2f, s.cdf,   s.L64, s.Lb,     s.Ltb, s.Lb_lo};

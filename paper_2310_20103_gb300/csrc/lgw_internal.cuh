@@ -165,6 +165,7 @@ void launch_gemm2_f64(const SysDev &s, const double *Y, int Bs, int epi, const d
 // k_gemm_tc.cu : BF16 tcgen05 contractions
 struct TcPlan;
 bool tc_available();
+bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, int *splits_out);
 TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *ypart,
                        __nv_bfloat16 *yh, int *splits_out, char *err, size_t errn);
 void tc_plan_destroy(TcPlan *p);
