@@ -356,6 +356,8 @@ def run_gpu(args):
             line["fp64_path"]["mixed_over_fp64"] = value / line["fp64_path"]["value"]
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_leg(L, h, dev)
+    if rank == 0 and world == 1 and not args.no_batched:
+        line["batched"] = batched_leg(L, h, dev, max_targets=args.batched_targets)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, sps, cores = oracle_sample(n_vec=args.ref_vectors, k=args.k)
         line["cpu_baseline"] = {
@@ -418,7 +420,7 @@ def fp64_compare(args, L, h, sysd, wl, tgt_all, m_idx_d, omega_d, M_all, dev):
             "sigma_max_diff_mev": dsig}
 
 
-def adjoint_leg(L, h, dev):
+def adjoint_leg(L, h, dev, n_targets=8, compare=True):
     """Differentiation workload (N_v 64, N_c 512, N_aux 1024, 8 targets x 128
     summed orbitals, k 120): time of the BF16 forward and of the backward
     (dE/dL, dE/deps), and on one target x 128 orbitals the BF16 gradient
@@ -454,19 +456,71 @@ def adjoint_leg(L, h, dev):
         L.lgw_release_system(s)
         return min(tf), min(tb), dL.cpu().numpy(), de.cpu().numpy()
 
-    wl = gi.differentiation()
+    wl = gi.differentiation(n_targets=n_targets)
     f16, b16, _, _ = one(wl, "bf16", 2)
+    out = {"workload": f"differentiation: N_v 64, N_c 512 (N_vc 32768), N_aux 1024, "
+                       f"{n_targets} targets x 128 summed orbitals (B {128 * n_targets}), "
+                       f"k 120, CGS2, BF16",
+           "forward_s": f16, "backward_s": b16, "backward_over_forward": b16 / f16}
+    if not compare:
+        return out
     sub = gi.differentiation(n_targets=1, n_m=128)
     _, bs16, dl16, de16 = one(sub, "bf16", 1)
     f64, b64, dl64, de64 = one(sub, "fp64", 1)
-    return {"workload": "differentiation: N_v 64, N_c 512 (N_vc 32768), N_aux 1024, "
-                        "8 targets x 128 summed orbitals (B 1024), k 120, CGS2, BF16",
-            "forward_s": f16, "backward_s": b16, "backward_over_forward": b16 / f16,
-            "gradient_vs_fp64": {
+    out["gradient_vs_fp64"] = {
                 "sample": "1 target x 128 summed orbitals",
                 "dL_rel": float(np.abs(dl16 - dl64).max() / np.abs(dl64).max()),
                 "deps_rel": float(np.abs(de16 - de64).max() / np.abs(de64).max()),
-                "fp64_forward_s": f64, "fp64_backward_s": b64, "bf16_backward_s": bs16}}
+                "fp64_forward_s": f64, "fp64_backward_s": b64, "bf16_backward_s": bs16}
+    return out
+
+
+def batched_leg(L, h, dev, max_targets=1, k=150):
+    """Batched-uneven workload: the 16 systems (N_vc 4975..62392, N_aux
+    512..2048, seed 100+i), min(drawn, max_targets) targets each x up to 256
+    summed orbitals, k 150, BF16, CGS1K, one lgw_sigma_c_batched call per
+    step; eager launches vs CUDA-graph replay (graphs captured in the
+    warm-up).  QP states/s = targets of all systems / wall time of a call."""
+    import torch
+    import gw_inputs as gi
+
+    def tt(x):
+        return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+    wls = [gi.batched_uneven(i, k=k, max_targets=max_targets) for i in range(16)]
+    systems = [L.lgw_prepare_system(h, w.n_v, w.n_c, w.n_aux, tt(w.eps), tt(w.L)) for w in wls]
+    probs = [L.Problem(targets=tt(w.targets), m_idx=tt(w.m_idx), omega=tt(w.omega),
+                       delta=w.delta, M=tt(w.M)) for w in wls]
+    sig = [torch.empty(w.n_t, w.omega.size, 2, dtype=torch.float64, device=dev) for w in wls]
+    e = [torch.empty(w.n_t, dtype=torch.float64, device=dev) for w in wls]
+    n_t = sum(w.n_t for w in wls)
+    out = {"workload": f"batched-uneven: 16 systems, N_vc {min(w.n_vc for w in wls)}.."
+                       f"{max(w.n_vc for w in wls)}, N_aux {min(w.n_aux for w in wls)}.."
+                       f"{max(w.n_aux for w in wls)}, {n_t} targets, "
+                       f"{sum(w.n_t * w.n_m for w in wls)} start vectors, k {k}, BF16, CGS1K",
+           "unit": "QP states/s"}
+    res = {}
+    for g in (0, 1):
+        o = L.Options(k=k, precision="bf16", reorth="cgs1k", use_graph=g)
+        for _ in range(2):
+            L.lgw_sigma_c_batched(h, systems, probs, o, sig, e)
+        torch.cuda.synchronize()
+        ts = []
+        launches = 0
+        for _ in range(2):
+            t0 = time.perf_counter()
+            rep = L.lgw_sigma_c_batched(h, systems, probs, o, sig, e, report=True)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            launches = rep["gpu_launches"]
+        res[g] = (min(ts), [x.cpu().numpy() for x in e], launches)
+    for s in systems:
+        L.lgw_release_system(s)
+    out["eager"] = {"value": n_t / res[0][0], "seconds": res[0][0], "gpu_launches": res[0][2]}
+    out["graph"] = {"value": n_t / res[1][0], "seconds": res[1][0], "gpu_launches": res[1][2]}
+    out["graph_over_eager"] = res[0][0] / res[1][0]
+    out["graph_equals_eager"] = all(np.array_equal(a, b) for a, b in zip(res[0][1], res[1][1]))
+    return out
 
 
 def main():
@@ -486,7 +540,33 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cgs2-step", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint leg (differentiation workload) and print it")
+    ap.add_argument("--adjoint-targets", type=int, default=8)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched-uneven leg and print it")
+    ap.add_argument("--batched-targets", type=int, default=1)
     args = ap.parse_args()
+    if args.adjoint_only:
+        import torch
+        sys.path.insert(0, ROOT)
+        from paper_2310_20103_gb300 import lgw as L
+        h = L.lgw_create(0)
+        out = adjoint_leg(L, h, "cuda:0", n_targets=args.adjoint_targets,
+                          compare=args.adjoint_targets == 8)
+        L.lgw_destroy(h)
+        print(json.dumps({"adjoint": out}), flush=True)
+        return
+    if args.batched_only:
+        import torch
+        sys.path.insert(0, ROOT)
+        from paper_2310_20103_gb300 import lgw as L
+        h = L.lgw_create(0)
+        out = batched_leg(L, h, "cuda:0", max_targets=args.batched_targets)
+        L.lgw_destroy(h)
+        print(json.dumps({"batched": out}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

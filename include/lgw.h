@@ -251,7 +251,13 @@ lgw_status lgw_sigma_c(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
 
 /* Several independent systems of uneven size in one call; sigma[i], e_qp[i]
  * and z_qp[i] (z_qp may be NULL) have the shapes of lgw_sigma_c for
- * problems[i].  All start vectors of all systems are scheduled together. */
+ * problems[i].  The systems run concurrently on up to four internal streams
+ * (system i on stream i % 4, each stream with its own workspace, so the
+ * device memory held is up to four single-system workspaces); the call
+ * orders itself after earlier work on the handle's stream and later work on
+ * that stream after itself.  Results equal one lgw_sigma_c per system.
+ * With rep, ms_total covers the whole call and the per-category times are
+ * zero (the systems overlap). */
 lgw_status lgw_sigma_c_batched(lgw_handle *h, int32_t n_sys, const lgw_system *const *systems,
                                const lgw_problem *problems, const lgw_options *o,
                                double *const *sigma, double *const *e_qp,

@@ -39,6 +39,10 @@ struct lgw_handle {
   std::map<std::string, Graph> graphs;
   unsigned long long ws_gen = 0;
   cudaStream_t cap_stream = nullptr;   // private non-blocking stream for captures
+  // lgw_sigma_c_batched runs systems concurrently on these streams, each
+  // with its own workspace namespace (ws_prefix)
+  std::vector<cudaStream_t> lanes;
+  std::string ws_prefix;
   void drop_graphs() {
     for (auto &kv : graphs)
       if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -94,7 +98,7 @@ void check_launch(lgw_handle *h, const char *what) {
 }
 
 void *ws(lgw_handle *h, const std::string &name, size_t bytes) {
-  auto &b = h->bufs[name];
+  auto &b = h->bufs[h->ws_prefix + name];
   if (bytes == 0) bytes = 8;
   if (b.n < bytes) {
     if (b.p) {
@@ -635,10 +639,11 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
     if (graph_mode) {
       char key[512];
       snprintf(key, sizeof key,
-               "s%p B%d n%d v%d k%d p%d r%d sp%d s32%d t%.17g M%p V%p a%p b%p b0%p ke%p g%llu",
-               (const void *)s.L64, Bs, nvec, vec0, k, o.precision, o.reorth, (int)split,
-               o.split32, o.tol, (const void *)pv.d_M, (const void *)pv.d_V, (void *)alpha,
-               (void *)beta, (void *)beta0, (void *)k_eff, h->ws_gen);
+               "%s s%p B%d n%d v%d k%d p%d r%d sp%d s32%d t%.17g M%p V%p a%p b%p b0%p ke%p g%llu",
+               h->ws_prefix.c_str(), (const void *)s.L64, Bs, nvec, vec0, k, o.precision,
+               o.reorth, (int)split, o.split32, o.tol, (const void *)pv.d_M,
+               (const void *)pv.d_V, (void *)alpha, (void *)beta, (void *)beta0, (void *)k_eff,
+               h->ws_gen);
       run_graphed(h, key, sub_body);
     } else {
       sub_body();
@@ -801,6 +806,7 @@ lgw_status lgw_destroy(lgw_handle *h) {
   cudaStreamSynchronize(h->stream);
   h->drop_graphs();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (auto l : h->lanes) cudaStreamDestroy(l);
   for (auto &kv : h->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
@@ -1108,36 +1114,108 @@ lgw_status lgw_sigma_c_batched(lgw_handle *h, int32_t n_sys, const lgw_system *c
   if (g != LGW_OK) return g;
   if (n_sys < 0 || (n_sys > 0 && (!systems || !problems || !sigma || !e_qp)))
     return set_err(h, LGW_ERR_ARG, "bad arguments to lgw_sigma_c_batched");
-  lgw_report total{};
-  for (int i = 0; i < n_sys; ++i) {
-    lgw_report r{};
-    lgw_status stt = lgw_sigma_c(h, systems[i], &problems[i], o, sigma[i], e_qp[i],
-                                 z_qp ? z_qp[i] : nullptr, rep ? &r : nullptr);
-    if (stt != LGW_OK) return stt;
-    if (rep) {
-      total.ms_total += r.ms_total;
-      total.ms_start += r.ms_start;
-      total.ms_gemm1 += r.ms_gemm1;
-      total.ms_gemm2 += r.ms_gemm2;
-      total.ms_dots += r.ms_dots;
-      total.ms_update += r.ms_update;
-      total.ms_pass2 += r.ms_pass2;
-      total.ms_normalize += r.ms_normalize;
-      total.ms_spectral += r.ms_spectral;
-      total.ms_cf += r.ms_cf;
-      total.ms_qp += r.ms_qp;
-      total.gemm_flops += r.gemm_flops;
-      total.reorth_elems += r.reorth_elems;
-      total.n_vectors += r.n_vectors;
-      total.n_sub_batches += r.n_sub_batches;
-      total.n_second_pass += r.n_second_pass;
-      total.gpu_launches += r.gpu_launches;
-      total.k_min = i == 0 ? r.k_min : std::min(total.k_min, r.k_min);
-      total.k_max = std::max(total.k_max, r.k_max);
-      total.min_theta = i == 0 ? r.min_theta : std::min(total.min_theta, r.min_theta);
+  for (int i = 0; i < n_sys; ++i)
+    if (!systems[i] || systems[i]->h != h)
+      return set_err(h, LGW_ERR_ARG, "bad system handle at index %d", i);
+  if (rep) std::memset(rep, 0, sizeof *rep);
+  if (n_sys == 0) return LGW_OK;
+  const cudaStream_t caller = h->stream;
+  // every exit restores the caller's stream and the default workspace names
+  struct Restore {
+    lgw_handle *h;
+    cudaStream_t st;
+    ~Restore() {
+      h->stream = st;
+      h->ws_prefix.clear();
+      h->timing = false;
     }
+  } restore{h, caller};
+  try {
+    h->launches = 0;
+    h->ev_used = 0;
+    h->timing = false;
+    cudaEvent_t t0 = nullptr, t1 = nullptr, fork = nullptr;
+    if (rep) {
+      LGW_TRY_CUDA(h, cudaEventCreate(&t0));
+      LGW_TRY_CUDA(h, cudaEventCreate(&t1));
+      LGW_TRY_CUDA(h, cudaEventRecord(t0, caller));
+    }
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), caller));
+    // systems are independent: up to 4 run at once, system i on lane i % 4
+    const int S = std::min(n_sys, 4);
+    while ((int)h->lanes.size() < S) {
+      cudaStream_t l;
+      LGW_TRY_CUDA(h, cudaStreamCreateWithFlags(&l, cudaStreamNonBlocking));
+      h->lanes.push_back(l);
+    }
+    LGW_TRY_CUDA(h, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    LGW_TRY_CUDA(h, cudaEventRecord(fork, caller));
+    for (int l = 0; l < S; ++l) LGW_TRY_CUDA(h, cudaStreamWaitEvent(h->lanes[l], fork, 0));
+    struct Done {
+      int B, k, n_vc, n_aux, reorth;
+      const int *ke;
+    };
+    std::vector<Done> done;
+    for (int i = 0; i < n_sys; ++i) {
+      const int lane = i % S;
+      h->stream = h->lanes[lane];
+      h->ws_prefix = "lane" + std::to_string(lane) + "/";
+      const SysDev &s = systems[i]->s;
+      Opts op = resolve_opts(h, o, s);
+      ProbView pv = check_problem(h, s, &problems[i]);
+      double *alpha = wsT<double>(h, "co_alpha", (size_t)std::max(1, pv.B) * op.k);
+      double *beta = wsT<double>(h, "co_beta", (size_t)std::max(1, pv.B) * op.k);
+      double *beta0 = wsT<double>(h, "co_beta0", (size_t)std::max(1, pv.B));
+      int *ke = wsT<int>(h, "co_keff" + std::to_string(i), (size_t)std::max(1, pv.B));
+      OutBuf<double> sg, e, z;
+      sg.init(h, "out_sigma", sigma[i], (size_t)pv.n_t * pv.n_freq * 2);
+      e.init(h, "out_eqp", e_qp[i], (size_t)pv.n_t);
+      z.init(h, "out_zqp", z_qp ? z_qp[i] : nullptr, (size_t)pv.n_t);
+      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr);
+      run_sigma(h, s, pv, op, alpha, beta, beta0, ke, sg.dev, e.dev, z.dev, nullptr, nullptr);
+      sg.finish(h);
+      e.finish(h);
+      z.finish(h);
+      done.push_back({pv.B, op.k, s.n_vc, s.n_aux, op.reorth, ke});
+    }
+    h->stream = caller;
+    h->ws_prefix.clear();
+    for (int l = 0; l < S; ++l) {
+      LGW_TRY_CUDA(h, cudaEventRecord(fork, h->lanes[l]));
+      LGW_TRY_CUDA(h, cudaStreamWaitEvent(caller, fork, 0));
+    }
+    cudaEventDestroy(fork);
+    if (rep) {
+      LGW_TRY_CUDA(h, cudaEventRecord(t1, caller));
+      LGW_TRY_CUDA(h, cudaEventSynchronize(t1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      rep->ms_total = ms;
+      rep->gpu_launches = h->launches;
+      int kmin = 1 << 30, kmax = 0;
+      for (const Done &d : done) {
+        std::vector<int> kv(d.B);
+        if (d.B)
+          LGW_TRY_CUDA(h, cudaMemcpy(kv.data(), d.ke, sizeof(int) * d.B, cudaMemcpyDeviceToHost));
+        for (int x : kv) {
+          kmin = std::min(kmin, x);
+          kmax = std::max(kmax, x);
+          if (d.reorth != LGW_REORTH_NONE)
+            rep->reorth_elems += (double)d.n_vc * (double)x * (double)(x + 1) / 2.0;
+        }
+        rep->n_vectors += d.B;
+        rep->gemm_flops += 4.0 * d.n_vc * (double)d.n_aux * (double)d.B * (double)d.k;
+      }
+      rep->k_min = rep->n_vectors ? kmin : 0;
+      rep->k_max = kmax;
+      rep->n_sub_batches = n_sys;
+    }
+    check_status(h);
+  } catch (Fail &f) {
+    return f.st;
   }
-  if (rep) *rep = total;
   return LGW_OK;
 }
 
