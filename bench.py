@@ -256,6 +256,24 @@ def run_gpu(args):
                   "steps": 1, "reorth_arith": "split32 (float-only basis)",
                   "qp_diff_mev_vs_cgs2_split48": float(
                       np.abs(e.cpu().numpy() - e_cgs2).max() * 1e3)}
+    # one step with E4M3 contractions (after one untimed call that makes the
+    # E4M3 copies of L and tunes its tiles), same batch
+    fp8 = None
+    if cgs2 is not None and args.precision == "bf16" and not args.no_fp8_step:
+        o4 = L.Options(k=args.k, precision="fp8", reorth=args.reorth,
+                       b_sub=args.tps * M_PER_TARGET)
+        L.lgw_sigma_c(h, sysd, batch(args.warmup + args.steps), o4, sig, e, z)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r8 = L.lgw_sigma_c(h, sysd, batch(args.warmup + args.steps), o4, sig, e, z, report=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f8ms = e0.elapsed_time(e1)
+        g8 = r8["ms_gemm1"] + r8["ms_gemm2"]
+        fp8 = {"value": tps / (f8ms / 1e3), "unit": "QP states/s", "ms_per_step": f8ms,
+               "steps": 1, "gemm_tflops": r8["gemm_flops"] / (g8 * 1e-3) / 1e12 if g8 else None,
+               "ms_gemm1": r8["ms_gemm1"], "ms_gemm2": r8["ms_gemm2"],
+               "qp_diff_mev_vs_bf16_cgs2": float(np.abs(e.cpu().numpy() - e_cgs2).max() * 1e3)}
     ms_max = R.max_over_ranks(ms, dev) if world > 1 else ms
     states = tps * args.steps * world
     value = states / (ms_max / 1e3)
@@ -348,6 +366,7 @@ def run_gpu(args):
         "n_second_pass": int(agg["n_second_pass"]),
         "cgs2_step": cgs2,
         "float_basis_step": fbasis,
+        "fp8_step": fp8,
     }
     if rank == 0 and world == 1 and not args.no_fp64_compare:
         line["fp64_path"] = fp64_compare(args, L, h, sysd, wl, tgt_all, m_idx_d, omega_d, M_all,
@@ -540,6 +559,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cgs2-step", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-fp8-step", action="store_true")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint leg (differentiation workload) and print it")
     ap.add_argument("--adjoint-targets", type=int, default=8)

@@ -61,10 +61,15 @@ typedef enum {
 
 /* Arithmetic of the two low-rank contractions L^T(Delta^1/2 X) and L Y.
  * Everything else (recurrence, reorthogonalisation, spectral map,
- * continued fractions, QP) is FP64 in both modes. */
+ * continued fractions, QP) is FP64 in every mode.  Start vectors V = L M
+ * are FP64 in the FP64 mode and split BF16 (three products) otherwise. */
 typedef enum {
   LGW_FP64 = 0,   /* FP64 CUDA-core GEMMs: the plain FP64 path            */
-  LGW_BF16 = 1    /* BF16 tcgen05 tensor-core GEMMs, FP32 accumulate      */
+  LGW_BF16 = 1,   /* BF16 tcgen05 tensor-core GEMMs, FP32 accumulate      */
+  LGW_FP8 = 3     /* E4M3 tcgen05 GEMMs (kind::f8f6f4), FP32 accumulate:
+                     L with one power-of-two scale per column (max -> (224,
+                     448]), the per-step operands Delta^1/2 q and y with one
+                     power-of-two scale per vector; 2 is reserved          */
 } lgw_precision;
 
 typedef enum {

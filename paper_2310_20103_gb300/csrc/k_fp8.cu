@@ -1,0 +1,192 @@
+// E4M3 operands of the low-rank Casida matvec.
+//
+// L is stored as L8 = e4m3(L / s_mu) with one power-of-two scale per column
+// mu (s_mu = 2^ceil(log2(max_vc |L[vc][mu]| / 448)), so the largest entry
+// maps into (224, 448] and dequantisation is exact); both row-major copies
+// L8 [N][A] (K = N_aux contiguous, gemm2) and L8t [A][N] (K = N_vc, gemm1).
+// Per Lanczos step:
+//   x8 = e4m3(Delta^1/2 q / s_b)       s_b per vector (k_quant_x8)
+//   Y^T[mu][b] = s_b s_mu sum_vc L8t[mu][vc] x8[b][vc]     (tensor cores)
+//   y'_mu = s_mu y_mu,  y8 = e4m3(y' / t_b)                  (k_reduce_y_fp8)
+//   U[vc][b] = t_b sum_mu L8[vc][mu] y8[b][mu]               (tensor cores)
+// so U = (s L8)(t y8 / s) ~ L y.  The FP64 recurrence is unchanged.
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "lgw_internal.cuh"
+
+namespace lgw {
+
+__device__ __forceinline__ float pow2_scale(float amax) {
+  // smallest power of two s with amax / s <= 448
+  if (!(amax > 0.0f)) return 1.0f;
+  int e;
+  const float m = frexpf(amax / 448.0f, &e);   // amax/448 = m 2^e, m in [0.5, 1)
+  if (m == 0.5f) e -= 1;
+  return ldexpf(1.0f, e);
+}
+
+__device__ __forceinline__ uint8_t to_e4m3(float v) {
+  return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+__device__ __forceinline__ float from_e4m3(uint8_t v) {
+  const __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)v, __NV_E4M3);
+  return __half2float(__half(hr));
+}
+
+// column maxima of |L64| (non-negative floats order like their bit patterns)
+__global__ void k_col_absmax(const double *__restrict__ L64, int N, int A,
+                             unsigned *__restrict__ colmax) {
+  __shared__ float red[8][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int mu = blockIdx.x * 32 + tx;
+  const int r0 = blockIdx.y * 1024;
+  float m = 0.0f;
+  if (mu < A)
+    for (int r = r0 + ty; r < min(N, r0 + 1024); r += 8)
+      m = fmaxf(m, (float)fabs(L64[(size_t)r * A + mu]));
+  red[ty][tx] = m;
+  __syncthreads();
+  if (ty == 0 && mu < A) {
+    for (int i = 1; i < 8; ++i) m = fmaxf(m, red[i][tx]);
+    atomicMax(colmax + mu, __float_as_uint(m));
+  }
+}
+
+__global__ void k_col_scales(const unsigned *__restrict__ colmax, int A, float *__restrict__ sL) {
+  const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mu < A) sL[mu] = pow2_scale(__uint_as_float(colmax[mu]));
+}
+
+// L8 = e4m3(L64 / s_mu) [N][A] and its transpose L8t [A][N] (32 x 32 tiles)
+__global__ void k_quantize_L8(const double *__restrict__ L64, int N, int A,
+                              const float *__restrict__ sL, uint8_t *__restrict__ L8,
+                              uint8_t *__restrict__ L8t) {
+  __shared__ uint8_t tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int r = r0 + rr, c = c0 + tx;
+    uint8_t v = 0;
+    if (r < N && c < A) {
+      v = to_e4m3((float)(L64[(size_t)r * A + c] / (double)sL[c]));
+      L8[(size_t)r * A + c] = v;
+    }
+    tile[rr][tx] = v;
+  }
+  __syncthreads();
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int c = c0 + cc, r = r0 + tx;
+    if (r < N && c < A) L8t[(size_t)c * N + r] = tile[tx][cc];
+  }
+}
+
+// x8[b] = e4m3(xh[b] / s_b), s_b from max |xh[b]|; one block per vector.
+__global__ void __launch_bounds__(256) k_quant_x8(const __nv_bfloat16 *__restrict__ xh, int N,
+                                                  uint8_t *__restrict__ x8,
+                                                  float *__restrict__ sx) {
+  __shared__ float red[8];
+  __shared__ float sc;
+  const int b = blockIdx.x;
+  const __nv_bfloat16 *x = xh + (size_t)b * N;
+  uint8_t *o = x8 + (size_t)b * N;
+  float m = 0.0f;
+  for (int i = threadIdx.x; i < N; i += 256) m = fmaxf(m, fabsf(__bfloat162float(x[i])));
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, s));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t = fmaxf(t, red[w]);
+    sc = pow2_scale(t);
+    sx[b] = sc;
+  }
+  __syncthreads();
+  const float inv = 1.0f / sc;   // a power of two: exact
+  for (int i = threadIdx.x; i < N; i += 256) o[i] = to_e4m3(__bfloat162float(x[i]) * inv);
+}
+
+// From the split-K partials of gemm1: y_mu = s_b s_mu sum_p Ypart, then
+// y8 = e4m3(s_mu y_mu / t_b) with t_b from the vector's max; yy[b] (slot 0
+// of n_yb) = sum_mu y_mu yhat_mu with yhat = t_b y8 / s_mu, the y that gemm2
+// effectively multiplies (for the alpha estimate).  One block per vector;
+// dynamic shared memory A floats.
+__global__ void __launch_bounds__(256) k_reduce_y_fp8(const float *__restrict__ Ypart, int splits,
+                                                      int Bs, int A, const float *__restrict__ sx,
+                                                      const float *__restrict__ sL,
+                                                      uint8_t *__restrict__ y8,
+                                                      float *__restrict__ ty,
+                                                      float *__restrict__ yy, int n_yb) {
+  extern __shared__ float yp[];   // [A]: s_mu y_mu
+  __shared__ float red[8];
+  __shared__ float sc;
+  const int b = blockIdx.x;
+  const size_t n = (size_t)Bs * A;
+  float m = 0.0f;
+  for (int mu = threadIdx.x; mu < A; mu += 256) {
+    float s = 0.0f;
+    for (int p = 0; p < splits; ++p) s += Ypart[(size_t)p * n + (size_t)b * A + mu];
+    const float v = sL[mu] * (sx[b] * sL[mu] * s);
+    yp[mu] = v;
+    m = fmaxf(m, fabsf(v));
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, s));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t = fmaxf(t, red[w]);
+    sc = pow2_scale(t);
+    ty[b] = sc;
+  }
+  __syncthreads();
+  const float t = sc, inv = 1.0f / sc;
+  float acc = 0.0f;
+  for (int mu = threadIdx.x; mu < A; mu += 256) {
+    const uint8_t q = to_e4m3(yp[mu] * inv);
+    y8[(size_t)b * A + mu] = q;
+    const float yv = yp[mu] / sL[mu];            // y_mu (exact: s_mu is a power of two)
+    acc = fmaf(yv, t * from_e4m3(q) / sL[mu], acc);
+  }
+  if (yy != nullptr) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float tot = 0.0f;
+      for (int w = 0; w < 8; ++w) tot += red[w];
+      yy[(size_t)b * n_yb] = tot;
+      for (int i = 1; i < n_yb; ++i) yy[(size_t)b * n_yb + i] = 0.0f;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+void launch_prepare_fp8(const SysDev &s, unsigned *colmax, uint8_t *L8, uint8_t *L8t, float *sL,
+                        cudaStream_t st) {
+  cudaMemsetAsync(colmax, 0, sizeof(unsigned) * s.A, st);
+  k_col_absmax<<<dim3((s.A + 31) / 32, (s.N + 1023) / 1024), 256, 0, st>>>(s.L64, s.N, s.A,
+                                                                          colmax);
+  k_col_scales<<<(s.A + 255) / 256, 256, 0, st>>>(colmax, s.A, sL);
+  k_quantize_L8<<<dim3((s.A + 31) / 32, (s.N + 31) / 32), 256, 0, st>>>(s.L64, s.N, s.A, sL, L8,
+                                                                        L8t);
+}
+
+void launch_quant_x8(const __nv_bfloat16 *xh, int Bs, int N, uint8_t *x8, float *sx,
+                     cudaStream_t st) {
+  k_quant_x8<<<Bs, 256, 0, st>>>(xh, N, x8, sx);
+}
+
+void launch_reduce_y_fp8(const float *Ypart, int splits, int Bs, int A, const float *sx,
+                         const float *sL, uint8_t *y8, float *ty, float *yy, int n_yb,
+                         cudaStream_t st) {
+  k_reduce_y_fp8<<<Bs, 256, (size_t)A * sizeof(float), st>>>(Ypart, splits, Bs, A, sx, sL, y8, ty,
+                                                             yy, n_yb);
+}
+
+}  // namespace lgw

@@ -121,6 +121,16 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// D[tmem] (+)= A * B^T, M=128, N=BN, K=32 (E4M3 x E4M3, FP32 accumulator)
+__device__ __forceinline__ void umma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // Arrive on an mbarrier once every MMA issued so far by this thread is done.
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile(
@@ -161,6 +171,11 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
+// Instruction descriptor, kind::f8f6f4: FP32 accumulator, A and B E4M3
+// (format code 0), both K-major.
+__host__ __device__ constexpr uint32_t make_idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 struct EpiArgs {
   // gemm1 (split-K partials)
@@ -177,12 +192,16 @@ struct EpiArgs {
   // FP64 output (E_F64): out[col * ldo + row] (=, or += when add != 0)
   double *out;
   int add;
+  // per-column (vector) scale of the accumulator (FP8 operands), or NULL
+  const float *colscale;
 };
 
 enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2, E_LANCZOS_NA = 3, E_SPLITB = 4, E_VACC = 5,
        E_F64 = 6 };
 
-template <int BN, int EPI>
+// EB: operand element bytes, 2 = BF16 (kind::f16, K block 64), 1 = E4M3
+// (kind::f8f6f4, K block 128); a K block is one 128-byte swizzle row either way.
+template <int BN, int EPI, int EB>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               int M, int Ncols, int num_kb, int kb_per_split, EpiArgs ea) {
@@ -231,7 +250,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(&empty[s], ph ^ 1, ea.status)) break;
         mbar_expect_tx(&full[s], C::STAGE);
         uint8_t *sa = smem + s * C::STAGE;
-        const int kx = (kb0 + (it + m_tile) % nk) * BK;
+        const int kx = (kb0 + (it + m_tile) % nk) * (BK * 2 / EB);
         tma_load_2d(sa, &tmA, &full[s], kx, m_tile * BM);
         tma_load_2d(sa + C::A_BYTES, &tmB, &full[s], kx, n_tile * BN);
         issued = it + 1;
@@ -242,7 +261,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = make_idesc(BM, BN);
+      constexpr uint32_t idesc = EB == 2 ? make_idesc(BM, BN) : make_idesc_e4m3(BM, BN);
       for (int it = 0; it < nk; ++it) {
         const int s = it % C::STAGES;
         const uint32_t ph = (it / C::STAGES) & 1;
@@ -252,7 +271,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint64_t da = make_sdesc(sa), db = make_sdesc(sa + C::A_BYTES);
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk)
-          umma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          if (EB == 2)
+            umma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          else
+            umma_e4m3(tmem, da + 2 * kk, db + 2 * kk, idesc, (it > 0 || kk > 0) ? 1u : 0u);
         umma_commit(&empty[s]);
       }
       umma_commit(tfull);
@@ -314,7 +336,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int col = ncol0 + c0 + i;
-          if (col < Ncols && row < M) ea.ucd[(size_t)col * ea.N + row] = cdf * __uint_as_float(r[i]);
+          if (col < Ncols && row < M) {
+            const float cs = ea.colscale ? ea.colscale[col] : 1.0f;
+            ea.ucd[(size_t)col * ea.N + row] = cdf * (cs * __uint_as_float(r[i]));
+          }
         }
       } else {
         double acc[32];
@@ -324,7 +349,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           acc[i] = 0.0;
           if (col < Ncols && row < M) {
             const size_t o = (size_t)col * ea.N + row;
-            const double u = (double)__uint_as_float(r[i]);
+            const double u = (double)__uint_as_float(r[i]) *
+                             (ea.colscale ? (double)ea.colscale[col] : 1.0);
             const double qv = ea.q[o];
             double wv = fma(d2, qv, cdr * u);
             if ((EPI == E_LANCZOS || EPI == E_LANCZOS_NA) && ea.qprev != nullptr)
@@ -397,6 +423,11 @@ __global__ void k_reduce_y_bf16(const float *__restrict__ Ypart, int splits, int
 // ---------------------------------------------------------------------------
 struct TcPlan {
   CUtensorMap g1A, g1B, g2A, g2B, g2Alo;
+  // E4M3 operands (fp8 plans): L8t / x8 for gemm1, L8 / y8 for gemm2
+  CUtensorMap f1A, f1B, f2A, f2B;
+  bool fp8 = false;
+  const uint8_t *x8 = nullptr, *y8 = nullptr;
+  const float *ty = nullptr;   // per-vector scale of y8 (gemm2 column scale)
   int BN1, BN2;   // N tile of gemm1 / gemm2 (and the coupling products)
   const __nv_bfloat16 *xh;
   int N, A, Bs;
@@ -430,15 +461,19 @@ bool tc_available() {
   return major == 10 && minor == 3 && get_encode() != nullptr;
 }
 
+// 2-D K-major tensor map: inner (K) extent, outer rows, a box of one
+// 128-byte swizzle row (64 BF16 or 128 E4M3 elements) by box_outer rows.
 static bool encode_2d(CUtensorMap *tm, const void *base, uint64_t inner, uint64_t outer,
-                      uint32_t box_outer, uint64_t row_elems = 0) {
+                      uint32_t box_outer, uint64_t row_elems = 0, int elem_bytes = 2) {
   auto enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {(row_elems ? row_elems : inner) * 2};
-  cuuint32_t box[2] = {(cuuint32_t)tc::BK, box_outer};
+  cuuint64_t strides[1] = {(row_elems ? row_elems : inner) * (uint64_t)elem_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), box_outer};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+  CUresult r = enc(tm,
+                   elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                   2, const_cast<void *>(base), dims, strides,
                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -510,31 +545,31 @@ TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *
 
 void tc_plan_destroy(TcPlan *p) { delete p; }
 
-template <int BN, int EPI>
+template <int BN, int EPI, int EB = 2>
 static void launch_tc(const CUtensorMap &A, const CUtensorMap &B, int M, int Ncols, int num_kb,
                       int kb_per_split, int splits, const tc::EpiArgs &ea, cudaStream_t st) {
   using C = tc::Cfg<BN>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(tc::k_gemm_tc<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(tc::k_gemm_tc<BN, EPI, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          C::SMEM);
     attr_done = true;
   }
   dim3 grid((M + tc::BM - 1) / tc::BM, (Ncols + BN - 1) / BN, splits);
-  tc::k_gemm_tc<BN, EPI><<<grid, tc::NTHREADS, C::SMEM, st>>>(A, B, M, Ncols, num_kb, kb_per_split,
-                                                              ea);
+  tc::k_gemm_tc<BN, EPI, EB><<<grid, tc::NTHREADS, C::SMEM, st>>>(A, B, M, Ncols, num_kb,
+                                                                  kb_per_split, ea);
 }
 
-template <int EPI>
+template <int EPI, int EB = 2>
 static void dispatch_bn(int BN, const CUtensorMap &A, const CUtensorMap &B, int M, int Ncols,
                         int num_kb, int kb_per_split, int splits, const tc::EpiArgs &ea,
                         cudaStream_t st) {
   if (BN == 256)
-    launch_tc<256, EPI>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
+    launch_tc<256, EPI, EB>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
   else if (BN == 128)
-    launch_tc<128, EPI>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
+    launch_tc<128, EPI, EB>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
   else
-    launch_tc<64, EPI>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
+    launch_tc<64, EPI, EB>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
 }
 
 void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st) {
@@ -542,6 +577,14 @@ void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st) {
   ea.ypart = p->ypart;
   ea.ldo = p->A;
   ea.status = status;
+  if (p->fp8) {
+    // same split count; K blocks of 128 elements
+    const int nkb = p->N / 128;
+    const int per = (nkb + p->splits - 1) / p->splits;
+    dispatch_bn<tc::E_SPLITK, 1>(p->BN1, p->f1A, p->f1B, p->A, p->Bs, nkb, per, p->splits, ea,
+                                 st);
+    return;
+  }
   dispatch_bn<tc::E_SPLITK>(p->BN1, p->g1A, p->g1B, p->A, p->Bs, p->N / tc::BK, p->kb_per_split,
                             p->splits, ea, st);
 }
@@ -565,6 +608,17 @@ void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qp
   ea.w = w;
   ea.alpha_part = alpha_part;
   ea.status = status;
+  if (p->fp8) {
+    ea.colscale = p->ty;
+    const int nkb = p->A / 128;
+    if (epi == EPI_LANCZOS && alpha_part == nullptr)
+      dispatch_bn<tc::E_LANCZOS_NA, 1>(p->BN2, p->f2A, p->f2B, p->N, p->Bs, nkb, nkb, 1, ea, st);
+    else if (epi == EPI_LANCZOS)
+      dispatch_bn<tc::E_LANCZOS, 1>(p->BN2, p->f2A, p->f2B, p->N, p->Bs, nkb, nkb, 1, ea, st);
+    else
+      dispatch_bn<tc::E_APPLY, 1>(p->BN2, p->f2A, p->f2B, p->N, p->Bs, nkb, nkb, 1, ea, st);
+    return;
+  }
   const int num_kb = p->A / tc::BK;
   if (epi == EPI_LANCZOS && alpha_part == nullptr)
     dispatch_bn<tc::E_LANCZOS_NA>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
@@ -616,6 +670,12 @@ void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaSt
   ea.cdf = p->cdf;
   ea.ucd = ucd;
   ea.status = status;
+  if (p->fp8) {
+    ea.colscale = p->ty;
+    const int nkb = p->A / 128;
+    dispatch_bn<tc::E_SPLITB, 1>(p->BN2, p->f2A, p->f2B, p->N, p->Bs, nkb, nkb, 1, ea, st);
+    return;
+  }
   const int num_kb = p->A / tc::BK;
   dispatch_bn<tc::E_SPLITB>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
 }
@@ -662,8 +722,9 @@ bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const __nv_bfloat16 *
 // ---------------------------------------------------------------------------
 namespace {
 struct TuneKey {
-  int dev, N, A, Bs;
+  int dev, N, A, Bs, fp8;
   bool operator<(const TuneKey &o) const {
+    if (fp8 != o.fp8) return fp8 < o.fp8;
     if (dev != o.dev) return dev < o.dev;
     if (N != o.N) return N < o.N;
     if (A != o.A) return A < o.A;
@@ -677,8 +738,12 @@ std::map<TuneKey, TuneVal> g_tune;
 std::mutex g_tune_mu;
 
 bool plan_encode_b(TcPlan *p) {
-  return encode_2d(&p->g1B, p->xh, (uint64_t)p->N, (uint64_t)p->Bs, (uint32_t)p->BN1) &&
-         encode_2d(&p->g2B, p->yh, (uint64_t)p->A, (uint64_t)p->Bs, (uint32_t)p->BN2);
+  bool ok = encode_2d(&p->g1B, p->xh, (uint64_t)p->N, (uint64_t)p->Bs, (uint32_t)p->BN1) &&
+            encode_2d(&p->g2B, p->yh, (uint64_t)p->A, (uint64_t)p->Bs, (uint32_t)p->BN2);
+  if (ok && p->fp8)
+    ok = encode_2d(&p->f1B, p->x8, (uint64_t)p->N, (uint64_t)p->Bs, (uint32_t)p->BN1, 0, 1) &&
+         encode_2d(&p->f2B, p->y8, (uint64_t)p->A, (uint64_t)p->Bs, (uint32_t)p->BN2, 0, 1);
+  return ok;
 }
 
 void plan_set_splits(TcPlan *p, int splits) {
@@ -714,7 +779,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
   if (env && env[0] == '0') return true;
   int dev = 0;
   cudaGetDevice(&dev);
-  const TuneKey key{dev, p->N, p->A, p->Bs};
+  const TuneKey key{dev, p->N, p->A, p->Bs, p->fp8 ? 1 : 0};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -790,6 +855,19 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
   }
   if (splits_out) *splits_out = p->splits;
   return cudaGetLastError() == cudaSuccess;
+}
+
+// Switch a plan to E4M3 operands: L8t [A][N] and x8 [Bs][N] for gemm1, L8
+// [N][A] and y8 [Bs][A] for gemm2 (ty: per-vector scale of y8).
+bool tc_plan_enable_fp8(TcPlan *p, const uint8_t *L8t, const uint8_t *L8, const uint8_t *x8,
+                        const uint8_t *y8, const float *ty) {
+  p->fp8 = true;
+  p->x8 = x8;
+  p->y8 = y8;
+  p->ty = ty;
+  return encode_2d(&p->f1A, L8t, (uint64_t)p->N, (uint64_t)p->A, tc::BM, 0, 1) &&
+         encode_2d(&p->f2A, L8, (uint64_t)p->A, (uint64_t)p->N, tc::BM, 0, 1) &&
+         plan_encode_b(p);
 }
 
 }  // namespace lgw

@@ -319,7 +319,7 @@ Opts resolve_opts(lgw_handle *h, const lgw_options *o, const SysDev &s) {
     throw Fail{LGW_ERR_ARG};
   }
   r.split = o->reorth_arith == LGW_RA_SPLIT || o->reorth_arith == LGW_RA_SPLIT32 ||
-            (o->reorth_arith == LGW_RA_AUTO && o->precision == LGW_BF16);
+            (o->reorth_arith == LGW_RA_AUTO && o->precision != LGW_FP64);
   r.split32 = o->reorth_arith == LGW_RA_SPLIT32;
   r.tol = o->breakdown_tol > 0 ? o->breakdown_tol : 1e-13;
   r.qp_tol = o->qp_tol > 0 ? o->qp_tol : 1e-10;
@@ -331,7 +331,7 @@ Opts resolve_opts(lgw_handle *h, const lgw_options *o, const SysDev &s) {
     set_err(h, LGW_ERR_UNSUPPORTED, "k = %d above the 4095-step limit of this build", r.k);
     throw Fail{LGW_ERR_UNSUPPORTED};
   }
-  if (r.precision != LGW_FP64 && r.precision != LGW_BF16) {
+  if (r.precision != LGW_FP64 && r.precision != LGW_BF16 && r.precision != LGW_FP8) {
     set_err(h, LGW_ERR_ARG, "unknown precision %d", r.precision);
     throw Fail{LGW_ERR_ARG};
   }
@@ -343,11 +343,36 @@ Opts resolve_opts(lgw_handle *h, const lgw_options *o, const SysDev &s) {
     set_err(h, LGW_ERR_ARG, "b_sub < 0");
     throw Fail{LGW_ERR_ARG};
   }
-  if (r.precision == LGW_BF16 && !tc_available()) {
-    set_err(h, LGW_ERR_UNSUPPORTED, "BF16 tensor-core path needs an sm_103 device");
+  if (r.precision != LGW_FP64 && !tc_available()) {
+    set_err(h, LGW_ERR_UNSUPPORTED, "tensor-core paths need an sm_103 device");
     throw Fail{LGW_ERR_UNSUPPORTED};
   }
   return r;
+}
+
+// The E4M3 copies of L are made on the first FP8 request for a system.
+void ensure_fp8(lgw_handle *h, const lgw_system *csys, const Opts &o) {
+  if (o.precision != LGW_FP8 || csys->s.L8) return;
+  lgw_system *sys = const_cast<lgw_system *>(csys);
+  SysDev &s = sys->s;
+  const size_t n = (size_t)s.N * s.A;
+  uint8_t *a = nullptr, *b = nullptr;
+  float *sc = nullptr;
+  if (cudaMalloc(&a, n) != cudaSuccess || cudaMalloc(&b, n) != cudaSuccess ||
+      cudaMalloc(&sc, sizeof(float) * s.A) != cudaSuccess) {
+    cudaGetLastError();
+    if (a) cudaFree(a);
+    if (b) cudaFree(b);
+    if (sc) cudaFree(sc);
+    set_err(h, LGW_ERR_OOM, "device allocation for the E4M3 copies of L failed");
+    throw Fail{LGW_ERR_OOM};
+  }
+  unsigned *colmax = wsT<unsigned>(h, "fp8_colmax", (size_t)s.A);
+  launch_prepare_fp8(s, colmax, a, b, sc, h->stream);
+  check_launch(h, "prepare_fp8");
+  s.L8 = a;
+  s.L8t = b;
+  s.sL = sc;
 }
 
 struct ProbView {
@@ -423,7 +448,8 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   if (B == 0) return;
   LGW_TRY_CUDA(h, cudaMemsetAsync(alpha, 0, sizeof(double) * B * k, st));
   LGW_TRY_CUDA(h, cudaMemsetAsync(beta, 0, sizeof(double) * B * k, st));
-  const bool tc = o.precision == LGW_BF16;
+  const bool tc = o.precision != LGW_FP64;
+  const bool fp8 = o.precision == LGW_FP8;
   int nsub_req = o.b_sub > 0 ? o.b_sub : std::min(B, 512);
   nsub_req = std::min(nsub_req, B);
   int Bs = round_up(nsub_req, PAD_VEC);
@@ -491,6 +517,8 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   const int splits64 = gemm1_f64_splits(s, Bs);
   double *Yp64 = tc ? nullptr : wsT<double>(h, "yp64", (size_t)splits64 * Bs * s.A);
   TcPlan *plan = nullptr;
+  uint8_t *x8 = nullptr, *y8 = nullptr;
+  float *sx = nullptr, *ty = nullptr;
   float *Yp32 = nullptr;
   __nv_bfloat16 *Yh = nullptr;
   int splits_tc = 1;
@@ -503,6 +531,17 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
     if (!plan) {
       set_err(h, LGW_ERR_CUDA, "%s", err);
       throw Fail{LGW_ERR_CUDA};
+    }
+    if (fp8) {
+      x8 = wsT<uint8_t>(h, "x8", (size_t)Bs * N);
+      y8 = wsT<uint8_t>(h, "y8", (size_t)Bs * s.A);
+      sx = wsT<float>(h, "sx", (size_t)Bs);
+      ty = wsT<float>(h, "ty", (size_t)Bs);
+      if (!tc_plan_enable_fp8(plan, s.L8t, s.L8, x8, y8, ty)) {
+        tc_plan_destroy(plan);
+        set_err(h, LGW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the E4M3 operands");
+        throw Fail{LGW_ERR_CUDA};
+      }
     }
     if (!tc_plan_autotune(plan, ucd_buf, h->d_status, st, &splits_tc)) {
       tc_plan_destroy(plan);
@@ -569,10 +608,17 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
         // ---- C q_j through the two contractions (Eq. 4) ----
         tm.mark(C_GEMM1);
         if (tc) {
+          if (fp8) {
+            launch_quant_x8(c.xh, Bs, N, x8, sx, st);
+            check_launch(h, "quant_x8");
+          }
           launch_gemm1_tc(plan, h->d_status, st);
           check_launch(h, "gemm1_tc");
-          launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, yy, st);
-          check_launch(h, "reduce_y_bf16");
+          if (fp8)
+            launch_reduce_y_fp8(Yp32, splits_tc, Bs, s.A, sx, s.sL, y8, ty, yy, c.n_yb, st);
+          else
+            launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, yy, st);
+          check_launch(h, "reduce_y");
           tm.mark(C_GEMM2);
           if (split)
             launch_gemm2_tc_split(plan, const_cast<float *>(c.ucd), h->d_status, st);
@@ -911,6 +957,9 @@ lgw_status lgw_release_system(lgw_system *sys) {
   for (void *p : ps)
     if (p) cudaFree(p);
   if (sys->Ltb_lo) cudaFree(sys->Ltb_lo);
+  if (s.L8) cudaFree(s.L8);
+  if (s.L8t) cudaFree(s.L8t);
+  if (s.sL) cudaFree(s.sL);
   delete sys;
   return LGW_OK;
 }
@@ -922,14 +971,21 @@ lgw_status lgw_apply_casida(lgw_handle *h, const lgw_system *sys, int32_t n_vec,
   if (!sys || sys->h != h || n_vec < 0 || (n_vec > 0 && (!X || !Y)))
     return set_err(h, LGW_ERR_ARG, "bad arguments to lgw_apply_casida");
   if (n_vec == 0) return LGW_OK;
-  if (precision != LGW_FP64 && precision != LGW_BF16) return set_err(h, LGW_ERR_ARG, "bad precision");
+  if (precision != LGW_FP64 && precision != LGW_BF16 && precision != LGW_FP8)
+    return set_err(h, LGW_ERR_ARG, "bad precision");
   try {
     const SysDev &s = sys->s;
     cudaStream_t st = h->stream;
-    const bool tc = precision == LGW_BF16;
+    const bool tc = precision != LGW_FP64;
+    const bool fp8 = precision == LGW_FP8;
     if (tc && !tc_available()) {
-      set_err(h, LGW_ERR_UNSUPPORTED, "BF16 tensor-core path needs an sm_103 device");
+      set_err(h, LGW_ERR_UNSUPPORTED, "tensor-core paths need an sm_103 device");
       throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    if (fp8) {
+      Opts o8{};
+      o8.precision = LGW_FP8;
+      ensure_fp8(h, sys, o8);
     }
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     const double *Xd = in_dev(h, "ap_xin", X, (size_t)n_vec * s.n_vc);
@@ -956,10 +1012,28 @@ lgw_status lgw_apply_casida(lgw_handle *h, const lgw_system *sys, int32_t n_vec,
         set_err(h, LGW_ERR_CUDA, "%s", err);
         throw Fail{LGW_ERR_CUDA};
       }
+      uint8_t *x8 = nullptr, *y8 = nullptr;
+      float *sx = nullptr, *ty = nullptr;
+      if (fp8) {
+        x8 = wsT<uint8_t>(h, "ap_x8", (size_t)Bs * s.N);
+        y8 = wsT<uint8_t>(h, "ap_y8", (size_t)Bs * s.A);
+        sx = wsT<float>(h, "ap_sx", (size_t)Bs);
+        ty = wsT<float>(h, "ap_ty", (size_t)Bs);
+        if (!tc_plan_enable_fp8(plan, s.L8t, s.L8, x8, y8, ty)) {
+          tc_plan_destroy(plan);
+          set_err(h, LGW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the E4M3 operands");
+          throw Fail{LGW_ERR_CUDA};
+        }
+        launch_quant_x8(xh, Bs, s.N, x8, sx, st);
+        check_launch(h, "quant_x8");
+      }
       launch_gemm1_tc(plan, h->d_status, st);
       check_launch(h, "gemm1_tc");
-      launch_reduce_y_bf16(yp, splits, Bs, s.A, yh, nullptr, st);
-      check_launch(h, "reduce_y_bf16");
+      if (fp8)
+        launch_reduce_y_fp8(yp, splits, Bs, s.A, sx, s.sL, y8, ty, nullptr, 1, st);
+      else
+        launch_reduce_y_bf16(yp, splits, Bs, s.A, yh, nullptr, st);
+      check_launch(h, "reduce_y");
       launch_gemm2_tc(plan, EPI_APPLY, xp, nullptr, nullptr, wp, nullptr, h->d_status, st);
       check_launch(h, "gemm2_tc");
       LGW_TRY_CUDA(h, cudaStreamSynchronize(st));
@@ -996,6 +1070,7 @@ lgw_status lgw_lanczos_coeffs(lgw_handle *h, const lgw_system *sys, const lgw_pr
     cudaStream_t st = h->stream;
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     Opts op = resolve_opts(h, o, s);
+    ensure_fp8(h, sys, op);
     ProbView pv = check_problem(h, s, p);
     OutBuf<double> a, b, b0;
     OutBuf<int32_t> ke;
@@ -1071,6 +1146,7 @@ lgw_status lgw_sigma_c(lgw_handle *h, const lgw_system *sys, const lgw_problem *
     }
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     Opts op = resolve_opts(h, o, s);
+    ensure_fp8(h, sys, op);
     ProbView pv = check_problem(h, s, p);
     double tacc[C_N] = {0};
     double *alpha = wsT<double>(h, "co_alpha", (size_t)std::max(1, pv.B) * op.k);
@@ -1162,6 +1238,7 @@ lgw_status lgw_sigma_c_batched(lgw_handle *h, int32_t n_sys, const lgw_system *c
       h->ws_prefix = "lane" + std::to_string(lane) + "/";
       const SysDev &s = systems[i]->s;
       Opts op = resolve_opts(h, o, s);
+      ensure_fp8(h, systems[i], op);
       ProbView pv = check_problem(h, s, &problems[i]);
       double *alpha = wsT<double>(h, "co_alpha", (size_t)std::max(1, pv.B) * op.k);
       double *beta = wsT<double>(h, "co_beta", (size_t)std::max(1, pv.B) * op.k);
@@ -1231,6 +1308,7 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
     h->timing = false;
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     Opts op = resolve_opts(h, o, s);
+    ensure_fp8(h, sys, op);
     // the adjoint contracts with the stored Krylov basis: FP64 (FP64 mode)
     // or the split float pair (BF16 mode with split arithmetic); the split
     // basis needs reorthogonalisation (otherwise the FP64 basis is kept)
@@ -1272,7 +1350,7 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
       LGW_TRY_CUDA(h, cudaStreamSynchronize(st));
       return LGW_OK;
     }
-    const bool tc = op.precision == LGW_BF16;
+    const bool tc = op.precision != LGW_FP64;
     // sub-batch: the caller's b_sub, else as many vectors as fit in half of
     // the free device memory (plus what the handle already holds)
     {

@@ -52,6 +52,10 @@ struct SysDev {
   __nv_bfloat16 *Lb;    // [N][A]   K-major operand of the L Y contraction
   __nv_bfloat16 *Ltb;   // [A][N]   K-major operand of the L^T X contraction
   __nv_bfloat16 *Lb_lo; // [N][A]   bf16(L - bf16(L)): second half of a split-BF16 L
+  // E4M3 copies with power-of-two column scales, made on the first FP8 call
+  uint8_t *L8;      // [N][A]   e4m3(L / s_mu)
+  uint8_t *L8t;     // [A][N]   its transpose
+  float *sL;        // [A]      s_mu
 };
 
 // ---------------------------------------------------------------------------
@@ -165,6 +169,15 @@ void launch_gemm2_f64(const SysDev &s, const double *Y, int Bs, int epi, const d
 // k_gemm_tc.cu : BF16 tcgen05 contractions
 struct TcPlan;
 bool tc_available();
+bool tc_plan_enable_fp8(TcPlan *p, const uint8_t *L8t, const uint8_t *L8, const uint8_t *x8,
+                        const uint8_t *y8, const float *ty);
+void launch_prepare_fp8(const SysDev &s, unsigned *colmax, uint8_t *L8, uint8_t *L8t, float *sL,
+                        cudaStream_t st);
+void launch_quant_x8(const __nv_bfloat16 *xh, int Bs, int N, uint8_t *x8, float *sx,
+                     cudaStream_t st);
+void launch_reduce_y_fp8(const float *Ypart, int splits, int Bs, int A, const float *sx,
+                         const float *sL, uint8_t *y8, float *ty, float *yy, int n_yb,
+                         cudaStream_t st);
 bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, int *splits_out);
 TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *ypart,
                        __nv_bfloat16 *yh, int *splits_out, char *err, size_t errn);
