@@ -542,6 +542,67 @@ def batched_leg(L, h, dev, max_targets=1, k=150):
     return out
 
 
+def large_leg(L, dev, n_targets=2, k=300):
+    """Large cluster-sized system (N_vc 1.6M, N_aux 8192), n_targets x 1024
+    summed orbitals in one sub-batch, k 300 without reorthogonalisation,
+    2000 frequencies: QP states/s with E4M3 and with BF16 contractions, and
+    the E4M3-vs-BF16 differences of E_qp and Sigma in meV.  L (105 GB FP64)
+    is drawn on the device; the system keeps the BF16 and E4M3 copies only
+    (LGW_SYS_NO_FP64), so the FP64 copy is freed before the runs."""
+    import torch
+    import gw_inputs as gi
+
+    def tt(x):
+        return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+    wl, sigma_L = gi.large_cluster(n_targets=n_targets, k=k)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    Ld = torch.randn(wl.n_v * wl.n_c, wl.n_aux, dtype=torch.float64, device=dev, generator=g)
+    Ld.mul_(sigma_L)
+    h = L.lgw_create(0)
+    t0 = time.perf_counter()
+    s = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, tt(wl.eps), Ld,
+                             flags=L.SYS_NO_FP64 | L.SYS_FP8)
+    torch.cuda.synchronize()
+    t_prep = time.perf_counter() - t0
+    del Ld
+    torch.cuda.empty_cache()
+    prob = L.Problem(targets=tt(wl.targets), m_idx=tt(wl.m_idx), omega=tt(wl.omega),
+                     delta=wl.delta, M=tt(wl.M))
+    B = wl.n_t * wl.n_m
+    out = {"workload": f"large cluster: N_v 400, N_c 4000 (N_vc 1.6M), N_aux 8192, "
+                       f"{wl.n_t} targets x {wl.n_m} summed orbitals (B {B}, one sub-batch), "
+                       f"k {k}, no reorthogonalisation, 2000 frequencies",
+           "data": "L drawn on the device (torch Philox, seed 5), eps and M numpy seed 5",
+           "prepare_s": t_prep, "unit": "QP states/s"}
+    res = {}
+    for prec in ("fp8", "bf16"):
+        sig = torch.empty(wl.n_t, wl.omega.size, 2, dtype=torch.float64, device=dev)
+        e = torch.empty(wl.n_t, dtype=torch.float64, device=dev)
+        warm = L.Options(k=2, precision=prec, reorth="none", b_sub=B)
+        L.lgw_sigma_c(h, s, prob, warm, sig, e)
+        torch.cuda.synchronize()
+        o = L.Options(k=k, precision=prec, reorth="none", b_sub=B)
+        t0 = time.perf_counter()
+        rep = L.lgw_sigma_c(h, s, prob, o, sig, e, report=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        gms = rep["ms_gemm1"] + rep["ms_gemm2"]
+        res[prec] = (sig.cpu().numpy(), e.cpu().numpy())
+        out[prec] = {"value": wl.n_t / dt, "seconds": dt,
+                     "gemm_tflops": rep["gemm_flops"] / (gms * 1e-3) / 1e12 if gms else None,
+                     "ms_gemm1": rep["ms_gemm1"], "ms_gemm2": rep["ms_gemm2"],
+                     "ms_total": rep["ms_total"], "k_min": rep["k_min"]}
+    out["qp_diff_mev_fp8_vs_bf16"] = float(np.abs(res["fp8"][1] - res["bf16"][1]).max() * 1e3)
+    out["sigma_max_diff_mev_fp8_vs_bf16"] = float(np.abs(res["fp8"][0] - res["bf16"][0]).max()
+                                                  * 1e3)
+    out["sigma_scale_mev"] = float(np.abs(res["bf16"][0]).max() * 1e3)
+    L.lgw_release_system(s)
+    L.lgw_destroy(h)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -567,6 +628,9 @@ def main():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched-uneven leg and print it")
     ap.add_argument("--batched-targets", type=int, default=1)
+    ap.add_argument("--large-only", action="store_true",
+                    help="run only the large cluster-sized leg (about 2 minutes, ~240 GB)")
+    ap.add_argument("--large-targets", type=int, default=2)
     args = ap.parse_args()
     if args.adjoint_only:
         import torch
@@ -577,6 +641,13 @@ def main():
                           compare=args.adjoint_targets == 8)
         L.lgw_destroy(h)
         print(json.dumps({"adjoint": out}), flush=True)
+        return
+    if args.large_only:
+        import torch
+        sys.path.insert(0, ROOT)
+        from paper_2310_20103_gb300 import lgw as L
+        print(json.dumps({"large": large_leg(L, "cuda:0", n_targets=args.large_targets)}),
+              flush=True)
         return
     if args.batched_only:
         import torch

@@ -153,6 +153,31 @@ def batched_uneven(i, k=150, n_freq=1000, max_targets=None, max_m=256):
                          aux_scaled=True)
 
 
+def large_cluster(n_targets=16, n_m=1024, k=300, n_freq=2000, target_offset=0, seed=5):
+    """Large cluster-sized system: N_v=400, N_c=4000 (N_vc=1.6M), N_aux=8192,
+    scaled distributions; targets HOMO-7..LUMO+7 (16 states), each summing
+    over 1024 orbitals (400 valence + lowest 624 conduction); k=300, 2000
+    frequencies.  Returns (workload without L, sigma_L): the 1.6M x 8192
+    FP64 factor (105 GB) is drawn by the caller on the device, N(0, sigma_L^2)
+    i.i.d. like every other workload here; eps and M follow make_workload's
+    recipe (eps from the seeded generator, then M, with no L draws between)."""
+    n_v, n_c, A = 400, 4000, 8192
+    all_t = list(range(n_v - 8, n_v + 8))
+    targets = np.asarray(all_t[target_offset:target_offset + n_targets], dtype=np.int32)
+    m_idx = np.asarray(list(range(n_m)), dtype=np.int32)
+    rng = np.random.default_rng(seed)
+    eps_v = np.sort(rng.uniform(-12.0, -5.0, n_v))
+    eps_c = np.sort(rng.uniform(-3.0, 20.0, n_c))
+    eps = np.concatenate([eps_v, eps_c]).astype(np.float64)
+    s = 1.0 / np.sqrt(A)
+    M = _pair_factors(rng, targets, m_idx, A, 0.1 * s)
+    omega = np.linspace(-30.0, 30.0, n_freq)
+    wl = Workload(name="large_cluster", n_v=n_v, n_c=n_c, n_aux=A, eps=eps, L=None,
+                  targets=targets, m_idx=m_idx, M=M, omega=omega, delta=0.05,
+                  kernel_factor=4.0, k=k, meta=dict(seed=seed, aux_scaled=True))
+    return wl, 0.05 * s
+
+
 def custom(n_v, n_c, n_aux, n_targets, n_m, n_freq, seed, k, aux_scaled=True):
     """Arbitrary shape with the same recipe: targets straddle the gap,
     the summed set is the lowest ``n_m`` orbitals."""

@@ -105,16 +105,36 @@ typedef enum {
 typedef struct lgw_handle lgw_handle;
 typedef struct lgw_system lgw_system;
 
+/* Which copies of L a system keeps (lgw_system_desc.flags, OR-ed).
+ *   LGW_SYS_NO_FP64  no padded FP64 copy: precision LGW_FP64,
+ *                    lgw_sigma_c_backward and FP64 start vectors are then
+ *                    LGW_ERR_UNSUPPORTED (start vectors from M use the split-
+ *                    BF16 tensor-core product, so the BF16 copies are needed)
+ *   LGW_SYS_NO_BF16  no BF16 copies (L, L^T, low half): precision LGW_BF16
+ *                    is unsupported; start vectors from M use the FP64 copy
+ *   LGW_SYS_FP8      make the E4M3 copies now (otherwise on the first FP8
+ *                    request; with LGW_SYS_NO_FP64 they are always made now)
+ * Every copy is made straight from desc->L, so a caller may free its L once
+ * lgw_prepare_system has returned (device memory at N_vc = 1.6M, N_aux =
+ * 8192: FP64 copy 105 GB, BF16 copies 79 GB, E4M3 copies 26 GB). */
+enum {
+  LGW_SYS_NO_FP64 = 1,
+  LGW_SYS_NO_BF16 = 2,
+  LGW_SYS_FP8 = 4
+};
+
 /* One electronic system: KS energies and the Coulomb-kernel factor.
  * eps  [n_v + n_c]          valence block first (Eq. 1-3: v occupied, c empty)
  * L    [n_v*n_c][n_aux]     row-major, K = L L^T (Eq. 15-17 fitted form)
  * kernel_factor             c_K in C = Delta^2 + c_K Delta^1/2 K Delta^1/2;
- *                           4.0 for a closed-shell spin sum, 0 switches K off. */
+ *                           4.0 for a closed-shell spin sum, 0 switches K off.
+ * flags                     LGW_SYS_* (0: FP64 and BF16 copies, E4M3 on use) */
 typedef struct {
   int32_t n_v, n_c, n_aux;
   const double *eps;
   const double *L;
   double kernel_factor;
+  int32_t flags;
 } lgw_system_desc;
 
 /* The self-energy request.
@@ -209,10 +229,12 @@ lgw_status lgw_destroy(lgw_handle *h);
  * n bytes).  Returns the last error code. */
 lgw_status lgw_last_error(lgw_handle *h, char *buf, size_t n);
 
-/* Build a system: copies eps and L to the device, forms Delta_vc,
- * Delta^1/2 and Delta^2 (Eq. 2-4), pads L to [N_pad][A_pad], and makes the
- * BF16 copies of L (row-major) and L^T used by the tensor-core path.
- * Fails with LGW_ERR_NOT_SPD if some eps_c - eps_v <= 0. */
+/* Build a system: copies eps to the device, forms Delta_vc, Delta^1/2 and
+ * Delta^2 (Eq. 2-4), and makes the copies of L that desc->flags asks for,
+ * each padded to [N_pad][A_pad]: FP64, BF16 (L, L^T and the low half
+ * bf16(L - bf16(L))) and E4M3 (L, L^T, column scales).
+ * Fails with LGW_ERR_NOT_SPD if some eps_c - eps_v <= 0 and with
+ * LGW_ERR_ARG for unknown flags or LGW_SYS_NO_FP64 | LGW_SYS_NO_BF16. */
 lgw_status lgw_prepare_system(lgw_handle *h, const lgw_system_desc *desc, lgw_system **out);
 
 /* Free a system's device memory.  NULL is accepted. */

@@ -7,6 +7,8 @@
 //   G(zeta) = W / (zeta - a_0 - b_1^2 / (zeta - a_1 - b_2^2 / (...)))
 // which is Eq. 11 (z_m = omega - eps_m - i eta_m delta, zeta = -eta_m z_m).
 // Sigma_t = sum over the summed set of Sigma_tm (Eq. 10).
+#include <algorithm>
+
 #include "lgw_internal.cuh"
 
 namespace lgw {
@@ -47,16 +49,19 @@ __device__ __forceinline__ void cf_eval(const double *__restrict__ a, const doub
   }
 }
 
-// One thread per (target, frequency): loops over the summed set and the
-// continued-fraction depth.  Threads of a warp share t and read the same
-// coefficients (broadcast loads).
-__global__ void k_cf_grid(CfProblem p, JacobiBufs jb, double *__restrict__ sigma) {
+// One thread per (target, frequency, slice of the summed set): loops over its
+// slice of m and the continued-fraction depth.  Threads of a warp share t and
+// m and read the same coefficients (broadcast loads).  With one slice the
+// thread writes Sigma_t(omega_f) itself; otherwise its partial sum goes to
+// part[slice] and k_cf_reduce adds the slices in a fixed order.
+__global__ void k_cf_grid(CfProblem p, JacobiBufs jb, double *__restrict__ out, int mchunk) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ti = blockIdx.y;
+  const int ti = blockIdx.y, sl = blockIdx.z;
   if (f >= p.n_freq) return;
   const double om = p.omega[f];
+  const int mi0 = sl * mchunk, mi1 = min(p.n_m, mi0 + mchunk);
   double sr = 0.0, si = 0.0;
-  for (int mi = 0; mi < p.n_m; ++mi) {
+  for (int mi = mi0; mi < mi1; ++mi) {
     const int v = ti * p.n_m + mi;
     const int n = jb.n[v];
     if (n <= 0) continue;
@@ -69,8 +74,18 @@ __global__ void k_cf_grid(CfProblem p, JacobiBufs jb, double *__restrict__ sigma
     sr -= eta * G.re;
     si -= eta * G.im;
   }
-  sigma[((size_t)ti * p.n_freq + f) * 2] = sr;
-  sigma[((size_t)ti * p.n_freq + f) * 2 + 1] = si;
+  const size_t o = (((size_t)sl * p.n_t + ti) * p.n_freq + f) * 2;
+  out[o] = sr;
+  out[o + 1] = si;
+}
+
+__global__ void k_cf_reduce(const double *__restrict__ part, int S, size_t n,
+                            double *__restrict__ sigma) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int sl = 0; sl < S; ++sl) s += part[(size_t)sl * n + i];
+  sigma[i] = s;
 }
 
 // Sigma_t(E) and dSigma_t/domega at one real E; lanes split the summed set,
@@ -175,10 +190,30 @@ __global__ void k_qp(CfProblem p, JacobiBufs jb, const double *__restrict__ sigm
   }
 }
 
-void launch_cf_grid(const CfProblem &p, JacobiBufs jb, double *sigma, cudaStream_t st) {
-  if (p.n_freq <= 0 || p.n_t <= 0) return;
-  dim3 grid((p.n_freq + 127) / 128, p.n_t);
-  k_cf_grid<<<grid, 128, 0, st>>>(p, jb, sigma);
+int cf_slices(const CfProblem &p) {
+  // enough (target, frequency, slice) threads to hide the FP64 latency of
+  // the continued-fraction chains: about 128k, at most 64 slices
+  if (p.n_t <= 0 || p.n_freq <= 0 || p.n_m <= 0) return 1;
+  const long long tf = (long long)p.n_t * p.n_freq;
+  long long S = (131072 + tf - 1) / tf;
+  S = std::min<long long>(S, std::min(p.n_m, 64));
+  return (int)std::max<long long>(S, 1);
+}
+
+int launch_cf_grid(const CfProblem &p, JacobiBufs jb, double *sigma, double *part, int S,
+                   cudaStream_t st) {
+  if (p.n_freq <= 0 || p.n_t <= 0) return 0;
+  if (part == nullptr) S = 1;
+  const int mchunk = (p.n_m + S - 1) / S;
+  S = std::max(1, (p.n_m + mchunk - 1) / std::max(1, mchunk));
+  dim3 grid((p.n_freq + 127) / 128, p.n_t, S);
+  k_cf_grid<<<grid, 128, 0, st>>>(p, jb, S == 1 ? sigma : part, std::max(1, mchunk));
+  if (S > 1) {
+    const size_t n = (size_t)p.n_t * p.n_freq * 2;
+    k_cf_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, S, n, sigma);
+    return 2;
+  }
+  return 1;
 }
 
 void launch_qp(const CfProblem &p, JacobiBufs jb, const double *sigma, int max_iter, double tol,

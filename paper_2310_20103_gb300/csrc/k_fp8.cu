@@ -35,20 +35,21 @@ __device__ __forceinline__ float from_e4m3(uint8_t v) {
   return __half2float(__half(hr));
 }
 
-// column maxima of |L64| (non-negative floats order like their bit patterns)
-__global__ void k_col_absmax(const double *__restrict__ L64, int N, int A,
+// column maxima of |L| over L [nr][nc] (row stride ld); non-negative floats
+// order like their bit patterns
+__global__ void k_col_absmax(const double *__restrict__ src, int ld, int nr, int nc,
                              unsigned *__restrict__ colmax) {
   __shared__ float red[8][32];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int mu = blockIdx.x * 32 + tx;
   const int r0 = blockIdx.y * 1024;
   float m = 0.0f;
-  if (mu < A)
-    for (int r = r0 + ty; r < min(N, r0 + 1024); r += 8)
-      m = fmaxf(m, (float)fabs(L64[(size_t)r * A + mu]));
+  if (mu < nc)
+    for (int r = r0 + ty; r < min(nr, r0 + 1024); r += 8)
+      m = fmaxf(m, (float)fabs(src[(size_t)r * ld + mu]));
   red[ty][tx] = m;
   __syncthreads();
-  if (ty == 0 && mu < A) {
+  if (ty == 0 && mu < nc) {
     for (int i = 1; i < 8; ++i) m = fmaxf(m, red[i][tx]);
     atomicMax(colmax + mu, __float_as_uint(m));
   }
@@ -59,8 +60,9 @@ __global__ void k_col_scales(const unsigned *__restrict__ colmax, int A, float *
   if (mu < A) sL[mu] = pow2_scale(__uint_as_float(colmax[mu]));
 }
 
-// L8 = e4m3(L64 / s_mu) [N][A] and its transpose L8t [A][N] (32 x 32 tiles)
-__global__ void k_quantize_L8(const double *__restrict__ L64, int N, int A,
+// L8 = e4m3(L / s_mu) [N][A] from L [nr][nc] (row stride ld, zero padded)
+// and its transpose L8t [A][N] (32 x 32 tiles)
+__global__ void k_quantize_L8(const double *__restrict__ src, int ld, int nr, int nc, int N, int A,
                               const float *__restrict__ sL, uint8_t *__restrict__ L8,
                               uint8_t *__restrict__ L8t) {
   __shared__ uint8_t tile[32][33];
@@ -70,7 +72,8 @@ __global__ void k_quantize_L8(const double *__restrict__ L64, int N, int A,
     const int r = r0 + rr, c = c0 + tx;
     uint8_t v = 0;
     if (r < N && c < A) {
-      v = to_e4m3((float)(L64[(size_t)r * A + c] / (double)sL[c]));
+      const double x = (r < nr && c < nc) ? src[(size_t)r * ld + c] : 0.0;
+      v = to_e4m3((float)(x / (double)sL[c]));
       L8[(size_t)r * A + c] = v;
     }
     tile[rr][tx] = v;
@@ -167,14 +170,14 @@ __global__ void __launch_bounds__(256) k_reduce_y_fp8(const float *__restrict__ 
 }
 
 // ----------------------------------------------------------------------------
-void launch_prepare_fp8(const SysDev &s, unsigned *colmax, uint8_t *L8, uint8_t *L8t, float *sL,
-                        cudaStream_t st) {
+void launch_prepare_fp8(const double *src, int ld, int nr, int nc, const SysDev &s,
+                        unsigned *colmax, uint8_t *L8, uint8_t *L8t, float *sL, cudaStream_t st) {
   cudaMemsetAsync(colmax, 0, sizeof(unsigned) * s.A, st);
-  k_col_absmax<<<dim3((s.A + 31) / 32, (s.N + 1023) / 1024), 256, 0, st>>>(s.L64, s.N, s.A,
-                                                                          colmax);
+  k_col_absmax<<<dim3((s.A + 31) / 32, (nr + 1023) / 1024), 256, 0, st>>>(src, ld, nr, nc,
+                                                                         colmax);
   k_col_scales<<<(s.A + 255) / 256, 256, 0, st>>>(colmax, s.A, sL);
-  k_quantize_L8<<<dim3((s.A + 31) / 32, (s.N + 31) / 32), 256, 0, st>>>(s.L64, s.N, s.A, sL, L8,
-                                                                        L8t);
+  k_quantize_L8<<<dim3((s.A + 31) / 32, (s.N + 31) / 32), 256, 0, st>>>(src, ld, nr, nc, s.N, s.A,
+                                                                        sL, L8, L8t);
 }
 
 void launch_quant_x8(const __nv_bfloat16 *xh, int Bs, int N, uint8_t *x8, float *sx,

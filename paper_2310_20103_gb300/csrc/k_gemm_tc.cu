@@ -194,6 +194,9 @@ struct EpiArgs {
   int add;
   // per-column (vector) scale of the accumulator (FP8 operands), or NULL
   const float *colscale;
+  // K loop start rotated by the M tile (spreads concurrent CTAs over HBM
+  // channels) or not (CTAs sharing the B tile stream it in step, from L2)
+  int rot;
 };
 
 enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2, E_LANCZOS_NA = 3, E_SPLITB = 4, E_VACC = 5,
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(&empty[s], ph ^ 1, ea.status)) break;
         mbar_expect_tx(&full[s], C::STAGE);
         uint8_t *sa = smem + s * C::STAGE;
-        const int kx = (kb0 + (it + m_tile) % nk) * (BK * 2 / EB);
+        const int kx = (kb0 + (it + (ea.rot ? m_tile : 0)) % nk) * (BK * 2 / EB);
         tma_load_2d(sa, &tmA, &full[s], kx, m_tile * BM);
         tma_load_2d(sa + C::A_BYTES, &tmB, &full[s], kx, n_tile * BN);
         issued = it + 1;
@@ -426,9 +429,11 @@ struct TcPlan {
   // E4M3 operands (fp8 plans): L8t / x8 for gemm1, L8 / y8 for gemm2
   CUtensorMap f1A, f1B, f2A, f2B;
   bool fp8 = false;
+  bool has_bf16 = false;   // g1A / g2A / g2Alo encoded (the system has BF16 copies)
   const uint8_t *x8 = nullptr, *y8 = nullptr;
   const float *ty = nullptr;   // per-vector scale of y8 (gemm2 column scale)
   int BN1, BN2;   // N tile of gemm1 / gemm2 (and the coupling products)
+  int rot1 = 1;   // gemm1 K-start rotation (tuned); gemm2 always rotates
   const __nv_bfloat16 *xh;
   int N, A, Bs;
   int splits, kb_per_split;
@@ -529,11 +534,16 @@ TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *
   p->cd = s.cd;
   p->d2f = s.d2f;
   p->cdf = s.cdf;
-  bool ok = encode_2d(&p->g1A, s.Ltb, (uint64_t)s.N, (uint64_t)s.A, tc::BM) &&
-            encode_2d(&p->g1B, xh, (uint64_t)s.N, (uint64_t)Bs, (uint32_t)p->BN1) &&
-            encode_2d(&p->g2A, s.Lb, (uint64_t)s.A, (uint64_t)s.N, tc::BM) &&
-            encode_2d(&p->g2Alo, s.Lb_lo, (uint64_t)s.A, (uint64_t)s.N, tc::BM) &&
+  // the BF16 copies of L are absent for a system prepared without them
+  // (E4M3 plans); their maps stay unset then
+  bool ok = encode_2d(&p->g1B, xh, (uint64_t)s.N, (uint64_t)Bs, (uint32_t)p->BN1) &&
             encode_2d(&p->g2B, yh, (uint64_t)s.A, (uint64_t)Bs, (uint32_t)p->BN2);
+  if (ok && s.Lb) {
+    ok = encode_2d(&p->g1A, s.Ltb, (uint64_t)s.N, (uint64_t)s.A, tc::BM) &&
+         encode_2d(&p->g2A, s.Lb, (uint64_t)s.A, (uint64_t)s.N, tc::BM) &&
+         encode_2d(&p->g2Alo, s.Lb_lo, (uint64_t)s.A, (uint64_t)s.N, tc::BM);
+    p->has_bf16 = ok;
+  }
   if (!ok) {
     snprintf(err, errn, "cuTensorMapEncodeTiled failed");
     delete p;
@@ -577,6 +587,7 @@ void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st) {
   ea.ypart = p->ypart;
   ea.ldo = p->A;
   ea.status = status;
+  ea.rot = p->rot1;
   if (p->fp8) {
     // same split count; K blocks of 128 elements
     const int nkb = p->N / 128;
@@ -585,6 +596,7 @@ void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st) {
                                  st);
     return;
   }
+  if (!p->has_bf16) return;   // callers check tc_plan_has_bf16 first
   dispatch_bn<tc::E_SPLITK>(p->BN1, p->g1A, p->g1B, p->A, p->Bs, p->N / tc::BK, p->kb_per_split,
                             p->splits, ea, st);
 }
@@ -599,6 +611,7 @@ void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qp
                      const double *betaj, double *w, double *alpha_part, unsigned *status,
                      cudaStream_t st) {
   tc::EpiArgs ea{};
+  ea.rot = 1;
   ea.N = p->N;
   ea.Delta2 = p->Delta2;
   ea.cd = p->cd;
@@ -619,6 +632,7 @@ void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qp
       dispatch_bn<tc::E_APPLY, 1>(p->BN2, p->f2A, p->f2B, p->N, p->Bs, nkb, nkb, 1, ea, st);
     return;
   }
+  if (!p->has_bf16) return;
   const int num_kb = p->A / tc::BK;
   if (epi == EPI_LANCZOS && alpha_part == nullptr)
     dispatch_bn<tc::E_LANCZOS_NA>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
@@ -645,11 +659,13 @@ __global__ void k_split_m(const double *__restrict__ M, int nvec, int n_aux, int
 }
 }  // namespace tc
 
-void launch_coupling_tc(const TcPlan *p, const SysDev &s, const double *M, int nvec,
+bool launch_coupling_tc(const TcPlan *p, const SysDev &s, const double *M, int nvec,
                         float *vf, unsigned *status, cudaStream_t st) {
+  if (!p->has_bf16) return false;
   const size_t n = (size_t)p->Bs * p->A;
   const unsigned blocks = (unsigned)((n + 255) / 256);
   tc::EpiArgs ea{};
+  ea.rot = 1;
   ea.N = p->N;
   ea.ucd = vf;
   ea.status = status;
@@ -662,10 +678,12 @@ void launch_coupling_tc(const TcPlan *p, const SysDev &s, const double *M, int n
   dispatch_bn<tc::E_VACC>(p->BN2, p->g2Alo, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
   tc::k_split_m<<<blocks, 256, 0, st>>>(M, nvec, s.n_aux, p->Bs, p->A, 1, p->yh);
   dispatch_bn<tc::E_VACC>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+  return true;
 }
 
 void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaStream_t st) {
   tc::EpiArgs ea{};
+  ea.rot = 1;
   ea.N = p->N;
   ea.cdf = p->cdf;
   ea.ucd = ucd;
@@ -676,6 +694,7 @@ void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaSt
     dispatch_bn<tc::E_SPLITB, 1>(p->BN2, p->f2A, p->f2B, p->N, p->Bs, nkb, nkb, 1, ea, st);
     return;
   }
+  if (!p->has_bf16) return;
   const int num_kb = p->A / tc::BK;
   dispatch_bn<tc::E_SPLITB>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
 }
@@ -692,6 +711,7 @@ bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const __nv_bfloat16 *
     return false;
   }
   tc::EpiArgs ea{};
+  ea.rot = 1;
   ea.out = out;
   ea.ldo = ldo;
   ea.status = status;
@@ -732,7 +752,7 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int BN1, splits, BN2;
+  int BN1, splits, BN2, rot1;
 };
 std::map<TuneKey, TuneVal> g_tune;
 std::mutex g_tune_mu;
@@ -786,6 +806,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
     if (it != g_tune.end()) {
       p->BN1 = it->second.BN1;
       p->BN2 = it->second.BN2;
+      p->rot1 = it->second.rot1;
       plan_set_splits(p, it->second.splits);
       if (splits_out) *splits_out = p->splits;
       return plan_encode_b(p);
@@ -799,8 +820,8 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
     launch_gemm1_tc(p, status, st);
     launch_reduce_y_bf16(p->ypart, p->splits, p->Bs, p->A, p->yh, nullptr, st);
   };
-  // gemm1: N tile x split count
-  const TuneVal def{p->BN1, p->splits, p->BN2};
+  // gemm1: N tile x split count x K-start rotation
+  const TuneVal def{p->BN1, p->splits, p->BN2, p->rot1};
   float t_def = time_best(gemm1, st);
   TuneVal best = def;
   float t_best = t_def;
@@ -808,26 +829,31 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
     const int tiles = ((p->A + tc::BM - 1) / tc::BM) * ((p->Bs + bn - 1) / bn);
     const int s0 = choose_splits(tiles, num_kb, nsm);
     const int cands[3] = {std::max(1, s0 / 2), s0, std::min(64, 2 * s0)};
-    for (int ci = 0; ci < 3; ++ci) {
-      const int sreq = cands[ci];
-      if (num_kb / sreq < 8 && sreq > 1) continue;
-      p->BN1 = bn;
-      plan_set_splits(p, sreq);
-      if (bn == def.BN1 && p->splits == def.splits) continue;
-      if (!plan_encode_b(p)) return false;
-      const float t = time_best(gemm1, st);
-      if (t < t_best) {
-        t_best = t;
-        best.BN1 = bn;
-        best.splits = p->splits;
+    for (int ci = 0; ci < 3; ++ci)
+      for (int rot = 0; rot <= 1; ++rot) {
+        const int sreq = cands[ci];
+        if (num_kb / sreq < 8 && sreq > 1) continue;
+        p->BN1 = bn;
+        p->rot1 = rot;
+        plan_set_splits(p, sreq);
+        if (bn == def.BN1 && p->splits == def.splits && rot == def.rot1) continue;
+        if (!plan_encode_b(p)) return false;
+        const float t = time_best(gemm1, st);
+        if (t < t_best) {
+          t_best = t;
+          best.BN1 = bn;
+          best.splits = p->splits;
+          best.rot1 = rot;
+        }
       }
-    }
   }
   if (t_best > 0.97f * t_def) {
     best.BN1 = def.BN1;
     best.splits = def.splits;
+    best.rot1 = def.rot1;
   }
   p->BN1 = best.BN1;
+  p->rot1 = best.rot1;
   plan_set_splits(p, best.splits);
   // gemm2 (store-only epilogue into the caller's scratch): N tile
   if (ucd != nullptr) {
@@ -869,5 +895,7 @@ bool tc_plan_enable_fp8(TcPlan *p, const uint8_t *L8t, const uint8_t *L8, const 
          encode_2d(&p->f2A, L8, (uint64_t)p->A, (uint64_t)p->N, tc::BM, 0, 1) &&
          plan_encode_b(p);
 }
+
+bool tc_plan_has_bf16(const TcPlan *p) { return p->has_bf16; }
 
 }  // namespace lgw

@@ -66,6 +66,44 @@ __device__ void dots_rows(const VecCtx &c, int nrows, int b, int chunk, const do
   }
 }
 
+// Tensor-core path without reorthogonalisation: the contraction leaves
+// ucd = c_K Delta^1/2 (L y) in FP32 (store-only epilogue); here, in FP64,
+//   w = Delta^2 q_j + ucd - beta_j q_{j-1}
+// and per-chunk partials of alpha_j = q_j . w (alpha_part[chunk][b]).
+__global__ void __launch_bounds__(VEC_THREADS) k_assemble_w(VecCtx c, int j,
+                                                           const float *__restrict__ ucd) {
+  __shared__ double red[VEC_THREADS / 32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  if (!vec_live(c, b, j)) return;
+  const size_t voff = (size_t)b * c.N;
+  const double *q = slot_ptr(c, j) + voff;
+  const double *qp = j > 0 ? slot_ptr(c, j - 1) + voff : nullptr;
+  const float *u = ucd + voff;
+  double *w = c.w + voff;
+  const double bj = c.betaj[b];
+  const int e0 = elem_base(chunk);
+  double ap = 0.0;
+#pragma unroll
+  for (int u4 = 0; u4 < 4; ++u4) {
+    const int e = e0 + u4 * 64;
+    if (e >= c.N) continue;
+    const double2 q2 = *reinterpret_cast<const double2 *>(q + e);
+    const float2 v2 = *reinterpret_cast<const float2 *>(u + e);
+    double2 w2;
+    w2.x = fma(c.Delta2[e], q2.x, (double)v2.x);
+    w2.y = fma(c.Delta2[e + 1], q2.y, (double)v2.y);
+    if (qp != nullptr) {
+      const double2 p2 = *reinterpret_cast<const double2 *>(qp + e);
+      w2.x = fma(-bj, p2.x, w2.x);
+      w2.y = fma(-bj, p2.y, w2.y);
+    }
+    *reinterpret_cast<double2 *>(w + e) = w2;
+    ap = fma(q2.x, w2.x, fma(q2.y, w2.y, ap));
+  }
+  ap = block_sum(ap, red);
+  if (threadIdx.x == 0) c.alpha_part[(size_t)chunk * c.Bs + b] = ap;
+}
+
 // alpha_j from the epilogue partials, w -= alpha_j q_j, ||w||^2 partials,
 // and (with reorthogonalisation) the first-pass dot products.
 __global__ void __launch_bounds__(VEC_THREADS) k_alpha_axpy(VecCtx c, int j) {
@@ -365,6 +403,9 @@ void launch_norm_partials(const VecCtx &c, const double *x, double *out, cudaStr
 }
 void launch_normalize(const VecCtx &c, int j, int is_start, const double *, cudaStream_t st) {
   k_normalize<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, j, is_start);
+}
+void launch_assemble_w(const VecCtx &c, int j, const float *ucd, cudaStream_t st) {
+  k_assemble_w<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, j, ucd);
 }
 void launch_alpha_axpy(const VecCtx &c, int j, cudaStream_t st) {
   k_alpha_axpy<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, j);

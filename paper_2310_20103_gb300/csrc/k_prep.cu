@@ -42,9 +42,10 @@ __global__ void k_pad_L(const double *__restrict__ L, int n_vc, int n_aux, int N
   }
 }
 
-// BF16 copies: Lb = bf16(L64) [N][A] and Ltb = bf16(L64)^T [A][N], through a
-// 32x32 shared-memory transpose tile so both writes are coalesced.
-__global__ void k_quantize_L(const double *__restrict__ L64, int N, int A,
+// BF16 copies from L [nr][nc] (row stride ld), zero padded to [N][A]:
+// Lb = bf16(L) [N][A], Ltb = bf16(L)^T [A][N] and Lb_lo = bf16(L - bf16(L)),
+// through a 32x32 shared-memory transpose tile so both writes are coalesced.
+__global__ void k_quantize_L(const double *__restrict__ src, int ld, int nr, int nc, int N, int A,
                              __nv_bfloat16 *__restrict__ Lb, __nv_bfloat16 *__restrict__ Ltb,
                              __nv_bfloat16 *__restrict__ Lb_lo) {
   __shared__ __nv_bfloat16 tile[32][33];
@@ -54,7 +55,7 @@ __global__ void k_quantize_L(const double *__restrict__ L64, int N, int A,
     int r = r0 + rr, c = c0 + tx;
     __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
     if (r < N && c < A) {
-      const double x = L64[(int64_t)r * A + c];
+      const double x = (r < nr && c < nc) ? src[(int64_t)r * ld + c] : 0.0;
       v = __double2bfloat16(x);
       Lb[(int64_t)r * A + c] = v;
       Lb_lo[(int64_t)r * A + c] = __double2bfloat16(x - (double)__bfloat162float(v));
@@ -87,9 +88,10 @@ void launch_pad_L(const double *L, const SysDev &s, cudaStream_t st) {
   k_pad_L<<<(int)bl, th, 0, st>>>(L, s.n_vc, s.n_aux, s.N, s.A, s.L64);
 }
 
-void launch_quantize_L(const SysDev &s, cudaStream_t st) {
+void launch_quantize_L(const double *src, int ld, int nr, int nc, const SysDev &s,
+                       cudaStream_t st) {
   dim3 grid((s.A + 31) / 32, (s.N + 31) / 32);
-  k_quantize_L<<<grid, 256, 0, st>>>(s.L64, s.N, s.A, s.Lb, s.Ltb, s.Lb_lo);
+  k_quantize_L<<<grid, 256, 0, st>>>(src, ld, nr, nc, s.N, s.A, s.Lb, s.Ltb, s.Lb_lo);
 }
 
 }  // namespace lgw

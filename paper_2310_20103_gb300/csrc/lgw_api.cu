@@ -350,11 +350,8 @@ Opts resolve_opts(lgw_handle *h, const lgw_options *o, const SysDev &s) {
   return r;
 }
 
-// The E4M3 copies of L are made on the first FP8 request for a system.
-void ensure_fp8(lgw_handle *h, const lgw_system *csys, const Opts &o) {
-  if (o.precision != LGW_FP8 || csys->s.L8) return;
-  lgw_system *sys = const_cast<lgw_system *>(csys);
-  SysDev &s = sys->s;
+// E4M3 copies of L from src [nr][nc] (row stride ld) into s.
+void make_fp8(lgw_handle *h, SysDev &s, const double *src, int ld, int nr, int nc) {
   const size_t n = (size_t)s.N * s.A;
   uint8_t *a = nullptr, *b = nullptr;
   float *sc = nullptr;
@@ -368,11 +365,32 @@ void ensure_fp8(lgw_handle *h, const lgw_system *csys, const Opts &o) {
     throw Fail{LGW_ERR_OOM};
   }
   unsigned *colmax = wsT<unsigned>(h, "fp8_colmax", (size_t)s.A);
-  launch_prepare_fp8(s, colmax, a, b, sc, h->stream);
+  launch_prepare_fp8(src, ld, nr, nc, s, colmax, a, b, sc, h->stream);
   check_launch(h, "prepare_fp8");
   s.L8 = a;
   s.L8t = b;
   s.sL = sc;
+}
+
+// The copies of L a request needs must exist; the E4M3 copies are made on
+// the first FP8 request for a system that keeps its FP64 copy.
+void ensure_copies(lgw_handle *h, const lgw_system *csys, const Opts &o) {
+  const SysDev &cs = csys->s;
+  if (o.precision == LGW_FP64 && !cs.L64) {
+    set_err(h, LGW_ERR_UNSUPPORTED, "the system keeps no FP64 copy of L (LGW_SYS_NO_FP64)");
+    throw Fail{LGW_ERR_UNSUPPORTED};
+  }
+  if (o.precision == LGW_BF16 && !cs.Lb) {
+    set_err(h, LGW_ERR_UNSUPPORTED, "the system keeps no BF16 copy of L (LGW_SYS_NO_BF16)");
+    throw Fail{LGW_ERR_UNSUPPORTED};
+  }
+  if (o.precision != LGW_FP8 || cs.L8) return;
+  if (!cs.L64) {
+    set_err(h, LGW_ERR_UNSUPPORTED, "no E4M3 copy of L and no FP64 copy to make it from");
+    throw Fail{LGW_ERR_UNSUPPORTED};
+  }
+  lgw_system *sys = const_cast<lgw_system *>(csys);
+  make_fp8(h, sys->s, cs.L64, cs.A, cs.N, cs.A);
 }
 
 struct ProbView {
@@ -493,7 +511,10 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   c.yy_part = yy;
   c.dq2_part = (split && tc) ? wsT<float>(h, "dq2_part", (size_t)Bs * nchunks) : nullptr;
   c.xh = tc ? wsT<__nv_bfloat16>(h, "xh", (size_t)Bs * N) : nullptr;
-  c.n_mt = tc ? tc_n_mt(s) : N / F64_TILE;
+  // alpha partials: per 2048-element chunk (tensor cores without
+  // reorthogonalisation), per GEMM2 tile otherwise
+  const bool tc_plain = tc && !reorth;
+  c.n_mt = tc_plain ? nchunks : (tc ? tc_n_mt(s) : N / F64_TILE);
   c.alpha_part = wsT<double>(h, "alpha_part", (size_t)c.n_mt * Bs);
   c.dot_part = reorth ? wsT<double>(h, "dot_part", (size_t)Bs * nchunks * kmax1) : nullptr;
   c.h = reorth ? wsT<double>(h, "hcoef", (size_t)Bs * kmax1) : nullptr;
@@ -531,6 +552,11 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
     if (!plan) {
       set_err(h, LGW_ERR_CUDA, "%s", err);
       throw Fail{LGW_ERR_CUDA};
+    }
+    if (!fp8 && !tc_plan_has_bf16(plan)) {
+      tc_plan_destroy(plan);
+      set_err(h, LGW_ERR_UNSUPPORTED, "BF16 contractions need the BF16 copies of L");
+      throw Fail{LGW_ERR_UNSUPPORTED};
     }
     if (fp8) {
       x8 = wsT<uint8_t>(h, "x8", (size_t)Bs * N);
@@ -575,14 +601,22 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
     auto sub_body = [&]() {
       // ---- start vectors b = Delta^1/2 V, V = L M (text after Eq. 8) ----
       tm.mark(C_START);
-      if (pv.d_M && tc) {
+      if (pv.d_M && tc && s.Lb) {
         // V = L M on the tensor cores in split BF16 (three products, FP32 sum)
         float *vf = ucd_buf;
-        launch_coupling_tc(plan, s, pv.d_M + (size_t)vec0 * s.n_aux, nvec, vf, h->d_status, st);
+        if (!launch_coupling_tc(plan, s, pv.d_M + (size_t)vec0 * s.n_aux, nvec, vf, h->d_status,
+                                st)) {
+          set_err(h, LGW_ERR_UNSUPPORTED, "tensor-core plan without the BF16 copies of L");
+          throw Fail{LGW_ERR_UNSUPPORTED};
+        }
         check_launch(h, "coupling_tc");
         launch_start_from_vf(c, vf, st);
         check_launch(h, "start_from_vf");
       } else if (pv.d_M) {
+        if (!s.L64) {
+          set_err(h, LGW_ERR_UNSUPPORTED, "start vectors from M need the BF16 or FP64 copy of L");
+          throw Fail{LGW_ERR_UNSUPPORTED};
+        }
         LGW_TRY_CUDA(h, cudaMemsetAsync(Y64, 0, sizeof(double) * Bs * s.A, st));
         LGW_TRY_CUDA(h, cudaMemcpy2DAsync(Y64, sizeof(double) * s.A, pv.d_M + (size_t)vec0 * s.n_aux,
                                           sizeof(double) * s.n_aux, sizeof(double) * s.n_aux, nvec,
@@ -620,12 +654,20 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
             launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, yy, st);
           check_launch(h, "reduce_y");
           tm.mark(C_GEMM2);
-          if (split)
+          if (split) {
             launch_gemm2_tc_split(plan, const_cast<float *>(c.ucd), h->d_status, st);
-          else
+          } else if (tc_plain) {
+            // store-only FP32 epilogue; w and the alpha partials in FP64 on
+            // the vector pass (an FP64 epilogue would serialise behind the
+            // MMAs on the narrow FP64 pipe)
+            launch_gemm2_tc_split(plan, ucd_buf, h->d_status, st);
+            check_launch(h, "gemm2_tc");
+            launch_assemble_w(c, j, ucd_buf, st);
+          } else {
             launch_gemm2_tc(plan, EPI_LANCZOS, qj, qp, c.betaj, c.w, c.alpha_part, h->d_status,
                             st);
-          check_launch(h, "gemm2_tc");
+          }
+          check_launch(h, tc_plain ? "assemble_w" : "gemm2_tc");
         } else {
           launch_gemm1_f64(s, qj, Bs, Yp64, splits64, st);
           check_launch(h, "gemm1_f64");
@@ -744,8 +786,11 @@ void run_sigma(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o
   cp.shift = pv.d_shift;
   tm.mark(C_CF);
   double *sig = sigma ? sigma : wsT<double>(h, "sigma_tmp", (size_t)std::max(1, pv.n_t * pv.n_freq * 2));
-  launch_cf_grid(cp, jb, sig, st);
-  if (pv.n_freq > 0 && pv.n_t > 0) check_launch(h, "cf_grid");
+  const int S = cf_slices(cp);
+  double *part = S > 1 ? wsT<double>(h, "cf_part", (size_t)S * pv.n_t * pv.n_freq * 2) : nullptr;
+  const int ncf = launch_cf_grid(cp, jb, sig, part, S, st);
+  if (ncf > 0) check_launch(h, "cf_grid");
+  if (ncf > 1) check_launch(h, "cf_reduce");
   tm.mark(C_QP);
   if (e_qp && pv.n_t > 0) {
     launch_qp(cp, jb, sig, o.qp_max_iter, o.qp_tol, e_qp, z_qp, h->d_status, st);
@@ -876,8 +921,9 @@ lgw_status lgw_prepare_system(lgw_handle *h, const lgw_system_desc *d, lgw_syste
   if (!d || !out || !d->eps || !d->L) return set_err(h, LGW_ERR_ARG, "NULL descriptor field");
   if (d->n_v < 1 || d->n_c < 1 || d->n_aux < 1)
     return set_err(h, LGW_ERR_ARG, "n_v, n_c, n_aux must be >= 1");
-  if ((int64_t)d->n_v * d->n_c > (int64_t)1 << 30)
-    return set_err(h, LGW_ERR_SHAPE, "n_v * n_c too large");
+  // the 32 x 32 transpose tiles of the operand copies use grid.y = N / 32
+  if ((int64_t)d->n_v * d->n_c > (int64_t)65535 * 32)
+    return set_err(h, LGW_ERR_SHAPE, "n_v * n_c above 2097120");
   if (!(d->kernel_factor >= 0.0)) return set_err(h, LGW_ERR_ARG, "kernel_factor must be >= 0");
   *out = nullptr;
   lgw_system *sys = new lgw_system();
@@ -900,6 +946,13 @@ lgw_status lgw_prepare_system(lgw_handle *h, const lgw_system_desc *d, lgw_syste
     allocs.push_back(p);
     return p;
   };
+  const int flags = d->flags;
+  if ((flags & ~(LGW_SYS_NO_FP64 | LGW_SYS_NO_BF16 | LGW_SYS_FP8)) != 0 ||
+      ((flags & LGW_SYS_NO_FP64) && (flags & LGW_SYS_NO_BF16))) {
+    delete sys;
+    return set_err(h, LGW_ERR_ARG, "bad system flags 0x%x", flags);
+  }
+  const bool keep64 = !(flags & LGW_SYS_NO_FP64), keep16 = !(flags & LGW_SYS_NO_BF16);
   const int norb = s.n_v + s.n_c;
   s.eps = (double *)alloc(sizeof(double) * norb);
   s.Delta = (double *)alloc(sizeof(double) * s.N);
@@ -909,12 +962,15 @@ lgw_status lgw_prepare_system(lgw_handle *h, const lgw_system_desc *d, lgw_syste
   s.dsqf = (float *)alloc(sizeof(float) * s.N);
   s.d2f = (float *)alloc(sizeof(float) * s.N);
   s.cdf = (float *)alloc(sizeof(float) * s.N);
-  s.L64 = (double *)alloc(sizeof(double) * (size_t)s.N * s.A);
-  s.Lb = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
-  s.Ltb = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
-  s.Lb_lo = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
-  if (!s.eps || !s.Delta || !s.dsq || !s.Delta2 || !s.cd || !s.dsqf || !s.d2f || !s.cdf ||
-      !s.L64 || !s.Lb || !s.Ltb || !s.Lb_lo) {
+  bool ok = s.eps && s.Delta && s.dsq && s.Delta2 && s.cd && s.dsqf && s.d2f && s.cdf;
+  if (ok && keep64) ok = (s.L64 = (double *)alloc(sizeof(double) * (size_t)s.N * s.A)) != nullptr;
+  if (ok && keep16) {
+    s.Lb = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
+    s.Ltb = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
+    s.Lb_lo = (__nv_bfloat16 *)alloc(sizeof(__nv_bfloat16) * (size_t)s.N * s.A);
+    ok = s.Lb && s.Ltb && s.Lb_lo;
+  }
+  if (!ok) {
     for (void *p : allocs) cudaFree(p);
     delete sys;
     return set_err(h, LGW_ERR_OOM, "device allocation for the system failed");
@@ -931,13 +987,21 @@ lgw_status lgw_prepare_system(lgw_handle *h, const lgw_system_desc *d, lgw_syste
     check_launch(h, "pair_energies");
     launch_check_delta(s, h->d_status, st);
     check_launch(h, "check_delta");
-    launch_pad_L(Lsrc, s, st);
-    check_launch(h, "pad_L");
-    launch_quantize_L(s, st);
-    check_launch(h, "quantize_L");
+    if (keep64) {
+      launch_pad_L(Lsrc, s, st);
+      check_launch(h, "pad_L");
+    }
+    if (keep16) {
+      launch_quantize_L(Lsrc, s.n_aux, s.n_vc, s.n_aux, s, st);
+      check_launch(h, "quantize_L");
+    }
+    if (!keep64 || (flags & LGW_SYS_FP8)) make_fp8(h, s, Lsrc, s.n_aux, s.n_vc, s.n_aux);
     check_status(h);
   } catch (Fail &f) {
     for (void *p : allocs) cudaFree(p);
+    if (s.L8) cudaFree(s.L8);
+    if (s.L8t) cudaFree(s.L8t);
+    if (s.sL) cudaFree(s.sL);
     delete sys;
     return f.st;
   }
@@ -982,10 +1046,10 @@ lgw_status lgw_apply_casida(lgw_handle *h, const lgw_system *sys, int32_t n_vec,
       set_err(h, LGW_ERR_UNSUPPORTED, "tensor-core paths need an sm_103 device");
       throw Fail{LGW_ERR_UNSUPPORTED};
     }
-    if (fp8) {
-      Opts o8{};
-      o8.precision = LGW_FP8;
-      ensure_fp8(h, sys, o8);
+    {
+      Opts oa{};
+      oa.precision = precision;
+      ensure_copies(h, sys, oa);
     }
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     const double *Xd = in_dev(h, "ap_xin", X, (size_t)n_vec * s.n_vc);
@@ -1070,7 +1134,7 @@ lgw_status lgw_lanczos_coeffs(lgw_handle *h, const lgw_system *sys, const lgw_pr
     cudaStream_t st = h->stream;
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     Opts op = resolve_opts(h, o, s);
-    ensure_fp8(h, sys, op);
+    ensure_copies(h, sys, op);
     ProbView pv = check_problem(h, s, p);
     OutBuf<double> a, b, b0;
     OutBuf<int32_t> ke;
@@ -1146,7 +1210,7 @@ lgw_status lgw_sigma_c(lgw_handle *h, const lgw_system *sys, const lgw_problem *
     }
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     Opts op = resolve_opts(h, o, s);
-    ensure_fp8(h, sys, op);
+    ensure_copies(h, sys, op);
     ProbView pv = check_problem(h, s, p);
     double tacc[C_N] = {0};
     double *alpha = wsT<double>(h, "co_alpha", (size_t)std::max(1, pv.B) * op.k);
@@ -1238,7 +1302,7 @@ lgw_status lgw_sigma_c_batched(lgw_handle *h, int32_t n_sys, const lgw_system *c
       h->ws_prefix = "lane" + std::to_string(lane) + "/";
       const SysDev &s = systems[i]->s;
       Opts op = resolve_opts(h, o, s);
-      ensure_fp8(h, systems[i], op);
+      ensure_copies(h, systems[i], op);
       ProbView pv = check_problem(h, s, &problems[i]);
       double *alpha = wsT<double>(h, "co_alpha", (size_t)std::max(1, pv.B) * op.k);
       double *beta = wsT<double>(h, "co_beta", (size_t)std::max(1, pv.B) * op.k);
@@ -1308,7 +1372,7 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
     h->timing = false;
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     Opts op = resolve_opts(h, o, s);
-    ensure_fp8(h, sys, op);
+    ensure_copies(h, sys, op);
     // the adjoint contracts with the stored Krylov basis: FP64 (FP64 mode)
     // or the split float pair (BF16 mode with split arithmetic); the split
     // basis needs reorthogonalisation (otherwise the FP64 basis is kept)
@@ -1319,6 +1383,11 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
     if (op.k > adj_max_k()) {
       set_err(h, LGW_ERR_UNSUPPORTED, "k = %d above the %d-step limit of the adjoint", op.k,
               adj_max_k());
+      throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    if (!s.L64 || (op.precision != LGW_FP64 && !s.Ltb)) {
+      set_err(h, LGW_ERR_UNSUPPORTED,
+              "the adjoint needs the FP64 copy of L (and the BF16 copies for BF16/FP8)");
       throw Fail{LGW_ERR_UNSUPPORTED};
     }
     ProbView pv = check_problem(h, s, p);
@@ -1632,7 +1701,7 @@ extern "C" lgw_status lgw_sigma_from_coeffs_noalloc(lgw_handle *h, const lgw_sys
   cp.omega = p->omega;
   cp.delta = p->delta;
   cp.shift = p->static_shift;
-  launch_cf_grid(cp, jb, sigma, st);
+  launch_cf_grid(cp, jb, sigma, nullptr, 1, st);
   const int qp_iter = o->qp_max_iter > 0 ? o->qp_max_iter : 50;
   const double qp_tol = o->qp_tol > 0 ? o->qp_tol : 1e-10;
   launch_qp(cp, jb, sigma, qp_iter, qp_tol, e_qp, z_qp, h->d_status, st);

@@ -149,7 +149,8 @@ constexpr long long WAIT_CYCLES = 2000000000LL;
 // k_prep.cu
 void launch_pair_energies(const SysDev &s, cudaStream_t st);
 void launch_pad_L(const double *L, const SysDev &s, cudaStream_t st);
-void launch_quantize_L(const SysDev &s, cudaStream_t st);
+void launch_quantize_L(const double *src, int ld, int nr, int nc, const SysDev &s,
+                       cudaStream_t st);
 void launch_check_delta(const SysDev &s, unsigned *status, cudaStream_t st);
 
 // k_gemm_f64.cu : CUDA-core FP64 contractions
@@ -171,13 +172,14 @@ struct TcPlan;
 bool tc_available();
 bool tc_plan_enable_fp8(TcPlan *p, const uint8_t *L8t, const uint8_t *L8, const uint8_t *x8,
                         const uint8_t *y8, const float *ty);
-void launch_prepare_fp8(const SysDev &s, unsigned *colmax, uint8_t *L8, uint8_t *L8t, float *sL,
-                        cudaStream_t st);
+void launch_prepare_fp8(const double *src, int ld, int nr, int nc, const SysDev &s,
+                        unsigned *colmax, uint8_t *L8, uint8_t *L8t, float *sL, cudaStream_t st);
 void launch_quant_x8(const __nv_bfloat16 *xh, int Bs, int N, uint8_t *x8, float *sx,
                      cudaStream_t st);
 void launch_reduce_y_fp8(const float *Ypart, int splits, int Bs, int A, const float *sx,
                          const float *sL, uint8_t *y8, float *ty, float *yy, int n_yb,
                          cudaStream_t st);
+bool tc_plan_has_bf16(const TcPlan *p);
 bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, int *splits_out);
 TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *ypart,
                        __nv_bfloat16 *yh, int *splits_out, char *err, size_t errn);
@@ -196,7 +198,7 @@ void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaSt
 // V ~ L_hi M_hi + L_hi M_lo + L_lo M_hi (FP32 accumulation into vf [Bs][N]).
 // M rows [nvec][n_aux] (FP64, device); uses the plan's yh buffer for the
 // bf16 halves of M.
-void launch_coupling_tc(const TcPlan *p, const SysDev &s, const double *M, int nvec,
+bool launch_coupling_tc(const TcPlan *p, const SysDev &s, const double *M, int nvec,
                         float *vf, unsigned *status, cudaStream_t st);
 int tc_n_mt(const SysDev &s);
 
@@ -206,6 +208,7 @@ void launch_start_from_v(const VecCtx &c, const double *V, int ldv, int n_valid,
 void launch_start_from_vf(const VecCtx &c, const float *vf, cudaStream_t st);
 void launch_norm_partials(const VecCtx &c, const double *x, double *out, cudaStream_t st);
 void launch_normalize(const VecCtx &c, int j, int is_start, const double *norm, cudaStream_t st);
+void launch_assemble_w(const VecCtx &c, int j, const float *ucd, cudaStream_t st);
 void launch_alpha_axpy(const VecCtx &c, int j, cudaStream_t st);
 void launch_reduce_dots(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_update(const VecCtx &c, int j, int pass, cudaStream_t st);
@@ -243,7 +246,11 @@ struct CfProblem {
   double delta;
   const double *shift;          // device [n_t] or nullptr
 };
-void launch_cf_grid(const CfProblem &p, JacobiBufs jb, double *sigma, cudaStream_t st);
+int cf_slices(const CfProblem &p);
+// part: S * n_t * n_freq * 2 doubles of scratch, or NULL for one slice;
+// returns the number of kernels launched
+int launch_cf_grid(const CfProblem &p, JacobiBufs jb, double *sigma, double *part, int S,
+                   cudaStream_t st);
 void launch_qp(const CfProblem &p, JacobiBufs jb, const double *sigma, int max_iter, double tol,
                double *e_qp, double *z_qp, unsigned *status, cudaStream_t st);
 

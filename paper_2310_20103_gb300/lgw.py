@@ -37,7 +37,10 @@ class LgwError(RuntimeError):
 class lgw_system_desc(ctypes.Structure):
     _fields_ = [("n_v", ctypes.c_int32), ("n_c", ctypes.c_int32), ("n_aux", ctypes.c_int32),
                 ("eps", ctypes.c_void_p), ("L", ctypes.c_void_p),
-                ("kernel_factor", ctypes.c_double)]
+                ("kernel_factor", ctypes.c_double), ("flags", ctypes.c_int32)]
+
+
+SYS_NO_FP64, SYS_NO_BF16, SYS_FP8 = 1, 2, 4
 
 
 class lgw_problem(ctypes.Structure):
@@ -254,9 +257,9 @@ def lgw_destroy(h: Handle) -> None:
 
 
 def lgw_prepare_system(h: Handle, n_v: int, n_c: int, n_aux: int, eps, L,
-                       kernel_factor: float = 4.0) -> System:
+                       kernel_factor: float = 4.0, flags: int = 0) -> System:
     d = lgw_system_desc(int(n_v), int(n_c), int(n_aux), _ptr(eps, "f64"), _ptr(L, "f64"),
-                        float(kernel_factor))
+                        float(kernel_factor), int(flags))
     out = ctypes.c_void_p()
     _check(h, load_library().lgw_prepare_system(h.ptr, ctypes.byref(d), ctypes.byref(out)))
     return System(out.value, h, n_v, n_c, n_aux, kernel_factor)

@@ -62,3 +62,43 @@ def test_binding_struct_layouts_match_header():
                        r"b_sub|k_min|k_max|n_second_pass|gpu_launches|gemm1_splits)\b", body)
     assert [f for f, _ in L.lgw_report._fields_] == names
     assert ctypes.sizeof(L.lgw_options) == 48
+
+
+def test_binding_offsets_match_c_compiler(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the header's struct, and the binding's enum
+    values equal the header's."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2310_20103_gb300 import lgw as L
+    structs = {"lgw_system_desc": L.lgw_system_desc, "lgw_problem": L.lgw_problem,
+               "lgw_options": L.lgw_options, "lgw_report": L.lgw_report}
+    enums = {"LGW_FP64": L.PRECISION["fp64"], "LGW_BF16": L.PRECISION["bf16"],
+             "LGW_FP8": L.PRECISION["fp8"], "LGW_REORTH_NONE": L.REORTH["none"],
+             "LGW_REORTH_CGS2": L.REORTH["cgs2"], "LGW_REORTH_CGS1K": L.REORTH["cgs1k"],
+             "LGW_RA_AUTO": L.REORTH_ARITH["auto"], "LGW_RA_FP64": L.REORTH_ARITH["fp64"],
+             "LGW_RA_SPLIT": L.REORTH_ARITH["split"], "LGW_RA_SPLIT32": L.REORTH_ARITH["split32"],
+             "LGW_SYS_NO_FP64": L.SYS_NO_FP64, "LGW_SYS_NO_BF16": L.SYS_NO_BF16,
+             "LGW_SYS_FP8": L.SYS_FP8}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lgw.h"', "int main(void) {"]
+    expect = []
+    for name, cls in structs.items():
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        expect.append(ctypes.sizeof(cls))
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {f}));')
+            expect.append(getattr(cls, f).offset)
+    for name, v in enums.items():
+        lines.append(f'  printf("%d\\n", (int){name});')
+        expect.append(v)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got == expect

@@ -139,3 +139,77 @@ def test_fp8_path_qp_energies(L, handle, wl_name, bound_mev):
     d = np.abs(e["fp8"] - e["fp64"]).max() * 1e3
     print(f"{wl_name}: |E_fp8 - E_fp64| = {d:.3e} meV")
     assert d <= bound_mev
+
+
+def test_system_flags(L, handle):
+    """Copies of L per LGW_SYS_* flag: a system without the FP64 copy (E4M3
+    copies made at preparation, straight from the caller's L) gives the same
+    BF16 and FP8 results as a full system, and refuses FP64 requests and the
+    adjoint; a system without the BF16 copies gives the same FP64 results,
+    refuses BF16, and runs FP8 with FP64 start vectors."""
+    wl = gi.custom(16, 96, 256, 2, 32, 100, 9, k=40)
+    prob = L.Problem(targets=_t(wl.targets), m_idx=_t(wl.m_idx), omega=_t(wl.omega),
+                     delta=wl.delta, M=_t(wl.M))
+
+    def run(flags, prec):
+        s = L.lgw_prepare_system(handle, wl.n_v, wl.n_c, wl.n_aux, _t(wl.eps), _t(wl.L),
+                                 flags=flags)
+        try:
+            sig = torch.empty(wl.n_t, wl.omega.size, 2, dtype=torch.float64, device=DEV)
+            e = torch.empty(wl.n_t, dtype=torch.float64, device=DEV)
+            L.lgw_sigma_c(handle, s, prob, L.Options(k=40, precision=prec, reorth="cgs2"), sig, e)
+            torch.cuda.synchronize()
+            return sig.cpu().numpy(), e.cpu().numpy()
+        finally:
+            L.lgw_release_system(s)
+
+    full = {p: run(0, p) for p in ("fp64", "bf16", "fp8")}
+    lean = L.SYS_NO_FP64 | L.SYS_FP8
+    for p in ("bf16", "fp8"):
+        got = run(lean, p)
+        np.testing.assert_array_equal(got[0], full[p][0])
+    with pytest.raises(L.LgwError) as ei:
+        run(lean, "fp64")
+    assert ei.value.status == 8
+    s = L.lgw_prepare_system(handle, wl.n_v, wl.n_c, wl.n_aux, _t(wl.eps), _t(wl.L), flags=lean)
+    try:
+        with pytest.raises(L.LgwError) as ei:
+            L.lgw_sigma_c_backward(handle, s, prob, L.Options(k=40, precision="bf16"),
+                                   _t(np.ones(wl.n_t)))
+        assert ei.value.status == 8
+    finally:
+        L.lgw_release_system(s)
+    np.testing.assert_array_equal(run(L.SYS_NO_BF16, "fp64")[0], full["fp64"][0])
+    with pytest.raises(L.LgwError) as ei:
+        run(L.SYS_NO_BF16, "bf16")
+    assert ei.value.status == 8
+    e8 = run(L.SYS_NO_BF16, "fp8")[1]
+    assert np.abs(e8 - full["fp8"][1]).max() < 1e-8     # start vectors by FP64 instead of split BF16
+    with pytest.raises(L.LgwError) as ei:
+        run(L.SYS_NO_FP64 | L.SYS_NO_BF16, "fp8")
+    assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("prec,bound_mev", [("bf16", 0.1), ("fp8", 1.0)])
+def test_tensor_core_path_without_reorth(L, handle, prec, bound_mev):
+    """Tensor-core contractions without reorthogonalisation (the large-system
+    mode: store-only FP32 contraction epilogue, FP64 assembly of w and alpha
+    on the vector pass) against the oracle's plain FP64 recurrence, k 24 on
+    the tiny system and on a ragged shape (N_vc = 13*347, N_aux = 300)."""
+    for wl in (gi.tiny(k=24), gi.make_workload("rg", 13, 347, 300, [11, 12, 13],
+                                               list(range(21)), 120, 3, k=24, aux_scaled=True)):
+        ref, poles, _ = O.sigma_lanczos(wl, k=24, reorth=False)
+        Er, _ = O.solve_all_qp(wl, poles)
+        s = L.lgw_prepare_system(handle, wl.n_v, wl.n_c, wl.n_aux, _t(wl.eps), _t(wl.L))
+        prob = L.Problem(targets=_t(wl.targets), m_idx=_t(wl.m_idx), omega=_t(wl.omega),
+                         delta=wl.delta, M=_t(wl.M))
+        try:
+            sig = torch.empty(wl.n_t, wl.omega.size, 2, dtype=torch.float64, device=DEV)
+            e = torch.empty(wl.n_t, dtype=torch.float64, device=DEV)
+            L.lgw_sigma_c(handle, s, prob, L.Options(k=24, precision=prec, reorth="none"), sig, e)
+            torch.cuda.synchronize()
+        finally:
+            L.lgw_release_system(s)
+        d = np.abs(e.cpu().numpy() - Er).max() * 1e3
+        print(f"{wl.name} {prec} no-reorth: |dE| = {d:.3e} meV")
+        assert d <= bound_mev
