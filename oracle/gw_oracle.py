@@ -37,7 +37,8 @@ __all__ = [
     "closed_form_poles", "lanczos", "lanczos_poles", "sigma_from_poles",
     "dsigma_from_poles", "sigma_closed_form", "sigma_lanczos", "qp_solve",
     "solve_all_qp", "qp_gradient", "qp_energies_closed_form", "qp_gradient_closed_form",
-    "qp_gradient_lanczos",
+    "qp_gradient_lanczos", "chebyshev_sqrt", "chebyshev_eval", "apply_poly",
+    "sigma_poly_lanczos", "haydock",
 ]
 
 
@@ -435,3 +436,108 @@ def qp_gradient_closed_form(wl, dE):
     E, Z = qp_energies_closed_form(wl)
     theta, Y = np.linalg.eigh(casida_matrix(wl.eps, wl.n_v, wl.L, wl.kernel_factor))
     return qp_gradient(wl, dE, E, Z, lambda v: (Y, theta))
+
+
+# --------------------------------------------------------------------------
+# Polynomial variant: Lanczos on D = p_g(C) ~ C^1/2 (paper text after Eq. 12,
+# Eq. 13-14).  p_g fits sqrt on the spectral interval [lo, hi] of C; here it
+# is the degree-g Chebyshev interpolant (reading: the paper's monomial sum is
+# the same polynomial, evaluated stably in the Chebyshev basis).
+# --------------------------------------------------------------------------
+def chebyshev_sqrt(lo, hi, g):
+    """Coefficients c_0..c_g with p(x) = sum_k c_k T_k(t), t = (2x - hi - lo) /
+    (hi - lo), interpolating sqrt at the g+1 Chebyshev points of the first
+    kind t_j = cos(pi (j + 1/2) / (g + 1))."""
+    n = g + 1
+    j = np.arange(n)
+    tj = np.cos(np.pi * (j + 0.5) / n)
+    fj = np.sqrt(0.5 * (hi + lo) + 0.5 * (hi - lo) * tj)
+    c = np.empty(n)
+    for k in range(n):
+        c[k] = 2.0 / n * np.sum(fj * np.cos(k * np.pi * (j + 0.5) / n))
+    c[0] *= 0.5
+    return c
+
+
+def chebyshev_eval(c, lo, hi, x):
+    """p(x) = sum_k c_k T_k(t) by the three-term recurrence of T_k."""
+    t = (2.0 * np.asarray(x, dtype=np.float64) - hi - lo) / (hi - lo)
+    tk_1, tk = np.ones_like(t), t
+    out = c[0] * tk_1
+    if len(c) > 1:
+        out = out + c[1] * tk
+    for k in range(2, len(c)):
+        tk_1, tk = tk, 2.0 * t * tk - tk_1
+        out = out + c[k] * tk
+    return out
+
+
+def apply_poly(apply_op, V, c, lo, hi):
+    """p(C) V for the Chebyshev series c on [lo, hi], with C given by apply_op
+    (rows of V are vectors): Clenshaw's recurrence in S = (2C - (hi+lo)) /
+    (hi - lo),  b_k = c_k V + 2 S b_{k+1} - b_{k+2},  p(C) V = c_0 V + S b_1 - b_2."""
+    V = np.atleast_2d(np.asarray(V, dtype=np.float64))
+    g = len(c) - 1
+    a_s, b_s = 2.0 / (hi - lo), -(hi + lo) / (hi - lo)
+
+    def S(X):
+        return a_s * apply_op(X) + b_s * X
+
+    b1 = np.zeros_like(V)
+    b2 = np.zeros_like(V)
+    for k in range(g, 0, -1):
+        b1, b2 = c[k] * V + 2.0 * S(b1) - b2, b1
+    return c[0] * V + S(b1) - b2
+
+
+def haydock(alpha, beta, beta0, k_eff, zeta):
+    """<P|(zeta - T)^-1|P> = beta0^2 / (zeta - a_0 - b_1^2 / (zeta - a_1 - ...))
+    for the tridiagonal (alpha, beta) of one start vector (Eq. 14), at
+    complex points zeta (array)."""
+    ke = int(k_eff)
+    zeta = np.asarray(zeta, dtype=np.complex128)
+    if ke == 0:
+        return np.zeros_like(zeta)
+    t = zeta - alpha[ke - 1]
+    for i in range(ke - 2, -1, -1):
+        t = zeta - alpha[i] - beta[i] ** 2 / t
+    return beta0 ** 2 / t
+
+
+def sigma_poly_lanczos(wl, g, lo, hi, k=None, reorth=True):
+    """Sigma_t(omega_f) with Lanczos on D = p_g(C) from each |P_tm> and
+    Sigma_tm(omega) = (1/z) <P|D^-1 - (D + eta z)^-1|P>
+                    = (1/z) [G(-eta z) - G(0)],  G(zeta) = <P|(zeta - D_L)^-1|P>,
+    z = omega - eps_m - i eta delta (the resolvent form after Eq. 12 and
+    Eq. 14).  Returns (sigma [n_t, n_freq], pole lists of the equivalent Gauss
+    rule, coefficients)."""
+    k = wl.k if k is None else k
+    c = chebyshev_sqrt(lo, hi, g)
+    b = start_vectors(wl.eps, wl.n_v, coupling_vectors(wl.L, wl.M)).reshape(wl.n_t * wl.n_m, -1)
+    coeffs = lanczos(lambda X: apply_poly(
+        lambda Y: apply_casida(wl.eps, wl.n_v, wl.L, Y, wl.kernel_factor), X, c, lo, hi),
+        b, k, reorth=reorth)
+    alpha, beta, beta0, k_eff = coeffs
+    eta_all = occupation_sign(wl.m_idx, wl.n_v)
+    sig = np.zeros((wl.n_t, wl.omega.size), dtype=np.complex128)
+    poles = []
+    for ti in range(wl.n_t):
+        P, Wt, E = [], [], []
+        for mi, m in enumerate(wl.m_idx):
+            v = ti * wl.n_m + mi
+            eta = eta_all[mi]
+            z = wl.omega - wl.eps[m] - 1j * eta * wl.delta
+            G0 = haydock(alpha[v], beta[v], beta0[v], k_eff[v], np.array([0.0]))[0]
+            sig[ti] += (haydock(alpha[v], beta[v], beta0[v], k_eff[v], -eta * z) - G0) / z
+            # the same sum as poles: nodes Om_j of D_L, weights beta0^2 u_1j^2
+            ke = int(k_eff[v])
+            if ke:
+                T = np.diag(alpha[v, :ke])
+                if ke > 1:
+                    T += np.diag(beta[v, : ke - 1], 1) + np.diag(beta[v, : ke - 1], -1)
+                Om, U = np.linalg.eigh(T)
+                P.append(wl.eps[m] - eta * Om)
+                Wt.append(beta0[v] ** 2 * U[0] ** 2 / Om)
+                E.append(np.full(ke, eta))
+        poles.append((np.concatenate(P), np.concatenate(Wt), np.concatenate(E)))
+    return sig, poles, coeffs
