@@ -276,6 +276,30 @@ lgw_status lgw_sigma_c(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
                        const lgw_options *o, double *sigma, double *e_qp, double *z_qp,
                        lgw_report *rep);
 
+/* The paper's polynomial form (text after Eq. 12): D = p_g(C) ~ C^1/2 with
+ * p_g the degree-g Chebyshev interpolant of sqrt at the g+1 Chebyshev points
+ * of the first kind on [x_lo, x_hi] (the spectral interval of C: x_lo <=
+ * lambda_min, x_hi >= lambda_max; eps_c - eps_v bounds lambda_min from
+ * below), Lanczos on D from each |P_tm> (Eq. 13; D applied by Clenshaw's
+ * recurrence, g applications of C per step, FP64 Krylov basis), and
+ * Sigma_tm(omega) = (1/z) <P|D^-1 - (D + eta z)^-1|P> from two Haydock
+ * continued fractions of D's tridiagonal (Eq. 14), z = omega - eps_m - i eta
+ * delta.  Outputs as lgw_sigma_c; the report's gemm_flops count g products
+ * per step. */
+typedef struct {
+  int32_t g;           /* degree, 1..256 */
+  double x_lo, x_hi;   /* 0 < x_lo < x_hi */
+} lgw_poly;
+
+lgw_status lgw_sigma_c_poly(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                            const lgw_options *o, const lgw_poly *poly, double *sigma,
+                            double *e_qp, double *z_qp, lgw_report *rep);
+
+/* Tridiagonals of D = p_g(C) only (as lgw_lanczos_coeffs). */
+lgw_status lgw_lanczos_coeffs_poly(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                                   const lgw_options *o, const lgw_poly *poly, double *alpha,
+                                   double *beta, double *beta0, int32_t *k_eff);
+
 /* Several independent systems of uneven size in one call; sigma[i], e_qp[i]
  * and z_qp[i] (z_qp may be NULL) have the shapes of lgw_sigma_c for
  * problems[i].  The systems run concurrently on up to four internal streams

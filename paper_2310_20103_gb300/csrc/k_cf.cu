@@ -71,8 +71,17 @@ __global__ void k_cf_grid(CfProblem p, JacobiBufs jb, double *__restrict__ out, 
     cplx G, dG;
     cf_eval<false>(jb.a + (size_t)v * p.k, jb.b2 + (size_t)v * p.k, n, jb.w0[v], zr, p.delta, G,
                    dG);
-    sr -= eta * G.re;
-    si -= eta * G.im;
+    if (jb.g0 == nullptr) {
+      sr -= eta * G.re;
+      si -= eta * G.im;
+    } else {
+      // (G(zeta) - G(0)) / z,  z = omega - eps_m - i eta delta
+      const double xr = om - p.eps[m], xi = -eta * p.delta;
+      const double inv = 1.0 / fma(xr, xr, xi * xi);
+      const double nr = G.re - jb.g0[v], ni = G.im;
+      sr += (nr * xr + ni * xi) * inv;
+      si += (ni * xr - nr * xi) * inv;
+    }
   }
   const size_t o = (((size_t)sl * p.n_t + ti) * p.n_freq + f) * 2;
   out[o] = sr;
@@ -103,10 +112,24 @@ __device__ void sigma_at(const CfProblem &p, const JacobiBufs &jb, int ti, doubl
     cplx G, dG;
     cf_eval<true>(jb.a + (size_t)v * p.k, jb.b2 + (size_t)v * p.k, n, jb.w0[v],
                   -eta * (E - p.eps[m]), p.delta, G, dG);
-    sr -= eta * G.re;
-    si -= eta * G.im;
-    dr += dG.re;
-    di += dG.im;
+    if (jb.g0 == nullptr) {
+      sr -= eta * G.re;
+      si -= eta * G.im;
+      dr += dG.re;
+      di += dG.im;
+    } else {
+      // S = (G(zeta) - G(0)) / z, zeta = -eta z:
+      // dS/dz = -eta G'(zeta) / z - S / z
+      const double xr = E - p.eps[m], xi = -eta * p.delta;
+      const double inv = 1.0 / fma(xr, xr, xi * xi);
+      const double nr = G.re - jb.g0[v], ni = G.im;
+      const double qr = (nr * xr + ni * xi) * inv, qi = (ni * xr - nr * xi) * inv;
+      sr += qr;
+      si += qi;
+      const double gr = -eta * dG.re - qr, gi = -eta * dG.im - qi;
+      dr += (gr * xr + gi * xi) * inv;
+      di += (gi * xr - gr * xi) * inv;
+    }
   }
   S.re = warp_sum(sr);
   S.im = warp_sum(si);

@@ -451,6 +451,37 @@ ProbView check_problem(lgw_handle *h, const SysDev &s, const lgw_problem *p) {
 // Lanczos over all start vectors, sub-batch by sub-batch.
 // alpha/beta [B][k], beta0 [B], k_eff [B] are device arrays.
 // ---------------------------------------------------------------------------
+// Polynomial operator D = p_g(C) (the paper's form after Eq. 12): the
+// Chebyshev interpolant of sqrt at the g+1 points of the first kind on
+// [lo, hi], applied by Clenshaw's recurrence in S = a_s C + b_s I.
+struct PolyOp {
+  int g;
+  double lo, hi, as, bs;
+  std::vector<double> c;   // c_0 .. c_g
+};
+
+PolyOp make_poly(int g, double lo, double hi) {
+  PolyOp p;
+  p.g = g;
+  p.lo = lo;
+  p.hi = hi;
+  p.as = 2.0 / (hi - lo);
+  p.bs = -(hi + lo) / (hi - lo);
+  const int n = g + 1;
+  const double pi = 3.14159265358979323846;
+  std::vector<double> f(n);
+  for (int j = 0; j < n; ++j)
+    f[j] = std::sqrt(0.5 * (hi + lo) + 0.5 * (hi - lo) * std::cos(pi * (j + 0.5) / n));
+  p.c.assign(n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc += f[j] * std::cos(k * pi * (j + 0.5) / n);
+    p.c[k] = 2.0 / n * acc;
+  }
+  p.c[0] *= 0.5;
+  return p;
+}
+
 // keep_basis stores all k + 1 FP64 basis vectors of a sub-batch (slot j of
 // sub-batch row b at basis + (j * Bs + b) * N) whatever the reorthogonalisation
 // mode; after_sub, if given, runs once each sub-batch's recurrence is done.
@@ -458,7 +489,8 @@ using SubBatchHook = std::function<void(const VecCtx &)>;
 
 void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o, double *alpha,
                  double *beta, double *beta0, int *k_eff, lgw_report *rep, double *tacc,
-                 bool keep_basis = false, const SubBatchHook *after_sub = nullptr) {
+                 bool keep_basis = false, const SubBatchHook *after_sub = nullptr,
+                 const PolyOp *poly = nullptr) {
   // a reference: a graph capture redirects the launches to the capture stream
   cudaStream_t &st = h->stream;
   const int B = pv.B;
@@ -514,7 +546,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   // alpha partials: per 2048-element chunk (tensor cores without
   // reorthogonalisation), per GEMM2 tile otherwise
   const bool tc_plain = tc && !reorth;
-  c.n_mt = tc_plain ? nchunks : (tc ? tc_n_mt(s) : N / F64_TILE);
+  c.n_mt = (tc_plain || poly) ? nchunks : (tc ? tc_n_mt(s) : N / F64_TILE);
   c.alpha_part = wsT<double>(h, "alpha_part", (size_t)c.n_mt * Bs);
   c.dot_part = reorth ? wsT<double>(h, "dot_part", (size_t)Bs * nchunks * kmax1) : nullptr;
   c.h = reorth ? wsT<double>(h, "hcoef", (size_t)Bs * kmax1) : nullptr;
@@ -592,6 +624,40 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
     bool v;
     ~TimingRestore() { h->timing = v; }
   } timing_restore{h, timing_saved};
+  // Clenshaw buffers of the polynomial operator
+  double *pb[3] = {nullptr, nullptr, nullptr};
+  double *pT = nullptr;
+  if (poly) {
+    for (int i = 0; i < 3; ++i)
+      pb[i] = wsT<double>(h, "poly_b" + std::to_string(i), (size_t)Bs * N);
+    if (!tc) pT = wsT<double>(h, "poly_t", (size_t)Bs * N);
+  }
+  // C b for the polynomial operator: FP64 product into pT, or the tensor
+  // cores from c.xh = bf16(Delta^1/2 b) into ucd_buf
+  auto apply_c = [&](const double *bsrc) {
+    if (tc) {
+      if (fp8) {
+        launch_quant_x8(c.xh, Bs, N, x8, sx, st);
+        check_launch(h, "quant_x8");
+      }
+      launch_gemm1_tc(plan, h->d_status, st);
+      check_launch(h, "gemm1_tc");
+      if (fp8)
+        launch_reduce_y_fp8(Yp32, splits_tc, Bs, s.A, sx, s.sL, y8, ty, nullptr, 1, st);
+      else
+        launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, nullptr, st);
+      check_launch(h, "reduce_y");
+      launch_gemm2_tc_split(plan, ucd_buf, h->d_status, st);
+      check_launch(h, "gemm2_tc");
+    } else {
+      launch_gemm1_f64(s, bsrc, Bs, Yp64, splits64, st);
+      check_launch(h, "gemm1_f64");
+      launch_reduce_y_f64(Yp64, splits64, Bs, s.A, Y64, st);
+      check_launch(h, "reduce_y_f64");
+      launch_gemm2_f64(s, Y64, Bs, EPI_APPLY, bsrc, nullptr, nullptr, pT, nullptr, st);
+      check_launch(h, "gemm2_f64");
+    }
+  };
   Timer tm(h);
   int nsub = 0;
   for (int vec0 = 0; vec0 < B; vec0 += nsub_req, ++nsub) {
@@ -641,7 +707,46 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
         const double *qp = j > 0 ? slot_ptr(c, j - 1) : nullptr;
         // ---- C q_j through the two contractions (Eq. 4) ----
         tm.mark(C_GEMM1);
-        if (tc) {
+        if (poly) {
+          // D q_j = p_g(C) q_j by Clenshaw; w = D q_j - beta_j q_{j-1}
+          PolyStep ps{};
+          ps.N = N;
+          ps.q = qj;
+          ps.Delta2 = s.Delta2;
+          ps.dsqf = s.dsqf;
+          ps.as = poly->as;
+          ps.bs = poly->bs;
+          ps.xh = tc ? c.xh : nullptr;
+          ps.ck = poly->c[poly->g];
+          ps.out = pb[0];
+          tm.mark(C_UPDATE);
+          launch_cheb_step(ps, nchunks, Bs, st);
+          check_launch(h, "cheb_step");
+          int i1 = 0, i2 = -1;
+          for (int kk = poly->g - 1; kk >= 0; --kk) {
+            tm.mark(C_GEMM1);
+            apply_c(pb[i1]);
+            tm.mark(C_UPDATE);
+            ps.b1 = pb[i1];
+            ps.b2 = i2 >= 0 ? pb[i2] : nullptr;
+            ps.T = tc ? nullptr : pT;
+            ps.ucd = tc ? ucd_buf : nullptr;
+            ps.ck = poly->c[kk];
+            if (kk > 0) {
+              const int io = (i1 + 1) % 3;
+              ps.out = pb[io];
+              launch_cheb_step(ps, nchunks, Bs, st);
+              check_launch(h, "cheb_step");
+              i2 = i1;
+              i1 = io;
+            } else {
+              ps.out = nullptr;
+              ps.xh = nullptr;
+              launch_cheb_final(ps, qp, c.betaj, c.w, c.alpha_part, nchunks, Bs, st);
+              check_launch(h, "cheb_final");
+            }
+          }
+        } else if (tc) {
           if (fp8) {
             launch_quant_x8(c.xh, Bs, N, x8, sx, st);
             check_launch(h, "quant_x8");
@@ -752,7 +857,8 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
 
 void run_sigma(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o,
                const double *alpha, const double *beta, const double *beta0, const int *k_eff,
-               double *sigma, double *e_qp, double *z_qp, lgw_report *rep, double *tacc) {
+               double *sigma, double *e_qp, double *z_qp, lgw_report *rep, double *tacc,
+               bool poly = false) {
   cudaStream_t st = h->stream;
   const int B = pv.B, k = o.k;
   Timer tm(h);
@@ -768,7 +874,13 @@ void run_sigma(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o
   std::memcpy(&bigbits, &big, sizeof big);
   LGW_TRY_CUDA(h, cudaMemcpyAsync(mt, &bigbits, sizeof bigbits, cudaMemcpyHostToDevice, st));
   tm.mark(C_SPEC);
-  if (B > 0) {
+  if (B > 0 && poly) {
+    // the fractions run on D = p_g(C)'s own tridiagonal (no spectral map)
+    jb.a = const_cast<double *>(alpha);
+    jb.g0 = wsT<double>(h, "jac_g0", (size_t)B);
+    launch_poly_prep(alpha, beta, beta0, k_eff, B, k, jb, h->d_status, st);
+    check_launch(h, "poly_prep");
+  } else if (B > 0) {
     launch_spectral_impl(alpha, beta, beta0, k_eff, B, k, jb, scratch, mt, h->d_status, st);
     check_launch(h, "spectral");
   }
@@ -852,6 +964,84 @@ lgw_status guard_handle(lgw_handle *h) {
 // ===========================================================================
 // exported C ABI
 // ===========================================================================
+namespace {
+const PolyOp *poly_arg(lgw_handle *h, const lgw_poly *pp, PolyOp &store) {
+  if (!pp) return nullptr;
+  if (pp->g < 1 || pp->g > 256 || !(pp->x_lo > 0.0) || !(pp->x_hi > pp->x_lo)) {
+    set_err(h, LGW_ERR_ARG, "polynomial: need 1 <= g <= 256 and 0 < x_lo < x_hi");
+    throw Fail{LGW_ERR_ARG};
+  }
+  store = make_poly(pp->g, pp->x_lo, pp->x_hi);
+  return &store;
+}
+
+lgw_status sigma_c_impl(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                        const lgw_options *o, const lgw_poly *pp, double *sigma, double *e_qp,
+                        double *z_qp, lgw_report *rep) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!sys || sys->h != h) return set_err(h, LGW_ERR_ARG, "bad system handle");
+  try {
+    const SysDev &s = sys->s;
+    cudaStream_t st = h->stream;
+    h->launches = 0;
+    h->ev_used = 0;
+    h->timing = rep != nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (rep) {
+      std::memset(rep, 0, sizeof *rep);
+      LGW_TRY_CUDA(h, cudaEventCreate(&t0));
+      LGW_TRY_CUDA(h, cudaEventCreate(&t1));
+      LGW_TRY_CUDA(h, cudaEventRecord(t0, st));
+    }
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    Opts op = resolve_opts(h, o, s);
+    ensure_copies(h, sys, op);
+    PolyOp pstore;
+    const PolyOp *poly = poly_arg(h, pp, pstore);
+    if (poly) {
+      // Lanczos on D = p_g(C) keeps the FP64 basis
+      op.split = 0;
+      op.split32 = 0;
+    }
+    ProbView pv = check_problem(h, s, p);
+    double tacc[C_N] = {0};
+    double *alpha = wsT<double>(h, "co_alpha", (size_t)std::max(1, pv.B) * op.k);
+    double *beta = wsT<double>(h, "co_beta", (size_t)std::max(1, pv.B) * op.k);
+    double *beta0 = wsT<double>(h, "co_beta0", (size_t)std::max(1, pv.B));
+    int *ke = wsT<int>(h, "co_keff", (size_t)std::max(1, pv.B));
+    OutBuf<double> sg, e, z;
+    sg.init(h, "out_sigma", sigma, (size_t)pv.n_t * pv.n_freq * 2);
+    e.init(h, "out_eqp", e_qp, (size_t)pv.n_t);
+    z.init(h, "out_zqp", z_qp, (size_t)pv.n_t);
+    run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, rep, tacc, false, nullptr, poly);
+    run_sigma(h, s, pv, op, alpha, beta, beta0, ke, sg.dev, e.dev, z.dev, rep, tacc,
+              poly != nullptr);
+    sg.finish(h);
+    e.finish(h);
+    z.finish(h);
+    if (rep) {
+      LGW_TRY_CUDA(h, cudaEventRecord(t1, st));
+      LGW_TRY_CUDA(h, cudaEventSynchronize(t1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      fill_report_common(h, s, pv, op, ke, rep, tacc);
+      if (poly) rep->gemm_flops *= poly->g;
+      rep->ms_total = ms;
+      rep->gpu_launches = h->launches;
+    }
+    check_status(h);
+    h->timing = false;
+  } catch (Fail &f) {
+    h->timing = false;
+    return f.st;
+  }
+  return LGW_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char *lgw_status_string(lgw_status s) {
@@ -1192,55 +1382,49 @@ lgw_status lgw_sigma_from_coeffs(lgw_handle *h, const lgw_system *sys, const lgw
 lgw_status lgw_sigma_c(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
                        const lgw_options *o, double *sigma, double *e_qp, double *z_qp,
                        lgw_report *rep) {
+  return sigma_c_impl(h, sys, p, o, nullptr, sigma, e_qp, z_qp, rep);
+}
+
+lgw_status lgw_sigma_c_poly(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                            const lgw_options *o, const lgw_poly *poly, double *sigma,
+                            double *e_qp, double *z_qp, lgw_report *rep) {
+  if (!poly) return h ? set_err(h, LGW_ERR_ARG, "polynomial descriptor is NULL") : LGW_ERR_ARG;
+  return sigma_c_impl(h, sys, p, o, poly, sigma, e_qp, z_qp, rep);
+}
+
+lgw_status lgw_lanczos_coeffs_poly(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                                   const lgw_options *o, const lgw_poly *pp, double *alpha,
+                                   double *beta, double *beta0, int32_t *k_eff) {
   lgw_status g = guard_handle(h);
   if (g != LGW_OK) return g;
-  if (!sys || sys->h != h) return set_err(h, LGW_ERR_ARG, "bad system handle");
+  if (!sys || sys->h != h || !pp || !alpha || !beta || !beta0 || !k_eff)
+    return set_err(h, LGW_ERR_ARG, "NULL argument to lgw_lanczos_coeffs_poly");
   try {
     const SysDev &s = sys->s;
     cudaStream_t st = h->stream;
-    h->launches = 0;
-    h->ev_used = 0;
-    h->timing = rep != nullptr;
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
-    if (rep) {
-      std::memset(rep, 0, sizeof *rep);
-      LGW_TRY_CUDA(h, cudaEventCreate(&t0));
-      LGW_TRY_CUDA(h, cudaEventCreate(&t1));
-      LGW_TRY_CUDA(h, cudaEventRecord(t0, st));
-    }
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     Opts op = resolve_opts(h, o, s);
     ensure_copies(h, sys, op);
+    PolyOp pstore;
+    const PolyOp *poly = poly_arg(h, pp, pstore);
+    op.split = 0;
+    op.split32 = 0;
     ProbView pv = check_problem(h, s, p);
-    double tacc[C_N] = {0};
-    double *alpha = wsT<double>(h, "co_alpha", (size_t)std::max(1, pv.B) * op.k);
-    double *beta = wsT<double>(h, "co_beta", (size_t)std::max(1, pv.B) * op.k);
-    double *beta0 = wsT<double>(h, "co_beta0", (size_t)std::max(1, pv.B));
-    int *ke = wsT<int>(h, "co_keff", (size_t)std::max(1, pv.B));
-    OutBuf<double> sg, e, z;
-    sg.init(h, "out_sigma", sigma, (size_t)pv.n_t * pv.n_freq * 2);
-    e.init(h, "out_eqp", e_qp, (size_t)pv.n_t);
-    z.init(h, "out_zqp", z_qp, (size_t)pv.n_t);
-    run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, rep, tacc);
-    run_sigma(h, s, pv, op, alpha, beta, beta0, ke, sg.dev, e.dev, z.dev, rep, tacc);
-    sg.finish(h);
-    e.finish(h);
-    z.finish(h);
-    if (rep) {
-      LGW_TRY_CUDA(h, cudaEventRecord(t1, st));
-      LGW_TRY_CUDA(h, cudaEventSynchronize(t1));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, t0, t1);
-      cudaEventDestroy(t0);
-      cudaEventDestroy(t1);
-      fill_report_common(h, s, pv, op, ke, rep, tacc);
-      rep->ms_total = ms;
-      rep->gpu_launches = h->launches;
-    }
+    OutBuf<double> a, b, b0;
+    OutBuf<int32_t> ke;
+    a.init(h, "out_alpha", alpha, (size_t)pv.B * op.k);
+    b.init(h, "out_beta", beta, (size_t)pv.B * op.k);
+    b0.init(h, "out_beta0", beta0, (size_t)pv.B);
+    ke.init(h, "out_keff", k_eff, (size_t)pv.B);
+    h->timing = false;
+    run_lanczos(h, s, pv, op, a.dev, b.dev, b0.dev, ke.dev, nullptr, nullptr, false, nullptr,
+                poly);
+    a.finish(h);
+    b.finish(h);
+    b0.finish(h);
+    ke.finish(h);
     check_status(h);
-    h->timing = false;
   } catch (Fail &f) {
-    h->timing = false;
     return f.st;
   }
   return LGW_OK;

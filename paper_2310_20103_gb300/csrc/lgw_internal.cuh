@@ -229,7 +229,31 @@ struct JacobiBufs {
   double *b2;   // [B][k]  b2[i][j] = b_{j+1}^2 couples j and j+1
   double *w0;   // [B]     total weight (zeroth moment)
   int *n;       // [B]     depth
+  // polynomial variant: G(0) per vector, and the fractions belong to
+  // D = p_g(C) (Sigma_tm = (G(zeta) - G(0)) / z); NULL for the Omega-space
+  // fractions of the spectral map (Sigma_tm = -eta G(zeta))
+  double *g0 = nullptr;
 };
+
+// k_poly.cu : one vector pass of Clenshaw's recurrence for p_g(C) q
+struct PolyStep {
+  int N;
+  const double *q;        // [Bs][N] the Lanczos vector q_j
+  const double *b1, *b2;  // b_{k+1}, b_{k+2} or NULL
+  const double *T;        // C b1 in FP64, or NULL
+  const float *ucd;       // c_K Delta^1/2 (L y) of b1 in FP32 (with T == NULL)
+  const double *Delta2;
+  const float *dsqf;
+  double ck, as, bs;      // c_k, a_s, b_s
+  double *out;            // b_k
+  __nv_bfloat16 *xh;      // bf16(Delta^1/2 b_k) or NULL
+};
+void launch_cheb_step(const PolyStep &p, int nchunks, int Bs, cudaStream_t st);
+void launch_cheb_final(const PolyStep &p, const double *qprev, const double *betaj, double *w,
+                       double *alpha_part, int nchunks, int Bs, cudaStream_t st);
+void launch_poly_prep(const double *alpha, const double *beta, const double *beta0,
+                      const int *k_eff, int B, int k, JacobiBufs jb, unsigned *status,
+                      cudaStream_t st);
 // scratch: 3 * B * k doubles; min_theta_bits: running minimum of the Gauss
 // nodes (positive doubles compare like their bit patterns)
 void launch_spectral_impl(const double *alpha, const double *beta, const double *beta0,

@@ -43,6 +43,10 @@ class lgw_system_desc(ctypes.Structure):
 SYS_NO_FP64, SYS_NO_BF16, SYS_FP8 = 1, 2, 4
 
 
+class lgw_poly(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_int32), ("x_lo", ctypes.c_double), ("x_hi", ctypes.c_double)]
+
+
 class lgw_problem(ctypes.Structure):
     _fields_ = [("n_t", ctypes.c_int32), ("targets", ctypes.c_void_p),
                 ("n_m", ctypes.c_int32), ("m_idx", ctypes.c_void_p),
@@ -104,6 +108,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                  ctypes.POINTER(lgw_report)], I),
         "lgw_sigma_c_backward": ([P, P, ctypes.POINTER(lgw_problem),
                                   ctypes.POINTER(lgw_options), P, P, P], I),
+        "lgw_sigma_c_poly": ([P, P, ctypes.POINTER(lgw_problem), ctypes.POINTER(lgw_options),
+                              ctypes.POINTER(lgw_poly), P, P, P, ctypes.POINTER(lgw_report)], I),
+        "lgw_lanczos_coeffs_poly": ([P, P, ctypes.POINTER(lgw_problem),
+                                     ctypes.POINTER(lgw_options), ctypes.POINTER(lgw_poly),
+                                     P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -302,6 +311,27 @@ def lgw_sigma_c(h: Handle, s: System, problem: Problem, options: Options, sigma,
         h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), _ptr(sigma, "f64"), _ptr(e_qp, "f64"),
         _ptr(z_qp, "f64"), ctypes.byref(rep) if report else None))
     return rep.as_dict() if report else None
+
+
+def lgw_sigma_c_poly(h: Handle, s: System, problem: Problem, options: Options, g: int,
+                     x_lo: float, x_hi: float, sigma, e_qp, z_qp=None,
+                     report: bool = False) -> Optional[dict]:
+    p, o = problem.to_c(), options.to_c()
+    pl = lgw_poly(int(g), float(x_lo), float(x_hi))
+    rep = lgw_report()
+    _check(h, load_library().lgw_sigma_c_poly(
+        h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), ctypes.byref(pl), _ptr(sigma, "f64"),
+        _ptr(e_qp, "f64"), _ptr(z_qp, "f64"), ctypes.byref(rep) if report else None))
+    return rep.as_dict() if report else None
+
+
+def lgw_lanczos_coeffs_poly(h: Handle, s: System, problem: Problem, options: Options, g: int,
+                            x_lo: float, x_hi: float, alpha, beta, beta0, k_eff) -> None:
+    p, o = problem.to_c(), options.to_c()
+    pl = lgw_poly(int(g), float(x_lo), float(x_hi))
+    _check(h, load_library().lgw_lanczos_coeffs_poly(
+        h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), ctypes.byref(pl), _ptr(alpha, "f64"),
+        _ptr(beta, "f64"), _ptr(beta0, "f64"), _ptr(k_eff, "i32")))
 
 
 def lgw_sigma_c_batched(h: Handle, systems: Sequence[System], problems: Sequence[Problem],

@@ -74,6 +74,7 @@ def test_binding_offsets_match_c_compiler(tmp_path):
         pytest.skip("no C compiler")
     from paper_2310_20103_gb300 import lgw as L
     structs = {"lgw_system_desc": L.lgw_system_desc, "lgw_problem": L.lgw_problem,
+               "lgw_poly": L.lgw_poly,
                "lgw_options": L.lgw_options, "lgw_report": L.lgw_report}
     enums = {"LGW_FP64": L.PRECISION["fp64"], "LGW_BF16": L.PRECISION["bf16"],
              "LGW_FP8": L.PRECISION["fp8"], "LGW_REORTH_NONE": L.REORTH["none"],
