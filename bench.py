@@ -274,6 +274,38 @@ def run_gpu(args):
                "steps": 1, "gemm_tflops": r8["gemm_flops"] / (g8 * 1e-3) / 1e12 if g8 else None,
                "ms_gemm1": r8["ms_gemm1"], "ms_gemm2": r8["ms_gemm2"],
                "qp_diff_mev_vs_bf16_cgs2": float(np.abs(e.cpu().numpy() - e_cgs2).max() * 1e3)}
+    # the paper's polynomial form (Lanczos on p_g(C) ~ C^1/2, no
+    # reorthogonalisation) on the same batch, against the primary result
+    poly = None
+    if cgs2 is not None and not args.no_poly:
+        # spectral interval of C: min Delta^2 (C >= Delta^2) and the bound
+        # max Delta^2 + c_K max Delta ||L||_2^2 (||L||_2^2 by power iteration)
+        Dl = (wl.eps[wl.n_v:][None, :] - wl.eps[:wl.n_v][:, None]).ravel()
+        xv = np.random.default_rng(0).standard_normal(wl.n_aux)
+        for _ in range(30):
+            xv = wl.L.T @ (wl.L @ xv)
+            nrm = np.linalg.norm(xv)
+            xv /= nrm
+        lmax = float(nrm) * 1.01
+        x_lo = float(Dl.min() ** 2)
+        x_hi = float(Dl.max() ** 2 + wl.kernel_factor * Dl.max() * lmax)
+        poly = {"interval": [x_lo, x_hi], "reorth": "none", "runs": []}
+        for g, kp in ((8, 8), (16, 16)):
+            op = L.Options(k=kp, precision=args.precision, reorth="none",
+                           b_sub=args.tps * M_PER_TARGET)
+            L.lgw_sigma_c_poly(h, sysd, batch(args.warmup + args.steps), op, g, x_lo, x_hi, sig, e)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            rp = L.lgw_sigma_c_poly(h, sysd, batch(args.warmup + args.steps), op, g, x_lo, x_hi,
+                                    sig, e, report=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pms = e0.elapsed_time(e1)
+            poly["runs"].append({"g": g, "k": kp, "value": tps / (pms / 1e3),
+                                 "unit": "QP states/s", "ms_per_step": pms,
+                                 "gemm_ms": rp["ms_gemm1"] + rp["ms_gemm2"],
+                                 "qp_diff_mev_vs_primary": float(
+                                     np.abs(e.cpu().numpy() - e_cgs2).max() * 1e3)})
     ms_max = R.max_over_ranks(ms, dev) if world > 1 else ms
     states = tps * args.steps * world
     value = states / (ms_max / 1e3)
@@ -367,6 +399,7 @@ def run_gpu(args):
         "cgs2_step": cgs2,
         "float_basis_step": fbasis,
         "fp8_step": fp8,
+        "poly_variant": poly,
     }
     if rank == 0 and world == 1 and not args.no_fp64_compare:
         line["fp64_path"] = fp64_compare(args, L, h, sysd, wl, tgt_all, m_idx_d, omega_d, M_all,
@@ -621,6 +654,7 @@ def main():
     ap.add_argument("--no-cgs2-step", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-fp8-step", action="store_true")
+    ap.add_argument("--no-poly", action="store_true")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint leg (differentiation workload) and print it")
     ap.add_argument("--adjoint-targets", type=int, default=8)
