@@ -38,7 +38,7 @@ __all__ = [
     "dsigma_from_poles", "sigma_closed_form", "sigma_lanczos", "qp_solve",
     "solve_all_qp", "qp_gradient", "qp_energies_closed_form", "qp_gradient_closed_form",
     "qp_gradient_lanczos", "chebyshev_sqrt", "chebyshev_eval", "apply_poly",
-    "sigma_poly_lanczos", "haydock",
+    "sigma_poly_lanczos", "haydock", "sigma_x", "qp_linearised", "fit_factors",
 ]
 
 
@@ -541,3 +541,38 @@ def sigma_poly_lanczos(wl, g, lo, hi, k=None, reorth=True):
                 E.append(np.full(ke, eta))
         poles.append((np.concatenate(P), np.concatenate(Wt), np.concatenate(E)))
     return sig, poles, coeffs
+
+
+# --------------------------------------------------------------------------
+# Static part (text around Eq. 5-6): exchange from the pair factors and the
+# linearised QP solution; density-fitting factors from a metric.
+# --------------------------------------------------------------------------
+def sigma_x(wl):
+    """Sigma^ex_t = -sum_v (vt|vt) over the occupied orbitals v of the summed
+    set.  The pair factors M share L's metric-folded form, (pq|rs) =
+    sum_mu B_pq,mu B_rs,mu, so (vt|vt) = sum_mu M[t, v, mu]^2."""
+    occ = np.asarray(wl.m_idx) < wl.n_v
+    return -np.einsum("tmu,tmu->t", wl.M[:, occ, :], wl.M[:, occ, :])
+
+
+def qp_linearised(wl, poles, static_shift=None):
+    """E_t = e0 + Z Re Sigma_t(e0), Z = 1 / (1 - Re Sigma_t'(e0)),
+    e0 = eps_t + s_t (first-order expansion of the QP equation at e0)."""
+    E = np.empty(wl.n_t)
+    Z = np.empty(wl.n_t)
+    for ti, t in enumerate(wl.targets):
+        pos, W, eta = poles[ti]
+        e0 = wl.eps[t] + (0.0 if static_shift is None else static_shift[ti])
+        S = sigma_from_poles([e0], pos, W, eta, wl.delta)[0]
+        dS = dsigma_from_poles([e0], pos, W, eta, wl.delta)[0]
+        Z[ti] = 1.0 / (1.0 - dS.real)
+        E[ti] = e0 + Z[ti] * S.real
+    return E, Z
+
+
+def fit_factors(C, metric):
+    """Density-fitting pair factors B = C R with metric = R R^T (Cholesky, R
+    lower), so that (ab|cd) = sum_{mu,nu} C_ab,mu metric_mu,nu C_cd,nu =
+    sum_kappa B_ab,kappa B_cd,kappa (the L and M of this problem)."""
+    R = np.linalg.cholesky(np.asarray(metric, dtype=np.float64))
+    return np.asarray(C, dtype=np.float64) @ R
