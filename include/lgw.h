@@ -172,7 +172,10 @@ typedef struct {
  *                replay it from a per-handle cache when the same system,
  *                shapes, options and buffers come again; the report's
  *                per-category times are then zero (ms_total stays)
- * reorth_arith   arithmetic of the Gram-Schmidt passes (lgw_reorth_arith) */
+ * reorth_arith   arithmetic of the Gram-Schmidt passes (lgw_reorth_arith)
+ * qp_mode        0: graphical solution of E = eps_t + s_t + Re Sigma_t(E)
+ *                (Newton, bracketing fallback); 1: linearised at e0 = eps_t +
+ *                s_t, E = e0 + Z Re Sigma_t(e0), Z = 1 / (1 - Re Sigma_t'(e0)) */
 typedef struct {
   int32_t k;
   int32_t precision;
@@ -183,6 +186,7 @@ typedef struct {
   double qp_tol;
   int32_t use_graph;
   int32_t reorth_arith;
+  int32_t qp_mode;
 } lgw_options;
 
 /* Filled by calls that take a report pointer (host memory).  Phase times are
@@ -299,6 +303,25 @@ lgw_status lgw_sigma_c_poly(lgw_handle *h, const lgw_system *s, const lgw_proble
 lgw_status lgw_lanczos_coeffs_poly(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
                                    const lgw_options *o, const lgw_poly *poly, double *alpha,
                                    double *beta, double *beta0, int32_t *k_eff);
+
+/* Exchange self-energy Sigma^ex_t = -sum_v (vt|vt) (text after Eq. 5) over
+ * the occupied orbitals v of the request's summed set, from its pair factors
+ * (which share L's metric-folded form, (pq|rs) = sum_mu B_pq,mu B_rs,mu):
+ * (vt|vt) = sum_mu M[t][v][mu]^2.  p->M is required (LGW_ERR_UNSUPPORTED with
+ * V).  sigma_x [n_t], host or device.  With a V_xc of the caller,
+ * static_shift = sigma_x - V_xc turns the QP equation into the full one. */
+lgw_status lgw_sigma_x(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                       double *sigma_x);
+
+/* Density-fitting factors: with fitting coefficients C [n_pairs][n_aux] of
+ * orbital pairs and the Coulomb metric [n_aux][n_aux] (symmetric positive
+ * definite), (ab|cd) = sum C_ab,mu metric_mu,nu C_cd,nu = sum_kappa B_ab,kappa
+ * B_cd,kappa with B = C R, metric = R R^T (FP64 blocked Cholesky and FP64
+ * product on the GPU).  B [n_pairs][n_aux]; the factors of the vc pairs are
+ * the system's L, those of the (t, m) pairs the request's M.  Host or device
+ * pointers; LGW_ERR_NOT_SPD if the metric is not positive definite. */
+lgw_status lgw_fit_factors(lgw_handle *h, int32_t n_pairs, int32_t n_aux, const double *C,
+                           const double *metric, double *B);
 
 /* Several independent systems of uneven size in one call; sigma[i], e_qp[i]
  * and z_qp[i] (z_qp may be NULL) have the shapes of lgw_sigma_c for

@@ -149,6 +149,16 @@ __global__ void k_qp(CfProblem p, JacobiBufs jb, const double *__restrict__ sigm
   double E = e0;
   bool ok = false;
   cplx S, dS;
+  if (p.qp_mode == 1) {
+    // linearised: E = e0 + Z Re Sigma(e0), Z = 1 / (1 - Re Sigma'(e0))
+    sigma_at(p, jb, ti, e0, S, dS);
+    const double Z = 1.0 / (1.0 - dS.re);
+    if ((threadIdx.x & 31) == 0) {
+      e_qp[ti] = e0 + Z * S.re;
+      if (z_qp) z_qp[ti] = Z;
+    }
+    return;
+  }
   for (int it = 0; it < max_iter; ++it) {
     sigma_at(p, jb, ti, E, S, dS);
     const double f = E - e0 - S.re;

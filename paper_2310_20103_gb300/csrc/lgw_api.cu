@@ -298,7 +298,7 @@ void run_graphed(lgw_handle *h, const std::string &key, F &&body) {
 }
 
 struct Opts {
-  int k, precision, reorth, b_sub, qp_max_iter, use_graph, split, split32;
+  int k, precision, reorth, b_sub, qp_max_iter, use_graph, split, split32, qp_mode;
   double tol, qp_tol;
 };
 
@@ -314,6 +314,11 @@ Opts resolve_opts(lgw_handle *h, const lgw_options *o, const SysDev &s) {
   r.b_sub = o->b_sub;
   r.qp_max_iter = o->qp_max_iter > 0 ? o->qp_max_iter : 50;
   r.use_graph = o->use_graph;
+  r.qp_mode = o->qp_mode;
+  if (r.qp_mode != 0 && r.qp_mode != 1) {
+    set_err(h, LGW_ERR_ARG, "unknown qp_mode %d", o->qp_mode);
+    throw Fail{LGW_ERR_ARG};
+  }
   if (o->reorth_arith < LGW_RA_AUTO || o->reorth_arith > LGW_RA_SPLIT32) {
     set_err(h, LGW_ERR_ARG, "unknown reorthogonalisation arithmetic %d", o->reorth_arith);
     throw Fail{LGW_ERR_ARG};
@@ -896,6 +901,7 @@ void run_sigma(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o
   cp.omega = pv.d_omega;
   cp.delta = pv.delta;
   cp.shift = pv.d_shift;
+  cp.qp_mode = o.qp_mode;
   tm.mark(C_CF);
   double *sig = sigma ? sigma : wsT<double>(h, "sigma_tmp", (size_t)std::max(1, pv.n_t * pv.n_freq * 2));
   const int S = cf_slices(cp);
@@ -1771,6 +1777,62 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
   return LGW_OK;
 }
 
+lgw_status lgw_sigma_x(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                       double *sigma_x) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!sys || sys->h != h || !sigma_x) return set_err(h, LGW_ERR_ARG, "NULL argument to lgw_sigma_x");
+  try {
+    const SysDev &s = sys->s;
+    cudaStream_t st = h->stream;
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    ProbView pv = check_problem(h, s, p);
+    if (!pv.d_M) {
+      set_err(h, LGW_ERR_UNSUPPORTED, "the exchange self-energy needs the pair factors M");
+      throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    OutBuf<double> out;
+    out.init(h, "out_sigma_x", sigma_x, (size_t)pv.n_t);
+    launch_sigma_x(pv.d_M, pv.n_t, pv.n_m, s.n_aux, pv.d_m_idx, s.n_v, out.dev, st);
+    if (pv.n_t > 0) check_launch(h, "sigma_x");
+    out.finish(h);
+    check_status(h);
+  } catch (Fail &f) {
+    return f.st;
+  }
+  return LGW_OK;
+}
+
+lgw_status lgw_fit_factors(lgw_handle *h, int32_t n_pairs, int32_t n_aux, const double *C,
+                           const double *metric, double *B) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (n_pairs < 0 || n_aux < 1 || (n_pairs > 0 && (!C || !B)) || !metric)
+    return set_err(h, LGW_ERR_ARG, "bad arguments to lgw_fit_factors");
+  try {
+    cudaStream_t st = h->stream;
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    const double *Vd = in_dev(h, "in_metric", metric, (size_t)n_aux * n_aux);
+    double *R = wsT<double>(h, "fit_R", (size_t)n_aux * n_aux);
+    LGW_TRY_CUDA(h, cudaMemcpyAsync(R, Vd, sizeof(double) * n_aux * n_aux,
+                                    cudaMemcpyDeviceToDevice, st));
+    h->launches += launch_cholesky(R, n_aux, h->d_status, st);
+    check_launch(h, "cholesky");
+    if (n_pairs > 0) {
+      const double *Cd = in_dev(h, "in_fitC", C, (size_t)n_pairs * n_aux);
+      OutBuf<double> out;
+      out.init(h, "out_fitB", B, (size_t)n_pairs * n_aux);
+      launch_gemm_nn_f64(Cd, R, n_pairs, n_aux, n_aux, out.dev, st);
+      check_launch(h, "gemm_nn_f64");
+      out.finish(h);
+    }
+    check_status(h);
+  } catch (Fail &f) {
+    return f.st;
+  }
+  return LGW_OK;
+}
+
 }  // extern "C"
 
 // ===========================================================================
@@ -1885,6 +1947,8 @@ extern "C" lgw_status lgw_sigma_from_coeffs_noalloc(lgw_handle *h, const lgw_sys
   cp.omega = p->omega;
   cp.delta = p->delta;
   cp.shift = p->static_shift;
+  if (o->qp_mode != 0 && o->qp_mode != 1) return set_err(h, LGW_ERR_ARG, "unknown qp_mode");
+  cp.qp_mode = o->qp_mode;
   launch_cf_grid(cp, jb, sigma, nullptr, 1, st);
   const int qp_iter = o->qp_max_iter > 0 ? o->qp_max_iter : 50;
   const double qp_tol = o->qp_tol > 0 ? o->qp_tol : 1e-10;

@@ -269,6 +269,7 @@ struct CfProblem {
   const double *omega;          // device [n_freq]
   double delta;
   const double *shift;          // device [n_t] or nullptr
+  int qp_mode;                  // 0 graphical (Newton), 1 linearised at eps_t + s_t
 };
 int cf_slices(const CfProblem &p);
 // part: S * n_t * n_freq * 2 doubles of scratch, or NULL for one slice;
@@ -277,6 +278,13 @@ int launch_cf_grid(const CfProblem &p, JacobiBufs jb, double *sigma, double *par
                    cudaStream_t st);
 void launch_qp(const CfProblem &p, JacobiBufs jb, const double *sigma, int max_iter, double tol,
                double *e_qp, double *z_qp, unsigned *status, cudaStream_t st);
+
+// k_static.cu : exchange self-energy and density-fitting factors
+void launch_sigma_x(const double *M, int n_t, int n_m, int n_aux, const int *m_idx, int n_v,
+                    double *out, cudaStream_t st);
+int launch_cholesky(double *A, int n, unsigned *status, cudaStream_t st);
+void launch_gemm_nn_f64(const double *A, const double *B, int M, int N, int K, double *C,
+                        cudaStream_t st);
 
 // k_adjoint.cu : gradient of the QP energies (implicit function + Daleckii-Krein)
 // A stored Krylov basis [slot][Bs][N]: FP64, or the float pair hi (+ lo).

@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "LGW_OK", 1: "LGW_ERR_ARG", 2: "LGW_ERR_SHAPE", 3: "LGW_ERR_C
 PRECISION = {"fp64": 0, "bf16": 1, "fp8": 3}
 REORTH = {"none": 0, "cgs2": 1, "cgs1k": 2}
 REORTH_ARITH = {"auto": 0, "fp64": 1, "split": 2, "split32": 3}
+QP_MODE = {"graphical": 0, "linearised": 1}
 
 
 class LgwError(RuntimeError):
@@ -60,7 +61,7 @@ class lgw_options(ctypes.Structure):
                 ("reorth", ctypes.c_int32), ("b_sub", ctypes.c_int32),
                 ("breakdown_tol", ctypes.c_double), ("qp_max_iter", ctypes.c_int32),
                 ("qp_tol", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("reorth_arith", ctypes.c_int32)]
+                ("reorth_arith", ctypes.c_int32), ("qp_mode", ctypes.c_int32)]
 
 
 class lgw_report(ctypes.Structure):
@@ -108,6 +109,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                  ctypes.POINTER(lgw_report)], I),
         "lgw_sigma_c_backward": ([P, P, ctypes.POINTER(lgw_problem),
                                   ctypes.POINTER(lgw_options), P, P, P], I),
+        "lgw_sigma_x": ([P, P, ctypes.POINTER(lgw_problem), P], I),
+        "lgw_fit_factors": ([P, I, I, P, P, P], I),
         "lgw_sigma_c_poly": ([P, P, ctypes.POINTER(lgw_problem), ctypes.POINTER(lgw_options),
                               ctypes.POINTER(lgw_poly), P, P, P, ctypes.POINTER(lgw_report)], I),
         "lgw_lanczos_coeffs_poly": ([P, P, ctypes.POINTER(lgw_problem),
@@ -216,6 +219,7 @@ class Options:
     qp_tol: float = 0.0
     use_graph: int = 0
     reorth_arith: str = "auto"
+    qp_mode: str = "graphical"
 
     def to_c(self) -> lgw_options:
         o = lgw_options()
@@ -228,6 +232,7 @@ class Options:
         o.qp_tol = float(self.qp_tol)
         o.use_graph = int(self.use_graph)
         o.reorth_arith = REORTH_ARITH[self.reorth_arith]
+        o.qp_mode = QP_MODE[self.qp_mode]
         return o
 
 
@@ -311,6 +316,17 @@ def lgw_sigma_c(h: Handle, s: System, problem: Problem, options: Options, sigma,
         h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), _ptr(sigma, "f64"), _ptr(e_qp, "f64"),
         _ptr(z_qp, "f64"), ctypes.byref(rep) if report else None))
     return rep.as_dict() if report else None
+
+
+def lgw_sigma_x(h: Handle, s: System, problem: Problem, sigma_x) -> None:
+    p = problem.to_c()
+    _check(h, load_library().lgw_sigma_x(h.ptr, s.ptr, ctypes.byref(p), _ptr(sigma_x, "f64")))
+
+
+def lgw_fit_factors(h: Handle, C, metric, B) -> None:
+    n_pairs, n_aux = (C.shape[0], C.shape[1]) if C is not None else (0, metric.shape[0])
+    _check(h, load_library().lgw_fit_factors(h.ptr, int(n_pairs), int(n_aux), _ptr(C, "f64"),
+                                             _ptr(metric, "f64"), _ptr(B, "f64")))
 
 
 def lgw_sigma_c_poly(h: Handle, s: System, problem: Problem, options: Options, g: int,

@@ -61,7 +61,7 @@ def test_binding_struct_layouts_match_header():
     names = re.findall(r"\b(ms_\w+|gemm_flops|reorth_elems|min_theta|n_vectors|n_sub_batches|"
                        r"b_sub|k_min|k_max|n_second_pass|gpu_launches|gemm1_splits)\b", body)
     assert [f for f, _ in L.lgw_report._fields_] == names
-    assert ctypes.sizeof(L.lgw_options) == 48
+    assert ctypes.sizeof(L.lgw_options) == 56
 
 
 def test_binding_offsets_match_c_compiler(tmp_path):
