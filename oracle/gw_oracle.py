@@ -39,6 +39,7 @@ __all__ = [
     "solve_all_qp", "qp_gradient", "qp_energies_closed_form", "qp_gradient_closed_form",
     "qp_gradient_lanczos", "chebyshev_sqrt", "chebyshev_eval", "apply_poly",
     "sigma_poly_lanczos", "haydock", "sigma_x", "qp_linearised", "fit_factors",
+    "tda_matrix", "sigma_tda_closed_form", "sigma_tda_lanczos", "sigma_offdiag_closed_form",
 ]
 
 
@@ -576,3 +577,76 @@ def fit_factors(C, metric):
     sum_kappa B_ab,kappa B_cd,kappa (the L and M of this problem)."""
     R = np.linalg.cholesky(np.asarray(metric, dtype=np.float64))
     return np.asarray(C, dtype=np.float64) @ R
+
+
+# --------------------------------------------------------------------------
+# Tamm-Dancoff variant (B = 0): the excitations are the eigenpairs of A
+# alone, A = Delta + (c_K / 2) L L^T (A holds the kernel once, A + B twice),
+# and W^s_tm = sum_vc (tm|vc) X^s_vc, so
+#   Sigma_tm(omega) = sum_s (V . X_s)^2 / (z + eta Omega_s) = V^T (z + eta A)^-1 V.
+# --------------------------------------------------------------------------
+def tda_matrix(eps, n_v, L, kernel_factor=4.0):
+    Delta = pair_energies(eps, n_v)
+    return np.diag(Delta) + 0.5 * kernel_factor * (L @ L.T)
+
+
+def sigma_tda_closed_form(wl):
+    """Sigma_t(omega) and its pole lists from the eigenpairs of A."""
+    Om, X = np.linalg.eigh(tda_matrix(wl.eps, wl.n_v, wl.L, wl.kernel_factor))
+    V = coupling_vectors(wl.L, wl.M)                       # [n_t, n_m, N_vc]
+    p = V @ X
+    eta = occupation_sign(wl.m_idx, wl.n_v)
+    poles = []
+    for ti in range(wl.n_t):
+        pos = (wl.eps[wl.m_idx][:, None] - eta[:, None] * Om[None, :]).ravel()
+        poles.append((pos, (p[ti] ** 2).ravel(), np.repeat(eta, Om.size)))
+    sig = np.stack([sigma_from_poles(wl.omega, *poles[ti], wl.delta) for ti in range(wl.n_t)])
+    return sig, poles
+
+
+def sigma_tda_lanczos(wl, k=None, reorth=True):
+    """k-step Lanczos on A from each V_tm; Sigma_tm = -eta G(-eta z) with
+    G(zeta) = <V|(zeta - A_k)^-1|V> the Haydock fraction of the tridiagonal;
+    also the equivalent Gauss-rule poles (nodes of A_k, weights beta0^2 u1^2)."""
+    k = wl.k if k is None else k
+    A = tda_matrix(wl.eps, wl.n_v, wl.L, wl.kernel_factor)
+    V = coupling_vectors(wl.L, wl.M).reshape(wl.n_t * wl.n_m, -1)
+    coeffs = lanczos(lambda X: X @ A.T, V, k, reorth=reorth)
+    alpha, beta, beta0, k_eff = coeffs
+    eta_all = occupation_sign(wl.m_idx, wl.n_v)
+    sig = np.zeros((wl.n_t, wl.omega.size), dtype=np.complex128)
+    poles = []
+    for ti in range(wl.n_t):
+        P, Wt, E = [], [], []
+        for mi, m in enumerate(wl.m_idx):
+            v = ti * wl.n_m + mi
+            eta = eta_all[mi]
+            z = wl.omega - wl.eps[m] - 1j * eta * wl.delta
+            sig[ti] += -eta * haydock(alpha[v], beta[v], beta0[v], k_eff[v], -eta * z)
+            ke = int(k_eff[v])
+            if ke:
+                T = np.diag(alpha[v, :ke])
+                if ke > 1:
+                    T += np.diag(beta[v, : ke - 1], 1) + np.diag(beta[v, : ke - 1], -1)
+                Om, U = np.linalg.eigh(T)
+                P.append(wl.eps[m] - eta * Om)
+                Wt.append(beta0[v] ** 2 * U[0] ** 2)
+                E.append(np.full(ke, eta))
+        poles.append((np.concatenate(P), np.concatenate(Wt), np.concatenate(E)))
+    return sig, poles, coeffs
+
+
+def sigma_offdiag_closed_form(wl, t_pair):
+    """Off-diagonal element Sigma_tt'(omega) = sum_m sum_s W^s_tm W^s_t'm /
+    (Omega_s (z + eta Omega_s)) (Eq. 7 with the two targets of t_pair, given as
+    indices into wl.targets; RPA, from the Casida eigenpairs)."""
+    Om, Z = casida_eigenpairs(casida_matrix(wl.eps, wl.n_v, wl.L, wl.kernel_factor))
+    b = start_vectors(wl.eps, wl.n_v, coupling_vectors(wl.L, wl.M))
+    i, j = t_pair
+    eta = occupation_sign(wl.m_idx, wl.n_v)
+    out = np.zeros(wl.omega.size, dtype=np.complex128)
+    for mi, m in enumerate(wl.m_idx):
+        pa, pb = b[i, mi] @ Z, b[j, mi] @ Z
+        z = wl.omega[:, None] - wl.eps[m] - 1j * eta[mi] * wl.delta
+        out += np.sum(pa * pb / (Om * (z + eta[mi] * Om)), axis=1)
+    return out
