@@ -323,6 +323,27 @@ lgw_status lgw_sigma_x(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
 lgw_status lgw_fit_factors(lgw_handle *h, int32_t n_pairs, int32_t n_aux, const double *C,
                            const double *metric, double *B);
 
+/* Tamm-Dancoff variant (B = 0 in Eq. 1): the excitations are the eigenpairs
+ * of A = Delta + (c_K / 2) L L^T (A carries the kernel once, A + B twice)
+ * and W^s_tm = sum_vc (tm|vc) X^s_vc, so Sigma_tm(omega) = V^T (z + eta A)^-1 V
+ * = -eta G(-eta z) with G the Haydock fraction of A's own k-step tridiagonal
+ * started from V = L M (Eq. 13-14; no square-root map).  Options, outputs and
+ * precisions as lgw_sigma_c; the adjoint is not available for it. */
+lgw_status lgw_sigma_c_tda(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                           const lgw_options *o, double *sigma, double *e_qp, double *z_qp,
+                           lgw_report *rep);
+
+/* Off-diagonal elements Sigma_tt'(omega) = sum_m sum_s W^s_tm W^s_t'm /
+ * (Omega_s (z + eta Omega_s)) (Eq. 7) for n_pairs pairs (t, t') given as
+ * indices into p->targets (pairs [n_pairs][2], host or device), by the
+ * polarisation identity over diagonal elements:
+ *   Sigma_tt' = (Sigma[b_t + b_t'] - Sigma[b_t - b_t']) / 4,
+ * i.e. 2 n_pairs requests whose factors are M_t +- M_t' (or V_t +- V_t').
+ * sigma_od [n_pairs][n_freq][2]; no QP solve. */
+lgw_status lgw_sigma_offdiag(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                             const lgw_options *o, int32_t n_pairs, const int32_t *pairs,
+                             double *sigma_od);
+
 /* Several independent systems of uneven size in one call; sigma[i], e_qp[i]
  * and z_qp[i] (z_qp may be NULL) have the shapes of lgw_sigma_c for
  * problems[i].  The systems run concurrently on up to four internal streams

@@ -120,6 +120,7 @@ __global__ void k_poly_prep(const double *__restrict__ alpha, const double *__re
     const double x = (i + 1 < n) ? beta[(size_t)v * k + i] : 0.0;
     b2[i] = x * x;
   }
+  if (jb.g0 == nullptr) return;   // Tamm-Dancoff fractions need no G(0)
   if (n <= 0) {
     jb.g0[v] = 0.0;
     return;
@@ -143,6 +144,63 @@ void launch_poly_prep(const double *alpha, const double *beta, const double *bet
                       const int *k_eff, int B, int k, JacobiBufs jb, unsigned *status,
                       cudaStream_t st) {
   k_poly_prep<<<(B + 127) / 128, 128, 0, st>>>(alpha, beta, beta0, k_eff, B, k, jb, status);
+}
+
+// Tamm-Dancoff view of a system: the Casida arrays of A = Delta + c L L^T
+// take the places of those of C (Delta^1/2 -> 1, Delta^2 -> Delta,
+// c_K Delta^1/2 -> c), zero in the padding.
+__global__ void k_tda_view(const double *__restrict__ Delta, int n_vc, int N, double c,
+                           double *ones, double *cd, float *onesf, float *d2f, float *cdf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const bool real = i < n_vc;
+  ones[i] = real ? 1.0 : 0.0;
+  cd[i] = real ? c : 0.0;
+  onesf[i] = real ? 1.0f : 0.0f;
+  d2f[i] = (float)Delta[i];
+  cdf[i] = real ? (float)c : 0.0f;
+}
+
+// Sigma_tt' = (Sigma[b_t + b_t'] - Sigma[b_t - b_t']) / 4: virtual requests
+// 2i and 2i+1 of pair i carry the rows of t + t' and t - t'.
+__global__ void k_pol_rows(const double *__restrict__ src, int n_m, int len,
+                           const int *__restrict__ pairs, int n_pairs, double *__restrict__ dst) {
+  const size_t row_len = (size_t)n_m * len;
+  const size_t n = (size_t)n_pairs * 2 * row_len;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = idx / row_len, e = idx % row_len;
+    const int i = (int)(r / 2);
+    const double a = src[(size_t)pairs[2 * i] * row_len + e];
+    const double b = src[(size_t)pairs[2 * i + 1] * row_len + e];
+    dst[idx] = (r % 2 == 0) ? a + b : a - b;
+  }
+}
+
+__global__ void k_pol_combine(const double *__restrict__ sig2, int n_pairs, int n_freq,
+                              double *__restrict__ out) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t per = (size_t)n_freq * 2;
+  if (idx >= (size_t)n_pairs * per) return;
+  const size_t i = idx / per, e = idx % per;
+  out[idx] = 0.25 * (sig2[(2 * i) * per + e] - sig2[(2 * i + 1) * per + e]);
+}
+
+void launch_tda_view(const double *Delta, int n_vc, int N, double c, double *ones, double *cd,
+                     float *onesf, float *d2f, float *cdf, cudaStream_t st) {
+  k_tda_view<<<(N + 255) / 256, 256, 0, st>>>(Delta, n_vc, N, c, ones, cd, onesf, d2f, cdf);
+}
+void launch_pol_rows(const double *src, int n_m, int len, const int *pairs, int n_pairs,
+                     double *dst, cudaStream_t st) {
+  const size_t n = (size_t)n_pairs * 2 * n_m * len;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (n) k_pol_rows<<<(unsigned)blocks, 256, 0, st>>>(src, n_m, len, pairs, n_pairs, dst);
+}
+void launch_pol_combine(const double *sig2, int n_pairs, int n_freq, double *out,
+                        cudaStream_t st) {
+  const size_t n = (size_t)n_pairs * n_freq * 2;
+  if (n) k_pol_combine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sig2, n_pairs, n_freq, out);
 }
 
 }  // namespace lgw

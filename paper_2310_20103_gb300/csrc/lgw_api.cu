@@ -54,6 +54,9 @@ struct lgw_system {
   lgw_handle *h = nullptr;
   SysDev s{};
   __nv_bfloat16 *Ltb_lo = nullptr;   // bf16(L - bf16(L))^T [A][N], made on first use
+  // Tamm-Dancoff view (A = Delta + (c_K/2) L L^T in place of C), made on first use
+  SysDev tda{};
+  void *tda_buf = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -863,7 +866,11 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
 void run_sigma(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o,
                const double *alpha, const double *beta, const double *beta0, const int *k_eff,
                double *sigma, double *e_qp, double *z_qp, lgw_report *rep, double *tacc,
-               bool poly = false) {
+               int cfmode = 0) {
+  // cfmode 0: spectral map of C's tridiagonals (Omega-space fractions);
+  // 1: D = p_g(C)'s own tridiagonal, (G(zeta) - G(0)) / z; 2: A's own
+  // tridiagonal (Tamm-Dancoff), -eta G(zeta)
+  const bool poly = cfmode != 0;
   cudaStream_t st = h->stream;
   const int B = pv.B, k = o.k;
   Timer tm(h);
@@ -882,7 +889,7 @@ void run_sigma(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o
   if (B > 0 && poly) {
     // the fractions run on D = p_g(C)'s own tridiagonal (no spectral map)
     jb.a = const_cast<double *>(alpha);
-    jb.g0 = wsT<double>(h, "jac_g0", (size_t)B);
+    jb.g0 = cfmode == 1 ? wsT<double>(h, "jac_g0", (size_t)B) : nullptr;
     launch_poly_prep(alpha, beta, beta0, k_eff, B, k, jb, h->d_status, st);
     check_launch(h, "poly_prep");
   } else if (B > 0) {
@@ -981,14 +988,44 @@ const PolyOp *poly_arg(lgw_handle *h, const lgw_poly *pp, PolyOp &store) {
   return &store;
 }
 
+// Tamm-Dancoff view of a system: the same copies of L with Delta^1/2 -> 1,
+// Delta^2 -> Delta, c_K Delta^1/2 -> c_K / 2 (refreshed on every use, so
+// copies made later, such as the E4M3 ones, are seen).
+const SysDev &tda_view(lgw_handle *h, const lgw_system *csys) {
+  lgw_system *sys = const_cast<lgw_system *>(csys);
+  const SysDev &s = sys->s;
+  if (!sys->tda_buf) {
+    const size_t N = (size_t)s.N;
+    void *buf = nullptr;
+    LGW_TRY_CUDA(h, cudaMalloc(&buf, N * (2 * sizeof(double) + 3 * sizeof(float))));
+    sys->tda_buf = buf;
+    double *ones = static_cast<double *>(buf), *cd = ones + N;
+    float *onesf = reinterpret_cast<float *>(cd + N), *d2f = onesf + N, *cdf = d2f + N;
+    launch_tda_view(s.Delta, s.n_vc, s.N, 0.5 * s.kf, ones, cd, onesf, d2f, cdf, h->stream);
+    check_launch(h, "tda_view");
+  }
+  const size_t N = (size_t)s.N;
+  double *ones = static_cast<double *>(sys->tda_buf), *cd = ones + N;
+  float *onesf = reinterpret_cast<float *>(cd + N), *d2f = onesf + N, *cdf = d2f + N;
+  SysDev &t = sys->tda;
+  t = s;
+  t.kf = 0.5 * s.kf;
+  t.dsq = ones;
+  t.Delta2 = s.Delta;
+  t.cd = cd;
+  t.dsqf = onesf;
+  t.d2f = d2f;
+  t.cdf = cdf;
+  return t;
+}
+
 lgw_status sigma_c_impl(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
                         const lgw_options *o, const lgw_poly *pp, double *sigma, double *e_qp,
-                        double *z_qp, lgw_report *rep) {
+                        double *z_qp, lgw_report *rep, bool tda = false) {
   lgw_status g = guard_handle(h);
   if (g != LGW_OK) return g;
   if (!sys || sys->h != h) return set_err(h, LGW_ERR_ARG, "bad system handle");
   try {
-    const SysDev &s = sys->s;
     cudaStream_t st = h->stream;
     h->launches = 0;
     h->ev_used = 0;
@@ -1001,7 +1038,7 @@ lgw_status sigma_c_impl(lgw_handle *h, const lgw_system *sys, const lgw_problem 
       LGW_TRY_CUDA(h, cudaEventRecord(t0, st));
     }
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
-    Opts op = resolve_opts(h, o, s);
+    Opts op = resolve_opts(h, o, sys->s);
     ensure_copies(h, sys, op);
     PolyOp pstore;
     const PolyOp *poly = poly_arg(h, pp, pstore);
@@ -1010,6 +1047,7 @@ lgw_status sigma_c_impl(lgw_handle *h, const lgw_system *sys, const lgw_problem 
       op.split = 0;
       op.split32 = 0;
     }
+    const SysDev &s = tda ? tda_view(h, sys) : sys->s;
     ProbView pv = check_problem(h, s, p);
     double tacc[C_N] = {0};
     double *alpha = wsT<double>(h, "co_alpha", (size_t)std::max(1, pv.B) * op.k);
@@ -1022,7 +1060,7 @@ lgw_status sigma_c_impl(lgw_handle *h, const lgw_system *sys, const lgw_problem 
     z.init(h, "out_zqp", z_qp, (size_t)pv.n_t);
     run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, rep, tacc, false, nullptr, poly);
     run_sigma(h, s, pv, op, alpha, beta, beta0, ke, sg.dev, e.dev, z.dev, rep, tacc,
-              poly != nullptr);
+              poly != nullptr ? 1 : (tda ? 2 : 0));
     sg.finish(h);
     e.finish(h);
     z.finish(h);
@@ -1217,6 +1255,7 @@ lgw_status lgw_release_system(lgw_system *sys) {
   for (void *p : ps)
     if (p) cudaFree(p);
   if (sys->Ltb_lo) cudaFree(sys->Ltb_lo);
+  if (sys->tda_buf) cudaFree(sys->tda_buf);
   if (s.L8) cudaFree(s.L8);
   if (s.L8t) cudaFree(s.L8t);
   if (s.sL) cudaFree(s.sL);
@@ -1389,6 +1428,73 @@ lgw_status lgw_sigma_c(lgw_handle *h, const lgw_system *sys, const lgw_problem *
                        const lgw_options *o, double *sigma, double *e_qp, double *z_qp,
                        lgw_report *rep) {
   return sigma_c_impl(h, sys, p, o, nullptr, sigma, e_qp, z_qp, rep);
+}
+
+lgw_status lgw_sigma_c_tda(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                           const lgw_options *o, double *sigma, double *e_qp, double *z_qp,
+                           lgw_report *rep) {
+  return sigma_c_impl(h, sys, p, o, nullptr, sigma, e_qp, z_qp, rep, true);
+}
+
+lgw_status lgw_sigma_offdiag(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                             const lgw_options *o, int32_t n_pairs, const int32_t *pairs,
+                             double *sigma_od) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!sys || sys->h != h || n_pairs < 0 || (n_pairs > 0 && (!pairs || !sigma_od)))
+    return set_err(h, LGW_ERR_ARG, "bad arguments to lgw_sigma_offdiag");
+  try {
+    const SysDev &s = sys->s;
+    cudaStream_t st = h->stream;
+    h->timing = false;
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    Opts op = resolve_opts(h, o, s);
+    ensure_copies(h, sys, op);
+    ProbView pv = check_problem(h, s, p);
+    if (n_pairs == 0) return LGW_OK;
+    std::vector<int> hp = to_host(h, pairs, (size_t)2 * n_pairs);
+    for (int x : hp)
+      if (x < 0 || x >= pv.n_t) {
+        set_err(h, LGW_ERR_SHAPE, "pair index %d outside [0, n_t = %d)", x, pv.n_t);
+        throw Fail{LGW_ERR_SHAPE};
+      }
+    // virtual request: rows 2i, 2i+1 = factors of t + t' and t - t' (pair i)
+    ProbView pv2 = pv;
+    pv2.n_t = 2 * n_pairs;
+    pv2.B = pv2.n_t * pv.n_m;
+    pv2.targets.assign(pv2.n_t, 0);
+    for (int i = 0; i < n_pairs; ++i) pv2.targets[2 * i] = pv2.targets[2 * i + 1] = pv.targets[hp[2 * i]];
+    pv2.d_targets = in_dev(h, "od_targets", pv2.targets.data(), (size_t)pv2.n_t);
+    const int *dpairs = in_dev(h, "od_pairs", hp.data(), hp.size());
+    pv2.d_shift = nullptr;
+    if (pv.d_M) {
+      double *M2 = wsT<double>(h, "od_M", (size_t)pv2.B * s.n_aux);
+      launch_pol_rows(pv.d_M, pv.n_m, s.n_aux, dpairs, n_pairs, M2, st);
+      check_launch(h, "pol_rows");
+      pv2.d_M = M2;
+    } else {
+      double *V2 = wsT<double>(h, "od_V", (size_t)pv2.B * s.n_vc);
+      launch_pol_rows(pv.d_V, pv.n_m, s.n_vc, dpairs, n_pairs, V2, st);
+      check_launch(h, "pol_rows");
+      pv2.d_V = V2;
+    }
+    double *alpha = wsT<double>(h, "co_alpha", (size_t)pv2.B * op.k);
+    double *beta = wsT<double>(h, "co_beta", (size_t)pv2.B * op.k);
+    double *beta0 = wsT<double>(h, "co_beta0", (size_t)pv2.B);
+    int *ke = wsT<int>(h, "co_keff", (size_t)pv2.B);
+    double *sig2 = wsT<double>(h, "od_sigma", (size_t)pv2.n_t * pv.n_freq * 2);
+    run_lanczos(h, s, pv2, op, alpha, beta, beta0, ke, nullptr, nullptr);
+    run_sigma(h, s, pv2, op, alpha, beta, beta0, ke, sig2, nullptr, nullptr, nullptr, nullptr);
+    OutBuf<double> out;
+    out.init(h, "out_sigma_od", sigma_od, (size_t)n_pairs * pv.n_freq * 2);
+    launch_pol_combine(sig2, n_pairs, pv.n_freq, out.dev, st);
+    check_launch(h, "pol_combine");
+    out.finish(h);
+    check_status(h);
+  } catch (Fail &f) {
+    return f.st;
+  }
+  return LGW_OK;
 }
 
 lgw_status lgw_sigma_c_poly(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,

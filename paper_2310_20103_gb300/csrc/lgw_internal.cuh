@@ -279,6 +279,13 @@ int launch_cf_grid(const CfProblem &p, JacobiBufs jb, double *sigma, double *par
 void launch_qp(const CfProblem &p, JacobiBufs jb, const double *sigma, int max_iter, double tol,
                double *e_qp, double *z_qp, unsigned *status, cudaStream_t st);
 
+void launch_tda_view(const double *Delta, int n_vc, int N, double c, double *ones, double *cd,
+                     float *onesf, float *d2f, float *cdf, cudaStream_t st);
+void launch_pol_rows(const double *src, int n_m, int len, const int *pairs, int n_pairs,
+                     double *dst, cudaStream_t st);
+void launch_pol_combine(const double *sig2, int n_pairs, int n_freq, double *out,
+                        cudaStream_t st);
+
 // k_static.cu : exchange self-energy and density-fitting factors
 void launch_sigma_x(const double *M, int n_t, int n_m, int n_aux, const int *m_idx, int n_v,
                     double *out, cudaStream_t st);

@@ -110,6 +110,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lgw_sigma_c_backward": ([P, P, ctypes.POINTER(lgw_problem),
                                   ctypes.POINTER(lgw_options), P, P, P], I),
         "lgw_sigma_x": ([P, P, ctypes.POINTER(lgw_problem), P], I),
+        "lgw_sigma_c_tda": ([P, P, ctypes.POINTER(lgw_problem), ctypes.POINTER(lgw_options),
+                             P, P, P, ctypes.POINTER(lgw_report)], I),
+        "lgw_sigma_offdiag": ([P, P, ctypes.POINTER(lgw_problem), ctypes.POINTER(lgw_options),
+                               I, P, P], I),
         "lgw_fit_factors": ([P, I, I, P, P, P], I),
         "lgw_sigma_c_poly": ([P, P, ctypes.POINTER(lgw_problem), ctypes.POINTER(lgw_options),
                               ctypes.POINTER(lgw_poly), P, P, P, ctypes.POINTER(lgw_report)], I),
@@ -316,6 +320,24 @@ def lgw_sigma_c(h: Handle, s: System, problem: Problem, options: Options, sigma,
         h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), _ptr(sigma, "f64"), _ptr(e_qp, "f64"),
         _ptr(z_qp, "f64"), ctypes.byref(rep) if report else None))
     return rep.as_dict() if report else None
+
+
+def lgw_sigma_c_tda(h: Handle, s: System, problem: Problem, options: Options, sigma, e_qp,
+                    z_qp=None, report: bool = False) -> Optional[dict]:
+    p, o = problem.to_c(), options.to_c()
+    rep = lgw_report()
+    _check(h, load_library().lgw_sigma_c_tda(
+        h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), _ptr(sigma, "f64"), _ptr(e_qp, "f64"),
+        _ptr(z_qp, "f64"), ctypes.byref(rep) if report else None))
+    return rep.as_dict() if report else None
+
+
+def lgw_sigma_offdiag(h: Handle, s: System, problem: Problem, options: Options, pairs,
+                      sigma_od) -> None:
+    p, o = problem.to_c(), options.to_c()
+    n = _numel(pairs) // 2
+    _check(h, load_library().lgw_sigma_offdiag(h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o),
+                                               int(n), _ptr(pairs, "i32"), _ptr(sigma_od, "f64")))
 
 
 def lgw_sigma_x(h: Handle, s: System, problem: Problem, sigma_x) -> None:
