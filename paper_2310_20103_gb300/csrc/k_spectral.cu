@@ -12,8 +12,11 @@
 // nodes one at a time and chasing the bulge with plane rotations (the
 // Rutishauser / Gragg-Harrod reconstruction, O(k^2), orthogonal, stable).
 //
-// One thread per start vector; the tridiagonal, its first eigenvector row
-// and the Jacobi matrix live in per-vector scratch rows of length k.
+// One warp per start vector: the Gauss rule of T_k by parallel bisection and
+// the product formula for the weights, then the Jacobi rebuild; the work
+// rows live in shared memory.
+#include <algorithm>
+
 #include "lgw_internal.cuh"
 
 namespace lgw {
@@ -42,52 +45,6 @@ __device__ __forceinline__ void givens(double x, double z, double &c, double &s,
     s = 0.0;
     r = 0.0;
   }
-}
-
-// Eigenvalues of the symmetric tridiagonal (d[0..n), e[0..n-1)) and the first
-// row u of its eigenvector matrix, by implicit symmetric QR steps with the
-// Wilkinson shift (Golub & Van Loan, implicit symmetric QR).  On return d
-// holds the eigenvalues (unordered) and u the first components.
-__device__ bool tridiag_eig_first_row(double *d, double *e, double *u, int n) {
-  const double eps = 2.220446049250313e-16;
-  for (int i = 0; i < n; ++i) u[i] = (i == 0) ? 1.0 : 0.0;
-  if (n > 0) e[n - 1] = 0.0;
-  int hi = n - 1;
-  int iter = 0;
-  const int max_iter = 60 * n + 60;
-  while (hi > 0) {
-    if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
-      e[hi - 1] = 0.0;
-      --hi;
-      continue;
-    }
-    int lo = hi - 1;
-    while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
-    if (lo > 0) e[lo - 1] = 0.0;
-    if (++iter > max_iter) return false;
-    // Wilkinson shift: eigenvalue of the trailing 2x2 block nearer d[hi]
-    const double dl = 0.5 * (d[hi - 1] - d[hi]);
-    const double bb = e[hi - 1];
-    const double den = dl + copysign(hypot(dl, bb), dl != 0.0 ? dl : 1.0);
-    const double mu = d[hi] - bb * bb / den;
-    double x = d[lo] - mu, z = e[lo];
-    for (int kk = lo; kk < hi; ++kk) {
-      double c, s, r;
-      givens(x, z, c, s, r);
-      if (kk > lo) e[kk - 1] = r;
-      rot_sym(c, s, d, e, kk);
-      if (kk + 1 < hi) {
-        const double bulge = s * e[kk + 1];
-        e[kk + 1] *= c;
-        x = e[kk];
-        z = bulge;
-      }
-      const double u0 = u[kk], u1 = u[kk + 1];
-      u[kk] = c * u0 + s * u1;
-      u[kk + 1] = -s * u0 + c * u1;
-    }
-  }
-  return true;
 }
 
 // Jacobi matrix (a[0..n), off-diagonal squares b2[0..n-1)) and total weight
@@ -137,92 +94,214 @@ __device__ double jacobi_from_nodes(const double *x, const double *wt, int n, do
   return W;
 }
 
-// Work rows (d, e, u and the Jacobi diagonal a) live in shared memory when
-// they fit: the rotation chains read values the same thread just wrote, and
-// through global memory each of those round trips costs an L2 latency.
-constexpr int SPEC_THREADS = 4;
-constexpr size_t SPEC_SMEM_MAX = 96 * 1024;
+// --------------------------------------------------------------------------
+// Warp-parallel Gauss rule: one warp per vector, lanes over the eigenvalues.
+//   theta_j (the (j+1)-th smallest eigenvalue of T) by bisection on the Sturm
+//   count: the number of sign changes of the leading principal minors
+//   p_i = det(T_i - x I) is the number of eigenvalues below x (division-free
+//   three-term recurrence, rescaled by exact powers of two);
+//   u_1j^2 = det(theta_j I - T_2:n) / (d/dtheta det(theta I - T))|theta_j,
+//   the product formula prod_i (theta_j - mu_i) / prod_{i != j} (theta_j -
+//   theta_i) (mu: eigenvalues of T without its first row and column).
+// A lane interleaves up to SPEC_ILP eigenvalues so that their independent
+// recurrences hide the FP64 latency.  The Omega-space Jacobi rebuild then
+// runs on lane 0 from the nodes and weights in shared memory.
+// --------------------------------------------------------------------------
+constexpr int SPEC_ILP = 8;
+constexpr double SCALE_UP = 0x1p+500, SCALE_DN = 0x1p-500;
 
-template <bool SMEM>
-__global__ void k_spectral(const double *__restrict__ alpha, const double *__restrict__ beta,
-                           const double *__restrict__ beta0, const int *__restrict__ k_eff, int B,
-                           int k, double *sd, double *se, double *su, JacobiBufs jb,
-                           unsigned long long *min_theta_bits, unsigned *status) {
+// sign with the Sturm convention for zeros (a zero takes the opposite sign
+// of its predecessor)
+__device__ __forceinline__ bool neg_sturm(double p, bool prev_neg) {
+  return p < 0.0 || (p == 0.0 && !prev_neg);
+}
+
+__global__ void k_spectral_warp(const double *__restrict__ alpha, const double *__restrict__ beta,
+                                const double *__restrict__ beta0, const int *__restrict__ k_eff,
+                                int B, int k, int warps, JacobiBufs jb,
+                                unsigned long long *min_theta_bits, unsigned *status) {
   extern __shared__ double sm[];
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int v = blockIdx.x * warps + wid;
   if (v >= B) return;
+  double *al = sm + (size_t)wid * 6 * k;   // alpha
+  double *b2 = al + k;                     // beta^2 (b2[i] couples i, i+1)
+  double *th = b2 + k;                     // nodes (theta, then Omega)
+  double *wt = th + k;                     // u_1^2, then the Omega-space weights
+  double *ja = wt + k;                     // Jacobi diagonal
+  double *jb_ = ja + k;                    // Jacobi off-diagonal
   const int n = k_eff[v];
-  jb.n[v] = n;
+  if (lane == 0) jb.n[v] = n;
   if (n <= 0) {
-    jb.w0[v] = 0.0;
+    if (lane == 0) jb.w0[v] = 0.0;
     return;
   }
-  double *d, *e, *u, *a;
-  if (SMEM) {
-    double *base = sm + (size_t)threadIdx.x * 4 * k;
-    d = base;
-    e = base + k;
-    u = base + 2 * k;
-    a = base + 3 * k;
-  } else {
-    d = sd + (size_t)v * k;
-    e = se + (size_t)v * k;
-    u = su + (size_t)v * k;
-    a = jb.a + (size_t)v * k;
+  double glo = 1e300, ghi = -1e300;
+  for (int i = lane; i < n; i += 32) {
+    const double a = alpha[(size_t)v * k + i];
+    const double bl = i > 0 ? fabs(beta[(size_t)v * k + i - 1]) : 0.0;
+    const double br = i + 1 < n ? fabs(beta[(size_t)v * k + i]) : 0.0;
+    al[i] = a;
+    b2[i] = (i + 1 < n) ? br * br : 0.0;
+    glo = fmin(glo, a - bl - br);
+    ghi = fmax(ghi, a + bl + br);
   }
-  for (int i = 0; i < n; ++i) {
-    d[i] = alpha[(size_t)v * k + i];
-    e[i] = (i + 1 < n) ? beta[(size_t)v * k + i] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+    ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
   }
-  if (!tridiag_eig_first_row(d, e, u, n)) {
-    atomicOr(status, ST_NO_CONV);
-    jb.n[v] = 0;
-    jb.w0[v] = 0.0;
-    return;
+  __syncwarp();
+  const double width = ghi - glo;
+  glo -= 1e-12 * width + 1e-300;
+  ghi += 1e-12 * width + 1e-300;
+
+  for (int j0 = 0; j0 < n; j0 += 32 * SPEC_ILP) {
+    double lo[SPEC_ILP], hi[SPEC_ILP];
+    int idx[SPEC_ILP];
+#pragma unroll
+    for (int r = 0; r < SPEC_ILP; ++r) {
+      idx[r] = j0 + lane + 32 * r;
+      lo[r] = glo;
+      hi[r] = ghi;
+    }
+    // bisection: count(lo) <= j < count(hi); 60 halvings reach the rounding
+    // level of the Gershgorin width
+    for (int it = 0; it < 60; ++it) {
+      double x[SPEC_ILP], p0[SPEC_ILP], p1[SPEC_ILP];
+      int cnt[SPEC_ILP];
+      bool pn[SPEC_ILP];
+#pragma unroll
+      for (int r = 0; r < SPEC_ILP; ++r) {
+        x[r] = 0.5 * (lo[r] + hi[r]);
+        p0[r] = 1.0;
+        p1[r] = al[0] - x[r];
+        pn[r] = neg_sturm(p1[r], false);
+        cnt[r] = pn[r] ? 1 : 0;
+      }
+      for (int i = 1; i < n; ++i) {
+        const double a = al[i], bb = b2[i - 1];
+#pragma unroll
+        for (int r = 0; r < SPEC_ILP; ++r) {
+          double p2 = fma(a - x[r], p1[r], -bb * p0[r]);
+          const bool ng = neg_sturm(p2, pn[r]);
+          cnt[r] += (ng != pn[r]) ? 1 : 0;
+          pn[r] = ng;
+          p0[r] = p1[r];
+          p1[r] = p2;
+          if (fabs(p2) > SCALE_UP) {
+            p0[r] *= SCALE_DN;
+            p1[r] *= SCALE_DN;
+          } else if (fabs(p2) < SCALE_DN && fabs(p0[r]) < SCALE_DN) {
+            p0[r] *= SCALE_UP;
+            p1[r] *= SCALE_UP;
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < SPEC_ILP; ++r) {
+        if (cnt[r] <= idx[r])
+          lo[r] = x[r];
+        else
+          hi[r] = x[r];
+      }
+    }
+    // weights: u_1j^2 = det(theta I - T_2:n) / d/dtheta det(theta I - T)
+#pragma unroll
+    for (int r = 0; r < SPEC_ILP; ++r) {
+      if (idx[r] >= n) continue;
+      const double t = 0.5 * (lo[r] + hi[r]);
+      double d0 = 1.0, d1 = t - al[0], q0 = 0.0, q1 = 1.0;   // det and derivative
+      int ed = 0;
+      for (int i = 1; i < n; ++i) {
+        const double c = t - al[i], bb = b2[i - 1];
+        const double d2 = fma(c, d1, -bb * d0);
+        const double q2 = fma(c, q1, fma(-bb, q0, d1));
+        d0 = d1;
+        d1 = d2;
+        q0 = q1;
+        q1 = q2;
+        if (fmax(fabs(d1), fabs(q1)) > SCALE_UP) {
+          d0 *= SCALE_DN;
+          d1 *= SCALE_DN;
+          q0 *= SCALE_DN;
+          q1 *= SCALE_DN;
+          ed += 500;
+        } else if (fmax(fmax(fabs(d1), fabs(q1)), fmax(fabs(d0), fabs(q0))) < SCALE_DN) {
+          d0 *= SCALE_UP;
+          d1 *= SCALE_UP;
+          q0 *= SCALE_UP;
+          q1 *= SCALE_UP;
+          ed -= 500;
+        }
+      }
+      double e0 = 1.0, e1 = n > 1 ? t - al[1] : 1.0;
+      int ee = 0;
+      for (int i = 2; i < n; ++i) {
+        const double e2 = fma(t - al[i], e1, -b2[i - 1] * e0);
+        e0 = e1;
+        e1 = e2;
+        if (fabs(e1) > SCALE_UP) {
+          e0 *= SCALE_DN;
+          e1 *= SCALE_DN;
+          ee += 500;
+        } else if (fmax(fabs(e1), fabs(e0)) < SCALE_DN) {
+          e0 *= SCALE_UP;
+          e1 *= SCALE_UP;
+          ee -= 500;
+        }
+      }
+      th[idx[r]] = t;
+      wt[idx[r]] = fabs(ldexp(e1 / q1, ee - ed));
+    }
   }
+  __syncwarp();
+  // Gauss nodes -> (Omega_j, wt_j) in place; smallest node for the report
   const double b0 = beta0[v];
-  double tmin = d[0];
-  // Gauss nodes -> (Omega_j, wt_j) in place: d <- Omega, u <- wt
-  for (int i = 0; i < n; ++i) {
-    const double th = d[i];
-    tmin = fmin(tmin, th);
-    const double Om = th > 0.0 ? sqrt(th) : 0.0;
-    d[i] = Om;
-    u[i] = (Om > 0.0) ? b0 * b0 * u[i] * u[i] / Om : 0.0;
+  double tmin = 1e300;
+  bool bad = false;
+  for (int i = lane; i < n; i += 32) {
+    const double t = th[i];
+    tmin = fmin(tmin, t);
+    bad |= !(t > 0.0);
+    const double Om = t > 0.0 ? sqrt(t) : 0.0;
+    th[i] = Om;
+    wt[i] = Om > 0.0 ? b0 * b0 * wt[i] / Om : 0.0;
   }
-  if (!(tmin > 0.0)) {
-    atomicOr(status, ST_NOT_SPD);
-  } else {
-    atomicMin(min_theta_bits, (unsigned long long)__double_as_longlong(tmin));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+  bad = __any_sync(0xffffffffu, bad);
+  __syncwarp();
+  if (lane == 0) {
+    if (bad)
+      atomicOr(status, ST_NOT_SPD);
+    else
+      atomicMin(min_theta_bits, (unsigned long long)__double_as_longlong(tmin));
+    const double W = jacobi_from_nodes(th, wt, n, ja, jb_);
+    jb.w0[v] = W;
   }
-  const double W = jacobi_from_nodes(d, u, n, a, e);
-  double *ga = jb.a + (size_t)v * k, *b2 = jb.b2 + (size_t)v * k;
-  for (int i = 0; i < n; ++i) {
-    if (SMEM) ga[i] = a[i];
-    b2[i] = (i + 1 < n) ? e[i] * e[i] : 0.0;
+  __syncwarp();
+  double *ga = jb.a + (size_t)v * k, *gb2 = jb.b2 + (size_t)v * k;
+  for (int i = lane; i < n; i += 32) {
+    ga[i] = ja[i];
+    gb2[i] = (i + 1 < n) ? jb_[i] * jb_[i] : 0.0;
   }
-  jb.w0[v] = W;
 }
 
 void launch_spectral_impl(const double *alpha, const double *beta, const double *beta0,
                           const int *k_eff, int B, int k, JacobiBufs jb, double *scratch,
                           unsigned long long *min_theta_bits, unsigned *status, cudaStream_t st) {
-  const int th = SPEC_THREADS;
-  const size_t smem = (size_t)th * 4 * k * sizeof(double);
-  const dim3 grid((B + th - 1) / th);
-  if (smem <= SPEC_SMEM_MAX) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_spectral<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SPEC_SMEM_MAX);
-      attr = true;
-    }
-    k_spectral<true><<<grid, th, smem, st>>>(alpha, beta, beta0, k_eff, B, k, nullptr, nullptr,
-                                             nullptr, jb, min_theta_bits, status);
-  } else {
-    k_spectral<false><<<grid, th, 0, st>>>(alpha, beta, beta0, k_eff, B, k, scratch,
-                                           scratch + (size_t)B * k, scratch + (size_t)2 * B * k,
-                                           jb, min_theta_bits, status);
+  // warp-parallel Gauss rule: 6 k doubles of shared memory per warp
+  const size_t per_warp = (size_t)6 * k * sizeof(double);
+  const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per_warp));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_spectral_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
   }
+  const dim3 grid((B + warps - 1) / warps);
+  k_spectral_warp<<<grid, 32 * warps, per_warp * warps, st>>>(alpha, beta, beta0, k_eff, B, k,
+                                                              warps, jb, min_theta_bits, status);
+  (void)scratch;
 }
 }  // namespace lgw
