@@ -249,6 +249,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_split(VecCtx c, int j) {
   float r[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) r[t] = 0.f;
+  // four rows per trip keep sixteen independent loads in flight per thread
+#pragma unroll 4
   for (int i = 0; i < nrows; ++i) {
     const float hf = hsf[i];
     const float *qh = bhi_row(c, i, b);
@@ -301,21 +303,51 @@ __global__ void k_second_pass_decide_split(VecCtx c, int j) {
 
 // beta = ||w||, breakdown test, q_next = w / beta into the FP64 ring, the
 // split basis slot and the bf16 contraction operand.  is_start: w = b_tm.
+// beta_{j+1} = ||w|| from the per-chunk partials (one warp per vector, fixed
+// order), the breakdown test, and 1/beta (0 when the vector stops or is not
+// live) for k_normalize_split.
+__global__ void k_beta_split(VecCtx c, int j) {
+  const int b = blockIdx.x, lane = threadIdx.x;
+  const int v = c.vec0 + b;
+  const bool live = b < c.nvec && c.k_eff[v] > j;
+  double inv = 0.0;
+  if (live) {
+    const double *np = c.flag2[b] ? c.norm_c : c.norm_b;
+    if (c.reorth == LGW_REORTH_NONE) np = c.norm_a;
+    double s = 0.0;
+    for (int ch = lane; ch < c.nchunks; ch += 32) s += np[(size_t)b * c.nchunks + ch];
+    s = warp_sum(s);
+    const double beta = sqrt(s);
+    const bool stop = !(beta > c.tol * c.amax[b]);
+    if (lane == 0) {
+      c.beta[(size_t)v * c.k + j] = beta;
+      c.betaj[b] = beta;
+      if (stop) c.k_eff[v] = j + 1;
+    }
+    inv = (stop || !(beta > 0.0)) ? 0.0 : 1.0 / beta;
+  } else if (lane == 0) {
+    c.betaj[b] = 0.0;
+  }
+  if (lane == 0) c.sinv[b] = inv;
+}
+
 __global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j, int is_start) {
   const int chunk = blockIdx.x, b = blockIdx.y;
   const int v = c.vec0 + b;
   const bool real = b < c.nvec;
-  bool live = real && (is_start || c.k_eff[v] > j);
+  bool live = real && is_start;
   __shared__ double sbeta, sinv;
   __shared__ float sdq[VEC_THREADS / 32];
-  double beta = 0.0;
-  if (live) {
-    // ||w||^2 from the per-chunk partials: one warp, fixed order, broadcast
+  double inv = 0.0;
+  if (!is_start) {
+    // beta, the breakdown test and 1/beta come from k_beta_split
+    inv = c.sinv[b];
+    live = inv > 0.0;
+  } else if (live) {
+    // ||b||^2 from the per-chunk partials: one warp, fixed order, broadcast
     if (threadIdx.x < 32) {
-      const double *np = is_start ? c.norm_a : (c.flag2[b] ? c.norm_c : c.norm_b);
-      if (!is_start && c.reorth == LGW_REORTH_NONE) np = c.norm_a;
       double s = 0.0;
-      for (int ch = threadIdx.x; ch < c.nchunks; ch += 32) s += np[(size_t)b * c.nchunks + ch];
+      for (int ch = threadIdx.x; ch < c.nchunks; ch += 32) s += c.norm_a[(size_t)b * c.nchunks + ch];
       s = warp_sum(s);
       if (threadIdx.x == 0) {
         sbeta = sqrt(s);
@@ -323,24 +355,15 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j
       }
     }
     __syncthreads();
-    beta = sbeta;
-    if (is_start) {
-      if (chunk == 0 && threadIdx.x == 0) {
-        c.beta0[v] = beta;
-        c.k_eff[v] = beta > 0.0 ? c.k : 0;
-        c.amax[b] = 0.0;
-        c.betaj[b] = 0.0;
-      }
-      live = beta > 0.0;
-    } else {
-      const bool stop = !(beta > c.tol * c.amax[b]);
-      if (chunk == 0 && threadIdx.x == 0) {
-        c.beta[(size_t)v * c.k + j] = beta;
-        c.betaj[b] = beta;
-        if (stop) c.k_eff[v] = j + 1;
-      }
-      if (stop) live = false;
+    const double beta = sbeta;
+    if (chunk == 0 && threadIdx.x == 0) {
+      c.beta0[v] = beta;
+      c.k_eff[v] = beta > 0.0 ? c.k : 0;
+      c.amax[b] = 0.0;
+      c.betaj[b] = 0.0;
     }
+    live = beta > 0.0;
+    inv = sinv;
   } else if (chunk == 0 && threadIdx.x == 0) {
     c.betaj[b] = 0.0;
   }
@@ -351,7 +374,6 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j
   float *hn = c.bhi + ((size_t)next * c.Bs + b) * c.N;
   float *ln = c.blo ? c.blo + ((size_t)next * c.Bs + b) * c.N : nullptr;
   const double *w = c.w + voff;
-  const double inv = live ? sinv : 0.0;
   const int e0 = elem_base_s(chunk);
   float dq = 0.0f;
 #pragma unroll
@@ -413,6 +435,9 @@ void launch_update_split(const VecCtx &c, int j, int pass, cudaStream_t st) {
 }
 void launch_second_pass_decide_split(const VecCtx &c, int j, cudaStream_t st) {
   k_second_pass_decide_split<<<(c.Bs + 255) / 256, 256, 0, st>>>(c, j);
+}
+void launch_beta_split(const VecCtx &c, int j, cudaStream_t st) {
+  k_beta_split<<<c.Bs, 32, 0, st>>>(c, j);
 }
 void launch_normalize_split(const VecCtx &c, int j, int is_start, cudaStream_t st) {
   k_normalize_split<<<grid_s(c), VEC_THREADS, 0, st>>>(c, j, is_start);

@@ -564,6 +564,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   c.flag2 = wsT<int>(h, "flag2", (size_t)Bs);
   c.amax = wsT<double>(h, "amax", (size_t)Bs);
   c.betaj = wsT<double>(h, "betaj", (size_t)Bs);
+  c.sinv = wsT<double>(h, "sinv", (size_t)Bs);
   c.alpha = alpha;
   c.beta = beta;
   c.beta0 = beta0;
@@ -810,6 +811,8 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
           launch_update_split(c, j, 2, st);
           check_launch(h, "update_split2");
           tm.mark(C_NORM);
+          launch_beta_split(c, j, st);
+          check_launch(h, "beta_split");
           launch_normalize_split(c, j, 0, st);
           check_launch(h, "normalize_split");
           continue;

@@ -91,6 +91,7 @@ struct VecCtx {
   int *flag2;             // [Bs] second CGS pass taken
   double *amax;           // [Bs]
   double *betaj;          // [Bs] beta_j for the running step
+  double *sinv;           // [Bs] 1 / beta_{j+1} (0: stopped or not live), split path
   double *alpha, *beta, *beta0;   // global [B][k], [B][k], [B]
   int *k_eff;             // global [B]
   int *n_second;          // counter of second passes
@@ -219,6 +220,7 @@ void launch_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_reduce_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_update_split(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_second_pass_decide_split(const VecCtx &c, int j, cudaStream_t st);
+void launch_beta_split(const VecCtx &c, int j, cudaStream_t st);
 void launch_normalize_split(const VecCtx &c, int j, int is_start, cudaStream_t st);
 void launch_scale_rows_to_bf16(const double *x, const double *dsq, int Bs, int N,
                                __nv_bfloat16 *out, cudaStream_t st);
