@@ -22,6 +22,10 @@
 //         BF16 operator), so the sum is formed in FP32 from q_hi alone (4
 //         bytes per element); its rounding is far below the FP64 resolution
 //         of w.  The second pass (where taken) is identical.
+//  norm   ||w - Q h||^2 = ||w||^2 - ||h||^2 gives beta_{j+1} before the
+//         update, so the update pass that finishes a vector also writes
+//         q_{j+1} = (w - Q h) / beta_{j+1} in every form the next step reads,
+//         and w is not stored and re-read for a separate normalisation.
 //
 // Block layout as in the FP64 kernels: one block per (chunk of VEC_CHUNK
 // elements, vector), eight elements per thread.
@@ -212,138 +216,184 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_dots_split(VecCtx c, int j) 
   }
 }
 
-// h[b][i] = sum over chunks (fixed order).
-__global__ void k_reduce_dots_split(VecCtx c, int j, int pass) {
+// h[b][i] = sum over chunks (fixed order), then the norm of the projected
+// vector without reading it back: with Q orthonormal,
+//   ||w - Q h||^2 = ||w||^2 - ||h||^2,
+// where the error of the right side (dot-product rounding, ~2^-48 ||w||
+// per h_i, and the departure of Q^T Q from I, met only through the small
+// h) is far below the FP64 resolution of ||w||^2 whenever no second pass
+// is due.  Pass 1 decides the second pass from it (CGS2: always; CGS1K:
+// when the first pass removes more than half of ||w||^2, the 1/sqrt(2)
+// criterion); every vector that takes no second pass gets beta_{j+1}, the
+// breakdown test and 1/beta here (pass 2: the others, from the measured
+// ||w'||^2 of pass 1), and its update kernel writes q_{j+1} directly.
+// Not-live vectors get flag2 = 0 and 1/beta = 0, so the update writes
+// zeros into their next slot.
+__global__ void __launch_bounds__(256) k_reduce_dots_split(VecCtx c, int j, int pass) {
+  __shared__ double red[256 / 32];
   const int b = blockIdx.x;
-  if (!live_s(c, b, j)) return;
+  const int v = c.vec0 + b;
+  if (!live_s(c, b, j)) {
+    if (pass == 1 && threadIdx.x == 0) {
+      c.flag2[b] = 0;
+      c.sinv[b] = 0.0;
+      c.betaj[b] = 0.0;
+    }
+    return;
+  }
   if (pass == 2 && !c.flag2[b]) return;
+  double hh = 0.0;
   for (int i = threadIdx.x; i <= j; i += blockDim.x) {
     const double *p = c.dot_part + (size_t)b * c.nchunks * c.kmax1 + i;
     double s = 0.0;
     for (int ch = 0; ch < c.nchunks; ++ch) s += p[(size_t)ch * c.kmax1];
     c.h[(size_t)b * c.kmax1 + i] = s;
+    hh = fma(s, s, hh);
     if (pass == 1 && i == j) {
-      const size_t ai = (size_t)(c.vec0 + b) * c.k + j;
+      const size_t ai = (size_t)v * c.k + j;
       const double a = c.alpha[ai] + s;
       c.alpha[ai] = a;
       c.amax[b] = fmax(c.amax[b], fabs(a));
     }
   }
+  const double *np = (pass == 1 ? c.norm_a : c.norm_b) + (size_t)b * c.nchunks;
+  double nw = 0.0;
+  for (int ch = threadIdx.x; ch < c.nchunks; ch += blockDim.x) nw += np[ch];
+  hh = block_sum(hh, red);   // the barriers also publish amax[b]
+  nw = block_sum(nw, red);
+  if (threadIdx.x != 0) return;
+  const double rest = nw - hh;   // ||w - Q h||^2
+  int f = 0;
+  if (pass == 1) {
+    f = c.reorth == LGW_REORTH_CGS2 ? 1 : (rest < 0.5 * nw);
+    c.flag2[b] = f;
+    if (f && c.reorth != LGW_REORTH_CGS2) atomicAdd(c.n_second, 1);
+  }
+  if (f) return;
+  const double beta = sqrt(fmax(rest, 0.0));
+  const bool stop = !(beta > c.tol * c.amax[b]);
+  c.beta[(size_t)v * c.k + j] = beta;
+  c.betaj[b] = beta;
+  if (stop) c.k_eff[v] = j + 1;
+  c.sinv[b] = (stop || !(beta > 0.0)) ? 0.0 : 1.0 / beta;
 }
 
 // w <- w - Q h with every coefficient small: FP32 products and sum from q_hi.
+// A vector whose beta_{j+1} is already known (no second pass after this
+// one) is normalised in the same pass: q_{j+1} = (w - Q h) / beta_{j+1}
+// into the FP64 ring, the split basis slot and the bf16 contraction
+// operand, with the per-chunk partials of sum Delta^2 q_{j+1}^2; w itself is
+// not written back.  A vector due for a second pass stores w and its norm
+// partials instead.  Not-live vectors (padding, stopped) get zeros in their
+// next slot.
 template <int PASS>
 __global__ void __launch_bounds__(VEC_THREADS) k_update_split(VecCtx c, int j) {
   extern __shared__ float hsf[];
   __shared__ double red[VEC_THREADS / 32];
+  __shared__ float sdq[VEC_THREADS / 32];
   const int chunk = blockIdx.x, b = blockIdx.y;
-  if (!live_s(c, b, j)) return;
-  if (PASS == 2 && !c.flag2[b]) return;
-  const double *hb = c.h + (size_t)b * c.kmax1;
-  const int nrows = j + 1;
-  for (int i = threadIdx.x; i < nrows; i += VEC_THREADS) hsf[i] = (float)hb[i];
-  __syncthreads();
+  const bool live = live_s(c, b, j);
+  const bool f2 = live && c.flag2[b];
+  if (PASS == 2 && !f2) return;
+  const bool fin = PASS == 2 || !f2;            // this launch writes q_{j+1}
+  const double inv = (fin && live) ? c.sinv[b] : 0.0;
+  const bool work = fin ? inv > 0.0 : true;     // w - Q h is needed
   const size_t voff = (size_t)b * c.N;
   double *w = c.w + voff;
   const int e0 = elem_base_s(chunk);
   float r[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) r[t] = 0.f;
-  // four rows per trip keep sixteen independent loads in flight per thread
+  if (work) {
+    const double *hb = c.h + (size_t)b * c.kmax1;
+    const int nrows = j + 1;
+    for (int i = threadIdx.x; i < nrows; i += VEC_THREADS) hsf[i] = (float)hb[i];
+    __syncthreads();
+    // four rows per trip keep sixteen independent loads in flight per thread
 #pragma unroll 4
-  for (int i = 0; i < nrows; ++i) {
-    const float hf = hsf[i];
-    const float *qh = bhi_row(c, i, b);
+    for (int i = 0; i < nrows; ++i) {
+      const float hf = hsf[i];
+      const float *qh = bhi_row(c, i, b);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int e = e0 + u * 64;
-      if (e < c.N) {
-        const float2 q2 = *reinterpret_cast<const float2 *>(qh + e);
-        r[2 * u] = fmaf(hf, q2.x, r[2 * u]);
-        r[2 * u + 1] = fmaf(hf, q2.y, r[2 * u + 1]);
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * 64;
+        if (e < c.N) {
+          const float2 q2 = *reinterpret_cast<const float2 *>(qh + e);
+          r[2 * u] = fmaf(hf, q2.x, r[2 * u]);
+          r[2 * u + 1] = fmaf(hf, q2.y, r[2 * u + 1]);
+        }
       }
     }
   }
-  double nrm = 0.0;
+  if (!fin) {
+    double nrm = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * 64;
+      if (e >= c.N) continue;
+      double2 w2 = *reinterpret_cast<const double2 *>(w + e);
+      w2.x -= (double)r[2 * u];
+      w2.y -= (double)r[2 * u + 1];
+      *reinterpret_cast<double2 *>(w + e) = w2;
+      nrm = fma(w2.x, w2.x, fma(w2.y, w2.y, nrm));
+    }
+    nrm = block_sum(nrm, red);
+    if (threadIdx.x == 0) c.norm_b[(size_t)b * c.nchunks + chunk] = nrm;
+    return;
+  }
+  const int next = j + 1;
+  double *qn = slot_ptr(c, next) + voff;
+  float *hn = c.bhi + ((size_t)next * c.Bs + b) * c.N;
+  float *ln = c.blo ? c.blo + ((size_t)next * c.Bs + b) * c.N : nullptr;
+  float dq = 0.0f;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int e = e0 + u * 64;
     if (e >= c.N) continue;
-    double2 w2 = *reinterpret_cast<const double2 *>(w + e);
-    w2.x -= (double)r[2 * u];
-    w2.y -= (double)r[2 * u + 1];
-    *reinterpret_cast<double2 *>(w + e) = w2;
-    nrm = fma(w2.x, w2.x, fma(w2.y, w2.y, nrm));
-  }
-  nrm = block_sum(nrm, red);
-  if (threadIdx.x == 0) (PASS == 1 ? c.norm_b : c.norm_c)[(size_t)b * c.nchunks + chunk] = nrm;
-}
-
-// Second pass where the first pass removed more than half of ||w||^2
-// (1/sqrt(2) norm criterion), or always (CGS2).
-__global__ void k_second_pass_decide_split(VecCtx c, int j) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= c.Bs) return;
-  int f = 0;
-  if (live_s(c, b, j)) {
-    if (c.reorth == LGW_REORTH_CGS2) {
-      f = 1;
-    } else {
-      double na = 0.0, nb = 0.0;
-      for (int ch = 0; ch < c.nchunks; ++ch) {
-        na += c.norm_a[(size_t)b * c.nchunks + ch];
-        nb += c.norm_b[(size_t)b * c.nchunks + ch];
-      }
-      f = nb < 0.5 * na;
-      if (f) atomicAdd(c.n_second, 1);
+    double2 q2 = make_double2(0.0, 0.0);
+    if (work) {
+      q2 = *reinterpret_cast<const double2 *>(w + e);
+      q2.x = (q2.x - (double)r[2 * u]) * inv;
+      q2.y = (q2.y - (double)r[2 * u + 1]) * inv;
+    }
+    *reinterpret_cast<double2 *>(qn + e) = q2;
+    const float hx = __double2float_rn(q2.x), hy = __double2float_rn(q2.y);
+    dq = fmaf(c.d2f[e] * hx, hx, fmaf(c.d2f[e + 1] * hy, hy, dq));
+    *reinterpret_cast<float2 *>(hn + e) = make_float2(hx, hy);
+    if (ln != nullptr)
+      *reinterpret_cast<float2 *>(ln + e) = make_float2(__double2float_rn(q2.x - (double)hx),
+                                                        __double2float_rn(q2.y - (double)hy));
+    if (c.xh != nullptr) {
+      __nv_bfloat162 x2;
+      x2.x = __float2bfloat16_rn(c.dsqf[e] * hx);
+      x2.y = __float2bfloat16_rn(c.dsqf[e + 1] * hy);
+      *reinterpret_cast<__nv_bfloat162 *>(c.xh + voff + e) = x2;
     }
   }
-  c.flag2[b] = f;
-}
-
-// beta = ||w||, breakdown test, q_next = w / beta into the FP64 ring, the
-// split basis slot and the bf16 contraction operand.  is_start: w = b_tm.
-// beta_{j+1} = ||w|| from the per-chunk partials (one warp per vector, fixed
-// order), the breakdown test, and 1/beta (0 when the vector stops or is not
-// live) for k_normalize_split.
-__global__ void k_beta_split(VecCtx c, int j) {
-  const int b = blockIdx.x, lane = threadIdx.x;
-  const int v = c.vec0 + b;
-  const bool live = b < c.nvec && c.k_eff[v] > j;
-  double inv = 0.0;
-  if (live) {
-    const double *np = c.flag2[b] ? c.norm_c : c.norm_b;
-    if (c.reorth == LGW_REORTH_NONE) np = c.norm_a;
-    double s = 0.0;
-    for (int ch = lane; ch < c.nchunks; ch += 32) s += np[(size_t)b * c.nchunks + ch];
-    s = warp_sum(s);
-    const double beta = sqrt(s);
-    const bool stop = !(beta > c.tol * c.amax[b]);
-    if (lane == 0) {
-      c.beta[(size_t)v * c.k + j] = beta;
-      c.betaj[b] = beta;
-      if (stop) c.k_eff[v] = j + 1;
+  if (c.dq2_part != nullptr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dq += __shfl_xor_sync(0xffffffffu, dq, o);
+    if ((threadIdx.x & 31) == 0) sdq[threadIdx.x >> 5] = dq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.0f;
+      for (int w8 = 0; w8 < VEC_THREADS / 32; ++w8) t += sdq[w8];
+      c.dq2_part[(size_t)b * c.nchunks + chunk] = t;
     }
-    inv = (stop || !(beta > 0.0)) ? 0.0 : 1.0 / beta;
-  } else if (lane == 0) {
-    c.betaj[b] = 0.0;
   }
-  if (lane == 0) c.sinv[b] = inv;
 }
 
-__global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j, int is_start) {
+// q_0 = b / ||b|| (b = Delta^1/2 L M in w, its norm partials in norm_a)
+// into ring slot 0, the split basis slot 0 and the bf16 contraction
+// operand; beta0, k_eff and the per-vector state of the recurrence.
+__global__ void __launch_bounds__(VEC_THREADS) k_start_split(VecCtx c) {
   const int chunk = blockIdx.x, b = blockIdx.y;
   const int v = c.vec0 + b;
-  const bool real = b < c.nvec;
-  bool live = real && is_start;
   __shared__ double sbeta, sinv;
   __shared__ float sdq[VEC_THREADS / 32];
+  bool live = b < c.nvec;
   double inv = 0.0;
-  if (!is_start) {
-    // beta, the breakdown test and 1/beta come from k_beta_split
-    inv = c.sinv[b];
-    live = inv > 0.0;
-  } else if (live) {
+  if (live) {
     // ||b||^2 from the per-chunk partials: one warp, fixed order, broadcast
     if (threadIdx.x < 32) {
       double s = 0.0;
@@ -367,12 +417,10 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j
   } else if (chunk == 0 && threadIdx.x == 0) {
     c.betaj[b] = 0.0;
   }
-  const int next = is_start ? 0 : j + 1;
   const size_t voff = (size_t)b * c.N;
-  double *qn = slot_ptr(c, next) + voff;
-  const bool keep_basis = next < c.k + 1;
-  float *hn = c.bhi + ((size_t)next * c.Bs + b) * c.N;
-  float *ln = c.blo ? c.blo + ((size_t)next * c.Bs + b) * c.N : nullptr;
+  double *qn = slot_ptr(c, 0) + voff;
+  float *hn = c.bhi + (size_t)b * c.N;
+  float *ln = c.blo ? c.blo + (size_t)b * c.N : nullptr;
   const double *w = c.w + voff;
   const int e0 = elem_base_s(chunk);
   float dq = 0.0f;
@@ -389,12 +437,10 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize_split(VecCtx c, int j
     *reinterpret_cast<double2 *>(qn + e) = q2;
     const float hx = __double2float_rn(q2.x), hy = __double2float_rn(q2.y);
     dq = fmaf(c.d2f[e] * hx, hx, fmaf(c.d2f[e + 1] * hy, hy, dq));
-    if (keep_basis) {
-      *reinterpret_cast<float2 *>(hn + e) = make_float2(hx, hy);
-      if (c.blo != nullptr)
-        *reinterpret_cast<float2 *>(ln + e) = make_float2(__double2float_rn(q2.x - (double)hx),
-                                                          __double2float_rn(q2.y - (double)hy));
-    }
+    *reinterpret_cast<float2 *>(hn + e) = make_float2(hx, hy);
+    if (ln != nullptr)
+      *reinterpret_cast<float2 *>(ln + e) = make_float2(__double2float_rn(q2.x - (double)hx),
+                                                        __double2float_rn(q2.y - (double)hy));
     if (c.xh != nullptr) {
       __nv_bfloat162 x2;
       x2.x = __float2bfloat16_rn(c.dsqf[e] * hx);
@@ -433,14 +479,8 @@ void launch_update_split(const VecCtx &c, int j, int pass, cudaStream_t st) {
   else
     k_update_split<2><<<grid_s(c), VEC_THREADS, sh, st>>>(c, j);
 }
-void launch_second_pass_decide_split(const VecCtx &c, int j, cudaStream_t st) {
-  k_second_pass_decide_split<<<(c.Bs + 255) / 256, 256, 0, st>>>(c, j);
-}
-void launch_beta_split(const VecCtx &c, int j, cudaStream_t st) {
-  k_beta_split<<<c.Bs, 32, 0, st>>>(c, j);
-}
-void launch_normalize_split(const VecCtx &c, int j, int is_start, cudaStream_t st) {
-  k_normalize_split<<<grid_s(c), VEC_THREADS, 0, st>>>(c, j, is_start);
+void launch_start_split(const VecCtx &c, cudaStream_t st) {
+  k_start_split<<<grid_s(c), VEC_THREADS, 0, st>>>(c);
 }
 
 }  // namespace lgw

@@ -706,7 +706,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
         check_launch(h, "start_from_v");
       }
       if (split)
-        launch_normalize_split(c, 0, 1, st);
+        launch_start_split(c, st);
       else
         launch_normalize(c, 0, 1, nullptr, st);
       check_launch(h, "normalize(start)");
@@ -799,22 +799,16 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
           launch_reduce_dots_split(c, j, 1, st);
           check_launch(h, "reduce_dots_split");
           tm.mark(C_UPDATE);
+          // q_{j+1} for the vectors that take no second pass, w' for the rest
           launch_update_split(c, j, 1, st);
           check_launch(h, "update_split");
           tm.mark(C_PASS2);
-          launch_second_pass_decide_split(c, j, st);
-          check_launch(h, "second_pass_decide_split");
           launch_dots_split(c, j, 2, st);
           check_launch(h, "dots_split2");
           launch_reduce_dots_split(c, j, 2, st);
           check_launch(h, "reduce_dots_split2");
           launch_update_split(c, j, 2, st);
           check_launch(h, "update_split2");
-          tm.mark(C_NORM);
-          launch_beta_split(c, j, st);
-          check_launch(h, "beta_split");
-          launch_normalize_split(c, j, 0, st);
-          check_launch(h, "normalize_split");
           continue;
         }
         launch_alpha_axpy(c, j, st);

@@ -219,9 +219,7 @@ void launch_second_pass_decide_j(const VecCtx &c, int j, cudaStream_t st);
 void launch_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_reduce_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_update_split(const VecCtx &c, int j, int pass, cudaStream_t st);
-void launch_second_pass_decide_split(const VecCtx &c, int j, cudaStream_t st);
-void launch_beta_split(const VecCtx &c, int j, cudaStream_t st);
-void launch_normalize_split(const VecCtx &c, int j, int is_start, cudaStream_t st);
+void launch_start_split(const VecCtx &c, cudaStream_t st);
 void launch_scale_rows_to_bf16(const double *x, const double *dsq, int Bs, int N,
                                __nv_bfloat16 *out, cudaStream_t st);
 
