@@ -3,7 +3,8 @@
 // L is stored as L8 = e4m3(L / s_mu) with one power-of-two scale per column
 // mu (s_mu = 2^ceil(log2(max_vc |L[vc][mu]| / 448)), so the largest entry
 // maps into (224, 448] and dequantisation is exact); both row-major copies
-// L8 [N][A] (K = N_aux contiguous, gemm2) and L8t [A][N] (K = N_vc, gemm1).
+// L8 [N][A] (K = N_aux contiguous, gemm2) and L8t [A][N] (K = N_vc, gemm1,
+// K-block-major like x8).
 // Per Lanczos step:
 //   x8 = e4m3(Delta^1/2 q / s_b)       s_b per vector (k_quant_x8)
 //   Y^T[mu][b] = s_b s_mu sum_vc L8t[mu][vc] x8[b][vc]     (tensor cores)
@@ -61,7 +62,7 @@ __global__ void k_col_scales(const unsigned *__restrict__ colmax, int A, float *
 }
 
 // L8 = e4m3(L / s_mu) [N][A] from L [nr][nc] (row stride ld, zero padded)
-// and its transpose L8t [A][N] (32 x 32 tiles)
+// and its transpose L8t [A][N], K-block-major (32 x 32 tiles)
 __global__ void k_quantize_L8(const double *__restrict__ src, int ld, int nr, int nc, int N, int A,
                               const float *__restrict__ sL, uint8_t *__restrict__ L8,
                               uint8_t *__restrict__ L8t) {
@@ -81,21 +82,21 @@ __global__ void k_quantize_L8(const double *__restrict__ src, int ld, int nr, in
   __syncthreads();
   for (int cc = ty; cc < 32; cc += 8) {
     const int c = c0 + cc, r = r0 + tx;
-    if (r < N && c < A) L8t[(size_t)c * N + r] = tile[tx][cc];
+    if (r < N && c < A) L8t[kblk_e4m3(c, r, A)] = tile[tx][cc];
   }
 }
 
 // x8[b] = e4m3(xh[b] / s_b), s_b from max |xh[b]|; one block per vector.
-__global__ void __launch_bounds__(256) k_quant_x8(const __nv_bfloat16 *__restrict__ xh, int N,
-                                                  uint8_t *__restrict__ x8,
+// Both operands are K-block-major over Bs rows.
+__global__ void __launch_bounds__(256) k_quant_x8(const __nv_bfloat16 *__restrict__ xh, int Bs,
+                                                  int N, uint8_t *__restrict__ x8,
                                                   float *__restrict__ sx) {
   __shared__ float red[8];
   __shared__ float sc;
   const int b = blockIdx.x;
-  const __nv_bfloat16 *x = xh + (size_t)b * N;
-  uint8_t *o = x8 + (size_t)b * N;
   float m = 0.0f;
-  for (int i = threadIdx.x; i < N; i += 256) m = fmaxf(m, fabsf(__bfloat162float(x[i])));
+  for (int i = threadIdx.x; i < N; i += 256)
+    m = fmaxf(m, fabsf(__bfloat162float(xh[kblk_bf16(b, i, Bs)])));
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, s));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -108,7 +109,8 @@ __global__ void __launch_bounds__(256) k_quant_x8(const __nv_bfloat16 *__restric
   }
   __syncthreads();
   const float inv = 1.0f / sc;   // a power of two: exact
-  for (int i = threadIdx.x; i < N; i += 256) o[i] = to_e4m3(__bfloat162float(x[i]) * inv);
+  for (int i = threadIdx.x; i < N; i += 256)
+    x8[kblk_e4m3(b, i, Bs)] = to_e4m3(__bfloat162float(xh[kblk_bf16(b, i, Bs)]) * inv);
 }
 
 // From the split-K partials of gemm1: y_mu = s_b s_mu sum_p Ypart, then
@@ -182,7 +184,7 @@ void launch_prepare_fp8(const double *src, int ld, int nr, int nc, const SysDev 
 
 void launch_quant_x8(const __nv_bfloat16 *xh, int Bs, int N, uint8_t *x8, float *sx,
                      cudaStream_t st) {
-  k_quant_x8<<<Bs, 256, 0, st>>>(xh, N, x8, sx);
+  k_quant_x8<<<Bs, 256, 0, st>>>(xh, Bs, N, x8, sx);
 }
 
 void launch_reduce_y_fp8(const float *Ypart, int splits, int Bs, int A, const float *sx,

@@ -94,6 +94,15 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, ui
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
 }
+// 3-D form for the K-block-major operands: (0, row, K block)
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, uint64_t *bar, int x,
+                                            int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                    smem_u32(slot)),
@@ -197,6 +206,8 @@ struct EpiArgs {
   // K loop start rotated by the M tile (spreads concurrent CTAs over HBM
   // channels) or not (CTAs sharing the B tile stream it in step, from L2)
   int rot;
+  // operand maps are 3-D K-block-major (kblk_*) instead of 2-D row-major
+  int a3, b3;
 };
 
 enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2, E_LANCZOS_NA = 3, E_SPLITB = 4, E_VACC = 5,
@@ -253,9 +264,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(&empty[s], ph ^ 1, ea.status)) break;
         mbar_expect_tx(&full[s], C::STAGE);
         uint8_t *sa = smem + s * C::STAGE;
-        const int kx = (kb0 + (it + (ea.rot ? m_tile : 0)) % nk) * (BK * 2 / EB);
-        tma_load_2d(sa, &tmA, &full[s], kx, m_tile * BM);
-        tma_load_2d(sa + C::A_BYTES, &tmB, &full[s], kx, n_tile * BN);
+        const int kb = kb0 + (it + (ea.rot ? m_tile : 0)) % nk;
+        const int kx = kb * (BK * 2 / EB);
+        if (ea.a3)
+          tma_load_3d(sa, &tmA, &full[s], 0, m_tile * BM, kb);
+        else
+          tma_load_2d(sa, &tmA, &full[s], kx, m_tile * BM);
+        if (ea.b3)
+          tma_load_3d(sa + C::A_BYTES, &tmB, &full[s], 0, n_tile * BN, kb);
+        else
+          tma_load_2d(sa + C::A_BYTES, &tmB, &full[s], kx, n_tile * BN);
         issued = it + 1;
       }
       // Drain: every issued copy must have landed before the CTA may exit.
@@ -484,6 +502,26 @@ static bool encode_2d(CUtensorMap *tm, const void *base, uint64_t inner, uint64_
   return r == CUDA_SUCCESS;
 }
 
+// 3-D map of a K-block-major operand (kblk_bf16 / kblk_e4m3): dims (one
+// 128-byte row of elements, rows, K blocks), box (128 bytes, box_rows, 1);
+// each box is one contiguous 128 x box_rows-byte run, swizzled into the
+// same shared-memory image as the 2-D row-major box.
+static bool encode_kblk(CUtensorMap *tm, const void *base, uint64_t kblocks, uint64_t rows,
+                        uint32_t box_rows, int elem_bytes = 2) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)(128 / elem_bytes), rows, kblocks};
+  cuuint64_t strides[2] = {128, rows * 128};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / elem_bytes), box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(tm,
+                   elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                   3, const_cast<void *>(base), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 static int choose_splits(int tiles, int num_kb, int nsm) {
   // Fill whole waves of one CTA per SM: pick the split count whose CTA total
   // wastes the least of its last wave, with at least 8 K blocks per split.
@@ -536,10 +574,10 @@ TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *
   p->cdf = s.cdf;
   // the BF16 copies of L are absent for a system prepared without them
   // (E4M3 plans); their maps stay unset then
-  bool ok = encode_2d(&p->g1B, xh, (uint64_t)s.N, (uint64_t)Bs, (uint32_t)p->BN1) &&
+  bool ok = encode_kblk(&p->g1B, xh, (uint64_t)s.N / 64, (uint64_t)Bs, (uint32_t)p->BN1) &&
             encode_2d(&p->g2B, yh, (uint64_t)s.A, (uint64_t)Bs, (uint32_t)p->BN2);
   if (ok && s.Lb) {
-    ok = encode_2d(&p->g1A, s.Ltb, (uint64_t)s.N, (uint64_t)s.A, tc::BM) &&
+    ok = encode_kblk(&p->g1A, s.Ltb, (uint64_t)s.N / 64, (uint64_t)s.A, tc::BM) &&
          encode_2d(&p->g2A, s.Lb, (uint64_t)s.A, (uint64_t)s.N, tc::BM) &&
          encode_2d(&p->g2Alo, s.Lb_lo, (uint64_t)s.A, (uint64_t)s.N, tc::BM);
     p->has_bf16 = ok;
@@ -588,6 +626,7 @@ void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st) {
   ea.ldo = p->A;
   ea.status = status;
   ea.rot = p->rot1;
+  ea.a3 = ea.b3 = 1;   // L^T and X are K-block-major
   if (p->fp8) {
     // same split count; K blocks of 128 elements
     const int nkb = p->N / 128;
@@ -700,14 +739,19 @@ void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaSt
 }
 
 // out (=, or += if add) sum_{p < np} A_p B_p^T with A_p [M][K], B_p [Ncols][K]
-// BF16 row-major (K contiguous), FP32 accumulation in tensor memory over
-// K chunks of at most kchunk, each chunk added to the FP64 output.
-// out[col * ldo + row].  K % 8 == 0 (16-byte TMA row stride).
-bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const __nv_bfloat16 *const *B, int M,
-                    int Ncols, int K, int kchunk, double *out, int ldo, int add, unsigned *status,
-                    cudaStream_t st, char *err, size_t errn) {
-  if (K % 8 != 0 || kchunk % tc::BK != 0 || kchunk <= 0) {
-    snprintf(err, errn, "tc_gemm_f64out: K = %d not a multiple of 8 or bad chunk", K);
+// BF16 row-major (K contiguous), or A_p K-block-major (kblk_bf16 over M
+// rows) where a_kblk[p] != 0; FP32 accumulation in tensor memory over K
+// chunks of at most kchunk, each chunk added to the FP64 output.
+// out[col * ldo + row].  K % 8 == 0 (16-byte TMA row stride); K % 64 == 0
+// for a K-block-major operand.
+bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const int *a_kblk,
+                    const __nv_bfloat16 *const *B, int M, int Ncols, int K, int kchunk,
+                    double *out, int ldo, int add, unsigned *status, cudaStream_t st, char *err,
+                    size_t errn) {
+  bool any_kblk = false;
+  for (int p = 0; p < np; ++p) any_kblk = any_kblk || (a_kblk && a_kblk[p]);
+  if (K % 8 != 0 || kchunk % tc::BK != 0 || kchunk <= 0 || (any_kblk && K % tc::BK != 0)) {
+    snprintf(err, errn, "tc_gemm_f64out: K = %d not a multiple of 8 (64 K-block-major) or bad chunk", K);
     return false;
   }
   tc::EpiArgs ea{};
@@ -720,8 +764,13 @@ bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const __nv_bfloat16 *
     const int kc = std::min(kchunk, K - k0);
     for (int p = 0; p < np; ++p) {
       CUtensorMap ta, tb;
-      if (!encode_2d(&ta, A[p] + k0, (uint64_t)kc, (uint64_t)M, tc::BM, (uint64_t)K) ||
-          !encode_2d(&tb, B[p] + k0, (uint64_t)kc, (uint64_t)Ncols, 256, (uint64_t)K)) {
+      const bool kb = a_kblk && a_kblk[p];
+      const bool ta_ok =
+          kb ? encode_kblk(&ta, A[p] + (size_t)(k0 / tc::BK) * M * tc::BK, (uint64_t)kc / tc::BK,
+                           (uint64_t)M, tc::BM)
+             : encode_2d(&ta, A[p] + k0, (uint64_t)kc, (uint64_t)M, tc::BM, (uint64_t)K);
+      ea.a3 = kb ? 1 : 0;
+      if (!ta_ok || !encode_2d(&tb, B[p] + k0, (uint64_t)kc, (uint64_t)Ncols, 256, (uint64_t)K)) {
         snprintf(err, errn, "cuTensorMapEncodeTiled failed (tc_gemm_f64out)");
         return false;
       }
@@ -758,10 +807,10 @@ std::map<TuneKey, TuneVal> g_tune;
 std::mutex g_tune_mu;
 
 bool plan_encode_b(TcPlan *p) {
-  bool ok = encode_2d(&p->g1B, p->xh, (uint64_t)p->N, (uint64_t)p->Bs, (uint32_t)p->BN1) &&
+  bool ok = encode_kblk(&p->g1B, p->xh, (uint64_t)p->N / 64, (uint64_t)p->Bs, (uint32_t)p->BN1) &&
             encode_2d(&p->g2B, p->yh, (uint64_t)p->A, (uint64_t)p->Bs, (uint32_t)p->BN2);
   if (ok && p->fp8)
-    ok = encode_2d(&p->f1B, p->x8, (uint64_t)p->N, (uint64_t)p->Bs, (uint32_t)p->BN1, 0, 1) &&
+    ok = encode_kblk(&p->f1B, p->x8, (uint64_t)p->N / 128, (uint64_t)p->Bs, (uint32_t)p->BN1, 1) &&
          encode_2d(&p->f2B, p->y8, (uint64_t)p->A, (uint64_t)p->Bs, (uint32_t)p->BN2, 0, 1);
   return ok;
 }
@@ -883,7 +932,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
   return cudaGetLastError() == cudaSuccess;
 }
 
-// Switch a plan to E4M3 operands: L8t [A][N] and x8 [Bs][N] for gemm1, L8
+// Switch a plan to E4M3 operands: L8t [A][N] and x8 [Bs][N] (K-block-major) for gemm1, L8
 // [N][A] and y8 [Bs][A] for gemm2 (ty: per-vector scale of y8).
 bool tc_plan_enable_fp8(TcPlan *p, const uint8_t *L8t, const uint8_t *L8, const uint8_t *x8,
                         const uint8_t *y8, const float *ty) {
@@ -891,7 +940,7 @@ bool tc_plan_enable_fp8(TcPlan *p, const uint8_t *L8t, const uint8_t *L8, const 
   p->x8 = x8;
   p->y8 = y8;
   p->ty = ty;
-  return encode_2d(&p->f1A, L8t, (uint64_t)p->N, (uint64_t)p->A, tc::BM, 0, 1) &&
+  return encode_kblk(&p->f1A, L8t, (uint64_t)p->N / 128, (uint64_t)p->A, tc::BM, 1) &&
          encode_2d(&p->f2A, L8, (uint64_t)p->A, (uint64_t)p->N, tc::BM, 0, 1) &&
          plan_encode_b(p);
 }

@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize(VecCtx c, int j, int 
       __nv_bfloat162 x2;
       x2.x = __double2bfloat16(c.dsq[e] * q2.x);
       x2.y = __double2bfloat16(c.dsq[e + 1] * q2.y);
-      *reinterpret_cast<__nv_bfloat162 *>(c.xh + voff + e) = x2;
+      *reinterpret_cast<__nv_bfloat162 *>(c.xh + kblk_bf16(b, e, c.Bs)) = x2;
     }
   }
 }
@@ -381,12 +381,14 @@ __global__ void __launch_bounds__(VEC_THREADS) k_norm_partials(VecCtx c, const d
   if (threadIdx.x == 0) out[(size_t)b * c.nchunks + chunk] = nrm;
 }
 
+// out = bf16(Delta^1/2 x) for x [Bs][N], written K-block-major (the GEMM1
+// operand layout)
 __global__ void k_scale_rows_to_bf16(const double *__restrict__ x, const double *__restrict__ dsq,
                                      int Bs, int N, __nv_bfloat16 *__restrict__ out) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t n = (size_t)Bs * N;
   if (i >= n) return;
-  out[i] = __double2bfloat16(dsq[i % N] * x[i]);
+  out[kblk_bf16((int)(i / N), (int)(i % N), Bs)] = __double2bfloat16(dsq[i % N] * x[i]);
 }
 
 // ---------------------------------------------------------------------------

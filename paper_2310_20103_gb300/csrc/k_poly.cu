@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cheb_step(PolyStep p) {
       __nv_bfloat162 x2;
       x2.x = __float2bfloat16_rn(p.dsqf[e] * (float)r.x);
       x2.y = __float2bfloat16_rn(p.dsqf[e + 1] * (float)r.y);
-      *reinterpret_cast<__nv_bfloat162 *>(p.xh + o) = x2;
+      // K-block-major over the Bs = gridDim.y vectors of the launch
+      *reinterpret_cast<__nv_bfloat162 *>(p.xh + kblk_bf16(b, e, gridDim.y)) = x2;
     }
   }
 }

@@ -43,7 +43,7 @@ __global__ void k_pad_L(const double *__restrict__ L, int n_vc, int n_aux, int N
 }
 
 // BF16 copies from L [nr][nc] (row stride ld), zero padded to [N][A]:
-// Lb = bf16(L) [N][A], Ltb = bf16(L)^T [A][N] and Lb_lo = bf16(L - bf16(L)),
+// Lb = bf16(L) [N][A], Ltb = bf16(L)^T [A][N] (K-block-major) and Lb_lo = bf16(L - bf16(L)),
 // through a 32x32 shared-memory transpose tile so both writes are coalesced.
 __global__ void k_quantize_L(const double *__restrict__ src, int ld, int nr, int nc, int N, int A,
                              __nv_bfloat16 *__restrict__ Lb, __nv_bfloat16 *__restrict__ Ltb,
@@ -65,7 +65,7 @@ __global__ void k_quantize_L(const double *__restrict__ src, int ld, int nr, int
   __syncthreads();
   for (int cc = ty; cc < 32; cc += 8) {
     int c = c0 + cc, r = r0 + tx;
-    if (r < N && c < A) Ltb[(int64_t)c * N + r] = tile[tx][cc];
+    if (r < N && c < A) Ltb[kblk_bf16(c, r, A)] = tile[tx][cc];
   }
 }
 

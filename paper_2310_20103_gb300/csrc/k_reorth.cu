@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_split(VecCtx c, int j) {
       __nv_bfloat162 x2;
       x2.x = __float2bfloat16_rn(c.dsqf[e] * hx);
       x2.y = __float2bfloat16_rn(c.dsqf[e + 1] * hy);
-      *reinterpret_cast<__nv_bfloat162 *>(c.xh + voff + e) = x2;
+      *reinterpret_cast<__nv_bfloat162 *>(c.xh + kblk_bf16(b, e, c.Bs)) = x2;
     }
   }
   if (c.dq2_part != nullptr) {
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_start_split(VecCtx c) {
       __nv_bfloat162 x2;
       x2.x = __float2bfloat16_rn(c.dsqf[e] * hx);
       x2.y = __float2bfloat16_rn(c.dsqf[e + 1] * hy);
-      *reinterpret_cast<__nv_bfloat162 *>(c.xh + voff + e) = x2;
+      *reinterpret_cast<__nv_bfloat162 *>(c.xh + kblk_bf16(b, e, c.Bs)) = x2;
     }
   }
   if (c.dq2_part != nullptr) {

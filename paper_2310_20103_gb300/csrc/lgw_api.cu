@@ -1809,9 +1809,11 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
         char err[256];
         launch_split_scaled(qb, rows, N, s.dsq, Shi, Slo, st);
         check_launch(h, "split_scaled(D Q)");
+        // Ltb is K-block-major; the adjoint's own Ltb_lo is row-major
         const __nv_bfloat16 *pa[3] = {s.Ltb, s.Ltb, sys->Ltb_lo};
+        const int pk[3] = {1, 1, 0};
         const __nv_bfloat16 *pb[3] = {Shi, Slo, Shi};
-        if (!tc_gemm_f64out(3, pa, pb, A, rows, N, 16384, P, A, 0, h->d_status, st, err,
+        if (!tc_gemm_f64out(3, pa, pk, pb, A, rows, N, 16384, P, A, 0, h->d_status, st, err,
                             sizeof err)) {
           set_err(h, LGW_ERR_CUDA, "%s", err);
           throw Fail{LGW_ERR_CUDA};
@@ -1826,7 +1828,7 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
         check_launch(h, "split_t(Q)");
         const __nv_bfloat16 *qa[3] = {Rhi, Rhi, Rlo};
         const __nv_bfloat16 *qb[3] = {Shi, Slo, Shi};
-        if (!tc_gemm_f64out(3, qa, qb, A, N, rows, 16384, SC, A, 1, h->d_status, st, err,
+        if (!tc_gemm_f64out(3, qa, nullptr, qb, A, N, rows, 16384, SC, A, 1, h->d_status, st, err,
                             sizeof err)) {
           set_err(h, LGW_ERR_CUDA, "%s", err);
           throw Fail{LGW_ERR_CUDA};

@@ -50,11 +50,11 @@ struct SysDev {
   float *cdf;       // [N]  c_K Delta^1/2 rounded to float (FP32 epilogue)
   double *L64;      // [N][A] row-major, zero padded
   __nv_bfloat16 *Lb;    // [N][A]   K-major operand of the L Y contraction
-  __nv_bfloat16 *Ltb;   // [A][N]   K-major operand of the L^T X contraction
+  __nv_bfloat16 *Ltb;   // [A][N]   operand of the L^T X contraction, K-block-major (kblk_bf16)
   __nv_bfloat16 *Lb_lo; // [N][A]   bf16(L - bf16(L)): second half of a split-BF16 L
   // E4M3 copies with power-of-two column scales, made on the first FP8 call
   uint8_t *L8;      // [N][A]   e4m3(L / s_mu)
-  uint8_t *L8t;     // [A][N]   its transpose
+  uint8_t *L8t;     // [A][N]   its transpose, K-block-major (kblk_e4m3)
   float *sL;        // [A]      s_mu
 };
 
@@ -72,7 +72,7 @@ struct VecCtx {
   const double *Delta2, *dsq, *cd;
   double *w;              // [Bs][N]
   double *basis;          // slot s: basis + s * Bs * N
-  __nv_bfloat16 *xh;      // [Bs][N]   bf16(Delta^1/2 q_j)
+  __nv_bfloat16 *xh;      // [Bs][N]   bf16(Delta^1/2 q_j), K-block-major (kblk_bf16)
   float *bhi, *blo;       // split basis [k+1][Bs][N]: q = hi + lo (48 bits); blo may be
                           // null (float-only basis)
   const float *dsqf;      // [N]
@@ -97,6 +97,21 @@ struct VecCtx {
   int *n_second;          // counter of second passes
   unsigned *status;
 };
+
+// K-block-major layout of the GEMM1 operands (L^T and the per-step X):
+// element (r, e) of a logical [rows][N] matrix (e along the contraction)
+// sits at ((e / KB) * rows + r) * KB + e % KB, KB being one 128-byte row
+// of the swizzled tile (64 BF16 or 128 E4M3 elements).  A TMA box of KB x
+// box_rows is then one contiguous run of memory, so the contraction's
+// concurrent tiles touch a handful of pages instead of one page per row
+// (rows of a row-major [rows][1.6M] BF16 matrix are 3.2 MB apart).
+// N must be a multiple of 128.
+__host__ __device__ inline size_t kblk_bf16(int r, int e, int rows) {
+  return ((size_t)(e >> 6) * rows + r) * 64 + (e & 63);
+}
+__host__ __device__ inline size_t kblk_e4m3(int r, int e, int rows) {
+  return ((size_t)(e >> 7) * rows + r) * 128 + (e & 127);
+}
 
 __host__ __device__ inline double *slot_ptr(const VecCtx &c, int j) {
   int s = c.ring ? (j % 3) : j;
@@ -322,9 +337,10 @@ struct AdjCtx {
   unsigned *status;
 };
 int adj_max_k();
-bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const __nv_bfloat16 *const *B, int M,
-                    int Ncols, int K, int kchunk, double *out, int ldo, int add, unsigned *status,
-                    cudaStream_t st, char *err, size_t errn);
+bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const int *a_kblk,
+                    const __nv_bfloat16 *const *B, int M, int Ncols, int K, int kchunk,
+                    double *out, int ldo, int add, unsigned *status, cudaStream_t st, char *err,
+                    size_t errn);
 void launch_split_t(BasisRef src, int R, int C, int lds, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
                     cudaStream_t st);
 void launch_split_scaled(BasisRef src, int R, int C, const double *scale, __nv_bfloat16 *hi,
