@@ -626,7 +626,9 @@ def large_leg(L, dev, n_targets=2, k=300):
         out[prec] = {"value": wl.n_t / dt, "seconds": dt,
                      "gemm_tflops": rep["gemm_flops"] / (gms * 1e-3) / 1e12 if gms else None,
                      "ms_gemm1": rep["ms_gemm1"], "ms_gemm2": rep["ms_gemm2"],
-                     "ms_total": rep["ms_total"], "k_min": rep["k_min"]}
+                     "ms_total": rep["ms_total"], "k_min": rep["k_min"],
+                     "breakdown_ms": {kk: round(v, 1) for kk, v in rep.items()
+                                      if kk.startswith("ms_")}}
     out["qp_diff_mev_fp8_vs_bf16"] = float(np.abs(res["fp8"][1] - res["bf16"][1]).max() * 1e3)
     out["sigma_max_diff_mev_fp8_vs_bf16"] = float(np.abs(res["fp8"][0] - res["bf16"][0]).max()
                                                   * 1e3)

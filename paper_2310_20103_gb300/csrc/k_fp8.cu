@@ -94,9 +94,19 @@ __global__ void __launch_bounds__(256) k_quant_x8(const __nv_bfloat16 *__restric
   __shared__ float red[8];
   __shared__ float sc;
   const int b = blockIdx.x;
+  // eight consecutive elements per thread: one 16-byte load of xh, one
+  // 8-byte store of x8 (N is a multiple of 128, so a group never straddles
+  // a K block)
   float m = 0.0f;
-  for (int i = threadIdx.x; i < N; i += 256)
-    m = fmaxf(m, fabsf(__bfloat162float(xh[kblk_bf16(b, i, Bs)])));
+  for (int g = threadIdx.x; g < N / 8; g += 256) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(xh + kblk_bf16(b, 8 * g, Bs));
+    const __nv_bfloat162 *p2 = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float2 f = __bfloat1622float2(p2[t]);
+      m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
+    }
+  }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, s));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -109,8 +119,18 @@ __global__ void __launch_bounds__(256) k_quant_x8(const __nv_bfloat16 *__restric
   }
   __syncthreads();
   const float inv = 1.0f / sc;   // a power of two: exact
-  for (int i = threadIdx.x; i < N; i += 256)
-    x8[kblk_e4m3(b, i, Bs)] = to_e4m3(__bfloat162float(xh[kblk_bf16(b, i, Bs)]) * inv);
+  for (int g = threadIdx.x; g < N / 8; g += 256) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(xh + kblk_bf16(b, 8 * g, Bs));
+    const __nv_bfloat162 *p2 = reinterpret_cast<const __nv_bfloat162 *>(&v);
+    uint32_t wq[2] = {0u, 0u};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float2 f = __bfloat1622float2(p2[t]);
+      const uint32_t lo = to_e4m3(f.x * inv), hi = to_e4m3(f.y * inv);
+      wq[t >> 1] |= (lo | (hi << 8)) << (16 * (t & 1));
+    }
+    *reinterpret_cast<uint2 *>(x8 + kblk_e4m3(b, 8 * g, Bs)) = make_uint2(wq[0], wq[1]);
+  }
 }
 
 // From the split-K partials of gemm1: y_mu = s_b s_mu sum_p Ypart, then

@@ -230,12 +230,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   double *red = reinterpret_cast<double *>(smem + C::STAGES * C::STAGE + C::BAR_BYTES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // N tiles vary fastest so the CTAs sharing an L tile run together (second
-  // read from L2); each CTA starts its K loop at a different block so that
-  // concurrent CTAs do not stream the same column offset of the row-strided
-  // operand at the same time (spreads the requests over HBM channels).
+  // CTAs are dispatched in linear block order (x fastest); numbering the
+  // tiles of that order with N fastest makes the CTAs that share an L tile
+  // (all N tiles of one M tile) run together, so L streams from HBM once
+  // and its other reads hit L2.  With rotation each M tile starts its K
+  // loop at a different block, spreading concurrent requests over HBM
+  // channels; CTAs of one M tile keep the same start and stay in step.
   const int n_tiles = gridDim.y;
-  const int lin = blockIdx.x * n_tiles + blockIdx.y;
+  const int lin = blockIdx.x + blockIdx.y * gridDim.x;
   const int m_tile = lin / n_tiles, n_tile = lin % n_tiles, split = blockIdx.z;
   const int kb0 = split * kb_per_split;
   const int kb1 = min(num_kb, kb0 + kb_per_split);
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int i = 0; i < 32; ++i) {
           const int col = ncol0 + c0 + i;
           if (col < Ncols && row < M) {
-            float *o = ea.ucd + (size_t)col * ea.N + row;
+            float *o = ea.ucd + kblk_f32(col, row, Ncols);
             *o = (ea.ldo ? *o : 0.0f) + __uint_as_float(r[i]);
           }
         }
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int col = ncol0 + c0 + i;
           if (col < Ncols && row < M) {
             const float cs = ea.colscale ? ea.colscale[col] : 1.0f;
-            ea.ucd[(size_t)col * ea.N + row] = cdf * (cs * __uint_as_float(r[i]));
+            ea.ucd[kblk_f32(col, row, Ncols)] = cdf * (cs * __uint_as_float(r[i]));
           }
         }
       } else {

@@ -78,7 +78,6 @@ __global__ void __launch_bounds__(VEC_THREADS) k_assemble_w(VecCtx c, int j,
   const size_t voff = (size_t)b * c.N;
   const double *q = slot_ptr(c, j) + voff;
   const double *qp = j > 0 ? slot_ptr(c, j - 1) + voff : nullptr;
-  const float *u = ucd + voff;
   double *w = c.w + voff;
   const double bj = c.betaj[b];
   const int e0 = elem_base(chunk);
@@ -88,7 +87,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_assemble_w(VecCtx c, int j,
     const int e = e0 + u4 * 64;
     if (e >= c.N) continue;
     const double2 q2 = *reinterpret_cast<const double2 *>(q + e);
-    const float2 v2 = *reinterpret_cast<const float2 *>(u + e);
+    const float2 v2 = *reinterpret_cast<const float2 *>(ucd + kblk_f32(b, e, c.Bs));
     double2 w2;
     w2.x = fma(c.Delta2[e], q2.x, (double)v2.x);
     w2.y = fma(c.Delta2[e + 1], q2.y, (double)v2.y);
@@ -104,20 +103,30 @@ __global__ void __launch_bounds__(VEC_THREADS) k_assemble_w(VecCtx c, int j,
   if (threadIdx.x == 0) c.alpha_part[(size_t)chunk * c.Bs + b] = ap;
 }
 
-// alpha_j from the epilogue partials, w -= alpha_j q_j, ||w||^2 partials,
-// and (with reorthogonalisation) the first-pass dot products.
+// alpha_j = q_j . w from the n_mt epilogue partials alpha_part[t][b], one
+// warp per vector in fixed order: the recorded coefficient and amax, read
+// back by every block of the axpy pass (which would otherwise each repeat
+// the n_mt strided loads: 12500 of them per block at N_vc 1.6M).
+__global__ void k_alpha_reduce(VecCtx c, int j) {
+  const int b = blockIdx.x, lane = threadIdx.x;
+  if (!vec_live(c, b, j)) return;
+  double s = 0.0;
+  for (int t = lane; t < c.n_mt; t += 32) s += c.alpha_part[(size_t)t * c.Bs + b];
+  s = warp_sum(s);
+  if (lane == 0) {
+    c.alpha[(size_t)(c.vec0 + b) * c.k + j] = s;
+    c.amax[b] = fmax(c.amax[b], fabs(s));
+  }
+}
+
+// w -= alpha_j q_j, ||w||^2 partials, and (with reorthogonalisation) the
+// first-pass dot products.
 __global__ void __launch_bounds__(VEC_THREADS) k_alpha_axpy(VecCtx c, int j) {
   __shared__ double red[VEC_THREADS / 32];
   __shared__ double sred[VEC_THREADS / 32][32];
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (!vec_live(c, b, j)) return;
-  double s = 0.0;
-  for (int t = threadIdx.x; t < c.n_mt; t += VEC_THREADS) s += c.alpha_part[(size_t)t * c.Bs + b];
-  const double alpha = block_sum(s, red);
-  if (chunk == 0 && threadIdx.x == 0) {
-    c.alpha[(size_t)(c.vec0 + b) * c.k + j] = alpha;
-    c.amax[b] = fmax(c.amax[b], fabs(alpha));
-  }
+  const double alpha = c.alpha[(size_t)(c.vec0 + b) * c.k + j];
   const size_t voff = (size_t)b * c.N;
   const double *q = slot_ptr(c, j) + voff;
   double *w = c.w + voff;
@@ -240,23 +249,51 @@ __global__ void k_second_pass_decide(VecCtx c, int j) {
   c.flag2[b] = f;
 }
 
-// beta = ||w|| (fixed-order sum of the chosen partials), breakdown test,
-// q_next = w / beta into the next basis slot and xh = bf16(Delta^1/2 q_next).
-// is_start: w holds b_tm; records beta0 and writes q_0 into slot 0.
+// beta_{j+1} = ||w|| from the chosen per-chunk partials (one warp per
+// vector, fixed order), the breakdown test, and 1/beta (0 when the vector
+// stops or is not live) for k_normalize.
+__global__ void k_beta_vec(VecCtx c, int j) {
+  const int b = blockIdx.x, lane = threadIdx.x;
+  const int v = c.vec0 + b;
+  double inv = 0.0;
+  if (b < c.nvec && c.k_eff[v] > j) {
+    const double *np = c.norm_a;
+    if (c.reorth != LGW_REORTH_NONE) np = c.flag2[b] ? c.norm_c : c.norm_b;
+    double s = 0.0;
+    for (int ch = lane; ch < c.nchunks; ch += 32) s += np[(size_t)b * c.nchunks + ch];
+    s = warp_sum(s);
+    const double beta = sqrt(s);
+    const bool stop = !(beta > c.tol * c.amax[b]);
+    if (lane == 0) {
+      c.beta[(size_t)v * c.k + j] = beta;
+      c.betaj[b] = beta;
+      if (stop) c.k_eff[v] = j + 1;
+    }
+    inv = (stop || !(beta > 0.0)) ? 0.0 : 1.0 / beta;
+  } else if (lane == 0) {
+    c.betaj[b] = 0.0;
+  }
+  if (lane == 0) c.sinv[b] = inv;
+}
+
+// q_next = w / beta into the next basis slot and xh = bf16(Delta^1/2 q_next)
+// (beta, the breakdown test and 1/beta from k_beta_vec).  is_start: w
+// holds b_tm; ||b|| from the partials here, beta0, and q_0 into slot 0.
 __global__ void __launch_bounds__(VEC_THREADS) k_normalize(VecCtx c, int j, int is_start) {
   const int chunk = blockIdx.x, b = blockIdx.y;
   const int v = c.vec0 + b;
   const bool real = b < c.nvec;
-  bool live = real && (is_start || c.k_eff[v] > j);
+  bool live = real && is_start;
   __shared__ double sbeta, sinv;
-  double beta = 0.0;
-  if (live) {
-    // ||w||^2 from the per-chunk partials: one warp, fixed order, broadcast
+  double inv = 0.0;
+  if (!is_start) {
+    inv = c.sinv[b];
+    live = inv > 0.0;
+  } else if (live) {
+    // ||b||^2 from the per-chunk partials: one warp, fixed order, broadcast
     if (threadIdx.x < 32) {
-      const double *np = c.norm_a;
-      if (!is_start && c.reorth != LGW_REORTH_NONE) np = c.flag2[b] ? c.norm_c : c.norm_b;
       double s = 0.0;
-      for (int ch = threadIdx.x; ch < c.nchunks; ch += 32) s += np[(size_t)b * c.nchunks + ch];
+      for (int ch = threadIdx.x; ch < c.nchunks; ch += 32) s += c.norm_a[(size_t)b * c.nchunks + ch];
       s = warp_sum(s);
       if (threadIdx.x == 0) {
         sbeta = sqrt(s);
@@ -264,24 +301,15 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize(VecCtx c, int j, int 
       }
     }
     __syncthreads();
-    beta = sbeta;
-    if (is_start) {
-      if (chunk == 0 && threadIdx.x == 0) {
-        c.beta0[v] = beta;
-        c.k_eff[v] = beta > 0.0 ? c.k : 0;
-        c.amax[b] = 0.0;
-        c.betaj[b] = 0.0;
-      }
-      live = beta > 0.0;
-    } else {
-      const bool stop = !(beta > c.tol * c.amax[b]);
-      if (chunk == 0 && threadIdx.x == 0) {
-        c.beta[(size_t)v * c.k + j] = beta;
-        c.betaj[b] = beta;
-        if (stop) c.k_eff[v] = j + 1;
-      }
-      if (stop) live = false;
+    const double beta = sbeta;
+    if (chunk == 0 && threadIdx.x == 0) {
+      c.beta0[v] = beta;
+      c.k_eff[v] = beta > 0.0 ? c.k : 0;
+      c.amax[b] = 0.0;
+      c.betaj[b] = 0.0;
     }
+    live = beta > 0.0;
+    inv = live ? sinv : 0.0;
   } else if (chunk == 0 && threadIdx.x == 0) {
     c.betaj[b] = 0.0;
   }
@@ -290,7 +318,6 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize(VecCtx c, int j, int 
   const size_t voff = (size_t)b * c.N;
   double *qn = slot_ptr(c, next) + voff;
   const double *w = c.w + voff;
-  const double inv = live ? sinv : 0.0;
   const int e0 = elem_base(chunk);
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -304,9 +331,11 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize(VecCtx c, int j, int 
     }
     *reinterpret_cast<double2 *>(qn + e) = q2;
     if (c.xh != nullptr) {
+      // the BF16 operand from the FP32 image of q (FP64 multiplies and
+      // FP64 -> BF16 conversions would load GB300's narrow FP64 pipe)
       __nv_bfloat162 x2;
-      x2.x = __double2bfloat16(c.dsq[e] * q2.x);
-      x2.y = __double2bfloat16(c.dsq[e + 1] * q2.y);
+      x2.x = __float2bfloat16_rn(c.dsqf[e] * __double2float_rn(q2.x));
+      x2.y = __float2bfloat16_rn(c.dsqf[e + 1] * __double2float_rn(q2.y));
       *reinterpret_cast<__nv_bfloat162 *>(c.xh + kblk_bf16(b, e, c.Bs)) = x2;
     }
   }
@@ -352,7 +381,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_start_from_vf(VecCtx c, const f
     if (e >= c.N) continue;
     double x0 = 0.0, x1 = 0.0;
     if (b < c.nvec) {
-      const float2 v2 = *reinterpret_cast<const float2 *>(vf + voff + e);
+      const float2 v2 = *reinterpret_cast<const float2 *>(vf + kblk_f32(b, e, c.Bs));
       x0 = c.dsq[e] * (double)v2.x;
       x1 = c.dsq[e + 1] * (double)v2.y;
     }
@@ -409,8 +438,14 @@ void launch_normalize(const VecCtx &c, int j, int is_start, const double *, cuda
 void launch_assemble_w(const VecCtx &c, int j, const float *ucd, cudaStream_t st) {
   k_assemble_w<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, j, ucd);
 }
+void launch_alpha_reduce(const VecCtx &c, int j, cudaStream_t st) {
+  k_alpha_reduce<<<c.Bs, 32, 0, st>>>(c, j);
+}
 void launch_alpha_axpy(const VecCtx &c, int j, cudaStream_t st) {
   k_alpha_axpy<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, j);
+}
+void launch_beta_vec(const VecCtx &c, int j, cudaStream_t st) {
+  k_beta_vec<<<c.Bs, 32, 0, st>>>(c, j);
 }
 void launch_reduce_dots(const VecCtx &c, int j, int pass, cudaStream_t st) {
   k_reduce_dots<<<c.Bs, 256, 0, st>>>(c, j, pass);

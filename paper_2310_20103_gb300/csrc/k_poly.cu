@@ -20,11 +20,12 @@ __device__ __forceinline__ int poly_elem_base(int chunk) {
   return chunk * VEC_CHUNK + wid * 256 + 2 * lane;
 }
 
-// C b at element pair e (FP64 product, or FP32 coupling + Delta^2 b)
+// C b at element pair e of vector b (FP64 product T [Bs][N], or the FP32
+// coupling ucd (kblk_f32 over Bs = gridDim.y vectors) + Delta^2 b)
 __device__ __forceinline__ double2 cb_pair(const double *T, const float *ucd, const double *Delta2,
-                                           const double2 b1, int e) {
-  if (T) return *reinterpret_cast<const double2 *>(T + e);
-  const float2 u = *reinterpret_cast<const float2 *>(ucd + e);
+                                           const double2 b1, int b, int e) {
+  if (T) return *reinterpret_cast<const double2 *>(T + e);   // T offset to vector b
+  const float2 u = *reinterpret_cast<const float2 *>(ucd + kblk_f32(b, e, gridDim.y));
   return make_double2(fma(Delta2[e], b1.x, (double)u.x), fma(Delta2[e + 1], b1.y, (double)u.y));
 }
 
@@ -43,8 +44,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cheb_step(PolyStep p) {
     double2 r = make_double2(p.ck * q.x, p.ck * q.y);
     if (p.b1) {
       const double2 b1 = *reinterpret_cast<const double2 *>(p.b1 + o);
-      const double2 t = cb_pair(p.T ? p.T + voff : nullptr, p.ucd ? p.ucd + voff : nullptr,
-                                p.Delta2, b1, e);
+      const double2 t = cb_pair(p.T ? p.T + voff : nullptr, p.ucd, p.Delta2, b1, b, e);
       r.x = fma(2.0 * p.as, t.x, fma(2.0 * p.bs, b1.x, r.x));
       r.y = fma(2.0 * p.as, t.y, fma(2.0 * p.bs, b1.y, r.y));
     }
@@ -82,8 +82,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cheb_final(PolyStep p, const do
     const size_t o = voff + e;
     const double2 q = *reinterpret_cast<const double2 *>(p.q + o);
     const double2 b1 = *reinterpret_cast<const double2 *>(p.b1 + o);
-    const double2 t = cb_pair(p.T ? p.T + voff : nullptr, p.ucd ? p.ucd + voff : nullptr,
-                              p.Delta2, b1, e);
+    const double2 t = cb_pair(p.T ? p.T + voff : nullptr, p.ucd, p.Delta2, b1, b, e);
     double2 r;
     r.x = fma(p.as, t.x, fma(p.bs, b1.x, p.ck * q.x));
     r.y = fma(p.as, t.y, fma(p.bs, b1.y, p.ck * q.y));

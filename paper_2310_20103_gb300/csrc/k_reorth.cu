@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_dots_split(VecCtx c, int j) 
   double *w = c.w + (size_t)b * c.N;
   const double *qj = slot_ptr(c, j) + (size_t)b * c.N;
   const double *qp = (j >= 1) ? slot_ptr(c, j - 1) + (size_t)b * c.N : nullptr;
-  const float *ucd = c.ucd ? c.ucd + (size_t)b * c.N : nullptr;
+  const float *ucd = c.ucd;
   const double bj = c.betaj[b];
   const int cbase = chunk * VEC_CHUNK;
   const int e0 = elem_base_s(chunk);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_dots_split(VecCtx c, int j) 
         const double2 q2 = *reinterpret_cast<const double2 *>(qj + e);
         if (ucd != nullptr) {
           // w = Delta^2 q_j + c_K Delta^1/2 (L y) - beta_j q_{j-1}   (Eq. 4, 13)
-          const float2 u2 = *reinterpret_cast<const float2 *>(ucd + e);
+          const float2 u2 = *reinterpret_cast<const float2 *>(ucd + kblk_f32(b, e, c.Bs));
           w2.x = fma(c.Delta2[e], q2.x, (double)u2.x);
           w2.y = fma(c.Delta2[e + 1], q2.y, (double)u2.y);
           if (qp != nullptr) {

@@ -811,6 +811,8 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
           check_launch(h, "update_split2");
           continue;
         }
+        launch_alpha_reduce(c, j, st);
+        check_launch(h, "alpha_reduce");
         launch_alpha_axpy(c, j, st);
         check_launch(h, "alpha_axpy");
         if (reorth) {
@@ -830,6 +832,8 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
           check_launch(h, "update2");
         }
         tm.mark(C_NORM);
+        launch_beta_vec(c, j, st);
+        check_launch(h, "beta_vec");
         launch_normalize(c, j, 0, nullptr, st);
         check_launch(h, "normalize");
       }

@@ -77,7 +77,7 @@ struct VecCtx {
                           // null (float-only basis)
   const float *dsqf;      // [N]
   const float *d2f;       // [N] Delta^2 (float)
-  const float *ucd;       // [Bs][N] c_K Delta^1/2 (L y) from the FP32 epilogue, or null
+  const float *ucd;       // [Bs][N] c_K Delta^1/2 (L y) from the FP32 epilogue (kblk_f32), or null
                           // (then w holds the full FP64 epilogue result)
   float *dq2_part;        // [Bs][nchunks] partials of sum Delta^2 q_j^2 (FP32)
   const float *yy_part;   // [Bs][n_yb]    partials of y . bf16(y) for the current q_j
@@ -111,6 +111,13 @@ __host__ __device__ inline size_t kblk_bf16(int r, int e, int rows) {
 }
 __host__ __device__ inline size_t kblk_e4m3(int r, int e, int rows) {
   return ((size_t)(e >> 7) * rows + r) * 128 + (e & 127);
+}
+// The FP32 contraction output ucd [Bs][N] (c_K Delta^1/2 L y, and the
+// start-vector product V) in blocks of 128 pair elements: element (b, e) at
+// ((e / 128) * Bs + b) * 128 + e % 128, so one 128 x BN output tile of the
+// tensor-core epilogue is one contiguous run.
+__host__ __device__ inline size_t kblk_f32(int b, int e, int Bs) {
+  return ((size_t)(e >> 7) * Bs + b) * 128 + (e & 127);
 }
 
 __host__ __device__ inline double *slot_ptr(const VecCtx &c, int j) {
@@ -225,7 +232,9 @@ void launch_start_from_vf(const VecCtx &c, const float *vf, cudaStream_t st);
 void launch_norm_partials(const VecCtx &c, const double *x, double *out, cudaStream_t st);
 void launch_normalize(const VecCtx &c, int j, int is_start, const double *norm, cudaStream_t st);
 void launch_assemble_w(const VecCtx &c, int j, const float *ucd, cudaStream_t st);
+void launch_alpha_reduce(const VecCtx &c, int j, cudaStream_t st);
 void launch_alpha_axpy(const VecCtx &c, int j, cudaStream_t st);
+void launch_beta_vec(const VecCtx &c, int j, cudaStream_t st);
 void launch_reduce_dots(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_update(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_dots(const VecCtx &c, int j, int pass, cudaStream_t st);
