@@ -638,6 +638,35 @@ def large_leg(L, dev, n_targets=2, k=300):
     return out
 
 
+def profile_case(prec="bf16"):
+    """The small case the kernel profiles are taken on: the mid-size system
+    (N_vc 131072, N_aux 2048), target HOMO-15 summed over its first 64
+    orbitals (64 start vectors), k 48, CGS1K, one lgw_sigma_c call with a
+    report.  The Krylov basis is about 3 GB, larger than L2."""
+    import torch
+    sys.path.insert(0, ROOT)
+    import gw_inputs as gi
+    from paper_2310_20103_gb300 import lgw as L
+
+    def tt(x):
+        return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+    wl = gi.mid(n_targets=1, k=48)
+    h = L.lgw_create(0)
+    s = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, tt(wl.eps), tt(wl.L))
+    prob = L.Problem(targets=tt(wl.targets), m_idx=tt(wl.m_idx[:64]), omega=tt(wl.omega),
+                     delta=wl.delta, M=tt(wl.M[:, :64]))
+    sig = torch.empty(1, wl.omega.size, 2, dtype=torch.float64, device="cuda:0")
+    e = torch.empty(1, dtype=torch.float64, device="cuda:0")
+    rep = L.lgw_sigma_c(h, s, prob, L.Options(k=48, precision=prec, reorth="cgs1k"), sig, e,
+                        report=True)
+    torch.cuda.synchronize()
+    print(json.dumps({kk: (round(v, 3) if isinstance(v, float) else v) for kk, v in rep.items()}),
+          flush=True)
+    L.lgw_release_system(s)
+    L.lgw_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -667,7 +696,14 @@ def main():
     ap.add_argument("--large-only", action="store_true",
                     help="run only the large cluster-sized leg (about 2 minutes, ~240 GB)")
     ap.add_argument("--large-targets", type=int, default=2)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one small call for kernel profiles (mid-size system, 64 start "
+                         "vectors, k 48, CGS1K; about 3 GB on the device) and its report")
+    ap.add_argument("--profile-precision", default="bf16", choices=["bf16", "fp8", "fp64"])
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_precision)
+        return
     if args.adjoint_only:
         import torch
         sys.path.insert(0, ROOT)

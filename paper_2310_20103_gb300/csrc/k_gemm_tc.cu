@@ -208,6 +208,10 @@ struct EpiArgs {
   int rot;
   // operand maps are 3-D K-block-major (kblk_*) instead of 2-D row-major
   int a3, b3;
+  // tile numbering in launch order: 0 = N tiles fastest (CTAs sharing an L
+  // tile run together), 1 = M tiles fastest (CTAs sharing the B tile run
+  // together)
+  int mfast;
 };
 
 enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2, E_LANCZOS_NA = 3, E_SPLITB = 4, E_VACC = 5,
@@ -230,15 +234,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   double *red = reinterpret_cast<double *>(smem + C::STAGES * C::STAGE + C::BAR_BYTES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // CTAs are dispatched in linear block order (x fastest); numbering the
+  // CTAs are dispatched in linear block order (x fastest).  Numbering the
   // tiles of that order with N fastest makes the CTAs that share an L tile
   // (all N tiles of one M tile) run together, so L streams from HBM once
-  // and its other reads hit L2.  With rotation each M tile starts its K
-  // loop at a different block, spreading concurrent requests over HBM
-  // channels; CTAs of one M tile keep the same start and stay in step.
+  // and its other reads hit L2; M fastest instead keeps the CTAs of one B
+  // tile together (chosen per shape by the autotuner).  With rotation each
+  // M tile starts its K loop at a different block, spreading concurrent
+  // requests over HBM channels; CTAs of one M tile keep the same start.
   const int n_tiles = gridDim.y;
   const int lin = blockIdx.x + blockIdx.y * gridDim.x;
-  const int m_tile = lin / n_tiles, n_tile = lin % n_tiles, split = blockIdx.z;
+  const int m_tile = ea.mfast ? (int)blockIdx.x : lin / n_tiles;
+  const int n_tile = ea.mfast ? (int)blockIdx.y : lin % n_tiles;
+  const int split = blockIdx.z;
   const int kb0 = split * kb_per_split;
   const int kb1 = min(num_kb, kb0 + kb_per_split);
   const int nk = max(0, kb1 - kb0);
@@ -454,6 +461,7 @@ struct TcPlan {
   const float *ty = nullptr;   // per-vector scale of y8 (gemm2 column scale)
   int BN1, BN2;   // N tile of gemm1 / gemm2 (and the coupling products)
   int rot1 = 1;   // gemm1 K-start rotation (tuned); gemm2 always rotates
+  int mfast2 = 0; // gemm2 tile numbering (EpiArgs::mfast), tuned
   const __nv_bfloat16 *xh;
   int N, A, Bs;
   int splits, kb_per_split;
@@ -725,6 +733,7 @@ bool launch_coupling_tc(const TcPlan *p, const SysDev &s, const double *M, int n
 void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaStream_t st) {
   tc::EpiArgs ea{};
   ea.rot = 1;
+  ea.mfast = p->mfast2;
   ea.N = p->N;
   ea.cdf = p->cdf;
   ea.ucd = ucd;
@@ -803,7 +812,7 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int BN1, splits, BN2, rot1;
+  int BN1, splits, BN2, rot1, mfast2;
 };
 std::map<TuneKey, TuneVal> g_tune;
 std::mutex g_tune_mu;
@@ -858,6 +867,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
       p->BN1 = it->second.BN1;
       p->BN2 = it->second.BN2;
       p->rot1 = it->second.rot1;
+      p->mfast2 = it->second.mfast2;
       plan_set_splits(p, it->second.splits);
       if (splits_out) *splits_out = p->splits;
       return plan_encode_b(p);
@@ -872,7 +882,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
     launch_reduce_y_bf16(p->ypart, p->splits, p->Bs, p->A, p->yh, nullptr, st);
   };
   // gemm1: N tile x split count x K-start rotation
-  const TuneVal def{p->BN1, p->splits, p->BN2, p->rot1};
+  const TuneVal def{p->BN1, p->splits, p->BN2, p->rot1, p->mfast2};
   float t_def = time_best(gemm1, st);
   TuneVal best = def;
   float t_best = t_def;
@@ -906,24 +916,32 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
   p->BN1 = best.BN1;
   p->rot1 = best.rot1;
   plan_set_splits(p, best.splits);
-  // gemm2 (store-only epilogue into the caller's scratch): N tile
+  // gemm2 (store-only epilogue into the caller's scratch): N tile x tile
+  // numbering
   if (ucd != nullptr) {
     auto gemm2 = [&]() { launch_gemm2_tc_split(p, ucd, status, st); };
     if (!plan_encode_b(p)) return false;
     const float t2_def = time_best(gemm2, st);
     float t2_best = t2_def;
-    for (int bn = 64; bn <= bn_max; bn *= 2) {
-      if (bn == def.BN2) continue;
-      p->BN2 = bn;
-      if (!plan_encode_b(p)) return false;
-      const float t = time_best(gemm2, st);
-      if (t < t2_best) {
-        t2_best = t;
-        best.BN2 = bn;
+    for (int bn = 64; bn <= bn_max; bn *= 2)
+      for (int mf = 0; mf <= 1; ++mf) {
+        if (bn == def.BN2 && mf == def.mfast2) continue;
+        p->BN2 = bn;
+        p->mfast2 = mf;
+        if (!plan_encode_b(p)) return false;
+        const float t = time_best(gemm2, st);
+        if (t < t2_best) {
+          t2_best = t;
+          best.BN2 = bn;
+          best.mfast2 = mf;
+        }
       }
+    if (t2_best > 0.97f * t2_def) {
+      best.BN2 = def.BN2;
+      best.mfast2 = def.mfast2;
     }
-    if (t2_best > 0.97f * t2_def) best.BN2 = def.BN2;
     p->BN2 = best.BN2;
+    p->mfast2 = best.mfast2;
   }
   if (!plan_encode_b(p)) return false;
   {
