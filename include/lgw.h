@@ -198,9 +198,11 @@ typedef struct {
   double ms_gemm1;       /* L^T (Delta^1/2 q) contraction + partial reduce   */
   double ms_gemm2;       /* L y contraction + fused recurrence epilogue      */
   double ms_dots;        /* alpha finish, axpy and first-pass Q^T w products */
-  double ms_update;      /* first-pass w -= Q h                              */
+  double ms_update;      /* first-pass w -= Q h (with the split basis also
+                            q_{j+1} for vectors that take no second pass)   */
   double ms_pass2;       /* second Gram-Schmidt pass (decision, Q^T w, update) */
-  double ms_normalize;   /* beta, breakdown test, q_{j+1}, bf16 operand      */
+  double ms_normalize;   /* beta, breakdown test, q_{j+1}, bf16 operand (0
+                            with the split basis: folded into the update)   */
   double ms_spectral;    /* tridiagonal eigenproblems and Jacobi rebuild     */
   double ms_cf;          /* continued fractions on the grid                  */
   double ms_qp;          /* quasiparticle solve                              */
