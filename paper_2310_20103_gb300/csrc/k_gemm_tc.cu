@@ -34,12 +34,16 @@ constexpr int BM = 128;
 constexpr int BK = 64;              // 64 bf16 = 128 bytes = one swizzle row
 constexpr int NTHREADS = 192;
 
-template <int BN>
+// HALF: half the pipeline stages (about 100 KB of shared memory), so that
+// two CTAs fit on an SM and one's epilogue overlaps the other's main loop
+// (tensor memory: 2 x BN <= 512 columns).  Used for the store-only
+// contraction, whose K loop is short.
+template <int BN, int HALF = 0>
 struct Cfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int STAGES = (BN == 256) ? 4 : (BN == 128 ? 6 : 8);
+  static constexpr int STAGES = ((BN == 256) ? 4 : (BN == 128 ? 6 : 8)) >> HALF;
   static constexpr int BAR_BYTES = 256;
   static constexpr int RED_BYTES = 4 * BN * 8;
   static constexpr int SMEM = 1024 + STAGES * STAGE + BAR_BYTES + RED_BYTES;
@@ -219,11 +223,11 @@ enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2, E_LANCZOS_NA = 3, E_SPLITB = 4,
 
 // EB: operand element bytes, 2 = BF16 (kind::f16, K block 64), 1 = E4M3
 // (kind::f8f6f4, K block 128); a K block is one 128-byte swizzle row either way.
-template <int BN, int EPI, int EB>
+template <int BN, int EPI, int EB, int HALF = 0>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               int M, int Ncols, int num_kb, int kb_per_split, EpiArgs ea) {
-  using C = Cfg<BN>;
+  using C = Cfg<BN, HALF>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -462,6 +466,7 @@ struct TcPlan {
   int BN1, BN2;   // N tile of gemm1 / gemm2 (and the coupling products)
   int rot1 = 1;   // gemm1 K-start rotation (tuned); gemm2 always rotates
   int mfast2 = 0; // gemm2 tile numbering (EpiArgs::mfast), tuned
+  int half2 = 0;  // gemm2 with the half-depth pipeline (two CTAs per SM), tuned
   const __nv_bfloat16 *xh;
   int N, A, Bs;
   int splits, kb_per_split;
@@ -603,25 +608,37 @@ TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *
 
 void tc_plan_destroy(TcPlan *p) { delete p; }
 
-template <int BN, int EPI, int EB = 2>
+template <int BN, int EPI, int EB = 2, int HALF = 0>
 static void launch_tc(const CUtensorMap &A, const CUtensorMap &B, int M, int Ncols, int num_kb,
                       int kb_per_split, int splits, const tc::EpiArgs &ea, cudaStream_t st) {
-  using C = tc::Cfg<BN>;
+  using C = tc::Cfg<BN, HALF>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(tc::k_gemm_tc<BN, EPI, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         C::SMEM);
+    cudaFuncSetAttribute(tc::k_gemm_tc<BN, EPI, EB, HALF>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     attr_done = true;
   }
   dim3 grid((M + tc::BM - 1) / tc::BM, (Ncols + BN - 1) / BN, splits);
-  tc::k_gemm_tc<BN, EPI, EB><<<grid, tc::NTHREADS, C::SMEM, st>>>(A, B, M, Ncols, num_kb,
-                                                                  kb_per_split, ea);
+  tc::k_gemm_tc<BN, EPI, EB, HALF><<<grid, tc::NTHREADS, C::SMEM, st>>>(A, B, M, Ncols, num_kb,
+                                                                        kb_per_split, ea);
 }
 
+// half: the half-depth pipeline (two CTAs per SM), store-only epilogue only
 template <int EPI, int EB = 2>
 static void dispatch_bn(int BN, const CUtensorMap &A, const CUtensorMap &B, int M, int Ncols,
                         int num_kb, int kb_per_split, int splits, const tc::EpiArgs &ea,
-                        cudaStream_t st) {
+                        cudaStream_t st, int half = 0) {
+  if constexpr (EPI == tc::E_SPLITB) {
+    if (half) {
+      if (BN == 256)
+        launch_tc<256, EPI, EB, 1>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
+      else if (BN == 128)
+        launch_tc<128, EPI, EB, 1>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
+      else
+        launch_tc<64, EPI, EB, 1>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
+      return;
+    }
+  }
   if (BN == 256)
     launch_tc<256, EPI, EB>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
   else if (BN == 128)
@@ -741,12 +758,14 @@ void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaSt
   if (p->fp8) {
     ea.colscale = p->ty;
     const int nkb = p->A / 128;
-    dispatch_bn<tc::E_SPLITB, 1>(p->BN2, p->f2A, p->f2B, p->N, p->Bs, nkb, nkb, 1, ea, st);
+    dispatch_bn<tc::E_SPLITB, 1>(p->BN2, p->f2A, p->f2B, p->N, p->Bs, nkb, nkb, 1, ea, st,
+                                 p->half2);
     return;
   }
   if (!p->has_bf16) return;
   const int num_kb = p->A / tc::BK;
-  dispatch_bn<tc::E_SPLITB>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st);
+  dispatch_bn<tc::E_SPLITB>(p->BN2, p->g2A, p->g2B, p->N, p->Bs, num_kb, num_kb, 1, ea, st,
+                            p->half2);
 }
 
 // out (=, or += if add) sum_{p < np} A_p B_p^T with A_p [M][K], B_p [Ncols][K]
@@ -812,7 +831,7 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int BN1, splits, BN2, rot1, mfast2;
+  int BN1, splits, BN2, rot1, mfast2, half2;
 };
 std::map<TuneKey, TuneVal> g_tune;
 std::mutex g_tune_mu;
@@ -868,6 +887,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
       p->BN2 = it->second.BN2;
       p->rot1 = it->second.rot1;
       p->mfast2 = it->second.mfast2;
+      p->half2 = it->second.half2;
       plan_set_splits(p, it->second.splits);
       if (splits_out) *splits_out = p->splits;
       return plan_encode_b(p);
@@ -882,7 +902,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
     launch_reduce_y_bf16(p->ypart, p->splits, p->Bs, p->A, p->yh, nullptr, st);
   };
   // gemm1: N tile x split count x K-start rotation
-  const TuneVal def{p->BN1, p->splits, p->BN2, p->rot1, p->mfast2};
+  const TuneVal def{p->BN1, p->splits, p->BN2, p->rot1, p->mfast2, p->half2};
   float t_def = time_best(gemm1, st);
   TuneVal best = def;
   float t_best = t_def;
@@ -917,31 +937,36 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
   p->rot1 = best.rot1;
   plan_set_splits(p, best.splits);
   // gemm2 (store-only epilogue into the caller's scratch): N tile x tile
-  // numbering
+  // numbering x pipeline depth
   if (ucd != nullptr) {
     auto gemm2 = [&]() { launch_gemm2_tc_split(p, ucd, status, st); };
     if (!plan_encode_b(p)) return false;
     const float t2_def = time_best(gemm2, st);
     float t2_best = t2_def;
     for (int bn = 64; bn <= bn_max; bn *= 2)
-      for (int mf = 0; mf <= 1; ++mf) {
-        if (bn == def.BN2 && mf == def.mfast2) continue;
-        p->BN2 = bn;
-        p->mfast2 = mf;
-        if (!plan_encode_b(p)) return false;
-        const float t = time_best(gemm2, st);
-        if (t < t2_best) {
-          t2_best = t;
-          best.BN2 = bn;
-          best.mfast2 = mf;
+      for (int mf = 0; mf <= 1; ++mf)
+        for (int hf = 0; hf <= 1; ++hf) {
+          if (bn == def.BN2 && mf == def.mfast2 && hf == def.half2) continue;
+          p->BN2 = bn;
+          p->mfast2 = mf;
+          p->half2 = hf;
+          if (!plan_encode_b(p)) return false;
+          const float t = time_best(gemm2, st);
+          if (t < t2_best) {
+            t2_best = t;
+            best.BN2 = bn;
+            best.mfast2 = mf;
+            best.half2 = hf;
+          }
         }
-      }
     if (t2_best > 0.97f * t2_def) {
       best.BN2 = def.BN2;
       best.mfast2 = def.mfast2;
+      best.half2 = def.half2;
     }
     p->BN2 = best.BN2;
     p->mfast2 = best.mfast2;
+    p->half2 = best.half2;
   }
   if (!plan_encode_b(p)) return false;
   {
