@@ -267,7 +267,9 @@ lgw_status lgw_lanczos_coeffs(lgw_handle *h, const lgw_system *s, const lgw_prob
 /* Self-energy and QP energies from stored tridiagonals (Eq. 12, 14, 10):
  * spectral map of each T_k, continued fractions on the grid, QP solve.
  * sigma [n_t][n_freq][2]; e_qp [n_t]; z_qp [n_t] (renormalisation factor
- * 1/(1 - dRe Sigma/domega) at E_qp) may be NULL. */
+ * 1/(1 - dRe Sigma/domega) at E_qp) may be NULL.  Orbital indices are
+ * checked on the host; a depth k_eff outside [0, k] makes the spectral map
+ * skip that vector and the call return LGW_ERR_SHAPE. */
 lgw_status lgw_sigma_from_coeffs(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
                                  const lgw_options *o, const double *alpha,
                                  const double *beta, const double *beta0,
@@ -375,11 +377,18 @@ lgw_status lgw_sigma_c_batched(lgw_handle *h, int32_t n_sys, const lgw_system *c
  * Requirements and limits
  *   - every array (alpha, beta, beta0, k_eff, sigma, e_qp, z_qp if given, and
  *     p->targets, p->m_idx, p->omega, p->static_shift if given) must be
- *     device memory of the handle's device; host pointers give LGW_ERR_ARG.
- *     p->M and p->V are not used.  sigma and e_qp are required.
+ *     device memory of the handle's device; host pointers and memory of
+ *     another device give LGW_ERR_ARG.  p->M and p->V are not used.  sigma
+ *     and e_qp are required.
  *   - B = n_t * n_m vectors with k steps need B * (5k + 2) + 1 doubles; larger
  *     requests are rejected with LGW_ERR_UNSUPPORTED and nothing runs.
- *   - indices out of range give LGW_ERR_SHAPE (checked on the device).
+ *     k above 4095 gives LGW_ERR_UNSUPPORTED and an unknown qp_mode
+ *     LGW_ERR_ARG, both before any launch.
+ *   - an orbital index outside [0, n_v + n_c) in p->targets or p->m_idx, or
+ *     a depth k_eff outside [0, k], gives LGW_ERR_SHAPE.  The arrays live on
+ *     the device, so a first kernel checks them and the call reads its
+ *     verdict back (one stream synchronisation) before it queues any kernel
+ *     that uses an index; on failure nothing else runs.
  *   - the first call on a device looks up the device address of the static
  *     array (cudaGetSymbolAddress); make that first call before any stream
  *     capture on that device.

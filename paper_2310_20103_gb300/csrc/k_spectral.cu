@@ -130,7 +130,13 @@ __global__ void k_spectral_warp(const double *__restrict__ alpha, const double *
   double *wt = th + k;                     // u_1^2, then the Omega-space weights
   double *ja = wt + k;                     // Jacobi diagonal
   double *jb_ = ja + k;                    // Jacobi off-diagonal
-  const int n = k_eff[v];
+  // A depth outside [0, k] (possible only for caller-supplied tridiagonals)
+  // is flagged and the vector skipped: its rows hold at most k entries.
+  int n = k_eff[v];
+  if (n < 0 || n > k) {
+    if (lane == 0) atomicOr(status, ST_BAD_INPUT);
+    n = 0;
+  }
   if (lane == 0) jb.n[v] = n;
   if (n <= 0) {
     if (lane == 0) jb.w0[v] = 0.0;

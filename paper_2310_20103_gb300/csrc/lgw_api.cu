@@ -243,6 +243,10 @@ void check_status(lgw_handle *h) {
     set_err(h, LGW_ERR_TIMEOUT, "a bounded device wait ran out");
     throw Fail{LGW_ERR_TIMEOUT};
   }
+  if (st & ST_BAD_INPUT) {
+    set_err(h, LGW_ERR_SHAPE, "a tridiagonal depth k_eff lies outside [0, k]");
+    throw Fail{LGW_ERR_SHAPE};
+  }
   if (st & ST_NOT_SPD) {
     set_err(h, LGW_ERR_NOT_SPD, "non-positive pair energy or Gauss node (C not positive definite)");
     throw Fail{LGW_ERR_NOT_SPD};
@@ -1968,13 +1972,30 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 double *g_noalloc_addr[kMaxDevices] = {nullptr};
 
-// Sets the Gauss-node minimum word and checks every target / summed index.
+// Sets the Gauss-node minimum word and checks every target / summed index
+// and every depth k_eff against [0, k].  It only reads the index arrays;
+// the caller reads the status word before launching anything that
+// dereferences an index.
 __global__ void k_noalloc_prologue(unsigned long long *min_theta_bits, const int *targets, int n_t,
-                                   const int *m_idx, int n_m, int norb, unsigned *status) {
+                                   const int *m_idx, int n_m, int norb, const int *k_eff, int B,
+                                   int k, unsigned *status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) *min_theta_bits = 0x7FEFFFFFFFFFFFFFull;   // largest finite double
   if (i < n_t && (targets[i] < 0 || targets[i] >= norb)) atomicOr(status, ST_BAD_INPUT);
   if (i < n_m && (m_idx[i] < 0 || m_idx[i] >= norb)) atomicOr(status, ST_BAD_INPUT);
+  if (i < B && (k_eff[i] < 0 || k_eff[i] > k)) atomicOr(status, ST_BAD_INPUT);
+}
+
+// Device memory of device `dev` (managed memory counts as any device's).
+bool is_device_ptr_on(const void *p, int dev) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 size_t noalloc_doubles_needed(size_t B, size_t k) {
@@ -1998,14 +2019,21 @@ extern "C" lgw_status lgw_sigma_from_coeffs_noalloc(lgw_handle *h, const lgw_sys
   if (n_t < 1 || n_m < 1 || n_freq < 1 || !p->targets || !p->m_idx || !p->omega)
     return set_err(h, LGW_ERR_ARG, "noalloc: n_t, n_m, n_freq must be >= 1 with their arrays");
   if (k < 1 || k > s.n_vc) return set_err(h, LGW_ERR_ARG, "noalloc: k outside [1, n_vc]");
+  if (k > 4095)
+    return set_err(h, LGW_ERR_UNSUPPORTED, "noalloc: k = %d above the 4095-step limit", k);
+  if (o->qp_mode != 0 && o->qp_mode != 1)
+    return set_err(h, LGW_ERR_ARG, "noalloc: unknown qp_mode %d", o->qp_mode);
   if (!(p->delta > 0.0)) return set_err(h, LGW_ERR_ARG, "noalloc: delta must be > 0");
   const void *dev_ptrs[] = {alpha, beta, beta0, k_eff, sigma, e_qp, p->targets, p->m_idx,
                             p->omega};
   for (const void *q : dev_ptrs)
-    if (!is_device_ptr(q))
-      return set_err(h, LGW_ERR_ARG, "noalloc: every array must be device memory");
-  if ((z_qp && !is_device_ptr(z_qp)) || (p->static_shift && !is_device_ptr(p->static_shift)))
-    return set_err(h, LGW_ERR_ARG, "noalloc: every array must be device memory");
+    if (!is_device_ptr_on(q, h->device))
+      return set_err(h, LGW_ERR_ARG, "noalloc: every array must be device memory of device %d",
+                     h->device);
+  if ((z_qp && !is_device_ptr_on(z_qp, h->device)) ||
+      (p->static_shift && !is_device_ptr_on(p->static_shift, h->device)))
+    return set_err(h, LGW_ERR_ARG, "noalloc: every array must be device memory of device %d",
+                   h->device);
   const size_t B = (size_t)n_t * (size_t)n_m;
   if (noalloc_doubles_needed(B, (size_t)k) > kNoallocDoubles)
     return set_err(h, LGW_ERR_UNSUPPORTED,
@@ -2040,9 +2068,25 @@ extern "C" lgw_status lgw_sigma_from_coeffs_noalloc(lgw_handle *h, const lgw_sys
   cudaStream_t st = h->stream;
   if (cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st) != cudaSuccess)
     return set_err(h, LGW_ERR_CUDA, "noalloc: status reset failed");
-  const int nmax = n_t > n_m ? n_t : n_m;
-  k_noalloc_prologue<<<(nmax + 255) / 256, 256, 0, st>>>(mt, p->targets, n_t, p->m_idx, n_m,
-                                                         s.n_v + s.n_c, h->d_status);
+  // Index check first, and its verdict read back before any kernel that
+  // dereferences an index (eps[m], eps[t], the k_eff-deep rows) is queued.
+  const size_t nmax = std::max<size_t>(std::max(n_t, n_m), B);
+  k_noalloc_prologue<<<(unsigned)((nmax + 255) / 256), 256, 0, st>>>(
+      mt, p->targets, n_t, p->m_idx, n_m, s.n_v + s.n_c, k_eff, (int)B, k, h->d_status);
+  {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+      return set_err(h, LGW_ERR_CUDA, "noalloc: index check launch failed: %s",
+                     cudaGetErrorString(e));
+    unsigned stw = 0;
+    if (cudaMemcpyAsync(&stw, h->d_status, sizeof stw, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return set_err(h, LGW_ERR_CUDA, "noalloc: status read failed");
+    if (stw & ST_BAD_INPUT)
+      return set_err(h, LGW_ERR_SHAPE,
+                     "noalloc: orbital index outside [0, n_v + n_c) or k_eff outside [0, k]");
+  }
   launch_spectral_impl(alpha, beta, beta0, k_eff, (int)B, k, jb, work, mt, h->d_status, st);
   CfProblem cp{};
   cp.n_t = n_t;
@@ -2056,7 +2100,6 @@ extern "C" lgw_status lgw_sigma_from_coeffs_noalloc(lgw_handle *h, const lgw_sys
   cp.omega = p->omega;
   cp.delta = p->delta;
   cp.shift = p->static_shift;
-  if (o->qp_mode != 0 && o->qp_mode != 1) return set_err(h, LGW_ERR_ARG, "unknown qp_mode");
   cp.qp_mode = o->qp_mode;
   launch_cf_grid(cp, jb, sigma, nullptr, 1, st);
   const int qp_iter = o->qp_max_iter > 0 ? o->qp_max_iter : 50;
@@ -2069,7 +2112,6 @@ extern "C" lgw_status lgw_sigma_from_coeffs_noalloc(lgw_handle *h, const lgw_sys
   if (cudaMemcpyAsync(&stw, h->d_status, sizeof stw, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return set_err(h, LGW_ERR_CUDA, "noalloc: status read failed");
-  if (stw & ST_BAD_INPUT) return set_err(h, LGW_ERR_SHAPE, "noalloc: orbital index out of range");
   if (stw & ST_TIMEOUT) return set_err(h, LGW_ERR_TIMEOUT, "a bounded device wait ran out");
   if (stw & ST_NOT_SPD) return set_err(h, LGW_ERR_NOT_SPD, "non-positive Gauss node");
   if (stw & ST_NO_CONV)

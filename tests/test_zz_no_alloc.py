@@ -69,6 +69,44 @@ def test_noalloc_matches_allocating_entry_point():
         with pytest.raises(L.LgwError) as ei:
             L.lgw_sigma_from_coeffs_noalloc(h, s, prob, opts, al.cpu(), be, b0, ke, *out())
         assert ei.value.status == 1
+        # an out-of-range summed orbital or target, or a depth beyond k, is
+        # caught by the device-side index check, whose verdict is read back
+        # before any kernel that would dereference the index is queued
+        norb = wl.n_v + wl.n_c
+        bad_m = wl.m_idx.copy()
+        bad_m[3] = norb
+        bad_t = wl.targets.copy()
+        bad_t[0] = -1
+        bad_k = ke.clone()
+        bad_k[5] = 49
+        cases = [
+            (L.Problem(targets=_t(wl.targets), m_idx=_t(bad_m), omega=_t(wl.omega),
+                       delta=wl.delta, M=_t(wl.M)), ke),
+            (L.Problem(targets=_t(bad_t), m_idx=_t(wl.m_idx), omega=_t(wl.omega),
+                       delta=wl.delta, M=_t(wl.M)), ke),
+            (prob, bad_k),
+        ]
+        for bp, kk in cases:
+            with pytest.raises(L.LgwError) as ei:
+                L.lgw_sigma_from_coeffs_noalloc(h, s, bp, opts, al, be, b0, kk, *out())
+            assert ei.value.status == 2
+        # an unknown QP mode is refused before any launch (raw C struct: the
+        # binding only maps the known mode names)
+        import ctypes
+        fn = L.load_library().lgw_sigma_from_coeffs_noalloc
+        co, cp = opts.to_c(), prob.to_c()
+        co.qp_mode = 7
+        o3 = out()
+        st = fn(h.ptr, s.ptr, ctypes.byref(cp), ctypes.byref(co), al.data_ptr(), be.data_ptr(),
+                b0.data_ptr(), ke.data_ptr(), o3[0].data_ptr(), o3[1].data_ptr(),
+                o3[2].data_ptr())
+        assert st == 1
+        # the handle stays usable after the refusals
+        got = out()
+        L.lgw_sigma_from_coeffs_noalloc(h, s, prob, opts, al, be, b0, ke, *got)
+        torch.cuda.synchronize()
+        for g, r in zip([x.cpu().numpy() for x in got], ref):
+            assert np.abs(g - r).max() <= 1e-11 * max(1.0, np.abs(r).max())
         L.lgw_release_system(s)
     finally:
         L.lgw_destroy(h)
