@@ -150,13 +150,36 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+GS_SCHEDULE = {
+    "dcgs": "delayed classical Gram-Schmidt: one pass over the stored basis per step "
+            "(projection of w_j and the delayed update of q_j in the same sweep), second "
+            "pass where the norm drops below 1/sqrt(2)",
+    "cgs1k": "classical Gram-Schmidt, two passes over the basis per step (dots, update), "
+             "second projection where the norm drops below 1/sqrt(2)",
+    "cgs2": "classical Gram-Schmidt, always two projections (four passes over the basis)",
+    "none": "three-term recurrence only",
+}
+
+
+def _reorth_arith(args):
+    if args.precision == "fp64" and args.reorth_arith == "auto":
+        a = "fp64"
+    else:
+        a = {"auto": "split", "split": "split"}.get(args.reorth_arith, args.reorth_arith)
+    return {"split": "split48: basis stored as float pairs hi+lo (48 significant bits), "
+                     "double-float dot products on the FP32 pipe, FP64 recurrence",
+            "split32": "split32: float-only basis, double-float dot products, FP64 recurrence",
+            "fp64": "fp64: basis, dots and updates in FP64"}[a]
+
+
 def _config(args):
     return {"workload": (f"Lanczos GW Sigma_c + QP, N_v=128 N_c=1024 (N_vc=131072) "
                          f"N_aux=2048, k={args.k} {args.reorth.upper()}, {args.tps} targets x "
                          f"256 summed orbitals per step, 1000 frequencies"),
             "n_vc": 131072, "n_aux": 2048, "k": args.k, "targets_per_step": args.tps,
             "start_vectors_per_step": args.tps * M_PER_TARGET, "n_freq": 1000,
-            "reorth": args.reorth, "precision": args.precision,
+            "reorth": args.reorth, "gram_schmidt": GS_SCHEDULE[args.reorth],
+            "reorth_arith": _reorth_arith(args), "precision": args.precision,
             "l2": "inputs larger than L2 (Krylov basis ~107 GB, bf16 L 2x0.54 GB)",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -179,6 +202,7 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
+    solo = rank == 0 and world == 1     # the comparison legs run on one replica only
 
     wl = gw_inputs.mid(n_targets=32, k=args.k)
     n_t_all = wl.n_t
@@ -191,9 +215,16 @@ def run_gpu(args):
     m_idx_d = torch.from_numpy(wl.m_idx).to(dev)
     tgt_all = torch.from_numpy(wl.targets).to(dev)
     sysd = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, eps_d, L_d, wl.kernel_factor)
-    opts = L.Options(k=args.k, precision=args.precision, reorth=args.reorth,
-                     b_sub=args.tps * M_PER_TARGET)
     tps = args.tps
+    B_step = tps * M_PER_TARGET
+
+    def options(**kw):
+        base = dict(k=args.k, precision=args.precision, reorth=args.reorth, b_sub=B_step,
+                    reorth_arith=args.reorth_arith)
+        base.update(kw)
+        return L.Options(**base)
+
+    opts = options()
     sig = torch.empty(tps, wl.omega.size, 2, dtype=torch.float64, device=dev)
     e = torch.empty(tps, dtype=torch.float64, device=dev)
     z = torch.empty(tps, dtype=torch.float64, device=dev)
@@ -227,88 +258,83 @@ def run_gpu(args):
     torch.cuda.synchronize()
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1)
-    # one CGS2 step (always two Gram-Schmidt passes) on the same workload, for comparison
-    cgs2 = None
-    if args.reorth == "cgs1k" and not args.no_cgs2_step:
-        o2 = L.Options(k=args.k, precision=args.precision, reorth="cgs2",
-                       b_sub=args.tps * M_PER_TARGET)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        L.lgw_sigma_c(h, sysd, batch(args.warmup + args.steps), o2, sig, e, z)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        cms = e0.elapsed_time(e1)
-        e_cgs2 = e.cpu().numpy().copy()
-        cgs2 = {"value": tps / (cms / 1e3), "unit": "QP states/s", "ms_per_step": cms,
-                "steps": 1}
-    # one step with the float-only Krylov basis (option), same batch as above
-    fbasis = None
-    if cgs2 is not None:
-        o3 = L.Options(k=args.k, precision=args.precision, reorth=args.reorth,
-                       b_sub=args.tps * M_PER_TARGET, reorth_arith="split32")
-        e0.record(stream)
-        L.lgw_sigma_c(h, sysd, batch(args.warmup + args.steps), o3, sig, e, z)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fms = e0.elapsed_time(e1)
-        fbasis = {"value": tps / (fms / 1e3), "unit": "QP states/s", "ms_per_step": fms,
-                  "steps": 1, "reorth_arith": "split32 (float-only basis)",
-                  "qp_diff_mev_vs_cgs2_split48": float(
-                      np.abs(e.cpu().numpy() - e_cgs2).max() * 1e3)}
-    # one step with E4M3 contractions (after one untimed call that makes the
-    # E4M3 copies of L and tunes its tiles), same batch
-    fp8 = None
-    if cgs2 is not None and args.precision == "bf16" and not args.no_fp8_step:
-        o4 = L.Options(k=args.k, precision="fp8", reorth=args.reorth,
-                       b_sub=args.tps * M_PER_TARGET)
-        L.lgw_sigma_c(h, sysd, batch(args.warmup + args.steps), o4, sig, e, z)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        r8 = L.lgw_sigma_c(h, sysd, batch(args.warmup + args.steps), o4, sig, e, z, report=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        f8ms = e0.elapsed_time(e1)
-        g8 = r8["ms_gemm1"] + r8["ms_gemm2"]
-        fp8 = {"value": tps / (f8ms / 1e3), "unit": "QP states/s", "ms_per_step": f8ms,
-               "steps": 1, "gemm_tflops": r8["gemm_flops"] / (g8 * 1e-3) / 1e12 if g8 else None,
-               "ms_gemm1": r8["ms_gemm1"], "ms_gemm2": r8["ms_gemm2"],
-               "qp_diff_mev_vs_bf16_cgs2": float(np.abs(e.cpu().numpy() - e_cgs2).max() * 1e3)}
-    # the paper's polynomial form (Lanczos on p_g(C) ~ C^1/2, no
-    # reorthogonalisation) on the same batch, against the primary result
-    poly = None
-    if cgs2 is not None and not args.no_poly:
-        # spectral interval of C: min Delta^2 (C >= Delta^2) and the bound
-        # max Delta^2 + c_K max Delta ||L||_2^2 (||L||_2^2 by power iteration)
-        Dl = (wl.eps[wl.n_v:][None, :] - wl.eps[:wl.n_v][:, None]).ravel()
-        xv = np.random.default_rng(0).standard_normal(wl.n_aux)
-        for _ in range(30):
-            xv = wl.L.T @ (wl.L @ xv)
-            nrm = np.linalg.norm(xv)
-            xv /= nrm
-        lmax = float(nrm) * 1.01
-        x_lo = float(Dl.min() ** 2)
-        x_hi = float(Dl.max() ** 2 + wl.kernel_factor * Dl.max() * lmax)
-        poly = {"interval": [x_lo, x_hi], "reorth": "none", "runs": []}
-        for g, kp in ((8, 8), (16, 16)):
-            op = L.Options(k=kp, precision=args.precision, reorth="none",
-                           b_sub=args.tps * M_PER_TARGET)
-            L.lgw_sigma_c_poly(h, sysd, batch(args.warmup + args.steps), op, g, x_lo, x_hi, sig, e)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            rp = L.lgw_sigma_c_poly(h, sysd, batch(args.warmup + args.steps), op, g, x_lo, x_hi,
-                                    sig, e, report=True)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            pms = e0.elapsed_time(e1)
-            poly["runs"].append({"g": g, "k": kp, "value": tps / (pms / 1e3),
-                                 "unit": "QP states/s", "ms_per_step": pms,
-                                 "gemm_ms": rp["ms_gemm1"] + rp["ms_gemm2"],
-                                 "qp_diff_mev_vs_primary": float(
-                                     np.abs(e.cpu().numpy() - e_cgs2).max() * 1e3)})
     ms_max = R.max_over_ranks(ms, dev) if world > 1 else ms
     states = tps * args.steps * world
     value = states / (ms_max / 1e3)
+
+    # The comparison legs all run on one batch (the first timed one, 2
+    # targets x 256 summed orbitals): the headline result on that batch is
+    # the reference for their QP differences.
+    cmp_batch = batch(args.warmup)
+    cmp_targets = [int(t) for t in wl.targets[R.targets_for_step(args.warmup, rank, world, tps,
+                                                                  n_t_all)]]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed_step(hh, ss, o, poly=None):
+        """One untimed call (workspace, E4M3 copies, tile tuning), then one
+        call timed with CUDA events on the stream; returns (ms, E, Sigma, report)."""
+        for rep_i in range(2):
+            if rep_i == 1:
+                e0.record(stream)
+            if poly is None:
+                r = L.lgw_sigma_c(hh, ss, cmp_batch, o, sig, e, z, report=rep_i == 1)
+            else:
+                r = L.lgw_sigma_c_poly(hh, ss, cmp_batch, o, poly[0], poly[1], poly[2], sig, e,
+                                       report=rep_i == 1)
+            if rep_i == 1:
+                e1.record(stream)
+            torch.cuda.synchronize()
+        return e0.elapsed_time(e1), e.cpu().numpy().copy(), sig.cpu().numpy().copy(), r
+
+    legs = {}
+    e_head = sig_head = None
+    if solo:
+        ms_head, e_head, sig_head, _ = timed_step(h, sysd, opts)
+
+        def leg(name, o, note):
+            lms, le, lsig, lr = timed_step(h, sysd, o)
+            g8 = lr["ms_gemm1"] + lr["ms_gemm2"]
+            legs[name] = {"value": tps / (lms / 1e3), "unit": "QP states/s", "ms_per_step": lms,
+                          "steps": 1, "what": note,
+                          "gemm_tflops": lr["gemm_flops"] / (g8 * 1e-3) / 1e12 if g8 else None,
+                          "qp_diff_mev_vs_headline": float(np.abs(le - e_head).max() * 1e3),
+                          "sigma_max_diff_mev_vs_headline":
+                              float(np.abs(lsig - sig_head).max() * 1e3)}
+        if not args.no_variants:
+            leg("cgs1k_two_pass_step", options(reorth="cgs1k"),
+                "two-pass CGS1K (dots, then update) on the same float-pair basis")
+            leg("cgs2_step", options(reorth="cgs2"),
+                "CGS2 (always two passes) on the same float-pair basis")
+            leg("float_basis_step", options(reorth_arith="split32"),
+                "delayed single sweep against a float-only basis (split32)")
+            if args.precision == "bf16":
+                leg("fp8_step", options(precision="fp8"),
+                    "E4M3 contractions (kind::f8f6f4) with power-of-two scales")
+        # the paper's polynomial form (Lanczos on p_g(C) ~ C^1/2, no
+        # reorthogonalisation) on the same batch, against the primary result
+        if not args.no_poly:
+            # spectral interval of C: min Delta^2 (C >= Delta^2) and the bound
+            # max Delta^2 + c_K max Delta ||L||_2^2 (||L||_2^2 by power iteration)
+            Dl = (wl.eps[wl.n_v:][None, :] - wl.eps[:wl.n_v][:, None]).ravel()
+            xv = np.random.default_rng(0).standard_normal(wl.n_aux)
+            for _ in range(30):
+                xv = wl.L.T @ (wl.L @ xv)
+                nrm = np.linalg.norm(xv)
+                xv /= nrm
+            lmax = float(nrm) * 1.01
+            x_lo = float(Dl.min() ** 2)
+            x_hi = float(Dl.max() ** 2 + wl.kernel_factor * Dl.max() * lmax)
+            poly = {"interval": [x_lo, x_hi], "reorth": "none", "runs": []}
+            for g, kp in ((8, 8), (16, 16)):
+                pms, pe, _, rp = timed_step(h, sysd, options(k=kp, reorth="none"),
+                                            poly=(g, x_lo, x_hi))
+                poly["runs"].append({"g": g, "k": kp, "value": tps / (pms / 1e3),
+                                     "unit": "QP states/s", "ms_per_step": pms,
+                                     "gemm_ms": rp["ms_gemm1"] + rp["ms_gemm2"],
+                                     "qp_diff_mev_vs_primary": float(
+                                         np.abs(pe - e_head).max() * 1e3)})
+            legs["poly_variant"] = poly
 
     # --- end to end through the public API with pinned host buffers ---
     eps_h = torch.from_numpy(wl.eps).pin_memory()
@@ -345,30 +371,14 @@ def run_gpu(args):
     agg = {k: sum(r[k] for r in reps) for k in reps[0] if k.startswith("ms_") or k in (
         "gemm_flops", "reorth_elems", "gpu_launches", "n_second_pass")}
     r0 = reps[0]
-    nvc, A = wl.n_vc, wl.n_aux
+    nvc = wl.n_vc
     B = r0["n_vectors"] * args.steps
     kk = args.k
     launches_per_cat = r0["n_sub_batches"] * kk * args.steps
     hbm, bf16_burst, bf16_sus, peak_src = _peaks()
-    split = args.precision == "bf16"     # the library's automatic choice
-    if split:   # float-pair basis: hi+lo read by the dots, hi by the update
-        by = {
-            "update": (4.0 * agg["reorth_elems"] + 16.0 * nvc * B * kk, agg["ms_update"],
-                       "k_update_split<1> (w -= Q h in FP32 from the hi basis)"),
-            "dots": (8.0 * agg["reorth_elems"] + 28.0 * nvc * B * kk, agg["ms_dots"],
-                     "k_dots_split<1> (w assembly, alpha axpy, double-float Q^T w)"),
-        }
-    else:
-        by = {
-            "update": (8.0 * agg["reorth_elems"] + 16.0 * nvc * B * kk, agg["ms_update"],
-                       "k_update (first Gram-Schmidt update w -= Q h)"),
-            "dots": (8.0 * agg["reorth_elems"] + 24.0 * nvc * B * kk, agg["ms_dots"],
-                     "k_alpha_axpy (alpha, axpy, first-pass Q^T w)"),
-        }
-    dom = max(by, key=lambda x: by[x][1])
-    bytes_, ms_k, kname = by[dom]
+    bytes_, ms_k, kname, tkey, rows_t = _roofline_kernel(args, agg, nvc, B, kk)
     achieved = bytes_ / (ms_k / 1e3) / 1e9
-    traffic = _dram_traffic(dom, split, agg["reorth_elems"], nvc * B * kk, launches_per_cat)
+    traffic = _dram_traffic(tkey, rows_t, nvc * B * kk, launches_per_cat)
     gemm_ms = agg["ms_gemm1"] + agg["ms_gemm2"]
     gemm_tflops = agg["gemm_flops"] / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
 
@@ -385,8 +395,10 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
-                     "traffic": traffic, "traffic_source": "ncu dram bytes of the same kernel "
-                     "on a 64-vector case, scaled per processed element (profiles/)",
+                     "traffic": traffic,
+                     "traffic_source": ("ncu dram bytes of the same kernel on a 64-vector case, "
+                                        "scaled per processed element (profiles/)")
+                     if traffic else "no ncu capture of this kernel version",
                      "algorithmic_bytes_per_launch": bytes_ / launches_per_cat,
                      "launches": launches_per_cat,
                      "avg_launch_ms": ms_k / launches_per_cat},
@@ -396,43 +408,90 @@ def run_gpu(args):
                  "splits": r0["gemm1_splits"]},
         "breakdown_ms": {k: agg[k] for k in agg if k.startswith("ms_")},
         "n_second_pass": int(agg["n_second_pass"]),
-        "cgs2_step": cgs2,
-        "float_basis_step": fbasis,
-        "fp8_step": fp8,
-        "poly_variant": poly,
     }
-    if rank == 0 and world == 1 and not args.no_fp64_compare:
-        line["fp64_path"] = fp64_compare(args, L, h, sysd, wl, tgt_all, m_idx_d, omega_d, M_all,
-                                         dev)
-        if line["fp64_path"].get("value"):
-            line["fp64_path"]["mixed_over_fp64"] = value / line["fp64_path"]["value"]
-    if rank == 0 and world == 1 and not args.no_adjoint:
-        line["adjoint"] = adjoint_leg(L, h, dev)
-    if rank == 0 and world == 1 and not args.no_batched:
-        line["batched"] = batched_leg(L, h, dev, max_targets=args.batched_targets)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    line.update(legs)
+    if solo:
+        line["comparison_batch"] = {"targets": cmp_targets, "summed_orbitals": M_PER_TARGET,
+                                    "start_vectors": B_step}
+    L.lgw_release_system(sysd)
+    L.lgw_destroy(h)
+    if solo and not args.no_fp64_compare:
+        line.update(fp64_legs(args, L, wl, eps_d, L_d, cmp_batch, e_head, sig_head, value, dev,
+                              stream))
+    del L_d, M_all
+    torch.cuda.empty_cache()
+    if solo and not args.no_adjoint:
+        ha = L.lgw_create(local, stream)
+        line["adjoint"] = adjoint_leg(L, ha, dev)
+        L.lgw_destroy(ha)
+    if solo and not args.no_batched:
+        hb = L.lgw_create(local, stream)
+        line["batched"] = batched_leg(L, hb, dev, max_targets=args.batched_targets,
+                                      reorth=args.reorth)
+        L.lgw_destroy(hb)
+    torch.cuda.empty_cache()
+    if solo and not args.no_large:
+        line["large"] = large_leg(L, dev, n_targets=args.large_targets)
+    if solo and not args.no_cpu_baseline:
         dt, sps, cores = oracle_sample(n_vec=args.ref_vectors, k=args.k)
         line["cpu_baseline"] = {
             "value": sps, "unit": "QP states/s", "cores": cores, "kind": "oracle",
             "sample": f"{args.ref_vectors} of 256 start vectors of one QP state, k={args.k} "
                       f"CGS2, numpy FP64 ({dt:.1f} s); extrapolated x256/{args.ref_vectors}"}
-    L.lgw_release_system(sysd)
-    L.lgw_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def _dram_traffic(dom, split, reorth_elems, elem_steps, launches):
+def _roofline_kernel(args, agg, nvc, B, k):
+    """Algorithmic bytes, CUDA-event time and name of the dominant kernel of
+    the timed steps, with the key of its ncu traffic coefficients.  Basis
+    row-elements: reorth_elems counts N_vc * sum_j (j+1) per vector (rows
+    0..j at step j); the delayed sweep of step j reads rows 0..j-1, one
+    fewer per step (every vector runs all k steps here)."""
+    rows = agg["reorth_elems"]
+    es = float(nvc) * B * k            # element-steps
+    split = args.precision != "fp64" and args.reorth_arith in ("auto", "split", "split32")
+    lo = args.reorth_arith != "split32"
+    if args.reorth == "dcgs" and split:
+        rows_d = rows - es
+        per_row = 8.0 if lo else 4.0
+        # reads: carried vector (8), c_K Delta^1/2 L y (4); writes: basis
+        # row j (8 or 4), carried vector (8), bf16 operand (2)
+        per_es = 8.0 + 4.0 + per_row + 8.0 + 2.0
+        return (per_row * rows_d + per_es * es, agg["ms_dots"],
+                "k_sweep_dcgs (delayed single-sweep Gram-Schmidt: double-float Q^T v, "
+                "delayed q_j update, w_j)", "k_sweep_dcgs", rows_d)
+    if split:   # float-pair basis: hi+lo read by the dots, hi by the update
+        by = {
+            "update": (4.0 * rows + 16.0 * es, agg["ms_update"],
+                       "k_update_split<1> (w -= Q h in FP32 from the hi basis)", None),
+            "dots": (8.0 * rows + 28.0 * es, agg["ms_dots"],
+                     "k_dots_split<1> (w assembly, alpha axpy, double-float Q^T w)",
+                     "k_dots_split"),
+        }
+    else:
+        by = {
+            "update": (8.0 * rows + 16.0 * es, agg["ms_update"],
+                       "k_update (first Gram-Schmidt update w -= Q h)", None),
+            "dots": (8.0 * rows + 24.0 * es, agg["ms_dots"],
+                     "k_alpha_axpy (alpha, axpy, first-pass Q^T w)", None),
+        }
+    dom = max(by, key=lambda x: by[x][1])
+    return by[dom] + (rows,)
+
+
+def _dram_traffic(key, rows, elem_steps, launches):
     """DRAM bytes per launch of the dominant kernel from the ncu coefficients in
-    profiles/k_dots_split_traffic.txt (bytes per basis-row element and per
-    element-step, measured on a small case of the same kernel), or None."""
-    if not (split and dom == "dots"):
+    profiles/<key>_traffic.txt (bytes per basis-row element and per
+    element-step, fitted on a small case of the same kernel), or None when
+    no capture of this kernel exists."""
+    if key is None or rows is None:
         return None
     try:
         vals = {}
-        with open(os.path.join(ROOT, "profiles", "k_dots_split_traffic.txt")) as f:
+        with open(os.path.join(ROOT, "profiles", f"{key}_traffic.txt")) as f:
             for line in f:
                 parts = line.split()
                 if len(parts) == 2:
@@ -441,35 +500,56 @@ def _dram_traffic(dom, split, reorth_elems, elem_steps, launches):
         per_step = float(vals["bytes_per_element_step"])
     except Exception:
         return None
-    return (per_row * reorth_elems + per_step * elem_steps) / launches
+    return (per_row * rows + per_step * elem_steps) / launches
 
 
-def fp64_compare(args, L, h, sysd, wl, tgt_all, m_idx_d, omega_d, M_all, dev):
-    """The plain FP64 path on a subsample: one target with the first n_m
-    summed orbitals, both precisions, same k and reorthogonalisation; gives
-    the FP64 states/s (vectors/s / 256) and the QP difference in meV."""
+def fp64_legs(args, L, wl, eps_d, L_d, prob, e_head, sig_head, value_head, dev, stream):
+    """On the comparison batch (the same 512 start vectors, k, frequencies),
+    in a fresh handle so that no other Krylov basis shares the device:
+      cgs2_fp64_basis_step  BF16 contractions, CGS2 against an FP64 basis
+                            (every product and sum on the FP64 pipe);
+      fp64_path             the plain FP64 GPU path: FP64 CUDA-core
+                            contractions, FP64 basis, CGS1K; its QP energies
+                            against the headline's (the 1 meV criterion).
+    mixed_over_fp64 = headline states/s over the FP64 path's states/s."""
     import torch
-    n_m = args.fp64_vectors
-    prob = L.Problem(targets=tgt_all[:1].contiguous(), m_idx=m_idx_d[:n_m].contiguous(),
-                     omega=omega_d, delta=wl.delta, M=M_all[:1, :n_m].contiguous())
+    tps = args.tps
+    h = L.lgw_create(dev.index if dev.index is not None else 0, stream)
+    s = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, eps_d, L_d, wl.kernel_factor)
+    sig = torch.empty(tps, wl.omega.size, 2, dtype=torch.float64, device=dev)
+    e = torch.empty(tps, dtype=torch.float64, device=dev)
     out = {}
-    for prec in ("fp64", "bf16"):
-        sg = torch.empty(1, wl.omega.size, 2, dtype=torch.float64, device=dev)
-        ee = torch.empty(1, dtype=torch.float64, device=dev)
-        o = L.Options(k=args.k, precision=prec, reorth=args.reorth)
-        L.lgw_sigma_c(h, sysd, prob, o, sg, ee)          # warm-up
-        torch.cuda.synchronize()
+    runs = [("cgs2_fp64_basis_step", "bf16", "cgs2", args.k, 1,
+             "BF16 contractions, CGS2 against an FP64 Krylov basis (FP64 dots and updates)"),
+            ("fp64_path", "fp64", "cgs1k", args.fp64_k, 0,
+             "plain FP64 path: FP64 CUDA-core contractions, FP64 basis, CGS1K")]
+    for name, prec, reorth, kk, warm, note in runs:
+        o = L.Options(k=kk, precision=prec, reorth=reorth, b_sub=tps * M_PER_TARGET,
+                      reorth_arith="fp64")
+        if warm:
+            L.lgw_sigma_c(h, s, prob, o, sig, e)
+            torch.cuda.synchronize()
         t0 = time.perf_counter()
-        L.lgw_sigma_c(h, sysd, prob, o, sg, ee)
+        rep = L.lgw_sigma_c(h, s, prob, o, sig, e, report=True)
         torch.cuda.synchronize()
-        out[prec] = (time.perf_counter() - t0, sg.cpu().numpy(), float(ee.item()))
-    t64 = out["fp64"][0]
-    dsig = np.abs(out["bf16"][1] - out["fp64"][1]).max() * 1e3
-    return {"value": n_m / t64 / M_PER_TARGET, "unit": "QP states/s",
-            "sample": f"1 target x {n_m} summed orbitals (of 256), same k and reorth; "
-                      f"states/s = vectors/s / 256",
-            "seconds": t64, "qp_diff_mev_bf16_vs_fp64": abs(out["bf16"][2] - out["fp64"][2]) * 1e3,
-            "sigma_max_diff_mev": dsig}
+        dt = time.perf_counter() - t0
+        gms = rep["ms_gemm1"] + rep["ms_gemm2"]
+        d = {"value": tps / dt, "unit": "QP states/s", "seconds": dt, "k": kk, "what": note,
+             "gemm_tflops": rep["gemm_flops"] / (gms * 1e-3) / 1e12 if gms else None,
+             "breakdown_ms": {x: round(v, 1) for x, v in rep.items() if x.startswith("ms_")}}
+        if kk == args.k:
+            d["qp_diff_mev_vs_headline"] = float(np.abs(e.cpu().numpy() - e_head).max() * 1e3)
+            d["sigma_max_diff_mev_vs_headline"] = float(
+                np.abs(sig.cpu().numpy() - sig_head).max() * 1e3)
+        out[name] = d
+    fp = out["fp64_path"]
+    fp["sample"] = (f"the headline's comparison batch: {tps} targets x 256 summed orbitals "
+                    f"({tps * M_PER_TARGET} start vectors), k {fp['k']}, one call")
+    if fp["k"] == args.k:
+        fp["mixed_over_fp64"] = value_head / fp["value"]
+    L.lgw_release_system(s)
+    L.lgw_destroy(h)
+    return out
 
 
 def adjoint_leg(L, h, dev, n_targets=8, compare=True):
@@ -527,12 +607,13 @@ def adjoint_leg(L, h, dev, n_targets=8, compare=True):
     return out
 
 
-def batched_leg(L, h, dev, max_targets=1, k=150):
+def batched_leg(L, h, dev, max_targets=64, k=150, reorth="dcgs", reps=1):
     """Batched-uneven workload: the 16 systems (N_vc 4975..62392, N_aux
-    512..2048, seed 100+i), min(drawn, max_targets) targets each x up to 256
-    summed orbitals, k 150, BF16, CGS1K, one lgw_sigma_c_batched call per
-    step; eager launches vs CUDA-graph replay (graphs captured in the
-    warm-up).  QP states/s = targets of all systems / wall time of a call."""
+    512..2048, seed 100+i), min(drawn, max_targets) targets each (the drawn
+    8..64 by default) x up to 256 summed orbitals, k 150, BF16, one
+    lgw_sigma_c_batched call per step; eager launches vs CUDA-graph replay
+    (graphs captured in the untimed call).  QP states/s = targets of all
+    systems / wall time of a call."""
     import torch
     import gw_inputs as gi
 
@@ -549,17 +630,17 @@ def batched_leg(L, h, dev, max_targets=1, k=150):
     out = {"workload": f"batched-uneven: 16 systems, N_vc {min(w.n_vc for w in wls)}.."
                        f"{max(w.n_vc for w in wls)}, N_aux {min(w.n_aux for w in wls)}.."
                        f"{max(w.n_aux for w in wls)}, {n_t} targets, "
-                       f"{sum(w.n_t * w.n_m for w in wls)} start vectors, k {k}, BF16, CGS1K",
+                       f"{sum(w.n_t * w.n_m for w in wls)} start vectors, k {k}, BF16, "
+                       f"{reorth.upper()}",
            "unit": "QP states/s"}
     res = {}
     for g in (0, 1):
-        o = L.Options(k=k, precision="bf16", reorth="cgs1k", use_graph=g)
-        for _ in range(2):
-            L.lgw_sigma_c_batched(h, systems, probs, o, sig, e)
+        o = L.Options(k=k, precision="bf16", reorth=reorth, use_graph=g)
+        L.lgw_sigma_c_batched(h, systems, probs, o, sig, e)
         torch.cuda.synchronize()
         ts = []
         launches = 0
-        for _ in range(2):
+        for _ in range(reps):
             t0 = time.perf_counter()
             rep = L.lgw_sigma_c_batched(h, systems, probs, o, sig, e, report=True)
             torch.cuda.synchronize()
@@ -638,11 +719,11 @@ def large_leg(L, dev, n_targets=2, k=300):
     return out
 
 
-def profile_case(prec="bf16"):
+def profile_case(prec="bf16", reorth="dcgs"):
     """The small case the kernel profiles are taken on: the mid-size system
     (N_vc 131072, N_aux 2048), target HOMO-15 summed over its first 64
-    orbitals (64 start vectors), k 48, CGS1K, one lgw_sigma_c call with a
-    report.  The Krylov basis is about 3 GB, larger than L2."""
+    orbitals (64 start vectors), k 48, one lgw_sigma_c call with a report.
+    The Krylov basis is about 3 GB, larger than L2."""
     import torch
     sys.path.insert(0, ROOT)
     import gw_inputs as gi
@@ -658,7 +739,7 @@ def profile_case(prec="bf16"):
                      delta=wl.delta, M=tt(wl.M[:, :64]))
     sig = torch.empty(1, wl.omega.size, 2, dtype=torch.float64, device="cuda:0")
     e = torch.empty(1, dtype=torch.float64, device="cuda:0")
-    rep = L.lgw_sigma_c(h, s, prob, L.Options(k=48, precision=prec, reorth="cgs1k"), sig, e,
+    rep = L.lgw_sigma_c(h, s, prob, L.Options(k=48, precision=prec, reorth=reorth), sig, e,
                         report=True)
     torch.cuda.synchronize()
     print(json.dumps({kk: (round(v, 3) if isinstance(v, float) else v) for kk, v in rep.items()}),
@@ -675,16 +756,21 @@ def main():
     ap.add_argument("--impl", default="lgw", choices=["lgw", "reference"])
     ap.add_argument("--k", type=int, default=200)
     ap.add_argument("--tps", type=int, default=2, help="target states per step")
-    ap.add_argument("--reorth", default="cgs1k", choices=["cgs2", "cgs1k", "none"])
+    ap.add_argument("--reorth", default="dcgs", choices=["dcgs", "cgs2", "cgs1k", "none"])
+    ap.add_argument("--reorth-arith", default="auto",
+                    choices=["auto", "split", "split32", "fp64"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--fp64-vectors", type=int, default=16)
+    ap.add_argument("--fp64-k", type=int, default=200,
+                    help="Lanczos steps of the FP64-path leg (the headline's k for a "
+                         "like-for-like ratio)")
     ap.add_argument("--ref-vectors", type=int, default=2)
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-cgs2-step", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the one-step variant legs (CGS1K, CGS2, float basis, E4M3)")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--no-fp8-step", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-poly", action="store_true")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint leg (differentiation workload) and print it")
@@ -692,7 +778,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched-uneven leg and print it")
-    ap.add_argument("--batched-targets", type=int, default=1)
+    ap.add_argument("--batched-targets", type=int, default=64)
     ap.add_argument("--large-only", action="store_true",
                     help="run only the large cluster-sized leg (about 2 minutes, ~240 GB)")
     ap.add_argument("--large-targets", type=int, default=2)
@@ -700,9 +786,10 @@ def main():
                     help="one small call for kernel profiles (mid-size system, 64 start "
                          "vectors, k 48, CGS1K; about 3 GB on the device) and its report")
     ap.add_argument("--profile-precision", default="bf16", choices=["bf16", "fp8", "fp64"])
+    ap.add_argument("--profile-reorth", default="dcgs", choices=["dcgs", "cgs1k", "cgs2"])
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_precision)
+        profile_case(args.profile_precision, args.profile_reorth)
         return
     if args.adjoint_only:
         import torch
@@ -726,7 +813,7 @@ def main():
         sys.path.insert(0, ROOT)
         from paper_2310_20103_gb300 import lgw as L
         h = L.lgw_create(0)
-        out = batched_leg(L, h, "cuda:0", max_targets=args.batched_targets)
+        out = batched_leg(L, h, "cuda:0", max_targets=args.batched_targets, reorth=args.reorth)
         L.lgw_destroy(h)
         print(json.dumps({"batched": out}), flush=True)
         return

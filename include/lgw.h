@@ -75,9 +75,23 @@ typedef enum {
 typedef enum {
   LGW_REORTH_NONE = 0,  /* three-term recurrence only                            */
   LGW_REORTH_CGS2 = 1,  /* full classical Gram-Schmidt, always two passes        */
-  LGW_REORTH_CGS1K = 2  /* full CGS, second pass only where the norm drops below
+  LGW_REORTH_CGS1K = 2, /* full CGS, second pass only where the norm drops below
                            1/sqrt(2) of its value before the pass (Kahan-Parlett
                            / Daniel-Gragg-Kaufman-Stewart criterion)              */
+  LGW_REORTH_DCGS = 3   /* full CGS with the update delayed by one step: the
+                           projection coefficients of w_j are computed in step
+                           j, and q_{j+1} = (w_j - Q_j h_j)/beta_{j+1} is formed
+                           in step j+1 inside the same single pass over the
+                           stored basis that computes w_{j+1}'s coefficients
+                           (one read of the basis per step instead of two).
+                           The contractions of step j+1 run on w_j/beta_{j+1};
+                           the difference C Q_j h_j/beta lies in span(Q_j) plus
+                           a multiple of q_{j+1} and is removed by the same
+                           projection, whose q_{j+1} coefficient is corrected
+                           by h_{j,j} in the recorded alpha_{j+1}.  A second
+                           pass is taken where the norm drops below 1/sqrt(2),
+                           as in CGS1K.  Split (float-pair / float) basis only;
+                           with the FP64 basis it runs as CGS1K.            */
 } lgw_reorth;
 
 /* Arithmetic of the full reorthogonalisation.
@@ -197,9 +211,11 @@ typedef struct {
   double ms_start;       /* coupling/start vectors and first normalisation   */
   double ms_gemm1;       /* L^T (Delta^1/2 q) contraction + partial reduce   */
   double ms_gemm2;       /* L y contraction + fused recurrence epilogue      */
-  double ms_dots;        /* alpha finish, axpy and first-pass Q^T w products */
+  double ms_dots;        /* alpha finish, axpy and first-pass Q^T w products
+                            (LGW_REORTH_DCGS: the single sweep)             */
   double ms_update;      /* first-pass w -= Q h (with the split basis also
-                            q_{j+1} for vectors that take no second pass)   */
+                            q_{j+1} for vectors that take no second pass;
+                            LGW_REORTH_DCGS: the per-vector reduction)      */
   double ms_pass2;       /* second Gram-Schmidt pass (decision, Q^T w, update) */
   double ms_normalize;   /* beta, breakdown test, q_{j+1}, bf16 operand (0
                             with the split basis: folded into the update)   */

@@ -90,7 +90,8 @@ __global__ void k_quantize_L8(const double *__restrict__ src, int ld, int nr, in
 // Both operands are K-block-major over Bs rows.
 __global__ void __launch_bounds__(256) k_quant_x8(const __nv_bfloat16 *__restrict__ xh, int Bs,
                                                   int N, uint8_t *__restrict__ x8,
-                                                  float *__restrict__ sx) {
+                                                  float *__restrict__ sx,
+                                                  const double *__restrict__ vscale) {
   __shared__ float red[8];
   __shared__ float sc;
   const int b = blockIdx.x;
@@ -115,7 +116,10 @@ __global__ void __launch_bounds__(256) k_quant_x8(const __nv_bfloat16 *__restric
     float t = 0.0f;
     for (int w = 0; w < 8; ++w) t = fmaxf(t, red[w]);
     sc = pow2_scale(t);
-    sx[b] = sc;
+    // the contraction result is scaled by sx; an unnormalised operand also
+    // carries its normalisation factor there (sx then need not be a power
+    // of two: it only multiplies the FP32 reduction)
+    sx[b] = vscale != nullptr ? sc * (float)vscale[b] : sc;
   }
   __syncthreads();
   const float inv = 1.0f / sc;   // a power of two: exact
@@ -203,8 +207,8 @@ void launch_prepare_fp8(const double *src, int ld, int nr, int nc, const SysDev 
 }
 
 void launch_quant_x8(const __nv_bfloat16 *xh, int Bs, int N, uint8_t *x8, float *sx,
-                     cudaStream_t st) {
-  k_quant_x8<<<Bs, 256, 0, st>>>(xh, Bs, N, x8, sx);
+                     cudaStream_t st, const double *vscale) {
+  k_quant_x8<<<Bs, 256, 0, st>>>(xh, Bs, N, x8, sx, vscale);
 }
 
 void launch_reduce_y_fp8(const float *Ypart, int splits, int Bs, int A, const float *sx,

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) k_gemm2_f64(const double *__restrict__ L6
         apart = fma(qv, wv, apart);
       }
     }
-    if (epi == EPI_LANCZOS && alpha_part != nullptr) {
+    if ((epi == EPI_LANCZOS || epi == EPI_APPLY) && alpha_part != nullptr) {
       // sum over the 16 threads (tx) that share row b: lanes differ in bits 0..3
 #pragma unroll
       for (int o = 8; o >= 1; o >>= 1) apart += __shfl_xor_sync(0xffffffffu, apart, o);

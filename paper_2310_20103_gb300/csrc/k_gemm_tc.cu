@@ -422,7 +422,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // Yh = bf16(sum_p Ypart[p]) in fixed order; optionally per-block partials of
 // sum_mu y_mu Yh_mu (grid: A/256 blocks per vector row).
 __global__ void k_reduce_y_bf16(const float *__restrict__ Ypart, int splits, int Bs, int A,
-                                __nv_bfloat16 *__restrict__ Yh, float *__restrict__ yy) {
+                                __nv_bfloat16 *__restrict__ Yh, float *__restrict__ yy,
+                                const double *__restrict__ vscale) {
   __shared__ float red[8];
   const int b = blockIdx.y;
   const int mu = blockIdx.x * 256 + threadIdx.x;
@@ -431,6 +432,8 @@ __global__ void k_reduce_y_bf16(const float *__restrict__ Ypart, int splits, int
   const size_t i = (size_t)b * A + mu;
   if (mu < A) {
     for (int p = 0; p < splits; ++p) s += Ypart[(size_t)p * n + i];
+    // a contraction of an unnormalised vector: scale to the normalised one
+    if (vscale != nullptr) s *= (float)vscale[b];
     const __nv_bfloat16 hq = __float2bfloat16_rn(s);
     Yh[i] = hq;
     s *= __bfloat162float(hq);
@@ -668,9 +671,9 @@ void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st) {
 }
 
 void launch_reduce_y_bf16(const float *Ypart, int splits, int Bs, int A, __nv_bfloat16 *Yh,
-                          float *yy, cudaStream_t st) {
+                          float *yy, cudaStream_t st, const double *vscale) {
   dim3 grid((A + 255) / 256, Bs);
-  tc::k_reduce_y_bf16<<<grid, 256, 0, st>>>(Ypart, splits, Bs, A, Yh, yy);
+  tc::k_reduce_y_bf16<<<grid, 256, 0, st>>>(Ypart, splits, Bs, A, Yh, yy, vscale);
 }
 
 void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qprev,

@@ -411,11 +411,13 @@ __global__ void __launch_bounds__(VEC_THREADS) k_start_split(VecCtx c) {
       c.k_eff[v] = beta > 0.0 ? c.k : 0;
       c.amax[b] = 0.0;
       c.betaj[b] = 0.0;
+      c.sinv[b] = beta > 0.0 ? 1.0 : 0.0;   // q_0 is carried normalised
     }
     live = beta > 0.0;
     inv = sinv;
   } else if (chunk == 0 && threadIdx.x == 0) {
     c.betaj[b] = 0.0;
+    c.sinv[b] = 0.0;
   }
   const size_t voff = (size_t)b * c.N;
   double *qn = slot_ptr(c, 0) + voff;
@@ -459,6 +461,547 @@ __global__ void __launch_bounds__(VEC_THREADS) k_start_split(VecCtx c) {
       c.dq2_part[(size_t)b * c.nchunks + chunk] = t;
     }
   }
+}
+
+// ===========================================================================
+// Delayed classical Gram-Schmidt (LGW_REORTH_DCGS): one pass over the
+// stored basis per step.
+//
+// Step j receives the carried vector w_{j-1} (c.wv, not normalised),
+// 1/beta_j (c.sinv) and the projection coefficients h = Q_{j-1}^T w_{j-1}
+// of the previous step (c.h), whose update has not been applied yet.  The
+// contractions of this step already ran on q~_j = w_{j-1} / beta_j.  The
+// basis vector is q_j = q~_j - Q_{j-1} h / beta_j.  Since C is linear,
+//   C q_j = C q~_j - Q_{j-1} T_{j-1} h / beta_j - h_{j-1} q_j + O(eps |h|),
+// i.e. C q~_j differs from C q_j by a vector of span(Q_j).  So the step
+// forms, per element (Eq. 13 with the estimate alpha~_j),
+//   v = C q~_j - alpha~_j q~_j - beta_j q_{j-1},
+// and the projection of v on Q_j removes everything the delay changed:
+// v - Q_j Q_j^T v equals the exactly recurred, fully reorthogonalised w_j,
+// and the q_j coefficient h'_j = q_j . v = alpha_j - alpha~_j + h_{j-1}
+// gives the FP64 Rayleigh quotient alpha_j = alpha~_j + h'_j - h_{j-1}.
+// The span(Q_{j-1}) part of v is known before the sweep: with c = h/beta_j,
+//   Q_{j-1}^T v = g + (rounding),   g = (T_{j-1} - alpha~_j) c,
+// T_{j-1} being the tridiagonal recorded so far.  If it stayed in the
+// carried vector, the next step's contraction would map it through T again
+// and the carried components would grow by ||T - alpha~||/beta every step
+// (the delay never cleans the vector).  So the sweep also subtracts Q_{j-1} g:
+// in one pass over the rows q_i (i < j) each element accumulates
+//   d_i  += q_i . v          (double-float, as k_dots_split)
+//   corr += c_i q_i          (FP32 from q_hi: every c_i is small)
+//   cv   += g_i q_i          (FP32 from q_hi: every g_i is small)
+// and then writes q_j = q~_j - corr into row j of the basis, the next
+// carried vector w_j = v - cv, the bf16 operand Delta^1/2 w_j (the
+// reduction after GEMM1 scales the contraction by 1/beta_{j+1}) and the
+// partials of q_j . w_j, ||w_j||^2 and sum Delta^2 w_j^2.  The reduction
+// takes Q_{j-1}^T w_j = d - g (Q orthonormal).  Bytes per element and step:
+// 8 per stored row (hi + lo) + 30, against 12 per row + 54 for the two
+// passes of k_dots_split and k_update_split.
+//
+// Thread layout: one block per (2048-element chunk, vector); each thread
+// owns elements e = chunk*2048 + warp*256 + 4*lane + 128*u + {0..3},
+// u = 0, 1, for all rows, so the correction needs no cross-thread sum.
+// Each row's dot partial is reduced by a double-float butterfly per warp
+// and across the eight warps through shared memory, 32 rows at a time.
+// ===========================================================================
+
+// Rows i_top, i_top - 1, ..., i_top - R + 1 of vector b: loads first (4R
+// independent 128-bit loads per thread), then the products.
+template <bool LO, bool CORR, int R>
+__device__ __forceinline__ void sweep_rows(const VecCtx &c, int b, int i_top, int ebase,
+                                           const float *cs, const float *gs,
+                                           const float (&vh)[8], const float (&vl)[8],
+                                           float (&corr)[8], float (&cv)[8],
+                                           float2 (*pp)[VEC_THREADS / 32], int slot0, int lane,
+                                           int wid) {
+  float4 hq[R][2], lq[R][2];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const float *qh = bhi_row(c, i_top - q, b);
+    const float *ql = LO ? blo_row(c, i_top - q, b) : nullptr;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = ebase + 128 * u;
+      if (e < c.N) {
+        hq[q][u] = __ldg(reinterpret_cast<const float4 *>(qh + e));
+        lq[q][u] = LO ? __ldg(reinterpret_cast<const float4 *>(ql + e))
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        hq[q][u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        lq[q][u] = hq[q][u];
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const float cf = CORR ? cs[i_top - q] : 0.0f;
+    const float gf = CORR ? gs[i_top - q] : 0.0f;
+    float sh = 0.f, sl = 0.f;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float xa[4] = {hq[q][u].x, hq[q][u].y, hq[q][u].z, hq[q][u].w};
+      const float xb[4] = {lq[q][u].x, lq[q][u].y, lq[q][u].z, lq[q][u].w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int m = 4 * u + t;
+        if (CORR) {
+          corr[m] = fmaf(cf, xa[t], corr[m]);
+          cv[m] = fmaf(gf, xa[t], cv[m]);
+        }
+        const float pr = __fmul_rn(xa[t], vh[m]);
+        float err = __fmaf_rn(xa[t], vh[m], -pr);
+        err = __fmaf_rn(xa[t], vl[m], err);
+        if (LO) err = __fmaf_rn(xb[t], vh[m], err);
+        two_sum_acc(sh, sl, pr);
+        sl = __fadd_rn(sl, err);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const float rh = __shfl_xor_sync(0xffffffffu, sh, o);
+      const float rl = __shfl_xor_sync(0xffffffffu, sl, o);
+      df_add(sh, sl, rh, rl);
+    }
+    if (lane == 0) pp[slot0 + q][wid] = make_float2(sh, sl);
+  }
+}
+
+// All rows i = nrows - 1 down to 0 (the newest row first: the sweep has just
+// read it and it is still in L1).  Row partials of the block go to
+// dp[i] (one double per row); CORR also accumulates the delayed update.
+template <bool LO, bool CORR>
+__device__ __forceinline__ void sweep_all_rows(const VecCtx &c, int b, int nrows, int ebase,
+                                               const float *cs, const float *gs,
+                                               const float (&vh)[8], const float (&vl)[8],
+                                               float (&corr)[8], float (&cv)[8],
+                                               float2 (*part)[32][VEC_THREADS / 32],
+                                               double *dp) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int t0 = 0; t0 < nrows; t0 += 32) {
+    const int nt = min(32, nrows - t0);
+    float2 (*pp)[VEC_THREADS / 32] = part[(t0 >> 5) & 1];
+    const int itop = nrows - 1 - t0;
+    // rows in flight per trip: 2 with the lo halves (8 loads of 16 bytes per
+    // thread), 4 without; more would spill
+    constexpr int RR = LO ? 2 : 4;
+    int r = 0;
+    for (; r + RR <= nt; r += RR)
+      sweep_rows<LO, CORR, RR>(c, b, itop - r, ebase, cs, gs, vh, vl, corr, cv, pp, r, lane, wid);
+    for (; r < nt; ++r)
+      sweep_rows<LO, CORR, 1>(c, b, itop - r, ebase, cs, gs, vh, vl, corr, cv, pp, r, lane, wid);
+    // the two tile buffers alternate, so one barrier per tile suffices: tile
+    // t + 2 reuses this buffer only after warp 0 passed tile t + 1's barrier
+    __syncthreads();
+    if (wid == 0 && lane < nt) {
+      float hs = 0.f, ls = 0.f;
+#pragma unroll
+      for (int w = 0; w < VEC_THREADS / 32; ++w) df_add(hs, ls, pp[lane][w].x, pp[lane][w].y);
+      dp[itop - lane] = (double)hs + (double)ls;
+    }
+  }
+}
+
+// Block-wide sum of a float through the double block_sum.
+__device__ __forceinline__ float block_sum_f(float v, double *red) {
+  return (float)block_sum((double)v, red);
+}
+
+template <bool LO, bool F64U>
+__global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) {
+  extern __shared__ float cs[];   // [2j]: c_i = h_i / beta_j, then g_i
+  __shared__ float2 part[2][32][VEC_THREADS / 32];
+  __shared__ double red[VEC_THREADS / 32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int ebase = chunk * VEC_CHUNK + wid * 256 + 4 * lane;
+  if (!live_s(c, b, j)) {
+    // stopped or padding vector: the contractions see zeros
+    if (c.xh != nullptr) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = ebase + 128 * u;
+        if (e < c.N) *reinterpret_cast<uint2 *>(c.xh + kblk_bf16(b, e, c.Bs)) = make_uint2(0u, 0u);
+      }
+    }
+    return;
+  }
+  const double sinv = c.sinv[b], bj = c.betaj[b];
+  float *gs = cs + j;
+  // alpha~_j = q~_j . C q~_j: from the FP64 contraction's partials, or
+  // sum Delta^2 q~^2 + c_K y . bf16(y) on the tensor-core path
+  double s = 0.0;
+  if (F64U) {
+    for (int t = threadIdx.x; t < c.n_mt; t += VEC_THREADS) s += c.alpha_part[(size_t)t * c.Bs + b];
+    s *= sinv * sinv;
+  } else {
+    double sq = 0.0, sy = 0.0;
+    for (int t = threadIdx.x; t < c.nchunks; t += VEC_THREADS)
+      sq += (double)c.dq2_part[(size_t)b * c.nchunks + t];
+    for (int t = threadIdx.x; t < c.n_yb; t += VEC_THREADS)
+      sy += (double)c.yy_part[(size_t)b * c.n_yb + t];
+    s = sq * sinv * sinv + c.kf * sy;
+  }
+  const double alpha = block_sum(s, red);
+  if (chunk == 0 && threadIdx.x == 0) c.alpha[(size_t)(c.vec0 + b) * c.k + j] = alpha;
+  // c_i = h_i / beta_j and g = (T_{j-1} - alpha~) c; the chunk-0 block keeps
+  // g in FP64 for the reduction
+  {
+    const size_t v = (size_t)(c.vec0 + b);
+    const double *hb = c.h + (size_t)b * c.kmax1;
+    for (int i = threadIdx.x; i < j; i += VEC_THREADS) {
+      const double ci = hb[i] * sinv;
+      double g = (c.alpha[v * c.k + i] - alpha) * ci;
+      if (i >= 1) g = fma(c.beta[v * c.k + i - 1], hb[i - 1] * sinv, g);
+      if (i + 1 < j) g = fma(c.beta[v * c.k + i], hb[i + 1] * sinv, g);
+      cs[i] = (float)ci;
+      gs[i] = (float)g;
+      if (chunk == 0) c.gq[(size_t)b * c.kmax1 + i] = g;
+    }
+  }
+  __syncthreads();
+
+  const size_t voff = (size_t)b * c.N;
+  // v is kept as the float pair (vh, vl), 48 bits: the projections are
+  // computed for exactly that vector, and it is what the next step carries
+  double qt[8];
+  float vh[8], vl[8], corr[8], cv[8];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = ebase + 128 * u;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      qt[4 * u + t] = 0.0;
+      vh[4 * u + t] = 0.0f;
+      vl[4 * u + t] = 0.0f;
+      corr[4 * u + t] = 0.0f;
+      cv[4 * u + t] = 0.0f;
+    }
+    if (e >= c.N) continue;
+    const double2 w0 = *reinterpret_cast<const double2 *>(c.wv + voff + e);
+    const double2 w1 = *reinterpret_cast<const double2 *>(c.wv + voff + e + 2);
+    const double wq[4] = {w0.x, w0.y, w1.x, w1.y};
+    double uu[4];
+    if (F64U) {
+      const double2 a0 = *reinterpret_cast<const double2 *>(c.uC + voff + e);
+      const double2 a1 = *reinterpret_cast<const double2 *>(c.uC + voff + e + 2);
+      const double av[4] = {a0.x, a0.y, a1.x, a1.y};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        qt[4 * u + t] = wq[t] * sinv;
+        uu[t] = av[t] * sinv;
+      }
+    } else {
+      const float4 uk = *reinterpret_cast<const float4 *>(c.ucd + kblk_f32(b, e, c.Bs));
+      const double2 d0 = *reinterpret_cast<const double2 *>(c.Delta2 + e);
+      const double2 d1 = *reinterpret_cast<const double2 *>(c.Delta2 + e + 2);
+      const double dd[4] = {d0.x, d0.y, d1.x, d1.y};
+      const float ku[4] = {uk.x, uk.y, uk.z, uk.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        qt[4 * u + t] = wq[t] * sinv;
+        // C q~ = Delta^2 q~ + c_K Delta^1/2 L L^T Delta^1/2 q~   (Eq. 4)
+        uu[t] = fma(dd[t], qt[4 * u + t], (double)ku[t]);
+      }
+    }
+    double qp[4] = {0.0, 0.0, 0.0, 0.0};
+    if (j >= 1) {
+      const float4 ph = *reinterpret_cast<const float4 *>(bhi_row(c, j - 1, b) + e);
+      const float4 pl = LO ? *reinterpret_cast<const float4 *>(blo_row(c, j - 1, b) + e)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      qp[0] = (double)ph.x + (double)pl.x;
+      qp[1] = (double)ph.y + (double)pl.y;
+      qp[2] = (double)ph.z + (double)pl.z;
+      qp[3] = (double)ph.w + (double)pl.w;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int m = 4 * u + t;
+      const double vd = fma(-bj, qp[t], fma(-alpha, qt[m], uu[t]));
+      vh[m] = __double2float_rn(vd);
+      vl[m] = __double2float_rn(vd - (double)vh[m]);
+    }
+  }
+
+  double *dp = c.dot_part + ((size_t)b * c.nchunks + chunk) * c.kmax1;
+  sweep_all_rows<LO, true>(c, b, j, ebase, cs, gs, vh, vl, corr, cv, part, dp);
+
+  // q_j into row j of the basis; carried vector, operand and partials
+  float *hn = c.bhi + ((size_t)j * c.Bs + b) * c.N;
+  float *ln = LO ? c.blo + ((size_t)j * c.Bs + b) * c.N : nullptr;
+  double hj = 0.0, nrm = 0.0;
+  float dq = 0.0f;
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = ebase + 128 * u;
+    if (e >= c.N) continue;
+    float qh4[4], ql4[4];
+    double vd[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int m = 4 * u + t;
+      vd[t] = ((double)vh[m] + (double)vl[m]) - (double)cv[m];   // w_j = v - Q_{j-1} g
+      vh[m] = __double2float_rn(vd[t]);
+      const double qj = qt[m] - (double)corr[m];
+      qh4[t] = __double2float_rn(qj);
+      ql4[t] = __double2float_rn(qj - (double)qh4[t]);
+      hj = fma(qj, vd[t], hj);
+      nrm = fma(vd[t], vd[t], nrm);
+    }
+    *reinterpret_cast<float4 *>(hn + e) = make_float4(qh4[0], qh4[1], qh4[2], qh4[3]);
+    if (LO) *reinterpret_cast<float4 *>(ln + e) = make_float4(ql4[0], ql4[1], ql4[2], ql4[3]);
+    *reinterpret_cast<double2 *>(c.wv + voff + e) = make_double2(vd[0], vd[1]);
+    *reinterpret_cast<double2 *>(c.wv + voff + e + 2) = make_double2(vd[2], vd[3]);
+    if (c.xh != nullptr) {
+      __nv_bfloat162 x01, x23;
+      x01.x = __float2bfloat16_rn(c.dsqf[e] * vh[4 * u]);
+      x01.y = __float2bfloat16_rn(c.dsqf[e + 1] * vh[4 * u + 1]);
+      x23.x = __float2bfloat16_rn(c.dsqf[e + 2] * vh[4 * u + 2]);
+      x23.y = __float2bfloat16_rn(c.dsqf[e + 3] * vh[4 * u + 3]);
+      uint2 pk;
+      pk.x = *reinterpret_cast<uint32_t *>(&x01);
+      pk.y = *reinterpret_cast<uint32_t *>(&x23);
+      *reinterpret_cast<uint2 *>(c.xh + kblk_bf16(b, e, c.Bs)) = pk;
+    }
+    if (c.dq2_part != nullptr) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) dq = fmaf(c.d2f[e + t] * vh[4 * u + t], vh[4 * u + t], dq);
+    }
+  }
+  hj = block_sum(hj, red);
+  nrm = block_sum(nrm, red);
+  if (c.dq2_part != nullptr) dq = block_sum_f(dq, red);
+  if (threadIdx.x == 0) {
+    const size_t pi = (size_t)b * c.nchunks + chunk;
+    c.hj_part[pi] = hj;
+    c.norm_a[pi] = nrm;
+    if (c.dq2_part != nullptr) c.dq2_part[pi] = dq;
+  }
+}
+
+// Per vector: h' = Q_j^T v (fixed-order sums over chunks), the recorded
+// alpha_j = alpha~_j + h'_j - h_{j-1}, and beta_{j+1}^2 = ||v||^2 - ||h'||^2.
+// Where the projection removes more than half of ||v||^2 the vector is
+// flagged for a second pass (the CGS1K criterion) and beta waits for it.
+__global__ void __launch_bounds__(256) k_reduce_dcgs(VecCtx c, int j) {
+  __shared__ double red[256 / 32];
+  __shared__ double hprev;
+  const int b = blockIdx.x;
+  const int v = c.vec0 + b;
+  if (!live_s(c, b, j)) {
+    if (threadIdx.x == 0) {
+      c.flag2[b] = 0;
+      c.sinv[b] = 0.0;
+      c.betaj[b] = 0.0;
+    }
+    return;
+  }
+  if (threadIdx.x == 0) hprev = j >= 1 ? c.h[(size_t)b * c.kmax1 + j - 1] : 0.0;
+  __syncthreads();
+  double hh = 0.0;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    double s = 0.0;
+    if (i < j) {
+      const double *p = c.dot_part + (size_t)b * c.nchunks * c.kmax1 + i;
+      for (int ch = 0; ch < c.nchunks; ++ch) s += p[(size_t)ch * c.kmax1];
+      s -= c.gq[(size_t)b * c.kmax1 + i];   // the sweep removed Q_{j-1} g
+    } else {
+      for (int ch = 0; ch < c.nchunks; ++ch) s += c.hj_part[(size_t)b * c.nchunks + ch];
+      const size_t ai = (size_t)v * c.k + j;
+      const double a = c.alpha[ai] + s - hprev;
+      c.alpha[ai] = a;
+      c.amax[b] = fmax(c.amax[b], fabs(a));
+    }
+    c.h[(size_t)b * c.kmax1 + i] = s;
+    hh = fma(s, s, hh);
+  }
+  double nw = 0.0;
+  for (int ch = threadIdx.x; ch < c.nchunks; ch += blockDim.x)
+    nw += c.norm_a[(size_t)b * c.nchunks + ch];
+  hh = block_sum(hh, red);   // the barriers also publish amax[b]
+  nw = block_sum(nw, red);
+  if (threadIdx.x != 0) return;
+  const double rest = nw - hh;
+  const int f = rest < 0.5 * nw;
+  c.flag2[b] = f;
+  if (f) {
+    atomicAdd(c.n_second, 1);
+    return;
+  }
+  const double beta = sqrt(fmax(rest, 0.0));
+  const bool stop = !(beta > c.tol * c.amax[b]);
+  c.beta[(size_t)v * c.k + j] = beta;
+  c.betaj[b] = beta;
+  if (stop) c.k_eff[v] = j + 1;
+  c.sinv[b] = (stop || !(beta > 0.0)) ? 0.0 : 1.0 / beta;
+}
+
+// Second pass of the flagged vectors (rare: a large part of v lay in
+// span(Q_j)).  Blocks loop over the sub-batch and skip unflagged vectors.
+//  update: w' = v - Q_j h' in FP64 from the full float pair (h' need not be
+//          small here), with ||w'||^2 partials and the operand written anew;
+//  dots:   h'' = Q_j^T w' (double-float);
+//  reduce: beta_{j+1}^2 = ||w'||^2 - ||h''||^2, and h'' becomes the delayed
+//          update that the next sweep applies.
+template <bool LO>
+__global__ void __launch_bounds__(VEC_THREADS) k_p2_update_dcgs(VecCtx c, int j) {
+  extern __shared__ double hs[];   // [j + 1]
+  __shared__ double red[VEC_THREADS / 32];
+  const int chunk = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int ebase = chunk * VEC_CHUNK + wid * 256 + 4 * lane;
+  for (int b = blockIdx.y; b < c.Bs; b += gridDim.y) {
+    if (!c.flag2[b]) continue;   // uniform over the block
+    __syncthreads();             // hs of the previous vector is no longer read
+    for (int i = threadIdx.x; i <= j; i += VEC_THREADS) hs[i] = c.h[(size_t)b * c.kmax1 + i];
+    __syncthreads();
+    double r[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) r[m] = 0.0;
+    for (int i = 0; i <= j; ++i) {
+      const double hc = hs[i];
+      const float *qh = bhi_row(c, i, b);
+      const float *ql = LO ? blo_row(c, i, b) : nullptr;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = ebase + 128 * u;
+        if (e >= c.N) continue;
+        const float4 a = *reinterpret_cast<const float4 *>(qh + e);
+        const float4 al = LO ? *reinterpret_cast<const float4 *>(ql + e)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        r[4 * u] = fma(hc, (double)a.x + (double)al.x, r[4 * u]);
+        r[4 * u + 1] = fma(hc, (double)a.y + (double)al.y, r[4 * u + 1]);
+        r[4 * u + 2] = fma(hc, (double)a.z + (double)al.z, r[4 * u + 2]);
+        r[4 * u + 3] = fma(hc, (double)a.w + (double)al.w, r[4 * u + 3]);
+      }
+    }
+    const size_t voff = (size_t)b * c.N;
+    double nrm = 0.0;
+    float dq = 0.0f;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = ebase + 128 * u;
+      if (e >= c.N) continue;
+      double w4[4];
+      const double2 w0 = *reinterpret_cast<const double2 *>(c.wv + voff + e);
+      const double2 w1 = *reinterpret_cast<const double2 *>(c.wv + voff + e + 2);
+      w4[0] = w0.x - r[4 * u];
+      w4[1] = w0.y - r[4 * u + 1];
+      w4[2] = w1.x - r[4 * u + 2];
+      w4[3] = w1.y - r[4 * u + 3];
+      *reinterpret_cast<double2 *>(c.wv + voff + e) = make_double2(w4[0], w4[1]);
+      *reinterpret_cast<double2 *>(c.wv + voff + e + 2) = make_double2(w4[2], w4[3]);
+      float f4[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        nrm = fma(w4[t], w4[t], nrm);
+        f4[t] = __double2float_rn(w4[t]);
+        if (c.dq2_part != nullptr) dq = fmaf(c.d2f[e + t] * f4[t], f4[t], dq);
+      }
+      if (c.xh != nullptr) {
+        __nv_bfloat162 x01, x23;
+        x01.x = __float2bfloat16_rn(c.dsqf[e] * f4[0]);
+        x01.y = __float2bfloat16_rn(c.dsqf[e + 1] * f4[1]);
+        x23.x = __float2bfloat16_rn(c.dsqf[e + 2] * f4[2]);
+        x23.y = __float2bfloat16_rn(c.dsqf[e + 3] * f4[3]);
+        uint2 pk;
+        pk.x = *reinterpret_cast<uint32_t *>(&x01);
+        pk.y = *reinterpret_cast<uint32_t *>(&x23);
+        *reinterpret_cast<uint2 *>(c.xh + kblk_bf16(b, e, c.Bs)) = pk;
+      }
+    }
+    nrm = block_sum(nrm, red);
+    if (c.dq2_part != nullptr) dq = block_sum_f(dq, red);
+    if (threadIdx.x == 0) {
+      c.norm_b[(size_t)b * c.nchunks + chunk] = nrm;
+      if (c.dq2_part != nullptr) c.dq2_part[(size_t)b * c.nchunks + chunk] = dq;
+    }
+  }
+}
+
+template <bool LO>
+__global__ void __launch_bounds__(VEC_THREADS) k_p2_dots_dcgs(VecCtx c, int j) {
+  __shared__ float2 part[2][32][VEC_THREADS / 32];
+  const int chunk = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int ebase = chunk * VEC_CHUNK + wid * 256 + 4 * lane;
+  for (int b = blockIdx.y; b < c.Bs; b += gridDim.y) {
+    if (!c.flag2[b]) continue;   // uniform over the block
+    const size_t voff = (size_t)b * c.N;
+    float vh[8], vl[8], corr[8];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = ebase + 128 * u;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        vh[4 * u + t] = vl[4 * u + t] = corr[4 * u + t] = 0.0f;
+        if (e < c.N) {
+          const double x = c.wv[voff + e + t];
+          vh[4 * u + t] = __double2float_rn(x);
+          vl[4 * u + t] = __double2float_rn(x - (double)vh[4 * u + t]);
+        }
+      }
+    }
+    double *dp = c.dot_part + ((size_t)b * c.nchunks + chunk) * c.kmax1;
+    __syncthreads();   // the tile buffers of the previous vector are free
+    sweep_all_rows<LO, false>(c, b, j + 1, ebase, nullptr, nullptr, vh, vl, corr, corr, part,
+                              dp);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_p2_reduce_dcgs(VecCtx c, int j) {
+  __shared__ double red[256 / 32];
+  const int b = blockIdx.x;
+  const int v = c.vec0 + b;
+  if (!c.flag2[b]) return;
+  double hh = 0.0;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double *p = c.dot_part + (size_t)b * c.nchunks * c.kmax1 + i;
+    double s = 0.0;
+    for (int ch = 0; ch < c.nchunks; ++ch) s += p[(size_t)ch * c.kmax1];
+    c.h[(size_t)b * c.kmax1 + i] = s;
+    hh = fma(s, s, hh);
+  }
+  double nw = 0.0;
+  for (int ch = threadIdx.x; ch < c.nchunks; ch += blockDim.x)
+    nw += c.norm_b[(size_t)b * c.nchunks + ch];
+  hh = block_sum(hh, red);
+  nw = block_sum(nw, red);
+  if (threadIdx.x != 0) return;
+  const double beta = sqrt(fmax(nw - hh, 0.0));
+  const bool stop = !(beta > c.tol * c.amax[b]);
+  c.beta[(size_t)v * c.k + j] = beta;
+  c.betaj[b] = beta;
+  if (stop) c.k_eff[v] = j + 1;
+  c.sinv[b] = (stop || !(beta > 0.0)) ? 0.0 : 1.0 / beta;
+}
+
+void launch_sweep_dcgs(const VecCtx &c, int j, cudaStream_t st) {
+  const dim3 grid(c.nchunks, c.Bs);
+  const size_t sh = (size_t)(j > 0 ? 2 * j : 1) * sizeof(float);
+  const bool lo = c.blo != nullptr, f64u = c.uC != nullptr;
+  if (lo && f64u)
+    k_sweep_dcgs<true, true><<<grid, VEC_THREADS, sh, st>>>(c, j);
+  else if (lo)
+    k_sweep_dcgs<true, false><<<grid, VEC_THREADS, sh, st>>>(c, j);
+  else if (f64u)
+    k_sweep_dcgs<false, true><<<grid, VEC_THREADS, sh, st>>>(c, j);
+  else
+    k_sweep_dcgs<false, false><<<grid, VEC_THREADS, sh, st>>>(c, j);
+}
+void launch_reduce_dcgs(const VecCtx &c, int j, cudaStream_t st) {
+  k_reduce_dcgs<<<c.Bs, 256, 0, st>>>(c, j);
+}
+void launch_pass2_dcgs(const VecCtx &c, int j, cudaStream_t st) {
+  const dim3 grid(c.nchunks, c.Bs < 16 ? c.Bs : 16);
+  const size_t sh = (size_t)(j + 1) * sizeof(double);
+  if (c.blo != nullptr) {
+    k_p2_update_dcgs<true><<<grid, VEC_THREADS, sh, st>>>(c, j);
+    k_p2_dots_dcgs<true><<<grid, VEC_THREADS, 0, st>>>(c, j);
+  } else {
+    k_p2_update_dcgs<false><<<grid, VEC_THREADS, sh, st>>>(c, j);
+    k_p2_dots_dcgs<false><<<grid, VEC_THREADS, 0, st>>>(c, j);
+  }
+  k_p2_reduce_dcgs<<<c.Bs, 256, 0, st>>>(c, j);
 }
 
 static dim3 grid_s(const VecCtx &c) { return dim3(c.nchunks, c.Bs); }

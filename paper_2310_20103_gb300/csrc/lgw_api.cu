@@ -347,7 +347,7 @@ Opts resolve_opts(lgw_handle *h, const lgw_options *o, const SysDev &s) {
     set_err(h, LGW_ERR_ARG, "unknown precision %d", r.precision);
     throw Fail{LGW_ERR_ARG};
   }
-  if (r.reorth < LGW_REORTH_NONE || r.reorth > LGW_REORTH_CGS1K) {
+  if (r.reorth < LGW_REORTH_NONE || r.reorth > LGW_REORTH_DCGS) {
     set_err(h, LGW_ERR_ARG, "unknown reorthogonalisation mode %d", r.reorth);
     throw Fail{LGW_ERR_ARG};
   }
@@ -521,6 +521,9 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   const int kmax1 = k + 1;
   const bool reorth = o.reorth != LGW_REORTH_NONE;
   const bool split = reorth && o.split;
+  // the delayed single-sweep Gram-Schmidt runs on the split basis; with the
+  // FP64 basis the same request runs as CGS1K
+  const bool dcgs = split && o.reorth == LGW_REORTH_DCGS;
   const bool full_basis = !split && (reorth || keep_basis);
   const int nslots = full_basis ? k + 1 : 3;
 
@@ -530,7 +533,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   c.nchunks = nchunks;
   c.k = k;
   c.kmax1 = kmax1;
-  c.reorth = o.reorth;
+  c.reorth = (o.reorth == LGW_REORTH_DCGS && !dcgs) ? (int)LGW_REORTH_CGS1K : o.reorth;
   c.ring = full_basis ? 0 : 1;
   c.nslots = nslots;
   c.tol = o.tol;
@@ -575,6 +578,14 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   c.k_eff = k_eff;
   c.n_second = wsT<int>(h, "n_second", 1);
   c.status = h->d_status;
+  if (dcgs) {
+    // the carried vector lives in ring slot 0 (where the start writes q_0);
+    // FP64 contractions leave C w in the w buffer
+    c.wv = slot_ptr(c, 0);
+    c.uC = tc ? nullptr : c.w;
+    c.hj_part = wsT<double>(h, "hj_part", (size_t)Bs * nchunks);
+    c.gq = wsT<double>(h, "gq", (size_t)Bs * kmax1);
+  }
   LGW_TRY_CUDA(h, cudaMemsetAsync(c.n_second, 0, sizeof(int), st));
   LGW_TRY_CUDA(h, cudaMemsetAsync(c.flag2, 0, sizeof(int) * Bs, st));
 
@@ -760,8 +771,11 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
             }
           }
         } else if (tc) {
+          // the delayed Gram-Schmidt contracts the unnormalised carried
+          // vector; 1/beta_j is applied to each column of the reduction
+          const double *vscale = dcgs ? c.sinv : nullptr;
           if (fp8) {
-            launch_quant_x8(c.xh, Bs, N, x8, sx, st);
+            launch_quant_x8(c.xh, Bs, N, x8, sx, st, vscale);
             check_launch(h, "quant_x8");
           }
           launch_gemm1_tc(plan, h->d_status, st);
@@ -769,7 +783,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
           if (fp8)
             launch_reduce_y_fp8(Yp32, splits_tc, Bs, s.A, sx, s.sL, y8, ty, yy, c.n_yb, st);
           else
-            launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, yy, st);
+            launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, yy, st, vscale);
           check_launch(h, "reduce_y");
           tm.mark(C_GEMM2);
           if (split) {
@@ -786,6 +800,16 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
                             st);
           }
           check_launch(h, tc_plain ? "assemble_w" : "gemm2_tc");
+        } else if (dcgs) {
+          // C w_{j-1} in FP64 with the partials of w . C w (alpha~ after
+          // scaling by 1/beta_j^2)
+          launch_gemm1_f64(s, c.wv, Bs, Yp64, splits64, st);
+          check_launch(h, "gemm1_f64");
+          launch_reduce_y_f64(Yp64, splits64, Bs, s.A, Y64, st);
+          check_launch(h, "reduce_y_f64");
+          tm.mark(C_GEMM2);
+          launch_gemm2_f64(s, Y64, Bs, EPI_APPLY, c.wv, nullptr, nullptr, c.w, c.alpha_part, st);
+          check_launch(h, "gemm2_f64");
         } else {
           launch_gemm1_f64(s, qj, Bs, Yp64, splits64, st);
           check_launch(h, "gemm1_f64");
@@ -797,6 +821,19 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
         }
         // ---- recurrence and reorthogonalisation ----
         tm.mark(C_DOTS);
+        if (dcgs) {
+          // one sweep over the basis: delayed update of q_j, w_j and its
+          // projection coefficients; then beta_{j+1}, and the rare second pass
+          launch_sweep_dcgs(c, j, st);
+          check_launch(h, "sweep_dcgs");
+          tm.mark(C_UPDATE);
+          launch_reduce_dcgs(c, j, st);
+          check_launch(h, "reduce_dcgs");
+          tm.mark(C_PASS2);
+          launch_pass2_dcgs(c, j, st);
+          check_launch(h, "pass2_dcgs");
+          continue;
+        }
         if (split) {
           launch_dots_split(c, j, 1, st);
           check_launch(h, "dots_split");

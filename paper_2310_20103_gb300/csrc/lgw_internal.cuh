@@ -96,6 +96,11 @@ struct VecCtx {
   int *k_eff;             // global [B]
   int *n_second;          // counter of second passes
   unsigned *status;
+  // delayed Gram-Schmidt (LGW_REORTH_DCGS)
+  double *wv;             // [Bs][N] the carried vector w_j (unnormalised q~_{j+1} = w_j / beta_{j+1})
+  const double *uC;       // [Bs][N] C w_j from the FP64 contractions, or null (tensor cores)
+  double *hj_part;        // [Bs][nchunks] partials of q_j . w_j
+  double *gq;             // [Bs][kmax1] g = (T_{j-1} - alpha~_j) h / beta_j, removed by the sweep
 };
 
 // K-block-major layout of the GEMM1 operands (L^T and the per-step X):
@@ -185,6 +190,7 @@ void launch_reduce_y_f64(const double *Ypart, int splits, int Bs, int A, double 
 // U[b][vc] = sum_mu Y[b][mu] L[vc][mu]; epilogue:
 //   EPI_START:   w = Delta^1/2 U
 //   EPI_LANCZOS: w = Delta^2 q + c_K Delta^1/2 U - beta_j q_prev; alpha partials per 64-row tile
+//   EPI_APPLY:   w = C q = Delta^2 q + c_K Delta^1/2 U; q . w partials per tile if alpha_part
 enum { EPI_START = 0, EPI_LANCZOS = 1, EPI_APPLY = 2 };
 void launch_gemm2_f64(const SysDev &s, const double *Y, int Bs, int epi, const double *q,
                       const double *qprev, const double *betaj, double *w, double *alpha_part,
@@ -197,8 +203,10 @@ bool tc_plan_enable_fp8(TcPlan *p, const uint8_t *L8t, const uint8_t *L8, const 
                         const uint8_t *y8, const float *ty);
 void launch_prepare_fp8(const double *src, int ld, int nr, int nc, const SysDev &s,
                         unsigned *colmax, uint8_t *L8, uint8_t *L8t, float *sL, cudaStream_t st);
+// vscale (optional, [Bs]): normalisation factor of an unnormalised operand,
+// folded into sx
 void launch_quant_x8(const __nv_bfloat16 *xh, int Bs, int N, uint8_t *x8, float *sx,
-                     cudaStream_t st);
+                     cudaStream_t st, const double *vscale = nullptr);
 void launch_reduce_y_fp8(const float *Ypart, int splits, int Bs, int A, const float *sx,
                          const float *sL, uint8_t *y8, float *ty, float *yy, int n_yb,
                          cudaStream_t st);
@@ -210,8 +218,10 @@ void tc_plan_destroy(TcPlan *p);
 void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st);
 // Yh = bf16(sum of split partials); yy (optional, [Bs][A/256]) receives
 // per-block partials of sum_mu y_mu * Yh_mu for the alpha estimate.
+// vscale (optional, [Bs]) multiplies each vector's sum before rounding: the
+// normalisation of an operand that was contracted unnormalised.
 void launch_reduce_y_bf16(const float *Ypart, int splits, int Bs, int A, __nv_bfloat16 *Yh,
-                          float *yy, cudaStream_t st);
+                          float *yy, cudaStream_t st, const double *vscale = nullptr);
 void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qprev,
                      const double *betaj, double *w, double *alpha_part, unsigned *status,
                      cudaStream_t st);
@@ -244,6 +254,11 @@ void launch_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_reduce_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_update_split(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_start_split(const VecCtx &c, cudaStream_t st);
+// delayed Gram-Schmidt: one sweep over the basis per step, its per-vector
+// reduction, and the second pass of the vectors the reduction flags
+void launch_sweep_dcgs(const VecCtx &c, int j, cudaStream_t st);
+void launch_reduce_dcgs(const VecCtx &c, int j, cudaStream_t st);
+void launch_pass2_dcgs(const VecCtx &c, int j, cudaStream_t st);
 void launch_scale_rows_to_bf16(const double *x, const double *dsq, int Bs, int N,
                                __nv_bfloat16 *out, cudaStream_t st);
 

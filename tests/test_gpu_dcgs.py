@@ -1,0 +1,213 @@
+"""GPU parity of the delayed single-sweep Gram-Schmidt (reorth="dcgs").
+
+The delayed schedule forms q_j inside the step after the one that computed
+its projection coefficients, and the contractions run on the not yet
+orthogonalised vector; every difference from the exact recurrence lies in
+span(Q_j) and is removed by the projection (Eq. 13 with full
+reorthogonalisation).  So the recurrence must give the same tridiagonals
+as classical Gram-Schmidt, and every result is held to the bars of the
+other reorthogonalisation modes:
+
+  * FP64 contractions (split basis) vs the oracle's CGS2 Lanczos: 1e-9 on
+    Sigma (relative, per target) and E_qp; 1e-8 on Z;
+  * k = N_vc vs the closed form (Eq. 7-9): 1e-9;
+  * float-only basis: 1e-6 on Sigma, 1e-8 eV on E_qp (as split32 CGS);
+  * BF16 / E4M3 contractions: 1 meV on E_qp;
+  * graph replay bit-identical to eager launches;
+  * an exact breakdown (invariant subspace) stops at the right depth, through
+    the second-pass kernels.
+"""
+import numpy as np
+import pytest
+
+import gw_inputs as gi
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2310_20103_gb300.build import build
+    build()
+    from paper_2310_20103_gb300 import lgw
+    return lgw
+
+
+@pytest.fixture(scope="module")
+def handle(L):
+    h = L.lgw_create(0)
+    yield h
+    L.lgw_destroy(h)
+
+
+def _t(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def _problem(L, wl):
+    return L.Problem(targets=_t(wl.targets), m_idx=_t(wl.m_idx), omega=_t(wl.omega),
+                     delta=wl.delta, M=_t(wl.M))
+
+
+def _run(L, h, wl, opts, report=False):
+    s = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, _t(wl.eps), _t(wl.L),
+                             wl.kernel_factor)
+    try:
+        sig = torch.empty(wl.n_t, wl.omega.size, 2, dtype=torch.float64, device=DEV)
+        e = torch.empty(wl.n_t, dtype=torch.float64, device=DEV)
+        z = torch.empty(wl.n_t, dtype=torch.float64, device=DEV)
+        rep = L.lgw_sigma_c(h, s, _problem(L, wl), opts, sig, e, z, report=report)
+        torch.cuda.synchronize()
+    finally:
+        L.lgw_release_system(s)
+    sg = sig.cpu().numpy()
+    return sg[..., 0] + 1j * sg[..., 1], e.cpu().numpy(), z.cpu().numpy(), rep
+
+
+def _coeffs(L, h, wl, opts, prob=None):
+    s = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, _t(wl.eps), _t(wl.L),
+                             wl.kernel_factor)
+    B = wl.n_t * wl.n_m
+    al = torch.empty(B, opts.k, dtype=torch.float64, device=DEV)
+    be = torch.empty_like(al)
+    b0 = torch.empty(B, dtype=torch.float64, device=DEV)
+    ke = torch.empty(B, dtype=torch.int32, device=DEV)
+    L.lgw_lanczos_coeffs(h, s, prob if prob is not None else _problem(L, wl), opts, al, be, b0,
+                         ke)
+    torch.cuda.synchronize()
+    L.lgw_release_system(s)
+    return al.cpu().numpy(), be.cpu().numpy(), b0.cpu().numpy(), ke.cpu().numpy()
+
+
+def _rel(a, b):
+    return max(np.abs(a[i] - b[i]).max() / np.abs(b[i]).max() for i in range(a.shape[0]))
+
+
+@pytest.fixture(scope="module")
+def tiny_ref():
+    wl = gi.tiny()
+    sig64, poles64, co64 = O.sigma_lanczos(wl, k=64)
+    E64, Z64 = O.solve_all_qp(wl, poles64)
+    sigx, polesx = O.sigma_closed_form(wl)
+    Ex, Zx = O.solve_all_qp(wl, polesx)
+    return wl, (sig64, E64, Z64, co64), (sigx, Ex, Zx)
+
+
+def test_fp64_contractions_vs_oracle(L, handle, tiny_ref):
+    wl, (sig64, E64, Z64, co64), _ = tiny_ref
+    sig, e, z, rep = _run(L, handle, wl, L.Options(k=64, precision="fp64", reorth="dcgs",
+                                                   reorth_arith="split"), report=True)
+    assert _rel(sig, sig64) < 1e-9
+    assert np.all(np.abs(e - E64) <= 1e-9 * np.maximum(1, np.abs(E64)))
+    assert np.all(np.abs(z - Z64) <= 1e-8)
+    a, b, b0, ke = _coeffs(L, handle, wl, L.Options(k=64, precision="fp64", reorth="dcgs",
+                                                    reorth_arith="split"))
+    np.testing.assert_allclose(a, co64[0], rtol=1e-9)
+    np.testing.assert_allclose(b, co64[1], rtol=1e-7)
+    assert np.array_equal(ke, co64[3])
+
+
+def test_full_space_vs_closed_form(L, handle, tiny_ref):
+    """k = N_vc: the Krylov space is exhausted, Gauss nodes are the Casida
+    eigenvalues and the result is the closed form."""
+    wl, _, (sigx, Ex, _) = tiny_ref
+    sig, e, _, _ = _run(L, handle, wl, L.Options(k=wl.n_vc, precision="fp64", reorth="dcgs",
+                                                 reorth_arith="split"))
+    assert _rel(sig, sigx) < 1e-9
+    assert np.all(np.abs(e - Ex) <= 1e-9 * np.maximum(1, np.abs(Ex)))
+
+
+def test_float_basis(L, handle, tiny_ref):
+    wl, (sig64, E64, _, _), _ = tiny_ref
+    sig, e, _, _ = _run(L, handle, wl, L.Options(k=64, precision="fp64", reorth="dcgs",
+                                                 reorth_arith="split32"))
+    assert _rel(sig, sig64) < 1e-6
+    assert np.abs(e - E64).max() < 1e-8
+
+
+@pytest.mark.parametrize("prec,bar", [("bf16", 1e-3), ("fp8", 1e-3)])
+def test_tensor_core_within_1meV(L, handle, tiny_ref, prec, bar):
+    wl, _, (sigx, Ex, _) = tiny_ref
+    for arith in ("auto", "split32"):
+        _, e, _, _ = _run(L, handle, wl, L.Options(k=64, precision=prec, reorth="dcgs",
+                                                   reorth_arith=arith))
+        assert np.abs(e - Ex).max() < bar
+    sigf, ef, _, _ = _run(L, handle, wl, L.Options(k=wl.n_vc, precision=prec, reorth="dcgs"))
+    assert np.abs(ef - Ex).max() < bar
+    if prec == "bf16":
+        assert _rel(sigf, sigx) < 1e-2
+
+
+def test_mid_ragged(L, handle):
+    """Several 2048-element chunks with a ragged tail (N_vc = 13*347), two
+    sub-batches, more than 32 basis rows (several row tiles of the sweep)."""
+    wl = gi.make_workload("m", 13, 347, 300, [11, 12, 13], list(range(21)), 120, 2, k=40,
+                          aux_scaled=True)
+    ref, poles, co = O.sigma_lanczos(wl, k=40)
+    Er, _ = O.solve_all_qp(wl, poles)
+    sig, e, _, rep = _run(L, handle, wl, L.Options(k=40, precision="fp64", b_sub=32,
+                                                   reorth="dcgs", reorth_arith="split"),
+                          report=True)
+    assert rep["n_sub_batches"] == 2
+    assert _rel(sig, ref) < 1e-9
+    assert np.abs(e - Er).max() < 1e-9
+    for arith in ("auto", "split32"):
+        _, eb, _, _ = _run(L, handle, wl, L.Options(k=40, precision="bf16", reorth="dcgs",
+                                                    reorth_arith=arith))
+        assert np.abs(eb - Er).max() < 1e-3
+
+
+def test_matches_cgs1k_bf16(L, handle):
+    """Same BF16 contractions, delayed vs two-pass Gram-Schmidt: the QP
+    energies agree far below 1 meV (both are the FP64-grade projection of
+    the same BF16 operator)."""
+    wl = gi.make_workload("c", 16, 160, 256, [14, 15, 16, 17], list(range(48)), 200, 7, k=80,
+                          aux_scaled=True)
+    _, e1, _, _ = _run(L, handle, wl, L.Options(k=80, precision="bf16", reorth="cgs1k"))
+    _, e2, _, _ = _run(L, handle, wl, L.Options(k=80, precision="bf16", reorth="dcgs"))
+    assert np.abs(e1 - e2).max() < 1e-6
+
+
+def test_breakdown_through_second_pass(L, handle):
+    """c_K = 0 makes C diagonal; a coupling vector with three nonzeros spans
+    a 3-dimensional Krylov space.  At step 2 the recurred vector is pure
+    rounding, mostly inside span(Q): the reduction flags it, the second pass
+    runs, and the recurrence stops at k_eff = 3 with the exact result."""
+    wl = gi.make_workload("b", 3, 5, 6, [1], [0, 4], 41, 12, k=8, kernel_factor=0.0)
+    V = np.zeros((1, 2, wl.n_vc))
+    V[0, 0, [0, 4, 9]] = [0.3, -0.2, 0.5]
+    V[0, 1, [1, 7, 14]] = [0.1, 0.4, -0.3]
+    prob = L.Problem(targets=_t(wl.targets), m_idx=_t(wl.m_idx), omega=_t(wl.omega),
+                     delta=wl.delta, V=_t(V))
+    opts = L.Options(k=8, precision="fp64", reorth="dcgs", reorth_arith="split")
+    a, b, b0, ke = _coeffs(L, handle, wl, opts, prob)
+    assert list(ke) == [3, 3]
+    Delta = O.pair_energies(wl.eps, wl.n_v)
+    s = L.lgw_prepare_system(handle, wl.n_v, wl.n_c, wl.n_aux, _t(wl.eps), _t(wl.L), 0.0)
+    sig = torch.empty(1, wl.omega.size, 2, dtype=torch.float64, device=DEV)
+    e = torch.empty(1, dtype=torch.float64, device=DEV)
+    L.lgw_sigma_c(handle, s, prob, opts, sig, e)
+    torch.cuda.synchronize()
+    L.lgw_release_system(s)
+    ref = np.zeros(wl.omega.size, complex)
+    for mi, m in enumerate(wl.m_idx):
+        eta = 1.0 if m < wl.n_v else -1.0
+        z = wl.omega - wl.eps[m] - 1j * eta * wl.delta
+        ref += np.sum(V[0, mi][None, :] ** 2 / (z[:, None] + eta * Delta[None, :]), axis=1)
+    sg = sig.cpu().numpy()[0]
+    assert np.abs(sg[:, 0] + 1j * sg[:, 1] - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_graph_replay_bit_identical(L, handle):
+    wl = gi.make_workload("g", 8, 64, 128, [6, 7, 8], list(range(24)), 100, 3, k=30,
+                          aux_scaled=True)
+    for prec in ("bf16", "fp64"):
+        eager = _run(L, handle, wl, L.Options(k=30, precision=prec, reorth="dcgs",
+                                              reorth_arith="split"))
+        graph = _run(L, handle, wl, L.Options(k=30, precision=prec, reorth="dcgs",
+                                              reorth_arith="split", use_graph=1))
+        assert np.array_equal(eager[0], graph[0])
+        assert np.array_equal(eager[1], graph[1])

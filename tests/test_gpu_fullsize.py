@@ -2,16 +2,19 @@
 
 Mid-size system (N_v=128, N_c=1024: N_vc=131072, N_aux=2048), k=200,
 targets HOMO-15 and HOMO-14 summed over 256 orbitals each (512 start
-vectors, one sub-batch), BF16 contractions with the split-precision CGS1K
-reorthogonalisation -- exactly one benchmark step.  The oracle cannot redo
-all 512 recurrences in a test, so:
+vectors, one sub-batch), BF16 contractions with the split-precision
+reorthogonalisation -- exactly one benchmark step, with the delayed
+single-sweep Gram-Schmidt the benchmark times (dcgs) and with the two-pass
+CGS1K.  The oracle cannot redo all 512 recurrences in a test, so:
 
   1. sampled start vectors are re-run from scratch by the oracle (FP64 L,
      CGS2) and their self-energy contributions compared in meV;
   2. the spectral map, continued fractions and QP solve at full size are
      checked against oracle pole sums built from the GPU's own 512
      tridiagonals (FP64 on both sides: 1e-9);
-  3. the FP64 GPU path on the sampled vectors matches the oracle at 1e-9.
+  3. the FP64 GPU path on the sampled vectors matches the oracle at 1e-9;
+  4. the two Gram-Schmidt schedules give the same QP energies far below
+     1 meV.
 """
 import numpy as np
 import pytest
@@ -29,6 +32,9 @@ def _t(x):
     return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
 
 
+REORTHS = ("dcgs", "cgs1k")
+
+
 @pytest.fixture(scope="module")
 def full():
     from paper_2310_20103_gb300.build import build
@@ -39,24 +45,30 @@ def full():
     s = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, _t(wl.eps), _t(wl.L))
     prob = L.Problem(targets=_t(wl.targets), m_idx=_t(wl.m_idx), omega=_t(wl.omega),
                      delta=wl.delta, M=_t(wl.M))
-    opts = L.Options(k=200, precision="bf16", reorth="cgs1k", b_sub=512)
     B = wl.n_t * wl.n_m
-    al = torch.empty(B, 200, dtype=torch.float64, device=DEV)
-    be = torch.empty_like(al)
-    b0 = torch.empty(B, dtype=torch.float64, device=DEV)
-    ke = torch.empty(B, dtype=torch.int32, device=DEV)
-    L.lgw_lanczos_coeffs(h, s, prob, opts, al, be, b0, ke)
-    sig = torch.empty(wl.n_t, wl.omega.size, 2, dtype=torch.float64, device=DEV)
-    e = torch.empty(wl.n_t, dtype=torch.float64, device=DEV)
-    L.lgw_sigma_c(h, s, prob, opts, sig, e)
-    torch.cuda.synchronize()
-    out = dict(wl=wl, L=L, h=h, s=s,
-               coeffs=(al.cpu().numpy(), be.cpu().numpy(), b0.cpu().numpy(),
-                       ke.cpu().numpy().astype(np.int64)),
-               sig=sig.cpu().numpy(), e=e.cpu().numpy())
+    out = dict(wl=wl, L=L, h=h, s=s)
+    for reorth in REORTHS:
+        opts = L.Options(k=200, precision="bf16", reorth=reorth, b_sub=512)
+        al = torch.empty(B, 200, dtype=torch.float64, device=DEV)
+        be = torch.empty_like(al)
+        b0 = torch.empty(B, dtype=torch.float64, device=DEV)
+        ke = torch.empty(B, dtype=torch.int32, device=DEV)
+        L.lgw_lanczos_coeffs(h, s, prob, opts, al, be, b0, ke)
+        sig = torch.empty(wl.n_t, wl.omega.size, 2, dtype=torch.float64, device=DEV)
+        e = torch.empty(wl.n_t, dtype=torch.float64, device=DEV)
+        L.lgw_sigma_c(h, s, prob, opts, sig, e)
+        torch.cuda.synchronize()
+        out[reorth] = dict(coeffs=(al.cpu().numpy(), be.cpu().numpy(), b0.cpu().numpy(),
+                                   ke.cpu().numpy().astype(np.int64)),
+                           sig=sig.cpu().numpy(), e=e.cpu().numpy())
     yield out
     L.lgw_release_system(s)
     L.lgw_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def oracle_sample(full):
+    return _oracle_sample(full["wl"], SAMPLE)
 
 
 def _sigma_tm(wl, v, coeffs, row=None):
@@ -78,10 +90,11 @@ def _oracle_sample(wl, vs, k=200):
                      b[vs], k)
 
 
-def test_spectral_cf_qp_at_full_size(full):
+@pytest.mark.parametrize("reorth", REORTHS)
+def test_spectral_cf_qp_at_full_size(full, reorth):
     """GPU Sigma_t(omega) and E_qp equal the oracle's pole sums and QP solve
     on the GPU's own 512 tridiagonals (FP64 both sides)."""
-    wl, co = full["wl"], full["coeffs"]
+    wl, co = full["wl"], full[reorth]["coeffs"]
     poles = []
     for ti in range(wl.n_t):
         P, Wt, E = [], [], []
@@ -95,21 +108,22 @@ def test_spectral_cf_qp_at_full_size(full):
             E.append(np.full(Om.size, eta))
         poles.append((np.concatenate(P), np.concatenate(Wt), np.concatenate(E)))
     ref = np.stack([O.sigma_from_poles(wl.omega, *poles[ti], wl.delta) for ti in range(wl.n_t)])
-    got = full["sig"][..., 0] + 1j * full["sig"][..., 1]
+    got = full[reorth]["sig"][..., 0] + 1j * full[reorth]["sig"][..., 1]
     for ti in range(wl.n_t):
         assert np.abs(got[ti] - ref[ti]).max() <= 1e-9 * np.abs(ref[ti]).max()
     Eref, _ = O.solve_all_qp(wl, poles)
-    assert np.all(np.abs(full["e"] - Eref) <= 1e-9 * np.maximum(1.0, np.abs(Eref)))
+    assert np.all(np.abs(full[reorth]["e"] - Eref) <= 1e-9 * np.maximum(1.0, np.abs(Eref)))
     assert np.all(co[3] == 200)
 
 
-def test_sampled_vectors_bf16_vs_oracle(full):
+@pytest.mark.parametrize("reorth", REORTHS)
+def test_sampled_vectors_bf16_vs_oracle(full, oracle_sample, reorth):
     """Each sampled start vector's contribution Sigma_tm(omega) from the
     BF16 path against the oracle's FP64 recurrence, in meV; and the QP
     energy of a target differs from the FP64 reference by far less than
     1 meV (checked through the per-vector contributions: 256 of them add)."""
-    wl, co = full["wl"], full["coeffs"]
-    ref = _oracle_sample(wl, SAMPLE)
+    wl, co = full["wl"], full[reorth]["coeffs"]
+    ref = oracle_sample
     for i, v in enumerate(SAMPLE):
         g = _sigma_tm(wl, v, co)
         r = _sigma_tm(wl, v, ref, row=i)
@@ -119,12 +133,20 @@ def test_sampled_vectors_bf16_vs_oracle(full):
         assert err_mev <= 1.0 / wl.n_m      # 256 contributions stay within 1 meV in total
 
 
-def test_sampled_vectors_fp64_path(full):
+def test_schedules_agree_on_qp(full):
+    """Delayed single-sweep vs two-pass Gram-Schmidt on the same BF16
+    contractions: E_qp within 1e-3 meV, Sigma within 1e-3 meV."""
+    a, b = full["dcgs"], full["cgs1k"]
+    assert np.abs(a["e"] - b["e"]).max() * 1e3 < 1e-3
+    assert np.abs(a["sig"] - b["sig"]).max() * 1e3 < 1e-3
+
+
+def test_sampled_vectors_fp64_path(full, oracle_sample):
     """The plain FP64 GPU path on the sampled vectors matches the oracle at
     1e-9 relative (each vector is its own problem: one target, one m)."""
     wl, L, h, s = full["wl"], full["L"], full["h"], full["s"]
     vs = SAMPLE[:3]
-    ref = _oracle_sample(wl, vs)
+    ref = oracle_sample
     for i, v in enumerate(vs):
         ti, mi = divmod(v, wl.n_m)
         prob = L.Problem(targets=_t(wl.targets[ti:ti + 1]), m_idx=_t(wl.m_idx[mi:mi + 1]),
