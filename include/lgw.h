@@ -30,7 +30,8 @@
  *   - The caller owns every buffer it passes; no call keeps a caller pointer
  *     after it returns.  A system owns its own copies of eps, Delta and L.
  *     A handle owns the device workspace (Krylov basis, vector blocks) and
- *     grows it on demand; it is freed by lgw_destroy.
+ *     grows it on demand; it is freed by lgw_destroy or
+ *     lgw_release_workspace, and lgw_set_workspace_limit caps it.
  *   - Errors are return codes; nothing aborts and no exception crosses the
  *     ABI.  Device-side failures (non-positive Gauss nodes, a bounded wait
  *     that ran out) are collected in a device status word read at the end of
@@ -251,6 +252,31 @@ lgw_status lgw_destroy(lgw_handle *h);
  * n bytes).  Returns the last error code. */
 lgw_status lgw_last_error(lgw_handle *h, char *buf, size_t n);
 
+/* Workspace budget (the paper has no counterpart; a service for callers that
+ * share a GPU).  lgw_set_workspace_limit caps the device bytes the handle's
+ * workspace may hold (0: no cap, the default).  A call whose next
+ * workspace allocation would pass the cap returns LGW_ERR_OOM before that
+ * allocation; nothing already held is freed and the handle stays usable
+ * (work queued earlier in the call completes on valid buffers).  A failed
+ * cudaMalloc gives LGW_ERR_OOM the same way.  lgw_workspace_bytes reports
+ * the bytes held; lgw_release_workspace waits for the handle's stream and
+ * frees the whole workspace (later calls allocate it again). */
+lgw_status lgw_set_workspace_limit(lgw_handle *h, size_t bytes);
+lgw_status lgw_workspace_bytes(lgw_handle *h, size_t *bytes);
+lgw_status lgw_release_workspace(lgw_handle *h);
+
+/* Diagnostic of the bounded device waits (the paper has no counterpart).
+ * Every wait of the library's kernels on an mbarrier phase (the tensor-core
+ * pipeline's TMA and MMA hand-offs) gives up after a cycle limit, sets a
+ * timeout bit in the handle's status word and lets the kernel finish, so
+ * the context stays usable and the call returns LGW_ERR_TIMEOUT.  This call
+ * runs that same wait once, in one small kernel, with a limit of `seconds`
+ * (1e-4 .. 2): with arrive != 0 another thread completes the barrier first
+ * and the call returns LGW_OK; with arrive == 0 nothing ever completes it,
+ * the wait runs out and the call returns LGW_ERR_TIMEOUT.  No copy or other
+ * asynchronous operation is in flight during the wait.  Synchronous. */
+lgw_status lgw_selftest_bounded_wait(lgw_handle *h, int32_t arrive, double seconds);
+
 /* Build a system: copies eps to the device, forms Delta_vc, Delta^1/2 and
  * Delta^2 (Eq. 2-4), and makes the copies of L that desc->flags asks for,
  * each padded to [N_pad][A_pad]: FP64, BF16 (L, L^T and the low half
@@ -309,11 +335,28 @@ lgw_status lgw_sigma_c(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
  * Sigma_tm(omega) = (1/z) <P|D^-1 - (D + eta z)^-1|P> from two Haydock
  * continued fractions of D's tridiagonal (Eq. 14), z = omega - eps_m - i eta
  * delta.  Outputs as lgw_sigma_c; the report's gemm_flops count g products
- * per step. */
+ * per step.  x_lo = x_hi = 0 asks the library for the interval
+ * (lgw_spectral_interval with k = 32, one extra synchronisation). */
 typedef struct {
   int32_t g;           /* degree, 1..256 */
-  double x_lo, x_hi;   /* 0 < x_lo < x_hi */
+  double x_lo, x_hi;   /* 0 < x_lo < x_hi, or both 0 */
 } lgw_poly;
+
+/* Interval [x_lo, x_hi] around the spectrum of C for the polynomial fit
+ * (the text after Eq. 12 fits p_g on the range of C's eigenvalues):
+ *   x_lo = min over pairs of Delta^2 = (eps_c - eps_v)^2, a lower bound of
+ *          lambda_min because C = Delta^2 + c_K Delta^1/2 L L^T Delta^1/2
+ *          adds a positive semidefinite term;
+ *   x_hi = the largest Ritz value of k Lanczos steps (Eq. 13, CGS2; FP64
+ *          contractions when the system keeps its FP64 copy, else BF16)
+ *          from a fixed pseudo-random start vector, plus that step's beta,
+ *          the residual norm, which bounds the distance from the Ritz value
+ *          to an eigenvalue of C.  The largest Ritz value converges to
+ *          lambda_max from below first; x_hi is an estimate, not a bound.
+ * Host outputs; synchronous.  LGW_ERR_NOT_SPD if the estimate is not a
+ * positive interval. */
+lgw_status lgw_spectral_interval(lgw_handle *h, const lgw_system *s, int32_t k, double *x_lo,
+                                 double *x_hi);
 
 lgw_status lgw_sigma_c_poly(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
                             const lgw_options *o, const lgw_poly *poly, double *sigma,

@@ -78,17 +78,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait on a barrier phase; false (and ST_TIMEOUT) after ~1 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *status) {
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait on a barrier phase: false (and ST_TIMEOUT in *status) once
+// `limit` clock cycles have passed without the phase completing.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, unsigned *status,
+                                              long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (clock64() - t0 > WAIT_CYCLES) {
+    if (clock64() - t0 > limit) {
       atomicOr(status, ST_TIMEOUT);
       return false;
     }
   }
+}
+// The pipeline's waits: ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *status) {
+  return mbar_wait_for(bar, parity, status, WAIT_CYCLES);
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, uint64_t *bar, int x,
                                             int y) {
@@ -453,7 +465,28 @@ __global__ void k_reduce_y_bf16(const float *__restrict__ Ypart, int splits, int
   }
 }
 
+// Diagnostic of the bounded wait: thread 0 waits on a fresh barrier with
+// the given limit; with `arrive`, thread 1 completes the barrier's phase
+// first, otherwise nothing does and the wait must run out and set
+// ST_TIMEOUT.  No asynchronous copy references the barrier.
+__global__ void k_wait_selftest(int arrive, long long limit, unsigned *status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 1) mbar_arrive(&bar);
+  if (threadIdx.x == 0) mbar_wait_for(&bar, 0, status, limit);
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_inval(&bar);
+}
+
 }  // namespace tc
+
+void launch_wait_selftest(int arrive, long long limit_cycles, unsigned *status, cudaStream_t st) {
+  tc::k_wait_selftest<<<1, 32, 0, st>>>(arrive, limit_cycles, status);
+}
 
 // ---------------------------------------------------------------------------
 // Host side

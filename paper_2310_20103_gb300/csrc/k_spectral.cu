@@ -310,4 +310,86 @@ void launch_spectral_impl(const double *alpha, const double *beta, const double 
                                                               warps, jb, min_theta_bits, status);
   (void)scratch;
 }
+
+// ---------------------------------------------------------------------------
+// Spectral interval of C for the polynomial form (text after Eq. 12: p_g is
+// fitted on the range of C's eigenvalues).
+// ---------------------------------------------------------------------------
+// Start vector with entries uniform in [-1, 1) from a counter-based hash
+// (splitmix64 of seed + index), zero in the padding.
+__global__ void k_hash_vector(double *v, int n_vc, int N, unsigned long long seed) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  if (e >= n_vc) {
+    v[e] = 0.0;
+    return;
+  }
+  unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(e + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  v[e] = (double)(z >> 11) * 0x1p-52 - 1.0;
+}
+
+// Number of eigenvalues of the tridiagonal (a, b) below x (Sturm count by
+// the LDL^T pivots, zero pivots nudged off zero).
+__device__ int sturm_below(const double *a, const double *b, int n, double x, double pivmin) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < n; ++i) {
+    const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+    d = a[i] - x - (i > 0 ? bb / d : 0.0);
+    if (fabs(d) < pivmin) d = -pivmin;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// One block: out[0] = min over the pairs of Delta^2 (C = Delta^2 + a positive
+// semidefinite term, so no eigenvalue lies below it); out[1] = the largest
+// Ritz value of the k-step tridiagonal (a, b) plus the last off-diagonal
+// b_k = ||C q_k - ...||, the residual norm that bounds how far the Ritz value
+// can lie from an eigenvalue.
+__global__ void k_interval(const double *__restrict__ Delta2, int n_vc, const double *a,
+                           const double *b, const int *k_eff, double *out) {
+  __shared__ double red[256];
+  double m = 1e300;
+  for (int e = threadIdx.x; e < n_vc; e += blockDim.x) m = fmin(m, Delta2[e]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const int n = *k_eff;
+  double hi = 0.0;
+  if (n > 0) {
+    double glo = 1e300, ghi = -1e300, scale = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0);
+      glo = fmin(glo, a[i] - r);
+      ghi = fmax(ghi, a[i] + r);
+      scale = fmax(scale, fabs(a[i]) + r);
+    }
+    const double pivmin = 1e-300 + 1e-15 * scale * 1e-15;
+    double lo = glo, up = ghi;   // the largest eigenvalue lies in (lo, up]
+    for (int it = 0; it < 200 && up - lo > 1e-14 * scale; ++it) {
+      const double mid = 0.5 * (lo + up);
+      if (sturm_below(a, b, n, mid, pivmin) >= n) up = mid; else lo = mid;
+    }
+    hi = up + (n - 1 < 0 ? 0.0 : fabs(b[n - 1]));
+  }
+  out[0] = red[0];
+  out[1] = hi;
+}
+
+void launch_interval(const double *Delta2, int n_vc, int N, const double *a, const double *b,
+                     const int *k_eff, double *out, double *vec, unsigned long long seed,
+                     bool make_vector, cudaStream_t st) {
+  if (make_vector)
+    k_hash_vector<<<(N + 255) / 256, 256, 0, st>>>(vec, n_vc, N, seed);
+  else
+    k_interval<<<1, 256, 0, st>>>(Delta2, n_vc, a, b, k_eff, out);
+}
 }  // namespace lgw

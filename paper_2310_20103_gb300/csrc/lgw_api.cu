@@ -26,6 +26,8 @@ struct lgw_handle {
     size_t n = 0;
   };
   std::map<std::string, Buf> bufs;
+  size_t ws_limit = 0;   // bytes the workspace may hold (0: no limit)
+  size_t ws_bytes = 0;   // bytes it holds
   int launches = 0;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -104,9 +106,18 @@ void *ws(lgw_handle *h, const std::string &name, size_t bytes) {
   auto &b = h->bufs[h->ws_prefix + name];
   if (bytes == 0) bytes = 8;
   if (b.n < bytes) {
+    // the handle's byte limit is checked before anything is freed, so a
+    // refused request leaves the workspace as it was
+    if (h->ws_limit && h->ws_bytes - b.n + bytes > h->ws_limit) {
+      set_err(h, LGW_ERR_OOM,
+              "workspace limit: %s needs %zu bytes, the handle holds %zu of its %zu-byte limit",
+              name.c_str(), bytes, h->ws_bytes, h->ws_limit);
+      throw Fail{LGW_ERR_OOM};
+    }
     if (b.p) {
       LGW_TRY_CUDA(h, cudaStreamSynchronize(h->stream));
       cudaFree(b.p);
+      h->ws_bytes -= b.n;
       b.p = nullptr;
       b.n = 0;
     }
@@ -120,6 +131,7 @@ void *ws(lgw_handle *h, const std::string &name, size_t bytes) {
     }
     b.p = p;
     b.n = bytes;
+    h->ws_bytes += bytes;
     h->ws_gen++;
     h->drop_graphs();
   }
@@ -905,6 +917,54 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   }
 }
 
+// Interval [x_lo, x_hi] around the spectrum of C for the polynomial form:
+// x_lo = min Delta^2 (a bound: C = Delta^2 + a positive semidefinite term);
+// x_hi = the largest Ritz value of k_est Lanczos steps (FP64 contractions
+// when the system keeps its FP64 copy, CGS2) from a hash start vector, plus
+// the last beta, the residual norm of that step.  Synchronous.
+void estimate_interval(lgw_handle *h, const SysDev &s, int k_est, double &lo, double &hi) {
+  cudaStream_t &st = h->stream;
+  Opts o{};
+  o.k = std::max(1, std::min(k_est, s.n_vc));
+  o.precision = s.L64 ? LGW_FP64 : LGW_BF16;
+  o.reorth = LGW_REORTH_CGS2;
+  o.b_sub = 1;
+  o.qp_max_iter = 50;
+  o.split = o.precision != LGW_FP64;
+  o.tol = 1e-13;
+  o.qp_tol = 1e-10;
+  const bool timing = h->timing;
+  h->timing = false;
+  double *vec = wsT<double>(h, "iv_vec", (size_t)s.n_vc);
+  launch_interval(nullptr, s.n_vc, s.n_vc, nullptr, nullptr, nullptr, nullptr, vec,
+                  0x5EEDull, true, st);
+  check_launch(h, "hash_vector");
+  ProbView pv{};
+  pv.n_t = 1;
+  pv.n_m = 1;
+  pv.B = 1;
+  pv.d_V = vec;
+  pv.delta = 1.0;
+  double *a = wsT<double>(h, "iv_alpha", (size_t)o.k);
+  double *b = wsT<double>(h, "iv_beta", (size_t)o.k);
+  double *b0 = wsT<double>(h, "iv_beta0", 1);
+  int *ke = wsT<int>(h, "iv_keff", 1);
+  run_lanczos(h, s, pv, o, a, b, b0, ke, nullptr, nullptr);
+  double *out = wsT<double>(h, "iv_out", 2);
+  launch_interval(s.Delta2, s.n_vc, s.N, a, b, ke, out, nullptr, 0, false, st);
+  check_launch(h, "interval");
+  double hv[2];
+  LGW_TRY_CUDA(h, cudaMemcpyAsync(hv, out, sizeof hv, cudaMemcpyDeviceToHost, st));
+  LGW_TRY_CUDA(h, cudaStreamSynchronize(st));
+  h->timing = timing;
+  lo = hv[0];
+  hi = hv[1];
+  if (!(lo > 0.0) || !(hi > lo)) {
+    set_err(h, LGW_ERR_NOT_SPD, "spectral interval estimate [%g, %g] is not positive", lo, hi);
+    throw Fail{LGW_ERR_NOT_SPD};
+  }
+}
+
 void run_sigma(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o,
                const double *alpha, const double *beta, const double *beta0, const int *k_eff,
                double *sigma, double *e_qp, double *z_qp, lgw_report *rep, double *tacc,
@@ -1020,13 +1080,16 @@ lgw_status guard_handle(lgw_handle *h) {
 // exported C ABI
 // ===========================================================================
 namespace {
-const PolyOp *poly_arg(lgw_handle *h, const lgw_poly *pp, PolyOp &store) {
+// x_lo = x_hi = 0 asks the library for the interval (estimate_interval).
+const PolyOp *poly_arg(lgw_handle *h, const SysDev &s, const lgw_poly *pp, PolyOp &store) {
   if (!pp) return nullptr;
-  if (pp->g < 1 || pp->g > 256 || !(pp->x_lo > 0.0) || !(pp->x_hi > pp->x_lo)) {
-    set_err(h, LGW_ERR_ARG, "polynomial: need 1 <= g <= 256 and 0 < x_lo < x_hi");
+  double lo = pp->x_lo, hi = pp->x_hi;
+  if (pp->g >= 1 && pp->g <= 256 && lo == 0.0 && hi == 0.0) estimate_interval(h, s, 32, lo, hi);
+  if (pp->g < 1 || pp->g > 256 || !(lo > 0.0) || !(hi > lo)) {
+    set_err(h, LGW_ERR_ARG, "polynomial: need 1 <= g <= 256 and 0 < x_lo < x_hi (or both 0)");
     throw Fail{LGW_ERR_ARG};
   }
-  store = make_poly(pp->g, pp->x_lo, pp->x_hi);
+  store = make_poly(pp->g, lo, hi);
   return &store;
 }
 
@@ -1083,7 +1146,7 @@ lgw_status sigma_c_impl(lgw_handle *h, const lgw_system *sys, const lgw_problem 
     Opts op = resolve_opts(h, o, sys->s);
     ensure_copies(h, sys, op);
     PolyOp pstore;
-    const PolyOp *poly = poly_arg(h, pp, pstore);
+    const PolyOp *poly = poly_arg(h, sys->s, pp, pstore);
     if (poly) {
       // Lanczos on D = p_g(C) keeps the FP64 basis
       op.split = 0;
@@ -1179,6 +1242,61 @@ lgw_status lgw_destroy(lgw_handle *h) {
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   if (h->d_status) cudaFree(h->d_status);
   delete h;
+  return LGW_OK;
+}
+
+lgw_status lgw_set_workspace_limit(lgw_handle *h, size_t bytes) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  h->ws_limit = bytes;
+  return LGW_OK;
+}
+
+lgw_status lgw_workspace_bytes(lgw_handle *h, size_t *bytes) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!bytes) return set_err(h, LGW_ERR_ARG, "NULL argument to lgw_workspace_bytes");
+  *bytes = h->ws_bytes;
+  return LGW_OK;
+}
+
+lgw_status lgw_release_workspace(lgw_handle *h) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return set_err(h, LGW_ERR_CUDA, "stream synchronisation before the release failed");
+  h->drop_graphs();
+  for (auto &kv : h->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  h->bufs.clear();
+  h->ws_bytes = 0;
+  h->ws_gen++;
+  return LGW_OK;
+}
+
+lgw_status lgw_selftest_bounded_wait(lgw_handle *h, int32_t arrive, double seconds) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!(seconds >= 1e-4 && seconds <= 2.0))
+    return set_err(h, LGW_ERR_ARG, "self-test wait must lie in [1e-4, 2] s");
+  int khz = 0;
+  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, h->device) != cudaSuccess || khz <= 0)
+    return set_err(h, LGW_ERR_CUDA, "clock rate query failed");
+  const long long cycles = (long long)(seconds * (double)khz * 1e3);
+  cudaStream_t st = h->stream;
+  if (cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st) != cudaSuccess)
+    return set_err(h, LGW_ERR_CUDA, "status reset failed");
+  launch_wait_selftest(arrive != 0, cycles, h->d_status, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return set_err(h, LGW_ERR_CUDA, "self-test launch failed: %s", cudaGetErrorString(e));
+  unsigned stw = 0;
+  if (cudaMemcpyAsync(&stw, h->d_status, sizeof stw, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return set_err(h, LGW_ERR_CUDA, "self-test status read failed");
+  if (stw & ST_TIMEOUT)
+    return set_err(h, LGW_ERR_TIMEOUT, "a bounded device wait ran out (self-test, %.3g s)",
+                   seconds);
   return LGW_OK;
 }
 
@@ -1539,6 +1657,26 @@ lgw_status lgw_sigma_offdiag(lgw_handle *h, const lgw_system *sys, const lgw_pro
   return LGW_OK;
 }
 
+lgw_status lgw_spectral_interval(lgw_handle *h, const lgw_system *sys, int32_t k, double *x_lo,
+                                 double *x_hi) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!sys || sys->h != h || !x_lo || !x_hi)
+    return set_err(h, LGW_ERR_ARG, "NULL argument to lgw_spectral_interval");
+  if (k < 1 || k > 4095) return set_err(h, LGW_ERR_ARG, "k = %d outside [1, 4095]", k);
+  if (!sys->s.L64 && !sys->s.Lb)
+    return set_err(h, LGW_ERR_UNSUPPORTED, "the interval needs the FP64 or the BF16 copy of L");
+  try {
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
+    h->timing = false;
+    estimate_interval(h, sys->s, k, *x_lo, *x_hi);
+    check_status(h);
+  } catch (Fail &f) {
+    return f.st;
+  }
+  return LGW_OK;
+}
+
 lgw_status lgw_sigma_c_poly(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
                             const lgw_options *o, const lgw_poly *poly, double *sigma,
                             double *e_qp, double *z_qp, lgw_report *rep) {
@@ -1560,7 +1698,7 @@ lgw_status lgw_lanczos_coeffs_poly(lgw_handle *h, const lgw_system *sys, const l
     Opts op = resolve_opts(h, o, s);
     ensure_copies(h, sys, op);
     PolyOp pstore;
-    const PolyOp *poly = poly_arg(h, pp, pstore);
+    const PolyOp *poly = poly_arg(h, sys->s, pp, pstore);
     op.split = 0;
     op.split32 = 0;
     ProbView pv = check_problem(h, s, p);

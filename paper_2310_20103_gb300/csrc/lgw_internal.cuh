@@ -234,6 +234,9 @@ void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaSt
 bool launch_coupling_tc(const TcPlan *p, const SysDev &s, const double *M, int nvec,
                         float *vf, unsigned *status, cudaStream_t st);
 int tc_n_mt(const SysDev &s);
+// one block: a bounded wait of limit_cycles on a barrier that is completed
+// (arrive != 0) or never completed (ST_TIMEOUT)
+void launch_wait_selftest(int arrive, long long limit_cycles, unsigned *status, cudaStream_t st);
 
 // k_lanczos.cu : vector kernels of one step
 void launch_start_from_v(const VecCtx &c, const double *V, int ldv, int n_valid, cudaStream_t st);
@@ -298,6 +301,13 @@ void launch_poly_prep(const double *alpha, const double *beta, const double *bet
 void launch_spectral_impl(const double *alpha, const double *beta, const double *beta0,
                           const int *k_eff, int B, int k, JacobiBufs jb, double *scratch,
                           unsigned long long *min_theta_bits, unsigned *status, cudaStream_t st);
+
+// make_vector: a hash start vector vec [N] (entries in [-1, 1), zero
+// padding); otherwise out[0..1] = [min Delta^2, largest Ritz value of the
+// tridiagonal (a, b) of depth *k_eff plus its last off-diagonal]
+void launch_interval(const double *Delta2, int n_vc, int N, const double *a, const double *b,
+                     const int *k_eff, double *out, double *vec, unsigned long long seed,
+                     bool make_vector, cudaStream_t st);
 
 // k_cf.cu : continued fractions on the grid and QP solve
 struct CfProblem {

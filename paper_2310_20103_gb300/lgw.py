@@ -274,6 +274,40 @@ def lgw_destroy(h: Handle) -> None:
         h.ptr = ctypes.c_void_p()
 
 
+def lgw_set_workspace_limit(h: Handle, nbytes: int) -> None:
+    lib = load_library()
+    fn = lib.lgw_set_workspace_limit
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    fn.restype = ctypes.c_int32
+    _check(h, fn(h.ptr, int(nbytes)))
+
+
+def lgw_workspace_bytes(h: Handle) -> int:
+    lib = load_library()
+    fn = lib.lgw_workspace_bytes
+    fn.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
+    fn.restype = ctypes.c_int32
+    n = ctypes.c_size_t(0)
+    _check(h, fn(h.ptr, ctypes.byref(n)))
+    return int(n.value)
+
+
+def lgw_release_workspace(h: Handle) -> None:
+    lib = load_library()
+    fn = lib.lgw_release_workspace
+    fn.argtypes = [ctypes.c_void_p]
+    fn.restype = ctypes.c_int32
+    _check(h, fn(h.ptr))
+
+
+def lgw_selftest_bounded_wait(h: Handle, arrive: bool, seconds: float) -> None:
+    lib = load_library()
+    fn = lib.lgw_selftest_bounded_wait
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double]
+    fn.restype = ctypes.c_int32
+    _check(h, fn(h.ptr, 1 if arrive else 0, float(seconds)))
+
+
 def lgw_prepare_system(h: Handle, n_v: int, n_c: int, n_aux: int, eps, L,
                        kernel_factor: float = 4.0, flags: int = 0) -> System:
     d = lgw_system_desc(int(n_v), int(n_c), int(n_aux), _ptr(eps, "f64"), _ptr(L, "f64"),
@@ -361,6 +395,18 @@ def lgw_sigma_c_poly(h: Handle, s: System, problem: Problem, options: Options, g
         h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), ctypes.byref(pl), _ptr(sigma, "f64"),
         _ptr(e_qp, "f64"), _ptr(z_qp, "f64"), ctypes.byref(rep) if report else None))
     return rep.as_dict() if report else None
+
+
+def lgw_spectral_interval(h: Handle, s: System, k: int = 32):
+    """(x_lo, x_hi) around the spectrum of C for the polynomial fit."""
+    lib = load_library()
+    fn = lib.lgw_spectral_interval
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    fn.restype = ctypes.c_int32
+    lo, hi = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(h, fn(h.ptr, s.ptr, int(k), ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
 
 
 def lgw_lanczos_coeffs_poly(h: Handle, s: System, problem: Problem, options: Options, g: int,

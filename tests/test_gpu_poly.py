@@ -113,3 +113,43 @@ def test_fig1_analogue(L, handle):
     print("meV by k (g=16):", {k: f"{v:.3e}" for k, v in by_k.items()})
     assert by_g[32] < by_g[8] < by_g[2]
     assert by_k[64] < by_k[8] < by_k[2]
+
+
+def test_spectral_interval_encloses_the_spectrum(L, handle):
+    """lgw_spectral_interval: x_lo = min Delta^2 lies below lambda_min (C =
+    Delta^2 + a positive semidefinite term) and x_hi, the largest Ritz value
+    plus its residual norm, lies above lambda_max and within 25% of it
+    (tiny system, dense eigenvalues by numpy)."""
+    wl = gi.tiny()
+    lam_lo, lam_hi = _bounds(wl)
+    s = L.lgw_prepare_system(handle, wl.n_v, wl.n_c, wl.n_aux, _t(wl.eps), _t(wl.L),
+                             wl.kernel_factor)
+    try:
+        lo, hi = L.lgw_spectral_interval(handle, s, 32)
+    finally:
+        L.lgw_release_system(s)
+    D = O.pair_energies(wl.eps, wl.n_v)
+    assert lo == pytest.approx(float((D ** 2).min()), rel=1e-15)
+    assert lo <= lam_lo
+    assert lam_hi <= hi <= 1.25 * lam_hi
+
+
+def test_poly_with_library_interval(L, handle):
+    """x_lo = x_hi = 0 makes lgw_sigma_c_poly take lgw_spectral_interval's
+    interval: the results are bit-identical to passing that interval, and
+    the QP energies stay within 1 meV of the closed form at g = 16."""
+    wl = gi.tiny()
+    s = L.lgw_prepare_system(handle, wl.n_v, wl.n_c, wl.n_aux, _t(wl.eps), _t(wl.L),
+                             wl.kernel_factor)
+    try:
+        lo, hi = L.lgw_spectral_interval(handle, s, 32)
+    finally:
+        L.lgw_release_system(s)
+    opts = L.Options(k=64, precision="fp64", reorth="cgs2")
+    sig_a, e_a, co_a = _run(L, handle, wl, 16, 0.0, 0.0, opts)
+    sig_b, e_b, co_b = _run(L, handle, wl, 16, lo, hi, opts)
+    assert np.array_equal(e_a, e_b)
+    assert np.array_equal(sig_a, sig_b)
+    _, polesx = O.sigma_closed_form(wl)
+    Ex, _ = O.solve_all_qp(wl, polesx)
+    assert np.abs(e_a - Ex).max() < 1e-3
