@@ -40,6 +40,7 @@ __all__ = [
     "qp_gradient_lanczos", "chebyshev_sqrt", "chebyshev_eval", "apply_poly",
     "sigma_poly_lanczos", "haydock", "sigma_x", "qp_linearised", "fit_factors",
     "tda_matrix", "sigma_tda_closed_form", "sigma_tda_lanczos", "sigma_offdiag_closed_form",
+    "band_lanczos", "band_gauss_rule", "sigma_band_lanczos",
 ]
 
 
@@ -650,3 +651,107 @@ def sigma_offdiag_closed_form(wl, t_pair):
         z = wl.omega[:, None] - wl.eps[m] - 1j * eta[mi] * wl.delta
         out += np.sum(pa * pb / (Om * (z + eta[mi] * Om)), axis=1)
     return out
+
+
+# --------------------------------------------------------------------------
+# Band Lanczos for off-diagonal elements: the band-Lanczos method for
+# matrix elements of a resolvent that the paper cites after Eq. 14, here in
+# the one-vector-per-step form with full reorthogonalisation.
+# --------------------------------------------------------------------------
+def band_lanczos(apply_op, B, k, breakdown_tol=1e-13):
+    """Band Lanczos from the p rows of B ([p, N]).
+
+    The start block is orthonormalised by classical Gram-Schmidt (twice):
+    b_a = sum_i R0[i, a] q_i, R0 [p, p] upper triangular, q_0..q_{p-1} the
+    first basis vectors.  Step j applies C to q_j (the j-th basis vector):
+        u = C q_j ;  twice: h = Q^T u, u = u - Q h     (all n vectors so far)
+        T[i, j] = T[j, i] = (sum of both passes' h_i)  for j <= i < n
+        beta = ||u||: unless beta <= breakdown_tol * max|T|, a new vector
+        q_n = u / beta with T[n, j] = T[j, n] = beta.
+    T on the first k basis vectors is Q^T C Q, banded with bandwidth p.  The
+    recurrence ends after k steps, or earlier once every basis vector has
+    been multiplied (the block's Krylov space is exhausted); vectors past
+    the k-th are not formed.
+    Returns (T [ke, ke], R0 [p, p], ke) with ke <= k the number of steps."""
+    B = np.atleast_2d(np.asarray(B, dtype=np.float64))
+    p, N = B.shape
+    Q = np.zeros((max(k, p), N))
+    R0 = np.zeros((p, p))
+    n = 0
+    scale = 0.0
+    for a in range(p):
+        u = B[a].copy()
+        h = np.zeros(n)
+        for _ in range(2):
+            d = Q[:n] @ u
+            u = u - Q[:n].T @ d
+            h = h + d
+        r = np.linalg.norm(u)
+        R0[:n, a] = h
+        scale = max(scale, np.linalg.norm(B[a]))
+        if r > breakdown_tol * scale:
+            R0[n, a] = r
+            Q[n] = u / r
+            n += 1
+    T = np.zeros((k, k))
+    tmax = 0.0
+    j = 0
+    while j < k and j < n:
+        u = apply_op(Q[j][None, :])[0]
+        h = np.zeros(n)
+        for _ in range(2):
+            d = Q[:n] @ u
+            u = u - Q[:n].T @ d
+            h = h + d
+        for i in range(j, min(n, k)):
+            T[i, j] = T[j, i] = h[i]
+        tmax = max(tmax, np.abs(h[j:n]).max())
+        beta = np.linalg.norm(u)
+        # vectors past the first k are never multiplied and do not enter T
+        if n < k and beta > breakdown_tol * tmax:
+            T[n, j] = T[j, n] = beta
+            Q[n] = u / beta
+            n += 1
+        j += 1
+    return T[:j, :j], R0, j
+
+
+def band_gauss_rule(T, R0):
+    """Matrix-valued Gauss rule of the band recurrence: nodes theta_s and
+    vectors r_s = R0^T U[:p, s] (U the eigenvectors of T), so that
+    b_a . f(C) b_b ~ sum_s f(theta_s) r_s[a] r_s[b]; exact once the block's
+    Krylov space is exhausted."""
+    theta, U = np.linalg.eigh(T)
+    p = R0.shape[0]
+    return theta, R0.T @ U[:p, :]
+
+
+def sigma_band_lanczos(wl, k=None, breakdown_tol=1e-13):
+    """Sigma_tt'(omega) for every pair of the workload's targets: one band
+    recurrence per summed orbital m from the block [b_tm over t], then
+        Sigma_tt'(omega) = sum_m sum_s r_s[t] r_s[t'] / (Omega_s (z_m + eta_m Omega_s)),
+    Omega_s = sqrt(theta_s), z_m = omega - eps_m - i eta_m delta (Eq. 7 with
+    the square-root map of Eq. 12).  Returns sigma [n_t, n_t, n_freq] and the
+    per-m recurrences [(T, R0, ke)]."""
+    k = wl.k if k is None else k
+    b = start_vectors(wl.eps, wl.n_v, coupling_vectors(wl.L, wl.M))   # [n_t, n_m, N]
+    eta = occupation_sign(wl.m_idx, wl.n_v)
+
+    def apply_op(X):
+        return apply_casida(wl.eps, wl.n_v, wl.L, X, wl.kernel_factor)
+
+    out = np.zeros((wl.n_t, wl.n_t, wl.omega.size), dtype=np.complex128)
+    recs = []
+    for mi, m in enumerate(wl.m_idx):
+        T, R0, ke = band_lanczos(apply_op, b[:, mi, :], k, breakdown_tol)
+        recs.append((T, R0, ke))
+        if ke == 0:
+            continue
+        theta, r = band_gauss_rule(T, R0)
+        if theta.min() <= 0.0:
+            raise ValueError("band tridiagonal is not positive definite")
+        Om = np.sqrt(theta)
+        z = wl.omega[:, None] - wl.eps[m] - 1j * eta[mi] * wl.delta
+        g = 1.0 / (Om * (z + eta[mi] * Om))           # [n_freq, ke]
+        out += np.einsum("as,bs,fs->abf", r, r, g)
+    return out, recs
