@@ -367,6 +367,30 @@ lgw_status lgw_lanczos_coeffs_poly(lgw_handle *h, const lgw_system *s, const lgw
                                    const lgw_options *o, const lgw_poly *poly, double *alpha,
                                    double *beta, double *beta0, int32_t *k_eff);
 
+/* Self-energy matrix Sigma_tt'(omega) of the request's targets (n_t = p,
+ * 1..8) by band Lanczos: the band method for matrix elements of a resolvent
+ * that the paper cites after Eq. 14, here with the square-root map of the
+ * Gauss rule (Eq. 12) in place of the resolvent of D.  For each summed
+ * orbital m one recurrence starts from the block [b_{t,m} over the
+ * targets], orthonormalised into q_0..q_{p-1} with b_t = sum_i R0[i][t] q_i;
+ * step j applies C to q_j (one matvec per m and step, through the same
+ * contractions as lgw_sigma_c) and projects the result out of all of m's
+ * basis vectors twice (classical Gram-Schmidt, FP64 basis), giving column j
+ * of the banded T = Q^T C Q and at most one new basis vector.  The k x k T
+ * then yields every element b_t . f(C) b_t' with f(theta) =
+ * 1/(sqrt(theta)(z_m + eta_m sqrt(theta))): a k-step Lanczos on T from
+ * R0 e_t (diagonal) and from R0 (e_t +- e_t') (pairs, combined by the
+ * polarisation identity), each mapped and summed like lgw_sigma_c's
+ * fractions (Eq. 7, 10-14).  This shares one recurrence per m among all
+ * p(p+1)/2 elements, where lgw_sigma_offdiag runs two per pair.  Exact once
+ * the block Krylov space is exhausted.
+ *   sigma [n_t][n_t][n_freq][2] (symmetric); rep or NULL.
+ * Limits: precision FP64 or BF16 (LGW_ERR_UNSUPPORTED for E4M3), k <= 512;
+ * o->reorth is not used (always two projections); the static shift and QP
+ * options are not used.  Scratch: k^2 doubles per (m, element vector). */
+lgw_status lgw_sigma_band(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                          const lgw_options *o, double *sigma, lgw_report *rep);
+
 /* Exchange self-energy Sigma^ex_t = -sum_v (vt|vt) (text after Eq. 5) over
  * the occupied orbitals v of the request's summed set, from its pair factors
  * (which share L's metric-folded form, (pq|rs) = sum_mu B_pq,mu B_rs,mu):

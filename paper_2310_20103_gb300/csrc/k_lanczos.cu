@@ -421,7 +421,420 @@ __global__ void k_scale_rows_to_bf16(const double *__restrict__ x, const double 
 }
 
 // ---------------------------------------------------------------------------
+// Band Lanczos (the band method for resolvent matrix elements cited after
+// Eq. 14), one new vector per step with full reorthogonalisation.  Each
+// group g (a summed orbital m) carries one recurrence; its start block is
+// the p targets' vectors b_{t,m}.  The start vectors are orthonormalised one
+// after the other, then step j applies C to basis vector q_j; both cases
+// end in the same orthogonalise-and-append: w is projected out of all of
+// the group's vectors twice (classical Gram-Schmidt in FP64), the
+// coefficients of both passes are recorded (a column of R0 or of the banded
+// T), and w / ||w|| becomes the next basis vector unless ||w|| fell below
+// the breakdown scale.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool band_act(const BandCtx &bc, int b) {
+  return b < bc.c.nvec && bc.act[b] != 0;
+}
+
+__global__ void k_band_init(BandCtx bc) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= bc.c.Bs) return;
+  bc.nv[b] = 0;
+  bc.act[b] = 0;
+  bc.newrow[b] = -1;
+  bc.inv[b] = 0.0;
+  bc.scale[b] = 0.0;
+  bc.tmax[b] = 0.0;
+}
+
+// mode 0 (a start vector): every real group; mode 1 (step j): the groups
+// whose basis vector j exists.
+__global__ void k_band_activate(BandCtx bc, int mode, int j) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= bc.c.Bs) return;
+  bc.act[b] = (b < bc.c.nvec && (mode == 0 || j < bc.nv[b])) ? 1 : 0;
+}
+
+// The contraction operand of q_j: FP64 copy (FP64 contractions) or
+// bf16(Delta^1/2 q_j); zeros for groups without vector j.
+__global__ void __launch_bounds__(VEC_THREADS) k_band_operand(BandCtx bc, int j) {
+  const VecCtx &c = bc.c;
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const bool act = band_act(bc, b);
+  const size_t voff = (size_t)b * c.N;
+  const double *q = slot_ptr(c, j) + voff;
+  const int e0 = elem_base(chunk);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= c.N) continue;
+    const double2 q2 = act ? *reinterpret_cast<const double2 *>(q + e) : make_double2(0.0, 0.0);
+    if (bc.xq != nullptr) *reinterpret_cast<double2 *>(bc.xq + voff + e) = q2;
+    if (c.xh != nullptr) {
+      __nv_bfloat162 x2;
+      x2.x = __float2bfloat16_rn(c.dsqf[e] * __double2float_rn(q2.x));
+      x2.y = __float2bfloat16_rn(c.dsqf[e + 1] * __double2float_rn(q2.y));
+      *reinterpret_cast<__nv_bfloat162 *>(c.xh + kblk_bf16(b, e, c.Bs)) = x2;
+    }
+  }
+}
+
+// w = Delta^2 q_j + c_K Delta^1/2 L y   (Eq. 4; the contraction in FP32)
+__global__ void __launch_bounds__(VEC_THREADS) k_band_assemble(BandCtx bc, int j,
+                                                              const float *__restrict__ ucd) {
+  const VecCtx &c = bc.c;
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  if (!band_act(bc, b)) return;
+  const size_t voff = (size_t)b * c.N;
+  const double *q = slot_ptr(c, j) + voff;
+  const int e0 = elem_base(chunk);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= c.N) continue;
+    const double2 q2 = *reinterpret_cast<const double2 *>(q + e);
+    const float2 v2 = *reinterpret_cast<const float2 *>(ucd + kblk_f32(b, e, c.Bs));
+    double2 w2;
+    w2.x = fma(c.Delta2[e], q2.x, (double)v2.x);
+    w2.y = fma(c.Delta2[e + 1], q2.y, (double)v2.y);
+    *reinterpret_cast<double2 *>(c.w + voff + e) = w2;
+  }
+}
+
+// Dots of w with the group's basis vectors; pass 1 also ||w||^2 (norm_a).
+__global__ void __launch_bounds__(VEC_THREADS) k_band_dots(BandCtx bc, int pass) {
+  __shared__ double red[VEC_THREADS / 32];
+  __shared__ double sred[VEC_THREADS / 32][32];
+  const VecCtx &c = bc.c;
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  if (!band_act(bc, b)) return;
+  const double *w = c.w + (size_t)b * c.N;
+  const int e0 = elem_base(chunk);
+  double wr[8];
+  double nrm = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    double2 w2 = make_double2(0.0, 0.0);
+    if (e < c.N) w2 = *reinterpret_cast<const double2 *>(w + e);
+    wr[2 * u] = w2.x;
+    wr[2 * u + 1] = w2.y;
+    nrm = fma(w2.x, w2.x, fma(w2.y, w2.y, nrm));
+  }
+  if (pass == 1) {
+    nrm = block_sum(nrm, red);
+    if (threadIdx.x == 0) c.norm_a[(size_t)b * c.nchunks + chunk] = nrm;
+  }
+  dots_rows(c, bc.nv[b], b, chunk, wr, sred);
+}
+
+// h = sum over chunks (fixed order); hsum accumulates the two passes.
+__global__ void k_band_reduce(BandCtx bc, int pass) {
+  const VecCtx &c = bc.c;
+  const int b = blockIdx.x;
+  if (!band_act(bc, b)) return;
+  const int n = bc.nv[b];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double *pp = c.dot_part + (size_t)b * c.nchunks * c.kmax1 + i;
+    double s = 0.0;
+    for (int ch = 0; ch < c.nchunks; ++ch) s += pp[(size_t)ch * c.kmax1];
+    const size_t hi = (size_t)b * c.kmax1 + i;
+    c.h[hi] = s;
+    bc.hsum[hi] = pass == 1 ? s : bc.hsum[hi] + s;
+  }
+}
+
+// w <- w - sum_i h_i q_i over the group's vectors; ||w||^2 partials
+// (pass 1: norm_b, pass 2: norm_c).
+__global__ void __launch_bounds__(VEC_THREADS) k_band_update(BandCtx bc, int pass) {
+  extern __shared__ double hs[];
+  __shared__ double red[VEC_THREADS / 32];
+  const VecCtx &c = bc.c;
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  if (!band_act(bc, b)) return;
+  const int n = bc.nv[b];
+  for (int i = threadIdx.x; i < n; i += VEC_THREADS) hs[i] = c.h[(size_t)b * c.kmax1 + i];
+  __syncthreads();
+  const size_t voff = (size_t)b * c.N;
+  double *w = c.w + voff;
+  const int e0 = elem_base(chunk);
+  double2 wv[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    wv[u] = (e < c.N) ? *reinterpret_cast<const double2 *>(w + e) : make_double2(0.0, 0.0);
+  }
+  for (int i = 0; i < n; ++i) {
+    const double hi = hs[i];
+    const double *qrow = slot_ptr(c, i) + voff;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * 64;
+      if (e < c.N) {
+        const double2 q2 = *reinterpret_cast<const double2 *>(qrow + e);
+        wv[u].x = fma(-hi, q2.x, wv[u].x);
+        wv[u].y = fma(-hi, q2.y, wv[u].y);
+      }
+    }
+  }
+  double nrm = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e < c.N) *reinterpret_cast<double2 *>(w + e) = wv[u];
+    nrm = fma(wv[u].x, wv[u].x, fma(wv[u].y, wv[u].y, nrm));
+  }
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) (pass == 1 ? c.norm_b : c.norm_c)[(size_t)b * c.nchunks + chunk] = nrm;
+}
+
+// One warp per group: beta = ||w|| after both passes, the coefficient
+// record and the breakdown test; sets the row to append (or -1).
+__global__ void k_band_beta(BandCtx bc, int mode, int idx) {
+  const VecCtx &c = bc.c;
+  const int b = blockIdx.x, lane = threadIdx.x;
+  if (!band_act(bc, b)) {
+    if (lane == 0 && b < c.Bs) bc.newrow[b] = -1;
+    return;
+  }
+  const int g = c.vec0 + b, p = bc.p, n = bc.nv[b];
+  double s2 = 0.0, s0 = 0.0;
+  for (int ch = lane; ch < c.nchunks; ch += 32) {
+    s2 += c.norm_c[(size_t)b * c.nchunks + ch];
+    s0 += c.norm_a[(size_t)b * c.nchunks + ch];
+  }
+  const double beta = sqrt(warp_sum(s2));
+  const double norm0 = sqrt(warp_sum(s0));
+  const double *hs = bc.hsum + (size_t)b * c.kmax1;
+  bool append;
+  if (mode == 0) {
+    // start vector a = idx: b_a = sum_{i<n} hsum_i q_i + beta q_n
+    const int a = idx;
+    for (int i = lane; i < n; i += 32) bc.R0[((size_t)g * p + i) * p + a] = hs[i];
+    const double sc = fmax(bc.scale[b], norm0);
+    append = beta > c.tol * sc;
+    if (lane == 0) {
+      bc.scale[b] = sc;
+      if (append) bc.R0[((size_t)g * p + n) * p + a] = beta;
+    }
+  } else {
+    // step j = idx: T[i][j] = hsum_i for j <= i < n (d = i - j <= p - 1),
+    // T[n][j] = beta for an appended vector (d = n - j <= p)
+    const int j = idx;
+    double tm = 0.0;
+    for (int i = j + lane; i < n; i += 32) {
+      bc.Tb[((size_t)g * c.k + j) * (p + 1) + (i - j)] = hs[i];
+      tm = fmax(tm, fabs(hs[i]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tm = fmax(tm, __shfl_xor_sync(0xffffffffu, tm, o));
+    const double tmax = fmax(bc.tmax[b], tm);
+    append = n < c.k && beta > c.tol * tmax;
+    if (lane == 0) {
+      bc.tmax[b] = tmax;
+      if (append) bc.Tb[((size_t)g * c.k + j) * (p + 1) + (n - j)] = beta;
+    }
+  }
+  if (lane == 0) {
+    bc.newrow[b] = append ? n : -1;
+    bc.inv[b] = append ? 1.0 / beta : 0.0;
+    if (append) bc.nv[b] = n + 1;
+  }
+}
+
+// q_new = w / beta into the appended row.
+__global__ void __launch_bounds__(VEC_THREADS) k_band_normalize(BandCtx bc) {
+  const VecCtx &c = bc.c;
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  if (b >= c.nvec) return;
+  const int r = bc.newrow[b];
+  if (r < 0) return;
+  const double inv = bc.inv[b];
+  const size_t voff = (size_t)b * c.N;
+  double *qn = slot_ptr(c, r) + voff;
+  const double *w = c.w + voff;
+  const int e0 = elem_base(chunk);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= c.N) continue;
+    double2 q2 = *reinterpret_cast<const double2 *>(w + e);
+    q2.x *= inv;
+    q2.y *= inv;
+    *reinterpret_cast<double2 *>(qn + e) = q2;
+  }
+}
+
+__global__ void k_band_finish(BandCtx bc) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= bc.c.nvec) return;
+  bc.keff[bc.c.vec0 + b] = min(bc.c.k, bc.nv[b]);
+}
+
+// T[i][j] of group g from the lower band (0 outside the band or past ke).
+__device__ __forceinline__ double band_T(const double *Tg, int p, int ke, int i, int j) {
+  const int lo = i < j ? i : j, d = i < j ? j - i : i - j;
+  if (d > p || lo < 0 || i >= ke || j >= ke) return 0.0;
+  return Tg[(size_t)lo * (p + 1) + d];
+}
+
+// One warp per (polarisation vector xi, group g): k_eff-step Lanczos on the
+// group's ke x ke banded T from y = R0 x (Eq. 13 on the projected matrix),
+// CGS2 against the stored vectors (scratch rows in global memory, lanes
+// over the ke components).  y^T f(T) y then follows from this tridiagonal
+// like any start vector's: Gauss rule, square-root map, fraction.
+__global__ void k_band_small(const double *__restrict__ Tb, const double *__restrict__ R0,
+                             const int *__restrict__ keff, int G, int k, int p,
+                             const double *__restrict__ xs, int nx, double tol,
+                             double *__restrict__ scratch, double *__restrict__ alpha,
+                             double *__restrict__ beta, double *__restrict__ beta0,
+                             int *__restrict__ keff_out) {
+  const int warps = blockDim.x >> 5;
+  const int wv = blockIdx.x * warps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (wv >= nx * G) return;
+  const int xi = wv / G, g = wv % G;
+  const int ke = keff[g];
+  double *Q = scratch + (size_t)wv * (k + 2) * k;   // rows 0..ke-1: basis; row k: u
+  double *u = Q + (size_t)k * k;
+  double *al = alpha + (size_t)wv * k, *be = beta + (size_t)wv * k;
+  for (int i = lane; i < k; i += 32) {
+    al[i] = 0.0;
+    be[i] = 0.0;
+  }
+  const double *Tg = Tb + (size_t)g * k * (p + 1);
+  const double *Rg = R0 + (size_t)g * p * p;
+  // y_i = sum_a R0[i][a] x_a (nonzero for i < p)
+  double ss = 0.0;
+  for (int i = lane; i < ke; i += 32) {
+    double y = 0.0;
+    if (i < p)
+      for (int a = 0; a < p; ++a) y = fma(Rg[(size_t)i * p + a], xs[(size_t)xi * p + a], y);
+    u[i] = y;
+    ss = fma(y, y, ss);
+  }
+  const double b0 = sqrt(warp_sum(ss));
+  if (lane == 0) beta0[wv] = b0;
+  if (!(b0 > 0.0) || ke <= 0) {
+    if (lane == 0) keff_out[wv] = 0;
+    return;
+  }
+  int kk = ke;
+  double bprev = 0.0, amax = 0.0;
+  double inv = 1.0 / b0;
+  for (int j = 0; j < ke; ++j) {
+    double *q = Q + (size_t)j * k;
+    __syncwarp();
+    for (int i = lane; i < ke; i += 32) q[i] = u[i] * inv;
+    __syncwarp();
+    // u = T q - beta_j q_{j-1}; alpha_j = q . u; u -= alpha_j q
+    double aj = 0.0;
+    for (int i = lane; i < ke; i += 32) {
+      double s = 0.0;
+      for (int d = -p; d <= p; ++d) {
+        const int c2 = i + d;
+        if (c2 >= 0 && c2 < ke) s = fma(band_T(Tg, p, ke, i, c2), q[c2], s);
+      }
+      if (j > 0) s = fma(-bprev, Q[(size_t)(j - 1) * k + i], s);
+      u[i] = s;
+      aj = fma(q[i], s, aj);
+    }
+    aj = warp_sum(aj);
+    __syncwarp();
+    for (int i = lane; i < ke; i += 32) u[i] = fma(-aj, q[i], u[i]);
+    // full reorthogonalisation, twice
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int r = 0; r <= j; ++r) {
+        const double *qr = Q + (size_t)r * k;
+        __syncwarp();
+        double d = 0.0;
+        for (int i = lane; i < ke; i += 32) d = fma(qr[i], u[i], d);
+        d = warp_sum(d);
+        __syncwarp();
+        for (int i = lane; i < ke; i += 32) u[i] = fma(-d, qr[i], u[i]);
+      }
+    }
+    __syncwarp();
+    double nn = 0.0;
+    for (int i = lane; i < ke; i += 32) nn = fma(u[i], u[i], nn);
+    const double bj = sqrt(warp_sum(nn));
+    amax = fmax(amax, fabs(aj));
+    if (lane == 0) {
+      al[j] = aj;
+      be[j] = bj;
+    }
+    if (!(bj > tol * amax) || j + 1 == ke) {
+      kk = j + 1;
+      break;
+    }
+    bprev = bj;
+    inv = 1.0 / bj;
+  }
+  if (lane == 0) keff_out[wv] = kk;
+}
+
+__global__ void k_band_combine(const double *__restrict__ sig, int p, int F,
+                               double *__restrict__ out) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ab = blockIdx.y;
+  if (f >= F) return;
+  const int a = ab / p, b = ab % p;
+  double re, im;
+  if (a == b) {
+    re = sig[((size_t)a * F + f) * 2];
+    im = sig[((size_t)a * F + f) * 2 + 1];
+  } else {
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    // pair index of (lo, hi) in the order (0,1), (0,2), ..., (1,2), ...
+    const int q = lo * p - lo * (lo + 1) / 2 + (hi - lo - 1);
+    const size_t xp = (size_t)(p + 2 * q), xm = xp + 1;
+    re = 0.25 * (sig[(xp * F + f) * 2] - sig[(xm * F + f) * 2]);
+    im = 0.25 * (sig[(xp * F + f) * 2 + 1] - sig[(xm * F + f) * 2 + 1]);
+  }
+  out[((size_t)ab * F + f) * 2] = re;
+  out[((size_t)ab * F + f) * 2 + 1] = im;
+}
+
+// ---------------------------------------------------------------------------
 static dim3 vec_grid(const VecCtx &c) { return dim3(c.nchunks, c.Bs); }
+
+void launch_band_init(const BandCtx &bc, cudaStream_t st) {
+  k_band_init<<<(bc.c.Bs + 255) / 256, 256, 0, st>>>(bc);
+}
+void launch_band_activate(const BandCtx &bc, int mode, int j, cudaStream_t st) {
+  k_band_activate<<<(bc.c.Bs + 255) / 256, 256, 0, st>>>(bc, mode, j);
+}
+void launch_band_operand(const BandCtx &bc, int j, cudaStream_t st) {
+  k_band_operand<<<vec_grid(bc.c), VEC_THREADS, 0, st>>>(bc, j);
+}
+void launch_band_assemble(const BandCtx &bc, int j, const float *ucd, cudaStream_t st) {
+  k_band_assemble<<<vec_grid(bc.c), VEC_THREADS, 0, st>>>(bc, j, ucd);
+}
+int launch_band_append(const BandCtx &bc, int mode, int idx, cudaStream_t st) {
+  const size_t sh = (size_t)bc.c.kmax1 * sizeof(double);
+  for (int pass = 1; pass <= 2; ++pass) {
+    k_band_dots<<<vec_grid(bc.c), VEC_THREADS, 0, st>>>(bc, pass);
+    k_band_reduce<<<bc.c.Bs, 256, 0, st>>>(bc, pass);
+    k_band_update<<<vec_grid(bc.c), VEC_THREADS, sh, st>>>(bc, pass);
+  }
+  k_band_beta<<<bc.c.Bs, 32, 0, st>>>(bc, mode, idx);
+  k_band_normalize<<<vec_grid(bc.c), VEC_THREADS, 0, st>>>(bc);
+  return 8;
+}
+void launch_band_finish(const BandCtx &bc, cudaStream_t st) {
+  k_band_finish<<<(bc.c.Bs + 255) / 256, 256, 0, st>>>(bc);
+}
+void launch_band_small(const double *Tb, const double *R0, const int *keff, int G, int k, int p,
+                       const double *xs, int nx, double tol, double *scratch, double *alpha,
+                       double *beta, double *beta0, int *keff_out, cudaStream_t st) {
+  const int warps = 4;
+  const int n = nx * G;
+  k_band_small<<<(n + warps - 1) / warps, 32 * warps, 0, st>>>(
+      Tb, R0, keff, G, k, p, xs, nx, tol, scratch, alpha, beta, beta0, keff_out);
+}
+void launch_band_combine(const double *sig, int p, int F, double *out, cudaStream_t st) {
+  dim3 grid((F + 127) / 128, p * p);
+  k_band_combine<<<grid, 128, 0, st>>>(sig, p, F, out);
+}
 
 void launch_start_from_v(const VecCtx &c, const double *V, int ldv, int n_valid, cudaStream_t st) {
   k_start_from_v<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, V, ldv, n_valid);

@@ -506,7 +506,9 @@ __global__ void __launch_bounds__(VEC_THREADS) k_start_split(VecCtx c) {
 // ===========================================================================
 
 // Rows i_top, i_top - 1, ..., i_top - R + 1 of vector b: loads first (4R
-// independent 128-bit loads per thread), then the products.
+// independent 128-bit loads per thread), then the products; the R row
+// partials of the warp are reduced together (R = 4: a transposed butterfly,
+// 12 shuffles for four rows instead of 40).
 template <bool LO, bool CORR, int R>
 __device__ __forceinline__ void sweep_rows(const VecCtx &c, int b, int i_top, int ebase,
                                            const float *cs, const float *gs,
@@ -514,6 +516,7 @@ __device__ __forceinline__ void sweep_rows(const VecCtx &c, int b, int i_top, in
                                            float (&corr)[8], float (&cv)[8],
                                            float2 (*pp)[VEC_THREADS / 32], int slot0, int lane,
                                            int wid) {
+  static_assert(R == 1 || R == 4, "row groups of 1 or 4");
   float4 hq[R][2], lq[R][2];
 #pragma unroll
   for (int q = 0; q < R; ++q) {
@@ -532,11 +535,13 @@ __device__ __forceinline__ void sweep_rows(const VecCtx &c, int b, int i_top, in
       }
     }
   }
+  float sh[R], sl[R];
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const float cf = CORR ? cs[i_top - q] : 0.0f;
     const float gf = CORR ? gs[i_top - q] : 0.0f;
-    float sh = 0.f, sl = 0.f;
+    sh[q] = 0.f;
+    sl[q] = 0.f;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const float xa[4] = {hq[q][u].x, hq[q][u].y, hq[q][u].z, hq[q][u].w};
@@ -552,17 +557,47 @@ __device__ __forceinline__ void sweep_rows(const VecCtx &c, int b, int i_top, in
         float err = __fmaf_rn(xa[t], vh[m], -pr);
         err = __fmaf_rn(xa[t], vl[m], err);
         if (LO) err = __fmaf_rn(xb[t], vh[m], err);
-        two_sum_acc(sh, sl, pr);
-        sl = __fadd_rn(sl, err);
+        two_sum_acc(sh[q], sl[q], pr);
+        sl[q] = __fadd_rn(sl[q], err);
       }
     }
+  }
+  if (R == 1) {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
-      const float rh = __shfl_xor_sync(0xffffffffu, sh, o);
-      const float rl = __shfl_xor_sync(0xffffffffu, sl, o);
-      df_add(sh, sl, rh, rl);
+      const float rh = __shfl_xor_sync(0xffffffffu, sh[0], o);
+      const float rl = __shfl_xor_sync(0xffffffffu, sl[0], o);
+      df_add(sh[0], sl[0], rh, rl);
     }
-    if (lane == 0) pp[slot0 + q][wid] = make_float2(sh, sl);
+    if (lane == 0) pp[slot0][wid] = make_float2(sh[0], sl[0]);
+  } else {
+    // lanes 16..31 keep rows 2, 3 and lanes 0..15 rows 0, 1; then lanes with
+    // bit 3 set keep the odd row; the rest is a plain butterfly over the 8
+    // lanes that share bits 3 and 4.  Row q ends in lane 8q.
+    const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+    float kh[2], kl[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const float sendh = up16 ? sh[r] : sh[R - 2 + r], sendl = up16 ? sl[r] : sl[R - 2 + r];
+      kh[r] = up16 ? sh[R - 2 + r] : sh[r];
+      kl[r] = up16 ? sl[R - 2 + r] : sl[r];
+      const float rh = __shfl_xor_sync(0xffffffffu, sendh, 16);
+      const float rl = __shfl_xor_sync(0xffffffffu, sendl, 16);
+      df_add(kh[r], kl[r], rh, rl);
+    }
+    float th = up8 ? kh[1] : kh[0], tl = up8 ? kl[1] : kl[0];
+    {
+      const float rh = __shfl_xor_sync(0xffffffffu, up8 ? kh[0] : kh[1], 8);
+      const float rl = __shfl_xor_sync(0xffffffffu, up8 ? kl[0] : kl[1], 8);
+      df_add(th, tl, rh, rl);
+    }
+#pragma unroll
+    for (int o = 4; o >= 1; o >>= 1) {
+      const float rh = __shfl_xor_sync(0xffffffffu, th, o);
+      const float rl = __shfl_xor_sync(0xffffffffu, tl, o);
+      df_add(th, tl, rh, rl);
+    }
+    if ((lane & 7) == 0) pp[slot0 + (lane >> 3)][wid] = make_float2(th, tl);
   }
 }
 
@@ -581,9 +616,7 @@ __device__ __forceinline__ void sweep_all_rows(const VecCtx &c, int b, int nrows
     const int nt = min(32, nrows - t0);
     float2 (*pp)[VEC_THREADS / 32] = part[(t0 >> 5) & 1];
     const int itop = nrows - 1 - t0;
-    // rows in flight per trip: 2 with the lo halves (8 loads of 16 bytes per
-    // thread), 4 without; more would spill
-    constexpr int RR = LO ? 2 : 4;
+    constexpr int RR = 4;   // rows in flight per trip
     int r = 0;
     for (; r + RR <= nt; r += RR)
       sweep_rows<LO, CORR, RR>(c, b, itop - r, ebase, cs, gs, vh, vl, corr, cv, pp, r, lane, wid);
@@ -662,15 +695,16 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
 
   const size_t voff = (size_t)b * c.N;
   // v is kept as the float pair (vh, vl), 48 bits: the projections are
-  // computed for exactly that vector, and it is what the next step carries
-  double qt[8];
+  // computed for exactly that vector, and it is what the next step carries.
+  // q~_j = w_{j-1} / beta_j is read again after the row loop rather than
+  // held in registers through it.
   float vh[8], vl[8], corr[8], cv[8];
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     const int e = ebase + 128 * u;
+    double qt[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      qt[4 * u + t] = 0.0;
       vh[4 * u + t] = 0.0f;
       vl[4 * u + t] = 0.0f;
       corr[4 * u + t] = 0.0f;
@@ -687,7 +721,7 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
       const double av[4] = {a0.x, a0.y, a1.x, a1.y};
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        qt[4 * u + t] = wq[t] * sinv;
+        qt[t] = wq[t] * sinv;
         uu[t] = av[t] * sinv;
       }
     } else {
@@ -698,9 +732,9 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
       const float ku[4] = {uk.x, uk.y, uk.z, uk.w};
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        qt[4 * u + t] = wq[t] * sinv;
+        qt[t] = wq[t] * sinv;
         // C q~ = Delta^2 q~ + c_K Delta^1/2 L L^T Delta^1/2 q~   (Eq. 4)
-        uu[t] = fma(dd[t], qt[4 * u + t], (double)ku[t]);
+        uu[t] = fma(dd[t], qt[t], (double)ku[t]);
       }
     }
     double qp[4] = {0.0, 0.0, 0.0, 0.0};
@@ -716,7 +750,7 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int m = 4 * u + t;
-      const double vd = fma(-bj, qp[t], fma(-alpha, qt[m], uu[t]));
+      const double vd = fma(-bj, qp[t], fma(-alpha, qt[t], uu[t]));
       vh[m] = __double2float_rn(vd);
       vl[m] = __double2float_rn(vd - (double)vh[m]);
     }
@@ -736,12 +770,15 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
     if (e >= c.N) continue;
     float qh4[4], ql4[4];
     double vd[4];
+    const double2 w0 = *reinterpret_cast<const double2 *>(c.wv + voff + e);
+    const double2 w1 = *reinterpret_cast<const double2 *>(c.wv + voff + e + 2);
+    const double wq[4] = {w0.x, w0.y, w1.x, w1.y};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int m = 4 * u + t;
       vd[t] = ((double)vh[m] + (double)vl[m]) - (double)cv[m];   // w_j = v - Q_{j-1} g
       vh[m] = __double2float_rn(vd[t]);
-      const double qj = qt[m] - (double)corr[m];
+      const double qj = wq[t] * sinv - (double)corr[m];
       qh4[t] = __double2float_rn(qj);
       ql4[t] = __double2float_rn(qj - (double)qh4[t]);
       hj = fma(qj, vd[t], hj);

@@ -965,6 +965,173 @@ void estimate_interval(lgw_handle *h, const SysDev &s, int k_est, double &lo, do
   }
 }
 
+// Band Lanczos over the request's targets (band width p = n_t): one
+// recurrence per summed orbital g, started from [b_{t,g} over t].  Outputs
+// the banded T, R0 and the step counts: Tb [G][k][p+1], R0 [G][p][p],
+// keff [G] (device).  FP64 basis, CGS2; FP64 or BF16 contractions.
+void run_band(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o, double *Tb,
+              double *R0, int *keff, double *tacc) {
+  cudaStream_t &st = h->stream;
+  const int p = pv.n_t, G = pv.n_m, k = o.k;
+  const bool tc = o.precision != LGW_FP64;
+  int nsub_req = o.b_sub > 0 ? std::min(o.b_sub, G) : std::min(G, 512);
+  int Bs = round_up(nsub_req, PAD_VEC);
+  if (tc) Bs = std::max(Bs, 64);
+  const int N = s.N;
+  const int nchunks = (N + VEC_CHUNK - 1) / VEC_CHUNK;
+  const int kmax1 = k + 1;
+  LGW_TRY_CUDA(h, cudaMemsetAsync(Tb, 0, sizeof(double) * (size_t)G * k * (p + 1), st));
+  LGW_TRY_CUDA(h, cudaMemsetAsync(R0, 0, sizeof(double) * (size_t)G * p * p, st));
+  LGW_TRY_CUDA(h, cudaMemsetAsync(keff, 0, sizeof(int) * (size_t)G, st));
+  BandCtx bc{};
+  VecCtx &c = bc.c;
+  c.N = N;
+  c.Bs = Bs;
+  c.nchunks = nchunks;
+  c.k = k;
+  c.kmax1 = kmax1;
+  c.reorth = LGW_REORTH_CGS2;
+  c.ring = 0;
+  c.nslots = k;
+  c.tol = o.tol;
+  c.Delta2 = s.Delta2;
+  c.dsq = s.dsq;
+  c.cd = s.cd;
+  c.dsqf = s.dsqf;
+  c.d2f = s.d2f;
+  c.kf = s.kf;
+  c.w = wsT<double>(h, "w", (size_t)Bs * N);
+  c.basis = wsT<double>(h, "basis", (size_t)k * Bs * N);
+  c.xh = tc ? wsT<__nv_bfloat16>(h, "xh", (size_t)Bs * N) : nullptr;
+  c.dot_part = wsT<double>(h, "dot_part", (size_t)Bs * nchunks * kmax1);
+  c.h = wsT<double>(h, "hcoef", (size_t)Bs * kmax1);
+  c.norm_a = wsT<double>(h, "norm_a", (size_t)Bs * nchunks);
+  c.norm_b = wsT<double>(h, "norm_b", (size_t)Bs * nchunks);
+  c.norm_c = wsT<double>(h, "norm_c", (size_t)Bs * nchunks);
+  c.status = h->d_status;
+  bc.p = p;
+  bc.G = G;
+  bc.nv = wsT<int>(h, "band_nv", (size_t)Bs);
+  bc.act = wsT<int>(h, "band_act", (size_t)Bs);
+  bc.newrow = wsT<int>(h, "band_newrow", (size_t)Bs);
+  bc.inv = wsT<double>(h, "band_inv", (size_t)Bs);
+  bc.scale = wsT<double>(h, "band_scale", (size_t)Bs);
+  bc.tmax = wsT<double>(h, "band_tmax", (size_t)Bs);
+  bc.hsum = wsT<double>(h, "band_hsum", (size_t)Bs * kmax1);
+  bc.Tb = Tb;
+  bc.R0 = R0;
+  bc.keff = keff;
+  bc.xq = tc ? nullptr : wsT<double>(h, "band_xq", (size_t)Bs * N);
+
+  double *Y64 = wsT<double>(h, "y64", (size_t)Bs * s.A);
+  const int splits64 = gemm1_f64_splits(s, Bs);
+  double *Yp64 = tc ? nullptr : wsT<double>(h, "yp64", (size_t)splits64 * Bs * s.A);
+  float *ucd_buf = tc ? wsT<float>(h, "ucd", (size_t)Bs * N) : nullptr;
+  TcPlan *plan = nullptr;
+  float *Yp32 = nullptr;
+  __nv_bfloat16 *Yh = nullptr;
+  int splits_tc = 1;
+  if (tc) {
+    Yp32 = wsT<float>(h, "yp32", (size_t)64 * Bs * s.A);
+    Yh = wsT<__nv_bfloat16>(h, "yh", (size_t)Bs * s.A);
+    char err[256];
+    plan = tc_plan_create(s, Bs, c.xh, Yp32, Yh, &splits_tc, err, sizeof err);
+    if (!plan) {
+      set_err(h, LGW_ERR_CUDA, "%s", err);
+      throw Fail{LGW_ERR_CUDA};
+    }
+    if (!tc_plan_has_bf16(plan)) {
+      tc_plan_destroy(plan);
+      set_err(h, LGW_ERR_UNSUPPORTED, "BF16 contractions need the BF16 copies of L");
+      throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    if (!tc_plan_autotune(plan, ucd_buf, h->d_status, st, &splits_tc)) {
+      tc_plan_destroy(plan);
+      set_err(h, LGW_ERR_CUDA, "tensor-core tile autotuning failed");
+      throw Fail{LGW_ERR_CUDA};
+    }
+  }
+  struct PlanGuard {
+    TcPlan *p;
+    ~PlanGuard() {
+      if (p) tc_plan_destroy(p);
+    }
+  } guard{plan};
+  Timer tm(h);
+  for (int vec0 = 0; vec0 < G; vec0 += nsub_req) {
+    const int nvec = std::min(nsub_req, G - vec0);
+    c.vec0 = vec0;
+    c.nvec = nvec;
+    launch_band_init(bc, st);
+    check_launch(h, "band_init");
+    // ---- the start block, one target's vectors at a time (text after Eq. 8) ----
+    for (int a = 0; a < p; ++a) {
+      tm.mark(C_START);
+      const size_t row0 = (size_t)a * G + vec0;
+      if (pv.d_M && tc) {
+        if (!launch_coupling_tc(plan, s, pv.d_M + row0 * s.n_aux, nvec, ucd_buf, h->d_status, st)) {
+          set_err(h, LGW_ERR_UNSUPPORTED, "tensor-core plan without the BF16 copies of L");
+          throw Fail{LGW_ERR_UNSUPPORTED};
+        }
+        check_launch(h, "coupling_tc");
+        launch_start_from_vf(c, ucd_buf, st);
+        check_launch(h, "start_from_vf");
+      } else if (pv.d_M) {
+        if (!s.L64) {
+          set_err(h, LGW_ERR_UNSUPPORTED, "start vectors from M need the BF16 or FP64 copy of L");
+          throw Fail{LGW_ERR_UNSUPPORTED};
+        }
+        LGW_TRY_CUDA(h, cudaMemsetAsync(Y64, 0, sizeof(double) * Bs * s.A, st));
+        LGW_TRY_CUDA(h, cudaMemcpy2DAsync(Y64, sizeof(double) * s.A, pv.d_M + row0 * s.n_aux,
+                                          sizeof(double) * s.n_aux, sizeof(double) * s.n_aux,
+                                          nvec, cudaMemcpyDeviceToDevice, st));
+        launch_gemm2_f64(s, Y64, Bs, EPI_START, nullptr, nullptr, nullptr, c.w, nullptr, st);
+        check_launch(h, "gemm2_f64(start)");
+      } else {
+        launch_start_from_v(c, pv.d_V + row0 * s.n_vc, s.n_vc, s.n_vc, st);
+        check_launch(h, "start_from_v");
+      }
+      tm.mark(C_DOTS);
+      launch_band_activate(bc, 0, a, st);
+      h->launches += launch_band_append(bc, 0, a, st);
+      check_launch(h, "band_append(start)");
+    }
+    // ---- k steps: C q_j, projected out of all of the group's vectors ----
+    for (int j = 0; j < k; ++j) {
+      tm.mark(C_GEMM1);
+      launch_band_activate(bc, 1, j, st);
+      launch_band_operand(bc, j, st);
+      check_launch(h, "band_operand");
+      if (tc) {
+        launch_gemm1_tc(plan, h->d_status, st);
+        check_launch(h, "gemm1_tc");
+        launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, nullptr, st);
+        check_launch(h, "reduce_y");
+        tm.mark(C_GEMM2);
+        launch_gemm2_tc_split(plan, ucd_buf, h->d_status, st);
+        check_launch(h, "gemm2_tc");
+        launch_band_assemble(bc, j, ucd_buf, st);
+        check_launch(h, "band_assemble");
+      } else {
+        launch_gemm1_f64(s, bc.xq, Bs, Yp64, splits64, st);
+        check_launch(h, "gemm1_f64");
+        launch_reduce_y_f64(Yp64, splits64, Bs, s.A, Y64, st);
+        check_launch(h, "reduce_y_f64");
+        tm.mark(C_GEMM2);
+        launch_gemm2_f64(s, Y64, Bs, EPI_APPLY, bc.xq, nullptr, nullptr, c.w, nullptr, st);
+        check_launch(h, "gemm2_f64");
+      }
+      tm.mark(C_DOTS);
+      h->launches += launch_band_append(bc, 1, j, st);
+      check_launch(h, "band_append");
+    }
+    launch_band_finish(bc, st);
+    check_launch(h, "band_finish");
+  }
+  tm.stop();
+  if (tacc) tm.collect(tacc, C_N);
+}
+
 void run_sigma(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o,
                const double *alpha, const double *beta, const double *beta0, const int *k_eff,
                double *sigma, double *e_qp, double *z_qp, lgw_report *rep, double *tacc,
@@ -1672,6 +1839,111 @@ lgw_status lgw_spectral_interval(lgw_handle *h, const lgw_system *sys, int32_t k
     estimate_interval(h, sys->s, k, *x_lo, *x_hi);
     check_status(h);
   } catch (Fail &f) {
+    return f.st;
+  }
+  return LGW_OK;
+}
+
+lgw_status lgw_sigma_band(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                          const lgw_options *o, double *sigma, lgw_report *rep) {
+  lgw_status g = guard_handle(h);
+  if (g != LGW_OK) return g;
+  if (!sys || sys->h != h || !sigma) return set_err(h, LGW_ERR_ARG, "bad arguments to lgw_sigma_band");
+  try {
+    const SysDev &s = sys->s;
+    cudaStream_t st = h->stream;
+    h->launches = 0;
+    h->ev_used = 0;
+    h->timing = rep != nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (rep) {
+      std::memset(rep, 0, sizeof *rep);
+      LGW_TRY_CUDA(h, cudaEventCreate(&t0));
+      LGW_TRY_CUDA(h, cudaEventCreate(&t1));
+      LGW_TRY_CUDA(h, cudaEventRecord(t0, st));
+    }
+    LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    Opts op = resolve_opts(h, o, s);
+    if (op.precision == LGW_FP8) {
+      set_err(h, LGW_ERR_UNSUPPORTED, "band Lanczos runs FP64 or BF16 contractions");
+      throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    if (op.k > 512) {
+      set_err(h, LGW_ERR_UNSUPPORTED, "band Lanczos: k = %d above its 512-step limit", op.k);
+      throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    ensure_copies(h, sys, op);
+    ProbView pv = check_problem(h, s, p);
+    const int P = pv.n_t, G = pv.n_m, F = pv.n_freq, k = op.k;
+    if (P < 1 || P > 8) {
+      set_err(h, LGW_ERR_UNSUPPORTED, "band Lanczos: n_t = %d targets, 1..8 supported", P);
+      throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    OutBuf<double> out;
+    out.init(h, "out_sigma_band", sigma, (size_t)P * P * F * 2);
+    double tacc[C_N] = {0};
+    if (G > 0 && F > 0) {
+      double *Tb = wsT<double>(h, "band_T", (size_t)G * k * (P + 1));
+      double *R0 = wsT<double>(h, "band_R0", (size_t)G * P * P);
+      int *keff = wsT<int>(h, "band_keff", (size_t)G);
+      run_band(h, s, pv, op, Tb, R0, keff, rep ? tacc : nullptr);
+      // polarisation vectors of the small problem: e_a, then e_a +- e_b
+      const int nx = P + P * (P - 1);
+      std::vector<double> xs((size_t)nx * P, 0.0);
+      for (int a = 0; a < P; ++a) xs[(size_t)a * P + a] = 1.0;
+      int q = 0;
+      for (int a = 0; a < P; ++a)
+        for (int b = a + 1; b < P; ++b, ++q) {
+          double *xp = &xs[(size_t)(P + 2 * q) * P], *xm = xp + P;
+          xp[a] = xm[a] = 1.0;
+          xp[b] = 1.0;
+          xm[b] = -1.0;
+        }
+      const double *dxs = in_dev(h, "band_xs", xs.data(), xs.size());
+      const int Bx = nx * G;
+      double *a2 = wsT<double>(h, "co_alpha", (size_t)Bx * k);
+      double *b2 = wsT<double>(h, "co_beta", (size_t)Bx * k);
+      double *b02 = wsT<double>(h, "co_beta0", (size_t)Bx);
+      int *ke2 = wsT<int>(h, "co_keff", (size_t)Bx);
+      double *scr = wsT<double>(h, "band_small", (size_t)Bx * (k + 2) * k);
+      launch_band_small(Tb, R0, keff, G, k, P, dxs, nx, op.tol, scr, a2, b2, b02, ke2, st);
+      check_launch(h, "band_small");
+      ProbView pv3 = pv;
+      pv3.n_t = nx;
+      pv3.B = Bx;
+      pv3.d_targets = nullptr;
+      pv3.d_shift = nullptr;
+      double *sigx = wsT<double>(h, "band_sigx", (size_t)nx * F * 2);
+      run_sigma(h, s, pv3, op, a2, b2, b02, ke2, sigx, nullptr, nullptr, rep, tacc);
+      launch_band_combine(sigx, P, F, out.dev, st);
+      check_launch(h, "band_combine");
+    } else if (out.dev) {
+      LGW_TRY_CUDA(h, cudaMemsetAsync(out.dev, 0, sizeof(double) * (size_t)P * P * F * 2, st));
+    }
+    out.finish(h);
+    if (rep) {
+      LGW_TRY_CUDA(h, cudaEventRecord(t1, st));
+      LGW_TRY_CUDA(h, cudaEventSynchronize(t1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      rep->ms_total = ms;
+      rep->ms_start = tacc[C_START];
+      rep->ms_gemm1 = tacc[C_GEMM1];
+      rep->ms_gemm2 = tacc[C_GEMM2];
+      rep->ms_dots = tacc[C_DOTS];
+      rep->ms_spectral = tacc[C_SPEC];
+      rep->ms_cf = tacc[C_CF];
+      rep->n_vectors = G;
+      rep->gemm_flops = 4.0 * s.n_vc * (double)s.n_aux * (double)G * (double)k;
+      rep->gpu_launches = h->launches;
+      rep->k_min = rep->k_max = k;
+    }
+    check_status(h);
+    h->timing = false;
+  } catch (Fail &f) {
+    h->timing = false;
     return f.st;
   }
   return LGW_OK;

@@ -252,6 +252,46 @@ void launch_reduce_dots(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_update(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_dots(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_second_pass_decide_j(const VecCtx &c, int j, cudaStream_t st);
+// Band Lanczos (off-diagonal Sigma_tt'): one recurrence per group (a summed
+// orbital) whose start block holds the p targets' vectors; one new basis
+// vector per step, CGS2 against all of the group's vectors, FP64 basis.
+struct BandCtx {
+  VecCtx c;          // groups as the sub-batch's vectors: basis (ring 0), w, xh,
+                     // dot_part, h, norm_a/b/c, vec0, nvec, k, kmax1, tol
+  int p;             // band width (targets)
+  int G;             // groups of the whole request
+  int *nv;           // [Bs] basis vectors formed
+  int *act;          // [Bs] the group takes part in the current operation
+  int *newrow;       // [Bs] row the current operation appends, or -1
+  double *inv;       // [Bs] 1 / norm of the appended vector
+  double *hsum;      // [Bs][kmax1] projection coefficients of both passes
+  double *scale;     // [Bs] largest start-vector norm (breakdown scale of the start)
+  double *tmax;      // [Bs] largest |T| entry so far (breakdown scale of the steps)
+  double *Tb;        // [G][k][p+1] Tb[g][j][d] = T[j+d][j]
+  double *R0;        // [G][p][p]   b_a = sum_i R0[g][i][a] q_i
+  int *keff;         // [G]         steps (columns of T) taken
+  double *xq;        // [Bs][N] FP64 operand for the FP64 contractions, or null
+};
+void launch_band_init(const BandCtx &bc, cudaStream_t st);
+void launch_band_activate(const BandCtx &bc, int mode, int j, cudaStream_t st);
+void launch_band_operand(const BandCtx &bc, int j, cudaStream_t st);
+void launch_band_assemble(const BandCtx &bc, int j, const float *ucd, cudaStream_t st);
+// one orthogonalise-and-append: CGS2 of w against the group's vectors, the
+// coefficient record (mode 0: column idx of R0; mode 1: column idx of T),
+// breakdown test and the new basis vector
+// the new basis vector; returns the number of kernels launched
+int launch_band_append(const BandCtx &bc, int mode, int idx, cudaStream_t st);
+void launch_band_finish(const BandCtx &bc, cudaStream_t st);
+// Lanczos on each group's small banded T from y = R0 x for the nx
+// polarisation vectors x [nx][p]; output tridiagonals [nx * G][k] (vector
+// index xi * G + g); scratch: nx * G * (k + 2) * k doubles
+void launch_band_small(const double *Tb, const double *R0, const int *keff, int G, int k, int p,
+                       const double *xs, int nx, double tol, double *scratch, double *alpha,
+                       double *beta, double *beta0, int *keff_out, cudaStream_t st);
+// out [p][p][F][2] from the nx fraction sums sig [nx][F][2]: diagonal a from
+// x = a, pair (a, b) from (x+ - x-) / 4
+void launch_band_combine(const double *sig, int p, int F, double *out, cudaStream_t st);
+
 // k_reorth.cu : split-precision basis (double-float dots, FP32 small updates)
 void launch_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st);
 void launch_reduce_dots_split(const VecCtx &c, int j, int pass, cudaStream_t st);

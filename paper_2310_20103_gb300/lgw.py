@@ -397,6 +397,24 @@ def lgw_sigma_c_poly(h: Handle, s: System, problem: Problem, options: Options, g
     return rep.as_dict() if report else None
 
 
+def lgw_sigma_band(h: Handle, s: System, problem: Problem, options: Options, sigma,
+                   report: bool = False) -> Optional[dict]:
+    """Sigma_tt'(omega) of the request's targets by band Lanczos:
+    sigma [n_t][n_t][n_freq][2]."""
+    lib = load_library()
+    fn = lib.lgw_sigma_band
+    if fn.argtypes is None:
+        P = ctypes.c_void_p
+        fn.argtypes = [P, P, ctypes.POINTER(lgw_problem), ctypes.POINTER(lgw_options), P,
+                       ctypes.POINTER(lgw_report)]
+        fn.restype = ctypes.c_int32
+    p, o = problem.to_c(), options.to_c()
+    rep = lgw_report()
+    _check(h, fn(h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), _ptr(sigma, "f64"),
+                 ctypes.byref(rep) if report else None))
+    return rep.as_dict() if report else None
+
+
 def lgw_spectral_interval(h: Handle, s: System, k: int = 32):
     """(x_lo, x_hi) around the spectrum of C for the polynomial fit."""
     lib = load_library()
