@@ -336,7 +336,8 @@ lgw_status lgw_sigma_c(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
  * continued fractions of D's tridiagonal (Eq. 14), z = omega - eps_m - i eta
  * delta.  Outputs as lgw_sigma_c; the report's gemm_flops count g products
  * per step.  x_lo = x_hi = 0 asks the library for the interval
- * (lgw_spectral_interval with k = 32, one extra synchronisation). */
+ * (lgw_spectral_interval with k = 32; estimated once per system, on the
+ * first such call, with one synchronisation, then kept with the system). */
 typedef struct {
   int32_t g;           /* degree, 1..256 */
   double x_lo, x_hi;   /* 0 < x_lo < x_hi, or both 0 */
@@ -347,8 +348,9 @@ typedef struct {
  *   x_lo = min over pairs of Delta^2 = (eps_c - eps_v)^2, a lower bound of
  *          lambda_min because C = Delta^2 + c_K Delta^1/2 L L^T Delta^1/2
  *          adds a positive semidefinite term;
- *   x_hi = the largest Ritz value of k Lanczos steps (Eq. 13, CGS2; FP64
- *          contractions when the system keeps its FP64 copy, else BF16)
+ *   x_hi = the largest Ritz value of k Lanczos steps (Eq. 13, CGS2; BF16
+ *          tensor-core contractions when the system has its BF16 copies,
+ *          else FP64)
  *          from a fixed pseudo-random start vector, plus that step's beta,
  *          the residual norm, which bounds the distance from the Ritz value
  *          to an eigenvalue of C.  The largest Ritz value converges to

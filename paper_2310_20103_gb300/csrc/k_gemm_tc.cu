@@ -431,6 +431,164 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// Persistent form of the store-only contraction (ucd = c_K Delta^1/2 L y,
+// the E_SPLITB epilogue): one CTA per SM walks the output tiles in launch
+// order with the grid as stride.  Two TMEM accumulators (2 x BN columns)
+// alternate, so the four epilogue warps drain tile i's accumulator while the
+// MMA thread fills the other one with tile i + 1; the stage ring and its
+// barrier phases run on across tiles, so TMA loads of the next tile start
+// during the current tile's last MMAs.  Per output element the K order (the
+// rotation by the M tile) is the one of k_gemm_tc, so results are
+// bit-identical.  Every wait is bounded; on a timeout the loops stop, the
+// producer still waits (bounded) for its own copies, and TMEM is freed.
+template <int BN, int EB>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm_persist(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   int M, int Ncols, int num_kb, EpiArgs ea) {
+  using C = Cfg<BN, 0>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE);
+  uint64_t *empty = full + C::STAGES;
+  uint64_t *tfull = empty + C::STAGES;   // [2] accumulator a holds a finished tile
+  uint64_t *tempty = tfull + 2;          // [2] the epilogue has drained accumulator a
+  uint64_t *mdone = tempty + 2;          // every MMA issued by the CTA has completed
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(mdone + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tiles = (Ncols + BN - 1) / BN;
+  const int m_tiles = (M + BM - 1) / BM;
+  const int total = m_tiles * n_tiles;
+  const int nk = num_kb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);   // one arrival per epilogue warp
+    }
+    mbar_init(mdone, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tslot, 2 * C::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  auto tile_of = [&](int t, int &m_tile, int &n_tile) {
+    if (ea.mfast) {
+      m_tile = t % m_tiles;
+      n_tile = t / m_tiles;
+    } else {
+      m_tile = t / n_tiles;
+      n_tile = t % n_tiles;
+    }
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0, issued = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        int m_tile, n_tile;
+        tile_of(t, m_tile, n_tile);
+        for (int kk = 0; kk < nk; ++kk, ++it) {
+          const int s = it % C::STAGES;
+          const uint32_t ph = (it / C::STAGES) & 1;
+          if (!mbar_wait(&empty[s], ph ^ 1, ea.status)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], C::STAGE);
+          uint8_t *sa = smem + s * C::STAGE;
+          const int kb = (kk + (ea.rot ? m_tile : 0)) % nk;
+          const int kx = kb * (BK * 2 / EB);
+          tma_load_2d(sa, &tmA, &full[s], kx, m_tile * BM);
+          tma_load_2d(sa + C::A_BYTES, &tmB, &full[s], kx, n_tile * BN);
+          issued = it + 1;
+        }
+      }
+      // every issued copy must have landed before the CTA may exit
+      for (int i = max(0, issued - C::STAGES); i < issued; ++i)
+        mbar_wait(&full[i % C::STAGES], (i / C::STAGES) & 1, ea.status);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = EB == 2 ? make_idesc(BM, BN) : make_idesc_e4m3(BM, BN);
+      int it = 0, i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
+        const int a = i & 1, use = i >> 1;
+        if (use > 0 && !mbar_wait(&tempty[a], (use - 1) & 1, ea.status)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(a * BN);
+        for (int kk = 0; kk < nk; ++kk, ++it) {
+          const int s = it % C::STAGES;
+          const uint32_t ph = (it / C::STAGES) & 1;
+          if (!mbar_wait(&full[s], ph, ea.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * C::STAGE);
+          const uint64_t da = make_sdesc(sa), db = make_sdesc(sa + C::A_BYTES);
+#pragma unroll
+          for (int q = 0; q < BK / 16; ++q)
+            if (EB == 2)
+              umma_bf16(acc, da + 2 * q, db + 2 * q, idesc, (kk > 0 || q > 0) ? 1u : 0u);
+            else
+              umma_e4m3(acc, da + 2 * q, db + 2 * q, idesc, (kk > 0 || q > 0) ? 1u : 0u);
+          umma_commit(&empty[s]);
+        }
+        if (ok) umma_commit(&tfull[a]);
+      }
+      // no MMA may still write TMEM when it is freed (also after a timeout)
+      umma_commit(mdone);
+      mbar_wait(mdone, 0, ea.status);
+    }
+  } else {
+    // ------------------------------ epilogue ------------------------------
+    const int qd = warp & 3;
+    int i = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+      const int a = i & 1, use = i >> 1;
+      if (!mbar_wait(&tfull[a], use & 1, ea.status)) break;
+      tc_fence_after();
+      int m_tile, n_tile;
+      tile_of(t, m_tile, n_tile);
+      const int row = m_tile * BM + qd * 32 + lane;
+      const int ncol0 = n_tile * BN;
+      const float cdf = row < M ? ea.cdf[row] : 0.f;
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(qd * 32) << 16) + (uint32_t)c0, r);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int col = ncol0 + c0 + q;
+          if (col < Ncols && row < M) {
+            const float cs = ea.colscale ? ea.colscale[col] : 1.0f;
+            ea.ucd[kblk_f32(col, row, Ncols)] = cdf * (cs * __uint_as_float(r[q]));
+          }
+        }
+      }
+      // the accumulator may be refilled once all four warps have read it
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[a]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 2 * C::TMEM_COLS);
+  }
+}
+
 // Yh = bf16(sum_p Ypart[p]) in fixed order; optionally per-block partials of
 // sum_mu y_mu Yh_mu (grid: A/256 blocks per vector row).
 __global__ void k_reduce_y_bf16(const float *__restrict__ Ypart, int splits, int Bs, int A,
@@ -502,7 +660,8 @@ struct TcPlan {
   int BN1, BN2;   // N tile of gemm1 / gemm2 (and the coupling products)
   int rot1 = 1;   // gemm1 K-start rotation (tuned); gemm2 always rotates
   int mfast2 = 0; // gemm2 tile numbering (EpiArgs::mfast), tuned
-  int half2 = 0;  // gemm2 with the half-depth pipeline (two CTAs per SM), tuned
+  int half2 = 0;  // gemm2 pipeline, tuned: 0 one CTA per tile, 1 half depth (two CTAs
+                  // per SM), 2 persistent with two TMEM accumulators
   const __nv_bfloat16 *xh;
   int N, A, Bs;
   int splits, kb_per_split;
@@ -659,12 +818,41 @@ static void launch_tc(const CUtensorMap &A, const CUtensorMap &B, int M, int Nco
                                                                         kb_per_split, ea);
 }
 
-// half: the half-depth pipeline (two CTAs per SM), store-only epilogue only
+template <int BN, int EB>
+static void launch_persist(const CUtensorMap &A, const CUtensorMap &B, int M, int Ncols,
+                           int num_kb, const tc::EpiArgs &ea, cudaStream_t st) {
+  using C = tc::Cfg<BN, 0>;
+  static bool attr_done = false;
+  static int nsm = 0;
+  if (!attr_done) {
+    cudaFuncSetAttribute(tc::k_gemm_persist<BN, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         C::SMEM);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    attr_done = true;
+  }
+  const int total = ((M + tc::BM - 1) / tc::BM) * ((Ncols + BN - 1) / BN);
+  const int grid = std::max(1, std::min(total, nsm > 0 ? nsm : 148));
+  tc::k_gemm_persist<BN, EB><<<grid, tc::NTHREADS, C::SMEM, st>>>(A, B, M, Ncols, num_kb, ea);
+}
+
+// half: 1 = the half-depth pipeline (two CTAs per SM), 2 = the persistent
+// kernel with two accumulators; store-only epilogue only
 template <int EPI, int EB = 2>
 static void dispatch_bn(int BN, const CUtensorMap &A, const CUtensorMap &B, int M, int Ncols,
                         int num_kb, int kb_per_split, int splits, const tc::EpiArgs &ea,
                         cudaStream_t st, int half = 0) {
   if constexpr (EPI == tc::E_SPLITB) {
+    if (half == 2 && splits == 1 && kb_per_split == num_kb) {
+      if (BN == 256)
+        launch_persist<256, EB>(A, B, M, Ncols, num_kb, ea, st);
+      else if (BN == 128)
+        launch_persist<128, EB>(A, B, M, Ncols, num_kb, ea, st);
+      else
+        launch_persist<64, EB>(A, B, M, Ncols, num_kb, ea, st);
+      return;
+    }
     if (half) {
       if (BN == 256)
         launch_tc<256, EPI, EB, 1>(A, B, M, Ncols, num_kb, kb_per_split, splits, ea, st);
@@ -909,9 +1097,20 @@ float time_best(F &&f, cudaStream_t st) {
 }
 }  // namespace
 
+// LGW_GEMM2_PIPE = 0, 1 or 2 forces GEMM2's pipeline variant (one CTA per
+// tile, half depth, persistent) after tuning; every variant gives the same
+// bits, so this only serves tests and measurements.
+static void apply_gemm2_override(TcPlan *p) {
+  const char *e = getenv("LGW_GEMM2_PIPE");
+  if (e && e[0] >= '0' && e[0] <= '2' && e[1] == '\0') p->half2 = e[0] - '0';
+}
+
 bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, int *splits_out) {
   const char *env = getenv("LGW_AUTOTUNE");
-  if (env && env[0] == '0') return true;
+  if (env && env[0] == '0') {
+    apply_gemm2_override(p);
+    return true;
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   const TuneKey key{dev, p->N, p->A, p->Bs, p->fp8 ? 1 : 0};
@@ -924,6 +1123,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
       p->rot1 = it->second.rot1;
       p->mfast2 = it->second.mfast2;
       p->half2 = it->second.half2;
+      apply_gemm2_override(p);
       plan_set_splits(p, it->second.splits);
       if (splits_out) *splits_out = p->splits;
       return plan_encode_b(p);
@@ -981,7 +1181,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
     float t2_best = t2_def;
     for (int bn = 64; bn <= bn_max; bn *= 2)
       for (int mf = 0; mf <= 1; ++mf)
-        for (int hf = 0; hf <= 1; ++hf) {
+        for (int hf = 0; hf <= 2; ++hf) {
           if (bn == def.BN2 && mf == def.mfast2 && hf == def.half2) continue;
           p->BN2 = bn;
           p->mfast2 = mf;
@@ -1009,6 +1209,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = best;
   }
+  apply_gemm2_override(p);
   if (splits_out) *splits_out = p->splits;
   return cudaGetLastError() == cudaSuccess;
 }

@@ -505,123 +505,149 @@ __global__ void __launch_bounds__(VEC_THREADS) k_start_split(VecCtx c) {
 // and across the eight warps through shared memory, 32 rows at a time.
 // ===========================================================================
 
-// Rows i_top, i_top - 1, ..., i_top - R + 1 of vector b: loads first (4R
-// independent 128-bit loads per thread), then the products; the R row
-// partials of the warp are reduced together (R = 4: a transposed butterfly,
-// 12 shuffles for four rows instead of 40).
-template <bool LO, bool CORR, int R>
-__device__ __forceinline__ void sweep_rows(const VecCtx &c, int b, int i_top, int ebase,
-                                           const float *cs, const float *gs,
-                                           const float (&vh)[8], const float (&vl)[8],
-                                           float (&corr)[8], float (&cv)[8],
-                                           float2 (*pp)[VEC_THREADS / 32], int slot0, int lane,
-                                           int wid) {
-  static_assert(R == 1 || R == 4, "row groups of 1 or 4");
-  float4 hq[R][2], lq[R][2];
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const float *qh = bhi_row(c, i_top - q, b);
-    const float *ql = LO ? blo_row(c, i_top - q, b) : nullptr;
+// ---------------------------------------------------------------------------
+// Row staging for the sweep: every thread copies the 8 elements of each row
+// that it consumes (hi and lo, four 16-byte pieces) into its own slots of a
+// shared-memory ring with cp.async, SW_SLOTS rows ahead, and reads them back
+// two rows at a time.  No thread reads another's slots, so the ring needs
+// no barrier; memory parallelism no longer competes with registers
+// (4 rows x 64 bytes in flight per thread while 2 rows are computed).
+// ---------------------------------------------------------------------------
+constexpr int SW_SLOTS = 6;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Staging bytes per block.
+template <bool LO>
+__host__ __device__ constexpr size_t sweep_stage_bytes() {
+  return (size_t)SW_SLOTS * (LO ? 4 : 2) * VEC_THREADS * sizeof(float4);
+}
+
+// Sequence index r (row nrows - 1 - r) into slot r % SW_SLOTS; one commit
+// group per index, empty past the last row.
+template <bool LO>
+__device__ __forceinline__ void stage_row(const VecCtx &c, int b, int r, int nrows, int ebase,
+                                          float4 *stg) {
+  constexpr int NV = LO ? 4 : 2;
+  if (r < nrows) {
+    const int i = nrows - 1 - r;
+    float4 *slot = stg + (size_t)(r % SW_SLOTS) * NV * VEC_THREADS + threadIdx.x;
+    const float *qh = bhi_row(c, i, b);
+    const float *ql = LO ? blo_row(c, i, b) : nullptr;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int e = ebase + 128 * u;
       if (e < c.N) {
-        hq[q][u] = __ldg(reinterpret_cast<const float4 *>(qh + e));
-        lq[q][u] = LO ? __ldg(reinterpret_cast<const float4 *>(ql + e))
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        cp_async16(slot + u * VEC_THREADS, qh + e);
+        if (LO) cp_async16(slot + (2 + u) * VEC_THREADS, ql + e);
       } else {
-        hq[q][u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        lq[q][u] = hq[q][u];
+        slot[u * VEC_THREADS] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (LO) slot[(2 + u) * VEC_THREADS] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
   }
-  float sh[R], sl[R];
+  cp_async_commit();
+}
+
+// Products of one staged row with v: double-float partial of q_i . v and,
+// with CORR, the delayed corrections corr += c_i q_i, cv += g_i q_i.
+template <bool LO, bool CORR>
+__device__ __forceinline__ void row_products(const float4 *slot, float cf, float gf,
+                                             const float (&vh)[8], const float (&vl)[8],
+                                             float (&corr)[8], float (&cv)[8], float &sh,
+                                             float &sl) {
+  sh = 0.f;
+  sl = 0.f;
 #pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const float cf = CORR ? cs[i_top - q] : 0.0f;
-    const float gf = CORR ? gs[i_top - q] : 0.0f;
-    sh[q] = 0.f;
-    sl[q] = 0.f;
+  for (int u = 0; u < 2; ++u) {
+    const float4 h4 = slot[u * VEC_THREADS];
+    const float4 l4 = LO ? slot[(2 + u) * VEC_THREADS] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float xa[4] = {h4.x, h4.y, h4.z, h4.w};
+    const float xb[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const float xa[4] = {hq[q][u].x, hq[q][u].y, hq[q][u].z, hq[q][u].w};
-      const float xb[4] = {lq[q][u].x, lq[q][u].y, lq[q][u].z, lq[q][u].w};
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int m = 4 * u + t;
-        if (CORR) {
-          corr[m] = fmaf(cf, xa[t], corr[m]);
-          cv[m] = fmaf(gf, xa[t], cv[m]);
-        }
-        const float pr = __fmul_rn(xa[t], vh[m]);
-        float err = __fmaf_rn(xa[t], vh[m], -pr);
-        err = __fmaf_rn(xa[t], vl[m], err);
-        if (LO) err = __fmaf_rn(xb[t], vh[m], err);
-        two_sum_acc(sh[q], sl[q], pr);
-        sl[q] = __fadd_rn(sl[q], err);
+    for (int t = 0; t < 4; ++t) {
+      const int m = 4 * u + t;
+      if (CORR) {
+        corr[m] = fmaf(cf, xa[t], corr[m]);
+        cv[m] = fmaf(gf, xa[t], cv[m]);
       }
+      const float pr = __fmul_rn(xa[t], vh[m]);
+      float err = __fmaf_rn(xa[t], vh[m], -pr);
+      err = __fmaf_rn(xa[t], vl[m], err);
+      if (LO) err = __fmaf_rn(xb[t], vh[m], err);
+      two_sum_acc(sh, sl, pr);
+      sl = __fadd_rn(sl, err);
     }
-  }
-  if (R == 1) {
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      const float rh = __shfl_xor_sync(0xffffffffu, sh[0], o);
-      const float rl = __shfl_xor_sync(0xffffffffu, sl[0], o);
-      df_add(sh[0], sl[0], rh, rl);
-    }
-    if (lane == 0) pp[slot0][wid] = make_float2(sh[0], sl[0]);
-  } else {
-    // lanes 16..31 keep rows 2, 3 and lanes 0..15 rows 0, 1; then lanes with
-    // bit 3 set keep the odd row; the rest is a plain butterfly over the 8
-    // lanes that share bits 3 and 4.  Row q ends in lane 8q.
-    const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
-    float kh[2], kl[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const float sendh = up16 ? sh[r] : sh[R - 2 + r], sendl = up16 ? sl[r] : sl[R - 2 + r];
-      kh[r] = up16 ? sh[R - 2 + r] : sh[r];
-      kl[r] = up16 ? sl[R - 2 + r] : sl[r];
-      const float rh = __shfl_xor_sync(0xffffffffu, sendh, 16);
-      const float rl = __shfl_xor_sync(0xffffffffu, sendl, 16);
-      df_add(kh[r], kl[r], rh, rl);
-    }
-    float th = up8 ? kh[1] : kh[0], tl = up8 ? kl[1] : kl[0];
-    {
-      const float rh = __shfl_xor_sync(0xffffffffu, up8 ? kh[0] : kh[1], 8);
-      const float rl = __shfl_xor_sync(0xffffffffu, up8 ? kl[0] : kl[1], 8);
-      df_add(th, tl, rh, rl);
-    }
-#pragma unroll
-    for (int o = 4; o >= 1; o >>= 1) {
-      const float rh = __shfl_xor_sync(0xffffffffu, th, o);
-      const float rl = __shfl_xor_sync(0xffffffffu, tl, o);
-      df_add(th, tl, rh, rl);
-    }
-    if ((lane & 7) == 0) pp[slot0 + (lane >> 3)][wid] = make_float2(th, tl);
   }
 }
 
-// All rows i = nrows - 1 down to 0 (the newest row first: the sweep has just
-// read it and it is still in L1).  Row partials of the block go to
-// dp[i] (one double per row); CORR also accumulates the delayed update.
+// All rows i = nrows - 1 down to 0 (the newest row first), two per trip.
+// Row partials of the block go to dp[i] (one double per row), through a
+// transposed butterfly over the warp (10 shuffles for the two rows) and a
+// fixed-order sum over the eight warps in shared memory, 32 rows at a time.
 template <bool LO, bool CORR>
 __device__ __forceinline__ void sweep_all_rows(const VecCtx &c, int b, int nrows, int ebase,
                                                const float *cs, const float *gs,
                                                const float (&vh)[8], const float (&vl)[8],
                                                float (&corr)[8], float (&cv)[8],
                                                float2 (*part)[32][VEC_THREADS / 32],
-                                               double *dp) {
+                                               double *dp, float4 *stg) {
+  constexpr int NV = LO ? 4 : 2;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int r = 0; r < SW_SLOTS; ++r) stage_row<LO>(c, b, r, nrows, ebase, stg);
   for (int t0 = 0; t0 < nrows; t0 += 32) {
     const int nt = min(32, nrows - t0);
     float2 (*pp)[VEC_THREADS / 32] = part[(t0 >> 5) & 1];
-    const int itop = nrows - 1 - t0;
-    constexpr int RR = 4;   // rows in flight per trip
-    int r = 0;
-    for (; r + RR <= nt; r += RR)
-      sweep_rows<LO, CORR, RR>(c, b, itop - r, ebase, cs, gs, vh, vl, corr, cv, pp, r, lane, wid);
-    for (; r < nt; ++r)
-      sweep_rows<LO, CORR, 1>(c, b, itop - r, ebase, cs, gs, vh, vl, corr, cv, pp, r, lane, wid);
+    for (int r = 0; r < nt; r += 2) {
+      const int rs = t0 + r;   // sequence indices rs, rs + 1 (rs + 1 may be past the end)
+      cp_async_wait<SW_SLOTS - 2>();
+      float sh[2], sl[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int rq = rs + q;
+        const int i = nrows - 1 - rq;
+        const bool real = rq < nrows;
+        const float cf = (CORR && real) ? cs[i] : 0.0f;
+        const float gf = (CORR && real) ? gs[i] : 0.0f;
+        const float4 *slot = stg + (size_t)(rq % SW_SLOTS) * NV * VEC_THREADS + threadIdx.x;
+        if (real) {
+          row_products<LO, CORR>(slot, cf, gf, vh, vl, corr, cv, sh[q], sl[q]);
+        } else {
+          sh[q] = 0.f;
+          sl[q] = 0.f;
+        }
+      }
+      stage_row<LO>(c, b, rs + SW_SLOTS, nrows, ebase, stg);
+      stage_row<LO>(c, b, rs + SW_SLOTS + 1, nrows, ebase, stg);
+      // lanes 16..31 keep row rs + 1, lanes 0..15 row rs; then a plain
+      // butterfly over the 16 lanes of each half.  Row rs + q ends in lane 16q.
+      const bool up16 = (lane & 16) != 0;
+      float th = up16 ? sh[1] : sh[0], tl = up16 ? sl[1] : sl[0];
+      {
+        const float rh = __shfl_xor_sync(0xffffffffu, up16 ? sh[0] : sh[1], 16);
+        const float rl = __shfl_xor_sync(0xffffffffu, up16 ? sl[0] : sl[1], 16);
+        df_add(th, tl, rh, rl);
+      }
+#pragma unroll
+      for (int o = 8; o >= 1; o >>= 1) {
+        const float rh = __shfl_xor_sync(0xffffffffu, th, o);
+        const float rl = __shfl_xor_sync(0xffffffffu, tl, o);
+        df_add(th, tl, rh, rl);
+      }
+      if ((lane & 15) == 0 && r + (lane >> 4) < nt) pp[r + (lane >> 4)][wid] = make_float2(th, tl);
+    }
     // the two tile buffers alternate, so one barrier per tile suffices: tile
     // t + 2 reuses this buffer only after warp 0 passed tile t + 1's barrier
     __syncthreads();
@@ -629,9 +655,10 @@ __device__ __forceinline__ void sweep_all_rows(const VecCtx &c, int b, int nrows
       float hs = 0.f, ls = 0.f;
 #pragma unroll
       for (int w = 0; w < VEC_THREADS / 32; ++w) df_add(hs, ls, pp[lane][w].x, pp[lane][w].y);
-      dp[itop - lane] = (double)hs + (double)ls;
+      dp[nrows - 1 - t0 - lane] = (double)hs + (double)ls;
     }
   }
+  cp_async_wait<0>();
 }
 
 // Block-wide sum of a float through the double block_sum.
@@ -641,7 +668,8 @@ __device__ __forceinline__ float block_sum_f(float v, double *red) {
 
 template <bool LO, bool F64U>
 __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) {
-  extern __shared__ float cs[];   // [2j]: c_i = h_i / beta_j, then g_i
+  extern __shared__ float4 dyn[];   // row staging ring, then [2j] floats: c_i, g_i
+  float *cs = reinterpret_cast<float *>(reinterpret_cast<char *>(dyn) + sweep_stage_bytes<LO>());
   __shared__ float2 part[2][32][VEC_THREADS / 32];
   __shared__ double red[VEC_THREADS / 32];
   const int chunk = blockIdx.x, b = blockIdx.y;
@@ -667,9 +695,13 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
     for (int t = threadIdx.x; t < c.n_mt; t += VEC_THREADS) s += c.alpha_part[(size_t)t * c.Bs + b];
     s *= sinv * sinv;
   } else {
+    // the partials of step j (parity j & 1): this kernel writes those of
+    // step j + 1 into the other half, so no block can read a sibling's
+    // new value
+    const float *dq2 = c.dq2_part + (size_t)(j & 1) * c.Bs * c.nchunks;
     double sq = 0.0, sy = 0.0;
     for (int t = threadIdx.x; t < c.nchunks; t += VEC_THREADS)
-      sq += (double)c.dq2_part[(size_t)b * c.nchunks + t];
+      sq += (double)dq2[(size_t)b * c.nchunks + t];
     for (int t = threadIdx.x; t < c.n_yb; t += VEC_THREADS)
       sy += (double)c.yy_part[(size_t)b * c.n_yb + t];
     s = sq * sinv * sinv + c.kf * sy;
@@ -757,7 +789,7 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
   }
 
   double *dp = c.dot_part + ((size_t)b * c.nchunks + chunk) * c.kmax1;
-  sweep_all_rows<LO, true>(c, b, j, ebase, cs, gs, vh, vl, corr, cv, part, dp);
+  sweep_all_rows<LO, true>(c, b, j, ebase, cs, gs, vh, vl, corr, cv, part, dp, dyn);
 
   // q_j into row j of the basis; carried vector, operand and partials
   float *hn = c.bhi + ((size_t)j * c.Bs + b) * c.N;
@@ -811,7 +843,7 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
     const size_t pi = (size_t)b * c.nchunks + chunk;
     c.hj_part[pi] = hj;
     c.norm_a[pi] = nrm;
-    if (c.dq2_part != nullptr) c.dq2_part[pi] = dq;
+    if (c.dq2_part != nullptr) c.dq2_part[(size_t)((j + 1) & 1) * c.Bs * c.nchunks + pi] = dq;
   }
 }
 
@@ -950,13 +982,15 @@ __global__ void __launch_bounds__(VEC_THREADS) k_p2_update_dcgs(VecCtx c, int j)
     if (c.dq2_part != nullptr) dq = block_sum_f(dq, red);
     if (threadIdx.x == 0) {
       c.norm_b[(size_t)b * c.nchunks + chunk] = nrm;
-      if (c.dq2_part != nullptr) c.dq2_part[(size_t)b * c.nchunks + chunk] = dq;
+      if (c.dq2_part != nullptr)
+        c.dq2_part[(size_t)((j + 1) & 1) * c.Bs * c.nchunks + (size_t)b * c.nchunks + chunk] = dq;
     }
   }
 }
 
 template <bool LO>
 __global__ void __launch_bounds__(VEC_THREADS) k_p2_dots_dcgs(VecCtx c, int j) {
+  extern __shared__ float4 stg[];   // row staging ring
   __shared__ float2 part[2][32][VEC_THREADS / 32];
   const int chunk = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -981,7 +1015,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_p2_dots_dcgs(VecCtx c, int j) {
     double *dp = c.dot_part + ((size_t)b * c.nchunks + chunk) * c.kmax1;
     __syncthreads();   // the tile buffers of the previous vector are free
     sweep_all_rows<LO, false>(c, b, j + 1, ebase, nullptr, nullptr, vh, vl, corr, corr, part,
-                              dp);
+                              dp, stg);
   }
 }
 
@@ -1012,18 +1046,34 @@ __global__ void __launch_bounds__(256) k_p2_reduce_dcgs(VecCtx c, int j) {
   c.sinv[b] = (stop || !(beta > 0.0)) ? 0.0 : 1.0 / beta;
 }
 
+// Dynamic shared memory above 48 KB needs the attribute, set once per kernel.
+template <class K>
+static void allow_smem(K kern, size_t bytes) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <bool LO, bool F64U>
+static void sweep_one(const VecCtx &c, int j, cudaStream_t st) {
+  static bool attr = false;
+  constexpr size_t max_sh = sweep_stage_bytes<LO>() + (size_t)2 * 4096 * sizeof(float);
+  if (!attr) {
+    allow_smem(k_sweep_dcgs<LO, F64U>, max_sh);
+    attr = true;
+  }
+  const size_t sh = sweep_stage_bytes<LO>() + (size_t)(j > 0 ? 2 * j : 1) * sizeof(float);
+  k_sweep_dcgs<LO, F64U><<<dim3(c.nchunks, c.Bs), VEC_THREADS, sh, st>>>(c, j);
+}
+
 void launch_sweep_dcgs(const VecCtx &c, int j, cudaStream_t st) {
-  const dim3 grid(c.nchunks, c.Bs);
-  const size_t sh = (size_t)(j > 0 ? 2 * j : 1) * sizeof(float);
   const bool lo = c.blo != nullptr, f64u = c.uC != nullptr;
   if (lo && f64u)
-    k_sweep_dcgs<true, true><<<grid, VEC_THREADS, sh, st>>>(c, j);
+    sweep_one<true, true>(c, j, st);
   else if (lo)
-    k_sweep_dcgs<true, false><<<grid, VEC_THREADS, sh, st>>>(c, j);
+    sweep_one<true, false>(c, j, st);
   else if (f64u)
-    k_sweep_dcgs<false, true><<<grid, VEC_THREADS, sh, st>>>(c, j);
+    sweep_one<false, true>(c, j, st);
   else
-    k_sweep_dcgs<false, false><<<grid, VEC_THREADS, sh, st>>>(c, j);
+    sweep_one<false, false>(c, j, st);
 }
 void launch_reduce_dcgs(const VecCtx &c, int j, cudaStream_t st) {
   k_reduce_dcgs<<<c.Bs, 256, 0, st>>>(c, j);
@@ -1031,12 +1081,18 @@ void launch_reduce_dcgs(const VecCtx &c, int j, cudaStream_t st) {
 void launch_pass2_dcgs(const VecCtx &c, int j, cudaStream_t st) {
   const dim3 grid(c.nchunks, c.Bs < 16 ? c.Bs : 16);
   const size_t sh = (size_t)(j + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    allow_smem(k_p2_dots_dcgs<true>, sweep_stage_bytes<true>());
+    allow_smem(k_p2_dots_dcgs<false>, sweep_stage_bytes<false>());
+    attr = true;
+  }
   if (c.blo != nullptr) {
     k_p2_update_dcgs<true><<<grid, VEC_THREADS, sh, st>>>(c, j);
-    k_p2_dots_dcgs<true><<<grid, VEC_THREADS, 0, st>>>(c, j);
+    k_p2_dots_dcgs<true><<<grid, VEC_THREADS, sweep_stage_bytes<true>(), st>>>(c, j);
   } else {
     k_p2_update_dcgs<false><<<grid, VEC_THREADS, sh, st>>>(c, j);
-    k_p2_dots_dcgs<false><<<grid, VEC_THREADS, 0, st>>>(c, j);
+    k_p2_dots_dcgs<false><<<grid, VEC_THREADS, sweep_stage_bytes<false>(), st>>>(c, j);
   }
   k_p2_reduce_dcgs<<<c.Bs, 256, 0, st>>>(c, j);
 }

@@ -55,6 +55,9 @@ struct lgw_handle {
 struct lgw_system {
   lgw_handle *h = nullptr;
   SysDev s{};
+  // spectral interval of C for the polynomial form, estimated on first use
+  bool ivl_ok = false;
+  double ivl_lo = 0.0, ivl_hi = 0.0;
   __nv_bfloat16 *Ltb_lo = nullptr;   // bf16(L - bf16(L))^T [A][N], made on first use
   // Tamm-Dancoff view (A = Delta + (c_K/2) L L^T in place of C), made on first use
   SysDev tda{};
@@ -568,7 +571,10 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   c.n_yb = (s.A + 255) / 256;
   float *yy = (split && tc) ? wsT<float>(h, "yy_part", (size_t)Bs * c.n_yb) : nullptr;
   c.yy_part = yy;
-  c.dq2_part = (split && tc) ? wsT<float>(h, "dq2_part", (size_t)Bs * nchunks) : nullptr;
+  // the delayed sweep reads step j's partials and writes step j + 1's in
+  // the same launch: two halves by step parity (the start writes half 0)
+  c.dq2_part = (split && tc) ? wsT<float>(h, "dq2_part", (size_t)(dcgs ? 2 : 1) * Bs * nchunks)
+                             : nullptr;
   c.xh = tc ? wsT<__nv_bfloat16>(h, "xh", (size_t)Bs * N) : nullptr;
   // alpha partials: per 2048-element chunk (tensor cores without
   // reorthogonalisation), per GEMM2 tile otherwise
@@ -919,14 +925,14 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
 
 // Interval [x_lo, x_hi] around the spectrum of C for the polynomial form:
 // x_lo = min Delta^2 (a bound: C = Delta^2 + a positive semidefinite term);
-// x_hi = the largest Ritz value of k_est Lanczos steps (FP64 contractions
-// when the system keeps its FP64 copy, CGS2) from a hash start vector, plus
-// the last beta, the residual norm of that step.  Synchronous.
+// x_hi = the largest Ritz value of k_est Lanczos steps (BF16 tensor-core
+// contractions when the system has them, else FP64; CGS2) from a hash start
+// vector, plus the last beta, the residual norm of that step.  Synchronous.
 void estimate_interval(lgw_handle *h, const SysDev &s, int k_est, double &lo, double &hi) {
   cudaStream_t &st = h->stream;
   Opts o{};
   o.k = std::max(1, std::min(k_est, s.n_vc));
-  o.precision = s.L64 ? LGW_FP64 : LGW_BF16;
+  o.precision = (s.Lb && tc_available()) ? LGW_BF16 : LGW_FP64;
   o.reorth = LGW_REORTH_CGS2;
   o.b_sub = 1;
   o.qp_max_iter = 50;
@@ -1247,11 +1253,20 @@ lgw_status guard_handle(lgw_handle *h) {
 // exported C ABI
 // ===========================================================================
 namespace {
-// x_lo = x_hi = 0 asks the library for the interval (estimate_interval).
-const PolyOp *poly_arg(lgw_handle *h, const SysDev &s, const lgw_poly *pp, PolyOp &store) {
+// x_lo = x_hi = 0 asks the library for the interval (estimate_interval,
+// kept with the system after its first estimate).
+const PolyOp *poly_arg(lgw_handle *h, const lgw_system *sys, const lgw_poly *pp, PolyOp &store) {
   if (!pp) return nullptr;
   double lo = pp->x_lo, hi = pp->x_hi;
-  if (pp->g >= 1 && pp->g <= 256 && lo == 0.0 && hi == 0.0) estimate_interval(h, s, 32, lo, hi);
+  if (pp->g >= 1 && pp->g <= 256 && lo == 0.0 && hi == 0.0) {
+    lgw_system *ms = const_cast<lgw_system *>(sys);
+    if (!ms->ivl_ok) {
+      estimate_interval(h, sys->s, 32, ms->ivl_lo, ms->ivl_hi);
+      ms->ivl_ok = true;
+    }
+    lo = ms->ivl_lo;
+    hi = ms->ivl_hi;
+  }
   if (pp->g < 1 || pp->g > 256 || !(lo > 0.0) || !(hi > lo)) {
     set_err(h, LGW_ERR_ARG, "polynomial: need 1 <= g <= 256 and 0 < x_lo < x_hi (or both 0)");
     throw Fail{LGW_ERR_ARG};
@@ -1313,7 +1328,7 @@ lgw_status sigma_c_impl(lgw_handle *h, const lgw_system *sys, const lgw_problem 
     Opts op = resolve_opts(h, o, sys->s);
     ensure_copies(h, sys, op);
     PolyOp pstore;
-    const PolyOp *poly = poly_arg(h, sys->s, pp, pstore);
+    const PolyOp *poly = poly_arg(h, sys, pp, pstore);
     if (poly) {
       // Lanczos on D = p_g(C) keeps the FP64 basis
       op.split = 0;
@@ -1838,6 +1853,12 @@ lgw_status lgw_spectral_interval(lgw_handle *h, const lgw_system *sys, int32_t k
     h->timing = false;
     estimate_interval(h, sys->s, k, *x_lo, *x_hi);
     check_status(h);
+    if (k == 32) {   // the estimate lgw_sigma_c_poly uses when asked for one
+      lgw_system *ms = const_cast<lgw_system *>(sys);
+      ms->ivl_lo = *x_lo;
+      ms->ivl_hi = *x_hi;
+      ms->ivl_ok = true;
+    }
   } catch (Fail &f) {
     return f.st;
   }
@@ -1970,7 +1991,7 @@ lgw_status lgw_lanczos_coeffs_poly(lgw_handle *h, const lgw_system *sys, const l
     Opts op = resolve_opts(h, o, s);
     ensure_copies(h, sys, op);
     PolyOp pstore;
-    const PolyOp *poly = poly_arg(h, sys->s, pp, pstore);
+    const PolyOp *poly = poly_arg(h, sys, pp, pstore);
     op.split = 0;
     op.split32 = 0;
     ProbView pv = check_problem(h, s, p);

@@ -79,7 +79,8 @@ struct VecCtx {
   const float *d2f;       // [N] Delta^2 (float)
   const float *ucd;       // [Bs][N] c_K Delta^1/2 (L y) from the FP32 epilogue (kblk_f32), or null
                           // (then w holds the full FP64 epilogue result)
-  float *dq2_part;        // [Bs][nchunks] partials of sum Delta^2 q_j^2 (FP32)
+  float *dq2_part;        // [Bs][nchunks] partials of sum Delta^2 q_j^2 (FP32); with
+                          // LGW_REORTH_DCGS two halves by step parity, [2][Bs][nchunks]
   const float *yy_part;   // [Bs][n_yb]    partials of y . bf16(y) for the current q_j
   int n_yb;
   double kf;

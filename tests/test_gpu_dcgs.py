@@ -211,3 +211,33 @@ def test_graph_replay_bit_identical(L, handle):
                                               reorth_arith="split", use_graph=1))
         assert np.array_equal(eager[0], graph[0])
         assert np.array_equal(eager[1], graph[1])
+
+
+def test_every_vector_of_a_multi_wave_sub_batch(L, handle):
+    """Batched-uneven system 6 (N_vc 62392, N_aux 512, 19 targets x 256
+    summed orbitals: sub-batches of 512 vectors, 31 chunks each, more blocks
+    than one wave).  The sweep of step j reads step j's alpha partials while
+    its blocks write step j + 1's, so the vector whose chunks straddle a wave
+    boundary is where a shared buffer would show: every vector's first three
+    alpha and beta must match the two-pass CGS1K recurrence."""
+    w = gi.batched_uneven(6, k=150, max_targets=64)
+    s = L.lgw_prepare_system(handle, w.n_v, w.n_c, w.n_aux, _t(w.eps), _t(w.L))
+    prob = L.Problem(targets=_t(w.targets), m_idx=_t(w.m_idx), omega=_t(w.omega),
+                     delta=w.delta, M=_t(w.M))
+    B, K = w.n_t * w.n_m, 3
+    out = {}
+    try:
+        for reorth in ("cgs1k", "dcgs"):
+            al = torch.zeros(B, K, dtype=torch.float64, device=DEV)
+            be = torch.zeros_like(al)
+            b0 = torch.zeros(B, dtype=torch.float64, device=DEV)
+            ke = torch.zeros(B, dtype=torch.int32, device=DEV)
+            L.lgw_lanczos_coeffs(handle, s, prob, L.Options(k=K, precision="bf16", reorth=reorth),
+                                 al, be, b0, ke)
+            torch.cuda.synchronize()
+            out[reorth] = (al.cpu().numpy(), be.cpu().numpy())
+    finally:
+        L.lgw_release_system(s)
+    (a1, b1), (a2, b2) = out["cgs1k"], out["dcgs"]
+    assert np.abs(a2 - a1).max() <= 1e-6 * np.abs(a1).max()
+    assert np.abs(b2 - b1).max() <= 1e-6 * np.abs(b1).max()

@@ -169,3 +169,42 @@ def test_batched_sampled_vectors_vs_oracle(L, handle, batch):
             r = O.sigma_from_poles(w.omega, w.eps[m] - eta * Om, W, np.full(Om.size, eta),
                                    w.delta)
             assert np.abs(g - r).max() * 1e3 <= 1.0 / w.n_m, (w.name, v)
+
+
+def test_gemm2_pipeline_variants_bit_identical():
+    """GEMM2 (L y with the store-only c_K Delta^1/2 epilogue) runs as one CTA
+    per tile, as the half-depth pipeline (two CTAs per SM) or as the
+    persistent kernel with two TMEM accumulators; all keep the same K order
+    per output element, so the Lanczos tridiagonals must agree bit for bit
+    (ragged N_vc, several M tiles per CTA, both tile orders through the
+    tuner's choice)."""
+    import os
+    from paper_2310_20103_gb300.build import build
+    build()
+    from paper_2310_20103_gb300 import lgw as L
+    wl = gi.make_workload("p2", 24, 700, 384, [22, 23, 24], list(range(48)), 50, 9, k=24,
+                          aux_scaled=True)
+    h = L.lgw_create(0)
+    s = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, _t(wl.eps), _t(wl.L))
+    prob = L.Problem(targets=_t(wl.targets), m_idx=_t(wl.m_idx), omega=_t(wl.omega),
+                     delta=wl.delta, M=_t(wl.M))
+    B = wl.n_t * wl.n_m
+    res = []
+    try:
+        for pipe in ("0", "1", "2"):
+            os.environ["LGW_GEMM2_PIPE"] = pipe
+            al = torch.empty(B, 24, dtype=torch.float64, device=DEV)
+            be = torch.empty_like(al)
+            b0 = torch.empty(B, dtype=torch.float64, device=DEV)
+            ke = torch.empty(B, dtype=torch.int32, device=DEV)
+            L.lgw_lanczos_coeffs(h, s, prob, L.Options(k=24, precision="bf16", reorth="dcgs"),
+                                 al, be, b0, ke)
+            torch.cuda.synchronize()
+            res.append((al.cpu().numpy(), be.cpu().numpy()))
+    finally:
+        os.environ.pop("LGW_GEMM2_PIPE", None)
+        L.lgw_release_system(s)
+        L.lgw_destroy(h)
+    for a, b in res[1:]:
+        assert np.array_equal(a, res[0][0])
+        assert np.array_equal(b, res[0][1])
