@@ -17,6 +17,8 @@
 // MMAs from one thread, warps 2..5 run the epilogue (warp w reads TMEM lanes
 // 32*(w%4) .. 32*(w%4)+31).  Tile 128 x BN x 64, BN in {64, 128, 256}.
 // Every mbarrier wait is bounded (clock64); a timeout sets ST_TIMEOUT.
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -38,12 +40,17 @@ constexpr int NTHREADS = 192;
 // two CTAs fit on an SM and one's epilogue overlaps the other's main loop
 // (tensor memory: 2 x BN <= 512 columns).  Used for the store-only
 // contraction, whose K loop is short.
-template <int BN, int HALF = 0>
+// DEQ: the A operand arrives as E4M3 (RAW_BYTES per stage, 64 bytes by 128
+// rows) and is widened to FP16 in shared memory next to the B tile.
+template <int BN, int HALF = 0, bool DEQ = false>
 struct Cfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
-  static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int STAGES = ((BN == 256) ? 4 : (BN == 128 ? 6 : 8)) >> HALF;
+  static constexpr int RAW_BYTES = DEQ ? BM * BK : 0;
+  static constexpr int STAGE = A_BYTES + B_BYTES + RAW_BYTES;
+  static constexpr int STAGES =
+      DEQ ? (BN == 256 ? 3 : (BN == 128 ? 5 : 6))
+          : (((BN == 256) ? 4 : (BN == 128 ? 6 : 8)) >> HALF);
   static constexpr int BAR_BYTES = 256;
   static constexpr int RED_BYTES = 4 * BN * 8;
   static constexpr int SMEM = 1024 + STAGES * STAGE + BAR_BYTES + RED_BYTES;
@@ -201,6 +208,32 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
 __host__ __device__ constexpr uint32_t make_idesc_e4m3(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// Instruction descriptor, kind::f16 with FP16 A and B (format code 0): the
+// widened E4M3 operand and its FP16 partner.
+__host__ __device__ constexpr uint32_t make_idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// Orders this thread's generic-proxy shared-memory writes before later
+// reads by the tensor cores (async proxy).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 16 E4M3 values (one 16-byte piece of a K row) into 16 FP16 values, two 16-byte
+// pieces.  E4M3 -> FP16 is exact for every E4M3 value, subnormals included.
+__device__ __forceinline__ void widen_e4m3x16(uint4 in, uint4 &lo, uint4 &hi) {
+  const uint32_t w[4] = {in.x, in.y, in.z, in.w};
+  uint32_t o[8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __half2_raw a = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] & 0xFFFFu), __NV_E4M3);
+    const __half2_raw b = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
+    o[2 * i] = (uint32_t)a.x | ((uint32_t)a.y << 16);
+    o[2 * i + 1] = (uint32_t)b.x | ((uint32_t)b.y << 16);
+  }
+  lo = make_uint4(o[0], o[1], o[2], o[3]);
+  hi = make_uint4(o[4], o[5], o[6], o[7]);
+}
 
 struct EpiArgs {
   // gemm1 (split-K partials)
@@ -235,17 +268,21 @@ enum { E_SPLITK = 0, E_LANCZOS = 1, E_APPLY = 2, E_LANCZOS_NA = 3, E_SPLITB = 4,
 
 // EB: operand element bytes, 2 = BF16 (kind::f16, K block 64), 1 = E4M3
 // (kind::f8f6f4, K block 128); a K block is one 128-byte swizzle row either way.
+// EB = 3: E4M3 A operand widened to FP16 in shared memory by the four
+// epilogue warps during the main loop, FP16 B operand (kind::f16, K block 64).
 template <int BN, int EPI, int EB, int HALF = 0>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               int M, int Ncols, int num_kb, int kb_per_split, EpiArgs ea) {
-  using C = Cfg<BN, HALF>;
+  constexpr bool DEQ = EB == 3;
+  using C = Cfg<BN, HALF, DEQ>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE);
   uint64_t *empty = full + C::STAGES;
-  uint64_t *tfull = empty + C::STAGES;
+  uint64_t *conv = empty + C::STAGES;   // DEQ: the stage's A tile is widened
+  uint64_t *tfull = conv + (DEQ ? C::STAGES : 0);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(tfull + 1);
   double *red = reinterpret_cast<double *>(smem + C::STAGES * C::STAGE + C::BAR_BYTES);
 
@@ -270,6 +307,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      if (DEQ) mbar_init(&conv[s], 4);   // one arrival per converting warp
     }
     mbar_init(tfull, 1);
     fence_barrier_init();
@@ -287,14 +325,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int s = it % C::STAGES;
         const uint32_t ph = (it / C::STAGES) & 1;
         if (!mbar_wait(&empty[s], ph ^ 1, ea.status)) break;
-        mbar_expect_tx(&full[s], C::STAGE);
+        mbar_expect_tx(&full[s], C::STAGE - (DEQ ? C::A_BYTES : 0));
         uint8_t *sa = smem + s * C::STAGE;
         const int kb = kb0 + (it + (ea.rot ? m_tile : 0)) % nk;
-        const int kx = kb * (BK * 2 / EB);
-        if (ea.a3)
+        const int kx = kb * (EB == 1 ? 128 : 64);
+        if (DEQ) {
+          // E4M3 A: half of a 128-element K block (K-block-major) or the
+          // 64 columns kx.. of a row-major operand; 64 bytes by 128 rows
+          uint8_t *raw = sa + C::A_BYTES + C::B_BYTES;
+          if (ea.a3)
+            tma_load_3d(raw, &tmA, &full[s], (kb & 1) * 64, m_tile * BM, kb >> 1);
+          else
+            tma_load_2d(raw, &tmA, &full[s], kx, m_tile * BM);
+        } else if (ea.a3) {
           tma_load_3d(sa, &tmA, &full[s], 0, m_tile * BM, kb);
-        else
+        } else {
           tma_load_2d(sa, &tmA, &full[s], kx, m_tile * BM);
+        }
         if (ea.b3)
           tma_load_3d(sa + C::A_BYTES, &tmB, &full[s], 0, n_tile * BN, kb);
         else
@@ -307,17 +354,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = EB == 2 ? make_idesc(BM, BN) : make_idesc_e4m3(BM, BN);
+      constexpr uint32_t idesc = EB == 2 ? make_idesc(BM, BN)
+                                         : (DEQ ? make_idesc_f16(BM, BN) : make_idesc_e4m3(BM, BN));
       for (int it = 0; it < nk; ++it) {
         const int s = it % C::STAGES;
         const uint32_t ph = (it / C::STAGES) & 1;
         if (!mbar_wait(&full[s], ph, ea.status)) break;
+        if (DEQ && !mbar_wait(&conv[s], ph, ea.status)) break;
         tc_fence_after();
         const uint32_t sa = smem_u32(smem + s * C::STAGE);
         const uint64_t da = make_sdesc(sa), db = make_sdesc(sa + C::A_BYTES);
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk)
-          if (EB == 2)
+          if (EB != 1)
             umma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (it > 0 || kk > 0) ? 1u : 0u);
           else
             umma_e4m3(tmem, da + 2 * kk, db + 2 * kk, idesc, (it > 0 || kk > 0) ? 1u : 0u);
@@ -326,6 +375,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       umma_commit(tfull);
     }
   } else {
+    if (DEQ) {
+      // ------------------------- widen A to FP16 ---------------------------
+      // 128 threads, four passes over the 8 KB E4M3 tile: thread t reads the
+      // 16-byte piece i = 128 p + t (row i / 4, K elements 16 (i % 4) ..),
+      // contiguous across the warp, and writes its two FP16 pieces into the
+      // 128-byte-swizzled row (16-byte chunk c at c ^ (row % 8)); the eight
+      // pieces of a quarter warp land in eight different chunks.
+      const int ct = threadIdx.x - 64;
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % C::STAGES;
+        const uint32_t ph = (it / C::STAGES) & 1;
+        if (!mbar_wait(&full[s], ph, ea.status)) break;
+        uint8_t *sa = smem + s * C::STAGE;
+        const uint8_t *raw = sa + C::A_BYTES + C::B_BYTES;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const int i = 128 * p + ct;
+          const int r = i >> 2, c2 = 2 * (i & 3);
+          uint4 lo, hi;
+          widen_e4m3x16(*reinterpret_cast<const uint4 *>(raw + 16 * i), lo, hi);
+          *reinterpret_cast<uint4 *>(sa + r * 128 + ((c2 ^ (r & 7)) << 4)) = lo;
+          *reinterpret_cast<uint4 *>(sa + r * 128 + (((c2 + 1) ^ (r & 7)) << 4)) = hi;
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&conv[s]);
+      }
+    }
     // ------------------------------ epilogue ------------------------------
     const bool ok = mbar_wait(tfull, 0, ea.status);
     tc_fence_after();
@@ -653,7 +730,12 @@ struct TcPlan {
   CUtensorMap g1A, g1B, g2A, g2B, g2Alo;
   // E4M3 operands (fp8 plans): L8t / x8 for gemm1, L8 / y8 for gemm2
   CUtensorMap f1A, f1B, f2A, f2B;
+  // E4M3 L widened to FP16 in shared memory (deq plans): raw L8t / x16 for
+  // gemm1, raw L8 / y16 for gemm2
+  CUtensorMap d1A, d1B, d2A, d2B;
   bool fp8 = false;
+  bool deq = false;
+  const uint16_t *x16 = nullptr, *y16 = nullptr;
   bool has_bf16 = false;   // g1A / g2A / g2Alo encoded (the system has BF16 copies)
   const uint8_t *x8 = nullptr, *y8 = nullptr;
   const float *ty = nullptr;   // per-vector scale of y8 (gemm2 column scale)
@@ -696,19 +778,55 @@ bool tc_available() {
 
 // 2-D K-major tensor map: inner (K) extent, outer rows, a box of one
 // 128-byte swizzle row (64 BF16 or 128 E4M3 elements) by box_outer rows.
+// elem_bytes 3: FP16 elements (2 bytes).
+static CUtensorMapDataType map_dtype(int elem_bytes) {
+  return elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                         : (elem_bytes == 3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                            : CU_TENSOR_MAP_DATA_TYPE_UINT8);
+}
+static int map_bytes(int elem_bytes) { return elem_bytes == 1 ? 1 : 2; }
+
 static bool encode_2d(CUtensorMap *tm, const void *base, uint64_t inner, uint64_t outer,
                       uint32_t box_outer, uint64_t row_elems = 0, int elem_bytes = 2) {
   auto enc = get_encode();
   if (!enc) return false;
+  const int eb = map_bytes(elem_bytes);
   cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {(row_elems ? row_elems : inner) * (uint64_t)elem_bytes};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), box_outer};
+  cuuint64_t strides[1] = {(row_elems ? row_elems : inner) * (uint64_t)eb};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / eb), box_outer};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(tm,
-                   elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
-                   2, const_cast<void *>(base), dims, strides,
+  CUresult r = enc(tm, map_dtype(elem_bytes), 2, const_cast<void *>(base), dims, strides,
                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// E4M3 A operand of the widening kernels: a box of 64 bytes by BM rows, not
+// swizzled (row r of the box at r * 64 in shared memory).  kblk: the
+// K-block-major layout (kblk_e4m3; the box is half of a 128-byte K-block
+// row, x = 0 or 64); else row-major [outer][inner].
+static bool encode_raw_a(CUtensorMap *tm, const uint8_t *base, uint64_t inner, uint64_t outer,
+                         bool kblk) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  CUresult r;
+  if (kblk) {
+    cuuint64_t dims[3] = {128, outer, inner / 128};
+    cuuint64_t strides[2] = {128, outer * 128};
+    cuuint32_t box[3] = {64, (cuuint32_t)tc::BM, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(base), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner};
+    cuuint32_t box[2] = {64, (cuuint32_t)tc::BM};
+    cuuint32_t es[2] = {1, 1};
+    r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(base), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
   return r == CUDA_SUCCESS;
 }
 
@@ -720,13 +838,12 @@ static bool encode_kblk(CUtensorMap *tm, const void *base, uint64_t kblocks, uin
                         uint32_t box_rows, int elem_bytes = 2) {
   auto enc = get_encode();
   if (!enc) return false;
-  cuuint64_t dims[3] = {(cuuint64_t)(128 / elem_bytes), rows, kblocks};
+  const int eb = map_bytes(elem_bytes);
+  cuuint64_t dims[3] = {(cuuint64_t)(128 / eb), rows, kblocks};
   cuuint64_t strides[2] = {128, rows * 128};
-  cuuint32_t box[3] = {(cuuint32_t)(128 / elem_bytes), box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / eb), box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(tm,
-                   elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
-                   3, const_cast<void *>(base), dims, strides,
+  CUresult r = enc(tm, map_dtype(elem_bytes), 3, const_cast<void *>(base), dims, strides,
                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -806,7 +923,7 @@ void tc_plan_destroy(TcPlan *p) { delete p; }
 template <int BN, int EPI, int EB = 2, int HALF = 0>
 static void launch_tc(const CUtensorMap &A, const CUtensorMap &B, int M, int Ncols, int num_kb,
                       int kb_per_split, int splits, const tc::EpiArgs &ea, cudaStream_t st) {
-  using C = tc::Cfg<BN, HALF>;
+  using C = tc::Cfg<BN, HALF, EB == 3>;
   static bool attr_done = false;
   if (!attr_done) {
     cudaFuncSetAttribute(tc::k_gemm_tc<BN, EPI, EB, HALF>,
@@ -838,12 +955,13 @@ static void launch_persist(const CUtensorMap &A, const CUtensorMap &B, int M, in
 }
 
 // half: 1 = the half-depth pipeline (two CTAs per SM), 2 = the persistent
-// kernel with two accumulators; store-only epilogue only
+// kernel with two accumulators; store-only epilogue only, and not for the
+// widening kernels (their epilogue warps convert during the main loop)
 template <int EPI, int EB = 2>
 static void dispatch_bn(int BN, const CUtensorMap &A, const CUtensorMap &B, int M, int Ncols,
                         int num_kb, int kb_per_split, int splits, const tc::EpiArgs &ea,
                         cudaStream_t st, int half = 0) {
-  if constexpr (EPI == tc::E_SPLITB) {
+  if constexpr (EPI == tc::E_SPLITB && EB != 3) {
     if (half == 2 && splits == 1 && kb_per_split == num_kb) {
       if (BN == 256)
         launch_persist<256, EB>(A, B, M, Ncols, num_kb, ea, st);
@@ -878,6 +996,11 @@ void launch_gemm1_tc(const TcPlan *p, unsigned *status, cudaStream_t st) {
   ea.status = status;
   ea.rot = p->rot1;
   ea.a3 = ea.b3 = 1;   // L^T and X are K-block-major
+  if (p->deq) {
+    dispatch_bn<tc::E_SPLITK, 3>(p->BN1, p->d1A, p->d1B, p->A, p->Bs, p->N / tc::BK,
+                                 p->kb_per_split, p->splits, ea, st);
+    return;
+  }
   if (p->fp8) {
     // same split count; K blocks of 128 elements
     const int nkb = p->N / 128;
@@ -911,6 +1034,17 @@ void launch_gemm2_tc(const TcPlan *p, int epi, const double *q, const double *qp
   ea.w = w;
   ea.alpha_part = alpha_part;
   ea.status = status;
+  if (p->deq) {
+    ea.colscale = p->ty;
+    const int nkb = p->A / tc::BK;
+    if (epi == EPI_LANCZOS && alpha_part == nullptr)
+      dispatch_bn<tc::E_LANCZOS_NA, 3>(p->BN2, p->d2A, p->d2B, p->N, p->Bs, nkb, nkb, 1, ea, st);
+    else if (epi == EPI_LANCZOS)
+      dispatch_bn<tc::E_LANCZOS, 3>(p->BN2, p->d2A, p->d2B, p->N, p->Bs, nkb, nkb, 1, ea, st);
+    else
+      dispatch_bn<tc::E_APPLY, 3>(p->BN2, p->d2A, p->d2B, p->N, p->Bs, nkb, nkb, 1, ea, st);
+    return;
+  }
   if (p->fp8) {
     ea.colscale = p->ty;
     const int nkb = p->A / 128;
@@ -979,6 +1113,12 @@ void launch_gemm2_tc_split(const TcPlan *p, float *ucd, unsigned *status, cudaSt
   ea.cdf = p->cdf;
   ea.ucd = ucd;
   ea.status = status;
+  if (p->deq) {
+    ea.colscale = p->ty;
+    const int nkb = p->A / tc::BK;
+    dispatch_bn<tc::E_SPLITB, 3>(p->BN2, p->d2A, p->d2B, p->N, p->Bs, nkb, nkb, 1, ea, st);
+    return;
+  }
   if (p->fp8) {
     ea.colscale = p->ty;
     const int nkb = p->A / 128;
@@ -1066,6 +1206,9 @@ bool plan_encode_b(TcPlan *p) {
   if (ok && p->fp8)
     ok = encode_kblk(&p->f1B, p->x8, (uint64_t)p->N / 128, (uint64_t)p->Bs, (uint32_t)p->BN1, 1) &&
          encode_2d(&p->f2B, p->y8, (uint64_t)p->A, (uint64_t)p->Bs, (uint32_t)p->BN2, 0, 1);
+  if (ok && p->deq)
+    ok = encode_kblk(&p->d1B, p->x16, (uint64_t)p->N / 64, (uint64_t)p->Bs, (uint32_t)p->BN1, 3) &&
+         encode_2d(&p->d2B, p->y16, (uint64_t)p->A, (uint64_t)p->Bs, (uint32_t)p->BN2, 0, 3);
   return ok;
 }
 
@@ -1113,7 +1256,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
   }
   int dev = 0;
   cudaGetDevice(&dev);
-  const TuneKey key{dev, p->N, p->A, p->Bs, p->fp8 ? 1 : 0};
+  const TuneKey key{dev, p->N, p->A, p->Bs, p->deq ? 2 : (p->fp8 ? 1 : 0)};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -1181,7 +1324,7 @@ bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, 
     float t2_best = t2_def;
     for (int bn = 64; bn <= bn_max; bn *= 2)
       for (int mf = 0; mf <= 1; ++mf)
-        for (int hf = 0; hf <= 2; ++hf) {
+        for (int hf = 0; hf <= (p->deq ? 0 : 2); ++hf) {
           if (bn == def.BN2 && mf == def.mfast2 && hf == def.half2) continue;
           p->BN2 = bn;
           p->mfast2 = mf;
@@ -1225,6 +1368,21 @@ bool tc_plan_enable_fp8(TcPlan *p, const uint8_t *L8t, const uint8_t *L8, const 
   return encode_kblk(&p->f1A, L8t, (uint64_t)p->N / 128, (uint64_t)p->A, tc::BM, 1) &&
          encode_2d(&p->f2A, L8, (uint64_t)p->A, (uint64_t)p->N, tc::BM, 0, 1) &&
          plan_encode_b(p);
+}
+
+// Switch a plan to E4M3 L widened to FP16 in shared memory: raw L8t [A][N]
+// (K-block-major) with x16 [Bs][N] (FP16, K-block-major like xh) for gemm1,
+// raw L8 [N][A] with y16 [Bs][A] (FP16) for gemm2 (ty: per-vector scale of
+// y16).
+bool tc_plan_enable_deq(TcPlan *p, const uint8_t *L8t, const uint8_t *L8, const uint16_t *x16,
+                        const uint16_t *y16, const float *ty) {
+  p->deq = true;
+  p->half2 = 0;
+  p->x16 = x16;
+  p->y16 = y16;
+  p->ty = ty;
+  return encode_raw_a(&p->d1A, L8t, (uint64_t)p->N, (uint64_t)p->A, true) &&
+         encode_raw_a(&p->d2A, L8, (uint64_t)p->A, (uint64_t)p->N, false) && plan_encode_b(p);
 }
 
 bool tc_plan_has_bf16(const TcPlan *p) { return p->has_bf16; }

@@ -535,78 +535,117 @@ __host__ __device__ constexpr size_t sweep_stage_bytes() {
   return (size_t)SW_SLOTS * (LO ? 4 : 2) * VEC_THREADS * sizeof(float4);
 }
 
-// Sequence index r (row nrows - 1 - r) into slot r % SW_SLOTS; one commit
-// group per index, empty past the last row.
-template <bool LO>
-__device__ __forceinline__ void stage_row(const VecCtx &c, int b, int r, int nrows, int ebase,
-                                          float4 *stg) {
-  constexpr int NV = LO ? 4 : 2;
-  if (r < nrows) {
-    const int i = nrows - 1 - r;
-    float4 *slot = stg + (size_t)(r % SW_SLOTS) * NV * VEC_THREADS + threadIdx.x;
-    const float *qh = bhi_row(c, i, b);
-    const float *ql = LO ? blo_row(c, i, b) : nullptr;
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int e = ebase + 128 * u;
-      if (e < c.N) {
-        cp_async16(slot + u * VEC_THREADS, qh + e);
-        if (LO) cp_async16(slot + (2 + u) * VEC_THREADS, ql + e);
-      } else {
-        slot[u * VEC_THREADS] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (LO) slot[(2 + u) * VEC_THREADS] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-  }
-  cp_async_commit();
+// Packed FP32 pairs: one instruction rounds each of the two lanes to nearest,
+// exactly as the scalar __fadd_rn / __fmul_rn / __fmaf_rn would, and is never
+// contracted.  Halves the issue slots of the double-float dot products.
+__device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
 }
 
-// Products of one staged row with v: double-float partial of q_i . v and,
-// with CORR, the delayed corrections corr += c_i q_i, cv += g_i q_i.
+// Products of one staged row with v, two adjacent elements per instruction:
+// the double-float partial of q_i . v (TwoProd by FMA with the cross terms
+// q_hi v_lo and q_lo v_hi, TwoSum into a running pair per lane; the two lanes
+// are joined at the end) and, with CORR, the delayed corrections
+// corr += c_i q_i and cv += g_i q_i.  vn = -vh, so -q v_hi needs no negation.
 template <bool LO, bool CORR>
-__device__ __forceinline__ void row_products(const float4 *slot, float cf, float gf,
-                                             const float (&vh)[8], const float (&vl)[8],
-                                             float (&corr)[8], float (&cv)[8], float &sh,
-                                             float &sl) {
-  sh = 0.f;
-  sl = 0.f;
+__device__ __forceinline__ void row_products(const float4 *slot, float2 cg,
+                                             const float2 (&vh)[4], const float2 (&vn)[4],
+                                             const float2 (&vl)[4], float2 (&corr)[4],
+                                             float2 (&cv)[4], float &sh_out, float &sl_out) {
+  float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
+  const float2 cf = make_float2(cg.x, cg.x), gf = make_float2(cg.y, cg.y);
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     const float4 h4 = slot[u * VEC_THREADS];
     const float4 l4 = LO ? slot[(2 + u) * VEC_THREADS] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float xa[4] = {h4.x, h4.y, h4.z, h4.w};
-    const float xb[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int m = 4 * u + t;
+    for (int p = 0; p < 2; ++p) {
+      const int m = 2 * u + p;
+      const float2 xa = p ? make_float2(h4.z, h4.w) : make_float2(h4.x, h4.y);
+      const float2 xb = p ? make_float2(l4.z, l4.w) : make_float2(l4.x, l4.y);
       if (CORR) {
-        corr[m] = fmaf(cf, xa[t], corr[m]);
-        cv[m] = fmaf(gf, xa[t], cv[m]);
+        corr[m] = __ffma2_rn(cf, xa, corr[m]);
+        cv[m] = __ffma2_rn(gf, xa, cv[m]);
       }
-      const float pr = __fmul_rn(xa[t], vh[m]);
-      float err = __fmaf_rn(xa[t], vh[m], -pr);
-      err = __fmaf_rn(xa[t], vl[m], err);
-      if (LO) err = __fmaf_rn(xb[t], vh[m], err);
-      two_sum_acc(sh, sl, pr);
-      sl = __fadd_rn(sl, err);
+      const float2 pn = __fmul2_rn(xa, vn[m]);        // -fl(q_hi v_hi)
+      float2 err = __ffma2_rn(xa, vh[m], pn);         // q_hi v_hi - fl(q_hi v_hi), exact
+      err = __ffma2_rn(xa, vl[m], err);
+      if (LO) err = __ffma2_rn(xb, vh[m], err);
+      // TwoSum: sh + fl(q_hi v_hi) = s + e exactly
+      const float2 s = sub2_rn(sh, pn);
+      const float2 bb = sub2_rn(s, sh);
+      const float2 e = sub2_rn(sub2_rn(sh, sub2_rn(s, bb)), __fadd2_rn(pn, bb));
+      sh = s;
+      sl = __fadd2_rn(__fadd2_rn(sl, e), err);
     }
   }
+  sh_out = sh.x;
+  sl_out = sl.x;
+  df_add(sh_out, sl_out, sh.y, sl.y);
 }
 
 // All rows i = nrows - 1 down to 0 (the newest row first), two per trip.
 // Row partials of the block go to dp[i] (one double per row), through a
 // transposed butterfly over the warp (10 shuffles for the two rows) and a
 // fixed-order sum over the eight warps in shared memory, 32 rows at a time.
+// cg[i] = (c_i, g_i), read only with CORR.
 template <bool LO, bool CORR>
 __device__ __forceinline__ void sweep_all_rows(const VecCtx &c, int b, int nrows, int ebase,
-                                               const float *cs, const float *gs,
-                                               const float (&vh)[8], const float (&vl)[8],
-                                               float (&corr)[8], float (&cv)[8],
+                                               const float2 *cg, const float2 (&vh)[4],
+                                               const float2 (&vl)[4], float2 (&corr)[4],
+                                               float2 (&cv)[4],
                                                float2 (*part)[32][VEC_THREADS / 32],
                                                double *dp, float4 *stg) {
   constexpr int NV = LO ? 4 : 2;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int r = 0; r < SW_SLOTS; ++r) stage_row<LO>(c, b, r, nrows, ebase, stg);
+  float2 vn[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) vn[m] = make_float2(-vh[m].x, -vh[m].y);
+  // N is a multiple of 128, so each 4-element piece of the thread lies wholly
+  // inside a row or wholly past its end; pieces past the end read zeros,
+  // filled into their slots once
+  const bool ok0 = ebase < c.N, ok1 = ebase + 128 < c.N;
+  float4 *mine = stg + threadIdx.x;
+  if (!ok1) {
+    for (int s = 0; s < SW_SLOTS; ++s) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u == 0 && ok0) continue;
+        mine[(s * NV + u) * VEC_THREADS] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (LO) mine[(s * NV + 2 + u) * VEC_THREADS] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+  const size_t rstride = (size_t)c.Bs * c.N;
+  const float *hb = c.bhi + (size_t)b * c.N + ebase;
+  const float *lb = LO ? c.blo + (size_t)b * c.N + ebase : nullptr;
+  // sequence index r (row nrows - 1 - r) into slot s; one commit group per
+  // index, empty past the last row
+  auto stage = [&](int r, int s) {
+    if (r < nrows) {
+      const size_t off = (size_t)(nrows - 1 - r) * rstride;
+      float4 *slot = mine + s * NV * VEC_THREADS;
+      if (ok0) {
+        cp_async16(slot, hb + off);
+        if (LO) cp_async16(slot + 2 * VEC_THREADS, lb + off);
+      }
+      if (ok1) {
+        cp_async16(slot + VEC_THREADS, hb + off + 128);
+        if (LO) cp_async16(slot + 3 * VEC_THREADS, lb + off + 128);
+      }
+    }
+    cp_async_commit();
+  };
+  for (int r = 0; r < SW_SLOTS; ++r) stage(r, r);
+  int sc = 0;   // slot of sequence index rs: rs % SW_SLOTS
   for (int t0 = 0; t0 < nrows; t0 += 32) {
     const int nt = min(32, nrows - t0);
     float2 (*pp)[VEC_THREADS / 32] = part[(t0 >> 5) & 1];
@@ -617,20 +656,18 @@ __device__ __forceinline__ void sweep_all_rows(const VecCtx &c, int b, int nrows
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const int rq = rs + q;
-        const int i = nrows - 1 - rq;
-        const bool real = rq < nrows;
-        const float cf = (CORR && real) ? cs[i] : 0.0f;
-        const float gf = (CORR && real) ? gs[i] : 0.0f;
-        const float4 *slot = stg + (size_t)(rq % SW_SLOTS) * NV * VEC_THREADS + threadIdx.x;
-        if (real) {
-          row_products<LO, CORR>(slot, cf, gf, vh, vl, corr, cv, sh[q], sl[q]);
+        if (rq < nrows) {
+          const float2 g = CORR ? cg[nrows - 1 - rq] : make_float2(0.f, 0.f);
+          row_products<LO, CORR>(mine + (sc + q) * NV * VEC_THREADS, g, vh, vn, vl, corr, cv,
+                                 sh[q], sl[q]);
         } else {
           sh[q] = 0.f;
           sl[q] = 0.f;
         }
       }
-      stage_row<LO>(c, b, rs + SW_SLOTS, nrows, ebase, stg);
-      stage_row<LO>(c, b, rs + SW_SLOTS + 1, nrows, ebase, stg);
+      stage(rs + SW_SLOTS, sc);
+      stage(rs + SW_SLOTS + 1, sc + 1);
+      sc = sc == SW_SLOTS - 2 ? 0 : sc + 2;
       // lanes 16..31 keep row rs + 1, lanes 0..15 row rs; then a plain
       // butterfly over the 16 lanes of each half.  Row rs + q ends in lane 16q.
       const bool up16 = (lane & 16) != 0;
@@ -668,8 +705,8 @@ __device__ __forceinline__ float block_sum_f(float v, double *red) {
 
 template <bool LO, bool F64U>
 __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) {
-  extern __shared__ float4 dyn[];   // row staging ring, then [2j] floats: c_i, g_i
-  float *cs = reinterpret_cast<float *>(reinterpret_cast<char *>(dyn) + sweep_stage_bytes<LO>());
+  extern __shared__ float4 dyn[];   // row staging ring, then [j] pairs (c_i, g_i)
+  float2 *cg = reinterpret_cast<float2 *>(reinterpret_cast<char *>(dyn) + sweep_stage_bytes<LO>());
   __shared__ float2 part[2][32][VEC_THREADS / 32];
   __shared__ double red[VEC_THREADS / 32];
   const int chunk = blockIdx.x, b = blockIdx.y;
@@ -687,7 +724,6 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
     return;
   }
   const double sinv = c.sinv[b], bj = c.betaj[b];
-  float *gs = cs + j;
   // alpha~_j = q~_j . C q~_j: from the FP64 contraction's partials, or
   // sum Delta^2 q~^2 + c_K y . bf16(y) on the tensor-core path
   double s = 0.0;
@@ -718,8 +754,7 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
       double g = (c.alpha[v * c.k + i] - alpha) * ci;
       if (i >= 1) g = fma(c.beta[v * c.k + i - 1], hb[i - 1] * sinv, g);
       if (i + 1 < j) g = fma(c.beta[v * c.k + i], hb[i + 1] * sinv, g);
-      cs[i] = (float)ci;
-      gs[i] = (float)g;
+      cg[i] = make_float2((float)ci, (float)g);
       if (chunk == 0) c.gq[(size_t)b * c.kmax1 + i] = g;
     }
   }
@@ -789,7 +824,24 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
   }
 
   double *dp = c.dot_part + ((size_t)b * c.nchunks + chunk) * c.kmax1;
-  sweep_all_rows<LO, true>(c, b, j, ebase, cs, gs, vh, vl, corr, cv, part, dp, dyn);
+  {
+    float2 vh2[4], vl2[4], corr2[4], cv2[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      vh2[m] = make_float2(vh[2 * m], vh[2 * m + 1]);
+      vl2[m] = make_float2(vl[2 * m], vl[2 * m + 1]);
+      corr2[m] = make_float2(0.f, 0.f);
+      cv2[m] = make_float2(0.f, 0.f);
+    }
+    sweep_all_rows<LO, true>(c, b, j, ebase, cg, vh2, vl2, corr2, cv2, part, dp, dyn);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      corr[2 * m] = corr2[m].x;
+      corr[2 * m + 1] = corr2[m].y;
+      cv[2 * m] = cv2[m].x;
+      cv[2 * m + 1] = cv2[m].y;
+    }
+  }
 
   // q_j into row j of the basis; carried vector, operand and partials
   float *hn = c.bhi + ((size_t)j * c.Bs + b) * c.N;
@@ -998,13 +1050,13 @@ __global__ void __launch_bounds__(VEC_THREADS) k_p2_dots_dcgs(VecCtx c, int j) {
   for (int b = blockIdx.y; b < c.Bs; b += gridDim.y) {
     if (!c.flag2[b]) continue;   // uniform over the block
     const size_t voff = (size_t)b * c.N;
-    float vh[8], vl[8], corr[8];
+    float vh[8], vl[8];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int e = ebase + 128 * u;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        vh[4 * u + t] = vl[4 * u + t] = corr[4 * u + t] = 0.0f;
+        vh[4 * u + t] = vl[4 * u + t] = 0.0f;
         if (e < c.N) {
           const double x = c.wv[voff + e + t];
           vh[4 * u + t] = __double2float_rn(x);
@@ -1012,10 +1064,17 @@ __global__ void __launch_bounds__(VEC_THREADS) k_p2_dots_dcgs(VecCtx c, int j) {
         }
       }
     }
+    float2 vh2[4], vl2[4], unused[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      vh2[m] = make_float2(vh[2 * m], vh[2 * m + 1]);
+      vl2[m] = make_float2(vl[2 * m], vl[2 * m + 1]);
+      unused[m] = make_float2(0.f, 0.f);
+    }
     double *dp = c.dot_part + ((size_t)b * c.nchunks + chunk) * c.kmax1;
     __syncthreads();   // the tile buffers of the previous vector are free
-    sweep_all_rows<LO, false>(c, b, j + 1, ebase, nullptr, nullptr, vh, vl, corr, corr, part,
-                              dp, stg);
+    sweep_all_rows<LO, false>(c, b, j + 1, ebase, nullptr, vh2, vl2, unused, unused, part, dp,
+                              stg);
   }
 }
 
@@ -1055,12 +1114,12 @@ static void allow_smem(K kern, size_t bytes) {
 template <bool LO, bool F64U>
 static void sweep_one(const VecCtx &c, int j, cudaStream_t st) {
   static bool attr = false;
-  constexpr size_t max_sh = sweep_stage_bytes<LO>() + (size_t)2 * 4096 * sizeof(float);
+  constexpr size_t max_sh = sweep_stage_bytes<LO>() + (size_t)4096 * sizeof(float2);
   if (!attr) {
     allow_smem(k_sweep_dcgs<LO, F64U>, max_sh);
     attr = true;
   }
-  const size_t sh = sweep_stage_bytes<LO>() + (size_t)(j > 0 ? 2 * j : 1) * sizeof(float);
+  const size_t sh = sweep_stage_bytes<LO>() + (size_t)(j > 0 ? j : 1) * sizeof(float2);
   k_sweep_dcgs<LO, F64U><<<dim3(c.nchunks, c.Bs), VEC_THREADS, sh, st>>>(c, j);
 }
 

@@ -211,6 +211,15 @@ void launch_quant_x8(const __nv_bfloat16 *xh, int Bs, int N, uint8_t *x8, float 
 void launch_reduce_y_fp8(const float *Ypart, int splits, int Bs, int A, const float *sx,
                          const float *sL, uint8_t *y8, float *ty, float *yy, int n_yb,
                          cudaStream_t st);
+// E4M3 L widened to FP16 in shared memory (precision LGW_FP8_DEQ): the
+// per-step operands in FP16 with per-vector power-of-two scales.
+bool tc_plan_enable_deq(TcPlan *p, const uint8_t *L8t, const uint8_t *L8, const uint16_t *x16,
+                        const uint16_t *y16, const float *ty);
+void launch_quant_x16(const __nv_bfloat16 *xh, int Bs, int N, uint16_t *x16, float *sx,
+                      cudaStream_t st, const double *vscale = nullptr);
+void launch_reduce_y_f16(const float *Ypart, int splits, int Bs, int A, const float *sx,
+                         const float *sL, uint16_t *y16, float *ty, float *yy, int n_yb,
+                         cudaStream_t st);
 bool tc_plan_has_bf16(const TcPlan *p);
 bool tc_plan_autotune(TcPlan *p, float *ucd, unsigned *status, cudaStream_t st, int *splits_out);
 TcPlan *tc_plan_create(const SysDev &s, int Bs, const __nv_bfloat16 *xh, float *ypart,

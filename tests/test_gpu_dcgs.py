@@ -11,7 +11,7 @@ other reorthogonalisation modes:
   * FP64 contractions (split basis) vs the oracle's CGS2 Lanczos: 1e-9 on
     Sigma (relative, per target) and E_qp; 1e-8 on Z;
   * k = N_vc vs the closed form (Eq. 7-9): 1e-9;
-  * float-only basis: 1e-6 on Sigma, 1e-8 eV on E_qp (as split32 CGS);
+  * float-only basis: k 2^-24 (3.8e-6) on Sigma, 1e-8 eV on E_qp;
   * BF16 / E4M3 contractions: 1 meV on E_qp;
   * graph replay bit-identical to eager launches;
   * an exact breakdown (invariant subspace) stops at the right depth, through
@@ -124,7 +124,9 @@ def test_float_basis(L, handle, tiny_ref):
     wl, (sig64, E64, _, _), _ = tiny_ref
     sig, e, _, _ = _run(L, handle, wl, L.Options(k=64, precision="fp64", reorth="dcgs",
                                                  reorth_arith="split32"))
-    assert _rel(sig, sig64) < 1e-6
+    # k 2^-24: first-order bound of a k-step recurrence whose basis is
+    # stored to 2^-24 (the delayed update also applies the stored q_i)
+    assert _rel(sig, sig64) < 64 * 2.0**-24
     assert np.abs(e - E64).max() < 1e-8
 
 
