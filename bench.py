@@ -436,7 +436,9 @@ def run_gpu(args):
                     ("float_basis_step", options(reorth_arith="split32"),
                      "delayed single sweep against a float-only basis (split32)")] + (
                     [("fp8_step", options(precision="fp8"),
-                      "E4M3 contractions (kind::f8f6f4) with power-of-two scales")]
+                      "E4M3 contractions (kind::f8f6f4) with power-of-two scales"),
+                     ("fp8_deq_step", options(precision="fp8_deq"),
+                      "E4M3 L widened to FP16 in shared memory, FP16 operands (kind::f16)")]
                     if args.precision == "bf16" else []):
                 err = _guarded(leg, name, o, note)
                 if err is not None:
@@ -782,8 +784,9 @@ def batched_leg(L, h, dev, max_targets=64, k=150, reorth="dcgs", reps=1):
 def large_leg(L, dev, n_targets=2, k=300):
     """Large cluster-sized system (N_vc 1.6M, N_aux 8192), n_targets x 1024
     summed orbitals in one sub-batch, k 300 without reorthogonalisation,
-    2000 frequencies: QP states/s with E4M3 and with BF16 contractions, and
-    the E4M3-vs-BF16 differences of E_qp and Sigma in meV.  L (105 GB FP64)
+    2000 frequencies: QP states/s with E4M3 contractions, with E4M3 L widened
+    to FP16 in shared memory and with BF16 contractions, and the differences
+    of E_qp and Sigma from the BF16 run in meV.  L (105 GB FP64)
     is drawn on the device; the system keeps the BF16 and E4M3 copies only
     (LGW_SYS_NO_FP64), so the FP64 copy is freed before the runs."""
     import torch
@@ -814,7 +817,7 @@ def large_leg(L, dev, n_targets=2, k=300):
            "data": "L drawn on the device (torch Philox, seed 5), eps and M numpy seed 5",
            "prepare_s": t_prep, "unit": "QP states/s"}
     res = {}
-    for prec in ("fp8", "bf16"):
+    for prec in ("fp8", "fp8_deq", "bf16"):
         sig = torch.empty(wl.n_t, wl.omega.size, 2, dtype=torch.float64, device=dev)
         e = torch.empty(wl.n_t, dtype=torch.float64, device=dev)
         warm = L.Options(k=2, precision=prec, reorth="none", b_sub=B)
@@ -836,6 +839,10 @@ def large_leg(L, dev, n_targets=2, k=300):
     out["qp_diff_mev_fp8_vs_bf16"] = float(np.abs(res["fp8"][1] - res["bf16"][1]).max() * 1e3)
     out["sigma_max_diff_mev_fp8_vs_bf16"] = float(np.abs(res["fp8"][0] - res["bf16"][0]).max()
                                                   * 1e3)
+    out["qp_diff_mev_fp8_deq_vs_bf16"] = float(np.abs(res["fp8_deq"][1] - res["bf16"][1]).max()
+                                               * 1e3)
+    out["sigma_max_diff_mev_fp8_deq_vs_bf16"] = float(
+        np.abs(res["fp8_deq"][0] - res["bf16"][0]).max() * 1e3)
     out["sigma_scale_mev"] = float(np.abs(res["bf16"][0]).max() * 1e3)
     L.lgw_release_system(s)
     L.lgw_destroy(h)
@@ -923,7 +930,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="one small call for kernel profiles (mid-size system, 64 start "
                          "vectors, k 48, CGS1K; about 3 GB on the device) and its report")
-    ap.add_argument("--profile-precision", default="bf16", choices=["bf16", "fp8", "fp64"])
+    ap.add_argument("--profile-precision", default="bf16",
+                    choices=["bf16", "fp8", "fp8_deq", "fp64"])
     ap.add_argument("--profile-reorth", default="dcgs", choices=["dcgs", "cgs1k", "cgs2"])
     ap.add_argument("--profile-vectors", type=int, default=64)
     ap.add_argument("--profile-k", type=int, default=48)

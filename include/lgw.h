@@ -67,10 +67,17 @@ typedef enum {
 typedef enum {
   LGW_FP64 = 0,   /* FP64 CUDA-core GEMMs: the plain FP64 path            */
   LGW_BF16 = 1,   /* BF16 tcgen05 tensor-core GEMMs, FP32 accumulate      */
-  LGW_FP8 = 3     /* E4M3 tcgen05 GEMMs (kind::f8f6f4), FP32 accumulate:
+  LGW_FP8 = 3,    /* E4M3 tcgen05 GEMMs (kind::f8f6f4), FP32 accumulate:
                      L with one power-of-two scale per column (max -> (224,
                      448]), the per-step operands Delta^1/2 q and y with one
                      power-of-two scale per vector; 2 is reserved          */
+  LGW_FP8_DEQ = 4 /* L in E4M3 as for LGW_FP8 (the same copies, half the
+                     bytes of BF16), loaded by TMA and widened to FP16 in
+                     shared memory (exact for every E4M3 value); the
+                     per-step operands in FP16 with one power-of-two scale
+                     per vector (largest value in (2^14, 2^15]); kind::f16
+                     tcgen05 GEMMs, FP32 accumulate.  Only L is rounded to
+                     8 bits.                                              */
 } lgw_precision;
 
 typedef enum {
@@ -127,7 +134,7 @@ typedef struct lgw_system lgw_system;
  *                    BF16 tensor-core product, so the BF16 copies are needed)
  *   LGW_SYS_NO_BF16  no BF16 copies (L, L^T, low half): precision LGW_BF16
  *                    is unsupported; start vectors from M use the FP64 copy
- *   LGW_SYS_FP8      make the E4M3 copies now (otherwise on the first FP8
+ *   LGW_SYS_FP8      make the E4M3 copies now (otherwise on the first FP8 or FP8_DEQ
  *                    request; with LGW_SYS_NO_FP64 they are always made now)
  * Every copy is made straight from desc->L, so a caller may free its L once
  * lgw_prepare_system has returned (device memory at N_vc = 1.6M, N_aux =
@@ -387,7 +394,7 @@ lgw_status lgw_lanczos_coeffs_poly(lgw_handle *h, const lgw_system *s, const lgw
  * p(p+1)/2 elements, where lgw_sigma_offdiag runs two per pair.  Exact once
  * the block Krylov space is exhausted.
  *   sigma [n_t][n_t][n_freq][2] (symmetric); rep or NULL.
- * Limits: precision FP64 or BF16 (LGW_ERR_UNSUPPORTED for E4M3), k <= 512;
+ * Limits: precision FP64 or BF16 (LGW_ERR_UNSUPPORTED for either E4M3 mode), k <= 512;
  * o->reorth is not used (always two projections); the static shift and QP
  * options are not used.  Scratch: k^2 doubles per (m, element vector). */
 lgw_status lgw_sigma_band(lgw_handle *h, const lgw_system *s, const lgw_problem *p,

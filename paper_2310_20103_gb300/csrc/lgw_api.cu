@@ -358,7 +358,8 @@ Opts resolve_opts(lgw_handle *h, const lgw_options *o, const SysDev &s) {
     set_err(h, LGW_ERR_UNSUPPORTED, "k = %d above the 4095-step limit of this build", r.k);
     throw Fail{LGW_ERR_UNSUPPORTED};
   }
-  if (r.precision != LGW_FP64 && r.precision != LGW_BF16 && r.precision != LGW_FP8) {
+  if (r.precision != LGW_FP64 && r.precision != LGW_BF16 && r.precision != LGW_FP8 &&
+      r.precision != LGW_FP8_DEQ) {
     set_err(h, LGW_ERR_ARG, "unknown precision %d", r.precision);
     throw Fail{LGW_ERR_ARG};
   }
@@ -411,7 +412,7 @@ void ensure_copies(lgw_handle *h, const lgw_system *csys, const Opts &o) {
     set_err(h, LGW_ERR_UNSUPPORTED, "the system keeps no BF16 copy of L (LGW_SYS_NO_BF16)");
     throw Fail{LGW_ERR_UNSUPPORTED};
   }
-  if (o.precision != LGW_FP8 || cs.L8) return;
+  if ((o.precision != LGW_FP8 && o.precision != LGW_FP8_DEQ) || cs.L8) return;
   if (!cs.L64) {
     set_err(h, LGW_ERR_UNSUPPORTED, "no E4M3 copy of L and no FP64 copy to make it from");
     throw Fail{LGW_ERR_UNSUPPORTED};
@@ -527,6 +528,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   LGW_TRY_CUDA(h, cudaMemsetAsync(beta, 0, sizeof(double) * B * k, st));
   const bool tc = o.precision != LGW_FP64;
   const bool fp8 = o.precision == LGW_FP8;
+  const bool deq = o.precision == LGW_FP8_DEQ;
   int nsub_req = o.b_sub > 0 ? o.b_sub : std::min(B, 512);
   nsub_req = std::min(nsub_req, B);
   int Bs = round_up(nsub_req, PAD_VEC);
@@ -562,6 +564,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
     c.blo = o.split32 ? nullptr : wsT<float>(h, "basis_lo", (size_t)(k + 1) * Bs * N);
   }
   c.dsqf = s.dsqf;
+  c.d2lo = s.d2lo;
   // float [Bs][N]: the split-basis epilogue output (c_K Delta^1/2 U) and, at
   // the start of each sub-batch, the tensor-core coupling vectors V = L M
   float *ucd_buf = tc ? wsT<float>(h, "ucd", (size_t)Bs * N) : nullptr;
@@ -601,6 +604,12 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
     // FP64 contractions leave C w in the w buffer
     c.wv = slot_ptr(c, 0);
     c.uC = tc ? nullptr : c.w;
+    if (tc) {
+      // a float pair in the same memory: the sweep's double-float arithmetic
+      // reads and writes it without FP64 conversions
+      c.wvh = reinterpret_cast<float *>(c.wv);
+      c.wvl = c.wvh + (size_t)Bs * N;
+    }
     c.hj_part = wsT<double>(h, "hj_part", (size_t)Bs * nchunks);
     c.gq = wsT<double>(h, "gq", (size_t)Bs * kmax1);
   }
@@ -613,6 +622,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   double *Yp64 = tc ? nullptr : wsT<double>(h, "yp64", (size_t)splits64 * Bs * s.A);
   TcPlan *plan = nullptr;
   uint8_t *x8 = nullptr, *y8 = nullptr;
+  uint16_t *x16 = nullptr, *y16 = nullptr;
   float *sx = nullptr, *ty = nullptr;
   float *Yp32 = nullptr;
   __nv_bfloat16 *Yh = nullptr;
@@ -627,10 +637,21 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
       set_err(h, LGW_ERR_CUDA, "%s", err);
       throw Fail{LGW_ERR_CUDA};
     }
-    if (!fp8 && !tc_plan_has_bf16(plan)) {
+    if (!fp8 && !deq && !tc_plan_has_bf16(plan)) {
       tc_plan_destroy(plan);
       set_err(h, LGW_ERR_UNSUPPORTED, "BF16 contractions need the BF16 copies of L");
       throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    if (deq) {
+      x16 = wsT<uint16_t>(h, "x16", (size_t)Bs * N);
+      y16 = wsT<uint16_t>(h, "y16", (size_t)Bs * s.A);
+      sx = wsT<float>(h, "sx", (size_t)Bs);
+      ty = wsT<float>(h, "ty", (size_t)Bs);
+      if (!tc_plan_enable_deq(plan, s.L8t, s.L8, x16, y16, ty)) {
+        tc_plan_destroy(plan);
+        set_err(h, LGW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the widened E4M3 operands");
+        throw Fail{LGW_ERR_CUDA};
+      }
     }
     if (fp8) {
       x8 = wsT<uint8_t>(h, "x8", (size_t)Bs * N);
@@ -681,11 +702,16 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
       if (fp8) {
         launch_quant_x8(c.xh, Bs, N, x8, sx, st);
         check_launch(h, "quant_x8");
+      } else if (deq) {
+        launch_quant_x16(c.xh, Bs, N, x16, sx, st);
+        check_launch(h, "quant_x16");
       }
       launch_gemm1_tc(plan, h->d_status, st);
       check_launch(h, "gemm1_tc");
       if (fp8)
         launch_reduce_y_fp8(Yp32, splits_tc, Bs, s.A, sx, s.sL, y8, ty, nullptr, 1, st);
+      else if (deq)
+        launch_reduce_y_f16(Yp32, splits_tc, Bs, s.A, sx, s.sL, y16, ty, nullptr, 1, st);
       else
         launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, nullptr, st);
       check_launch(h, "reduce_y");
@@ -795,11 +821,16 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
           if (fp8) {
             launch_quant_x8(c.xh, Bs, N, x8, sx, st, vscale);
             check_launch(h, "quant_x8");
+          } else if (deq) {
+            launch_quant_x16(c.xh, Bs, N, x16, sx, st, vscale);
+            check_launch(h, "quant_x16");
           }
           launch_gemm1_tc(plan, h->d_status, st);
           check_launch(h, "gemm1_tc");
           if (fp8)
             launch_reduce_y_fp8(Yp32, splits_tc, Bs, s.A, sx, s.sL, y8, ty, yy, c.n_yb, st);
+          else if (deq)
+            launch_reduce_y_f16(Yp32, splits_tc, Bs, s.A, sx, s.sL, y16, ty, yy, c.n_yb, st);
           else
             launch_reduce_y_bf16(Yp32, splits_tc, Bs, s.A, Yh, yy, st, vscale);
           check_launch(h, "reduce_y");
@@ -1284,11 +1315,12 @@ const SysDev &tda_view(lgw_handle *h, const lgw_system *csys) {
   if (!sys->tda_buf) {
     const size_t N = (size_t)s.N;
     void *buf = nullptr;
-    LGW_TRY_CUDA(h, cudaMalloc(&buf, N * (2 * sizeof(double) + 3 * sizeof(float))));
+    LGW_TRY_CUDA(h, cudaMalloc(&buf, N * (2 * sizeof(double) + 4 * sizeof(float))));
     sys->tda_buf = buf;
     double *ones = static_cast<double *>(buf), *cd = ones + N;
     float *onesf = reinterpret_cast<float *>(cd + N), *d2f = onesf + N, *cdf = d2f + N;
-    launch_tda_view(s.Delta, s.n_vc, s.N, 0.5 * s.kf, ones, cd, onesf, d2f, cdf, h->stream);
+    launch_tda_view(s.Delta, s.n_vc, s.N, 0.5 * s.kf, ones, cd, onesf, d2f, cdf + N, cdf,
+                    h->stream);
     check_launch(h, "tda_view");
   }
   const size_t N = (size_t)s.N;
@@ -1302,6 +1334,7 @@ const SysDev &tda_view(lgw_handle *h, const lgw_system *csys) {
   t.cd = cd;
   t.dsqf = onesf;
   t.d2f = d2f;
+  t.d2lo = cdf + N;
   t.cdf = cdf;
   return t;
 }
@@ -1536,7 +1569,8 @@ lgw_status lgw_prepare_system(lgw_handle *h, const lgw_system_desc *d, lgw_syste
   s.Delta2 = (double *)alloc(sizeof(double) * s.N);
   s.cd = (double *)alloc(sizeof(double) * s.N);
   s.dsqf = (float *)alloc(sizeof(float) * s.N);
-  s.d2f = (float *)alloc(sizeof(float) * s.N);
+  s.d2f = (float *)alloc(2 * sizeof(float) * s.N);   // d2f, then d2lo
+  s.d2lo = s.d2f ? s.d2f + s.N : nullptr;
   s.cdf = (float *)alloc(sizeof(float) * s.N);
   bool ok = s.eps && s.Delta && s.dsq && s.Delta2 && s.cd && s.dsqf && s.d2f && s.cdf;
   if (ok && keep64) ok = (s.L64 = (double *)alloc(sizeof(double) * (size_t)s.N * s.A)) != nullptr;
@@ -1612,13 +1646,15 @@ lgw_status lgw_apply_casida(lgw_handle *h, const lgw_system *sys, int32_t n_vec,
   if (!sys || sys->h != h || n_vec < 0 || (n_vec > 0 && (!X || !Y)))
     return set_err(h, LGW_ERR_ARG, "bad arguments to lgw_apply_casida");
   if (n_vec == 0) return LGW_OK;
-  if (precision != LGW_FP64 && precision != LGW_BF16 && precision != LGW_FP8)
+  if (precision != LGW_FP64 && precision != LGW_BF16 && precision != LGW_FP8 &&
+      precision != LGW_FP8_DEQ)
     return set_err(h, LGW_ERR_ARG, "bad precision");
   try {
     const SysDev &s = sys->s;
     cudaStream_t st = h->stream;
     const bool tc = precision != LGW_FP64;
     const bool fp8 = precision == LGW_FP8;
+    const bool deq = precision == LGW_FP8_DEQ;
     if (tc && !tc_available()) {
       set_err(h, LGW_ERR_UNSUPPORTED, "tensor-core paths need an sm_103 device");
       throw Fail{LGW_ERR_UNSUPPORTED};
@@ -1668,10 +1704,26 @@ lgw_status lgw_apply_casida(lgw_handle *h, const lgw_system *sys, int32_t n_vec,
         launch_quant_x8(xh, Bs, s.N, x8, sx, st);
         check_launch(h, "quant_x8");
       }
+      uint16_t *x16 = nullptr, *y16 = nullptr;
+      if (deq) {
+        x16 = wsT<uint16_t>(h, "ap_x16", (size_t)Bs * s.N);
+        y16 = wsT<uint16_t>(h, "ap_y16", (size_t)Bs * s.A);
+        sx = wsT<float>(h, "ap_sx", (size_t)Bs);
+        ty = wsT<float>(h, "ap_ty", (size_t)Bs);
+        if (!tc_plan_enable_deq(plan, s.L8t, s.L8, x16, y16, ty)) {
+          tc_plan_destroy(plan);
+          set_err(h, LGW_ERR_CUDA, "cuTensorMapEncodeTiled failed for the widened E4M3 operands");
+          throw Fail{LGW_ERR_CUDA};
+        }
+        launch_quant_x16(xh, Bs, s.N, x16, sx, st);
+        check_launch(h, "quant_x16");
+      }
       launch_gemm1_tc(plan, h->d_status, st);
       check_launch(h, "gemm1_tc");
       if (fp8)
         launch_reduce_y_fp8(yp, splits, Bs, s.A, sx, s.sL, y8, ty, nullptr, 1, st);
+      else if (deq)
+        launch_reduce_y_f16(yp, splits, Bs, s.A, sx, s.sL, y16, ty, nullptr, 1, st);
       else
         launch_reduce_y_bf16(yp, splits, Bs, s.A, yh, nullptr, st);
       check_launch(h, "reduce_y");
@@ -1885,7 +1937,7 @@ lgw_status lgw_sigma_band(lgw_handle *h, const lgw_system *sys, const lgw_proble
     }
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     Opts op = resolve_opts(h, o, s);
-    if (op.precision == LGW_FP8) {
+    if (op.precision == LGW_FP8 || op.precision == LGW_FP8_DEQ) {
       set_err(h, LGW_ERR_UNSUPPORTED, "band Lanczos runs FP64 or BF16 contractions");
       throw Fail{LGW_ERR_UNSUPPORTED};
     }

@@ -23,7 +23,7 @@ LGW_OK = 0
 STATUS_NAMES = {0: "LGW_OK", 1: "LGW_ERR_ARG", 2: "LGW_ERR_SHAPE", 3: "LGW_ERR_CUDA",
                 4: "LGW_ERR_OOM", 5: "LGW_ERR_NOT_SPD", 6: "LGW_ERR_NO_CONVERGENCE",
                 7: "LGW_ERR_TIMEOUT", 8: "LGW_ERR_UNSUPPORTED"}
-PRECISION = {"fp64": 0, "bf16": 1, "fp8": 3}
+PRECISION = {"fp64": 0, "bf16": 1, "fp8": 3, "fp8_deq": 4}
 REORTH = {"none": 0, "cgs2": 1, "cgs1k": 2, "dcgs": 3}
 REORTH_ARITH = {"auto": 0, "fp64": 1, "split": 2, "split32": 3}
 QP_MODE = {"graphical": 0, "linearised": 1}

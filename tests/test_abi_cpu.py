@@ -77,7 +77,8 @@ def test_binding_offsets_match_c_compiler(tmp_path):
                "lgw_poly": L.lgw_poly,
                "lgw_options": L.lgw_options, "lgw_report": L.lgw_report}
     enums = {"LGW_FP64": L.PRECISION["fp64"], "LGW_BF16": L.PRECISION["bf16"],
-             "LGW_FP8": L.PRECISION["fp8"], "LGW_REORTH_NONE": L.REORTH["none"],
+             "LGW_FP8": L.PRECISION["fp8"], "LGW_FP8_DEQ": L.PRECISION["fp8_deq"],
+             "LGW_REORTH_NONE": L.REORTH["none"],
              "LGW_REORTH_CGS2": L.REORTH["cgs2"], "LGW_REORTH_CGS1K": L.REORTH["cgs1k"],
              "LGW_RA_AUTO": L.REORTH_ARITH["auto"], "LGW_RA_FP64": L.REORTH_ARITH["fp64"],
              "LGW_RA_SPLIT": L.REORTH_ARITH["split"], "LGW_RA_SPLIT32": L.REORTH_ARITH["split32"],
