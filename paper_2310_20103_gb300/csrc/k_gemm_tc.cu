@@ -41,19 +41,25 @@ constexpr int NTHREADS = 192;
 // (tensor memory: 2 x BN <= 512 columns).  Used for the store-only
 // contraction, whose K loop is short.
 // DEQ: the A operand arrives as E4M3 (RAW_BYTES per stage, 64 bytes by 128
-// rows) and is widened to FP16 in shared memory next to the B tile.
+// rows) next to the B tile, and is widened to FP16 into a ring of its own
+// (A_SLOTS tiles ahead of the TMA stages), so the TMA ring stays as deep as
+// the BF16 one while the conversion runs one K block ahead of the MMAs.
 template <int BN, int HALF = 0, bool DEQ = false>
 struct Cfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int RAW_BYTES = DEQ ? BM * BK : 0;
-  static constexpr int STAGE = A_BYTES + B_BYTES + RAW_BYTES;
+  static constexpr int A_SLOTS = DEQ ? 2 : 0;
+  static constexpr int A_RING = A_SLOTS * A_BYTES;
+  static constexpr int B_OFF = DEQ ? 0 : A_BYTES;   // B tile within a stage
+  static constexpr int RAW_OFF = B_OFF + B_BYTES;
+  static constexpr int STAGE = (DEQ ? 0 : A_BYTES) + B_BYTES + RAW_BYTES;
   static constexpr int STAGES =
-      DEQ ? (BN == 256 ? 3 : (BN == 128 ? 5 : 6))
+      DEQ ? (BN == 256 ? 4 : (BN == 128 ? 6 : 8))
           : (((BN == 256) ? 4 : (BN == 128 ? 6 : 8)) >> HALF);
   static constexpr int BAR_BYTES = 256;
   static constexpr int RED_BYTES = 4 * BN * 8;
-  static constexpr int SMEM = 1024 + STAGES * STAGE + BAR_BYTES + RED_BYTES;
+  static constexpr int SMEM = 1024 + A_RING + STAGES * STAGE + BAR_BYTES + RED_BYTES;
   static constexpr uint32_t TMEM_COLS = BN;
 };
 
@@ -279,10 +285,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE);
+  uint8_t *aring = smem;                 // DEQ: widened A tiles
+  uint8_t *stages = smem + C::A_RING;
+  uint64_t *full = reinterpret_cast<uint64_t *>(stages + C::STAGES * C::STAGE);
   uint64_t *empty = full + C::STAGES;
-  uint64_t *conv = empty + C::STAGES;   // DEQ: the stage's A tile is widened
-  uint64_t *tfull = conv + (DEQ ? C::STAGES : 0);
+  uint64_t *conv = empty + C::STAGES;    // DEQ: A slot widened (4 warps)
+  uint64_t *afree = conv + C::A_SLOTS;   // DEQ: A slot read by the MMAs
+  uint64_t *tfull = afree + C::A_SLOTS;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(tfull + 1);
   double *red = reinterpret_cast<double *>(smem + C::STAGES * C::STAGE + C::BAR_BYTES);
 
@@ -307,7 +316,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      if (DEQ) mbar_init(&conv[s], 4);   // one arrival per converting warp
+    }
+    for (int a = 0; a < C::A_SLOTS; ++a) {
+      mbar_init(&conv[a], 4);   // one arrival per converting warp
+      mbar_init(&afree[a], 1);
     }
     mbar_init(tfull, 1);
     fence_barrier_init();
@@ -325,14 +337,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int s = it % C::STAGES;
         const uint32_t ph = (it / C::STAGES) & 1;
         if (!mbar_wait(&empty[s], ph ^ 1, ea.status)) break;
-        mbar_expect_tx(&full[s], C::STAGE - (DEQ ? C::A_BYTES : 0));
-        uint8_t *sa = smem + s * C::STAGE;
+        mbar_expect_tx(&full[s], C::STAGE);
+        uint8_t *sa = stages + s * C::STAGE;
         const int kb = kb0 + (it + (ea.rot ? m_tile : 0)) % nk;
         const int kx = kb * (EB == 1 ? 128 : 64);
         if (DEQ) {
           // E4M3 A: half of a 128-element K block (K-block-major) or the
           // 64 columns kx.. of a row-major operand; 64 bytes by 128 rows
-          uint8_t *raw = sa + C::A_BYTES + C::B_BYTES;
+          uint8_t *raw = sa + C::RAW_OFF;
           if (ea.a3)
             tma_load_3d(raw, &tmA, &full[s], (kb & 1) * 64, m_tile * BM, kb >> 1);
           else
@@ -343,9 +355,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tma_load_2d(sa, &tmA, &full[s], kx, m_tile * BM);
         }
         if (ea.b3)
-          tma_load_3d(sa + C::A_BYTES, &tmB, &full[s], 0, n_tile * BN, kb);
+          tma_load_3d(sa + C::B_OFF, &tmB, &full[s], 0, n_tile * BN, kb);
         else
-          tma_load_2d(sa + C::A_BYTES, &tmB, &full[s], kx, n_tile * BN);
+          tma_load_2d(sa + C::B_OFF, &tmB, &full[s], kx, n_tile * BN);
         issued = it + 1;
       }
       // Drain: every issued copy must have landed before the CTA may exit.
@@ -360,10 +372,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int s = it % C::STAGES;
         const uint32_t ph = (it / C::STAGES) & 1;
         if (!mbar_wait(&full[s], ph, ea.status)) break;
-        if (DEQ && !mbar_wait(&conv[s], ph, ea.status)) break;
+        if (DEQ && !mbar_wait(&conv[it & 1], (it >> 1) & 1, ea.status)) break;
         tc_fence_after();
-        const uint32_t sa = smem_u32(smem + s * C::STAGE);
-        const uint64_t da = make_sdesc(sa), db = make_sdesc(sa + C::A_BYTES);
+        const uint32_t sb = smem_u32(stages + s * C::STAGE);
+        const uint32_t sa = DEQ ? smem_u32(aring + (it & 1) * C::A_BYTES) : sb;
+        const uint64_t da = make_sdesc(sa), db = make_sdesc(sb + C::B_OFF);
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk)
           if (EB != 1)
@@ -371,6 +384,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           else
             umma_e4m3(tmem, da + 2 * kk, db + 2 * kk, idesc, (it > 0 || kk > 0) ? 1u : 0u);
         umma_commit(&empty[s]);
+        if (DEQ) umma_commit(&afree[it & 1]);
       }
       umma_commit(tfull);
     }
@@ -387,8 +401,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int s = it % C::STAGES;
         const uint32_t ph = (it / C::STAGES) & 1;
         if (!mbar_wait(&full[s], ph, ea.status)) break;
-        uint8_t *sa = smem + s * C::STAGE;
-        const uint8_t *raw = sa + C::A_BYTES + C::B_BYTES;
+        // the A slot is free once the MMAs of K block it - 2 are done
+        if (!mbar_wait(&afree[it & 1], ((it >> 1) & 1) ^ 1, ea.status)) break;
+        uint8_t *sa = aring + (it & 1) * C::A_BYTES;
+        const uint8_t *raw = stages + s * C::STAGE + C::RAW_OFF;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           const int i = 128 * p + ct;
@@ -400,7 +416,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&conv[s]);
+        if (lane == 0) mbar_arrive(&conv[it & 1]);
       }
     }
     // ------------------------------ epilogue ------------------------------

@@ -51,52 +51,6 @@ __device__ __forceinline__ void two_sum_acc(float &s_hi, float &s_lo, float p) {
   s_lo = __fadd_rn(s_lo, err);
 }
 
-// ---------------------------------------------------------------------------
-// Double-float arithmetic on the FP32 pipe (Dekker 1971; Knuth's TwoSum):
-// a value is an unevaluated sum hi + lo with |lo| <= ulp(hi) / 2, 48
-// significant bits.  On this part FP64 runs at 2 lanes per SM clock and
-// FP32 at 128, so a double-float product (7 FP32 operations) or sum (about
-// 20) costs a fraction of one FP64 operation, and the pair needs no FP64
-// conversions.  Products drop lo * lo (relative error about 2^-46).
-// ---------------------------------------------------------------------------
-struct dfl {
-  float h, l;
-};
-// a + b for |a| >= |b| (or a = 0)
-__device__ __forceinline__ dfl df_fast(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ dfl df_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-  const float p = __fmul_rn(a.h, b.h);
-  float e = __fmaf_rn(a.h, b.h, -p);
-  e = __fmaf_rn(a.h, b.l, e);
-  e = __fmaf_rn(a.l, b.h, e);
-  return df_fast(p, e);
-}
-// accurate sum of two pairs (both parts by TwoSum), exact under cancellation
-// up to the final rounding
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-  dfl s = df_two_sum(a.h, b.h);
-  const dfl t = df_two_sum(a.l, b.l);
-  s = df_fast(s.h, __fadd_rn(s.l, t.h));
-  return df_fast(s.h, __fadd_rn(s.l, t.l));
-}
-__device__ __forceinline__ dfl df_add_f(dfl a, float b) {
-  const dfl s = df_two_sum(a.h, b);
-  return df_fast(s.h, __fadd_rn(s.l, a.l));
-}
-__device__ __forceinline__ dfl df_from(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
-
 // Double-float sum of two (hi, lo) pairs.
 __device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl) {
   const float s = __fadd_rn(ah, bh);
@@ -482,19 +436,13 @@ __global__ void __launch_bounds__(VEC_THREADS) k_start_split(VecCtx c) {
       q2.x *= inv;
       q2.y *= inv;
     }
+    *reinterpret_cast<double2 *>(qn + e) = q2;
     const float hx = __double2float_rn(q2.x), hy = __double2float_rn(q2.y);
-    const float2 lo2 = make_float2(__double2float_rn(q2.x - (double)hx),
-                                   __double2float_rn(q2.y - (double)hy));
-    if (c.wvh != nullptr) {
-      // the delayed sweep carries q_0 as a float pair
-      *reinterpret_cast<float2 *>(c.wvh + voff + e) = make_float2(hx, hy);
-      *reinterpret_cast<float2 *>(c.wvl + voff + e) = lo2;
-    } else {
-      *reinterpret_cast<double2 *>(qn + e) = q2;
-    }
     dq = fmaf(c.d2f[e] * hx, hx, fmaf(c.d2f[e + 1] * hy, hy, dq));
     *reinterpret_cast<float2 *>(hn + e) = make_float2(hx, hy);
-    if (ln != nullptr) *reinterpret_cast<float2 *>(ln + e) = lo2;
+    if (ln != nullptr)
+      *reinterpret_cast<float2 *>(ln + e) = make_float2(__double2float_rn(q2.x - (double)hx),
+                                                        __double2float_rn(q2.y - (double)hy));
     if (c.xh != nullptr) {
       __nv_bfloat162 x2;
       x2.x = __float2bfloat16_rn(c.dsqf[e] * hx);
@@ -819,57 +767,59 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
   // held in registers through it.
   float vh[8], vl[8], corr[8], cv[8];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) vh[m] = vl[m] = corr[m] = cv[m] = 0.0f;
-  // scalars of the double-float form, split once per thread
-  const dfl si = df_from(sinv), nal = df_from(-alpha), nbj = df_from(-bj);
-#pragma unroll
   for (int u = 0; u < 2; ++u) {
     const int e = ebase + 128 * u;
-    if (e >= c.N) continue;
-    float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), pl = ph;
-    if (j >= 1) {
-      ph = *reinterpret_cast<const float4 *>(bhi_row(c, j - 1, b) + e);
-      if (LO) pl = *reinterpret_cast<const float4 *>(blo_row(c, j - 1, b) + e);
+    double qt[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      vh[4 * u + t] = 0.0f;
+      vl[4 * u + t] = 0.0f;
+      corr[4 * u + t] = 0.0f;
+      cv[4 * u + t] = 0.0f;
     }
-    if constexpr (F64U) {
-      const double2 w0 = *reinterpret_cast<const double2 *>(c.wv + voff + e);
-      const double2 w1 = *reinterpret_cast<const double2 *>(c.wv + voff + e + 2);
-      const double wq[4] = {w0.x, w0.y, w1.x, w1.y};
+    if (e >= c.N) continue;
+    const double2 w0 = *reinterpret_cast<const double2 *>(c.wv + voff + e);
+    const double2 w1 = *reinterpret_cast<const double2 *>(c.wv + voff + e + 2);
+    const double wq[4] = {w0.x, w0.y, w1.x, w1.y};
+    double uu[4];
+    if (F64U) {
       const double2 a0 = *reinterpret_cast<const double2 *>(c.uC + voff + e);
       const double2 a1 = *reinterpret_cast<const double2 *>(c.uC + voff + e + 2);
       const double av[4] = {a0.x, a0.y, a1.x, a1.y};
-      const double qp[4] = {(double)ph.x + (double)pl.x, (double)ph.y + (double)pl.y,
-                            (double)ph.z + (double)pl.z, (double)ph.w + (double)pl.w};
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const int m = 4 * u + t;
-        const double qt = wq[t] * sinv;
-        const double vd = fma(-bj, qp[t], fma(-alpha, qt, av[t] * sinv));
-        vh[m] = __double2float_rn(vd);
-        vl[m] = __double2float_rn(vd - (double)vh[m]);
+        qt[t] = wq[t] * sinv;
+        uu[t] = av[t] * sinv;
       }
     } else {
-      // v = (Delta^2 - alpha~) q~ + c_K Delta^1/2 L Y^ - beta_j q_{j-1}  (Eq. 4, 13)
-      // in double-float: the carried w_{j-1} and Delta^2 are float pairs
       const float4 uk = *reinterpret_cast<const float4 *>(c.ucd + kblk_f32(b, e, c.Bs));
-      const float4 wh = *reinterpret_cast<const float4 *>(c.wvh + voff + e);
-      const float4 wl = *reinterpret_cast<const float4 *>(c.wvl + voff + e);
-      const float4 dh = *reinterpret_cast<const float4 *>(c.d2f + e);
-      const float4 dl = *reinterpret_cast<const float4 *>(c.d2lo + e);
-      const float whv[4] = {wh.x, wh.y, wh.z, wh.w}, wlv[4] = {wl.x, wl.y, wl.z, wl.w};
-      const float dhv[4] = {dh.x, dh.y, dh.z, dh.w}, dlv[4] = {dl.x, dl.y, dl.z, dl.w};
-      const float phv[4] = {ph.x, ph.y, ph.z, ph.w}, plv[4] = {pl.x, pl.y, pl.z, pl.w};
+      const double2 d0 = *reinterpret_cast<const double2 *>(c.Delta2 + e);
+      const double2 d1 = *reinterpret_cast<const double2 *>(c.Delta2 + e + 2);
+      const double dd[4] = {d0.x, d0.y, d1.x, d1.y};
       const float ku[4] = {uk.x, uk.y, uk.z, uk.w};
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const int m = 4 * u + t;
-        const dfl qt = df_mul({whv[t], wlv[t]}, si);
-        dfl v = df_mul(df_add({dhv[t], dlv[t]}, nal), qt);
-        v = df_add_f(v, ku[t]);
-        v = df_add(v, df_mul(nbj, {phv[t], plv[t]}));
-        vh[m] = v.h;
-        vl[m] = v.l;
+        qt[t] = wq[t] * sinv;
+        // C q~ = Delta^2 q~ + c_K Delta^1/2 L L^T Delta^1/2 q~   (Eq. 4)
+        uu[t] = fma(dd[t], qt[t], (double)ku[t]);
       }
+    }
+    double qp[4] = {0.0, 0.0, 0.0, 0.0};
+    if (j >= 1) {
+      const float4 ph = *reinterpret_cast<const float4 *>(bhi_row(c, j - 1, b) + e);
+      const float4 pl = LO ? *reinterpret_cast<const float4 *>(blo_row(c, j - 1, b) + e)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      qp[0] = (double)ph.x + (double)pl.x;
+      qp[1] = (double)ph.y + (double)pl.y;
+      qp[2] = (double)ph.z + (double)pl.z;
+      qp[3] = (double)ph.w + (double)pl.w;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int m = 4 * u + t;
+      const double vd = fma(-bj, qp[t], fma(-alpha, qt[t], uu[t]));
+      vh[m] = __double2float_rn(vd);
+      vl[m] = __double2float_rn(vd - (double)vh[m]);
     }
   }
 
@@ -897,64 +847,31 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
   float *hn = c.bhi + ((size_t)j * c.Bs + b) * c.N;
   float *ln = LO ? c.blo + ((size_t)j * c.Bs + b) * c.N : nullptr;
   double hj = 0.0, nrm = 0.0;
-  float hjh = 0.f, hjl = 0.f, nrh = 0.f, nrl = 0.f;   // double-float partials
   float dq = 0.0f;
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     const int e = ebase + 128 * u;
     if (e >= c.N) continue;
     float qh4[4], ql4[4];
-    if constexpr (F64U) {
-      double vd[4];
-      const double2 w0 = *reinterpret_cast<const double2 *>(c.wv + voff + e);
-      const double2 w1 = *reinterpret_cast<const double2 *>(c.wv + voff + e + 2);
-      const double wq[4] = {w0.x, w0.y, w1.x, w1.y};
+    double vd[4];
+    const double2 w0 = *reinterpret_cast<const double2 *>(c.wv + voff + e);
+    const double2 w1 = *reinterpret_cast<const double2 *>(c.wv + voff + e + 2);
+    const double wq[4] = {w0.x, w0.y, w1.x, w1.y};
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int m = 4 * u + t;
-        vd[t] = ((double)vh[m] + (double)vl[m]) - (double)cv[m];   // w_j = v - Q_{j-1} g
-        vh[m] = __double2float_rn(vd[t]);
-        const double qj = wq[t] * sinv - (double)corr[m];
-        qh4[t] = __double2float_rn(qj);
-        ql4[t] = __double2float_rn(qj - (double)qh4[t]);
-        hj = fma(qj, vd[t], hj);
-        nrm = fma(vd[t], vd[t], nrm);
-      }
-      *reinterpret_cast<double2 *>(c.wv + voff + e) = make_double2(vd[0], vd[1]);
-      *reinterpret_cast<double2 *>(c.wv + voff + e + 2) = make_double2(vd[2], vd[3]);
-    } else {
-      const float4 wh = *reinterpret_cast<const float4 *>(c.wvh + voff + e);
-      const float4 wl = *reinterpret_cast<const float4 *>(c.wvl + voff + e);
-      const float whv[4] = {wh.x, wh.y, wh.z, wh.w}, wlv[4] = {wl.x, wl.y, wl.z, wl.w};
-      float nh[4], nl[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int m = 4 * u + t;
-        const dfl wj = df_add_f({vh[m], vl[m]}, -cv[m]);              // w_j = v - Q_{j-1} g
-        const dfl qj = df_add_f(df_mul({whv[t], wlv[t]}, si), -corr[m]);   // q~_j - Q c
-        qh4[t] = qj.h;
-        ql4[t] = qj.l;
-        nh[t] = wj.h;
-        nl[t] = wj.l;
-        vh[m] = wj.h;
-        // q_j . w_j and ||w_j||^2: TwoProd with the cross terms, TwoSum
-        // into the thread's pair
-        float pr = __fmul_rn(qj.h, wj.h);
-        float er = __fmaf_rn(qj.h, wj.h, -pr);
-        er = __fmaf_rn(qj.h, wj.l, __fmaf_rn(qj.l, wj.h, er));
-        two_sum_acc(hjh, hjl, pr);
-        hjl = __fadd_rn(hjl, er);
-        pr = __fmul_rn(wj.h, wj.h);
-        er = __fmaf_rn(wj.h, wj.h, -pr);
-        er = __fmaf_rn(2.0f * wj.h, wj.l, er);
-        two_sum_acc(nrh, nrl, pr);
-        nrl = __fadd_rn(nrl, er);
-      }
-      *reinterpret_cast<float4 *>(c.wvh + voff + e) = make_float4(nh[0], nh[1], nh[2], nh[3]);
-      *reinterpret_cast<float4 *>(c.wvl + voff + e) = make_float4(nl[0], nl[1], nl[2], nl[3]);
+    for (int t = 0; t < 4; ++t) {
+      const int m = 4 * u + t;
+      vd[t] = ((double)vh[m] + (double)vl[m]) - (double)cv[m];   // w_j = v - Q_{j-1} g
+      vh[m] = __double2float_rn(vd[t]);
+      const double qj = wq[t] * sinv - (double)corr[m];
+      qh4[t] = __double2float_rn(qj);
+      ql4[t] = __double2float_rn(qj - (double)qh4[t]);
+      hj = fma(qj, vd[t], hj);
+      nrm = fma(vd[t], vd[t], nrm);
     }
     *reinterpret_cast<float4 *>(hn + e) = make_float4(qh4[0], qh4[1], qh4[2], qh4[3]);
     if (LO) *reinterpret_cast<float4 *>(ln + e) = make_float4(ql4[0], ql4[1], ql4[2], ql4[3]);
+    *reinterpret_cast<double2 *>(c.wv + voff + e) = make_double2(vd[0], vd[1]);
+    *reinterpret_cast<double2 *>(c.wv + voff + e + 2) = make_double2(vd[2], vd[3]);
     if (c.xh != nullptr) {
       __nv_bfloat162 x01, x23;
       x01.x = __float2bfloat16_rn(c.dsqf[e] * vh[4 * u]);
@@ -970,10 +887,6 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_sweep_dcgs(VecCtx c, int j) 
 #pragma unroll
       for (int t = 0; t < 4; ++t) dq = fmaf(c.d2f[e + t] * vh[4 * u + t], vh[4 * u + t], dq);
     }
-  }
-  if constexpr (!F64U) {
-    hj = (double)hjh + (double)hjl;
-    nrm = (double)nrh + (double)nrl;
   }
   hj = block_sum(hj, red);
   nrm = block_sum(nrm, red);
@@ -1090,31 +1003,14 @@ __global__ void __launch_bounds__(VEC_THREADS) k_p2_update_dcgs(VecCtx c, int j)
       const int e = ebase + 128 * u;
       if (e >= c.N) continue;
       double w4[4];
-      if (c.wvh != nullptr) {
-        const float4 wh = *reinterpret_cast<const float4 *>(c.wvh + voff + e);
-        const float4 wl = *reinterpret_cast<const float4 *>(c.wvl + voff + e);
-        w4[0] = ((double)wh.x + (double)wl.x) - r[4 * u];
-        w4[1] = ((double)wh.y + (double)wl.y) - r[4 * u + 1];
-        w4[2] = ((double)wh.z + (double)wl.z) - r[4 * u + 2];
-        w4[3] = ((double)wh.w + (double)wl.w) - r[4 * u + 3];
-        float h4[4], l4[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          h4[t] = __double2float_rn(w4[t]);
-          l4[t] = __double2float_rn(w4[t] - (double)h4[t]);
-        }
-        *reinterpret_cast<float4 *>(c.wvh + voff + e) = make_float4(h4[0], h4[1], h4[2], h4[3]);
-        *reinterpret_cast<float4 *>(c.wvl + voff + e) = make_float4(l4[0], l4[1], l4[2], l4[3]);
-      } else {
-        const double2 w0 = *reinterpret_cast<const double2 *>(c.wv + voff + e);
-        const double2 w1 = *reinterpret_cast<const double2 *>(c.wv + voff + e + 2);
-        w4[0] = w0.x - r[4 * u];
-        w4[1] = w0.y - r[4 * u + 1];
-        w4[2] = w1.x - r[4 * u + 2];
-        w4[3] = w1.y - r[4 * u + 3];
-        *reinterpret_cast<double2 *>(c.wv + voff + e) = make_double2(w4[0], w4[1]);
-        *reinterpret_cast<double2 *>(c.wv + voff + e + 2) = make_double2(w4[2], w4[3]);
-      }
+      const double2 w0 = *reinterpret_cast<const double2 *>(c.wv + voff + e);
+      const double2 w1 = *reinterpret_cast<const double2 *>(c.wv + voff + e + 2);
+      w4[0] = w0.x - r[4 * u];
+      w4[1] = w0.y - r[4 * u + 1];
+      w4[2] = w1.x - r[4 * u + 2];
+      w4[3] = w1.y - r[4 * u + 3];
+      *reinterpret_cast<double2 *>(c.wv + voff + e) = make_double2(w4[0], w4[1]);
+      *reinterpret_cast<double2 *>(c.wv + voff + e + 2) = make_double2(w4[2], w4[3]);
       float f4[4];
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
@@ -1161,10 +1057,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_p2_dots_dcgs(VecCtx c, int j) {
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         vh[4 * u + t] = vl[4 * u + t] = 0.0f;
-        if (e < c.N && c.wvh != nullptr) {
-          vh[4 * u + t] = c.wvh[voff + e + t];
-          vl[4 * u + t] = c.wvl[voff + e + t];
-        } else if (e < c.N) {
+        if (e < c.N) {
           const double x = c.wv[voff + e + t];
           vh[4 * u + t] = __double2float_rn(x);
           vl[4 * u + t] = __double2float_rn(x - (double)vh[4 * u + t]);

@@ -47,8 +47,6 @@ struct SysDev {
   double *cd;       // [N]  c_K Delta^1/2
   float *dsqf;      // [N]  Delta^1/2 rounded to float (bf16 operand scaling)
   float *d2f;       // [N]  Delta^2 rounded to float   (alpha estimate)
-  float *d2lo;      // [N]  Delta^2 - d2f rounded to float: (d2f, d2lo) is Delta^2 as a
-                    //      double-float (the delayed sweep's FP32-pipe arithmetic)
   float *cdf;       // [N]  c_K Delta^1/2 rounded to float (FP32 epilogue)
   double *L64;      // [N][A] row-major, zero padded
   __nv_bfloat16 *Lb;    // [N][A]   K-major operand of the L Y contraction
@@ -101,9 +99,6 @@ struct VecCtx {
   unsigned *status;
   // delayed Gram-Schmidt (LGW_REORTH_DCGS)
   double *wv;             // [Bs][N] the carried vector w_j (unnormalised q~_{j+1} = w_j / beta_{j+1})
-  float *wvh, *wvl;       // [Bs][N] each: w_j as a float pair in wv's memory (tensor-core
-                          // contractions; null: w_j in FP64 in wv)
-  const float *d2lo;      // [N] second float of Delta^2
   const double *uC;       // [Bs][N] C w_j from the FP64 contractions, or null (tensor cores)
   double *hj_part;        // [Bs][nchunks] partials of q_j . w_j
   double *gq;             // [Bs][kmax1] g = (T_{j-1} - alpha~_j) h / beta_j, removed by the sweep
@@ -384,7 +379,7 @@ void launch_qp(const CfProblem &p, JacobiBufs jb, const double *sigma, int max_i
                double *e_qp, double *z_qp, unsigned *status, cudaStream_t st);
 
 void launch_tda_view(const double *Delta, int n_vc, int N, double c, double *ones, double *cd,
-                     float *onesf, float *d2f, float *d2lo, float *cdf, cudaStream_t st);
+                     float *onesf, float *d2f, float *cdf, cudaStream_t st);
 void launch_pol_rows(const double *src, int n_m, int len, const int *pairs, int n_pairs,
                      double *dst, cudaStream_t st);
 void launch_pol_combine(const double *sig2, int n_pairs, int n_freq, double *out,
