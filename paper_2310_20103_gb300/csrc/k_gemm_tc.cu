@@ -225,20 +225,15 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// 16 E4M3 values (one 16-byte piece of a K row) into 16 FP16 values, two 16-byte
-// pieces.  E4M3 -> FP16 is exact for every E4M3 value, subnormals included.
-__device__ __forceinline__ void widen_e4m3x16(uint4 in, uint4 &lo, uint4 &hi) {
-  const uint32_t w[4] = {in.x, in.y, in.z, in.w};
-  uint32_t o[8];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const __half2_raw a = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] & 0xFFFFu), __NV_E4M3);
-    const __half2_raw b = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
-    o[2 * i] = (uint32_t)a.x | ((uint32_t)a.y << 16);
-    o[2 * i + 1] = (uint32_t)b.x | ((uint32_t)b.y << 16);
-  }
-  lo = make_uint4(o[0], o[1], o[2], o[3]);
-  hi = make_uint4(o[4], o[5], o[6], o[7]);
+// E4M3 -> FP16 is exact for every E4M3 value, subnormals included.
+// One instruction per pair: the lower byte of each 16-bit half is the first
+// element and lands in the lower FP16 half.
+__device__ __forceinline__ uint32_t cvt_e4m3x2_f16x2(uint32_t pair16) {
+  uint32_t d;
+  asm("{\n\t.reg .b16 a;\n\tcvt.u16.u32 a, %1;\n\tcvt.rn.f16x2.e4m3x2 %0, a;\n\t}"
+      : "=r"(d)
+      : "r"(pair16));
+  return d;
 }
 
 struct EpiArgs {
@@ -391,11 +386,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else {
     if (DEQ) {
       // ------------------------- widen A to FP16 ---------------------------
-      // 128 threads, four passes over the 8 KB E4M3 tile: thread t reads the
-      // 16-byte piece i = 128 p + t (row i / 4, K elements 16 (i % 4) ..),
-      // contiguous across the warp, and writes its two FP16 pieces into the
-      // 128-byte-swizzled row (16-byte chunk c at c ^ (row % 8)); the eight
-      // pieces of a quarter warp land in eight different chunks.
+      // 128 threads, eight passes over the 8 KB E4M3 tile: thread t reads the
+      // 8-byte piece i = 128 p + t (row i / 8, K elements 8 (i % 8) ..),
+      // contiguous across the warp, and writes one whole 16-byte FP16 chunk
+      // of the 128-byte-swizzled row (chunk c at c ^ (row % 8)); the eight
+      // threads of a quarter warp fill the eight chunks of one row.
       const int ct = threadIdx.x - 64;
       for (int it = 0; it < nk; ++it) {
         const int s = it % C::STAGES;
@@ -406,13 +401,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint8_t *sa = aring + (it & 1) * C::A_BYTES;
         const uint8_t *raw = stages + s * C::STAGE + C::RAW_OFF;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < 8; ++p) {
           const int i = 128 * p + ct;
-          const int r = i >> 2, c2 = 2 * (i & 3);
-          uint4 lo, hi;
-          widen_e4m3x16(*reinterpret_cast<const uint4 *>(raw + 16 * i), lo, hi);
-          *reinterpret_cast<uint4 *>(sa + r * 128 + ((c2 ^ (r & 7)) << 4)) = lo;
-          *reinterpret_cast<uint4 *>(sa + r * 128 + (((c2 + 1) ^ (r & 7)) << 4)) = hi;
+          const int r = i >> 3, c = i & 7;
+          const uint2 in = *reinterpret_cast<const uint2 *>(raw + 8 * i);
+          const uint4 out = make_uint4(cvt_e4m3x2_f16x2(in.x & 0xFFFFu), cvt_e4m3x2_f16x2(in.x >> 16),
+                                       cvt_e4m3x2_f16x2(in.y & 0xFFFFu), cvt_e4m3x2_f16x2(in.y >> 16));
+          *reinterpret_cast<uint4 *>(sa + r * 128 + ((c ^ (r & 7)) << 4)) = out;
         }
         fence_proxy_async_smem();
         __syncwarp();

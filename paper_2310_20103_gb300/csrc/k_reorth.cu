@@ -521,6 +521,13 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
                "l"(gmem)
                : "memory");
 }
+// the same with immediate byte offsets on both addresses
+template <int SOFF, int GOFF>
+__device__ __forceinline__ void cp_async16_at(uint32_t saddr, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0+%2], [%1+%3], 16;\n" ::"r"(saddr), "l"(gmem),
+               "n"(SOFF), "n"(GOFF)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -550,16 +557,25 @@ __device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) {
   return d;
 }
 
+// Double-float sums of two rows at once (the hi and lo parts packed as pairs).
+__device__ __forceinline__ void df_add2(float2 &ah, float2 &al, float2 bh, float2 bl) {
+  const float2 s = __fadd2_rn(ah, bh);
+  const float2 bb = sub2_rn(s, ah);
+  const float2 err = __fadd2_rn(sub2_rn(ah, sub2_rn(s, bb)), sub2_rn(bh, bb));
+  ah = s;
+  al = __fadd2_rn(__fadd2_rn(al, bl), err);
+}
+
 // Products of one staged row with v, two adjacent elements per instruction:
 // the double-float partial of q_i . v (TwoProd by FMA with the cross terms
-// q_hi v_lo and q_lo v_hi, TwoSum into a running pair per lane; the two lanes
-// are joined at the end) and, with CORR, the delayed corrections
+// q_hi v_lo and q_lo v_hi, TwoSum into a running pair per lane; the even and
+// odd lanes are returned unjoined) and, with CORR, the delayed corrections
 // corr += c_i q_i and cv += g_i q_i.  vn = -vh, so -q v_hi needs no negation.
 template <bool LO, bool CORR>
 __device__ __forceinline__ void row_products(const float4 *slot, float2 cg,
                                              const float2 (&vh)[4], const float2 (&vn)[4],
                                              const float2 (&vl)[4], float2 (&corr)[4],
-                                             float2 (&cv)[4], float &sh_out, float &sl_out) {
+                                             float2 (&cv)[4], float2 &sh_out, float2 &sl_out) {
   float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
   const float2 cf = make_float2(cg.x, cg.x), gf = make_float2(cg.y, cg.y);
 #pragma unroll
@@ -587,15 +603,15 @@ __device__ __forceinline__ void row_products(const float4 *slot, float2 cg,
       sl = __fadd2_rn(__fadd2_rn(sl, e), err);
     }
   }
-  sh_out = sh.x;
-  sl_out = sl.x;
-  df_add(sh_out, sl_out, sh.y, sl.y);
+  sh_out = sh;   // even and odd elements: joined by the caller, two rows at a time
+  sl_out = sl;
 }
 
 // All rows i = nrows - 1 down to 0 (the newest row first), two per trip.
 // Row partials of the block go to dp[i] (one double per row), through a
-// transposed butterfly over the warp (10 shuffles for the two rows) and a
-// fixed-order sum over the eight warps in shared memory, 32 rows at a time.
+// transposed butterfly over the warp every two trips (12 shuffles for four
+// rows) and a fixed-order sum over the eight warps in shared memory, 32 rows
+// at a time.
 // cg[i] = (c_i, g_i), read only with CORR.
 template <bool LO, bool CORR>
 __device__ __forceinline__ void sweep_all_rows(const VecCtx &c, int b, int nrows, int ebase,
@@ -629,17 +645,23 @@ __device__ __forceinline__ void sweep_all_rows(const VecCtx &c, int b, int nrows
   const float *lb = LO ? c.blo + (size_t)b * c.N + ebase : nullptr;
   // sequence index r (row nrows - 1 - r) into slot s; one commit group per
   // index, empty past the last row
+  // shared addresses as 32-bit offsets and the four pieces of a row at
+  // immediate offsets from one global and one shared address
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(mine);
+  // the lo row sits at a fixed distance from the hi row (flat addresses)
+  const uintptr_t dlo = LO ? (uintptr_t)lb - (uintptr_t)hb : 0;
+  constexpr int PB = VEC_THREADS * 16;   // bytes between a thread's pieces
   auto stage = [&](int r, int s) {
     if (r < nrows) {
-      const size_t off = (size_t)(nrows - 1 - r) * rstride;
-      float4 *slot = mine + s * NV * VEC_THREADS;
+      const float *g = hb + (size_t)(nrows - 1 - r) * rstride;
+      const uint32_t sa = sbase + (uint32_t)(s * NV * PB);
       if (ok0) {
-        cp_async16(slot, hb + off);
-        if (LO) cp_async16(slot + 2 * VEC_THREADS, lb + off);
+        cp_async16_at<0, 0>(sa, g);
+        if (LO) cp_async16_at<2 * PB, 0>(sa, reinterpret_cast<const void *>((uintptr_t)g + dlo));
       }
       if (ok1) {
-        cp_async16(slot + VEC_THREADS, hb + off + 128);
-        if (LO) cp_async16(slot + 3 * VEC_THREADS, lb + off + 128);
+        cp_async16_at<PB, 512>(sa, g);
+        if (LO) cp_async16_at<3 * PB, 512>(sa, reinterpret_cast<const void *>((uintptr_t)g + dlo));
       }
     }
     cp_async_commit();
@@ -649,41 +671,69 @@ __device__ __forceinline__ void sweep_all_rows(const VecCtx &c, int b, int nrows
   for (int t0 = 0; t0 < nrows; t0 += 32) {
     const int nt = min(32, nrows - t0);
     float2 (*pp)[VEC_THREADS / 32] = part[(t0 >> 5) & 1];
-    for (int r = 0; r < nt; r += 2) {
-      const int rs = t0 + r;   // sequence indices rs, rs + 1 (rs + 1 may be past the end)
-      cp_async_wait<SW_SLOTS - 2>();
-      float sh[2], sl[2];
+    for (int r = 0; r < nt; r += 4) {
+      // two trips of two rows each, then one butterfly for the four
+      float sh[4], sl[4];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int rq = rs + q;
-        if (rq < nrows) {
-          const float2 g = CORR ? cg[nrows - 1 - rq] : make_float2(0.f, 0.f);
-          row_products<LO, CORR>(mine + (sc + q) * NV * VEC_THREADS, g, vh, vn, vl, corr, cv,
-                                 sh[q], sl[q]);
-        } else {
-          sh[q] = 0.f;
-          sl[q] = 0.f;
+      for (int hf = 0; hf < 2; ++hf) {
+        const int rs = t0 + r + 2 * hf;   // sequence indices rs, rs + 1
+        if (r + 2 * hf >= nt) {         // past the last row (uniform)
+          sh[2 * hf] = sl[2 * hf] = sh[2 * hf + 1] = sl[2 * hf + 1] = 0.f;
+          continue;
         }
+        cp_async_wait<SW_SLOTS - 2>();
+        float2 ph[2], pl[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int rq = rs + q;
+          if (rq < nrows) {
+            const float2 g = CORR ? cg[nrows - 1 - rq] : make_float2(0.f, 0.f);
+            row_products<LO, CORR>(mine + (sc + q) * NV * VEC_THREADS, g, vh, vn, vl, corr, cv,
+                                   ph[q], pl[q]);
+          } else {
+            ph[q] = pl[q] = make_float2(0.f, 0.f);
+          }
+        }
+        {
+          // join even and odd elements of both rows in one packed sum
+          float2 jh = make_float2(ph[0].x, ph[1].x), jl = make_float2(pl[0].x, pl[1].x);
+          df_add2(jh, jl, make_float2(ph[0].y, ph[1].y), make_float2(pl[0].y, pl[1].y));
+          sh[2 * hf] = jh.x;
+          sh[2 * hf + 1] = jh.y;
+          sl[2 * hf] = jl.x;
+          sl[2 * hf + 1] = jl.y;
+        }
+        stage(rs + SW_SLOTS, sc);
+        stage(rs + SW_SLOTS + 1, sc + 1);
+        sc = sc == SW_SLOTS - 2 ? 0 : sc + 2;
       }
-      stage(rs + SW_SLOTS, sc);
-      stage(rs + SW_SLOTS + 1, sc + 1);
-      sc = sc == SW_SLOTS - 2 ? 0 : sc + 2;
-      // lanes 16..31 keep row rs + 1, lanes 0..15 row rs; then a plain
-      // butterfly over the 16 lanes of each half.  Row rs + q ends in lane 16q.
-      const bool up16 = (lane & 16) != 0;
-      float th = up16 ? sh[1] : sh[0], tl = up16 ? sl[1] : sl[0];
+      // transposed butterfly over the four rows: across 16 lanes each half
+      // keeps two rows (packed), across 8 lanes one; row q ends in lane 8q
+      const bool b16 = (lane & 16) != 0, b8 = (lane & 8) != 0;
+      float2 kh = b16 ? make_float2(sh[2], sh[3]) : make_float2(sh[0], sh[1]);
+      float2 kl = b16 ? make_float2(sl[2], sl[3]) : make_float2(sl[0], sl[1]);
       {
-        const float rh = __shfl_xor_sync(0xffffffffu, up16 ? sh[0] : sh[1], 16);
-        const float rl = __shfl_xor_sync(0xffffffffu, up16 ? sl[0] : sl[1], 16);
+        const float2 oh = b16 ? make_float2(sh[0], sh[1]) : make_float2(sh[2], sh[3]);
+        const float2 ol = b16 ? make_float2(sl[0], sl[1]) : make_float2(sl[2], sl[3]);
+        const float2 rh = make_float2(__shfl_xor_sync(0xffffffffu, oh.x, 16),
+                                      __shfl_xor_sync(0xffffffffu, oh.y, 16));
+        const float2 rl = make_float2(__shfl_xor_sync(0xffffffffu, ol.x, 16),
+                                      __shfl_xor_sync(0xffffffffu, ol.y, 16));
+        df_add2(kh, kl, rh, rl);
+      }
+      float th = b8 ? kh.y : kh.x, tl = b8 ? kl.y : kl.x;
+      {
+        const float rh = __shfl_xor_sync(0xffffffffu, b8 ? kh.x : kh.y, 8);
+        const float rl = __shfl_xor_sync(0xffffffffu, b8 ? kl.x : kl.y, 8);
         df_add(th, tl, rh, rl);
       }
 #pragma unroll
-      for (int o = 8; o >= 1; o >>= 1) {
+      for (int o = 4; o >= 1; o >>= 1) {
         const float rh = __shfl_xor_sync(0xffffffffu, th, o);
         const float rl = __shfl_xor_sync(0xffffffffu, tl, o);
         df_add(th, tl, rh, rl);
       }
-      if ((lane & 15) == 0 && r + (lane >> 4) < nt) pp[r + (lane >> 4)][wid] = make_float2(th, tl);
+      if ((lane & 7) == 0 && r + (lane >> 3) < nt) pp[r + (lane >> 3)][wid] = make_float2(th, tl);
     }
     // the two tile buffers alternate, so one barrier per tile suffices: tile
     // t + 2 reuses this buffer only after warp 0 passed tile t + 1's barrier
