@@ -932,7 +932,7 @@ def main():
                          "vectors, k 48, CGS1K; about 3 GB on the device) and its report")
     ap.add_argument("--profile-precision", default="bf16",
                     choices=["bf16", "fp8", "fp8_deq", "fp64"])
-    ap.add_argument("--profile-reorth", default="dcgs", choices=["dcgs", "cgs1k", "cgs2"])
+    ap.add_argument("--profile-reorth", default="dcgs", choices=["dcgs", "cgs1k", "cgs2", "none"])
     ap.add_argument("--profile-vectors", type=int, default=64)
     ap.add_argument("--profile-k", type=int, default=48)
     args = ap.parse_args()

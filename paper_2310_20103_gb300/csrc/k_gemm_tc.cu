@@ -386,11 +386,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else {
     if (DEQ) {
       // ------------------------- widen A to FP16 ---------------------------
-      // 128 threads, eight passes over the 8 KB E4M3 tile: thread t reads the
-      // 8-byte piece i = 128 p + t (row i / 8, K elements 8 (i % 8) ..),
-      // contiguous across the warp, and writes one whole 16-byte FP16 chunk
-      // of the 128-byte-swizzled row (chunk c at c ^ (row % 8)); the eight
-      // threads of a quarter warp fill the eight chunks of one row.
+      // 128 threads, four passes over the 8 KB E4M3 tile: thread t reads the
+      // 16-byte piece i = 128 p + t (row i / 4, K elements 16 (i % 4) ..),
+      // contiguous across the warp, and writes its two FP16 pieces into the
+      // 128-byte-swizzled row (16-byte chunk c at c ^ (row % 8)).  (One
+      // 8-byte read and one whole chunk per thread measured 15% slower.)
       const int ct = threadIdx.x - 64;
       for (int it = 0; it < nk; ++it) {
         const int s = it % C::STAGES;
@@ -401,13 +401,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint8_t *sa = aring + (it & 1) * C::A_BYTES;
         const uint8_t *raw = stages + s * C::STAGE + C::RAW_OFF;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
+        for (int p = 0; p < 4; ++p) {
           const int i = 128 * p + ct;
-          const int r = i >> 3, c = i & 7;
-          const uint2 in = *reinterpret_cast<const uint2 *>(raw + 8 * i);
-          const uint4 out = make_uint4(cvt_e4m3x2_f16x2(in.x & 0xFFFFu), cvt_e4m3x2_f16x2(in.x >> 16),
-                                       cvt_e4m3x2_f16x2(in.y & 0xFFFFu), cvt_e4m3x2_f16x2(in.y >> 16));
-          *reinterpret_cast<uint4 *>(sa + r * 128 + ((c ^ (r & 7)) << 4)) = out;
+          const int r = i >> 2, c2 = 2 * (i & 3);
+          const uint4 in = *reinterpret_cast<const uint4 *>(raw + 16 * i);
+          const uint32_t w[4] = {in.x, in.y, in.z, in.w};
+          uint32_t o[8];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            o[2 * q] = cvt_e4m3x2_f16x2(w[q] & 0xFFFFu);
+            o[2 * q + 1] = cvt_e4m3x2_f16x2(w[q] >> 16);
+          }
+          *reinterpret_cast<uint4 *>(sa + r * 128 + ((c2 ^ (r & 7)) << 4)) =
+              make_uint4(o[0], o[1], o[2], o[3]);
+          *reinterpret_cast<uint4 *>(sa + r * 128 + (((c2 + 1) ^ (r & 7)) << 4)) =
+              make_uint4(o[4], o[5], o[6], o[7]);
         }
         fence_proxy_async_smem();
         __syncwarp();
