@@ -119,11 +119,13 @@ __global__ void k_alpha_reduce(VecCtx c, int j) {
   }
 }
 
-// w -= alpha_j q_j, ||w||^2 partials, and (with reorthogonalisation) the
-// first-pass dot products.
+// w -= alpha_j q_j, ||w||^2 partials, and (DOTS: with reorthogonalisation)
+// the first-pass dot products.  Without them the kernel needs a quarter of
+// the registers, so four times the warps stay resident on the FP64 pipe.
+template <bool DOTS>
 __global__ void __launch_bounds__(VEC_THREADS) k_alpha_axpy(VecCtx c, int j) {
   __shared__ double red[VEC_THREADS / 32];
-  __shared__ double sred[VEC_THREADS / 32][32];
+  __shared__ double sred[DOTS ? VEC_THREADS / 32 : 1][32];
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (!vec_live(c, b, j)) return;
   const double alpha = c.alpha[(size_t)(c.vec0 + b) * c.k + j];
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_alpha_axpy(VecCtx c, int j) {
   }
   nrm = block_sum(nrm, red);
   if (threadIdx.x == 0) c.norm_a[(size_t)b * c.nchunks + chunk] = nrm;
-  if (c.reorth != LGW_REORTH_NONE) dots_rows(c, j + 1, b, chunk, wr, sred);
+  if constexpr (DOTS) dots_rows(c, j + 1, b, chunk, wr, sred);
 }
 
 // Second-pass dot products of the current w with rows 0..j.
@@ -855,7 +857,10 @@ void launch_alpha_reduce(const VecCtx &c, int j, cudaStream_t st) {
   k_alpha_reduce<<<c.Bs, 32, 0, st>>>(c, j);
 }
 void launch_alpha_axpy(const VecCtx &c, int j, cudaStream_t st) {
-  k_alpha_axpy<<<vec_grid(c), VEC_THREADS, 0, st>>>(c, j);
+  if (c.reorth != LGW_REORTH_NONE)
+    k_alpha_axpy<true><<<vec_grid(c), VEC_THREADS, 0, st>>>(c, j);
+  else
+    k_alpha_axpy<false><<<vec_grid(c), VEC_THREADS, 0, st>>>(c, j);
 }
 void launch_beta_vec(const VecCtx &c, int j, cudaStream_t st) {
   k_beta_vec<<<c.Bs, 32, 0, st>>>(c, j);
