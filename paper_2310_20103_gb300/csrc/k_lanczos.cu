@@ -26,6 +26,63 @@ __device__ __forceinline__ bool vec_live(const VecCtx &c, int b, int j) {
   return b < c.nvec && c.k_eff[c.vec0 + b] > j;
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic for the float-pair vector passes (Dekker 1971,
+// Knuth's TwoSum): a value is hi + lo with |lo| <= ulp(hi) / 2, 48 bits.
+// These passes leave most issue slots idle while GB300's FP64 pipe (2 lanes
+// per SM clock) bounds them, so FP32-pipe arithmetic costs nothing there.
+// Products drop lo * lo (relative error about 2^-46).
+// ---------------------------------------------------------------------------
+struct dfl {
+  float h, l;
+};
+__device__ __forceinline__ dfl df_fast(float a, float b) {   // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return df_fast(p, e);
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {   // accurate under cancellation
+  dfl s = df_two_sum(a.h, b.h);
+  const dfl t = df_two_sum(a.l, b.l);
+  s = df_fast(s.h, __fadd_rn(s.l, t.h));
+  return df_fast(s.h, __fadd_rn(s.l, t.l));
+}
+__device__ __forceinline__ dfl df_add_f(dfl a, float b) {
+  const dfl s = df_two_sum(a.h, b);
+  return df_fast(s.h, __fadd_rn(s.l, a.l));
+}
+__device__ __forceinline__ dfl df_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+// (sh, sl) += a . b, TwoProd with the cross terms and TwoSum
+__device__ __forceinline__ void df_dot_acc(float &sh, float &sl, dfl a, dfl b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+  const dfl s = df_two_sum(sh, p);
+  sh = s.h;
+  sl = __fadd_rn(__fadd_rn(sl, s.l), e);
+}
+// hi and lo halves of a float-pair slot [Bs][N] (hi, then lo)
+__device__ __forceinline__ float *pair_hi(double *slot, const VecCtx &c) {
+  return reinterpret_cast<float *>(slot);
+}
+__device__ __forceinline__ float *pair_lo(double *slot, const VecCtx &c) {
+  return reinterpret_cast<float *>(slot) + (size_t)c.Bs * c.N;
+}
+
 // Partial dot products of the thread's eight elements of w with basis rows
 // 0..nrows-1 of vector b; one partial per (row, chunk) after a warp
 // transposed reduction and a fixed-order sum over the eight warps.
@@ -76,11 +133,49 @@ __global__ void __launch_bounds__(VEC_THREADS) k_assemble_w(VecCtx c, int j,
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (!vec_live(c, b, j)) return;
   const size_t voff = (size_t)b * c.N;
+  const double bj = c.betaj[b];
+  const int e0 = elem_base(chunk);
+  if (c.pair) {
+    // the same in double-float on float pairs (w = (Delta^2 q + ucd) - beta_j q_{j-1})
+    const float *qh = pair_hi(slot_ptr(c, j), c) + voff, *ql = pair_lo(slot_ptr(c, j), c) + voff;
+    const float *ph = j > 0 ? pair_hi(slot_ptr(c, j - 1), c) + voff : nullptr;
+    const float *pl = j > 0 ? pair_lo(slot_ptr(c, j - 1), c) + voff : nullptr;
+    float *wh = pair_hi(c.w, c) + voff, *wl = pair_lo(c.w, c) + voff;
+    const dfl nbj = df_from(-bj);
+    float sh = 0.f, sl = 0.f;
+#pragma unroll
+    for (int u4 = 0; u4 < 4; ++u4) {
+      const int e = e0 + u4 * 64;
+      if (e >= c.N) continue;
+      const float2 a2 = *reinterpret_cast<const float2 *>(qh + e);
+      const float2 b2 = *reinterpret_cast<const float2 *>(ql + e);
+      const float2 v2 = *reinterpret_cast<const float2 *>(ucd + kblk_f32(b, e, c.Bs));
+      const float2 dh = *reinterpret_cast<const float2 *>(c.d2f + e);
+      const float2 dl = *reinterpret_cast<const float2 *>(c.d2lo + e);
+      float2 p2 = make_float2(0.f, 0.f), r2 = p2;
+      if (ph != nullptr) {
+        p2 = *reinterpret_cast<const float2 *>(ph + e);
+        r2 = *reinterpret_cast<const float2 *>(pl + e);
+      }
+      const dfl q0{a2.x, b2.x}, q1{a2.y, b2.y};
+      dfl w0 = df_add_f(df_mul({dh.x, dl.x}, q0), v2.x);
+      dfl w1 = df_add_f(df_mul({dh.y, dl.y}, q1), v2.y);
+      if (ph != nullptr) {
+        w0 = df_add(w0, df_mul(nbj, {p2.x, r2.x}));
+        w1 = df_add(w1, df_mul(nbj, {p2.y, r2.y}));
+      }
+      *reinterpret_cast<float2 *>(wh + e) = make_float2(w0.h, w1.h);
+      *reinterpret_cast<float2 *>(wl + e) = make_float2(w0.l, w1.l);
+      df_dot_acc(sh, sl, q0, w0);
+      df_dot_acc(sh, sl, q1, w1);
+    }
+    const double ap = block_sum((double)sh + (double)sl, red);
+    if (threadIdx.x == 0) c.alpha_part[(size_t)chunk * c.Bs + b] = ap;
+    return;
+  }
   const double *q = slot_ptr(c, j) + voff;
   const double *qp = j > 0 ? slot_ptr(c, j - 1) + voff : nullptr;
   double *w = c.w + voff;
-  const double bj = c.betaj[b];
-  const int e0 = elem_base(chunk);
   double ap = 0.0;
 #pragma unroll
   for (int u4 = 0; u4 < 4; ++u4) {
@@ -130,9 +225,36 @@ __global__ void __launch_bounds__(VEC_THREADS) k_alpha_axpy(VecCtx c, int j) {
   if (!vec_live(c, b, j)) return;
   const double alpha = c.alpha[(size_t)(c.vec0 + b) * c.k + j];
   const size_t voff = (size_t)b * c.N;
+  const int e0 = elem_base(chunk);
+  if constexpr (!DOTS) {
+    if (c.pair) {
+      const float *qh = pair_hi(slot_ptr(c, j), c) + voff;
+      const float *ql = pair_lo(slot_ptr(c, j), c) + voff;
+      float *wh = pair_hi(c.w, c) + voff, *wl = pair_lo(c.w, c) + voff;
+      const dfl nal = df_from(-alpha);
+      float sh = 0.f, sl = 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * 64;
+        if (e >= c.N) continue;
+        const float2 a2 = *reinterpret_cast<const float2 *>(qh + e);
+        const float2 b2 = *reinterpret_cast<const float2 *>(ql + e);
+        const float2 x2 = *reinterpret_cast<const float2 *>(wh + e);
+        const float2 y2 = *reinterpret_cast<const float2 *>(wl + e);
+        const dfl w0 = df_add({x2.x, y2.x}, df_mul(nal, {a2.x, b2.x}));
+        const dfl w1 = df_add({x2.y, y2.y}, df_mul(nal, {a2.y, b2.y}));
+        *reinterpret_cast<float2 *>(wh + e) = make_float2(w0.h, w1.h);
+        *reinterpret_cast<float2 *>(wl + e) = make_float2(w0.l, w1.l);
+        df_dot_acc(sh, sl, w0, w0);
+        df_dot_acc(sh, sl, w1, w1);
+      }
+      const double nrm = block_sum((double)sh + (double)sl, red);
+      if (threadIdx.x == 0) c.norm_a[(size_t)b * c.nchunks + chunk] = nrm;
+      return;
+    }
+  }
   const double *q = slot_ptr(c, j) + voff;
   double *w = c.w + voff;
-  const int e0 = elem_base(chunk);
   double wr[8];
   double nrm = 0.0;
 #pragma unroll
@@ -318,9 +440,41 @@ __global__ void __launch_bounds__(VEC_THREADS) k_normalize(VecCtx c, int j, int 
   const int next = is_start ? 0 : j + 1;
   if (next >= c.nslots && c.reorth != LGW_REORTH_NONE) return;
   const size_t voff = (size_t)b * c.N;
+  const int e0 = elem_base(chunk);
+  if (c.pair) {
+    // float-pair slots: the start reads the FP64 b of the start kernels,
+    // a step the float-pair w of the axpy pass
+    float *qh = pair_hi(slot_ptr(c, next), c) + voff, *ql = pair_lo(slot_ptr(c, next), c) + voff;
+    const float *wh = pair_hi(c.w, c) + voff, *wl = pair_lo(c.w, c) + voff;
+    const dfl si = df_from(inv);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * 64;
+      if (e >= c.N) continue;
+      dfl q0{0.f, 0.f}, q1{0.f, 0.f};
+      if (live && is_start) {
+        const double2 w2 = *reinterpret_cast<const double2 *>(c.w + voff + e);
+        q0 = df_from(w2.x * inv);
+        q1 = df_from(w2.y * inv);
+      } else if (live) {
+        const float2 x2 = *reinterpret_cast<const float2 *>(wh + e);
+        const float2 y2 = *reinterpret_cast<const float2 *>(wl + e);
+        q0 = df_mul({x2.x, y2.x}, si);
+        q1 = df_mul({x2.y, y2.y}, si);
+      }
+      *reinterpret_cast<float2 *>(qh + e) = make_float2(q0.h, q1.h);
+      *reinterpret_cast<float2 *>(ql + e) = make_float2(q0.l, q1.l);
+      if (c.xh != nullptr) {
+        __nv_bfloat162 x2;
+        x2.x = __float2bfloat16_rn(c.dsqf[e] * q0.h);
+        x2.y = __float2bfloat16_rn(c.dsqf[e + 1] * q1.h);
+        *reinterpret_cast<__nv_bfloat162 *>(c.xh + kblk_bf16(b, e, c.Bs)) = x2;
+      }
+    }
+    return;
+  }
   double *qn = slot_ptr(c, next) + voff;
   const double *w = c.w + voff;
-  const int e0 = elem_base(chunk);
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int e = e0 + u * 64;

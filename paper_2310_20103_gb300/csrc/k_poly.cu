@@ -150,7 +150,8 @@ void launch_poly_prep(const double *alpha, const double *beta, const double *bet
 // take the places of those of C (Delta^1/2 -> 1, Delta^2 -> Delta,
 // c_K Delta^1/2 -> c), zero in the padding.
 __global__ void k_tda_view(const double *__restrict__ Delta, int n_vc, int N, double c,
-                           double *ones, double *cd, float *onesf, float *d2f, float *cdf) {
+                           double *ones, double *cd, float *onesf, float *d2f, float *d2lo,
+                           float *cdf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const bool real = i < n_vc;
@@ -158,6 +159,7 @@ __global__ void k_tda_view(const double *__restrict__ Delta, int n_vc, int N, do
   cd[i] = real ? c : 0.0;
   onesf[i] = real ? 1.0f : 0.0f;
   d2f[i] = (float)Delta[i];
+  d2lo[i] = (float)(Delta[i] - (double)d2f[i]);
   cdf[i] = real ? (float)c : 0.0f;
 }
 
@@ -187,8 +189,9 @@ __global__ void k_pol_combine(const double *__restrict__ sig2, int n_pairs, int 
 }
 
 void launch_tda_view(const double *Delta, int n_vc, int N, double c, double *ones, double *cd,
-                     float *onesf, float *d2f, float *cdf, cudaStream_t st) {
-  k_tda_view<<<(N + 255) / 256, 256, 0, st>>>(Delta, n_vc, N, c, ones, cd, onesf, d2f, cdf);
+                     float *onesf, float *d2f, float *d2lo, float *cdf, cudaStream_t st) {
+  k_tda_view<<<(N + 255) / 256, 256, 0, st>>>(Delta, n_vc, N, c, ones, cd, onesf, d2f, d2lo,
+                                               cdf);
 }
 void launch_pol_rows(const double *src, int n_m, int len, const int *pairs, int n_pairs,
                      double *dst, cudaStream_t st) {

@@ -8,7 +8,7 @@ namespace lgw {
 // The padding tail [n_vc, N) is zero so padded vectors stay zero.
 __global__ void k_pair_energies(const double *__restrict__ eps, int n_v, int n_c, int n_vc, int N,
                                 double kf, double *Delta, double *dsq, double *Delta2,
-                                double *cd, float *dsqf, float *d2f, float *cdf) {
+                                double *cd, float *dsqf, float *d2f, float *d2lo, float *cdf) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double D = 0.0;
@@ -23,6 +23,7 @@ __global__ void k_pair_energies(const double *__restrict__ eps, int n_v, int n_c
   cd[i] = kf * s;
   dsqf[i] = (float)s;
   d2f[i] = (float)(D * D);
+  d2lo[i] = (float)(D * D - (double)d2f[i]);
   cdf[i] = (float)(kf * s);
 }
 
@@ -72,7 +73,7 @@ __global__ void k_quantize_L(const double *__restrict__ src, int ld, int nr, int
 void launch_pair_energies(const SysDev &s, cudaStream_t st) {
   int th = 256, bl = (s.N + th - 1) / th;
   k_pair_energies<<<bl, th, 0, st>>>(s.eps, s.n_v, s.n_c, s.n_vc, s.N, s.kf, s.Delta, s.dsq,
-                                     s.Delta2, s.cd, s.dsqf, s.d2f, s.cdf);
+                                     s.Delta2, s.cd, s.dsqf, s.d2f, s.d2lo, s.cdf);
 }
 
 void launch_check_delta(const SysDev &s, unsigned *status, cudaStream_t st) {

@@ -564,6 +564,10 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
     c.blo = o.split32 ? nullptr : wsT<float>(h, "basis_lo", (size_t)(k + 1) * Bs * N);
   }
   c.dsqf = s.dsqf;
+  c.d2lo = s.d2lo;
+  // tensor cores without reorthogonalisation (the three-vector ring): the
+  // slots and w as float pairs, the vector passes in double-float arithmetic
+  c.pair = (tc && !reorth && !full_basis && poly == nullptr && s.d2lo != nullptr) ? 1 : 0;
   // float [Bs][N]: the split-basis epilogue output (c_K Delta^1/2 U) and, at
   // the start of each sub-batch, the tensor-core coupling vectors V = L M
   float *ucd_buf = tc ? wsT<float>(h, "ucd", (size_t)Bs * N) : nullptr;
@@ -1308,11 +1312,12 @@ const SysDev &tda_view(lgw_handle *h, const lgw_system *csys) {
   if (!sys->tda_buf) {
     const size_t N = (size_t)s.N;
     void *buf = nullptr;
-    LGW_TRY_CUDA(h, cudaMalloc(&buf, N * (2 * sizeof(double) + 3 * sizeof(float))));
+    LGW_TRY_CUDA(h, cudaMalloc(&buf, N * (2 * sizeof(double) + 4 * sizeof(float))));
     sys->tda_buf = buf;
     double *ones = static_cast<double *>(buf), *cd = ones + N;
     float *onesf = reinterpret_cast<float *>(cd + N), *d2f = onesf + N, *cdf = d2f + N;
-    launch_tda_view(s.Delta, s.n_vc, s.N, 0.5 * s.kf, ones, cd, onesf, d2f, cdf, h->stream);
+    launch_tda_view(s.Delta, s.n_vc, s.N, 0.5 * s.kf, ones, cd, onesf, d2f, cdf + N, cdf,
+                    h->stream);
     check_launch(h, "tda_view");
   }
   const size_t N = (size_t)s.N;
@@ -1326,6 +1331,7 @@ const SysDev &tda_view(lgw_handle *h, const lgw_system *csys) {
   t.cd = cd;
   t.dsqf = onesf;
   t.d2f = d2f;
+  t.d2lo = cdf + N;
   t.cdf = cdf;
   return t;
 }
@@ -1560,7 +1566,8 @@ lgw_status lgw_prepare_system(lgw_handle *h, const lgw_system_desc *d, lgw_syste
   s.Delta2 = (double *)alloc(sizeof(double) * s.N);
   s.cd = (double *)alloc(sizeof(double) * s.N);
   s.dsqf = (float *)alloc(sizeof(float) * s.N);
-  s.d2f = (float *)alloc(sizeof(float) * s.N);
+  s.d2f = (float *)alloc(2 * sizeof(float) * s.N);   // d2f, then d2lo
+  s.d2lo = s.d2f ? s.d2f + s.N : nullptr;
   s.cdf = (float *)alloc(sizeof(float) * s.N);
   bool ok = s.eps && s.Delta && s.dsq && s.Delta2 && s.cd && s.dsqf && s.d2f && s.cdf;
   if (ok && keep64) ok = (s.L64 = (double *)alloc(sizeof(double) * (size_t)s.N * s.A)) != nullptr;

@@ -47,6 +47,8 @@ struct SysDev {
   double *cd;       // [N]  c_K Delta^1/2
   float *dsqf;      // [N]  Delta^1/2 rounded to float (bf16 operand scaling)
   float *d2f;       // [N]  Delta^2 rounded to float   (alpha estimate)
+  float *d2lo;      // [N]  Delta^2 - d2f rounded to float: (d2f, d2lo) is Delta^2 as a
+                    //      double-float (the float-pair vector passes)
   float *cdf;       // [N]  c_K Delta^1/2 rounded to float (FP32 epilogue)
   double *L64;      // [N][A] row-major, zero padded
   __nv_bfloat16 *Lb;    // [N][A]   K-major operand of the L Y contraction
@@ -77,6 +79,12 @@ struct VecCtx {
                           // null (float-only basis)
   const float *dsqf;      // [N]
   const float *d2f;       // [N] Delta^2 (float)
+  const float *d2lo;      // [N] second float of Delta^2
+  // pair: the ring slots and w hold float pairs (hi = the first Bs*N floats
+  // of the slot, lo = the next Bs*N) and the vector passes run in double-
+  // float arithmetic on the FP32 pipe (tensor-core path without
+  // reorthogonalisation, ring mode)
+  int pair;
   const float *ucd;       // [Bs][N] c_K Delta^1/2 (L y) from the FP32 epilogue (kblk_f32), or null
                           // (then w holds the full FP64 epilogue result)
   float *dq2_part;        // [Bs][nchunks] partials of sum Delta^2 q_j^2 (FP32); with
@@ -379,7 +387,7 @@ void launch_qp(const CfProblem &p, JacobiBufs jb, const double *sigma, int max_i
                double *e_qp, double *z_qp, unsigned *status, cudaStream_t st);
 
 void launch_tda_view(const double *Delta, int n_vc, int N, double c, double *ones, double *cd,
-                     float *onesf, float *d2f, float *cdf, cudaStream_t st);
+                     float *onesf, float *d2f, float *d2lo, float *cdf, cudaStream_t st);
 void launch_pol_rows(const double *src, int n_m, int len, const int *pairs, int n_pairs,
                      double *dst, cudaStream_t st);
 void launch_pol_combine(const double *sig2, int n_pairs, int n_freq, double *out,
