@@ -165,10 +165,20 @@ __global__ void __launch_bounds__(COEF_THREADS) k_adj_coeffs(AdjCtx a) {
   double *Om = sm, *u1 = sm + k, *fu = sm + 2 * k;
   double dzp = 0.0;
   for (int s = tid; s < n; s += COEF_THREADS) {
-    const double om = sqrt(fmax(th[s], 0.0));
     const double u = V[(size_t)s * k];
-    Om[s] = om;
     u1[s] = u;
+    if (a.tda) {
+      // f = 1/(z + eta theta):  a = z + eta theta;  Re f = Re 1/a;  dF/dz term -u^2 / a^2
+      const double t = th[s];
+      Om[s] = t;
+      const double ar = zr + eta * t;
+      fu[s] = ar / (ar * ar + zi * zi) * u;
+      const double sr = ar * ar - zi * zi, si = 2.0 * ar * zi;
+      dzp += -(u * u) * (sr / (sr * sr + si * si));
+      continue;
+    }
+    const double om = sqrt(fmax(th[s], 0.0));
+    Om[s] = om;
     // a = z + eta Om;  Re f = Re 1/(Om a);  dF/dz term -u^2 / (Om a^2)
     const double ar = zr + eta * om;
     fu[s] = ar / (om * (ar * ar + zi * zi)) * u;
@@ -191,10 +201,16 @@ __global__ void __launch_bounds__(COEF_THREADS) k_adj_coeffs(AdjCtx a) {
   for (int idx = tid; idx < n * n; idx += COEF_THREADS) {
     const int s = idx / n, t = idx % n;
     const double as_r = zr + eta * Om[s], at_r = zr + eta * Om[t];
-    const double nr = -(zr + eta * (Om[s] + Om[t])), ni = -zi;
     const double pr = as_r * at_r - zi * zi, pi = zi * (as_r + at_r);   // a_s a_t
-    const double scale = Om[s] * Om[t] * (Om[s] + Om[t]);
-    const double Fr = (nr * pr + ni * pi) / ((pr * pr + pi * pi) * scale);
+    double Fr;
+    if (a.tda) {
+      // f[theta_s, theta_t] = -eta / (a_s a_t)
+      Fr = -eta * pr / (pr * pr + pi * pi);
+    } else {
+      const double nr = -(zr + eta * (Om[s] + Om[t])), ni = -zi;
+      const double scale = Om[s] * Om[t] * (Om[s] + Om[t]);
+      Fr = (nr * pr + ni * pi) / ((pr * pr + pi * pi) * scale);
+    }
     Phi[(size_t)s * k + t] = Fr * u1[s] * u1[t];
   }
   __syncthreads();
@@ -399,6 +415,10 @@ __global__ void k_adj_accumulate(AdjCtx a, const double *Delta, BasisRef basis,
   if (i < a.N && Delta[i] > 0.0) {
     double s = 0.0;
     for (int b = 0; b < a.nvec; ++b) {
+      if (a.tda) {   // dA/dDelta_i = e_i e_i^T; b = L M
+        s += Gd[(size_t)b * a.N + i];
+        continue;
+      }
       const double q0 = basis.at((size_t)b * a.N + i);
       s += 2.0 * Delta[i] * Gd[(size_t)b * a.N + i] +
            Y[(size_t)b * a.N + i] * a.beta0[a.vec0 + b] * q0 / (2.0 * Delta[i]);
@@ -417,9 +437,10 @@ __global__ void k_adj_accumulate(AdjCtx a, const double *Delta, BasisRef basis,
 
 // dL = D (2 c_K SC + SB) (unpadded output), dDelta += c_K (L o SC) 1 / d.
 // SC [N][A], SB [N][n_aux] or NULL (coupling vectors given directly).
+// tda: D = 1, so no dDelta term from the coupling.
 __global__ void k_adj_dL(const double *L64, const double *dsq, const double *SC,
                          const double *SB, int A, int n_vc, int n_aux, double kf, double *dL,
-                         double *dDelta) {
+                         double *dDelta, int tda) {
   const int i = blockIdx.x;
   if (i >= n_vc) return;
   __shared__ double red[8];
@@ -433,7 +454,7 @@ __global__ void k_adj_dL(const double *L64, const double *dsq, const double *SC,
     }
   }
   s = block_sum(s, red);
-  if (threadIdx.x == 0 && dsq[i] > 0.0) dDelta[i] += kf * s / dsq[i];
+  if (threadIdx.x == 0 && dsq[i] > 0.0 && !tda) dDelta[i] += kf * s / dsq[i];
 }
 
 // deps from dDelta (Delta_vc = eps_c - eps_v) plus the direct dE_t Z_t term.
@@ -520,9 +541,9 @@ void launch_adj_accumulate(const AdjCtx &a, const double *Delta, BasisRef basis,
   k_adj_accumulate<<<(a.N + 255) / 256, 256, 0, st>>>(a, Delta, basis, Y, Gd, dDelta, deps);
 }
 void launch_adj_dL(const double *L64, const double *dsq, const double *SC, const double *SB,
-                   int A, int n_vc, int n_aux, double kf, double *dL, double *dDelta,
+                   int A, int n_vc, int n_aux, double kf, double *dL, double *dDelta, int tda,
                    cudaStream_t st) {
-  k_adj_dL<<<n_vc, 256, 0, st>>>(L64, dsq, SC, SB, A, n_vc, n_aux, kf, dL, dDelta);
+  k_adj_dL<<<n_vc, 256, 0, st>>>(L64, dsq, SC, SB, A, n_vc, n_aux, kf, dL, dDelta, tda);
 }
 void launch_adj_deps(const double *dDelta, int n_v, int n_c, const int *targets, int n_t,
                      const double *Z, const double *dE, double *deps, cudaStream_t st) {

@@ -427,6 +427,10 @@ struct AdjCtx {
   float *Gamf;     // [Bs][k][k] FP32 copy of Gam, or NULL
   double *dz;      // [Bs]
   unsigned *status;
+  // Tamm-Dancoff: F = b^T (z + eta A)^-1 b with A = Delta + c L L^T and
+  // b = L M (the nodes are theta, not Omega = sqrt(theta); A is linear in
+  // Delta and b does not depend on it)
+  int tda;
 };
 int adj_max_k();
 bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const int *a_kblk,
@@ -449,7 +453,7 @@ void launch_adj_accumulate(const AdjCtx &a, const double *Delta, BasisRef basis,
                            const double *Y, const double *Gd, double *dDelta, double *deps,
                            cudaStream_t st);
 void launch_adj_dL(const double *L64, const double *dsq, const double *SC, const double *SB,
-                   int A, int n_vc, int n_aux, double kf, double *dL, double *dDelta,
+                   int A, int n_vc, int n_aux, double kf, double *dL, double *dDelta, int tda,
                    cudaStream_t st);
 void launch_adj_deps(const double *dDelta, int n_v, int n_c, const int *targets, int n_t,
                      const double *Z, const double *dE, double *deps, cudaStream_t st);
