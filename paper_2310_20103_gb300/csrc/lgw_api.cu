@@ -2391,7 +2391,7 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
       run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, true, &adjoint);
     }
     double *dLdev = oL.dev ? oL.dev : wsT<double>(h, "adj_dL", (size_t)s.n_vc * s.n_aux);
-    launch_adj_dL(s.L64, s.dsq, SC, SB, A, s.n_vc, s.n_aux, s.kf, dLdev, dD, st);
+    launch_adj_dL(s.L64, s.dsq, SC, SB, A, s.n_vc, s.n_aux, s.kf, dLdev, dD, 0, st);
     check_launch(h, "adj_dL");
     launch_adj_deps(dD, s.n_v, s.n_c, pv.d_targets, pv.n_t, Z, d_dE, gdeps, st);
     check_launch(h, "adj_deps");
