@@ -37,7 +37,8 @@ __all__ = [
     "closed_form_poles", "lanczos", "lanczos_poles", "sigma_from_poles",
     "dsigma_from_poles", "sigma_closed_form", "sigma_lanczos", "qp_solve",
     "solve_all_qp", "qp_gradient", "qp_energies_closed_form", "qp_gradient_closed_form",
-    "qp_gradient_lanczos", "chebyshev_sqrt", "chebyshev_eval", "apply_poly",
+    "qp_gradient_lanczos", "lanczos_reverse", "qp_gradient_recurrence",
+    "qp_energies_tda_closed_form", "qp_gradient_tda_closed_form", "chebyshev_sqrt", "chebyshev_eval", "apply_poly",
     "sigma_poly_lanczos", "haydock", "sigma_x", "qp_linearised", "fit_factors",
     "tda_matrix", "sigma_tda_closed_form", "sigma_tda_lanczos", "sigma_offdiag_closed_form",
     "band_lanczos", "band_gauss_rule", "sigma_band_lanczos",
@@ -438,6 +439,222 @@ def qp_gradient_closed_form(wl, dE):
     E, Z = qp_energies_closed_form(wl)
     theta, Y = np.linalg.eigh(casida_matrix(wl.eps, wl.n_v, wl.L, wl.kernel_factor))
     return qp_gradient(wl, dE, E, Z, lambda v: (Y, theta))
+
+
+# --------------------------------------------------------------------------
+# Exact derivative of the k-step QP energies: reverse mode of the three-term
+# recurrence (Eq. 13 without reorthogonalisation), the Gauss rule of T_k
+# (Eq. 12, 14) and the QP equation.  Unlike the Krylov form above, which is
+# the derivative of the converged f(C) seen through the k-step basis, this
+# differentiates exactly what k steps compute, so it is the derivative of
+# E_k at any k.
+# --------------------------------------------------------------------------
+def lanczos_reverse(apply_op, b, k, abar, bbar, breakdown_tol=1e-13):
+    """Reverse mode of ``lanczos(apply_op, b, k, reorth=False)`` for one
+    start vector b [N] (C symmetric, given by apply_op on rows).
+
+    Forward step j (q_{-1} = 0, beta_0 = 0 as the coupling of q_{-1}):
+        u = C q_j ;  w1 = u - beta_j q_{j-1} ;  alpha_j = q_j . w1
+        w2 = w1 - alpha_j q_j ;  beta_{j+1} = ||w2|| ;  q_{j+1} = w2 / beta_{j+1}
+    T_k holds alpha_0..alpha_{ke-1} and beta_1..beta_{ke-1}; the last
+    residual beta_{ke} and q_{ke} do not enter it.  Given the adjoints
+    abar[j] = dF/dalpha_j and bbar[j] = dF/dbeta[j] (beta[j] the coupling of
+    steps j and j+1, as ``lanczos`` returns it), the steps are taken back
+    in reverse order, j = ke-1 .. 0:
+        w2bar = (qbar_{j+1} - (qbar_{j+1} . q_{j+1}) q_{j+1}) / beta_{j+1}
+                + bbar[j] q_{j+1}                       (0 for j = ke-1)
+        abar_j' = abar[j] - w2bar . q_j
+        qbar_j += -alpha_j w2bar + abar_j' w1
+        ubar_j = w1bar = w2bar + abar_j' q_j
+        bbar[j-1] -= w1bar . q_{j-1} ;  qbar_{j-1} -= beta_j w1bar
+        qbar_j += C ubar_j                              (C symmetric)
+    Returns (qbar_0 = dF/dq_0 at fixed C, ubar [ke, N], Q [ke, N], (alpha,
+    beta, beta0, ke)); the derivative with respect to C is
+    dF/dC = sum_j ubar_j q_j^T (its symmetric part for a symmetric dC)."""
+    b = np.asarray(b, dtype=np.float64)
+    alpha, beta, beta0, k_eff, Q = lanczos(apply_op, b[None, :], k, reorth=False,
+                                           breakdown_tol=breakdown_tol, return_basis=True)
+    alpha, beta, ke = alpha[0], beta[0], int(k_eff[0])
+    Q = Q[:ke, 0, :]
+    N = b.size
+    zero = np.zeros(N)
+    bb = np.array(bbar, dtype=np.float64)[: max(ke, 1)].copy()
+    qbar = np.zeros((ke + 1, N))
+    ubar = np.zeros((ke, N))
+    for j in range(ke - 1, -1, -1):
+        qj = Q[j]
+        qm = Q[j - 1] if j > 0 else zero
+        bj = beta[j - 1] if j > 0 else 0.0
+        w1 = apply_op(qj[None, :])[0] - bj * qm
+        if j < ke - 1:
+            q1 = Q[j + 1]
+            w2bar = (qbar[j + 1] - (qbar[j + 1] @ q1) * q1) / beta[j] + bb[j] * q1
+        else:
+            w2bar = zero
+        at = abar[j] - w2bar @ qj
+        qbar[j] += -alpha[j] * w2bar + at * w1
+        w1bar = w2bar + at * qj
+        if j > 0:
+            bb[j - 1] -= w1bar @ qm
+            qbar[j - 1] -= bj * w1bar
+        qbar[j] += apply_op(w1bar[None, :])[0]
+        ubar[j] = w1bar
+    return qbar[0], ubar, Q, (alpha, beta, beta0[0], ke)
+
+
+def _tridiag(alpha, beta, ke):
+    T = np.diag(alpha[:ke])
+    if ke > 1:
+        T += np.diag(beta[: ke - 1], 1) + np.diag(beta[: ke - 1], -1)
+    return T
+
+
+def _tda_f_and_divdiff(theta, z, eta):
+    """f(theta) = 1 / (z + eta theta) and f[theta_s, theta_t] = -eta / ((z +
+    eta theta_s)(z + eta theta_t)) (Tamm-Dancoff form of Eq. 7, no square
+    root)."""
+    a = z + eta * theta
+    return 1.0 / a, -eta / (a[:, None] * a[None, :])
+
+
+def qp_gradient_recurrence(wl, dE, k=None, tda=False, breakdown_tol=1e-13):
+    """Exact gradient of sum_t dE[t] E_t^(k) with respect to L and eps, E^(k)
+    the QP energies of k-step Lanczos without reorthogonalisation
+    (``sigma_lanczos(reorth=False)``, or ``sigma_tda_lanczos(reorth=False)``
+    with tda) and the QP equation.
+
+    Per start vector, F = beta0^2 Re e_1^T f(T_k) e_1 at z = E_t - eps_m -
+    i eta_m delta (the Gauss rule of Eq. 12-14), weighted by c = dE_t Z_t:
+        dF/dT_k = c beta0^2 Re U (F_div o u1 u1^T) U^T   (Daleckii-Krein on T_k)
+    gives abar_j (diagonal) and bbar_j (twice the off-diagonal); the
+    recurrence's reverse mode (``lanczos_reverse``) gives qbar_0 and the
+    pairs (ubar_j, q_j); beta0 = ||b|| enters directly with
+    dF/dbeta0 = 2 c beta0 Re e_1^T f(T_k) e_1, so
+        y = dF/db = (dF/dbeta0) q_0 + (qbar_0 - (qbar_0 . q_0) q_0) / beta0,
+        G = dF/dC = sym(sum_j ubar_j q_j^T).
+    Assembly as in ``qp_gradient`` (C = Delta^2 + c_K D L L^T D, b = D L M):
+        dL = 2 c_K D G D L + (D y) M^T,
+        dDelta = 2 Delta diag(G) + c_K diag(K D G) / d + y V / (2 d);
+    Tamm-Dancoff (A = Delta + c_K/2 L L^T, b = V = L M):
+        dL = c_K G L + y M^T,  dDelta = diag(G).
+    eps_m enters z: deps[m] -= c Re dF/dz.  Returns (dL, deps)."""
+    k = wl.k if k is None else k
+    Delta = pair_energies(wl.eps, wl.n_v)
+    d = np.sqrt(Delta)
+    V_all = coupling_vectors(wl.L, wl.M)                       # [n_t, n_m, N_vc]
+    eta_all = occupation_sign(wl.m_idx, wl.n_v)
+    if tda:
+        Amat = tda_matrix(wl.eps, wl.n_v, wl.L, wl.kernel_factor)
+
+        def apply_op(X):
+            return X @ Amat.T
+
+        b_all = V_all
+        _, poles, coeffs = sigma_tda_lanczos(wl, k=k, reorth=False)
+    else:
+        def apply_op(X):
+            return apply_casida(wl.eps, wl.n_v, wl.L, X, wl.kernel_factor)
+
+        b_all = d * V_all
+        _, poles, coeffs = sigma_lanczos(wl, k=k, reorth=False)
+    E, Z = solve_all_qp(wl, poles)
+    alpha, beta, beta0, k_eff = coeffs
+    SC = np.zeros_like(wl.L)          # G D L (G L for Tamm-Dancoff)
+    SB = np.zeros_like(wl.L)          # (D y) M^T
+    dDelta = np.zeros(wl.n_vc)
+    deps = np.zeros(wl.n_v + wl.n_c)
+    for ti, t in enumerate(wl.targets):
+        cw = dE[ti] * Z[ti]
+        deps[t] += cw
+        for mi, m in enumerate(wl.m_idx):
+            v = ti * wl.n_m + mi
+            ke = int(k_eff[v])
+            if ke == 0:
+                continue
+            eta = eta_all[mi]
+            z = E[ti] - wl.eps[m] - 1j * eta * wl.delta
+            theta, U = np.linalg.eigh(_tridiag(alpha[v], beta[v], ke))
+            u1 = U[0]
+            if tda:
+                f, Fd = _tda_f_and_divdiff(theta, z, eta)
+                dfdz = -1.0 / (z + eta * theta) ** 2
+            else:
+                Om = np.sqrt(theta)
+                f, Fd = _f_and_divdiff(Om, z, eta)
+                dfdz = -1.0 / (Om * (z + eta * Om) ** 2)
+            b0 = beta0[v]
+            Gam = cw * b0 ** 2 * (U @ (Fd * np.outer(u1, u1)).real @ U.T)
+            abar = np.diag(Gam).copy()
+            bbar = np.zeros(ke)
+            bbar[: ke - 1] = 2.0 * np.diag(Gam, 1)
+            qbar0, ubar, Q, _ = lanczos_reverse(apply_op, b_all[ti, mi], k, abar, bbar,
+                                                breakdown_tol)
+            q0 = Q[0]
+            b0bar = 2.0 * cw * b0 * np.sum(u1 * u1 * f).real
+            y = b0bar * q0 + (qbar0 - (qbar0 @ q0) * q0) / b0
+            Cbar = ubar.T @ Q
+            G = 0.5 * (Cbar + Cbar.T)
+            deps[m] -= cw * (b0 ** 2 * np.sum(u1 * u1 * dfdz)).real
+            if tda:
+                SC += G @ wl.L
+                SB += np.outer(y, wl.M[ti, mi])
+                dDelta += np.diag(G)
+            else:
+                SC += G @ (d[:, None] * wl.L)
+                SB += np.outer(d * y, wl.M[ti, mi])
+                dDelta += 2.0 * Delta * np.diag(G) + y * V_all[ti, mi] / (2.0 * d)
+    if tda:
+        dL = wl.kernel_factor * SC + SB
+    else:
+        dL = 2.0 * wl.kernel_factor * d[:, None] * SC + SB
+        dDelta += wl.kernel_factor * np.sum(wl.L * SC, axis=1) / d
+    dD = dDelta.reshape(wl.n_v, wl.n_c)
+    deps[wl.n_v:] += dD.sum(axis=0)
+    deps[: wl.n_v] -= dD.sum(axis=1)
+    return dL, deps
+
+
+def qp_energies_tda_closed_form(wl):
+    """E_t and Z_t of the Tamm-Dancoff closed form."""
+    _, poles = sigma_tda_closed_form(wl)
+    return solve_all_qp(wl, poles)
+
+
+def qp_gradient_tda_closed_form(wl, dE):
+    """Gradient of sum_t dE[t] E_t for the Tamm-Dancoff closed form, from the
+    eigenpairs (Omega_s, X_s) of A = Delta + c_K/2 L L^T: each term
+    F = V^T (z + eta A)^-1 V varies as
+        dF = 2 (f(A) V) . dV + tr(G dA) - (dF/dz) d eps_m,
+        G = X (F_div o p p^T) X^T,  p = X^T V,  f(theta) = 1/(z + eta theta)
+    (Daleckii-Krein), and with V = L M, dA = diag(dDelta) + c_K/2 (dL L^T +
+    L dL^T):  dL = c_K G L + y M^T (y = 2 f(A) V),  dDelta = diag(G)."""
+    E, Z = qp_energies_tda_closed_form(wl)
+    theta, X = np.linalg.eigh(tda_matrix(wl.eps, wl.n_v, wl.L, wl.kernel_factor))
+    V_all = coupling_vectors(wl.L, wl.M)
+    eta_all = occupation_sign(wl.m_idx, wl.n_v)
+    SC = np.zeros_like(wl.L)
+    SB = np.zeros_like(wl.L)
+    dDelta = np.zeros(wl.n_vc)
+    deps = np.zeros(wl.n_v + wl.n_c)
+    for ti, t in enumerate(wl.targets):
+        cw = dE[ti] * Z[ti]
+        deps[t] += cw
+        for mi, m in enumerate(wl.m_idx):
+            eta = eta_all[mi]
+            z = E[ti] - wl.eps[m] - 1j * eta * wl.delta
+            p = X.T @ V_all[ti, mi]
+            f, Fd = _tda_f_and_divdiff(theta, z, eta)
+            y = 2.0 * (X @ (f * p)).real
+            G = X @ (Fd * np.outer(p, p)).real @ X.T
+            deps[m] -= cw * np.sum(-p * p / (z + eta * theta) ** 2).real
+            SC += cw * (G @ wl.L)
+            SB += cw * np.outer(y, wl.M[ti, mi])
+            dDelta += cw * np.diag(G)
+    dL = wl.kernel_factor * SC + SB
+    dD = dDelta.reshape(wl.n_v, wl.n_c)
+    deps[wl.n_v:] += dD.sum(axis=0)
+    deps[: wl.n_v] -= dD.sum(axis=1)
+    return dL, deps
 
 
 # --------------------------------------------------------------------------
