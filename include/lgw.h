@@ -197,7 +197,11 @@ typedef struct {
  * reorth_arith   arithmetic of the Gram-Schmidt passes (lgw_reorth_arith)
  * qp_mode        0: graphical solution of E = eps_t + s_t + Re Sigma_t(E)
  *                (Newton, bracketing fallback); 1: linearised at e0 = eps_t +
- *                s_t, E = e0 + Z Re Sigma_t(e0), Z = 1 / (1 - Re Sigma_t'(e0)) */
+ *                s_t, E = e0 + Z Re Sigma_t(e0), Z = 1 / (1 - Re Sigma_t'(e0))
+ * ckpt_every     backward calls, FP64 without reorthogonalisation: steps
+ *                between Krylov checkpoints of the exact reverse sweep
+ *                (0: 16; the forward keeps q_{s-1}, q_s at every multiple s
+ *                of it and recomputes the steps in between) */
 typedef struct {
   int32_t k;
   int32_t precision;
@@ -209,6 +213,7 @@ typedef struct {
   int32_t use_graph;
   int32_t reorth_arith;
   int32_t qp_mode;
+  int32_t ckpt_every;
 } lgw_options;
 
 /* Filled by calls that take a report pointer (host memory).  Phase times are
@@ -495,12 +500,33 @@ lgw_status lgw_sigma_from_coeffs_noalloc(lgw_handle *h, const lgw_system *s,
 
 /* Gradient of sum_t dE[t] * E_qp[t] with respect to L ([n_v*n_c][n_aux]) and
  * eps ([n_v+n_c]) for the request p, through the adjoint of the Lanczos
- * recurrence, the spectral map, the continued fractions and the QP
- * equation (implicit-function factor Z_t).  dL / deps are overwritten;
- * either may be NULL. */
+ * recurrence (Eq. 13), the spectral map and Gauss rule (Eq. 12, 14), the
+ * continued fractions and the QP equation (graphical solution, qp_mode 0;
+ * implicit-function factor Z_t).  dL / deps are overwritten; either may be
+ * NULL.  Two forms:
+ *   - precision LGW_FP64 with reorth LGW_REORTH_NONE: the exact derivative
+ *     of the k-step energies, by reverse mode of the three-term recurrence.
+ *     The forward keeps Krylov checkpoints every o->ckpt_every steps (0: 16)
+ *     and each segment is recomputed before it is taken back, so device
+ *     memory holds 2 k / ckpt_every + 2 ckpt_every + 12 vectors per start
+ *     vector instead of the k + 1 of a stored basis.
+ *   - otherwise (full reorthogonalisation, or BF16/E4M3 contractions): the
+ *     Krylov form over the stored basis, dF/db = Q a, dF/dC = Q Gam Q^T with
+ *     the Daleckii-Krein coefficients of T_k.  Exact at k = n_v*n_c; at
+ *     truncated k it approximates the derivative of the k-step energies to
+ *     the accuracy with which those energies have converged in k.
+ * qp_mode 1 gives LGW_ERR_UNSUPPORTED; a negative ckpt_every LGW_ERR_ARG. */
 lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
                                 const lgw_options *o, const double *dE, double *dL,
                                 double *deps);
+
+/* The same gradient for the Tamm-Dancoff energies of lgw_sigma_c_tda
+ * (A = Delta + c_K/2 L L^T, b = V = L M, f(theta) = 1/(z + eta theta); the
+ * text after Eq. 4 and Eq. 7 with the resonant block alone):
+ * dL = c_K G L + y M^T, dDelta = diag(G).  Same two forms and limits. */
+lgw_status lgw_sigma_c_tda_backward(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                                    const lgw_options *o, const double *dE, double *dL,
+                                    double *deps);
 
 #ifdef __cplusplus
 }

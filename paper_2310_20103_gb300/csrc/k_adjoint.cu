@@ -474,6 +474,245 @@ __global__ void k_adj_deps(const double *dDelta, int n_v, int n_c, const int *ta
   deps[o] += s;
 }
 
+// --------------------------------------------------------------------------
+// Reverse mode of the three-term recurrence (no reorthogonalisation): the
+// exact derivative of what k steps compute.  Forward step j:
+//   u = C q_j,  w1 = u - beta_j q_{j-1},  alpha_j = q_j . w1,
+//   w2 = w1 - alpha_j q_j,  beta_{j+1} = ||w2||,  q_{j+1} = w2 / beta_{j+1}.
+// Taken back from the last step (j = k_eff - 1: w2bar = 0) to step 0:
+//   w2bar  = (qbar_{j+1} - (qbar_{j+1}.q_{j+1}) q_{j+1}) / beta_{j+1} + bbar_j q_{j+1}
+//   abar'  = Gam_jj - w2bar . q_j
+//   ubar_j = w1bar = w2bar + abar' q_j
+//   qbar_j += -alpha_j w2bar + abar' w1,  w1 = beta_{j+1} q_{j+1} + alpha_j q_j
+//   bbar_{j-1} -= w1bar . q_{j-1},  qbar_{j-1} = -beta_j w1bar
+//   qbar_j += C ubar_j (the contraction kernels, next step's first pass)
+// so one pass of six dot products, one scalar step per vector and one
+// elementwise pass per step, besides the matvec.  dF/dC = sum_j ubar_j q_j^T.
+// --------------------------------------------------------------------------
+__global__ void k_rev_init(RevCtx r) {
+  const int b = blockIdx.x;
+  const int k = r.k;
+  for (int j = threadIdx.x; j < k; j += blockDim.x)
+    r.bbar[(size_t)b * k + j] =
+        (j + 1 < k) ? 2.0 * r.Gam[((size_t)b * k + j) * k + j + 1] : 0.0;
+}
+
+__global__ void k_rev_set_betaj(RevCtx r, double *betaj) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= r.Bs) return;
+  double v = 0.0;
+  if (b < r.nvec && r.s0 > 0 && r.k_eff[r.vec0 + b] > r.s0)
+    v = r.beta[(size_t)(r.vec0 + b) * r.k + r.s0 - 1];
+  betaj[b] = v;
+}
+
+__device__ __forceinline__ int rev_elem_base(int chunk) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  return chunk * VEC_CHUNK + wid * 256 + 2 * lane;
+}
+
+// qbar_{j+1} += C ubar_{j+1} (written back), and per-chunk partials of
+// qbar_{j+1}.q_{j+1}, qbar_{j+1}.q_j, q_{j+1}.q_j, qbar_{j+1}.q_{j-1},
+// q_{j+1}.q_{j-1}, q_j.q_{j-1}.
+__global__ void __launch_bounds__(VEC_THREADS) k_rev_dots(RevCtx r, int j) {
+  __shared__ double red[VEC_THREADS / 32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const size_t BN = (size_t)r.Bs * r.N, voff = (size_t)b * r.N;
+  const double *q1 = r.seg + (size_t)(j - r.s0 + 2) * BN + voff;
+  const double *q0 = r.seg + (size_t)(j - r.s0 + 1) * BN + voff;
+  const double *qm = r.seg + (size_t)(j - r.s0) * BN + voff;
+  double *qb1 = r.qbar + (size_t)((j + 1) % 3) * BN + voff;
+  const double *cu = r.cu + voff;
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const int e0 = rev_elem_base(chunk);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= r.N) continue;
+    double2 x = *reinterpret_cast<const double2 *>(qb1 + e);
+    const double2 c2 = *reinterpret_cast<const double2 *>(cu + e);
+    x.x += c2.x;
+    x.y += c2.y;
+    *reinterpret_cast<double2 *>(qb1 + e) = x;
+    const double2 a = *reinterpret_cast<const double2 *>(q1 + e);
+    const double2 p = *reinterpret_cast<const double2 *>(q0 + e);
+    const double2 m = *reinterpret_cast<const double2 *>(qm + e);
+    acc[0] = fma(x.x, a.x, fma(x.y, a.y, acc[0]));
+    acc[1] = fma(x.x, p.x, fma(x.y, p.y, acc[1]));
+    acc[2] = fma(a.x, p.x, fma(a.y, p.y, acc[2]));
+    acc[3] = fma(x.x, m.x, fma(x.y, m.y, acc[3]));
+    acc[4] = fma(a.x, m.x, fma(a.y, m.y, acc[4]));
+    acc[5] = fma(p.x, m.x, fma(p.y, m.y, acc[5]));
+  }
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const double s = block_sum(acc[t], red);
+    if (threadIdx.x == 0) r.dpart[((size_t)b * r.nchunks + chunk) * 6 + t] = s;
+  }
+}
+
+// One warp per vector: the six dots in fixed order and the step's
+// coefficients: ubar = a1 qbar_{j+1} + a2 q_{j+1} + ab q_j,
+// qbar_j += cA qbar_{j+1} + cB q_{j+1} + cC q_j, qbar_{j-1} = mb ubar.
+__global__ void k_rev_scalars(RevCtx r, int j) {
+  const int b = blockIdx.x, lane = threadIdx.x;
+  double d[6];
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    double s = 0.0;
+    for (int ch = lane; ch < r.nchunks; ch += 32)
+      s += r.dpart[((size_t)b * r.nchunks + ch) * 6 + t];
+    d[t] = warp_sum(s);
+  }
+  if (lane != 0) return;
+  const int v = r.vec0 + b;
+  const int ke = b < r.nvec ? r.k_eff[v] : 0;
+  double a1 = 0.0, a2 = 0.0, ab = 0.0, cA = 0.0, cB = 0.0, cC = 0.0, mb = 0.0;
+  if (j < ke) {
+    const int k = r.k;
+    const double al = r.alpha[(size_t)v * k + j];
+    const double bn = r.beta[(size_t)v * k + j];
+    const double bj = j > 0 ? r.beta[(size_t)v * k + j - 1] : 0.0;
+    if (j + 1 < ke) {
+      a1 = 1.0 / bn;
+      a2 = r.bbar[(size_t)b * k + j] - d[0] * a1;
+    }
+    const double w2q = a1 * d[1] + a2 * d[2];
+    ab = r.Gam[((size_t)b * k + j) * k + j] - w2q;
+    if (j > 0) r.bbar[(size_t)b * k + j - 1] -= a1 * d[3] + a2 * d[4] + ab * d[5];
+    cA = -al * a1;
+    cB = fma(ab, bn, -al * a2);
+    cC = ab * al;
+    mb = -bj;
+  }
+  double *cf = r.coef + (size_t)b * 8;
+  cf[0] = a1;
+  cf[1] = a2;
+  cf[2] = ab;
+  cf[3] = cA;
+  cf[4] = cB;
+  cf[5] = cC;
+  cf[6] = mb;
+}
+
+__global__ void __launch_bounds__(VEC_THREADS) k_rev_elem(RevCtx r, int j) {
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const size_t BN = (size_t)r.Bs * r.N, voff = (size_t)b * r.N;
+  const double *cf = r.coef + (size_t)b * 8;
+  const double a1 = cf[0], a2 = cf[1], ab = cf[2], cA = cf[3], cB = cf[4], cC = cf[5],
+               mb = cf[6];
+  const double *q1 = r.seg + (size_t)(j - r.s0 + 2) * BN + voff;
+  const double *q0 = r.seg + (size_t)(j - r.s0 + 1) * BN + voff;
+  const double *qb1 = r.qbar + (size_t)((j + 1) % 3) * BN + voff;
+  double *qbj = r.qbar + (size_t)(j % 3) * BN + voff;
+  double *qbm = r.qbar + (size_t)((j + 2) % 3) * BN + voff;   // slot of q_{j-1}
+  double *ub = r.useg + (size_t)(j - r.s0) * BN + voff;
+  double *gd = r.Gd + voff;
+  const int e0 = rev_elem_base(chunk);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= r.N) continue;
+    const double2 x = *reinterpret_cast<const double2 *>(qb1 + e);
+    const double2 a = *reinterpret_cast<const double2 *>(q1 + e);
+    const double2 p = *reinterpret_cast<const double2 *>(q0 + e);
+    double2 w;
+    w.x = fma(a1, x.x, fma(a2, a.x, ab * p.x));
+    w.y = fma(a1, x.y, fma(a2, a.y, ab * p.y));
+    double2 y = *reinterpret_cast<const double2 *>(qbj + e);
+    y.x += fma(cA, x.x, fma(cB, a.x, cC * p.x));
+    y.y += fma(cA, x.y, fma(cB, a.y, cC * p.y));
+    *reinterpret_cast<double2 *>(qbj + e) = y;
+    if (j > 0) *reinterpret_cast<double2 *>(qbm + e) = make_double2(mb * w.x, mb * w.y);
+    *reinterpret_cast<double2 *>(ub + e) = w;
+    double2 g = *reinterpret_cast<const double2 *>(gd + e);
+    g.x = fma(w.x, p.x, g.x);
+    g.y = fma(w.y, p.y, g.y);
+    *reinterpret_cast<double2 *>(gd + e) = g;
+  }
+}
+
+// qbar_0 += C ubar_0 (written back) and per-chunk partials of qbar_0 . q_0.
+__global__ void __launch_bounds__(VEC_THREADS) k_rev_final_dot(RevCtx r, const double *q0v) {
+  __shared__ double red[VEC_THREADS / 32];
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const size_t voff = (size_t)b * r.N;
+  double *qb = r.qbar + voff;
+  const double *cu = r.cu + voff;
+  const double *q0 = q0v + voff;
+  double acc = 0.0;
+  const int e0 = rev_elem_base(chunk);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= r.N) continue;
+    double2 x = *reinterpret_cast<const double2 *>(qb + e);
+    const double2 c2 = *reinterpret_cast<const double2 *>(cu + e);
+    x.x += c2.x;
+    x.y += c2.y;
+    *reinterpret_cast<double2 *>(qb + e) = x;
+    const double2 p = *reinterpret_cast<const double2 *>(q0 + e);
+    acc = fma(x.x, p.x, fma(x.y, p.y, acc));
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) r.dpart[(size_t)b * r.nchunks + chunk] = acc;
+}
+
+// y = dF/db = (dF/dbeta0) q_0 + (qbar_0 - (qbar_0 . q_0) q_0) / beta0.
+__global__ void __launch_bounds__(VEC_THREADS) k_rev_final(RevCtx r, const double *q0v,
+                                                           double *Y) {
+  __shared__ double sdot;
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const int v = r.vec0 + b;
+  const bool live = b < r.nvec && r.k_eff[v] > 0 && r.beta0[v] > 0.0;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int ch = threadIdx.x; ch < r.nchunks; ch += 32) s += r.dpart[(size_t)b * r.nchunks + ch];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) sdot = s;
+  }
+  __syncthreads();
+  const double dq = sdot;
+  const double b0 = live ? r.beta0[v] : 1.0;
+  const double b0bar = live ? r.ay[(size_t)b * r.k] : 0.0;
+  const double inv = live ? 1.0 / b0 : 0.0;
+  const size_t voff = (size_t)b * r.N;
+  const double *qb = r.qbar + voff;
+  const double *q0 = q0v + voff;
+  double *y = Y + voff;
+  const int e0 = rev_elem_base(chunk);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u * 64;
+    if (e >= r.N) continue;
+    const double2 x = *reinterpret_cast<const double2 *>(qb + e);
+    const double2 p = *reinterpret_cast<const double2 *>(q0 + e);
+    double2 o;
+    o.x = fma(b0bar, p.x, inv * fma(-dq, p.x, x.x));
+    o.y = fma(b0bar, p.y, inv * fma(-dq, p.y, x.y));
+    if (!live) o = make_double2(0.0, 0.0);
+    *reinterpret_cast<double2 *>(y + e) = o;
+  }
+}
+
+void launch_rev_init(const RevCtx &r, cudaStream_t st) {
+  k_rev_init<<<r.Bs, 128, 0, st>>>(r);
+}
+void launch_rev_set_betaj(const RevCtx &r, double *betaj, cudaStream_t st) {
+  k_rev_set_betaj<<<(r.Bs + 127) / 128, 128, 0, st>>>(r, betaj);
+}
+void launch_rev_step(const RevCtx &r, int j, cudaStream_t st) {
+  dim3 grid(r.nchunks, r.Bs);
+  k_rev_dots<<<grid, VEC_THREADS, 0, st>>>(r, j);
+  k_rev_scalars<<<r.Bs, 32, 0, st>>>(r, j);
+  k_rev_elem<<<grid, VEC_THREADS, 0, st>>>(r, j);
+}
+void launch_rev_finish(const RevCtx &r, const double *q0, double *Y, cudaStream_t st) {
+  dim3 grid(r.nchunks, r.Bs);
+  k_rev_final_dot<<<grid, VEC_THREADS, 0, st>>>(r, q0);
+  k_rev_final<<<grid, VEC_THREADS, 0, st>>>(r, q0, Y);
+}
+
 // ----------------------------------------------------------------------------
 int adj_max_k() {
   // k_adj_rows stages k * ROW_THREADS doubles; k_eig_full 4 k per warp

@@ -514,11 +514,15 @@ PolyOp make_poly(int g, double lo, double hi) {
 // sub-batch row b at basis + (j * Bs + b) * N) whatever the reorthogonalisation
 // mode; after_sub, if given, runs once each sub-batch's recurrence is done.
 using SubBatchHook = std::function<void(const VecCtx &)>;
+// after_step, if given, runs after the start (j = -1) and after each step j
+// that ends with the plain normalisation (FP64 basis or ring; not the split
+// basis), once q_{j+1} is in its slot.
+using StepHook = std::function<void(const VecCtx &, int)>;
 
 void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &o, double *alpha,
                  double *beta, double *beta0, int *k_eff, lgw_report *rep, double *tacc,
                  bool keep_basis = false, const SubBatchHook *after_sub = nullptr,
-                 const PolyOp *poly = nullptr) {
+                 const PolyOp *poly = nullptr, const StepHook *after_step = nullptr) {
   // a reference: a graph capture redirects the launches to the capture stream
   cudaStream_t &st = h->stream;
   const int B = pv.B;
@@ -766,6 +770,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
       else
         launch_normalize(c, 0, 1, nullptr, st);
       check_launch(h, "normalize(start)");
+      if (after_step) (*after_step)(c, -1);
 
       for (int j = 0; j < k; ++j) {
         const double *qj = slot_ptr(c, j);
@@ -923,6 +928,7 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
         check_launch(h, "beta_vec");
         launch_normalize(c, j, 0, nullptr, st);
         check_launch(h, "normalize");
+        if (after_step) (*after_step)(c, j);
       }
     };
     if (graph_mode) {
@@ -1400,6 +1406,115 @@ lgw_status sigma_c_impl(lgw_handle *h, const lgw_system *sys, const lgw_problem 
     return f.st;
   }
   return LGW_OK;
+}
+// Exact reverse mode of one sub-batch's three-term recurrence (FP64, no
+// reorthogonalisation), segment by segment from the last: each segment
+// [s0, s0 + ci) is recomputed from its checkpoint (q_{s0-1}, q_s0) with the
+// forward's own kernels (breakdown test off: the recorded depths stand),
+// then taken back step by step (k_rev_*: one dot pass, one scalar step, one
+// elementwise pass, and C ubar_j through the FP64 contractions).  SC
+// accumulates sum_j (ubar_j (L^T D q_j)^T + q_j (L^T D ubar_j)^T) = 2 G D L;
+// then y = dF/db, SB += y M^T and the diagonal terms of dDelta.
+void reverse_sweep(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &op,
+                   const VecCtx &c, const AdjCtx &a, const double *ckpt, int ci, double *SC,
+                   double *SB, double *dD, double *gdeps) {
+  cudaStream_t &st = h->stream;
+  const int Bs = c.Bs, N = c.N, A = s.A, k = op.k;
+  const size_t BN = (size_t)Bs * N, BA = (size_t)Bs * A;
+  const int cs = std::min(ci, k), nseg = (k + ci - 1) / ci;
+  double *seg = wsT<double>(h, "rev_seg", (size_t)(cs + 2) * BN);
+  double *useg = wsT<double>(h, "rev_useg", (size_t)cs * BN);
+  double *yseg = wsT<double>(h, "rev_yseg", (size_t)cs * BA);
+  double *ybseg = wsT<double>(h, "rev_ybseg", (size_t)cs * BA);
+  const int sp = gemm1_f64_splits(s, Bs);
+  double *yp = wsT<double>(h, "rev_yp", (size_t)sp * BA);
+  double *Y = wsT<double>(h, "adj_Y", BN);
+  RevCtx r{};
+  r.N = N;
+  r.Bs = Bs;
+  r.nvec = c.nvec;
+  r.vec0 = c.vec0;
+  r.k = k;
+  r.nchunks = c.nchunks;
+  r.seg = seg;
+  r.qbar = wsT<double>(h, "rev_qbar", 3 * BN);
+  double *cu = wsT<double>(h, "rev_cu", BN);
+  r.cu = cu;
+  r.useg = useg;
+  r.Gd = wsT<double>(h, "adj_Gd", BN);
+  r.dpart = wsT<double>(h, "rev_dpart", (size_t)Bs * c.nchunks * 6);
+  r.coef = wsT<double>(h, "rev_coef", (size_t)Bs * 8);
+  r.bbar = wsT<double>(h, "rev_bbar", (size_t)Bs * k);
+  r.Gam = a.Gam;
+  r.ay = a.ay;
+  r.alpha = a.alpha;
+  r.beta = a.beta;
+  r.beta0 = a.beta0;
+  r.k_eff = a.k_eff;
+  LGW_TRY_CUDA(h, cudaMemsetAsync(r.qbar, 0, sizeof(double) * 3 * BN, st));
+  LGW_TRY_CUDA(h, cudaMemsetAsync(cu, 0, sizeof(double) * BN, st));
+  LGW_TRY_CUDA(h, cudaMemsetAsync(r.Gd, 0, sizeof(double) * BN, st));
+  launch_rev_init(r, st);
+  check_launch(h, "rev_init");
+  // the recomputation window: q_j at slot j - (s0 - 1) of seg
+  VecCtx rc = c;
+  rc.ring = 0;
+  rc.basis = seg;
+  rc.nslots = cs + 2;
+  rc.tol = 0.0;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int s0 = sg * ci, e = std::min(s0 + ci, k), n = e - s0;
+    LGW_TRY_CUDA(h, cudaMemcpyAsync(seg, ckpt + (size_t)sg * 2 * BN, sizeof(double) * 2 * BN,
+                                    cudaMemcpyDeviceToDevice, st));
+    rc.slot0 = s0 - 1;
+    r.s0 = s0;
+    launch_rev_set_betaj(r, rc.betaj, st);
+    check_launch(h, "rev_set_betaj");
+    for (int j = s0; j < e; ++j) {
+      const double *qj = slot_ptr(rc, j);
+      const double *qp = j > 0 ? slot_ptr(rc, j - 1) : nullptr;
+      double *yj = yseg + (size_t)(j - s0) * BA;
+      launch_gemm1_f64(s, qj, Bs, yp, sp, st);
+      check_launch(h, "gemm1_f64(recompute)");
+      launch_reduce_y_f64(yp, sp, Bs, A, yj, st);
+      check_launch(h, "reduce_y_f64(recompute)");
+      launch_gemm2_f64(s, yj, Bs, EPI_LANCZOS, qj, qp, rc.betaj, rc.w, rc.alpha_part, st);
+      check_launch(h, "gemm2_f64(recompute)");
+      launch_alpha_reduce(rc, j, st);
+      check_launch(h, "alpha_reduce(recompute)");
+      launch_alpha_axpy(rc, j, st);
+      check_launch(h, "alpha_axpy(recompute)");
+      launch_beta_vec(rc, j, st);
+      check_launch(h, "beta_vec(recompute)");
+      launch_normalize(rc, j, 0, nullptr, st);
+      check_launch(h, "normalize(recompute)");
+    }
+    for (int j = e - 1; j >= s0; --j) {
+      launch_rev_step(r, j, st);
+      check_launch(h, "rev_step");
+      const double *uj = useg + (size_t)(j - s0) * BN;
+      double *ybj = ybseg + (size_t)(j - s0) * BA;
+      launch_gemm1_f64(s, uj, Bs, yp, sp, st);
+      check_launch(h, "gemm1_f64(reverse)");
+      launch_reduce_y_f64(yp, sp, Bs, A, ybj, st);
+      check_launch(h, "reduce_y_f64(reverse)");
+      launch_gemm2_f64(s, ybj, Bs, EPI_APPLY, uj, nullptr, nullptr, cu, nullptr, st);
+      check_launch(h, "gemm2_f64(reverse)");
+    }
+    launch_atb_f64(useg, N, yseg, A, n * Bs, N, A, SC, st);
+    check_launch(h, "atb_f64(SC, ubar)");
+    launch_atb_f64(seg + BN, N, ybseg, A, n * Bs, N, A, SC, st);
+    check_launch(h, "atb_f64(SC, q)");
+  }
+  const double *q0 = ckpt + BN;
+  launch_rev_finish(r, q0, Y, st);
+  check_launch(h, "rev_finish");
+  if (SB) {
+    launch_atb_f64(Y, N, pv.d_M + (size_t)c.vec0 * s.n_aux, s.n_aux, c.nvec, N, s.n_aux, SB, st);
+    check_launch(h, "atb_f64(SB)");
+  }
+  launch_adj_accumulate(a, s.Delta, BasisRef{q0, nullptr, nullptr}, Y, r.Gd, dD, gdeps, st);
+  check_launch(h, "adj_accumulate");
 }
 }  // namespace
 
@@ -2178,19 +2293,32 @@ lgw_status lgw_sigma_c_batched(lgw_handle *h, int32_t n_sys, const lgw_system *c
   return LGW_OK;
 }
 
-lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+static lgw_status backward_impl(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
                                 const lgw_options *o, const double *dE, double *dL,
-                                double *deps) {
+                                double *deps, bool tda) {
   lgw_status g = guard_handle(h);
   if (g != LGW_OK) return g;
-  if (!sys || sys->h != h || !dE) return set_err(h, LGW_ERR_ARG, "NULL argument to lgw_sigma_c_backward");
+  if (!sys || sys->h != h || !dE) return set_err(h, LGW_ERR_ARG, "NULL argument to the backward call");
   try {
-    const SysDev &s = sys->s;
     cudaStream_t st = h->stream;
     h->timing = false;
     LGW_TRY_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
-    Opts op = resolve_opts(h, o, s);
+    Opts op = resolve_opts(h, o, sys->s);
     ensure_copies(h, sys, op);
+    const SysDev &s = tda ? tda_view(h, sys) : sys->s;
+    if (op.qp_mode != 0) {
+      set_err(h, LGW_ERR_UNSUPPORTED, "the adjoint differentiates the graphical QP solution (qp_mode 0)");
+      throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    // FP64 contractions without reorthogonalisation: the exact reverse mode
+    // of the three-term recurrence, recomputed from Krylov checkpoints;
+    // otherwise the Krylov form over the stored basis
+    const bool exact = op.reorth == LGW_REORTH_NONE && op.precision == LGW_FP64;
+    const int ci = (o->ckpt_every > 0) ? o->ckpt_every : 16;
+    if (o->ckpt_every < 0) {
+      set_err(h, LGW_ERR_ARG, "ckpt_every < 0");
+      throw Fail{LGW_ERR_ARG};
+    }
     // the adjoint contracts with the stored Krylov basis: FP64 (FP64 mode)
     // or the split float pair (BF16 mode with split arithmetic); the split
     // basis needs reorthogonalisation (otherwise the FP64 basis is kept)
@@ -2245,8 +2373,11 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
       LGW_TRY_CUDA(h, cudaMemGetInfo(&fr, &tot));
       size_t held = 0;
       for (auto &kv : h->bufs) held += kv.second.n;
-      const double per_vec = 8.0 * (k + 1) * N + (tc ? 4.0 * k * N : 0.0) + 20.0 * k * A +
-                             48.0 * N + 40.0 * k * k;
+      const int cs = std::min(ci, k), nseg = (k + ci - 1) / ci;
+      const double per_vec =
+          exact ? 8.0 * (2 * nseg + 2 * cs + 12) * N + 16.0 * cs * A + 40.0 * k * k
+                : 8.0 * (k + 1) * N + (tc ? 4.0 * k * N : 0.0) + 20.0 * k * A + 48.0 * N +
+                      40.0 * k * k;
       const double budget = 0.5 * (double)(fr + held);
       int fit = (int)std::min<double>(budget / per_vec, 1 << 20);
       fit = std::max(PAD_VEC, fit / PAD_VEC * PAD_VEC);
@@ -2276,7 +2407,30 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
     LGW_TRY_CUDA(h, cudaMemsetAsync(dD, 0, sizeof(double) * N, st));
 
     auto forward_sigma = [&]() {
-      run_sigma(h, s, pv, op, alpha, beta, beta0, ke, nullptr, E, Z, nullptr, nullptr);
+      run_sigma(h, s, pv, op, alpha, beta, beta0, ke, nullptr, E, Z, nullptr, nullptr,
+                tda ? 2 : 0);
+    };
+    // Krylov checkpoints of the exact mode: (q_{s0-1}, q_s0) at every segment
+    // start s0 = 0, ci, 2 ci, ... (q_{-1} = 0), copied out of the forward's
+    // three-vector ring
+    const int nseg = (k + ci - 1) / ci;
+    double *ckpt = nullptr;
+    StepHook keep_ckpt = [&](const VecCtx &c, int j) {
+      const size_t BN = (size_t)c.Bs * c.N;
+      if (j < 0) {
+        ckpt = wsT<double>(h, "rev_ckpt", (size_t)nseg * 2 * BN);
+        LGW_TRY_CUDA(h, cudaMemsetAsync(ckpt, 0, sizeof(double) * BN, st));
+        LGW_TRY_CUDA(h, cudaMemcpyAsync(ckpt + BN, slot_ptr(c, 0), sizeof(double) * BN,
+                                        cudaMemcpyDeviceToDevice, st));
+        return;
+      }
+      const int nx = j + 1;
+      if (nx % ci != 0 || nx >= k) return;
+      double *dst = ckpt + (size_t)(nx / ci) * 2 * BN;
+      LGW_TRY_CUDA(h, cudaMemcpyAsync(dst, slot_ptr(c, j), sizeof(double) * BN,
+                                      cudaMemcpyDeviceToDevice, st));
+      LGW_TRY_CUDA(h, cudaMemcpyAsync(dst + BN, slot_ptr(c, nx), sizeof(double) * BN,
+                                      cudaMemcpyDeviceToDevice, st));
     };
     SubBatchHook adjoint = [&](const VecCtx &c) {
       if (one_pass) forward_sigma();
@@ -2311,10 +2465,15 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
       a.Gamf = tc ? wsT<float>(h, "adj_Gamf", (size_t)Bs * kk) : nullptr;
       a.dz = wsT<double>(h, "adj_dz", (size_t)Bs);
       a.status = h->d_status;
+      a.tda = tda ? 1 : 0;
       launch_eig_full(a, st);
       check_launch(h, "eig_full");
       launch_adj_coeffs(a, st);
       check_launch(h, "adj_coeffs");
+      if (exact) {
+        reverse_sweep(h, s, pv, op, c, a, ckpt, ci, SC, SB, dD, gdeps);
+        return;
+      }
       double *Y = wsT<double>(h, "adj_Y", (size_t)Bs * N);
       double *Gd = wsT<double>(h, "adj_Gd", (size_t)Bs * N);
       if (tc)
@@ -2383,15 +2542,22 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
       launch_adj_accumulate(a, s.Delta, qb, Y, Gd, dD, gdeps, st);
       check_launch(h, "adj_accumulate");
     };
+    // the exact mode keeps only the three-vector ring and the checkpoints
+    const bool keep = !exact;
+    const StepHook *sh = exact ? &keep_ckpt : nullptr;
     if (one_pass) {
-      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, true, &adjoint);
+      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, keep, &adjoint, nullptr,
+                  sh);
     } else {
       run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, false, nullptr);
       forward_sigma();
-      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, true, &adjoint);
+      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, keep, &adjoint, nullptr,
+                  sh);
     }
     double *dLdev = oL.dev ? oL.dev : wsT<double>(h, "adj_dL", (size_t)s.n_vc * s.n_aux);
-    launch_adj_dL(s.L64, s.dsq, SC, SB, A, s.n_vc, s.n_aux, s.kf, dLdev, dD, 0, st);
+    // the exact mode accumulates SC = sum_j (ubar_j y_j^T + q_j ybar_j^T) = 2 G D L
+    launch_adj_dL(s.L64, s.dsq, SC, SB, A, s.n_vc, s.n_aux, exact ? 0.5 * s.kf : s.kf, dLdev, dD,
+                  tda ? 1 : 0, st);
     check_launch(h, "adj_dL");
     launch_adj_deps(dD, s.n_v, s.n_c, pv.d_targets, pv.n_t, Z, d_dE, gdeps, st);
     check_launch(h, "adj_deps");
@@ -2405,6 +2571,18 @@ lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_
     return f.st;
   }
   return LGW_OK;
+}
+
+lgw_status lgw_sigma_c_backward(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                                const lgw_options *o, const double *dE, double *dL,
+                                double *deps) {
+  return backward_impl(h, sys, p, o, dE, dL, deps, false);
+}
+
+lgw_status lgw_sigma_c_tda_backward(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                                    const lgw_options *o, const double *dE, double *dL,
+                                    double *deps) {
+  return backward_impl(h, sys, p, o, dE, dL, deps, true);
 }
 
 lgw_status lgw_sigma_x(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,

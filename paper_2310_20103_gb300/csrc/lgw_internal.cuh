@@ -70,6 +70,8 @@ struct VecCtx {
   int reorth;             // lgw_reorth
   int ring;               // 1: FP64 vectors live in a 3-slot ring (slot j % 3)
   int nslots;             // FP64 slots (k + 1 for the FP64 basis, else 3)
+  int slot0;              // without the ring, q_j lives in slot j - slot0 (a window of
+                          // the basis, used by the recomputation from a checkpoint)
   double tol;
   const double *Delta2, *dsq, *cd;
   double *w;              // [Bs][N]
@@ -135,7 +137,7 @@ __host__ __device__ inline size_t kblk_f32(int b, int e, int Bs) {
 }
 
 __host__ __device__ inline double *slot_ptr(const VecCtx &c, int j) {
-  int s = c.ring ? (j % 3) : j;
+  int s = c.ring ? (j % 3) : (j - c.slot0);
   return c.basis + (size_t)s * c.Bs * c.N;
 }
 
@@ -432,6 +434,29 @@ struct AdjCtx {
   // Delta and b does not depend on it)
   int tda;
 };
+// Reverse mode of the three-term recurrence (no reorthogonalisation) over
+// one segment of steps [s0, e) of a sub-batch, the steps taken back from
+// e - 1 to s0.  Vector buffers are [Bs][N] per slot.
+struct RevCtx {
+  int N, Bs, nvec, vec0, k, nchunks;
+  int s0;                 // first step of the segment
+  const double *seg;      // q_{s0-1} .. q_e at slot j - s0 + 1 (q_{-1} = 0)
+  double *qbar;           // [3] adjoints of q_j at slot j % 3
+  const double *cu;       // C ubar_{j+1} of the step taken back before (0 at the start)
+  double *useg;           // ubar_j at slot j - s0
+  double *Gd;             // [Bs][N] running sum_j ubar_j o q_j
+  double *dpart;          // [Bs][nchunks][6] dot-product partials
+  double *coef;           // [Bs][8] per-vector coefficients of the running step
+  double *bbar;           // [Bs][k] running adjoints of beta[j] (coupling of j, j+1)
+  const double *Gam;      // [Bs][k][k] dF/dT_k (weights folded in)
+  const double *ay;       // [Bs][k]; ay[0] = dF/dbeta0
+  const double *alpha, *beta, *beta0;   // global [B][k], [B][k], [B]
+  const int *k_eff;       // global [B]
+};
+void launch_rev_init(const RevCtx &r, cudaStream_t st);
+void launch_rev_set_betaj(const RevCtx &r, double *betaj, cudaStream_t st);
+void launch_rev_step(const RevCtx &r, int j, cudaStream_t st);
+void launch_rev_finish(const RevCtx &r, const double *q0, double *Y, cudaStream_t st);
 int adj_max_k();
 bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const int *a_kblk,
                     const __nv_bfloat16 *const *B, int M, int Ncols, int K, int kchunk,

@@ -61,7 +61,8 @@ class lgw_options(ctypes.Structure):
                 ("reorth", ctypes.c_int32), ("b_sub", ctypes.c_int32),
                 ("breakdown_tol", ctypes.c_double), ("qp_max_iter", ctypes.c_int32),
                 ("qp_tol", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("reorth_arith", ctypes.c_int32), ("qp_mode", ctypes.c_int32)]
+                ("reorth_arith", ctypes.c_int32), ("qp_mode", ctypes.c_int32),
+                ("ckpt_every", ctypes.c_int32)]
 
 
 class lgw_report(ctypes.Structure):
@@ -109,6 +110,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                  ctypes.POINTER(lgw_report)], I),
         "lgw_sigma_c_backward": ([P, P, ctypes.POINTER(lgw_problem),
                                   ctypes.POINTER(lgw_options), P, P, P], I),
+        "lgw_sigma_c_tda_backward": ([P, P, ctypes.POINTER(lgw_problem),
+                                      ctypes.POINTER(lgw_options), P, P, P], I),
         "lgw_sigma_x": ([P, P, ctypes.POINTER(lgw_problem), P], I),
         "lgw_sigma_c_tda": ([P, P, ctypes.POINTER(lgw_problem), ctypes.POINTER(lgw_options),
                              P, P, P, ctypes.POINTER(lgw_report)], I),
@@ -224,6 +227,7 @@ class Options:
     use_graph: int = 0
     reorth_arith: str = "auto"
     qp_mode: str = "graphical"
+    ckpt_every: int = 0
 
     def to_c(self) -> lgw_options:
         o = lgw_options()
@@ -237,6 +241,7 @@ class Options:
         o.use_graph = int(self.use_graph)
         o.reorth_arith = REORTH_ARITH[self.reorth_arith]
         o.qp_mode = QP_MODE[self.qp_mode]
+        o.ckpt_every = int(self.ckpt_every)
         return o
 
 
@@ -457,6 +462,14 @@ def lgw_sigma_c_backward(h: Handle, s: System, problem: Problem, options: Option
                          dL=None, deps=None) -> None:
     p, o = problem.to_c(), options.to_c()
     _check(h, load_library().lgw_sigma_c_backward(
+        h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), _ptr(dE, "f64"), _ptr(dL, "f64"),
+        _ptr(deps, "f64")))
+
+
+def lgw_sigma_c_tda_backward(h: Handle, s: System, problem: Problem, options: Options, dE,
+                             dL=None, deps=None) -> None:
+    p, o = problem.to_c(), options.to_c()
+    _check(h, load_library().lgw_sigma_c_tda_backward(
         h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), _ptr(dE, "f64"), _ptr(dL, "f64"),
         _ptr(deps, "f64")))
 
