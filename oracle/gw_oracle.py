@@ -39,7 +39,7 @@ __all__ = [
     "solve_all_qp", "qp_gradient", "qp_energies_closed_form", "qp_gradient_closed_form",
     "qp_gradient_lanczos", "lanczos_reverse", "qp_gradient_recurrence",
     "qp_energies_tda_closed_form", "qp_gradient_tda_closed_form", "chebyshev_sqrt", "chebyshev_eval", "apply_poly",
-    "sigma_poly_lanczos", "haydock", "sigma_x", "qp_linearised", "fit_factors",
+    "sigma_poly_lanczos", "apply_poly_reverse", "qp_gradient_poly_recurrence", "haydock", "sigma_x", "qp_linearised", "fit_factors",
     "tda_matrix", "sigma_tda_closed_form", "sigma_tda_lanczos", "sigma_offdiag_closed_form",
     "band_lanczos", "band_gauss_rule", "sigma_band_lanczos",
 ]
@@ -760,6 +760,122 @@ def sigma_poly_lanczos(wl, g, lo, hi, k=None, reorth=True):
                 E.append(np.full(ke, eta))
         poles.append((np.concatenate(P), np.concatenate(Wt), np.concatenate(E)))
     return sig, poles, coeffs
+
+
+def apply_poly_reverse(apply_op, u, x, c, lo, hi):
+    """Reverse mode of ``apply_poly`` for one vector: y = p(C) x by
+    Clenshaw's recurrence in S = a_s C + b_s I,
+        b_g = c_g x,  b_k = c_k x + 2 S b_{k+1} - b_{k+2} (k = g-1 .. 1),
+        y = c_0 x + S b_1 - b_2,
+    and the scalar u . y.  Taking the recurrence back with ybar = u gives
+        bbar_1 = S u,  bbar_k = 2 S bbar_{k-1} - bbar_{k-2}  (bbar_0 = u),
+        xbar = c_0 u + sum_{k>=1} c_k bbar_k      (= p(C)^T u),
+        Sbar = u b_1^T + 2 sum_{k=1}^{g-1} bbar_k b_{k+1}^T,  Cbar = a_s Sbar.
+    Returns (xbar, pairs) with d(u . p(C) x)/dC = sum (coef * a) b^T over the
+    pairs (coef, a, b)."""
+    g = len(c) - 1
+    a_s, b_s = 2.0 / (hi - lo), -(hi + lo) / (hi - lo)
+
+    def S(X):
+        return a_s * apply_op(X[None, :])[0] + b_s * X
+
+    bk = [None] * (g + 2)
+    bk[g + 1] = np.zeros_like(x)
+    if g >= 1:
+        bk[g] = c[g] * x
+        for k in range(g - 1, 0, -1):
+            bk[k] = c[k] * x + 2.0 * S(bk[k + 1]) - (bk[k + 2] if k + 2 <= g else 0.0)
+    xbar = c[0] * u
+    pairs = []
+    if g == 0:
+        return xbar, pairs
+    bbar = [u, S(u)]
+    pairs.append((a_s, u, bk[1]))
+    for k in range(2, g + 1):
+        bbar.append(2.0 * S(bbar[k - 1]) - bbar[k - 2])
+    for k in range(1, g + 1):
+        xbar = xbar + c[k] * bbar[k]
+        if k <= g - 1:
+            pairs.append((2.0 * a_s, bbar[k], bk[k + 1]))
+    return xbar, pairs
+
+
+def qp_gradient_poly_recurrence(wl, dE, g, lo, hi, k=None, breakdown_tol=1e-13):
+    """Exact gradient of sum_t dE[t] E_t^(k) for the polynomial form: k-step
+    Lanczos on D = p_g(C) without reorthogonalisation
+    (``sigma_poly_lanczos(reorth=False)``) and the QP equation.
+
+    Per start vector the Gauss rule of D's tridiagonal gives
+    F = beta0^2 Re e_1^T f(T_k) e_1 with f(Om) = 1 / (Om (z + eta Om)) on D's
+    nodes Om (no square root: D already approximates C^1/2), so
+        dF/dT_k = c beta0^2 Re U (F_div o u1 u1^T) U^T,
+        F_div[s, t] = -(z + eta (Om_s + Om_t)) / (Om_s Om_t (z + eta Om_s)(z + eta Om_t)).
+    The recurrence is taken back with operator D (``lanczos_reverse``),
+    giving dF/dD = sum_j ubar_j q_j^T; each term passes to C through the
+    reverse of the Clenshaw recurrence (``apply_poly_reverse``):
+        dF/dC = sum_j sum_pairs coef a b^T   (a, b from ubar_j and q_j).
+    Assembly as in ``qp_gradient_recurrence`` (Casida C, b = D L M)."""
+    k = wl.k if k is None else k
+    c = chebyshev_sqrt(lo, hi, g)
+    Delta = pair_energies(wl.eps, wl.n_v)
+    d = np.sqrt(Delta)
+    V_all = coupling_vectors(wl.L, wl.M)
+    eta_all = occupation_sign(wl.m_idx, wl.n_v)
+
+    def apply_C(X):
+        return apply_casida(wl.eps, wl.n_v, wl.L, X, wl.kernel_factor)
+
+    def apply_D(X):
+        return apply_poly(apply_C, X, c, lo, hi)
+
+    _, poles, coeffs = sigma_poly_lanczos(wl, g, lo, hi, k=k, reorth=False)
+    E, Z = solve_all_qp(wl, poles)
+    alpha, beta, beta0, k_eff = coeffs
+    SC = np.zeros_like(wl.L)
+    SB = np.zeros_like(wl.L)
+    dDelta = np.zeros(wl.n_vc)
+    deps = np.zeros(wl.n_v + wl.n_c)
+    for ti, t in enumerate(wl.targets):
+        cw = dE[ti] * Z[ti]
+        deps[t] += cw
+        for mi, m in enumerate(wl.m_idx):
+            v = ti * wl.n_m + mi
+            ke = int(k_eff[v])
+            if ke == 0:
+                continue
+            eta = eta_all[mi]
+            z = E[ti] - wl.eps[m] - 1j * eta * wl.delta
+            Om, U = np.linalg.eigh(_tridiag(alpha[v], beta[v], ke))
+            u1 = U[0]
+            a = z + eta * Om
+            f = 1.0 / (Om * a)
+            Fd = -(z + eta * (Om[:, None] + Om[None, :])) / (
+                (Om[:, None] * Om[None, :]) * (a[:, None] * a[None, :]))
+            b0 = beta0[v]
+            Gam = cw * b0 ** 2 * (U @ (Fd * np.outer(u1, u1)).real @ U.T)
+            abar = np.diag(Gam).copy()
+            bbar = np.zeros(ke)
+            bbar[: ke - 1] = 2.0 * np.diag(Gam, 1)
+            bvec = d * V_all[ti, mi]
+            qbar0, ubar, Q, _ = lanczos_reverse(apply_D, bvec, k, abar, bbar, breakdown_tol)
+            q0 = Q[0]
+            y = 2.0 * cw * b0 * np.sum(u1 * u1 * f).real * q0 + (qbar0 - (qbar0 @ q0) * q0) / b0
+            Cbar = np.zeros((wl.n_vc, wl.n_vc))
+            for j in range(ke):
+                _, pairs = apply_poly_reverse(apply_C, ubar[j], Q[j], c, lo, hi)
+                for coef, pa, pb in pairs:
+                    Cbar += coef * np.outer(pa, pb)
+            G = 0.5 * (Cbar + Cbar.T)
+            deps[m] -= cw * (b0 ** 2 * np.sum(u1 * u1 * (-1.0 / (Om * a ** 2)))).real
+            SC += G @ (d[:, None] * wl.L)
+            SB += np.outer(d * y, wl.M[ti, mi])
+            dDelta += 2.0 * Delta * np.diag(G) + y * V_all[ti, mi] / (2.0 * d)
+    dL = 2.0 * wl.kernel_factor * d[:, None] * SC + SB
+    dDelta += wl.kernel_factor * np.sum(wl.L * SC, axis=1) / d
+    dD = dDelta.reshape(wl.n_v, wl.n_c)
+    deps[wl.n_v:] += dD.sum(axis=0)
+    deps[: wl.n_v] -= dD.sum(axis=1)
+    return dL, deps
 
 
 # --------------------------------------------------------------------------

@@ -12,6 +12,10 @@ recurrence) and for its Tamm-Dancoff closed-form gradient.
     truncated k where the Krylov form of the gradient is visibly off.
   * The Tamm-Dancoff closed-form gradient against central differences of the
     Tamm-Dancoff closed-form QP energies.
+  * Polynomial form (Lanczos on D = p_g(C)): the reverse Clenshaw recurrence
+    gives p(C)^T u and the directional derivative of u . p(C) x (central
+    differences on a dense matrix), and the whole k-step gradient matches
+    central differences of the oracle's polynomial-form QP energies.
 """
 import numpy as np
 import pytest
@@ -153,3 +157,69 @@ def test_tda_recurrence_gradient_approaches_closed_form():
     dL, deps = O.qp_gradient_tda_closed_form(wl, dE)
     np.testing.assert_allclose(dLr, dL, rtol=0, atol=1e-6 * np.abs(dL).max())
     np.testing.assert_allclose(depsr, deps, rtol=0, atol=1e-6 * np.abs(deps).max())
+
+
+# --------------------------------------------------------------------------
+# Polynomial form: Lanczos on D = p_g(C) without reorthogonalisation
+# --------------------------------------------------------------------------
+def _interval(wl):
+    th = np.linalg.eigvalsh(O.casida_matrix(wl.eps, wl.n_v, wl.L, wl.kernel_factor))
+    return 0.9 * th.min(), 1.1 * th.max()
+
+
+@pytest.mark.parametrize("g", [1, 2, 5, 8])
+def test_poly_reverse_gives_transpose_product_and_directional_derivative(g):
+    """xbar = p(C) u (C symmetric); the pairs' contraction with a symmetric
+    direction E equals central differences of u . p(C + hE) x."""
+    n = 10
+    C = _spd(n, 300 + g) * 3.0
+    rng = np.random.default_rng(400 + g)
+    u, x = rng.normal(size=n), rng.normal(size=n)
+    lo, hi = 2.5, 13.0
+    c = O.chebyshev_sqrt(lo, hi, g)
+
+    def op(M):
+        return lambda X: X @ M.T
+
+    xbar, pairs = O.apply_poly_reverse(op(C), u, x, c, lo, hi)
+    np.testing.assert_allclose(xbar, O.apply_poly(op(C), u[None, :], c, lo, hi)[0],
+                               rtol=0, atol=1e-12 * np.abs(xbar).max())
+    E = rng.normal(size=(n, n))
+    E = E + E.T
+    ana = sum(coef * (pa @ E @ pb) for coef, pa, pb in pairs)
+    h = 1e-5
+    fp = u @ O.apply_poly(op(C + h * E), x[None, :], c, lo, hi)[0]
+    fm = u @ O.apply_poly(op(C - h * E), x[None, :], c, lo, hi)[0]
+    assert ana == pytest.approx((fp - fm) / (2 * h), rel=1e-7, abs=1e-10)
+
+
+def _Ek_poly(w, g, lo, hi, k):
+    _, poles, _ = O.sigma_poly_lanczos(w, g, lo, hi, k=k, reorth=False)
+    return O.solve_all_qp(w, poles)[0]
+
+
+@pytest.mark.parametrize("g,k", [(4, 4), (8, 8), (8, 14)])
+def test_poly_recurrence_gradient_matches_central_differences(g, k):
+    wl = _wl()
+    lo, hi = _interval(wl)
+    rng = np.random.default_rng(80 + g + k)
+    dE = rng.normal(size=wl.n_t)
+    dL, deps = O.qp_gradient_poly_recurrence(wl, dE, g, lo, hi, k=k)
+    h = 1e-6
+    for trial in range(2):
+        PL = rng.normal(size=wl.L.shape)
+        Pe = rng.normal(size=wl.eps.shape) * 0.1
+        for which in ("L", "eps"):
+            wp = gi.Workload(**wl.__dict__)
+            wm = gi.Workload(**wl.__dict__)
+            if which == "L":
+                wp.L = wl.L + h * PL
+                wm.L = wl.L - h * PL
+                ana = np.sum(dL * PL)
+            else:
+                wp.eps = wl.eps + h * Pe
+                wm.eps = wl.eps - h * Pe
+                ana = np.sum(deps * Pe)
+            # the interval [lo, hi] is a fixed input of the polynomial form
+            fd = (dE @ _Ek_poly(wp, g, lo, hi, k) - dE @ _Ek_poly(wm, g, lo, hi, k)) / (2 * h)
+            assert ana == pytest.approx(fd, rel=1e-6, abs=1e-9), (which, trial)
