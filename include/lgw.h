@@ -528,6 +528,19 @@ lgw_status lgw_sigma_c_tda_backward(lgw_handle *h, const lgw_system *s, const lg
                                     const lgw_options *o, const double *dE, double *dL,
                                     double *deps);
 
+/* The same gradient for the polynomial form of lgw_sigma_c_poly (Lanczos on
+ * D = p_g(C), the fit of sqrt after Eq. 12; fractions on D's tridiagonal,
+ * Eq. 14).  Exact form only: o->precision LGW_FP64 and o->reorth
+ * LGW_REORTH_NONE (otherwise LGW_ERR_UNSUPPORTED).  Each step is taken back
+ * through the reverse of Clenshaw's recurrence, so a step costs 3 g
+ * products with C besides the forward's g.  The interval [x_lo, x_hi] is a
+ * fixed input: with x_lo = x_hi = 0 the library's own estimate (as in
+ * lgw_sigma_c_poly) is used and its dependence on L and eps is not part of
+ * the gradient. */
+lgw_status lgw_sigma_c_poly_backward(lgw_handle *h, const lgw_system *s, const lgw_problem *p,
+                                     const lgw_options *o, const lgw_poly *poly,
+                                     const double *dE, double *dL, double *deps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -167,6 +167,16 @@ __global__ void __launch_bounds__(COEF_THREADS) k_adj_coeffs(AdjCtx a) {
   for (int s = tid; s < n; s += COEF_THREADS) {
     const double u = V[(size_t)s * k];
     u1[s] = u;
+    if (a.poly) {
+      // nodes of D = p_g(C) ~ C^1/2 directly: f = 1/(Om (z + eta Om)), Om = theta
+      const double om = th[s];
+      Om[s] = om;
+      const double ar = zr + eta * om;
+      fu[s] = ar / (om * (ar * ar + zi * zi)) * u;
+      const double sr = ar * ar - zi * zi, si = 2.0 * ar * zi;
+      dzp += -(u * u / om) * (sr / (sr * sr + si * si));
+      continue;
+    }
     if (a.tda) {
       // f = 1/(z + eta theta):  a = z + eta theta;  Re f = Re 1/a;  dF/dz term -u^2 / a^2
       const double t = th[s];
@@ -207,8 +217,10 @@ __global__ void __launch_bounds__(COEF_THREADS) k_adj_coeffs(AdjCtx a) {
       // f[theta_s, theta_t] = -eta / (a_s a_t)
       Fr = -eta * pr / (pr * pr + pi * pi);
     } else {
+      // g[Om_s, Om_t] = -(z + eta (Om_s + Om_t)) / (Om_s Om_t a_s a_t); divided by
+      // (Om_s + Om_t) for the nodes theta = Om^2 of C (not for D's own nodes)
       const double nr = -(zr + eta * (Om[s] + Om[t])), ni = -zi;
-      const double scale = Om[s] * Om[t] * (Om[s] + Om[t]);
+      const double scale = Om[s] * Om[t] * (a.poly ? 1.0 : (Om[s] + Om[t]));
       Fr = (nr * pr + ni * pi) / ((pr * pr + pi * pi) * scale);
     }
     Phi[(size_t)s * k + t] = Fr * u1[s] * u1[t];
@@ -360,7 +372,8 @@ __global__ void k_gamma_p(AdjCtx a, const double *P, int A, double *R) {
 // S[i][mu] += sum_r X[r][i] Yr[r][mu]  (FP64, 64 x 64 tiles, r = contraction)
 __global__ void __launch_bounds__(256) k_atb_f64(const double *__restrict__ X, int ldx,
                                                  const double *__restrict__ Yr, int ldy, int R,
-                                                 int Ni, int Nmu, double *__restrict__ S) {
+                                                 int Ni, int Nmu, double *__restrict__ S,
+                                                 double scale) {
   __shared__ double Xs[16][65];
   __shared__ double Ys[16][65];
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
@@ -401,7 +414,7 @@ __global__ void __launch_bounds__(256) k_atb_f64(const double *__restrict__ X, i
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int mu = mu0 + tx + 16 * q;
-      if (mu < Nmu) S[(size_t)i * Nmu + mu] += acc[p][q];
+      if (mu < Nmu) S[(size_t)i * Nmu + mu] = fma(scale, acc[p][q], S[(size_t)i * Nmu + mu]);
     }
   }
 }
@@ -695,6 +708,35 @@ __global__ void __launch_bounds__(VEC_THREADS) k_rev_final(RevCtx r, const doubl
   }
 }
 
+// out = a x + b out (b = 0: out is not read), over [Bs][N]
+__global__ void k_rev_axpby(double *out, double a, const double *__restrict__ x, double b,
+                            size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (b == 0.0) ? a * x[i] : fma(a, x[i], b * out[i]);
+}
+
+// Gd += coef x o y over [Bs][N]
+__global__ void k_rev_gd(double *Gd, double coef, const double *__restrict__ x,
+                         const double *__restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    Gd[i] = fma(coef * x[i], y[i], Gd[i]);
+}
+
+static unsigned flat_blocks(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (unsigned)(b > (size_t)152 * 16 ? (size_t)152 * 16 : b);
+}
+void launch_rev_axpby(double *out, double a, const double *x, double b, size_t n,
+                      cudaStream_t st) {
+  k_rev_axpby<<<flat_blocks(n), 256, 0, st>>>(out, a, x, b, n);
+}
+void launch_rev_gd(double *Gd, double coef, const double *x, const double *y, size_t n,
+                   cudaStream_t st) {
+  k_rev_gd<<<flat_blocks(n), 256, 0, st>>>(Gd, coef, x, y, n);
+}
+
 void launch_rev_init(const RevCtx &r, cudaStream_t st) {
   k_rev_init<<<r.Bs, 128, 0, st>>>(r);
 }
@@ -770,9 +812,9 @@ void launch_gamma_p(const AdjCtx &a, const double *P, int A, double *R, cudaStre
   k_gamma_p<<<grid, 128, 0, st>>>(a, P, A, R);
 }
 void launch_atb_f64(const double *X, int ldx, const double *Yr, int ldy, int R, int Ni, int Nmu,
-                    double *S, cudaStream_t st) {
+                    double *S, cudaStream_t st, double scale) {
   dim3 grid((Nmu + 63) / 64, (Ni + 63) / 64);
-  k_atb_f64<<<grid, 256, 0, st>>>(X, ldx, Yr, ldy, R, Ni, Nmu, S);
+  k_atb_f64<<<grid, 256, 0, st>>>(X, ldx, Yr, ldy, R, Ni, Nmu, S, scale);
 }
 void launch_adj_accumulate(const AdjCtx &a, const double *Delta, BasisRef basis,
                            const double *Y, const double *Gd, double *dDelta, double *deps,

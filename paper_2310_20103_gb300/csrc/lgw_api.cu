@@ -1415,9 +1415,17 @@ lgw_status sigma_c_impl(lgw_handle *h, const lgw_system *sys, const lgw_problem 
 // elementwise pass, and C ubar_j through the FP64 contractions).  SC
 // accumulates sum_j (ubar_j (L^T D q_j)^T + q_j (L^T D ubar_j)^T) = 2 G D L;
 // then y = dF/db, SB += y M^T and the diagonal terms of dDelta.
+//
+// Polynomial form (poly != NULL: the recurrence runs on D = p_g(C)): each
+// product D x is Clenshaw's recurrence in S = a_s C + b_s I (g products with
+// C).  Taking step j back needs D ubar_j and the pairs through which dF/dD
+// reaches C: Clenshaw on q_j is redone (b_1..b_g and their L^T D b_k), then
+// the reverse recurrence bbar_1 = S u, bbar_k = 2 S bbar_{k-1} - bbar_{k-2}
+// (u = bbar_0 = ubar_j) gives D u = c_0 u + sum_k c_k bbar_k and
+//   dF/dC += a_s u b_1^T + 2 a_s sum_{k=1}^{g-1} bbar_k b_{k+1}^T.
 void reverse_sweep(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts &op,
                    const VecCtx &c, const AdjCtx &a, const double *ckpt, int ci, double *SC,
-                   double *SB, double *dD, double *gdeps) {
+                   double *SB, double *dD, double *gdeps, const PolyOp *poly) {
   cudaStream_t &st = h->stream;
   const int Bs = c.Bs, N = c.N, A = s.A, k = op.k;
   const size_t BN = (size_t)Bs * N, BA = (size_t)Bs * A;
@@ -1456,6 +1464,64 @@ void reverse_sweep(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opt
   LGW_TRY_CUDA(h, cudaMemsetAsync(r.Gd, 0, sizeof(double) * BN, st));
   launch_rev_init(r, st);
   check_launch(h, "rev_init");
+  // polynomial form: Clenshaw vectors b_k (slot k - 1), their L^T D b_k, the
+  // reverse vectors bbar_1..bbar_g (slot k - 1) and L^T D bbar_{k-1}
+  const int g = poly ? poly->g : 0;
+  double *fb = nullptr, *fy = nullptr, *rb = nullptr, *ry = nullptr, *T = nullptr,
+         *apart = nullptr, *zeros = nullptr;
+  if (poly) {
+    fb = wsT<double>(h, "rev_fb", (size_t)g * BN);
+    fy = wsT<double>(h, "rev_fy", (size_t)g * BA);
+    rb = wsT<double>(h, "rev_rb", (size_t)g * BN);
+    ry = wsT<double>(h, "rev_ry", (size_t)g * BA);
+    T = wsT<double>(h, "rev_T", BN);
+    apart = wsT<double>(h, "rev_apart", (size_t)c.nchunks * Bs);
+    zeros = wsT<double>(h, "rev_zeros", (size_t)Bs);
+    LGW_TRY_CUDA(h, cudaMemsetAsync(zeros, 0, sizeof(double) * Bs, st));
+  }
+  // T = C x with L^T D x into yout (FP64 contractions)
+  auto apply_c = [&](const double *x, double *yout) {
+    launch_gemm1_f64(s, x, Bs, yp, sp, st);
+    check_launch(h, "gemm1_f64(reverse)");
+    launch_reduce_y_f64(yp, sp, Bs, A, yout, st);
+    check_launch(h, "reduce_y_f64(reverse)");
+    launch_gemm2_f64(s, yout, Bs, EPI_APPLY, x, nullptr, nullptr, T, nullptr, st);
+    check_launch(h, "gemm2_f64(reverse)");
+  };
+  auto fbk = [&](int k) { return fb + (size_t)(k - 1) * BN; };
+  auto rbk = [&](int k) { return rb + (size_t)(k - 1) * BN; };
+  // Clenshaw on x: b_g .. b_1 into fb and L^T D b_k into fy; with w given,
+  // also the Lanczos step's w = D x - beta_j q_{j-1} and its alpha partials
+  auto clenshaw = [&](const double *x, const double *qprev, const double *betaj, double *w,
+                      double *alpha_part) {
+    PolyStep ps{};
+    ps.N = N;
+    ps.q = x;
+    ps.Delta2 = s.Delta2;
+    ps.dsqf = s.dsqf;
+    ps.as = poly->as;
+    ps.bs = poly->bs;
+    ps.ck = poly->c[g];
+    ps.out = fbk(g);
+    launch_cheb_step(ps, c.nchunks, Bs, st);
+    check_launch(h, "cheb_step(reverse)");
+    for (int kk = g - 1; kk >= 0; --kk) {
+      apply_c(fbk(kk + 1), fy + (size_t)kk * BA);
+      ps.b1 = fbk(kk + 1);
+      ps.b2 = kk + 2 <= g ? fbk(kk + 2) : nullptr;
+      ps.T = T;
+      ps.ck = poly->c[kk];
+      if (kk > 0) {
+        ps.out = fbk(kk);
+        launch_cheb_step(ps, c.nchunks, Bs, st);
+        check_launch(h, "cheb_step(reverse)");
+      } else if (w) {
+        ps.out = nullptr;
+        launch_cheb_final(ps, qprev, betaj, w, alpha_part, c.nchunks, Bs, st);
+        check_launch(h, "cheb_final(reverse)");
+      }
+    }
+  };
   // the recomputation window: q_j at slot j - (s0 - 1) of seg
   VecCtx rc = c;
   rc.ring = 0;
@@ -1473,13 +1539,17 @@ void reverse_sweep(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opt
     for (int j = s0; j < e; ++j) {
       const double *qj = slot_ptr(rc, j);
       const double *qp = j > 0 ? slot_ptr(rc, j - 1) : nullptr;
-      double *yj = yseg + (size_t)(j - s0) * BA;
-      launch_gemm1_f64(s, qj, Bs, yp, sp, st);
-      check_launch(h, "gemm1_f64(recompute)");
-      launch_reduce_y_f64(yp, sp, Bs, A, yj, st);
-      check_launch(h, "reduce_y_f64(recompute)");
-      launch_gemm2_f64(s, yj, Bs, EPI_LANCZOS, qj, qp, rc.betaj, rc.w, rc.alpha_part, st);
-      check_launch(h, "gemm2_f64(recompute)");
+      if (poly) {
+        clenshaw(qj, qp, rc.betaj, rc.w, rc.alpha_part);
+      } else {
+        double *yj = yseg + (size_t)(j - s0) * BA;
+        launch_gemm1_f64(s, qj, Bs, yp, sp, st);
+        check_launch(h, "gemm1_f64(recompute)");
+        launch_reduce_y_f64(yp, sp, Bs, A, yj, st);
+        check_launch(h, "reduce_y_f64(recompute)");
+        launch_gemm2_f64(s, yj, Bs, EPI_LANCZOS, qj, qp, rc.betaj, rc.w, rc.alpha_part, st);
+        check_launch(h, "gemm2_f64(recompute)");
+      }
       launch_alpha_reduce(rc, j, st);
       check_launch(h, "alpha_reduce(recompute)");
       launch_alpha_axpy(rc, j, st);
@@ -1493,14 +1563,57 @@ void reverse_sweep(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opt
       launch_rev_step(r, j, st);
       check_launch(h, "rev_step");
       const double *uj = useg + (size_t)(j - s0) * BN;
-      double *ybj = ybseg + (size_t)(j - s0) * BA;
-      launch_gemm1_f64(s, uj, Bs, yp, sp, st);
-      check_launch(h, "gemm1_f64(reverse)");
-      launch_reduce_y_f64(yp, sp, Bs, A, ybj, st);
-      check_launch(h, "reduce_y_f64(reverse)");
-      launch_gemm2_f64(s, ybj, Bs, EPI_APPLY, uj, nullptr, nullptr, cu, nullptr, st);
-      check_launch(h, "gemm2_f64(reverse)");
+      if (!poly) {
+        double *ybj = ybseg + (size_t)(j - s0) * BA;
+        launch_gemm1_f64(s, uj, Bs, yp, sp, st);
+        check_launch(h, "gemm1_f64(reverse)");
+        launch_reduce_y_f64(yp, sp, Bs, A, ybj, st);
+        check_launch(h, "reduce_y_f64(reverse)");
+        launch_gemm2_f64(s, ybj, Bs, EPI_APPLY, uj, nullptr, nullptr, cu, nullptr, st);
+        check_launch(h, "gemm2_f64(reverse)");
+        continue;
+      }
+      // Clenshaw vectors of q_j, then the reverse recurrence from u = ubar_j
+      clenshaw(slot_ptr(rc, j), nullptr, nullptr, nullptr, nullptr);
+      PolyStep ps{};
+      ps.N = N;
+      ps.q = uj;
+      ps.Delta2 = s.Delta2;
+      ps.dsqf = s.dsqf;
+      ps.as = poly->as;
+      ps.bs = poly->bs;
+      ps.ck = 0.0;
+      apply_c(uj, ry);
+      ps.b1 = uj;
+      ps.T = T;
+      launch_cheb_final(ps, nullptr, zeros, rbk(1), apart, c.nchunks, Bs, st);   // S u
+      check_launch(h, "cheb_final(reverse S u)");
+      for (int kk = 2; kk <= g; ++kk) {
+        apply_c(rbk(kk - 1), ry + (size_t)(kk - 1) * BA);
+        ps.b1 = rbk(kk - 1);
+        ps.b2 = kk == 2 ? uj : rbk(kk - 2);
+        ps.out = rbk(kk);
+        launch_cheb_step(ps, c.nchunks, Bs, st);
+        check_launch(h, "cheb_step(reverse)");
+      }
+      // D u for qbar_j (added by the next step's first pass)
+      launch_rev_axpby(cu, poly->c[0], uj, 0.0, BN, st);
+      for (int kk = 1; kk <= g; ++kk) launch_rev_axpby(cu, poly->c[kk], rbk(kk), 1.0, BN, st);
+      check_launch(h, "rev_axpby");
+      // pairs (a_s: u, b_1) and (2 a_s: bbar_k, b_{k+1}), k = 1 .. g-1
+      const double as = poly->as;
+      launch_rev_gd(r.Gd, as, uj, fbk(1), BN, st);
+      for (int kk = 1; kk < g; ++kk) launch_rev_gd(r.Gd, 2.0 * as, rbk(kk), fbk(kk + 1), BN, st);
+      check_launch(h, "rev_gd");
+      launch_atb_f64(uj, N, fy, A, Bs, N, A, SC, st, as);
+      launch_atb_f64(fbk(1), N, ry, A, Bs, N, A, SC, st, as);
+      if (g > 1) {
+        launch_atb_f64(rbk(1), N, fy + BA, A, (g - 1) * Bs, N, A, SC, st, 2.0 * as);
+        launch_atb_f64(fbk(2), N, ry + BA, A, (g - 1) * Bs, N, A, SC, st, 2.0 * as);
+      }
+      check_launch(h, "atb_f64(SC, poly pairs)");
     }
+    if (poly) continue;
     launch_atb_f64(useg, N, yseg, A, n * Bs, N, A, SC, st);
     check_launch(h, "atb_f64(SC, ubar)");
     launch_atb_f64(seg + BN, N, ybseg, A, n * Bs, N, A, SC, st);
@@ -2295,7 +2408,7 @@ lgw_status lgw_sigma_c_batched(lgw_handle *h, int32_t n_sys, const lgw_system *c
 
 static lgw_status backward_impl(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
                                 const lgw_options *o, const double *dE, double *dL,
-                                double *deps, bool tda) {
+                                double *deps, bool tda, const lgw_poly *pp = nullptr) {
   lgw_status g = guard_handle(h);
   if (g != LGW_OK) return g;
   if (!sys || sys->h != h || !dE) return set_err(h, LGW_ERR_ARG, "NULL argument to the backward call");
@@ -2318,6 +2431,19 @@ static lgw_status backward_impl(lgw_handle *h, const lgw_system *sys, const lgw_
     if (o->ckpt_every < 0) {
       set_err(h, LGW_ERR_ARG, "ckpt_every < 0");
       throw Fail{LGW_ERR_ARG};
+    }
+    // the polynomial form is differentiated exactly only (the Krylov form
+    // would need the eigenvectors of C behind p_g); its interval is held fixed
+    PolyOp pstore;
+    const PolyOp *poly = poly_arg(h, sys, pp, pstore);
+    if (poly && !exact) {
+      set_err(h, LGW_ERR_UNSUPPORTED,
+              "the polynomial form's adjoint needs FP64 contractions without reorthogonalisation");
+      throw Fail{LGW_ERR_UNSUPPORTED};
+    }
+    if (poly) {
+      op.split = 0;
+      op.split32 = 0;
     }
     // the adjoint contracts with the stored Krylov basis: FP64 (FP64 mode)
     // or the split float pair (BF16 mode with split arithmetic); the split
@@ -2408,7 +2534,7 @@ static lgw_status backward_impl(lgw_handle *h, const lgw_system *sys, const lgw_
 
     auto forward_sigma = [&]() {
       run_sigma(h, s, pv, op, alpha, beta, beta0, ke, nullptr, E, Z, nullptr, nullptr,
-                tda ? 2 : 0);
+                poly ? 1 : (tda ? 2 : 0));
     };
     // Krylov checkpoints of the exact mode: (q_{s0-1}, q_s0) at every segment
     // start s0 = 0, ci, 2 ci, ... (q_{-1} = 0), copied out of the forward's
@@ -2466,12 +2592,13 @@ static lgw_status backward_impl(lgw_handle *h, const lgw_system *sys, const lgw_
       a.dz = wsT<double>(h, "adj_dz", (size_t)Bs);
       a.status = h->d_status;
       a.tda = tda ? 1 : 0;
+      a.poly = poly ? 1 : 0;
       launch_eig_full(a, st);
       check_launch(h, "eig_full");
       launch_adj_coeffs(a, st);
       check_launch(h, "adj_coeffs");
       if (exact) {
-        reverse_sweep(h, s, pv, op, c, a, ckpt, ci, SC, SB, dD, gdeps);
+        reverse_sweep(h, s, pv, op, c, a, ckpt, ci, SC, SB, dD, gdeps, poly);
         return;
       }
       double *Y = wsT<double>(h, "adj_Y", (size_t)Bs * N);
@@ -2546,12 +2673,12 @@ static lgw_status backward_impl(lgw_handle *h, const lgw_system *sys, const lgw_
     const bool keep = !exact;
     const StepHook *sh = exact ? &keep_ckpt : nullptr;
     if (one_pass) {
-      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, keep, &adjoint, nullptr,
+      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, keep, &adjoint, poly,
                   sh);
     } else {
-      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, false, nullptr);
+      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, false, nullptr, poly);
       forward_sigma();
-      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, keep, &adjoint, nullptr,
+      run_lanczos(h, s, pv, op, alpha, beta, beta0, ke, nullptr, nullptr, keep, &adjoint, poly,
                   sh);
     }
     double *dLdev = oL.dev ? oL.dev : wsT<double>(h, "adj_dL", (size_t)s.n_vc * s.n_aux);
@@ -2583,6 +2710,13 @@ lgw_status lgw_sigma_c_tda_backward(lgw_handle *h, const lgw_system *sys, const 
                                     const lgw_options *o, const double *dE, double *dL,
                                     double *deps) {
   return backward_impl(h, sys, p, o, dE, dL, deps, true);
+}
+
+lgw_status lgw_sigma_c_poly_backward(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,
+                                     const lgw_options *o, const lgw_poly *poly, const double *dE,
+                                     double *dL, double *deps) {
+  if (!poly) return set_err(h, LGW_ERR_ARG, "NULL polynomial to lgw_sigma_c_poly_backward");
+  return backward_impl(h, sys, p, o, dE, dL, deps, false, poly);
 }
 
 lgw_status lgw_sigma_x(lgw_handle *h, const lgw_system *sys, const lgw_problem *p,

@@ -433,6 +433,9 @@ struct AdjCtx {
   // b = L M (the nodes are theta, not Omega = sqrt(theta); A is linear in
   // Delta and b does not depend on it)
   int tda;
+  // polynomial form: the nodes of D = p_g(C)'s tridiagonal are Omega
+  // directly, f(Omega) = 1 / (Omega (z + eta Omega))
+  int poly;
 };
 // Reverse mode of the three-term recurrence (no reorthogonalisation) over
 // one segment of steps [s0, e) of a sub-batch, the steps taken back from
@@ -457,6 +460,10 @@ void launch_rev_init(const RevCtx &r, cudaStream_t st);
 void launch_rev_set_betaj(const RevCtx &r, double *betaj, cudaStream_t st);
 void launch_rev_step(const RevCtx &r, int j, cudaStream_t st);
 void launch_rev_finish(const RevCtx &r, const double *q0, double *Y, cudaStream_t st);
+void launch_rev_axpby(double *out, double a, const double *x, double b, size_t n,
+                      cudaStream_t st);
+void launch_rev_gd(double *Gd, double coef, const double *x, const double *y, size_t n,
+                   cudaStream_t st);
 int adj_max_k();
 bool tc_gemm_f64out(int np, const __nv_bfloat16 *const *A, const int *a_kblk,
                     const __nv_bfloat16 *const *B, int M, int Ncols, int K, int kchunk,
@@ -472,8 +479,9 @@ void launch_eig_full(const AdjCtx &a, cudaStream_t st);
 void launch_adj_coeffs(const AdjCtx &a, cudaStream_t st);
 void launch_adj_rows(const AdjCtx &a, BasisRef basis, double *Y, double *Gd, cudaStream_t st);
 void launch_gamma_p(const AdjCtx &a, const double *P, int A, double *R, cudaStream_t st);
+// S[i][mu] += scale * sum_r X[r][i] Yr[r][mu]
 void launch_atb_f64(const double *X, int ldx, const double *Yr, int ldy, int R, int Ni, int Nmu,
-                    double *S, cudaStream_t st);
+                    double *S, cudaStream_t st, double scale = 1.0);
 void launch_adj_accumulate(const AdjCtx &a, const double *Delta, BasisRef basis,
                            const double *Y, const double *Gd, double *dDelta, double *deps,
                            cudaStream_t st);

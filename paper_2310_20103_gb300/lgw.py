@@ -112,6 +112,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                   ctypes.POINTER(lgw_options), P, P, P], I),
         "lgw_sigma_c_tda_backward": ([P, P, ctypes.POINTER(lgw_problem),
                                       ctypes.POINTER(lgw_options), P, P, P], I),
+        "lgw_sigma_c_poly_backward": ([P, P, ctypes.POINTER(lgw_problem),
+                                       ctypes.POINTER(lgw_options), ctypes.POINTER(lgw_poly),
+                                       P, P, P], I),
         "lgw_sigma_x": ([P, P, ctypes.POINTER(lgw_problem), P], I),
         "lgw_sigma_c_tda": ([P, P, ctypes.POINTER(lgw_problem), ctypes.POINTER(lgw_options),
                              P, P, P, ctypes.POINTER(lgw_report)], I),
@@ -472,6 +475,15 @@ def lgw_sigma_c_tda_backward(h: Handle, s: System, problem: Problem, options: Op
     _check(h, load_library().lgw_sigma_c_tda_backward(
         h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), _ptr(dE, "f64"), _ptr(dL, "f64"),
         _ptr(deps, "f64")))
+
+
+def lgw_sigma_c_poly_backward(h: Handle, s: System, problem: Problem, options: Options, g: int,
+                              x_lo: float, x_hi: float, dE, dL=None, deps=None) -> None:
+    p, o = problem.to_c(), options.to_c()
+    pl = lgw_poly(int(g), float(x_lo), float(x_hi))
+    _check(h, load_library().lgw_sigma_c_poly_backward(
+        h.ptr, s.ptr, ctypes.byref(p), ctypes.byref(o), ctypes.byref(pl), _ptr(dE, "f64"),
+        _ptr(dL, "f64"), _ptr(deps, "f64")))
 
 
 def lgw_sigma_from_coeffs_noalloc(h: Handle, s: System, problem: Problem, options: Options,

@@ -13,6 +13,9 @@ derivative of the k-step QP energies at any k:
     N_aux 1024), where the Krylov form of the gradient is far off;
   * Tamm-Dancoff: the exact form against the oracle's reverse mode, and the
     Krylov form at k = N_vc against the closed-form Tamm-Dancoff gradient;
+  * the polynomial form (Lanczos on D = p_g(C), reverse Clenshaw recurrence)
+    against the oracle's reverse mode and against central differences of
+    the GPU's polynomial-form energies at the differentiation shapes;
   * through torch.autograd with tda=True.
 """
 import numpy as np
@@ -211,3 +214,90 @@ def test_autograd_tda_exact(L, handle):
     dL, de = _grad(L, handle, wl, w.cpu().numpy(), opts, tda=True)
     np.testing.assert_array_equal(Lt.grad.cpu().numpy(), dL)
     np.testing.assert_array_equal(et.grad.cpu().numpy(), de)
+
+
+# --------------------------------------------------------------------------
+# Polynomial form
+# --------------------------------------------------------------------------
+def _interval(wl):
+    th = np.linalg.eigvalsh(O.casida_matrix(wl.eps, wl.n_v, wl.L, wl.kernel_factor))
+    return 0.9 * th.min(), 1.1 * th.max()
+
+
+def _poly_grad(L, h, wl, dE, opts, g, lo, hi):
+    s = _system(L, h, wl)
+    try:
+        dL = torch.empty(wl.n_vc, wl.n_aux, dtype=torch.float64, device=DEV)
+        de = torch.empty(wl.n_v + wl.n_c, dtype=torch.float64, device=DEV)
+        L.lgw_sigma_c_poly_backward(h, s, _problem(L, wl), opts, g, lo, hi, _t(dE), dL, de)
+        torch.cuda.synchronize()
+    finally:
+        L.lgw_release_system(s)
+    return dL.cpu().numpy(), de.cpu().numpy()
+
+
+def _poly_energies(L, h, wl, opts, g, lo, hi):
+    s = _system(L, h, wl)
+    try:
+        sig = torch.empty(wl.n_t, wl.omega.size, 2, dtype=torch.float64, device=DEV)
+        e = torch.empty(wl.n_t, dtype=torch.float64, device=DEV)
+        L.lgw_sigma_c_poly(h, s, _problem(L, wl), opts, g, lo, hi, sig, e)
+        torch.cuda.synchronize()
+    finally:
+        L.lgw_release_system(s)
+    return e.cpu().numpy()
+
+
+@pytest.mark.parametrize("g,k,ckpt", [(1, 4, 0), (4, 8, 0), (8, 16, 5)])
+def test_poly_exact_reverse_vs_oracle(L, handle, g, k, ckpt):
+    wl = gi.tiny(k=k)
+    lo, hi = _interval(wl)
+    dE = np.random.default_rng(90 + g + k).normal(size=wl.n_t)
+    dLr, der = O.qp_gradient_poly_recurrence(wl, dE, g, lo, hi, k=k)
+    dL, de = _poly_grad(L, handle, wl, dE, _exact(k, ckpt), g, lo, hi)
+    _close(dL, dLr, 1e-9)
+    _close(de, der, 1e-9)
+
+
+def test_poly_central_differences_differentiation_shapes(L, handle):
+    """The paper's depths (g 8, k 8) at N_vc 32768, N_aux 1024: directional
+    derivatives vs central differences (h = 1e-6) of the GPU's FP64
+    polynomial-form energies on a fixed interval, 1e-6 relative."""
+    wl = gi.make_workload("diff", 64, 512, 1024, [62, 64], [0, 30, 63, 64], 200, 4,
+                          k=8, aux_scaled=True)
+    s = _system(L, handle, wl)
+    try:
+        lo, hi = L.lgw_spectral_interval(handle, s, 32)
+    finally:
+        L.lgw_release_system(s)
+    rng = np.random.default_rng(95)
+    dE = rng.normal(size=wl.n_t)
+    opts = _exact(8)
+    opts.qp_tol = 1e-13
+    dL, de = _poly_grad(L, handle, wl, dE, opts, 8, lo, hi)
+    h = 1e-6
+    for trial in range(2):
+        PL = rng.normal(size=wl.L.shape)
+        Pe = rng.normal(size=wl.eps.shape)
+        for which in ("L", "eps"):
+            wp = gi.Workload(**wl.__dict__)
+            wm = gi.Workload(**wl.__dict__)
+            if which == "L":
+                wp.L, wm.L = wl.L + h * PL, wl.L - h * PL
+                ana = np.sum(dL * PL)
+            else:
+                wp.eps, wm.eps = wl.eps + h * Pe, wl.eps - h * Pe
+                ana = np.sum(de * Pe)
+            fd = (dE @ _poly_energies(L, handle, wp, opts, 8, lo, hi)
+                  - dE @ _poly_energies(L, handle, wm, opts, 8, lo, hi)) / (2 * h)
+            print(f"poly {which} trial {trial}: analytic {ana:.10e} fd {fd:.10e}")
+            assert ana == pytest.approx(fd, rel=1e-6), (which, trial)
+
+
+def test_poly_backward_needs_the_exact_form(L, handle):
+    wl = gi.tiny(k=8)
+    lo, hi = _interval(wl)
+    o = L.Options(k=8, precision="fp64", reorth="cgs2")
+    with pytest.raises(L.LgwError) as e:
+        _poly_grad(L, handle, wl, np.ones(wl.n_t), o, 4, lo, hi)
+    assert e.value.status == 8
