@@ -721,6 +721,7 @@ def adjoint_leg(L, h, dev, n_targets=8, compare=True):
            "forward_s": f16, "backward_s": b16, "backward_over_forward": b16 / f16}
     if not compare:
         return out
+    out["exact_short_k"] = _guarded(exact_adjoint_leg, L, h, dev)
     sub = gi.differentiation(n_targets=1, n_m=128)
     _, bs16, dl16, de16 = one(sub, "bf16", 1)
     f64, b64, dl64, de64 = one(sub, "fp64", 1)
@@ -730,6 +731,54 @@ def adjoint_leg(L, h, dev, n_targets=8, compare=True):
                 "deps_rel": float(np.abs(de16 - de64).max() / np.abs(de64).max()),
                 "fp64_forward_s": f64, "fp64_backward_s": b64, "bf16_backward_s": bs16}
     return out
+
+
+def exact_adjoint_leg(L, h, dev, n_m=128):
+    """Exact k-step adjoint (FP64, no reorthogonalisation, reverse mode with
+    Krylov checkpoints) at the paper's short depths on the differentiation
+    shapes, 1 target x n_m summed orbitals: the plain recurrence at k 8 and
+    the polynomial form at g 8, k 8 (interval from lgw_spectral_interval),
+    forward and backward seconds (best of 2)."""
+    import torch
+    import gw_inputs as gi
+
+    def tt(x):
+        return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+    wl = gi.differentiation(n_targets=1, n_m=n_m, k=8)
+    s = L.lgw_prepare_system(h, wl.n_v, wl.n_c, wl.n_aux, tt(wl.eps), tt(wl.L))
+    try:
+        prob = L.Problem(targets=tt(wl.targets), m_idx=tt(wl.m_idx), omega=tt(wl.omega),
+                         delta=wl.delta, M=tt(wl.M))
+        o = L.Options(k=8, precision="fp64", reorth="none")
+        lo, hi = L.lgw_spectral_interval(h, s, 32)
+        sg = torch.empty(wl.n_t, wl.omega.size, 2, dtype=torch.float64, device=dev)
+        e = torch.empty(wl.n_t, dtype=torch.float64, device=dev)
+        dL = torch.empty(wl.n_vc, wl.n_aux, dtype=torch.float64, device=dev)
+        de = torch.empty(wl.n_v + wl.n_c, dtype=torch.float64, device=dev)
+        dE = tt(np.ones(wl.n_t))
+
+        def timed(fn):
+            best = 1e30
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fn()
+                torch.cuda.synchronize()
+                best = min(best, time.perf_counter() - t0)
+            return best
+
+        out = {"workload": f"N_vc 32768, N_aux 1024, 1 target x {n_m} summed orbitals, k 8, "
+                           f"FP64, no reorthogonalisation, checkpoints every 16 steps"}
+        f = timed(lambda: L.lgw_sigma_c(h, s, prob, o, sg, e))
+        b = timed(lambda: L.lgw_sigma_c_backward(h, s, prob, o, dE, dL, de))
+        out["plain"] = {"forward_s": f, "backward_s": b, "backward_over_forward": b / f}
+        f = timed(lambda: L.lgw_sigma_c_poly(h, s, prob, o, 8, lo, hi, sg, e))
+        b = timed(lambda: L.lgw_sigma_c_poly_backward(h, s, prob, o, 8, lo, hi, dE, dL, de))
+        out["poly_g8"] = {"forward_s": f, "backward_s": b, "backward_over_forward": b / f}
+        return out
+    finally:
+        L.lgw_release_system(s)
 
 
 def batched_leg(L, h, dev, max_targets=64, k=150, reorth="dcgs", reps=1):
