@@ -638,10 +638,12 @@ __global__ void __launch_bounds__(VEC_THREADS) k_rev_elem(RevCtx r, int j) {
     *reinterpret_cast<double2 *>(qbj + e) = y;
     if (j > 0) *reinterpret_cast<double2 *>(qbm + e) = make_double2(mb * w.x, mb * w.y);
     *reinterpret_cast<double2 *>(ub + e) = w;
-    double2 g = *reinterpret_cast<const double2 *>(gd + e);
-    g.x = fma(w.x, p.x, g.x);
-    g.y = fma(w.y, p.y, g.y);
-    *reinterpret_cast<double2 *>(gd + e) = g;
+    if (r.gd_from_steps) {
+      double2 g = *reinterpret_cast<const double2 *>(gd + e);
+      g.x = fma(w.x, p.x, g.x);
+      g.y = fma(w.y, p.y, g.y);
+      *reinterpret_cast<double2 *>(gd + e) = g;
+    }
   }
 }
 

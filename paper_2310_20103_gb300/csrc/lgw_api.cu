@@ -1450,6 +1450,8 @@ void reverse_sweep(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opt
   r.cu = cu;
   r.useg = useg;
   r.Gd = wsT<double>(h, "adj_Gd", BN);
+  // on D = p_g(C) the pairs of the reverse Clenshaw recurrence give diag(dF/dC)
+  r.gd_from_steps = poly ? 0 : 1;
   r.dpart = wsT<double>(h, "rev_dpart", (size_t)Bs * c.nchunks * 6);
   r.coef = wsT<double>(h, "rev_coef", (size_t)Bs * 8);
   r.bbar = wsT<double>(h, "rev_bbar", (size_t)Bs * k);

@@ -447,7 +447,9 @@ struct RevCtx {
   double *qbar;           // [3] adjoints of q_j at slot j % 3
   const double *cu;       // C ubar_{j+1} of the step taken back before (0 at the start)
   double *useg;           // ubar_j at slot j - s0
-  double *Gd;             // [Bs][N] running sum_j ubar_j o q_j
+  double *Gd;             // [Bs][N] running diag(dF/dC): sum_j ubar_j o q_j when the
+                          // recurrence runs on C (gd_from_steps), else added by the caller
+  int gd_from_steps;
   double *dpart;          // [Bs][nchunks][6] dot-product partials
   double *coef;           // [Bs][8] per-vector coefficients of the running step
   double *bbar;           // [Bs][k] running adjoints of beta[j] (coupling of j, j+1)
