@@ -13,8 +13,8 @@
 // Rutishauser / Gragg-Harrod reconstruction, O(k^2), orthogonal, stable).
 //
 // One warp per start vector: the Gauss rule of T_k by parallel bisection and
-// the product formula for the weights, then the Jacobi rebuild; the work
-// rows live in shared memory.
+// the product formula for the weights, then the Jacobi rebuild (lane-
+// pipelined node insertions); the work rows live in shared memory.
 #include <algorithm>
 
 #include "lgw_internal.cuh"
@@ -47,51 +47,83 @@ __device__ __forceinline__ void givens(double x, double z, double &c, double &s,
   }
 }
 
-// Jacobi matrix (a[0..n), off-diagonal squares b2[0..n-1)) and total weight
-// of the discrete measure sum_j wt_j delta(x - x_j), n = number of nodes.
-// Node j is added as a new leading row with start-vector weight wt_j; one
-// rotation in plane (0,1) folds it into the start vector and the bulge it
-// leaves is chased to the bottom.  b holds the off-diagonal (not squared)
-// during the build.
-__device__ double jacobi_from_nodes(const double *x, const double *wt, int n, double *a, double *b) {
+// Jacobi matrix (a[0..n), off-diagonal b[0..n-1), not squared) and total
+// weight of the discrete measure sum_j wt_j delta(x - x_j), n = number of
+// nodes.  Node jn enters as a new leading row with start-vector weight wt_jn:
+// one rotation in plane (0, 1) folds it into the start vector, and the bulge
+// it leaves in b is chased to the bottom by rotations in planes (kk, kk+1).
+//
+// The insertions are pipelined over the warp: in each group of 32 nodes,
+// lane l inserts node g0 + l and chases its bulge two rows behind lane l-1.
+// Rows are stored bottom-up (with m rows present the leading row sits at
+// index n - m), so a new leading row shifts nothing.  A rotation in plane
+// (kk, kk+1) touches rows kk-1 .. kk+1, so the rotations of one super-step
+// are at least three rows apart, and each row that two insertions both
+// rotate is rotated by the earlier insertion first: every rotation sees the
+// operands it would see in the one-node-at-a-time order.  Wp (n doubles)
+// receives the running weights W_jn = sum_{i < jn} wt_i.  All 32 lanes call
+// this; the total weight is returned to every lane.
+__device__ double jacobi_from_nodes_warp(const double *x, const double *wt, int n, double *a,
+                                         double *b, double *Wp) {
+  const int lane = threadIdx.x & 31;
   if (n <= 0) return 0.0;
-  a[0] = x[0];
-  double W = wt[0];
-  int m = 1;
-  for (int jn = 1; jn < n; ++jn) {
-    for (int i = m; i >= 1; --i) a[i] = a[i - 1];
-    for (int i = m - 1; i >= 1; --i) b[i] = b[i - 1];
-    a[0] = x[jn];
-    b[0] = 0.0;
-    const double wj = wt[jn];
-    double c = 1.0, s = 0.0;
-    if (W + wj > 0.0) {
-      const double inv = rsqrt(W + wj);
-      c = sqrt(wj) * inv;
-      s = sqrt(W) * inv;
+  double Wtot = 0.0;
+  if (lane == 0) {
+    double W = 0.0;
+    for (int j = 0; j < n; ++j) {
+      Wp[j] = W;
+      W += wt[j];
     }
-    ++m;
-    rot_sym(c, s, a, b, 0);
-    double bulge = 0.0;
-    if (m > 2) {
-      bulge = s * b[1];
-      b[1] *= c;
-    }
-    for (int kk = 1; kk < m - 1 && bulge != 0.0; ++kk) {
-      double rr;
-      givens(b[kk - 1], bulge, c, s, rr);
-      b[kk - 1] = rr;
-      rot_sym(c, s, a, b, kk);
-      if (kk + 1 < m - 1) {
-        bulge = s * b[kk + 1];
-        b[kk + 1] *= c;
-      } else {
-        bulge = 0.0;
-      }
-    }
-    W += wj;
+    Wtot = W;
+    a[n - 1] = x[0];
   }
-  return W;
+  __syncwarp();
+  for (int g0 = 1; g0 < n; g0 += 32) {
+    const int nl = min(32, n - g0);
+    const bool act = lane < nl;
+    const int jn = g0 + lane;
+    const int L = n - 1 - jn;   // leading row once node jn is in
+    const int m = jn + 1;       // rows after the insertion
+    double bulge = 0.0;
+    bool live = false;
+    // lane l's last chase step (kk = m - 2) comes at super-step 2 l + m - 2
+    const int steps = 3 * (nl - 1) + g0;
+    for (int tau = 0; tau < steps; ++tau) {
+      const int kk = tau - 2 * lane;
+      if (act && kk == 0) {
+        a[L] = x[jn];
+        b[L] = 0.0;
+        const double wj = wt[jn], W = Wp[jn];
+        double c = 1.0, s = 0.0;
+        if (W + wj > 0.0) {
+          const double inv = rsqrt(W + wj);
+          c = sqrt(wj) * inv;
+          s = sqrt(W) * inv;
+        }
+        rot_sym(c, s, a, b, L);
+        bulge = 0.0;
+        if (m > 2) {
+          bulge = s * b[L + 1];
+          b[L + 1] *= c;
+        }
+        live = bulge != 0.0;
+      } else if (act && live && kk >= 1 && kk < m - 1) {
+        double c, s, rr;
+        givens(b[L + kk - 1], bulge, c, s, rr);
+        b[L + kk - 1] = rr;
+        rot_sym(c, s, a, b, L + kk);
+        if (kk + 1 < m - 1) {
+          bulge = s * b[L + kk + 1];
+          b[L + kk + 1] *= c;
+        } else {
+          bulge = 0.0;
+        }
+        live = bulge != 0.0;
+      }
+      __syncwarp();
+    }
+  }
+  return __shfl_sync(0xffffffffu, Wtot, 0);
 }
 
 // --------------------------------------------------------------------------
@@ -105,7 +137,8 @@ __device__ double jacobi_from_nodes(const double *x, const double *wt, int n, do
 //   theta_i) (mu: eigenvalues of T without its first row and column).
 // A lane interleaves up to SPEC_ILP eigenvalues so that their independent
 // recurrences hide the FP64 latency.  The Omega-space Jacobi rebuild then
-// runs on lane 0 from the nodes and weights in shared memory.
+// runs from the nodes and weights in shared memory, its insertions pipelined
+// over the lanes.
 // --------------------------------------------------------------------------
 constexpr int SPEC_ILP = 8;
 constexpr double SCALE_UP = 0x1p+500, SCALE_DN = 0x1p-500;
@@ -283,9 +316,10 @@ __global__ void k_spectral_warp(const double *__restrict__ alpha, const double *
       atomicOr(status, ST_NOT_SPD);
     else
       atomicMin(min_theta_bits, (unsigned long long)__double_as_longlong(tmin));
-    const double W = jacobi_from_nodes(th, wt, n, ja, jb_);
-    jb.w0[v] = W;
   }
+  // alpha's rows are free now: the running weights of the rebuild
+  const double W = jacobi_from_nodes_warp(th, wt, n, ja, jb_, al);
+  if (lane == 0) jb.w0[v] = W;
   __syncwarp();
   double *ga = jb.a + (size_t)v * k, *gb2 = jb.b2 + (size_t)v * k;
   for (int i = lane; i < n; i += 32) {
