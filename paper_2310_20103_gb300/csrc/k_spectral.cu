@@ -142,11 +142,22 @@ __device__ double jacobi_from_nodes_warp(const double *x, const double *wt, int 
 // --------------------------------------------------------------------------
 constexpr int SPEC_ILP = 8;
 constexpr double SCALE_UP = 0x1p+500, SCALE_DN = 0x1p-500;
+// bit patterns of 2^500 and 2^-500 (biased exponents 1523 and 523)
+constexpr unsigned long long kUpBits = 1523ULL << 52, kDnBits = 523ULL << 52;
 
 // sign with the Sturm convention for zeros (a zero takes the opposite sign
-// of its predecessor)
+// of its predecessor): p < 0, or p == 0 and the predecessor was not
+// negative.  Tested on the bit pattern, and |p| against the rescaling
+// thresholds likewise (bit patterns of non-negative doubles order like
+// their values), so that the bisection's FP64 pipe, on which GB300 runs
+// 2 lanes per SM clock, issues only the recurrence's subtract, multiply and
+// fused multiply-add; the comparisons go to the integer pipe.
 __device__ __forceinline__ bool neg_sturm(double p, bool prev_neg) {
-  return p < 0.0 || (p == 0.0 && !prev_neg);
+  const long long bits = __double_as_longlong(p);
+  return ((bits << 1) == 0) ? !prev_neg : (bits < 0);
+}
+__device__ __forceinline__ unsigned long long abs_bits(double p) {
+  return (unsigned long long)__double_as_longlong(p) & 0x7fffffffffffffffULL;
 }
 
 __global__ void k_spectral_warp(const double *__restrict__ alpha, const double *__restrict__ beta,
@@ -228,10 +239,10 @@ __global__ void k_spectral_warp(const double *__restrict__ alpha, const double *
           pn[r] = ng;
           p0[r] = p1[r];
           p1[r] = p2;
-          if (fabs(p2) > SCALE_UP) {
+          if (abs_bits(p2) > kUpBits) {
             p0[r] *= SCALE_DN;
             p1[r] *= SCALE_DN;
-          } else if (fabs(p2) < SCALE_DN && fabs(p0[r]) < SCALE_DN) {
+          } else if (abs_bits(p2) < kDnBits && abs_bits(p0[r]) < kDnBits) {
             p0[r] *= SCALE_UP;
             p1[r] *= SCALE_UP;
           }
