@@ -2502,8 +2502,12 @@ static lgw_status backward_impl(lgw_handle *h, const lgw_system *sys, const lgw_
       size_t held = 0;
       for (auto &kv : h->bufs) held += kv.second.n;
       const int cs = std::min(ci, k), nseg = (k + ci - 1) / ci;
+      // exact form: checkpoints, the recomputation window, ubar_j, the qbar ring
+      // and row buffers, plus (polynomial form) Clenshaw's 2 g + 1 vectors
+      const int gp = poly ? poly->g : 0;
       const double per_vec =
-          exact ? 8.0 * (2 * nseg + 2 * cs + 12) * N + 16.0 * cs * A + 40.0 * k * k
+          exact ? 8.0 * (2 * nseg + 2 * cs + 12 + 2 * gp + 1) * N + 16.0 * (cs + gp) * A +
+                      40.0 * k * k
                 : 8.0 * (k + 1) * N + (tc ? 4.0 * k * N : 0.0) + 20.0 * k * A + 48.0 * N +
                       40.0 * k * k;
       const double budget = 0.5 * (double)(fr + held);
