@@ -160,6 +160,25 @@ def test_exact_central_differences_differentiation_shapes(L, handle, k, ckpt):
             assert ana == pytest.approx(fd, rel=1e-5, abs=2e-9), (which, trial)
 
 
+@pytest.mark.parametrize("ckpt", [0, 2])
+def test_exact_reverse_at_breakdown_vs_oracle(L, handle, ckpt):
+    """L nonzero on three pair rows: every start vector lies in a
+    3-dimensional invariant subspace of C, so the recurrence stops at
+    k_eff = 3 of k = 8 (with interval 2 the checkpoints straddle the stop).
+    The k_eff-step gradient (pinned by central differences in the oracle
+    tests) against the oracle, 1e-9."""
+    wl = gi.make_workload("bd", 2, 6, 4, [1, 2], list(range(8)), 61, 9, k=8,
+                          sigma_L=0.3, sigma_M=0.5)
+    keep = np.zeros(wl.n_vc, dtype=bool)
+    keep[[0, 3, 7]] = True
+    wl.L = np.where(keep[:, None], wl.L, 0.0)
+    dE = np.random.default_rng(98).normal(size=wl.n_t)
+    dLr, der = O.qp_gradient_recurrence(wl, dE, k=8)
+    dL, de = _grad(L, handle, wl, dE, _exact(8, ckpt))
+    _close(dL, dLr, 1e-9)
+    _close(de, der, 1e-9)
+
+
 @pytest.mark.parametrize("k,ckpt", [(8, 0), (24, 5)])
 def test_tda_exact_reverse_vs_oracle(L, handle, k, ckpt):
     wl = gi.tiny(k=k)

@@ -223,3 +223,44 @@ def test_poly_recurrence_gradient_matches_central_differences(g, k):
             # the interval [lo, hi] is a fixed input of the polynomial form
             fd = (dE @ _Ek_poly(wp, g, lo, hi, k) - dE @ _Ek_poly(wm, g, lo, hi, k)) / (2 * h)
             assert ana == pytest.approx(fd, rel=1e-6, abs=1e-9), (which, trial)
+
+
+def _breakdown_wl(kf=4.0):
+    """L nonzero on three pair rows only: C is block-diagonal and every start
+    vector b = D L M lies in that 3-dimensional invariant subspace, so the
+    recurrence stops (k_eff = 3) long before k."""
+    wl = gi.make_workload("bd", 2, 6, 4, [1, 2], list(range(8)), 61, 9, k=8,
+                          sigma_L=0.3, sigma_M=0.5, kernel_factor=kf)
+    keep = np.zeros(wl.n_vc, dtype=bool)
+    keep[[0, 3, 7]] = True
+    wl.L = np.where(keep[:, None], wl.L, 0.0)
+    return wl
+
+
+def test_recurrence_gradient_at_breakdown_matches_central_differences():
+    """At breakdown T_k stops at k_eff; a perturbation of L leaves the
+    invariant subspace and adds poles of weight O(h^2), which central
+    differences cancel.  The k_eff-step gradient must match."""
+    wl = _breakdown_wl()
+    _, _, (_, _, _, k_eff) = O.sigma_lanczos(wl, k=8, reorth=False)
+    assert set(int(x) for x in k_eff) == {3}
+    rng = np.random.default_rng(97)
+    dE = rng.normal(size=wl.n_t)
+    dL, deps = O.qp_gradient_recurrence(wl, dE, k=8)
+    h = 1e-6
+    for trial in range(2):
+        PL = rng.normal(size=wl.L.shape)
+        Pe = rng.normal(size=wl.eps.shape) * 0.1
+        for which in ("L", "eps"):
+            wp = gi.Workload(**wl.__dict__)
+            wm = gi.Workload(**wl.__dict__)
+            if which == "L":
+                wp.L = wl.L + h * PL
+                wm.L = wl.L - h * PL
+                ana = np.sum(dL * PL)
+            else:
+                wp.eps = wl.eps + h * Pe
+                wm.eps = wl.eps - h * Pe
+                ana = np.sum(deps * Pe)
+            fd = (dE @ _Ek(wp, 8, False) - dE @ _Ek(wm, 8, False)) / (2 * h)
+            assert ana == pytest.approx(fd, rel=1e-6, abs=1e-9), (which, trial)
