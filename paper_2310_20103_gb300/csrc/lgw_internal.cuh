@@ -72,6 +72,8 @@ struct VecCtx {
   int nslots;             // FP64 slots (k + 1 for the FP64 basis, else 3)
   int slot0;              // without the ring, q_j lives in slot j - slot0 (a window of
                           // the basis, used by the recomputation from a checkpoint)
+  int cpb;                // chunks per block of the assembly, axpy and normalisation
+                          // passes (0 or 1: one; each chunk keeps its own partial)
   double tol;
   const double *Delta2, *dsq, *cd;
   double *w;              // [Bs][N]
