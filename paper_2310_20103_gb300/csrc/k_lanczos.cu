@@ -141,7 +141,7 @@ __device__ __forceinline__ void assemble_w_chunk(const VecCtx &c, int j,
     const float *ph = j > 0 ? pair_hi(slot_ptr(c, j - 1), c) + voff : nullptr;
     const float *pl = j > 0 ? pair_lo(slot_ptr(c, j - 1), c) + voff : nullptr;
     float *wh = pair_hi(c.w, c) + voff, *wl = pair_lo(c.w, c) + voff;
-    const dfl nbj = df_from(-bj);
+    const dfl nbj = (j > 0 && c.nbeta_f) ? dfl{c.nbeta_f[b].x, c.nbeta_f[b].y} : df_from(-bj);
     float sh = 0.f, sl = 0.f;
 #pragma unroll
     for (int u4 = 0; u4 < 4; ++u4) {
@@ -169,7 +169,7 @@ __device__ __forceinline__ void assemble_w_chunk(const VecCtx &c, int j,
       df_dot_acc(sh, sl, q0, w0);
       df_dot_acc(sh, sl, q1, w1);
     }
-    const double ap = block_sum((double)sh + (double)sl, red);
+    const double ap = block_sum_to0((double)sh + (double)sl, red);
     if (threadIdx.x == 0) c.alpha_part[(size_t)chunk * c.Bs + b] = ap;
     return;
   }
@@ -194,7 +194,7 @@ __device__ __forceinline__ void assemble_w_chunk(const VecCtx &c, int j,
     *reinterpret_cast<double2 *>(w + e) = w2;
     ap = fma(q2.x, w2.x, fma(q2.y, w2.y, ap));
   }
-  ap = block_sum(ap, red);
+  ap = block_sum_to0(ap, red);
   if (threadIdx.x == 0) c.alpha_part[(size_t)chunk * c.Bs + b] = ap;
 }
 
@@ -204,7 +204,7 @@ __device__ __forceinline__ void assemble_w_chunk(const VecCtx &c, int j,
 // system's normalisation: 15.5 -> 9.4 ms per step, bit-identical).
 __device__ __forceinline__ int cpb_of(const VecCtx &c) { return c.cpb > 1 ? c.cpb : 1; }
 
-__global__ void __launch_bounds__(VEC_THREADS) k_assemble_w(VecCtx c, int j,
+__global__ void __launch_bounds__(VEC_THREADS, 8) k_assemble_w(VecCtx c, int j,
                                                            const float *__restrict__ ucd) {
   const int n = cpb_of(c), c0 = blockIdx.x * n, c1 = min(c.nchunks, c0 + n);
   for (int chunk = c0; chunk < c1; ++chunk) assemble_w_chunk(c, j, ucd, chunk, blockIdx.y);
@@ -223,6 +223,10 @@ __global__ void k_alpha_reduce(VecCtx c, int j) {
   if (lane == 0) {
     c.alpha[(size_t)(c.vec0 + b) * c.k + j] = s;
     c.amax[b] = fmax(c.amax[b], fabs(s));
+    if (c.nalpha_f) {
+      const dfl n = df_from(-s);
+      c.nalpha_f[b] = make_float2(n.h, n.l);
+    }
   }
 }
 
@@ -242,7 +246,7 @@ __device__ __forceinline__ void alpha_axpy_chunk(const VecCtx &c, int j, int chu
       const float *qh = pair_hi(slot_ptr(c, j), c) + voff;
       const float *ql = pair_lo(slot_ptr(c, j), c) + voff;
       float *wh = pair_hi(c.w, c) + voff, *wl = pair_lo(c.w, c) + voff;
-      const dfl nal = df_from(-alpha);
+      const dfl nal = c.nalpha_f ? dfl{c.nalpha_f[b].x, c.nalpha_f[b].y} : df_from(-alpha);
       float sh = 0.f, sl = 0.f;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -259,7 +263,7 @@ __device__ __forceinline__ void alpha_axpy_chunk(const VecCtx &c, int j, int chu
         df_dot_acc(sh, sl, w0, w0);
         df_dot_acc(sh, sl, w1, w1);
       }
-      const double nrm = block_sum((double)sh + (double)sl, red);
+      const double nrm = block_sum_to0((double)sh + (double)sl, red);
       if (threadIdx.x == 0) c.norm_a[(size_t)b * c.nchunks + chunk] = nrm;
       return;
     }
@@ -408,11 +412,16 @@ __global__ void k_beta_vec(VecCtx c, int j) {
     if (lane == 0) {
       c.beta[(size_t)v * c.k + j] = beta;
       c.betaj[b] = beta;
+      if (c.nbeta_f) {
+        const dfl n = df_from(-beta);
+        c.nbeta_f[b] = make_float2(n.h, n.l);
+      }
       if (stop) c.k_eff[v] = j + 1;
     }
     inv = (stop || !(beta > 0.0)) ? 0.0 : 1.0 / beta;
   } else if (lane == 0) {
     c.betaj[b] = 0.0;
+    if (c.nbeta_f) c.nbeta_f[b] = make_float2(-0.0f, 0.0f);
   }
   if (lane == 0) c.sinv[b] = inv;
 }

@@ -573,6 +573,8 @@ void run_lanczos(lgw_handle *h, const SysDev &s, const ProbView &pv, const Opts 
   // tensor cores without reorthogonalisation (the three-vector ring): the
   // slots and w as float pairs, the vector passes in double-float arithmetic
   c.pair = (tc && !reorth && !full_basis && poly == nullptr && s.d2lo != nullptr) ? 1 : 0;
+  c.nalpha_f = c.pair ? wsT<float2>(h, "nalpha_f", (size_t)Bs) : nullptr;
+  c.nbeta_f = c.pair ? wsT<float2>(h, "nbeta_f", (size_t)Bs) : nullptr;
   // float [Bs][N]: the split-basis epilogue output (c_K Delta^1/2 U) and, at
   // the start of each sub-batch, the tensor-core coupling vectors V = L M
   float *ucd_buf = tc ? wsT<float>(h, "ucd", (size_t)Bs * N) : nullptr;

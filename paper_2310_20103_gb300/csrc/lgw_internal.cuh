@@ -89,6 +89,9 @@ struct VecCtx {
   // float arithmetic on the FP32 pipe (tensor-core path without
   // reorthogonalisation, ring mode)
   int pair;
+  float2 *nalpha_f;       // [Bs] -alpha_j as a float pair (pair mode; written by the
+                          // alpha reduction, so the passes convert no FP64 per thread)
+  float2 *nbeta_f;        // [Bs] -beta_{j+1} as a float pair (pair mode; k_beta_vec)
   const float *ucd;       // [Bs][N] c_K Delta^1/2 (L y) from the FP32 epilogue (kblk_f32), or null
                           // (then w holds the full FP64 epilogue result)
   float *dq2_part;        // [Bs][nchunks] partials of sum Delta^2 q_j^2 (FP32); with
@@ -162,6 +165,22 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   __syncthreads();
   double s = 0.0;
   for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+// The same sum in the same order, formed by thread 0 only (the value is
+// valid there alone): passes that only write a partial save the other
+// threads' share of the final FP64 additions, which load GB300's narrow FP64
+// pipe.
+__device__ __forceinline__ double block_sum_to0(double v, double *red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) s += red[i];
   return s;
 }
 
