@@ -36,6 +36,26 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def test_every_declared_symbol_has_a_binding_of_the_same_name():
+    from paper_2310_20103_gb300 import lgw
+    missing = [n for n in _declared() if not callable(getattr(lgw, n, None))]
+    assert not missing, missing
+
+
+def test_null_handle_is_rejected_by_the_backward_entry_points(lib):
+    """A NULL handle gives LGW_ERR_ARG before anything touches the device."""
+    P = ctypes.c_void_p
+    for name in ("lgw_sigma_c_backward", "lgw_sigma_c_tda_backward"):
+        fn = getattr(lib, name)
+        fn.argtypes = [P] * 7
+        fn.restype = ctypes.c_int
+        assert fn(None, None, None, None, None, None, None) == 1, name
+    fn = lib.lgw_sigma_c_poly_backward
+    fn.argtypes = [P] * 8
+    fn.restype = ctypes.c_int
+    assert fn(None, None, None, None, None, None, None, None) == 1
+
+
 def test_status_strings(lib):
     lib.lgw_status_string.restype = ctypes.c_char_p
     lib.lgw_status_string.argtypes = [ctypes.c_int]
